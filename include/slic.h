@@ -1,0 +1,151 @@
+/*
+ * slic.h -- C ABI of libslicgb.so: SLIC superpixel segmentation on one
+ * NVIDIA GB300 (sm_103a), following gSLICr (Ren, Prisacariu and Reid,
+ * "gSLICr: SLIC superpixels at over 250Hz", arXiv 1509.04232).
+ *
+ * Conventions for every call
+ * --------------------------
+ *  - Pointers named d_* are DEVICE pointers on the current CUDA device,
+ *    owned by the caller; the library never frees them. Pointers named h_*
+ *    are host pointers. `stream` is a cudaStream_t passed as void* (NULL =
+ *    the legacy default stream).
+ *  - Work is enqueued on `stream` and the call returns without waiting for
+ *    it, unless the description says otherwise. Buffers must stay valid
+ *    until the stream reaches that work.
+ *  - A handle owns its device scratch (allocated in slic_create) and is not
+ *    thread-safe: use one handle per host thread and per stream.
+ *  - Every call returns a slic_status. On failure slic_last_error() gives a
+ *    one-line reason. CUDA launch errors map to SLIC_ERR_CUDA.
+ *  - Images are 8-bit R,G,B (in_channels = 3) or R,G,B,A (in_channels = 4,
+ *    alpha ignored), row-major, rows of width*in_channels bytes.
+ *  - Labels are int32 [height][width]; label k = r*ns_c + c names the grid
+ *    cell (column c, row r) the centre started in.
+ *  - Centres are float [K_eff][6] = (f0, f1, f2, x, y, count) where
+ *    (f0,f1,f2) = (L*, a*, b*) for SLIC_CIELAB, K_eff = ns_c*ns_r.
+ *  - Features are float [3][height][width] (planar).
+ */
+#ifndef SLIC_H
+#define SLIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slic_ctx *slic_handle;
+
+typedef enum {
+    SLIC_OK = 0,
+    SLIC_ERR_INVALID = -1, /* bad argument or size; nothing was enqueued */
+    SLIC_ERR_NOMEM = -2,   /* device or host allocation failed */
+    SLIC_ERR_CUDA = -3,    /* a CUDA call or kernel launch failed */
+    SLIC_ERR_TIMEOUT = -4, /* a bounded device-side wait gave up */
+    SLIC_ERR_STATE = -5    /* call not valid in the handle's state */
+} slic_status;
+
+/* Feature space of Sec. 2 / Sec. 4 (the listing's color_space setting). */
+typedef enum {
+    SLIC_CIELAB = 0, /* sRGB (IEC 61966-2-1) -> CIE 1976 L*a*b*, D65 */
+    SLIC_RGB = 1,    /* raw R,G,B bytes as floats */
+    SLIC_XYZ = 2     /* CIE XYZ (D65) x 100 */
+} slic_color_space;
+
+/* Problem statement of Sec. 2 (K or S, m) and the settings of the Sec. 4
+   listing (color_space, no_iters, do_enforce_connectivity). */
+typedef struct {
+    int width, height;        /* > 0 */
+    int K;                    /* desired superpixel count, used when S == 0:
+                                 S = max(1, round(sqrt(width*height/K))) */
+    int S;                    /* grid interval in pixels; > 0 overrides K */
+    float m;                  /* compactness, >= 0 (Eq. 1) */
+    int iterations;           /* >= 0: centre updates after the first assignment */
+    int color_space;          /* slic_color_space */
+    int enforce_connectivity; /* 0 or 1 */
+    int in_channels;          /* 3 or 4 */
+} slic_params;
+
+/* Create a handle for one image geometry; allocates the handle's device
+   scratch on the current device. Grid (Sec. 2): ns_c = ceil(width/S),
+   ns_r = ceil(height/S). Returns SLIC_ERR_INVALID for bad params (also
+   when K_eff exceeds 2^26 or an image exceeds 2^31 pixels). */
+slic_status slic_create(const slic_params *params, slic_handle *out);
+
+/* Release the handle and its scratch (waits for the device to finish any
+   work of this handle first). NULL is accepted. */
+slic_status slic_destroy(slic_handle h);
+
+/* Grid of the handle: S, ns_c, ns_r (any may be NULL). */
+slic_status slic_grid(slic_handle h, int *S, int *ns_c, int *ns_r);
+
+/* Whole segmentation, in the order of the Sec. 4 Perform_Segmentation
+   listing: colour conversion (Sec. 3 "Image space conversion"), grid
+   initialisation ("Cluster center initialisation"), assignment (Eq. 1,
+   "Finding the cluster associations"), `iterations` x {update ("Updating
+   the cluster center"), assignment}, then two connectivity passes ("Enforce
+   connectivity") when enabled.
+     d_image    uint8 [height][width][in_channels]
+     d_labels   int32 [height][width], output
+     d_centres  float [K_eff][6], output: the centres the final labels were
+                assigned against (count = members in that assignment's
+                input partition; 0 for an empty cluster, which keeps its
+                previous position and colour)
+   When slic_set_init_centres() armed initial centres, they replace the grid
+   initialisation for this call only. */
+slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_labels, float *d_centres,
+                         void *stream);
+
+/* Use d_init [K_eff][6] (e.g. the previous video frame's centres) instead of
+   the grid initialisation on the next slic_segment call. The buffer is read
+   when that call's work runs. Pass NULL to disarm. */
+slic_status slic_set_init_centres(slic_handle h, const float *d_init);
+
+/* Sec. 3 "Image space conversion" only: d_features float [3][height][width]. */
+slic_status slic_convert(slic_handle h, const uint8_t *d_image, float *d_features, void *stream);
+
+/* Sec. 3 "Cluster center initialisation" only, from converted features. */
+slic_status slic_init_centres(slic_handle h, const float *d_features, float *d_centres, void *stream);
+
+/* One assignment pass (Eq. 1): every pixel takes the centre with the
+   smallest D_s among the (at most) nine centres of its own grid cell and
+   the eight around it; exact ties go to the first in scan order (dy outer,
+   dx inner). d_features float [3][H][W], d_centres float [K_eff][6],
+   d_labels int32 [H][W] output. */
+slic_status slic_assign(slic_handle h, const float *d_features, const float *d_centres, int32_t *d_labels,
+                        void *stream);
+
+/* One centre update (Sec. 3 "Updating the cluster center") from a label map:
+   centre k = mean (f0,f1,f2,x,y) of the pixels labelled k, count = their
+   number; a centre with no pixels keeps d_centres_in's values and gets
+   count 0. Labels must lie in [0, K_eff) (else the result is undefined for
+   those pixels; they are ignored). d_centres_in may equal d_centres_out. */
+slic_status slic_update(slic_handle h, const float *d_features, const int32_t *d_labels,
+                        const float *d_centres_in, float *d_centres_out, void *stream);
+
+/* One connectivity pass (Sec. 3 "Enforce connectivity"): a pixel whose
+   every in-image 4-neighbour has a different label takes the most frequent
+   neighbour label (ties: earliest of left, up, right, down). Reads d_in,
+   writes d_out; they must not overlap. */
+slic_status slic_connectivity_pass(slic_handle h, const int32_t *d_in, int32_t *d_out, void *stream);
+
+/* Kernel launches enqueued by this handle since creation (all calls). */
+slic_status slic_launch_count(slic_handle h, long long *count);
+
+/* Per-kernel device-time accounting, for measurement. When enabled, the
+   library records a CUDA event pair around every assignment-kernel launch
+   on the launching stream. slic_profile_read synchronises those events and
+   returns the summed duration (ms) and launch count since the last read
+   (or since enabling), then resets them. */
+slic_status slic_profile_enable(slic_handle h, int enable);
+slic_status slic_profile_read(slic_handle h, double *assign_ms, long long *assign_launches);
+
+/* Reason for the last failure on this handle (or of the last failed
+   slic_create on this thread when h is NULL). Never NULL. */
+const char *slic_last_error(slic_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLIC_H */

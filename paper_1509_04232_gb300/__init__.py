@@ -1,0 +1,103 @@
+"""SLIC superpixels on one GB300 (gSLICr, arXiv 1509.04232), GB300-native.
+
+The compute path is ``libslicgb.so`` (hand-written sm_103a CUDA behind the C
+ABI in ``include/slic.h``). This package is its thin binding: the C-named
+functions in :mod:`._binding` plus :class:`Segmenter`, which only allocates
+output tensors with PyTorch and passes their device pointers and the current
+stream through. There is no CPU fallback: if the library is missing, calls
+raise.
+"""
+from __future__ import annotations
+
+from ._binding import (SLIC_CIELAB, SLIC_RGB, SLIC_XYZ, SlicError, library_path, slic_assign,  # noqa: F401
+                       slic_connectivity_pass, slic_convert, slic_create, slic_destroy, slic_grid,
+                       slic_init_centres, slic_last_error, slic_launch_count, slic_params,
+                       slic_profile_enable, slic_profile_read, slic_segment, slic_set_init_centres,
+                       slic_update)
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Segmenter:
+    """One image geometry and parameter set (Sec. 2: K or S, m; Sec. 4:
+    colour space, iterations, connectivity), owning a library handle."""
+
+    def __init__(self, width: int, height: int, *, K: int = 0, S: int = 0, m: float = 10.0,
+                 iterations: int = 10, color_space: int = SLIC_CIELAB, enforce_connectivity: bool = True,
+                 in_channels: int = 3):
+        self.params = slic_params(width, height, K, S, float(m), iterations, color_space,
+                                  int(bool(enforce_connectivity)), in_channels)
+        self.handle = slic_create(self.params)
+        self.S, self.ns_c, self.ns_r = slic_grid(self.handle)
+        self.K_eff = self.ns_c * self.ns_r
+
+    def close(self):
+        if getattr(self, "handle", None):
+            slic_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_image(self, image):
+        p = self.params
+        if (not image.is_cuda or image.dtype.itemsize != 1 or tuple(image.shape) != (p.height, p.width, p.in_channels)
+                or not image.is_contiguous()):
+            raise ValueError(f"image must be a contiguous uint8 CUDA tensor of shape "
+                             f"({p.height}, {p.width}, {p.in_channels})")
+
+    def segment(self, image, labels=None, centres=None, init_centres=None, stream=None):
+        """Labels int32 [H, W] and centres float32 [K_eff, 6] for one image."""
+        import torch
+        self._check_image(image)
+        dev = image.device
+        if labels is None:
+            labels = torch.empty((self.params.height, self.params.width), dtype=torch.int32, device=dev)
+        if centres is None:
+            centres = torch.empty((self.K_eff, 6), dtype=torch.float32, device=dev)
+        if init_centres is not None:
+            slic_set_init_centres(self.handle, init_centres.data_ptr())
+        slic_segment(self.handle, image.data_ptr(), labels.data_ptr(), centres.data_ptr(), _stream_handle(stream))
+        return labels, centres
+
+    def convert(self, image, stream=None):
+        import torch
+        self._check_image(image)
+        feat = torch.empty((3, self.params.height, self.params.width), dtype=torch.float32, device=image.device)
+        slic_convert(self.handle, image.data_ptr(), feat.data_ptr(), _stream_handle(stream))
+        return feat
+
+    def init_centres(self, features, stream=None):
+        import torch
+        out = torch.empty((self.K_eff, 6), dtype=torch.float32, device=features.device)
+        slic_init_centres(self.handle, features.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def assign(self, features, centres, stream=None):
+        import torch
+        labels = torch.empty((self.params.height, self.params.width), dtype=torch.int32, device=features.device)
+        slic_assign(self.handle, features.data_ptr(), centres.data_ptr(), labels.data_ptr(), _stream_handle(stream))
+        return labels
+
+    def update(self, features, labels, centres_in, stream=None):
+        out = centres_in.clone()
+        slic_update(self.handle, features.data_ptr(), labels.data_ptr(), centres_in.data_ptr(), out.data_ptr(),
+                    _stream_handle(stream))
+        return out
+
+    def connectivity_pass(self, labels, stream=None):
+        import torch
+        out = torch.empty_like(labels)
+        slic_connectivity_pass(self.handle, labels.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    @property
+    def launches(self) -> int:
+        return slic_launch_count(self.handle)

@@ -1,0 +1,148 @@
+"""ctypes binding of libslicgb.so (include/slic.h), argument marshalling only.
+
+Every function keeps its C name and takes plain integers for device
+pointers and streams (e.g. ``tensor.data_ptr()`` and
+``torch.cuda.current_stream().cuda_stream``). A non-zero status raises
+:class:`SlicError` carrying ``slic_last_error``. The library is loaded on
+first use; if it has not been built this raises instead of falling back to
+anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+SLIC_OK, SLIC_ERR_INVALID, SLIC_ERR_NOMEM, SLIC_ERR_CUDA, SLIC_ERR_TIMEOUT, SLIC_ERR_STATE = 0, -1, -2, -3, -4, -5
+SLIC_CIELAB, SLIC_RGB, SLIC_XYZ = 0, 1, 2
+
+_STATUS_NAMES = {0: "SLIC_OK", -1: "SLIC_ERR_INVALID", -2: "SLIC_ERR_NOMEM", -3: "SLIC_ERR_CUDA",
+                 -4: "SLIC_ERR_TIMEOUT", -5: "SLIC_ERR_STATE"}
+
+
+class SlicError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class slic_params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("K", ctypes.c_int), ("S", ctypes.c_int),
+                ("m", ctypes.c_float), ("iterations", ctypes.c_int), ("color_space", ctypes.c_int),
+                ("enforce_connectivity", ctypes.c_int), ("in_channels", ctypes.c_int)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+
+# name -> argtypes (all return slic_status, except slic_last_error)
+_SIGNATURES = {
+    "slic_create": [ctypes.POINTER(slic_params), ctypes.POINTER(_P)],
+    "slic_destroy": [_P],
+    "slic_grid": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "slic_segment": [_P, _P, _P, _P, _P],
+    "slic_set_init_centres": [_P, _P],
+    "slic_convert": [_P, _P, _P, _P],
+    "slic_init_centres": [_P, _P, _P, _P],
+    "slic_assign": [_P, _P, _P, _P, _P],
+    "slic_update": [_P, _P, _P, _P, _P, _P],
+    "slic_connectivity_pass": [_P, _P, _P, _P],
+    "slic_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
+    "slic_profile_enable": [_P, _I],
+    "slic_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
+}
+
+
+def library_path() -> str:
+    return _build.SLIC_LIB
+
+
+def lib():
+    """Load libslicgb.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_1509_04232_gb300.build.build_all() "
+                               "(the CUDA path has no CPU fallback)")
+        L = ctypes.CDLL(path)
+        for name, args in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.slic_last_error.argtypes = [_P]
+        L.slic_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def slic_last_error(h) -> str:
+    return lib().slic_last_error(h).decode()
+
+
+def _check(status: int, h):
+    if status != SLIC_OK:
+        raise SlicError(status, slic_last_error(h))
+
+
+def slic_create(params: slic_params) -> int:
+    h = _P()
+    _check(lib().slic_create(ctypes.byref(params), ctypes.byref(h)), None)
+    return h.value
+
+
+def slic_destroy(h: int) -> None:
+    _check(lib().slic_destroy(h), None)
+
+
+def slic_grid(h: int):
+    s, c, r = _I(), _I(), _I()
+    _check(lib().slic_grid(h, ctypes.byref(s), ctypes.byref(c), ctypes.byref(r)), h)
+    return s.value, c.value, r.value
+
+
+def slic_segment(h: int, d_image: int, d_labels: int, d_centres: int, stream: int = 0) -> None:
+    _check(lib().slic_segment(h, d_image, d_labels, d_centres, stream or None), h)
+
+
+def slic_set_init_centres(h: int, d_init: int | None) -> None:
+    _check(lib().slic_set_init_centres(h, d_init or None), h)
+
+
+def slic_convert(h: int, d_image: int, d_features: int, stream: int = 0) -> None:
+    _check(lib().slic_convert(h, d_image, d_features, stream or None), h)
+
+
+def slic_init_centres(h: int, d_features: int, d_centres: int, stream: int = 0) -> None:
+    _check(lib().slic_init_centres(h, d_features, d_centres, stream or None), h)
+
+
+def slic_assign(h: int, d_features: int, d_centres: int, d_labels: int, stream: int = 0) -> None:
+    _check(lib().slic_assign(h, d_features, d_centres, d_labels, stream or None), h)
+
+
+def slic_update(h: int, d_features: int, d_labels: int, d_centres_in: int, d_centres_out: int,
+                stream: int = 0) -> None:
+    _check(lib().slic_update(h, d_features, d_labels, d_centres_in, d_centres_out, stream or None), h)
+
+
+def slic_connectivity_pass(h: int, d_in: int, d_out: int, stream: int = 0) -> None:
+    _check(lib().slic_connectivity_pass(h, d_in, d_out, stream or None), h)
+
+
+def slic_launch_count(h: int) -> int:
+    n = ctypes.c_longlong()
+    _check(lib().slic_launch_count(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def slic_profile_enable(h: int, enable: bool) -> None:
+    _check(lib().slic_profile_enable(h, int(bool(enable))), h)
+
+
+def slic_profile_read(h: int):
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    _check(lib().slic_profile_read(h, ctypes.byref(ms), ctypes.byref(n)), h)
+    return ms.value, n.value

@@ -1,0 +1,379 @@
+// C ABI of libslicgb.so (declared and documented in include/slic.h).
+//
+// Host-side responsibilities: parameter validation, the grid of Sec. 2,
+// the colour constants (computed here in double precision from the sRGB and
+// CIE definitions, then rounded to float), device scratch ownership, the
+// stage order of the Sec. 4 Perform_Segmentation listing, launch accounting
+// and the optional per-kernel event timing.
+#include "slic.h"
+#include "slic_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+using namespace slicgb;
+
+struct slic_ctx {
+    slic_params p{};
+    int S = 0, ns_c = 0, ns_r = 0, K = 0, P = 0;
+    int device = 0;
+    float *feat = nullptr;        // 3 planes [H][P]
+    long long *acc = nullptr;     // [K][6]
+    int32_t *lbl_tmp = nullptr;   // [H][W] connectivity ping-pong
+    float fix_scale = 0.0f;
+    size_t smem_max = 0;
+    ConvConsts conv{};
+    const float *init_centres = nullptr;
+    long long launches = 0;
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    size_t ev_used = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+slic_status fail(slic_ctx *h, slic_status st, const std::string &msg) {
+    if (h)
+        h->err = msg;
+    else
+        g_create_error = msg;
+    return st;
+}
+
+slic_status cuda_fail(slic_ctx *h, cudaError_t e, const char *what) {
+    return fail(h, SLIC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// sRGB linearisation (IEC 61966-2-1) of every byte value.
+void make_lut(float lut[256]) {
+    for (int i = 0; i < 256; ++i) {
+        const double v = i / 255.0;
+        const double lin = v <= 0.04045 ? v / 12.92 : std::pow((v + 0.055) / 1.055, 2.4);
+        lut[i] = (float)lin;
+    }
+}
+
+// Linear sRGB -> XYZ (D65). For CIELAB each row is divided by the white
+// point (the row sum, i.e. the XYZ of linear white); for XYZ output the
+// rows are scaled by 100.
+ConvConsts make_conv(int color_space) {
+    static const double M[3][3] = {{0.4124564, 0.3575761, 0.1804375},
+                                   {0.2126729, 0.7151522, 0.0721750},
+                                   {0.0193339, 0.1191920, 0.9503041}};
+    ConvConsts c{};
+    for (int r = 0; r < 3; ++r) {
+        const double white = M[r][0] + M[r][1] + M[r][2];
+        for (int k = 0; k < 3; ++k) c.m[3 * r + k] = (float)(color_space == SLIC_XYZ ? 100.0 * M[r][k] : M[r][k] / white);
+    }
+    c.eps = (float)(216.0 / 24389.0);
+    c.k_slope = (float)((24389.0 / 27.0) / 116.0);
+    c.k_offset = (float)(16.0 / 116.0);
+    c.color_space = color_space;
+    return c;
+}
+
+std::mutex g_lut_mu;
+std::vector<int> g_lut_devices;
+std::vector<std::pair<int, size_t>> g_smem_set;  // device -> largest dynamic smem configured
+
+// Raise (never lower) the dynamic shared-memory limit of the assignment
+// kernels on this device, so handles with different S can coexist.
+cudaError_t ensure_smem(int dev, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_lut_mu);
+    for (auto &d : g_smem_set)
+        if (d.first == dev) {
+            if (d.second >= bytes) return cudaSuccess;
+            cudaError_t e = configure_kernels(bytes);
+            if (e == cudaSuccess) d.second = bytes;
+            return e;
+        }
+    cudaError_t e = configure_kernels(bytes);
+    if (e == cudaSuccess) g_smem_set.emplace_back(dev, bytes);
+    return e;
+}
+
+cudaError_t ensure_lut(int dev) {
+    std::lock_guard<std::mutex> lk(g_lut_mu);
+    for (int d : g_lut_devices)
+        if (d == dev) return cudaSuccess;
+    float lut[256];
+    make_lut(lut);
+    cudaError_t e = upload_lut(lut);
+    if (e == cudaSuccess) g_lut_devices.push_back(dev);
+    return e;
+}
+
+FrameArgs frame_args(slic_ctx *h, const uint8_t *rgb, float *feat, int P, const float *centres, int32_t *labels) {
+    FrameArgs a{};
+    a.conv = h->conv;
+    a.rgb = rgb;
+    a.feat = feat;
+    a.centres = centres;
+    a.centres_out = const_cast<float *>(centres);
+    a.acc = h->acc;
+    a.labels = labels;
+    a.W = h->p.width;
+    a.H = h->p.height;
+    a.P = P;
+    a.C = h->p.in_channels;
+    a.S = h->S;
+    a.ns_c = h->ns_c;
+    a.ns_r = h->ns_r;
+    a.w = h->p.m / (float)h->S;
+    a.win_max = assign_max_window(h->S, h->ns_c, h->ns_r);
+    a.direct_acc = assign_direct_acc(a.win_max) ? 1 : 0;
+    a.rgb_vec = (rgb && (h->p.width & 3) == 0 && ((uintptr_t)rgb & 15) == 0) ? 1 : 0;
+    a.labels_vec = (labels && (h->p.width & 3) == 0 && ((uintptr_t)labels & 15) == 0) ? 1 : 0;
+    a.mask_keys = h->S >= 4 ? 1 : 0;
+    a.fix_scale = h->fix_scale;
+    return a;
+}
+
+slic_status assign_launch(slic_ctx *h, const FrameArgs &a, bool first, bool last, bool store_feat, cudaStream_t s) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->profiling) {
+        if (h->ev_used == h->events.size()) {
+            cudaEvent_t x, y;
+            if (cudaEventCreate(&x) != cudaSuccess || cudaEventCreate(&y) != cudaSuccess)
+                return fail(h, SLIC_ERR_CUDA, "cudaEventCreate failed");
+            h->events.emplace_back(x, y);
+        }
+        e0 = h->events[h->ev_used].first;
+        e1 = h->events[h->ev_used].second;
+        ++h->ev_used;
+        cudaEventRecord(e0, s);
+    }
+    cudaError_t e = launch_assign(a, first, last, store_feat, assign_smem_bytes(assign_max_window(h->S, h->ns_c, h->ns_r), first), s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "assignment kernel launch");
+    ++h->launches;
+    if (h->profiling) cudaEventRecord(e1, s);
+    return SLIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+slic_status slic_create(const slic_params *params, slic_handle *out) {
+    if (!params || !out) return fail(nullptr, SLIC_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    const slic_params &p = *params;
+    if (p.width <= 0 || p.height <= 0 || p.width > (1 << 20) || p.height > (1 << 20) ||
+        (long long)p.width * p.height >= (1LL << 31))
+        return fail(nullptr, SLIC_ERR_INVALID, "width and height must be in [1, 2^20] with width*height < 2^31");
+    if (p.S < 0 || (p.S == 0 && p.K <= 0)) return fail(nullptr, SLIC_ERR_INVALID, "need S > 0 or K > 0");
+    if (!(p.m >= 0.0f) || !std::isfinite(p.m)) return fail(nullptr, SLIC_ERR_INVALID, "m must be finite and >= 0");
+    if (p.iterations < 0) return fail(nullptr, SLIC_ERR_INVALID, "iterations must be >= 0");
+    if (p.color_space < 0 || p.color_space > 2) return fail(nullptr, SLIC_ERR_INVALID, "unknown color_space");
+    if (p.in_channels != 3 && p.in_channels != 4) return fail(nullptr, SLIC_ERR_INVALID, "in_channels must be 3 or 4");
+    if (p.enforce_connectivity != 0 && p.enforce_connectivity != 1)
+        return fail(nullptr, SLIC_ERR_INVALID, "enforce_connectivity must be 0 or 1");
+
+    slic_ctx *h = new (std::nothrow) slic_ctx;
+    if (!h) return fail(nullptr, SLIC_ERR_NOMEM, "host allocation failed");
+    h->p = p;
+    int S = p.S;
+    if (S == 0) {
+        S = (int)std::lround(std::sqrt((double)p.width * (double)p.height / (double)p.K));
+        if (S < 1) S = 1;
+    }
+    h->S = S;
+    h->ns_c = (p.width + S - 1) / S;
+    h->ns_r = (p.height + S - 1) / S;
+    if ((long long)h->ns_c * h->ns_r > (1LL << 26)) {
+        delete h;
+        return fail(nullptr, SLIC_ERR_INVALID, "too many superpixels (K_eff > 2^26)");
+    }
+    h->K = h->ns_c * h->ns_r;
+    h->P = (p.width + 3) & ~3;
+    h->conv = make_conv(p.color_space);
+    h->fix_scale = p.color_space == SLIC_RGB ? 1.0f : kFixScaleFrac;
+
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = ensure_lut(h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(nullptr, SLIC_ERR_CUDA, std::string("CUDA initialisation: ") + cudaGetErrorString(e));
+    }
+    const size_t npix = (size_t)p.width * p.height;
+    if (cudaMalloc(&h->feat, sizeof(float) * 3 * (size_t)p.height * h->P) != cudaSuccess ||
+        cudaMalloc(&h->acc, sizeof(long long) * 6 * (size_t)h->K) != cudaSuccess ||
+        cudaMalloc(&h->lbl_tmp, sizeof(int32_t) * npix) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->feat);
+        cudaFree(h->acc);
+        cudaFree(h->lbl_tmp);
+        delete h;
+        return fail(nullptr, SLIC_ERR_NOMEM, "device allocation of scratch failed");
+    }
+    h->smem_max = assign_smem_bytes(assign_max_window(S, h->ns_c, h->ns_r), true);
+    e = ensure_smem(h->device, h->smem_max);
+    if (e != cudaSuccess) {
+        slic_destroy(h);
+        return fail(nullptr, SLIC_ERR_CUDA, std::string("kernel configuration: ") + cudaGetErrorString(e));
+    }
+    *out = h;
+    return SLIC_OK;
+}
+
+slic_status slic_destroy(slic_handle h) {
+    if (!h) return SLIC_OK;
+    cudaDeviceSynchronize();
+    cudaFree(h->feat);
+    cudaFree(h->acc);
+    cudaFree(h->lbl_tmp);
+    for (auto &ev : h->events) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    delete h;
+    return SLIC_OK;
+}
+
+slic_status slic_grid(slic_handle h, int *S, int *ns_c, int *ns_r) {
+    if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    if (S) *S = h->S;
+    if (ns_c) *ns_c = h->ns_c;
+    if (ns_r) *ns_r = h->ns_r;
+    return SLIC_OK;
+}
+
+slic_status slic_set_init_centres(slic_handle h, const float *d_init) {
+    if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    h->init_centres = d_init;
+    return SLIC_OK;
+}
+
+slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_labels, float *d_centres, void *stream) {
+    if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    if (!d_image || !d_labels || !d_centres) return fail(h, SLIC_ERR_INVALID, "NULL buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = h->p.iterations;
+    FrameArgs a = frame_args(h, d_image, h->feat, h->P, d_centres, d_labels);
+    cudaError_t e;
+    if (h->init_centres) {
+        if (h->init_centres != d_centres) {
+            e = cudaMemcpyAsync(d_centres, h->init_centres, sizeof(float) * 6 * (size_t)h->K,
+                                cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "copy of initial centres");
+        }
+        h->init_centres = nullptr;
+        e = launch_zero_acc(h->acc, h->K, s);
+    } else {
+        e = launch_init_from_rgb(a, d_centres, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "initialisation kernel launch");
+    ++h->launches;
+    for (int pass = 0; pass <= n; ++pass) {
+        if (pass > 0) {
+            e = launch_update(h->acc, d_centres, d_centres, h->K, 1.0 / h->fix_scale, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "update kernel launch");
+            ++h->launches;
+        }
+        slic_status st = assign_launch(h, a, pass == 0, pass == n, pass != n, s);
+        if (st != SLIC_OK) return st;
+    }
+    if (h->p.enforce_connectivity) {
+        e = launch_connectivity(d_labels, h->lbl_tmp, h->p.width, h->p.height, s);
+        if (e == cudaSuccess) e = launch_connectivity(h->lbl_tmp, d_labels, h->p.width, h->p.height, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "connectivity kernel launch");
+        h->launches += 2;
+    }
+    return SLIC_OK;
+}
+
+slic_status slic_convert(slic_handle h, const uint8_t *d_image, float *d_features, void *stream) {
+    if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    if (!d_image || !d_features) return fail(h, SLIC_ERR_INVALID, "NULL buffer");
+    cudaError_t e = launch_convert(h->conv, d_image, h->p.width, h->p.height, h->p.in_channels, d_features,
+                                   h->p.width, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "conversion kernel launch");
+    ++h->launches;
+    return SLIC_OK;
+}
+
+slic_status slic_init_centres(slic_handle h, const float *d_features, float *d_centres, void *stream) {
+    if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    if (!d_features || !d_centres) return fail(h, SLIC_ERR_INVALID, "NULL buffer");
+    cudaError_t e = launch_init_from_feat(d_features, h->p.width, h->p.height, h->p.width, h->S, h->ns_c, h->ns_r,
+                                          d_centres, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "initialisation kernel launch");
+    ++h->launches;
+    return SLIC_OK;
+}
+
+slic_status slic_assign(slic_handle h, const float *d_features, const float *d_centres, int32_t *d_labels,
+                        void *stream) {
+    if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    if (!d_features || !d_centres || !d_labels) return fail(h, SLIC_ERR_INVALID, "NULL buffer");
+    if (((uintptr_t)d_features & 15) != 0)
+        return fail(h, SLIC_ERR_INVALID, "features must be 16-byte aligned");
+    FrameArgs a = frame_args(h, nullptr, const_cast<float *>(d_features), h->p.width, d_centres, d_labels);
+    return assign_launch(h, a, false, true, false, (cudaStream_t)stream);
+}
+
+slic_status slic_update(slic_handle h, const float *d_features, const int32_t *d_labels, const float *d_centres_in,
+                        float *d_centres_out, void *stream) {
+    if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    if (!d_features || !d_labels || !d_centres_in || !d_centres_out) return fail(h, SLIC_ERR_INVALID, "NULL buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_zero_acc(h->acc, h->K, s);
+    if (e == cudaSuccess)
+        e = launch_accumulate_labels(d_features, h->p.width, h->p.height, h->p.width, d_labels, h->K, h->acc,
+                                     h->fix_scale, s);
+    if (e == cudaSuccess) e = launch_update(h->acc, d_centres_in, d_centres_out, h->K, 1.0 / h->fix_scale, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "update kernel launch");
+    h->launches += 3;
+    return SLIC_OK;
+}
+
+slic_status slic_connectivity_pass(slic_handle h, const int32_t *d_in, int32_t *d_out, void *stream) {
+    if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    if (!d_in || !d_out || d_in == d_out) return fail(h, SLIC_ERR_INVALID, "need distinct input and output");
+    cudaError_t e = launch_connectivity(d_in, d_out, h->p.width, h->p.height, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "connectivity kernel launch");
+    ++h->launches;
+    return SLIC_OK;
+}
+
+slic_status slic_launch_count(slic_handle h, long long *count) {
+    if (!h || !count) return fail(h, SLIC_ERR_INVALID, "NULL argument");
+    *count = h->launches;
+    return SLIC_OK;
+}
+
+slic_status slic_profile_enable(slic_handle h, int enable) {
+    if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    h->profiling = enable != 0;
+    h->ev_used = 0;
+    return SLIC_OK;
+}
+
+slic_status slic_profile_read(slic_handle h, double *assign_ms, long long *assign_launches) {
+    if (!h || !assign_ms || !assign_launches) return fail(h, SLIC_ERR_INVALID, "NULL argument");
+    double total = 0.0;
+    for (size_t i = 0; i < h->ev_used; ++i) {
+        cudaError_t e = cudaEventSynchronize(h->events[i].second);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->events[i].first, h->events[i].second);
+        if (e != cudaSuccess) return cuda_fail(h, e, "profile event");
+        total += ms;
+    }
+    *assign_ms = total;
+    *assign_launches = (long long)h->ev_used;
+    h->ev_used = 0;
+    return SLIC_OK;
+}
+
+const char *slic_last_error(slic_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

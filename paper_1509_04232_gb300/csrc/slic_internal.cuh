@@ -1,0 +1,77 @@
+// Internal declarations shared by the kernels and the C-ABI layer of
+// libslicgb.so. Not part of the public interface (that is include/slic.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace slicgb {
+
+// Fixed-point scale for the centre-update sums: CIELAB and XYZ features
+// (|f| < 128) are rounded to multiples of 2^-16 before summation, RGB
+// features are integers already (scale 1). Every partial sum is then an
+// exact integer, so the result does not depend on summation order, tiling
+// or batching.
+constexpr float kFixScaleFrac = 65536.0f;
+
+// Assignment tile: 32 x 32 pixels, 256 threads, 4 horizontally adjacent
+// pixels per thread.
+constexpr int kTileW = 32;
+constexpr int kTileH = 32;
+constexpr int kPPT = 4;
+constexpr int kThreads = (kTileW / kPPT) * kTileH;
+
+// Colour-conversion constants, computed on the host in double precision and
+// rounded to float (see slic_api.cu).
+struct ConvConsts {
+    float m[9];       // linear sRGB -> (X/Xn, Y/Yn, Z/Zn) for CIELAB, or XYZ*100
+    float eps;        // CIE epsilon 216/24389
+    float k_slope;    // kappa/116
+    float k_offset;   // 16/116
+    int color_space;  // 0 CIELAB, 1 RGB, 2 XYZ
+};
+
+// One frame's geometry and buffers as seen by the kernels.
+struct FrameArgs {
+    ConvConsts conv;
+    const uint8_t *rgb;     // [H][W][C]
+    float *feat;            // 3 planes [H][P]; plane stride H*P
+    const float *centres;   // [K][6] read by the assignment
+    float *centres_out;     // [K][6] written by the update
+    long long *acc;         // [K][6] fixed-point sums (l,a,b scaled; x,y,count exact)
+    int32_t *labels;        // [H][W]
+    int W, H, P, C, S, ns_c, ns_r;
+    float w;                // m / S
+    int win_max;            // largest centre window of any tile (sizes shared memory)
+    int direct_acc;         // 1: partial sums go straight to global atomics
+    int rgb_vec;            // 1: image rows allow 4-pixel vector loads
+    int labels_vec;         // 1: label rows allow 4-pixel vector stores
+    float fix_scale;        // fixed-point scale of the feature sums
+    int mask_keys;          // 1: a warp's keys fit a 64-bit mask (S >= 4)
+};
+
+// Shared memory for one assignment CTA whose tile spans at most win_n cells.
+size_t assign_smem_bytes(int win_n, bool first);
+int assign_max_window(int S, int ns_c, int ns_r);
+bool assign_direct_acc(int win_n);
+
+cudaError_t upload_lut(const float *lut256);
+cudaError_t configure_kernels(size_t max_smem);
+
+cudaError_t launch_init_from_rgb(const FrameArgs &a, float *centres, cudaStream_t s);
+cudaError_t launch_init_from_feat(const float *feat, int W, int H, int P, int S, int ns_c, int ns_r,
+                                  float *centres, cudaStream_t s);
+cudaError_t launch_zero_acc(long long *acc, int K, cudaStream_t s);
+// first: convert from RGB (and store features unless last); last: write labels
+// instead of accumulating.
+cudaError_t launch_assign(const FrameArgs &a, bool first, bool last, bool store_feat, size_t smem,
+                          cudaStream_t s);
+cudaError_t launch_update(long long *acc, const float *centres_in, float *centres_out, int K, double fix_inv,
+                          cudaStream_t s);
+cudaError_t launch_accumulate_labels(const float *feat, int W, int H, int P, const int32_t *labels, int K,
+                                     long long *acc, float fix_scale, cudaStream_t s);
+cudaError_t launch_convert(const ConvConsts &cc, const uint8_t *rgb, int W, int H, int C, float *feat, int P,
+                           cudaStream_t s);
+cudaError_t launch_connectivity(const int32_t *in, int32_t *out, int W, int H, cudaStream_t s);
+
+}  // namespace slicgb

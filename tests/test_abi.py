@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads without a GPU, exports every function that
+include/*.h declares, and validates arguments before touching CUDA."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_1509_04232_gb300 as pkg
+from paper_1509_04232_gb300 import _binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(slic_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build_slic()
+    return _binding.lib()
+
+
+def test_header_declares_the_core_calls():
+    names = _declared_functions()
+    for core in ("slic_create", "slic_segment", "slic_destroy", "slic_grid", "slic_last_error"):
+        assert core in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    for n in _declared_functions():
+        assert hasattr(_binding, n), n
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(width=0), "width"),
+    (dict(height=-3), "width"),
+    (dict(K=0, S=0), "S > 0 or K > 0"),
+    (dict(m=-1.0), "m must"),
+    (dict(iterations=-1), "iterations"),
+    (dict(color_space=7), "color_space"),
+    (dict(in_channels=2), "in_channels"),
+    (dict(enforce_connectivity=2), "enforce_connectivity"),
+    (dict(width=1 << 21), "width"),
+])
+def test_invalid_params_rejected_without_cuda(lib, kw, msg):
+    base = dict(width=64, height=48, K=12, S=0, m=10.0, iterations=3, color_space=0,
+                enforce_connectivity=1, in_channels=3)
+    base.update(kw)
+    p = _binding.slic_params(**base)
+    with pytest.raises(pkg.SlicError) as ei:
+        pkg.slic_create(p)
+    assert ei.value.status == _binding.SLIC_ERR_INVALID
+    assert msg in str(ei.value)
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.slic_grid(None, None, None, None) == _binding.SLIC_ERR_INVALID
+    assert lib.slic_segment(None, None, None, None, None) == _binding.SLIC_ERR_INVALID
+    assert lib.slic_destroy(None) == _binding.SLIC_OK
+    assert b"NULL" in lib.slic_last_error(None)
+
+
+def test_library_has_no_torch_dependency(lib):
+    # the boundary is plain C: nothing from libtorch/libc10 may be needed
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--undefined-only", build.SLIC_LIB], capture_output=True, text=True).stdout
+    assert "c10" not in out and "torch" not in out
