@@ -132,11 +132,13 @@ slic_status slic_connectivity_pass(slic_handle h, const int32_t *d_in, int32_t *
 /* Kernel launches enqueued by this handle since creation (all calls). */
 slic_status slic_launch_count(slic_handle h, long long *count);
 
-/* Per-kernel device-time accounting, for measurement. When enabled, the
-   library records a CUDA event pair around every assignment-kernel launch
-   on the launching stream. slic_profile_read synchronises those events and
-   returns the summed duration (ms) and launch count since the last read
-   (or since enabling), then resets them. */
+/* Per-kernel device-time accounting, for measurement. Enabling (from the
+   disabled state) forgets earlier records; while enabled, the library
+   records a CUDA event pair around every assignment-kernel launch it
+   enqueues, on the launching stream (inside a stream capture these become
+   event-record nodes that every replay of the graph re-records).
+   slic_profile_read waits for those events and returns the summed duration
+   (ms) of the recorded pairs and their number; it does not reset them. */
 slic_status slic_profile_enable(slic_handle h, int enable);
 slic_status slic_profile_read(slic_handle h, double *assign_ms, long long *assign_launches);
 

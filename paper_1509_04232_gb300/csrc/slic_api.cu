@@ -133,7 +133,6 @@ FrameArgs frame_args(slic_ctx *h, const uint8_t *rgb, float *feat, int P, const 
     a.direct_acc = assign_direct_acc(a.win_max) ? 1 : 0;
     a.rgb_vec = (rgb && (h->p.width & 3) == 0 && ((uintptr_t)rgb & 15) == 0) ? 1 : 0;
     a.labels_vec = (labels && (h->p.width & 3) == 0 && ((uintptr_t)labels & 15) == 0) ? 1 : 0;
-    a.mask_keys = h->S >= 4 ? 1 : 0;
     a.fix_scale = h->fix_scale;
     return a;
 }
@@ -150,12 +149,13 @@ slic_status assign_launch(slic_ctx *h, const FrameArgs &a, bool first, bool last
         e0 = h->events[h->ev_used].first;
         e1 = h->events[h->ev_used].second;
         ++h->ev_used;
-        cudaEventRecord(e0, s);
+        // External records become event-record nodes under stream capture.
+        cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
     }
     cudaError_t e = launch_assign(a, first, last, store_feat, assign_smem_bytes(assign_max_window(h->S, h->ns_c, h->ns_r), first), s);
     if (e != cudaSuccess) return cuda_fail(h, e, "assignment kernel launch");
     ++h->launches;
-    if (h->profiling) cudaEventRecord(e1, s);
+    if (h->profiling) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
     return SLIC_OK;
 }
 
@@ -353,8 +353,8 @@ slic_status slic_launch_count(slic_handle h, long long *count) {
 
 slic_status slic_profile_enable(slic_handle h, int enable) {
     if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    if (enable && !h->profiling) h->ev_used = 0;
     h->profiling = enable != 0;
-    h->ev_used = 0;
     return SLIC_OK;
 }
 
@@ -370,7 +370,6 @@ slic_status slic_profile_read(slic_handle h, double *assign_ms, long long *assig
     }
     *assign_ms = total;
     *assign_launches = (long long)h->ev_used;
-    h->ev_used = 0;
     return SLIC_OK;
 }
 

@@ -47,7 +47,6 @@ struct FrameArgs {
     int rgb_vec;            // 1: image rows allow 4-pixel vector loads
     int labels_vec;         // 1: label rows allow 4-pixel vector stores
     float fix_scale;        // fixed-point scale of the feature sums
-    int mask_keys;          // 1: a warp's keys fit a 64-bit mask (S >= 4)
 };
 
 // Shared memory for one assignment CTA whose tile spans at most win_n cells.

@@ -163,11 +163,11 @@ int assign_max_window(int S, int ns_c, int ns_r) {
     return wx * wy;
 }
 
-bool assign_direct_acc(int win_n) { return (size_t)kWarps * win_n * 6 * sizeof(int) > kPrivateAccLimit; }
+bool assign_direct_acc(int win_n) { return (size_t)kWarps * win_n * 4 * sizeof(int) > kPrivateAccLimit; }
 
 size_t assign_smem_bytes(int win_n, bool first) {
     size_t b = ((size_t)win_n * 20 + 15) & ~(size_t)15;
-    if (!assign_direct_acc(win_n)) b += (size_t)kWarps * win_n * 6 * sizeof(int);
+    if (!assign_direct_acc(win_n)) b += (size_t)kWarps * win_n * 4 * sizeof(int);
     if (first) b += 256 * sizeof(float);
     return b;
 }
@@ -176,8 +176,8 @@ namespace {
 
 // Warp-aggregated accumulation of one value set per lane, keyed by window
 // index (key < 0: no contribution). All 32 lanes must call it.
-__device__ __forceinline__ void warp_accumulate(int key, const int (&v)[6], int *wacc, unsigned long long *gacc,
-                                                int wx0, int wy0, int wnx, int ns_c) {
+__device__ __forceinline__ void warp_accumulate(int key, const int (&v)[6], unsigned long long *gacc, int wx0,
+                                                int wy0, int wnx, int ns_c) {
     const int lane = threadIdx.x & 31;
     unsigned pending = __ballot_sync(kFull, key >= 0);
     while (pending) {
@@ -193,12 +193,8 @@ __device__ __forceinline__ void warp_accumulate(int key, const int (&v)[6], int 
         const int r5 = __reduce_add_sync(kFull, mine ? v[5] : 0);
         if (lane < 6) {
             const int val = lane == 0 ? r0 : lane == 1 ? r1 : lane == 2 ? r2 : lane == 3 ? r3 : lane == 4 ? r4 : r5;
-            if (gacc) {
-                const int cell = (wy0 + k / wnx) * ns_c + (wx0 + k % wnx);
-                atomicAdd(&gacc[(size_t)cell * 6 + lane], (unsigned long long)(long long)val);
-            } else {
-                wacc[k * 6 + lane] += val;
-            }
+            const int cell = (wy0 + k / wnx) * ns_c + (wx0 + k % wnx);
+            atomicAdd(&gacc[(size_t)cell * 6 + lane], (unsigned long long)(long long)val);
         }
         pending &= ~grp;
     }
@@ -209,11 +205,10 @@ __device__ __forceinline__ void warp_accumulate(int key, const int (&v)[6], int 
 namespace {
 
 // Merge runs of equal keys among a lane's kPPT pixels, then reduce each run
-// across the warp with a shuffle-driven key loop (all 32 lanes must call it).
-// Used when a warp's keys do not fit a 64-bit mask (S < 4) and for the
-// global-atomic path.
-__device__ __forceinline__ void accumulate_runs(const int (&key)[kPPT], int (&v)[kPPT][6], int *wacc,
-                                                unsigned long long *gacc, int wx0, int wy0, int wnx, int ns_c) {
+// across the warp with a shuffle-driven key loop and add it to the global
+// sums (all 32 lanes must call it).
+__device__ __forceinline__ void accumulate_runs(const int (&key)[kPPT], int (&v)[kPPT][6], unsigned long long *gacc,
+                                                int wx0, int wy0, int wnx, int ns_c) {
 #pragma unroll
     for (int j = kPPT - 2; j >= 0; --j) {
         if (key[j + 1] == key[j]) {
@@ -224,7 +219,7 @@ __device__ __forceinline__ void accumulate_runs(const int (&key)[kPPT], int (&v)
 #pragma unroll
     for (int j = 0; j < kPPT; ++j) {
         const int k = (j == 0 || key[j] != key[j - 1]) ? key[j] : -1;
-        if (__any_sync(kFull, k >= 0)) warp_accumulate(k, v[j], wacc, gacc, wx0, wy0, wnx, ns_c);
+        if (__any_sync(kFull, k >= 0)) warp_accumulate(k, v[j], gacc, wx0, wy0, wnx, ns_c);
     }
 }
 
@@ -254,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_f
     float4 *cA = reinterpret_cast<float4 *>(smem_raw);
     float *cY = reinterpret_cast<float *>(cA + nwin);
     int *wacc = reinterpret_cast<int *>(smem_raw + (((size_t)a.win_max * 20 + 15) & ~(size_t)15));
-    float *lut = reinterpret_cast<float *>(wacc + (direct ? 0 : (size_t)kWarps * a.win_max * 6));
+    float *lut = reinterpret_cast<float *>(wacc + (direct ? 0 : (size_t)kWarps * a.win_max * 4));
 
     // Out-of-grid window cells hold a sentinel centre whose D is ~1e18, so
     // the candidate loop needs no bounds checks (the own cell is always
@@ -271,9 +266,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_f
         }
     }
     if (!LAST && !direct) {
-        for (int i = tid; i < kWarps * nwin * 6; i += kThreads) {
-            const int q = i / (nwin * 6);
-            wacc[q * a.win_max * 6 + (i - q * nwin * 6)] = 0;
+        for (int i = tid; i < kWarps * nwin * 4; i += kThreads) {
+            const int q = i / (nwin * 4);
+            wacc[q * a.win_max * 4 + (i - q * nwin * 4)] = 0;
         }
     }
     if (FIRST) {
@@ -368,67 +363,53 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_f
         }
     }
 
-    // Eq. (1) over the nine centres of the pixel's 3x3 cell window, in scan
-    // order (dy outer, dx inner); strict '<' keeps the first of equal D.
-    // best[j] tracks the winner as its label (LAST) or its window index.
-    int best[kPPT];
+    // Eq. (1) over the nine centres of the pixel's 3x3 cell window. The
+    // candidate's scan position t (dy outer, dx inner) replaces the low 4
+    // bits of D (D >= 0, so its bits order like unsigned integers) and one
+    // integer min picks the winner: the smallest D, ties to the first in scan
+    // order. Values closer than 2^-19 relative also go to scan order.
+    unsigned bk[kPPT];
 #pragma unroll
-    for (int j = 0; j < kPPT; ++j) best[j] = -1;
+    for (int j = 0; j < kPPT; ++j) bk[j] = 0xFFFFFFFFu;
     if (row_ok) {
         const float w = a.w;
         const float fy = (float)y;
-        float bD[kPPT], fxs[kPPT];
+        float fxs[kPPT];
 #pragma unroll
-        for (int j = 0; j < kPPT; ++j) {
-            bD[j] = __int_as_float(0x7f800000);
-            fxs[j] = (float)(x + j);
-        }
+        for (int j = 0; j < kPPT; ++j) fxs[j] = (float)(x + j);
         const int rowoff = (pcy - wy0) * wnx - wx0;
-        const int lrow = pcy * a.ns_c;
-        if (SAME) {
-            const int own = rowoff + cx[0];
-            const int own_label = lrow + cx[0];
+#pragma unroll
+        for (int jj = 0; jj < (SAME ? 1 : kPPT); ++jj) {
+            const int own = rowoff + cx[jj];
 #pragma unroll
             for (int t = 0; t < 9; ++t) {
                 const int wi = own + (t / 3 - 1) * wnx + (t % 3 - 1);
-                const int val = LAST ? own_label + (t / 3 - 1) * a.ns_c + (t % 3 - 1) : wi;
                 const float4 c = cA[wi];
                 const float ddy = cY[wi] - fy;
                 const float ddy2 = ddy * ddy;
 #pragma unroll
-                for (int j = 0; j < kPPT; ++j) {
+                for (int j = (SAME ? 0 : jj); j < (SAME ? kPPT : jj + 1); ++j) {
                     const float ddx = c.w - fxs[j];
                     const float dl = c.x - f0[j], da = c.y - f1[j], db = c.z - f2[j];
                     const float d_lab = fsqrt_approx(fmaf(dl, dl, fmaf(da, da, db * db)));
                     const float D = fmaf(w, fsqrt_approx(fmaf(ddx, ddx, ddy2)), d_lab);
-                    const bool better = D < bD[j];
-                    bD[j] = better ? D : bD[j];
-                    best[j] = better ? val : best[j];
-                }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j) {
-                const int own = rowoff + cx[j];
-                const int own_label = lrow + cx[j];
-#pragma unroll
-                for (int t = 0; t < 9; ++t) {
-                    const int wi = own + (t / 3 - 1) * wnx + (t % 3 - 1);
-                    const int val = LAST ? own_label + (t / 3 - 1) * a.ns_c + (t % 3 - 1) : wi;
-                    const float4 c = cA[wi];
-                    const float ddy = cY[wi] - fy, ddx = c.w - fxs[j];
-                    const float dl = c.x - f0[j], da = c.y - f1[j], db = c.z - f2[j];
-                    const float d_lab = fsqrt_approx(fmaf(dl, dl, fmaf(da, da, db * db)));
-                    const float D = fmaf(w, fsqrt_approx(fmaf(ddx, ddx, ddy * ddy)), d_lab);
-                    const bool better = D < bD[j];
-                    bD[j] = better ? D : bD[j];
-                    best[j] = better ? val : best[j];
+                    bk[j] = min(bk[j], (__float_as_uint(D) & ~15u) | (unsigned)t);
                 }
             }
         }
+    }
+    // best[j]: the winner as a label (LAST) or as a window index; -1 for
+    // pixels outside the image.
+    int best[kPPT];
 #pragma unroll
-        for (int j = 0; j < kPPT; ++j)
-            if (x + j >= W) best[j] = -1;
+    for (int j = 0; j < kPPT; ++j) {
+        const int t = (int)(bk[j] & 15u);
+        const int dy = t / 3 - 1, dx = t % 3 - 1;
+        const bool ok = row_ok && (x + j < W);
+        if (LAST)
+            best[j] = ok ? (pcy + dy) * a.ns_c + cx[j] + dx : -1;
+        else
+            best[j] = ok ? (pcy + dy - wy0) * wnx + (cx[j] + dx - wx0) : -1;
     }
 
     if constexpr (LAST) {
@@ -441,90 +422,83 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_f
             }
         }
     } else {
-        // Partial update sums of this tile: each pixel adds its features
-        // (fixed point), coordinates and 1 to the centre it chose (key =
-        // window index). Runs of equal keys within a lane are merged first.
-        int v[kPPT][6];
+        // Partial update sums of this tile. Each lane merges runs of equal
+        // choices among its kPPT pixels and adds each run to its warp's
+        // private accumulators with four shared-memory atomics: the three
+        // feature sums (fixed point) and one word packing the x and y
+        // offsets from the tile origin and the count (a warp covers 128
+        // pixels, so the fields stay below 2^12, 2^12 and 2^8).
         const float fs = a.fix_scale;
+        if (!direct) {
+            unsigned v[kPPT][4];
 #pragma unroll
-        for (int j = 0; j < kPPT; ++j) {
-            v[j][0] = __float2int_rn(f0[j] * fs);
-            v[j][1] = __float2int_rn(f1[j] * fs);
-            v[j][2] = __float2int_rn(f2[j] * fs);
-            v[j][3] = x + j;
-            v[j][4] = y;
-            v[j][5] = 1;
-        }
-        int *my = wacc + (size_t)warp * a.win_max * 6;
-        if (a.mask_keys && !direct) {
-            // rk[j]: key of the run starting at pixel j (-1 if none); v[j]
-            // becomes that run's sums.
-            int rk[kPPT];
+            for (int j = 0; j < kPPT; ++j) {
+                v[j][0] = (unsigned)__float2int_rn(f0[j] * fs);
+                v[j][1] = (unsigned)__float2int_rn(f1[j] * fs);
+                v[j][2] = (unsigned)__float2int_rn(f2[j] * fs);
+                v[j][3] = (unsigned)(x + j - tx0) + ((unsigned)(y - ty0) << 12) + (1u << 24);
+            }
 #pragma unroll
             for (int j = kPPT - 2; j >= 0; --j) {
                 if (best[j + 1] == best[j]) {
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) v[j][c] += v[j + 1][c];
+                    for (int c = 0; c < 4; ++c) v[j][c] += v[j + 1][c];
                 }
             }
+            unsigned *my = reinterpret_cast<unsigned *>(wacc) + (size_t)warp * a.win_max * 4;
 #pragma unroll
-            for (int j = 0; j < kPPT; ++j) rk[j] = (j == 0 || best[j] != best[j - 1]) ? best[j] : -1;
-            bool multi = false;
+            for (int j = 0; j < kPPT; ++j) {
+                const int k = (j == 0 || best[j] != best[j - 1]) ? best[j] : -1;
+                if (k >= 0) {
 #pragma unroll
-            for (int j = 1; j < kPPT; ++j) multi |= rk[j] >= 0;
-            // The warp's keys lie in [wbase, wbase + 64): gather the set of
-            // keys present with two OR-reductions, then reduce each key's
-            // values with six ADD-reductions (uniform loop, no shuffles).
-            const int bx0 = tx0 + 16 * (warp & 1), by0 = ty0 + 8 * (warp >> 1);
-            const int wbase = (by0 / S - 1 - wy0) * wnx + (bx0 / S - 1 - wx0);
-            unsigned long long lm = 0;
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j)
-                if (rk[j] >= 0) lm |= 1ull << (rk[j] - wbase);
-            const unsigned lo = __reduce_or_sync(kFull, (unsigned)lm);
-            const unsigned hi = __reduce_or_sync(kFull, (unsigned)(lm >> 32));
-            unsigned long long mask = ((unsigned long long)hi << 32) | lo;
-            while (mask) {
-                const int k = wbase + __ffsll((long long)mask) - 1;
-                mask &= mask - 1;
-                int l[6];
-#pragma unroll
-                for (int c = 0; c < 6; ++c) l[c] = rk[0] == k ? v[0][c] : 0;
-                if (multi) {
-#pragma unroll
-                    for (int j = 1; j < kPPT; ++j) {
-                        if (rk[j] == k) {
-#pragma unroll
-                            for (int c = 0; c < 6; ++c) l[c] += v[j][c];
-                        }
-                    }
+                    for (int c = 0; c < 4; ++c) atomicAdd(&my[k * 4 + c], v[j][c]);
                 }
-                const int r0 = __reduce_add_sync(kFull, l[0]);
-                const int r1 = __reduce_add_sync(kFull, l[1]);
-                const int r2 = __reduce_add_sync(kFull, l[2]);
-                const int r3 = __reduce_add_sync(kFull, l[3]);
-                const int r4 = __reduce_add_sync(kFull, l[4]);
-                const int r5 = __reduce_add_sync(kFull, l[5]);
-                if (lane < 6)
-                    my[k * 6 + lane] += lane == 0 ? r0 : lane == 1 ? r1 : lane == 2 ? r2 : lane == 3 ? r3 : lane == 4 ? r4 : r5;
             }
-        } else {
-            unsigned long long *gacc = direct ? reinterpret_cast<unsigned long long *>(a.acc) : nullptr;
-            accumulate_runs(best, v, my, gacc, wx0, wy0, wnx, a.ns_c);
-        }
-        if (!direct) {
             __syncthreads();
-            for (int i = tid; i < nwin * 6; i += kThreads) {
-                long long t = 0;
-#pragma unroll
-                for (int q = 0; q < kWarps; ++q) t += wacc[(size_t)q * a.win_max * 6 + i];
-                if (t == 0) continue;
-                const int wi = i / 6;
+            // One thread per (window centre, word): add up the 8 warps in
+            // int64 and flush to the global sums.
+            const unsigned *all = reinterpret_cast<const unsigned *>(wacc);
+            for (int i = tid; i < nwin * 4; i += kThreads) {
+                const int wi = i >> 2, c = i & 3;
                 const int cy = wy0 + wi / wnx, cxg = wx0 + wi - (wi / wnx) * wnx;
                 unsigned long long *g =
                     reinterpret_cast<unsigned long long *>(a.acc) + ((size_t)cy * a.ns_c + cxg) * 6;
-                atomicAdd(&g[i - wi * 6], (unsigned long long)t);
+                if (c < 3) {
+                    long long t = 0;
+#pragma unroll
+                    for (int q = 0; q < kWarps; ++q) t += (int)all[(size_t)q * a.win_max * 4 + i];
+                    if (t != 0) atomicAdd(&g[c], (unsigned long long)t);
+                } else {
+                    long long xs = 0, ys = 0, n = 0;
+#pragma unroll
+                    for (int q = 0; q < kWarps; ++q) {
+                        const unsigned pk = all[(size_t)q * a.win_max * 4 + i];
+                        xs += pk & 0xFFFu;
+                        ys += (pk >> 12) & 0xFFFu;
+                        n += pk >> 24;
+                    }
+                    if (n != 0) {
+                        atomicAdd(&g[3], (unsigned long long)(xs + n * tx0));
+                        atomicAdd(&g[4], (unsigned long long)(ys + n * ty0));
+                        atomicAdd(&g[5], (unsigned long long)n);
+                    }
+                }
             }
+        } else {
+            // Very small S: the window is too large for private
+            // accumulators; reduce equal keys across the warp and add them to
+            // the global sums directly.
+            int v[kPPT][6];
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) {
+                v[j][0] = __float2int_rn(f0[j] * fs);
+                v[j][1] = __float2int_rn(f1[j] * fs);
+                v[j][2] = __float2int_rn(f2[j] * fs);
+                v[j][3] = x + j;
+                v[j][4] = y;
+                v[j][5] = 1;
+            }
+            accumulate_runs(best, v, reinterpret_cast<unsigned long long *>(a.acc), wx0, wy0, wnx, a.ns_c);
         }
     }
 }
