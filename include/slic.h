@@ -142,6 +142,27 @@ slic_status slic_launch_count(slic_handle h, long long *count);
 slic_status slic_profile_enable(slic_handle h, int enable);
 slic_status slic_profile_read(slic_handle h, double *assign_ms, long long *assign_launches);
 
+/* Allocation-free variant of slic_segment. The paper has no counterpart:
+   it exists for callers that cannot allocate device memory (code running
+   while a stream is captured into a CUDA graph, processes whose device
+   memory belongs to another allocator with a fixed budget, loops that
+   cannot afford the device synchronisation of cudaMalloc/cudaFree). It
+   takes the parameters directly (no handle) and the same image, label and
+   centre buffers, calls no cudaMalloc/cudaFree, and keeps its scratch in a
+   32 MiB array in device memory that each GPU loading this library holds
+   until the process exits. Images whose scratch (12*height*P + 48*K_eff +
+   4*width*height bytes, P = width rounded up to 4, each part rounded up to
+   256) exceeds 32 MiB are rejected with SLIC_ERR_INVALID; that admits e.g.
+   1280x720 or 1024x1024 at S >= 4. The first call on each device does a
+   one-time set-up (sRGB table upload, kernel attributes, device address of
+   the array) and should come before any stream capture. All calls share the
+   one array: calls whose work overlaps on the GPU (different streams, or
+   several host threads) race and corrupt each other's results; serialise
+   them. The sums left by the previous call are cleared by each call.
+   Errors are reported through slic_last_error(NULL). */
+slic_status slic_segment_noalloc(const slic_params *params, const uint8_t *d_image, int32_t *d_labels,
+                                 float *d_centres, void *stream);
+
 /* Reason for the last failure on this handle (or of the last failed
    slic_create on this thread when h is NULL). Never NULL. */
 const char *slic_last_error(slic_handle h);

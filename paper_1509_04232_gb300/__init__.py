@@ -12,8 +12,8 @@ from __future__ import annotations
 from ._binding import (SLIC_CIELAB, SLIC_RGB, SLIC_XYZ, SlicError, library_path, slic_assign,  # noqa: F401
                        slic_connectivity_pass, slic_convert, slic_create, slic_destroy, slic_grid,
                        slic_init_centres, slic_last_error, slic_launch_count, slic_params,
-                       slic_profile_enable, slic_profile_read, slic_segment, slic_set_init_centres,
-                       slic_update)
+                       slic_profile_enable, slic_profile_read, slic_segment, slic_segment_noalloc,
+                       slic_set_init_centres, slic_update)
 
 
 def _stream_handle(stream) -> int:

@@ -52,6 +52,7 @@ _SIGNATURES = {
     "slic_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
     "slic_profile_enable": [_P, _I],
     "slic_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
+    "slic_segment_noalloc": [ctypes.POINTER(slic_params), _P, _P, _P, _P],
 }
 
 
@@ -146,3 +147,9 @@ def slic_profile_read(h: int):
     ms, n = ctypes.c_double(), ctypes.c_longlong()
     _check(lib().slic_profile_read(h, ctypes.byref(ms), ctypes.byref(n)), h)
     return ms.value, n.value
+
+
+def slic_segment_noalloc(params: slic_params, d_image: int, d_labels: int, d_centres: int, stream: int = 0) -> None:
+    """Whole segmentation without any device allocation (scratch in a static
+    32 MiB device array shared by all calls; see include/slic.h)."""
+    _check(lib().slic_segment_noalloc(ctypes.byref(params), d_image, d_labels, d_centres, stream or None), None)

@@ -376,3 +376,127 @@ slic_status slic_profile_read(slic_handle h, double *assign_ms, long long *assig
 const char *slic_last_error(slic_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free segmentation (slic_segment_noalloc)
+//
+// For callers that must not allocate device memory at all: code that runs
+// while a stream is being captured into a CUDA graph (where cudaMalloc is not
+// permitted), processes whose device memory is owned by another allocator
+// under a fixed budget, and latency-critical loops that cannot afford the
+// implicit device synchronisation of cudaMalloc/cudaFree. The scratch lives
+// in one file-scope device array that every GPU which loads this library
+// holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB per device
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned char *g_static_addr[kMaxDevices] = {};
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Once per device, with that device current: the sRGB table, the kernels'
+// shared-memory limit and the device address of the static scratch (the
+// symbol itself is only a host-side stand-in).
+slic_status static_setup(int dev, size_t smem, unsigned char **addr) {
+    if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, SLIC_ERR_INVALID, "device ordinal out of range");
+    cudaError_t e = ensure_lut(dev);
+    if (e == cudaSuccess) e = ensure_smem(dev, smem);
+    if (e != cudaSuccess) return fail(nullptr, SLIC_ERR_CUDA, std::string("set-up: ") + cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(nullptr, SLIC_ERR_CUDA,
+                        std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
+        g_static_addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *addr = g_static_addr[dev];
+    return SLIC_OK;
+}
+
+}  // namespace
+
+extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uint8_t *d_image, int32_t *d_labels,
+                                            float *d_centres, void *stream) {
+    if (!params || !d_image || !d_labels || !d_centres) return fail(nullptr, SLIC_ERR_INVALID, "NULL argument");
+    const slic_params &p = *params;
+    if (p.width <= 0 || p.height <= 0 || p.width > (1 << 20) || p.height > (1 << 20) ||
+        (long long)p.width * p.height >= (1LL << 31))
+        return fail(nullptr, SLIC_ERR_INVALID, "width and height must be in [1, 2^20] with width*height < 2^31");
+    if (p.S < 0 || (p.S == 0 && p.K <= 0)) return fail(nullptr, SLIC_ERR_INVALID, "need S > 0 or K > 0");
+    if (!(p.m >= 0.0f) || !std::isfinite(p.m)) return fail(nullptr, SLIC_ERR_INVALID, "m must be finite and >= 0");
+    if (p.iterations < 0) return fail(nullptr, SLIC_ERR_INVALID, "iterations must be >= 0");
+    if (p.color_space < 0 || p.color_space > 2) return fail(nullptr, SLIC_ERR_INVALID, "unknown color_space");
+    if (p.in_channels != 3 && p.in_channels != 4) return fail(nullptr, SLIC_ERR_INVALID, "in_channels must be 3 or 4");
+    if (p.enforce_connectivity != 0 && p.enforce_connectivity != 1)
+        return fail(nullptr, SLIC_ERR_INVALID, "enforce_connectivity must be 0 or 1");
+    int S = p.S;
+    if (S == 0) {
+        S = (int)std::lround(std::sqrt((double)p.width * (double)p.height / (double)p.K));
+        if (S < 1) S = 1;
+    }
+    const int ns_c = (p.width + S - 1) / S, ns_r = (p.height + S - 1) / S;
+    const long long K = (long long)ns_c * ns_r;
+    const int P = (p.width + 3) & ~3;
+    // Scratch layout: features [3][H][P] f32 | sums [K][6] i64 | labels [H][W] i32.
+    const size_t feat_b = align256(sizeof(float) * 3 * (size_t)p.height * P);
+    const size_t acc_b = align256(sizeof(long long) * 6 * (size_t)K);
+    const size_t lbl_b = align256(sizeof(int32_t) * (size_t)p.width * p.height);
+    if (feat_b + acc_b + lbl_b > kStaticScratchBytes)
+        return fail(nullptr, SLIC_ERR_INVALID,
+                    "image too large for the static scratch: needs " + std::to_string(feat_b + acc_b + lbl_b) +
+                        " bytes, the limit is " + std::to_string(kStaticScratchBytes) + " (32 MiB)");
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, SLIC_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    const int win = assign_max_window(S, ns_c, ns_r);
+    unsigned char *base = nullptr;
+    slic_status st = static_setup(dev, assign_smem_bytes(win, true), &base);
+    if (st != SLIC_OK) return st;
+
+    FrameArgs a{};
+    a.conv = make_conv(p.color_space);
+    a.rgb = d_image;
+    a.feat = reinterpret_cast<float *>(base);
+    a.centres = d_centres;
+    a.centres_out = d_centres;
+    a.acc = reinterpret_cast<long long *>(base + feat_b);
+    a.labels = d_labels;
+    a.W = p.width;
+    a.H = p.height;
+    a.P = P;
+    a.C = p.in_channels;
+    a.S = S;
+    a.ns_c = ns_c;
+    a.ns_r = ns_r;
+    a.w = p.m / (float)S;
+    a.win_max = win;
+    a.direct_acc = assign_direct_acc(win) ? 1 : 0;
+    a.rgb_vec = ((p.width & 3) == 0 && ((uintptr_t)d_image & 15) == 0) ? 1 : 0;
+    a.labels_vec = ((p.width & 3) == 0 && ((uintptr_t)d_labels & 15) == 0) ? 1 : 0;
+    a.fix_scale = p.color_space == SLIC_RGB ? 1.0f : kFixScaleFrac;
+    int32_t *lbl_tmp = reinterpret_cast<int32_t *>(base + feat_b + acc_b);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t smem = assign_smem_bytes(win, true);
+
+    // Same stage order as slic_segment; the initialisation kernel zeroes the
+    // sums left in the shared array by the previous call.
+    e = launch_init_from_rgb(a, d_centres, s);
+    for (int pass = 0; e == cudaSuccess && pass <= p.iterations; ++pass) {
+        if (pass > 0) e = launch_update(a.acc, d_centres, d_centres, (int)K, 1.0 / a.fix_scale, s);
+        if (e == cudaSuccess) e = launch_assign(a, pass == 0, pass == p.iterations, false, smem, s);
+    }
+    if (e == cudaSuccess && p.enforce_connectivity) {
+        e = launch_connectivity(d_labels, lbl_tmp, p.width, p.height, s);
+        if (e == cudaSuccess) e = launch_connectivity(lbl_tmp, d_labels, p.width, p.height, s);
+    }
+    if (e != cudaSuccess) return fail(nullptr, SLIC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return SLIC_OK;
+}
