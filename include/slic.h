@@ -142,6 +142,63 @@ slic_status slic_launch_count(slic_handle h, long long *count);
 slic_status slic_profile_enable(slic_handle h, int enable);
 slic_status slic_profile_read(slic_handle h, double *assign_ms, long long *assign_launches);
 
+/* ---- Batches: many frames in one set of launches -------------------------
+   A batch segments n frames that may differ in size, S (or K), m, colour
+   space and channels (iterations and connectivity are shared) with one
+   launch per stage for all frames: the assignment kernel is persistent, its
+   grid sized to the GPU, looping over the 32x32 tiles of every frame. Per
+   frame the results are bit-identical to slic_segment's. The enqueued work
+   can be captured into a CUDA graph and replayed. */
+typedef struct slic_batch_ctx *slic_batch;
+
+/* params[f] describes frame f (same rules as slic_create); all frames need
+   the same iterations and enforce_connectivity. Allocates the batch's device
+   scratch (12*H*P + 48*K_eff + 4*W*H bytes per frame, 256-aligned parts). */
+slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batch *out);
+
+/* Bind the frames' buffers: host arrays of n device pointers, as in
+   slic_segment (d_images[f] uint8 image, d_labels[f] int32 labels,
+   d_centres[f] float [K_eff_f][6] centres). d_init may be NULL, or an array
+   whose entry f is NULL or a float [K_eff_f][6] set of initial centres used
+   instead of the grid initialisation (e.g. the previous video frame's
+   centres; d_init[f] may equal d_centres[f]). Waits for the device to be
+   idle, then uploads the frame table (synchronous). */
+slic_status slic_batch_set_buffers(slic_batch b, const uint8_t *const *d_images, int32_t *const *d_labels,
+                                   float *const *d_centres, const float *const *d_init);
+
+/* Segment every frame of the batch (Sec. 4 stage order, as slic_segment);
+   SLIC_ERR_STATE before slic_batch_set_buffers. */
+slic_status slic_batch_segment(slic_batch b, void *stream);
+
+/* Launch shape of the persistent assignment kernel: resident CTAs per SM
+   (0 = as many as fit). */
+slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm);
+
+/* Autotuner: time slic_batch_segment on the bound buffers for every launch
+   shape that fits (3 timed runs each, CUDA events on `stream`; this waits
+   for the device), keep the fastest, and append it to the JSON-lines file
+   cache_path (may be NULL) under a key of GPU name, frame count,
+   iterations and the distinct (width, height, S). When the key is already
+   in the file its entry is used without timing. The chosen value is
+   returned in *ctas_per_sm (may be NULL). */
+slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm);
+
+/* Pixels of all frames, kernel launches enqueued so far, CTAs per SM in use
+   (any may be NULL). */
+slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm);
+
+/* Device time of the batch's assignment launches, as slic_profile_enable /
+   slic_profile_read do for a handle. */
+slic_status slic_batch_profile_enable(slic_batch b, int enable);
+slic_status slic_batch_profile_read(slic_batch b, double *assign_ms, long long *assign_launches);
+
+/* Release the batch (waits for the device first). NULL is accepted. */
+slic_status slic_batch_destroy(slic_batch b);
+
+/* Reason for the last failure of this batch (or of the last failed
+   slic_batch_create on this thread when b is NULL). Never NULL. */
+const char *slic_batch_last_error(slic_batch b);
+
 /* Allocation-free variant of slic_segment. The paper has no counterpart:
    it exists for callers that cannot allocate device memory (code running
    while a stream is captured into a CUDA graph, processes whose device

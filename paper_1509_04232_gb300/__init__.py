@@ -10,6 +10,8 @@ raise.
 from __future__ import annotations
 
 from ._binding import (SLIC_CIELAB, SLIC_RGB, SLIC_XYZ, SlicError, library_path, slic_assign,  # noqa: F401
+                       slic_batch_autotune, slic_batch_create, slic_batch_destroy, slic_batch_info,
+                       slic_batch_last_error, slic_batch_profile_enable, slic_batch_profile_read, slic_batch_segment, slic_batch_set_buffers, slic_batch_set_tuning,
                        slic_connectivity_pass, slic_convert, slic_create, slic_destroy, slic_grid,
                        slic_init_centres, slic_last_error, slic_launch_count, slic_params,
                        slic_profile_enable, slic_profile_read, slic_segment, slic_segment_noalloc,
@@ -101,3 +103,64 @@ class Segmenter:
     @property
     def launches(self) -> int:
         return slic_launch_count(self.handle)
+
+
+class BatchSegmenter:
+    """Many frames (uneven size, S or K, m) segmented by one set of launches
+    per pass. ``frames`` is a sequence of dicts with keys width, height and
+    K or S, optionally m, color_space, in_channels; ``iterations`` and
+    ``enforce_connectivity`` are shared. Output tensors are allocated here
+    (``labels[f]`` int32 [H, W], ``centres[f]`` float32 [K_eff, 6])."""
+
+    def __init__(self, frames, *, iterations: int = 5, enforce_connectivity: bool = True, device=None):
+        import torch
+        self.params = [slic_params(f["width"], f["height"], f.get("K", 0), f.get("S", 0), float(f.get("m", 10.0)),
+                                   iterations, f.get("color_space", SLIC_CIELAB), int(bool(enforce_connectivity)),
+                                   f.get("in_channels", 3)) for f in frames]
+        self.handle = slic_batch_create(self.params)
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.labels, self.centres, self.K_eff = [], [], []
+        for p in self.params:
+            S = p.S if p.S > 0 else max(1, int(round((p.width * p.height / p.K) ** 0.5)))
+            k = (-(-p.width // S)) * (-(-p.height // S))
+            self.K_eff.append(k)
+            self.labels.append(torch.empty((p.height, p.width), dtype=torch.int32, device=dev))
+            self.centres.append(torch.empty((k, 6), dtype=torch.float32, device=dev))
+        self.images = None
+
+    def bind(self, images, init_centres=None):
+        """Bind input tensors (uint8 [H, W, C] CUDA, one per frame); keep them alive while in use."""
+        for img, p in zip(images, self.params):
+            if not img.is_cuda or not img.is_contiguous() or tuple(img.shape) != (p.height, p.width, p.in_channels):
+                raise ValueError("each image must be a contiguous uint8 CUDA tensor of its frame's shape")
+        self.images = list(images)
+        init = None
+        if init_centres is not None:
+            init = [t.data_ptr() if t is not None else None for t in init_centres]
+        slic_batch_set_buffers(self.handle, [t.data_ptr() for t in self.images], [t.data_ptr() for t in self.labels],
+                               [t.data_ptr() for t in self.centres], init)
+
+    def segment(self, stream=None):
+        slic_batch_segment(self.handle, _stream_handle(stream))
+        return self.labels, self.centres
+
+    def autotune(self, cache_path=None, stream=None) -> int:
+        return slic_batch_autotune(self.handle, cache_path, _stream_handle(stream))
+
+    def set_tuning(self, ctas_per_sm: int):
+        slic_batch_set_tuning(self.handle, ctas_per_sm)
+
+    @property
+    def info(self):
+        return slic_batch_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            slic_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -53,6 +53,16 @@ _SIGNATURES = {
     "slic_profile_enable": [_P, _I],
     "slic_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
     "slic_segment_noalloc": [ctypes.POINTER(slic_params), _P, _P, _P, _P],
+    "slic_batch_create": [ctypes.POINTER(slic_params), _I, ctypes.POINTER(_P)],
+    "slic_batch_set_buffers": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)],
+    "slic_batch_segment": [_P, _P],
+    "slic_batch_set_tuning": [_P, _I],
+    "slic_batch_autotune": [_P, ctypes.c_char_p, _P, ctypes.POINTER(_I)],
+    "slic_batch_info": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                        ctypes.POINTER(_I)],
+    "slic_batch_destroy": [_P],
+    "slic_batch_profile_enable": [_P, _I],
+    "slic_batch_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
 }
 
 
@@ -75,6 +85,8 @@ def lib():
             f.restype = ctypes.c_int
         L.slic_last_error.argtypes = [_P]
         L.slic_last_error.restype = ctypes.c_char_p
+        L.slic_batch_last_error.argtypes = [_P]
+        L.slic_batch_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -153,3 +165,67 @@ def slic_segment_noalloc(params: slic_params, d_image: int, d_labels: int, d_cen
     """Whole segmentation without any device allocation (scratch in a static
     32 MiB device array shared by all calls; see include/slic.h)."""
     _check(lib().slic_segment_noalloc(ctypes.byref(params), d_image, d_labels, d_centres, stream or None), None)
+
+
+# --- batches ---------------------------------------------------------------
+
+def slic_batch_last_error(b) -> str:
+    return lib().slic_batch_last_error(b).decode()
+
+
+def _bcheck(status: int, b):
+    if status != SLIC_OK:
+        raise SlicError(status, slic_batch_last_error(b))
+
+
+def _ptr_array(ptrs):
+    return (_P * len(ptrs))(*[p or None for p in ptrs])
+
+
+def slic_batch_create(params) -> int:
+    """params: sequence of slic_params, one per frame."""
+    arr = (slic_params * len(params))(*params)
+    b = _P()
+    _bcheck(lib().slic_batch_create(arr, len(params), ctypes.byref(b)), None)
+    return b.value
+
+
+def slic_batch_set_buffers(b: int, d_images, d_labels, d_centres, d_init=None) -> None:
+    init = _ptr_array(d_init) if d_init is not None else None
+    _bcheck(lib().slic_batch_set_buffers(b, _ptr_array(d_images), _ptr_array(d_labels), _ptr_array(d_centres),
+                                         init), b)
+
+
+def slic_batch_segment(b: int, stream: int = 0) -> None:
+    _bcheck(lib().slic_batch_segment(b, stream or None), b)
+
+
+def slic_batch_set_tuning(b: int, ctas_per_sm: int) -> None:
+    _bcheck(lib().slic_batch_set_tuning(b, int(ctas_per_sm)), b)
+
+
+def slic_batch_autotune(b: int, cache_path: str | None = None, stream: int = 0) -> int:
+    c = _I()
+    path = cache_path.encode() if cache_path else None
+    _bcheck(lib().slic_batch_autotune(b, path, stream or None, ctypes.byref(c)), b)
+    return c.value
+
+
+def slic_batch_info(b: int):
+    px, n, c = ctypes.c_longlong(), ctypes.c_longlong(), _I()
+    _bcheck(lib().slic_batch_info(b, ctypes.byref(px), ctypes.byref(n), ctypes.byref(c)), b)
+    return px.value, n.value, c.value
+
+
+def slic_batch_profile_enable(b: int, enable: bool) -> None:
+    _bcheck(lib().slic_batch_profile_enable(b, int(bool(enable))), b)
+
+
+def slic_batch_profile_read(b: int):
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    _bcheck(lib().slic_batch_profile_read(b, ctypes.byref(ms), ctypes.byref(n)), b)
+    return ms.value, n.value
+
+
+def slic_batch_destroy(b: int) -> None:
+    _bcheck(lib().slic_batch_destroy(b), None)

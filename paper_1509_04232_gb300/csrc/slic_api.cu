@@ -112,6 +112,19 @@ cudaError_t ensure_lut(int dev) {
     return e;
 }
 
+}  // namespace
+
+namespace slicgb {
+ConvConsts conv_consts(int color_space) { return make_conv(color_space); }
+cudaError_t device_setup(int dev, size_t smem) {
+    cudaError_t e = ensure_lut(dev);
+    if (e == cudaSuccess) e = ensure_smem(dev, smem);
+    return e;
+}
+}  // namespace slicgb
+
+namespace {
+
 FrameArgs frame_args(slic_ctx *h, const uint8_t *rgb, float *feat, int P, const float *centres, int32_t *labels) {
     FrameArgs a{};
     a.conv = h->conv;
@@ -129,6 +142,8 @@ FrameArgs frame_args(slic_ctx *h, const uint8_t *rgb, float *feat, int P, const 
     a.ns_c = h->ns_c;
     a.ns_r = h->ns_r;
     a.w = h->p.m / (float)h->S;
+    a.s_mul = h->S <= 2048 ? (unsigned)((0x100000000ULL + (unsigned)h->S - 1) / (unsigned)h->S) : 0u;
+    a.tiles_x = (h->p.width + kTileW - 1) / kTileW;
     a.win_max = assign_max_window(h->S, h->ns_c, h->ns_r);
     a.direct_acc = assign_direct_acc(a.win_max) ? 1 : 0;
     a.rgb_vec = (rgb && (h->p.width & 3) == 0 && ((uintptr_t)rgb & 15) == 0) ? 1 : 0;
@@ -269,7 +284,7 @@ slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_label
         h->init_centres = nullptr;
         e = launch_zero_acc(h->acc, h->K, s);
     } else {
-        e = launch_init_from_rgb(a, d_centres, s);
+        e = launch_init_from_rgb(a, s);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "initialisation kernel launch");
     ++h->launches;
@@ -482,13 +497,15 @@ extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uin
     a.rgb_vec = ((p.width & 3) == 0 && ((uintptr_t)d_image & 15) == 0) ? 1 : 0;
     a.labels_vec = ((p.width & 3) == 0 && ((uintptr_t)d_labels & 15) == 0) ? 1 : 0;
     a.fix_scale = p.color_space == SLIC_RGB ? 1.0f : kFixScaleFrac;
+    a.s_mul = S <= 2048 ? (unsigned)((0x100000000ULL + (unsigned)S - 1) / (unsigned)S) : 0u;
+    a.tiles_x = (p.width + kTileW - 1) / kTileW;
     int32_t *lbl_tmp = reinterpret_cast<int32_t *>(base + feat_b + acc_b);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t smem = assign_smem_bytes(win, true);
 
     // Same stage order as slic_segment; the initialisation kernel zeroes the
     // sums left in the shared array by the previous call.
-    e = launch_init_from_rgb(a, d_centres, s);
+    e = launch_init_from_rgb(a, s);
     for (int pass = 0; e == cudaSuccess && pass <= p.iterations; ++pass) {
         if (pass > 0) e = launch_update(a.acc, d_centres, d_centres, (int)K, 1.0 / a.fix_scale, s);
         if (e == cudaSuccess) e = launch_assign(a, pass == 0, pass == p.iterations, false, smem, s);

@@ -1,0 +1,388 @@
+// Batched C ABI of libslicgb.so (declared and documented in include/slic.h):
+// many frames of uneven resolution, superpixel size and compactness
+// segmented by one set of launches per pass (a persistent assignment kernel
+// loops over the tiles of all frames), plus the autotuner of its launch
+// shape.
+#include "slic.h"
+#include "slic_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
+using namespace slicgb;
+
+struct slic_batch_ctx {
+    int n = 0;
+    int iterations = 0;
+    int connectivity = 0;
+    int device = 0;
+    int sms = 0;
+    std::vector<slic_params> params;
+    std::vector<FrameArgs> frames;    // host copy of the descriptor table
+    FrameArgs *d_frames = nullptr;    // device copy
+    unsigned char *scratch = nullptr; // features, sums, connectivity labels of all frames
+    int total_tiles = 0, total_centres = 0, total_rows = 0, max_w = 0, win_max = 0;
+    long long total_pixels = 0;
+    bool same = true;
+    bool buffers_set = false;
+    size_t smem = 0;
+    int occupancy = 0;
+    int ctas_per_sm = 0;  // 0: occupancy
+    long long launches = 0;
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    size_t ev_used = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_error = "no error";
+
+slic_status bfail(slic_batch_ctx *b, slic_status st, const std::string &msg) {
+    if (b)
+        b->err = msg;
+    else
+        g_batch_error = msg;
+    return st;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+bool valid_params(const slic_params &p, std::string &why) {
+    if (p.width <= 0 || p.height <= 0 || p.width > (1 << 20) || p.height > (1 << 20) ||
+        (long long)p.width * p.height >= (1LL << 31)) {
+        why = "width and height must be in [1, 2^20] with width*height < 2^31";
+        return false;
+    }
+    if (p.S < 0 || (p.S == 0 && p.K <= 0)) { why = "need S > 0 or K > 0"; return false; }
+    if (!(p.m >= 0.0f) || !std::isfinite(p.m)) { why = "m must be finite and >= 0"; return false; }
+    if (p.iterations < 0) { why = "iterations must be >= 0"; return false; }
+    if (p.color_space < 0 || p.color_space > 2) { why = "unknown color_space"; return false; }
+    if (p.in_channels != 3 && p.in_channels != 4) { why = "in_channels must be 3 or 4"; return false; }
+    if (p.enforce_connectivity != 0 && p.enforce_connectivity != 1) {
+        why = "enforce_connectivity must be 0 or 1";
+        return false;
+    }
+    return true;
+}
+
+int grid_for(const slic_batch_ctx *b) {
+    const int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, b->occupancy) : b->occupancy;
+    return std::max(1, per_sm) * b->sms;
+}
+
+std::string tune_key(const slic_batch_ctx *b) {
+    cudaDeviceProp prop;
+    std::string gpu = cudaGetDeviceProperties(&prop, b->device) == cudaSuccess ? prop.name : "unknown";
+    std::set<std::tuple<int, int, int>> shapes;
+    for (const FrameArgs &f : b->frames) shapes.insert(std::make_tuple(f.W, f.H, f.S));
+    std::string key = gpu + "|frames=" + std::to_string(b->n) + "|it=" + std::to_string(b->iterations);
+    for (const auto &s : shapes)
+        key += "|" + std::to_string(std::get<0>(s)) + "x" + std::to_string(std::get<1>(s)) + "s" +
+               std::to_string(std::get<2>(s));
+    for (char &c : key)
+        if (c == '"' || c == '\\' || c == '\n') c = '_';
+    return key;
+}
+
+// Cache lines: {"key": "<key>", "ctas_per_sm": <int>, "ms": <float>}
+bool cache_lookup(const char *path, const std::string &key, int *ctas) {
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[4096];
+    bool found = false;
+    const std::string needle = "\"key\": \"" + key + "\"";
+    while (std::fgets(line, sizeof line, f)) {
+        if (std::strstr(line, needle.c_str())) {
+            const char *q = std::strstr(line, "\"ctas_per_sm\":");
+            int v = 0;
+            if (q && std::sscanf(q + 14, "%d", &v) == 1 && v > 0) {
+                *ctas = v;
+                found = true;
+            }
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, int ctas, float ms) {
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"ms\": %.4f}\n", key.c_str(), ctas, ms);
+    std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
+slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batch *out) {
+    if (!params || !out || n_frames <= 0) return bfail(nullptr, SLIC_ERR_INVALID, "need params, n_frames > 0 and out");
+    *out = nullptr;
+    std::string why;
+    for (int f = 0; f < n_frames; ++f) {
+        if (!valid_params(params[f], why)) return bfail(nullptr, SLIC_ERR_INVALID, "frame " + std::to_string(f) + ": " + why);
+        if (params[f].iterations != params[0].iterations ||
+            params[f].enforce_connectivity != params[0].enforce_connectivity)
+            return bfail(nullptr, SLIC_ERR_INVALID, "all frames of a batch need the same iterations and connectivity");
+    }
+    slic_batch_ctx *b = new (std::nothrow) slic_batch_ctx;
+    if (!b) return bfail(nullptr, SLIC_ERR_NOMEM, "host allocation failed");
+    b->n = n_frames;
+    b->iterations = params[0].iterations;
+    b->connectivity = params[0].enforce_connectivity;
+    b->params.assign(params, params + n_frames);
+    b->frames.resize(n_frames);
+
+    // Geometry, bases and the scratch layout.
+    size_t bytes = 0;
+    std::vector<size_t> off_feat(n_frames), off_acc(n_frames), off_lbl(n_frames);
+    long long tiles = 0, centres = 0, rows = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        const slic_params &p = params[f];
+        FrameArgs &a = b->frames[f];
+        std::memset(&a, 0, sizeof a);
+        int S = p.S;
+        if (S == 0) {
+            S = (int)std::lround(std::sqrt((double)p.width * (double)p.height / (double)p.K));
+            if (S < 1) S = 1;
+        }
+        a.conv = conv_consts(p.color_space);
+        a.W = p.width;
+        a.H = p.height;
+        a.P = (p.width + 3) & ~3;
+        a.C = p.in_channels;
+        a.S = S;
+        a.ns_c = (p.width + S - 1) / S;
+        a.ns_r = (p.height + S - 1) / S;
+        a.w = p.m / (float)S;
+        a.fix_scale = p.color_space == SLIC_RGB ? 1.0f : kFixScaleFrac;
+        a.s_mul = S <= 2048 ? (unsigned)((0x100000000ULL + (unsigned)S - 1) / (unsigned)S) : 0u;
+        a.tiles_x = (p.width + kTileW - 1) / kTileW;
+        a.tile_base = (int)tiles;
+        a.centre_base = (int)centres;
+        a.row_base = (int)rows;
+        tiles += (long long)a.tiles_x * ((p.height + kTileH - 1) / kTileH);
+        centres += (long long)a.ns_c * a.ns_r;
+        rows += p.height;
+        if (tiles >= (1LL << 31) || centres >= (1LL << 31) || rows >= (1LL << 31)) {
+            delete b;
+            return bfail(nullptr, SLIC_ERR_INVALID, "batch too large (tiles, centres or rows exceed 2^31)");
+        }
+        b->win_max = std::max(b->win_max, assign_max_window(S, a.ns_c, a.ns_r));
+        b->max_w = std::max(b->max_w, p.width);
+        b->same = b->same && (S % kPPT) == 0;
+        b->total_pixels += (long long)p.width * p.height;
+        off_feat[f] = bytes;
+        bytes += align256(sizeof(float) * 3 * (size_t)p.height * a.P);
+        off_acc[f] = bytes;
+        bytes += align256(sizeof(long long) * 6 * (size_t)a.ns_c * a.ns_r);
+        off_lbl[f] = bytes;
+        bytes += align256(sizeof(int32_t) * (size_t)p.width * p.height);
+    }
+    b->total_tiles = (int)tiles;
+    b->total_centres = (int)centres;
+    b->total_rows = (int)rows;
+    for (FrameArgs &a : b->frames) {
+        a.win_max = b->win_max;
+        a.direct_acc = assign_direct_acc(b->win_max) ? 1 : 0;
+    }
+    b->smem = assign_smem_bytes(b->win_max, true);
+
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = device_setup(b->device, b->smem);
+    if (e != cudaSuccess) {
+        delete b;
+        return bfail(nullptr, SLIC_ERR_CUDA, std::string("CUDA set-up: ") + cudaGetErrorString(e));
+    }
+    b->occupancy = std::max(1, assign_batch_occupancy(b->same, b->smem));
+    if (cudaMalloc(&b->scratch, bytes) != cudaSuccess ||
+        cudaMalloc(&b->d_frames, sizeof(FrameArgs) * n_frames) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b->scratch);
+        cudaFree(b->d_frames);
+        delete b;
+        return bfail(nullptr, SLIC_ERR_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    for (int f = 0; f < n_frames; ++f) {
+        FrameArgs &a = b->frames[f];
+        a.feat = reinterpret_cast<float *>(b->scratch + off_feat[f]);
+        a.acc = reinterpret_cast<long long *>(b->scratch + off_acc[f]);
+        a.lbl_tmp = reinterpret_cast<int32_t *>(b->scratch + off_lbl[f]);
+    }
+    *out = b;
+    return SLIC_OK;
+}
+
+slic_status slic_batch_destroy(slic_batch b) {
+    if (!b) return SLIC_OK;
+    cudaDeviceSynchronize();
+    cudaFree(b->scratch);
+    cudaFree(b->d_frames);
+    for (auto &ev : b->events) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    delete b;
+    return SLIC_OK;
+}
+
+slic_status slic_batch_set_buffers(slic_batch b, const uint8_t *const *d_images, int32_t *const *d_labels,
+                                   float *const *d_centres, const float *const *d_init) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (!d_images || !d_labels || !d_centres) return bfail(b, SLIC_ERR_INVALID, "NULL pointer array");
+    for (int f = 0; f < b->n; ++f) {
+        if (!d_images[f] || !d_labels[f] || !d_centres[f])
+            return bfail(b, SLIC_ERR_INVALID, "NULL buffer for frame " + std::to_string(f));
+        FrameArgs &a = b->frames[f];
+        a.rgb = d_images[f];
+        a.labels = d_labels[f];
+        a.centres = d_centres[f];
+        a.centres_out = d_centres[f];
+        a.init = d_init ? d_init[f] : nullptr;
+        a.rgb_vec = ((a.W & 3) == 0 && ((uintptr_t)a.rgb & 15) == 0) ? 1 : 0;
+        a.labels_vec = ((a.W & 3) == 0 && ((uintptr_t)a.labels & 15) == 0) ? 1 : 0;
+    }
+    // Synchronous upload: the table must not change under queued work.
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_frames, b->frames.data(), sizeof(FrameArgs) * b->n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("frame table upload: ") + cudaGetErrorString(e));
+    b->buffers_set = true;
+    return SLIC_OK;
+}
+
+slic_status slic_batch_segment(slic_batch b, void *stream) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int grid = grid_for(b);
+    cudaError_t e = launch_init_batch(b->d_frames, b->n, b->total_centres, s);
+    long long n_launch = 1;
+    for (int pass = 0; e == cudaSuccess && pass <= b->iterations; ++pass) {
+        if (pass > 0) {
+            e = launch_update_batch(b->d_frames, b->n, b->total_centres, s);
+            ++n_launch;
+        }
+        if (e == cudaSuccess) {
+            cudaEvent_t e1 = nullptr;
+            if (b->profiling) {
+                if (b->ev_used == b->events.size()) {
+                    cudaEvent_t x, y;
+                    if (cudaEventCreate(&x) != cudaSuccess || cudaEventCreate(&y) != cudaSuccess)
+                        return bfail(b, SLIC_ERR_CUDA, "cudaEventCreate failed");
+                    b->events.emplace_back(x, y);
+                }
+                // External records become event-record nodes under stream capture.
+                cudaEventRecordWithFlags(b->events[b->ev_used].first, s, cudaEventRecordExternal);
+                e1 = b->events[b->ev_used++].second;
+            }
+            e = launch_assign_batch(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == 0,
+                                    pass == b->iterations, b->smem, grid, s);
+            if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+            ++n_launch;
+        }
+    }
+    if (e == cudaSuccess && b->connectivity) {
+        e = launch_connectivity_batch(b->d_frames, b->n, b->total_rows, b->max_w, 0, s);
+        if (e == cudaSuccess) e = launch_connectivity_batch(b->d_frames, b->n, b->total_rows, b->max_w, 1, s);
+        n_launch += 2;
+    }
+    if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    b->launches += n_launch;
+    return SLIC_OK;
+}
+
+slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (ctas_per_sm < 0) return bfail(b, SLIC_ERR_INVALID, "ctas_per_sm must be >= 0");
+    b->ctas_per_sm = ctas_per_sm;
+    return SLIC_OK;
+}
+
+slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
+    const std::string key = tune_key(b);
+    int best = 0;
+    if (cache_path && cache_lookup(cache_path, key, &best)) {
+        b->ctas_per_sm = std::min(best, b->occupancy);
+        if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+        return SLIC_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bfail(b, SLIC_ERR_CUDA, "cudaEventCreate failed");
+    float best_ms = 1e30f;
+    slic_status st = SLIC_OK;
+    for (int c = 1; c <= b->occupancy && st == SLIC_OK; ++c) {
+        b->ctas_per_sm = c;
+        if ((st = slic_batch_segment(b, stream)) != SLIC_OK) break;  // warm-up
+        float total = 0.0f;
+        for (int rep = 0; rep < 3 && st == SLIC_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            st = slic_batch_segment(b, stream);
+            cudaEventRecord(e1, s);
+            float ms = 0.0f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                st = bfail(b, SLIC_ERR_CUDA, "autotune timing failed");
+            total += ms;
+        }
+        if (st == SLIC_OK && total / 3 < best_ms) {
+            best_ms = total / 3;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SLIC_OK) return st;
+    b->ctas_per_sm = best;
+    if (cache_path) cache_store(cache_path, key, best, best_ms);
+    if (ctas_per_sm) *ctas_per_sm = best;
+    return SLIC_OK;
+}
+
+slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (total_pixels) *total_pixels = b->total_pixels;
+    if (launches) *launches = b->launches;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, b->occupancy) : b->occupancy;
+    return SLIC_OK;
+}
+
+slic_status slic_batch_profile_enable(slic_batch b, int enable) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (enable && !b->profiling) b->ev_used = 0;
+    b->profiling = enable != 0;
+    return SLIC_OK;
+}
+
+slic_status slic_batch_profile_read(slic_batch b, double *assign_ms, long long *assign_launches) {
+    if (!b || !assign_ms || !assign_launches) return bfail(b, SLIC_ERR_INVALID, "NULL argument");
+    double total = 0.0;
+    for (size_t i = 0; i < b->ev_used; ++i) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(b->events[i].second);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->events[i].first, b->events[i].second);
+        if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("profile event: ") + cudaGetErrorString(e));
+        total += ms;
+    }
+    *assign_ms = total;
+    *assign_launches = (long long)b->ev_used;
+    return SLIC_OK;
+}
+
+const char *slic_batch_last_error(slic_batch b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
+}  // extern "C"

@@ -31,15 +31,19 @@ struct ConvConsts {
     int color_space;  // 0 CIELAB, 1 RGB, 2 XYZ
 };
 
-// One frame's geometry and buffers as seen by the kernels.
+// One frame's geometry and buffers as seen by the kernels (a kernel
+// parameter for single-frame launches, an entry of a device-side table for
+// batched ones).
 struct FrameArgs {
     ConvConsts conv;
     const uint8_t *rgb;     // [H][W][C]
     float *feat;            // 3 planes [H][P]; plane stride H*P
     const float *centres;   // [K][6] read by the assignment
-    float *centres_out;     // [K][6] written by the update
+    float *centres_out;     // [K][6] written by init and update
     long long *acc;         // [K][6] fixed-point sums (l,a,b scaled; x,y,count exact)
     int32_t *labels;        // [H][W]
+    int32_t *lbl_tmp;       // [H][W] connectivity ping-pong (batched path)
+    const float *init;      // [K][6] initial centres instead of the grid (batched path)
     int W, H, P, C, S, ns_c, ns_r;
     float w;                // m / S
     int win_max;            // largest centre window of any tile (sizes shared memory)
@@ -47,17 +51,30 @@ struct FrameArgs {
     int rgb_vec;            // 1: image rows allow 4-pixel vector loads
     int labels_vec;         // 1: label rows allow 4-pixel vector stores
     float fix_scale;        // fixed-point scale of the feature sums
+    unsigned s_mul;         // ceil(2^32 / S) for S <= 2048, else 0
+    int tiles_x;            // 32x32 tiles per row
+    int tile_base;          // first tile / centre / row of this frame in the
+    int centre_base;        // batch's concatenated lists (0 for a single
+    int row_base;           // frame)
 };
 
 // Shared memory for one assignment CTA whose tile spans at most win_n cells.
 size_t assign_smem_bytes(int win_n, bool first);
 int assign_max_window(int S, int ns_c, int ns_r);
 bool assign_direct_acc(int win_n);
+// Resident CTAs per SM of the batched assignment kernel.
+int assign_batch_occupancy(bool same, size_t smem);
+
+// Host helpers shared by the C-ABI files: colour constants of a feature
+// space, and the once-per-device set-up (sRGB table, shared-memory limit).
+ConvConsts conv_consts(int color_space);
+cudaError_t device_setup(int dev, size_t smem);
 
 cudaError_t upload_lut(const float *lut256);
 cudaError_t configure_kernels(size_t max_smem);
 
-cudaError_t launch_init_from_rgb(const FrameArgs &a, float *centres, cudaStream_t s);
+cudaError_t launch_init_from_rgb(const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_init_batch(const FrameArgs *d_frames, int n, int total_centres, cudaStream_t s);
 cudaError_t launch_init_from_feat(const float *feat, int W, int H, int P, int S, int ns_c, int ns_r,
                                   float *centres, cudaStream_t s);
 cudaError_t launch_zero_acc(long long *acc, int K, cudaStream_t s);
@@ -65,12 +82,17 @@ cudaError_t launch_zero_acc(long long *acc, int K, cudaStream_t s);
 // instead of accumulating.
 cudaError_t launch_assign(const FrameArgs &a, bool first, bool last, bool store_feat, size_t smem,
                           cudaStream_t s);
+cudaError_t launch_assign_batch(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool first,
+                                bool last, size_t smem, int grid, cudaStream_t s);
 cudaError_t launch_update(long long *acc, const float *centres_in, float *centres_out, int K, double fix_inv,
                           cudaStream_t s);
+cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_centres, cudaStream_t s);
 cudaError_t launch_accumulate_labels(const float *feat, int W, int H, int P, const int32_t *labels, int K,
                                      long long *acc, float fix_scale, cudaStream_t s);
 cudaError_t launch_convert(const ConvConsts &cc, const uint8_t *rgb, int W, int H, int C, float *feat, int P,
                            cudaStream_t s);
 cudaError_t launch_connectivity(const int32_t *in, int32_t *out, int W, int H, cudaStream_t s);
+cudaError_t launch_connectivity_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w, int pass,
+                                      cudaStream_t s);
 
 }  // namespace slicgb

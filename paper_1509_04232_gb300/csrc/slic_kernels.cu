@@ -1,24 +1,25 @@
 // SLIC kernels for sm_103a (gSLICr, arXiv 1509.04232, Sec. 3).
 //
-//   k_init_rgb / k_init_feat  "Cluster center initialisation": one thread per
-//                             centre, position = midpoint of the in-image part
-//                             of its grid cell, colour = the pixel under it.
-//   k_assign<FIRST,LAST>      "Finding the cluster associations" (Eq. 1) for a
-//                             32x32-pixel tile, with the tile's window of
-//                             centres staged in shared memory. FIRST fuses
-//                             "Image space conversion" (RGB bytes in, features
-//                             stored once); !LAST fuses the first half of
-//                             "Updating the cluster center": per-tile sums of
-//                             the members of each window centre, reduced with
-//                             warp-wide integer reductions and flushed with
-//                             one atomic per (centre, component) per tile.
-//   k_update                  second half of the update: centre = sum/count
-//                             (empty centre keeps its position and colour).
-//   k_connectivity            one pass of "Enforce connectivity".
+//   init      "Cluster center initialisation": one thread per centre; position
+//             = midpoint of the in-image part of its grid cell, colour = the
+//             pixel under it (converted on the fly).
+//   assign    "Finding the cluster associations" (Eq. 1) for one 32x32-pixel
+//             tile, with the tile's window of centres staged in shared memory.
+//             The first pass fuses "Image space conversion" (RGB bytes in,
+//             features stored once); every pass but the last fuses the first
+//             half of "Updating the cluster center" (per-tile member sums,
+//             flushed with one global atomic per centre component per tile).
+//   update    second half of the update: centre = sums / count; an empty
+//             centre keeps its position and colour.
+//   connect   one pass of "Enforce connectivity".
 //
-// The sums are exact integers (features in fixed point with a 2^-16
-// quantum), so the result is independent of the order in which tiles, warps
-// or frames contribute.
+// Every stage exists as a single-frame kernel (a frame's arguments are a
+// __grid_constant__ parameter) and as a batched kernel over a table of frame
+// descriptors in device memory (the assignment one persistent: a grid sized
+// to the GPU loops over the tiles of all frames). The member sums are exact
+// integers (features in fixed point), so results do not depend on the order
+// in which tiles, warps or frames contribute: a frame segmented alone or in
+// any batch gives bit-identical labels and centres.
 #include "slic_internal.cuh"
 
 #include <cstdint>
@@ -30,11 +31,20 @@ __device__ float g_lut[256];  // sRGB byte -> linear, filled by the host
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kWarps = kThreads / 32;
+constexpr float kSentinel = 1e18f;
+constexpr size_t kPrivateAccLimit = 64 * 1024;
 
 __device__ __forceinline__ float fsqrt_approx(float x) {
     float r;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// x / S for 0 <= x < 2^21 using the frame's multiplier ceil(2^32 / S) (exact
+// for S <= 2048; s_mul == 0 selects a plain division).
+__device__ __forceinline__ int div_s(int x, unsigned s_mul, int S) {
+    return s_mul ? (int)__umulhi((unsigned)x, s_mul) : x / S;
 }
 
 __device__ __forceinline__ float lab_f(const ConvConsts &cc, float t) {
@@ -68,6 +78,36 @@ __device__ __forceinline__ void convert_pixel(const ConvConsts &cc, unsigned r, 
     f2 = 200.0f * (fy - fz);
 }
 
+// Index of the frame whose [base, next base) range holds `idx` (frames are
+// sorted by base; base of frame 0 is 0).
+enum BaseField { kTileBase, kCentreBase, kRowBase };
+template <BaseField F>
+__device__ __forceinline__ int base_of(const FrameArgs &a) {
+    return F == kTileBase ? a.tile_base : F == kCentreBase ? a.centre_base : a.row_base;
+}
+template <BaseField F>
+__device__ __forceinline__ int find_frame(const FrameArgs *frames, int n, int idx) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base_of<F>(frames[mid]) <= idx)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Dynamic shared memory of an assignment CTA: window centres, per-warp
+// private accumulators (unless the window is too large), sRGB table (first
+// pass). Also the offset of the table when `first` is false.
+__host__ __device__ __forceinline__ size_t smem_layout(int win_n, bool first) {
+    size_t b = ((size_t)win_n * 20 + 15) & ~(size_t)15;
+    if ((size_t)kWarps * win_n * 4 * sizeof(int) <= kPrivateAccLimit) b += (size_t)kWarps * win_n * 4 * sizeof(int);
+    if (first) b += 256 * sizeof(float);
+    return b;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -86,26 +126,46 @@ __device__ __forceinline__ void init_centre_position(int k, int W, int H, int S,
     py = (y_first + y_last) >> 1;
 }
 
-__global__ void k_init_rgb(FrameArgs a, float *centres, long long *acc) {
-    const int K = a.ns_c * a.ns_r;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
+__device__ __forceinline__ void init_centre(const FrameArgs &a, int k) {
     float xk, yk;
     int px, py;
     init_centre_position(k, a.W, a.H, a.S, a.ns_c, xk, yk, px, py);
     const uint8_t *p = a.rgb + ((size_t)py * a.W + px) * a.C;
     float f0, f1, f2;
     convert_pixel(a.conv, p[0], p[1], p[2], g_lut, f0, f1, f2);
-    float *ck = centres + (size_t)k * 6;
+    float *ck = a.centres_out + (size_t)k * 6;
     ck[0] = f0;
     ck[1] = f1;
     ck[2] = f2;
     ck[3] = xk;
     ck[4] = yk;
     ck[5] = 0.0f;
-    long long *ak = acc + (size_t)k * 6;
+    long long *ak = a.acc + (size_t)k * 6;
 #pragma unroll
     for (int c = 0; c < 6; ++c) ak[c] = 0;
+}
+
+__global__ void k_init_rgb(const __grid_constant__ FrameArgs a) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < a.ns_c * a.ns_r) init_centre(a, k);
+}
+
+// Batched initialisation; a frame with `init` set copies those centres
+// (e.g. the previous video frame's) instead of the grid initialisation.
+__global__ void k_init_batch(const FrameArgs *frames, int n, int total) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int f = find_frame<kCentreBase>(frames, n, g);
+    const FrameArgs &a = frames[f];
+    const int k = g - a.centre_base;
+    if (a.init) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a.centres_out[(size_t)k * 6 + c] = a.init[(size_t)k * 6 + c];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a.acc[(size_t)k * 6 + c] = 0;
+    } else {
+        init_centre(a, k);
+    }
 }
 
 __global__ void k_init_feat(const float *feat, int W, int H, int P, int S, int ns_c, int ns_r, float *centres) {
@@ -134,24 +194,10 @@ __global__ void k_zero_acc(long long *acc, int n) {
 // Assignment (+ fused conversion and partial update sums)
 // ---------------------------------------------------------------------------
 //
-// CTA = 32x32-pixel tile, 8 warps; warp w covers the 16x8 block at
-// (16*(w%2), 8*(w/2)) of the tile; lane l covers 4 horizontally adjacent
+// A tile is 32x32 pixels handled by 8 warps; warp w covers the 16x8 block at
+// (16*(w%2), 8*(w/2)) of the tile and lane l the 4 horizontally adjacent
 // pixels at (4*(l%4), l/4) of that block, so a warp reads 8 rows of 64
 // contiguous bytes per feature plane.
-//
-// Partial sums for the update: each lane merges runs of equal labels among
-// its 4 pixels, each warp reduces equal keys with redux.sync into private
-// int32 accumulators in shared memory (a warp covers 128 pixels, so a sum
-// is below 128 * 255 * 2^16 < 2^31), and the CTA adds its 8 warps' totals
-// in int64 and issues one global atomic per non-zero (centre, component).
-// Windows too large for private accumulators (S <= 2) use warp-aggregated
-// global atomics instead.
-
-namespace {
-constexpr int kWarps = kThreads / 32;
-constexpr float kSentinel = 1e18f;
-constexpr size_t kPrivateAccLimit = 64 * 1024;
-}  // namespace
 
 // Window of cells a tile can reference: the cells its pixels fall in plus
 // one ring, clamped to what the grid can offer.
@@ -165,17 +211,13 @@ int assign_max_window(int S, int ns_c, int ns_r) {
 
 bool assign_direct_acc(int win_n) { return (size_t)kWarps * win_n * 4 * sizeof(int) > kPrivateAccLimit; }
 
-size_t assign_smem_bytes(int win_n, bool first) {
-    size_t b = ((size_t)win_n * 20 + 15) & ~(size_t)15;
-    if (!assign_direct_acc(win_n)) b += (size_t)kWarps * win_n * 4 * sizeof(int);
-    if (first) b += 256 * sizeof(float);
-    return b;
-}
+size_t assign_smem_bytes(int win_n, bool first) { return smem_layout(win_n, first); }
 
 namespace {
 
-// Warp-aggregated accumulation of one value set per lane, keyed by window
-// index (key < 0: no contribution). All 32 lanes must call it.
+// Warp-aggregated accumulation of one value set per lane into the global
+// sums, keyed by window index (key < 0: no contribution). All 32 lanes must
+// call it. Used only when the window is too large for private accumulators.
 __device__ __forceinline__ void warp_accumulate(int key, const int (&v)[6], unsigned long long *gacc, int wx0,
                                                 int wy0, int wnx, int ns_c) {
     const int lane = threadIdx.x & 31;
@@ -200,13 +242,8 @@ __device__ __forceinline__ void warp_accumulate(int key, const int (&v)[6], unsi
     }
 }
 
-}  // namespace
-
-namespace {
-
 // Merge runs of equal keys among a lane's kPPT pixels, then reduce each run
-// across the warp with a shuffle-driven key loop and add it to the global
-// sums (all 32 lanes must call it).
+// across the warp and add it to the global sums (all 32 lanes must call it).
 __device__ __forceinline__ void accumulate_runs(const int (&key)[kPPT], int (&v)[kPPT][6], unsigned long long *gacc,
                                                 int wx0, int wy0, int wnx, int ns_c) {
 #pragma unroll
@@ -225,39 +262,87 @@ __device__ __forceinline__ void accumulate_runs(const int (&key)[kPPT], int (&v)
 
 }  // namespace
 
-// Assignment pass over one 32x32 tile.
+// One assignment pass over the tile at (tx0, ty0) of frame `fa`.
 //   FIRST: features come from the RGB bytes (and are stored for later passes).
 //   LAST:  labels are written; otherwise every centre's member sums are
 //          accumulated for the update (exact integers).
 //   SAME:  S is a multiple of kPPT, so a thread's kPPT pixels share a cell.
+// `smem` is the CTA's dynamic shared memory; `lut` (FIRST) holds the sRGB
+// table. The caller must __syncthreads() before reusing shared memory.
 template <bool FIRST, bool LAST, bool SAME>
-__global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_feat) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void assign_tile(const FrameArgs &fa, int tx0, int ty0, int store_feat,
+                                            unsigned char *smem, const float *lut) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int W = a.W, H = a.H, S = a.S;
-    const int tx0 = blockIdx.x * kTileW, ty0 = blockIdx.y * kTileH;
+    const int W = fa.W, H = fa.H, S = fa.S, P = fa.P, C = fa.C, ns_c = fa.ns_c, ns_r = fa.ns_r;
+    const int win_max = fa.win_max;
+    const unsigned s_mul = fa.s_mul;
+    const bool direct = fa.direct_acc != 0;
+    const float *const feat_in = fa.feat;
+    float *const feat_out = fa.feat;
 
-    // Window of centres for this tile: the cells its pixels fall in plus one
-    // ring.
-    const int ccx0 = tx0 / S, ccx1 = min(tx0 + kTileW - 1, W - 1) / S;
-    const int ccy0 = ty0 / S, ccy1 = min(ty0 + kTileH - 1, H - 1) / S;
+    // Window of centres for this tile.
+    const int ccx0 = div_s(tx0, s_mul, S), ccx1 = div_s(min(tx0 + kTileW - 1, W - 1), s_mul, S);
+    const int ccy0 = div_s(ty0, s_mul, S), ccy1 = div_s(min(ty0 + kTileH - 1, H - 1), s_mul, S);
     const int wx0 = ccx0 - 1, wy0 = ccy0 - 1;
     const int wnx = ccx1 - ccx0 + 3, wny = ccy1 - ccy0 + 3;
     const int nwin = wnx * wny;
-    const bool direct = a.direct_acc != 0;
 
-    float4 *cA = reinterpret_cast<float4 *>(smem_raw);
+    float4 *cA = reinterpret_cast<float4 *>(smem);
     float *cY = reinterpret_cast<float *>(cA + nwin);
-    int *wacc = reinterpret_cast<int *>(smem_raw + (((size_t)a.win_max * 20 + 15) & ~(size_t)15));
-    float *lut = reinterpret_cast<float *>(wacc + (direct ? 0 : (size_t)kWarps * a.win_max * 4));
+    unsigned *wacc = reinterpret_cast<unsigned *>(smem + (((size_t)win_max * 20 + 15) & ~(size_t)15));
+
+    // Pixels of this thread; their loads are issued before the staging
+    // barrier so both latencies overlap.
+    const int x = tx0 + 16 * (warp & 1) + 4 * (lane & 3);
+    const int y = ty0 + 8 * (warp >> 1) + (lane >> 2);
+    const bool row_ok = (y < H) && (x < W);
+    const size_t plane = (size_t)H * P;
+    const size_t foff = (size_t)y * P + x;
+    float f0[kPPT] = {}, f1[kPPT] = {}, f2[kPPT] = {};
+    unsigned rgbw[4] = {0u, 0u, 0u, 0u};
+    if (row_ok) {
+        if (FIRST) {
+            if (fa.rgb_vec) {
+                const uint8_t *p = fa.rgb + ((size_t)y * W + x) * C;
+                if (C == 3) {
+                    const uint32_t *q = reinterpret_cast<const uint32_t *>(p);
+                    rgbw[0] = __ldg(q);
+                    rgbw[1] = __ldg(q + 1);
+                    rgbw[2] = __ldg(q + 2);
+                } else {
+                    const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
+                    rgbw[0] = q.x;
+                    rgbw[1] = q.y;
+                    rgbw[2] = q.z;
+                    rgbw[3] = q.w;
+                }
+            }
+        } else if ((P & 3) == 0) {
+            const float4 v0 = __ldg(reinterpret_cast<const float4 *>(feat_in + foff));
+            const float4 v1 = __ldg(reinterpret_cast<const float4 *>(feat_in + plane + foff));
+            const float4 v2 = __ldg(reinterpret_cast<const float4 *>(feat_in + 2 * plane + foff));
+            f0[0] = v0.x; f0[1] = v0.y; f0[2] = v0.z; f0[3] = v0.w;
+            f1[0] = v1.x; f1[1] = v1.y; f1[2] = v1.z; f1[3] = v1.w;
+            f2[0] = v2.x; f2[1] = v2.y; f2[2] = v2.z; f2[3] = v2.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) {
+                const bool ok = x + j < W;
+                f0[j] = ok ? feat_in[foff + j] : 0.0f;
+                f1[j] = ok ? feat_in[plane + foff + j] : 0.0f;
+                f2[j] = ok ? feat_in[2 * plane + foff + j] : 0.0f;
+            }
+        }
+    }
 
     // Out-of-grid window cells hold a sentinel centre whose D is ~1e18, so
     // the candidate loop needs no bounds checks (the own cell is always
     // valid and always beats it).
     for (int i = tid; i < nwin; i += kThreads) {
-        const int cy = wy0 + i / wnx, cx = wx0 + i - (i / wnx) * wnx;
-        if (cx >= 0 && cx < a.ns_c && cy >= 0 && cy < a.ns_r) {
-            const float *ck = a.centres + ((size_t)cy * a.ns_c + cx) * 6;
+        const int qy = i / wnx;
+        const int cy = wy0 + qy, cx = wx0 + i - qy * wnx;
+        if (cx >= 0 && cx < ns_c && cy >= 0 && cy < ns_r) {
+            const float *ck = fa.centres + ((size_t)cy * ns_c + cx) * 6;
             cA[i] = make_float4(ck[0], ck[1], ck[2], ck[3]);
             cY[i] = ck[4];
         } else {
@@ -268,88 +353,55 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_f
     if (!LAST && !direct) {
         for (int i = tid; i < kWarps * nwin * 4; i += kThreads) {
             const int q = i / (nwin * 4);
-            wacc[q * a.win_max * 4 + (i - q * nwin * 4)] = 0;
+            wacc[q * win_max * 4 + (i - q * nwin * 4)] = 0u;
         }
-    }
-    if (FIRST) {
-        for (int i = tid; i < 256; i += kThreads) lut[i] = g_lut[i];
     }
     __syncthreads();
 
-    const int x = tx0 + 16 * (warp & 1) + 4 * (lane & 3);
-    const int y = ty0 + 8 * (warp >> 1) + (lane >> 2);
-    const bool row_ok = (y < H) && (x < W);
-    float f0[kPPT] = {}, f1[kPPT] = {}, f2[kPPT] = {};
-    const size_t plane = (size_t)H * a.P;
-    const size_t foff = (size_t)y * a.P + x;
-
-    if (row_ok) {
-        if (FIRST) {
-            const uint8_t *p = a.rgb + ((size_t)y * W + x) * a.C;
-            unsigned r[kPPT], g[kPPT], b[kPPT];
-            if (a.rgb_vec && a.C == 3) {
-                const uint32_t *q = reinterpret_cast<const uint32_t *>(p);
-                const uint32_t w0 = __ldg(q), w1 = __ldg(q + 1), w2 = __ldg(q + 2);
-                r[0] = w0 & 255; g[0] = (w0 >> 8) & 255; b[0] = (w0 >> 16) & 255; r[1] = w0 >> 24;
-                g[1] = w1 & 255; b[1] = (w1 >> 8) & 255; r[2] = (w1 >> 16) & 255; g[2] = w1 >> 24;
-                b[2] = w2 & 255; r[3] = (w2 >> 8) & 255; g[3] = (w2 >> 16) & 255; b[3] = w2 >> 24;
-            } else if (a.rgb_vec) {
-                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
-                const uint32_t ws[4] = {q.x, q.y, q.z, q.w};
+    if (FIRST && row_ok) {
+        unsigned r[kPPT], g[kPPT], b[kPPT];
+        if (fa.rgb_vec && C == 3) {
+            const uint32_t w0 = rgbw[0], w1 = rgbw[1], w2 = rgbw[2];
+            r[0] = w0 & 255; g[0] = (w0 >> 8) & 255; b[0] = (w0 >> 16) & 255; r[1] = w0 >> 24;
+            g[1] = w1 & 255; b[1] = (w1 >> 8) & 255; r[2] = (w1 >> 16) & 255; g[2] = w1 >> 24;
+            b[2] = w2 & 255; r[3] = (w2 >> 8) & 255; g[3] = (w2 >> 16) & 255; b[3] = w2 >> 24;
+        } else if (fa.rgb_vec) {
 #pragma unroll
-                for (int j = 0; j < kPPT; ++j) {
-                    r[j] = ws[j] & 255; g[j] = (ws[j] >> 8) & 255; b[j] = (ws[j] >> 16) & 255;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < kPPT; ++j) {
-                    const bool ok = x + j < W;
-                    r[j] = ok ? p[j * a.C + 0] : 0;
-                    g[j] = ok ? p[j * a.C + 1] : 0;
-                    b[j] = ok ? p[j * a.C + 2] : 0;
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j) convert_pixel(a.conv, r[j], g[j], b[j], lut, f0[j], f1[j], f2[j]);
-            if (!LAST || store_feat) {
-                if ((a.P & 3) == 0) {
-                    *reinterpret_cast<float4 *>(a.feat + foff) = make_float4(f0[0], f0[1], f0[2], f0[3]);
-                    *reinterpret_cast<float4 *>(a.feat + plane + foff) = make_float4(f1[0], f1[1], f1[2], f1[3]);
-                    *reinterpret_cast<float4 *>(a.feat + 2 * plane + foff) =
-                        make_float4(f2[0], f2[1], f2[2], f2[3]);
-                } else {
-                    for (int j = 0; j < kPPT && x + j < W; ++j) {
-                        a.feat[foff + j] = f0[j];
-                        a.feat[plane + foff + j] = f1[j];
-                        a.feat[2 * plane + foff + j] = f2[j];
-                    }
-                }
+            for (int j = 0; j < kPPT; ++j) {
+                r[j] = rgbw[j] & 255; g[j] = (rgbw[j] >> 8) & 255; b[j] = (rgbw[j] >> 16) & 255;
             }
         } else {
-            if ((a.P & 3) == 0) {
-                const float4 v0 = __ldg(reinterpret_cast<const float4 *>(a.feat + foff));
-                const float4 v1 = __ldg(reinterpret_cast<const float4 *>(a.feat + plane + foff));
-                const float4 v2 = __ldg(reinterpret_cast<const float4 *>(a.feat + 2 * plane + foff));
-                f0[0] = v0.x; f0[1] = v0.y; f0[2] = v0.z; f0[3] = v0.w;
-                f1[0] = v1.x; f1[1] = v1.y; f1[2] = v1.z; f1[3] = v1.w;
-                f2[0] = v2.x; f2[1] = v2.y; f2[2] = v2.z; f2[3] = v2.w;
-            } else {
+            const uint8_t *p = fa.rgb + ((size_t)y * W + x) * C;
 #pragma unroll
-                for (int j = 0; j < kPPT; ++j) {
-                    const bool ok = x + j < W;
-                    f0[j] = ok ? a.feat[foff + j] : 0.0f;
-                    f1[j] = ok ? a.feat[plane + foff + j] : 0.0f;
-                    f2[j] = ok ? a.feat[2 * plane + foff + j] : 0.0f;
+            for (int j = 0; j < kPPT; ++j) {
+                const bool ok = x + j < W;
+                r[j] = ok ? p[j * C + 0] : 0;
+                g[j] = ok ? p[j * C + 1] : 0;
+                b[j] = ok ? p[j * C + 2] : 0;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kPPT; ++j) convert_pixel(fa.conv, r[j], g[j], b[j], lut, f0[j], f1[j], f2[j]);
+        if (!LAST || store_feat) {
+            if ((P & 3) == 0) {
+                *reinterpret_cast<float4 *>(feat_out + foff) = make_float4(f0[0], f0[1], f0[2], f0[3]);
+                *reinterpret_cast<float4 *>(feat_out + plane + foff) = make_float4(f1[0], f1[1], f1[2], f1[3]);
+                *reinterpret_cast<float4 *>(feat_out + 2 * plane + foff) = make_float4(f2[0], f2[1], f2[2], f2[3]);
+            } else {
+                for (int j = 0; j < kPPT && x + j < W; ++j) {
+                    feat_out[foff + j] = f0[j];
+                    feat_out[plane + foff + j] = f1[j];
+                    feat_out[2 * plane + foff + j] = f2[j];
                 }
             }
         }
     }
 
     // Own cell of each pixel: column cx[j], row pcy.
-    const int pcy = y / S;
+    const int pcy = div_s(y, s_mul, S);
     int cx[kPPT];
     {
-        const int c0 = x / S;
+        const int c0 = div_s(x, s_mul, S);
         if (SAME) {
 #pragma unroll
             for (int j = 0; j < kPPT; ++j) cx[j] = c0;
@@ -372,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_f
 #pragma unroll
     for (int j = 0; j < kPPT; ++j) bk[j] = 0xFFFFFFFFu;
     if (row_ok) {
-        const float w = a.w;
+        const float w = fa.w;
         const float fy = (float)y;
         float fxs[kPPT];
 #pragma unroll
@@ -407,15 +459,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_f
         const int dy = t / 3 - 1, dx = t % 3 - 1;
         const bool ok = row_ok && (x + j < W);
         if (LAST)
-            best[j] = ok ? (pcy + dy) * a.ns_c + cx[j] + dx : -1;
+            best[j] = ok ? (pcy + dy) * ns_c + cx[j] + dx : -1;
         else
             best[j] = ok ? (pcy + dy - wy0) * wnx + (cx[j] + dx - wx0) : -1;
     }
 
     if constexpr (LAST) {
         if (row_ok) {
-            int32_t *out = a.labels + (size_t)y * W + x;
-            if (a.labels_vec) {
+            int32_t *out = fa.labels + (size_t)y * W + x;
+            if (fa.labels_vec) {
                 *reinterpret_cast<int4 *>(out) = make_int4(best[0], best[1], best[2], best[3]);
             } else {
                 for (int j = 0; j < kPPT && x + j < W; ++j) out[j] = best[j];
@@ -428,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_f
         // feature sums (fixed point) and one word packing the x and y
         // offsets from the tile origin and the count (a warp covers 128
         // pixels, so the fields stay below 2^12, 2^12 and 2^8).
-        const float fs = a.fix_scale;
+        const float fs = fa.fix_scale;
         if (!direct) {
             unsigned v[kPPT][4];
 #pragma unroll
@@ -445,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_f
                     for (int c = 0; c < 4; ++c) v[j][c] += v[j + 1][c];
                 }
             }
-            unsigned *my = reinterpret_cast<unsigned *>(wacc) + (size_t)warp * a.win_max * 4;
+            unsigned *my = wacc + (size_t)warp * win_max * 4;
 #pragma unroll
             for (int j = 0; j < kPPT; ++j) {
                 const int k = (j == 0 || best[j] != best[j - 1]) ? best[j] : -1;
@@ -457,22 +509,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_f
             __syncthreads();
             // One thread per (window centre, word): add up the 8 warps in
             // int64 and flush to the global sums.
-            const unsigned *all = reinterpret_cast<const unsigned *>(wacc);
             for (int i = tid; i < nwin * 4; i += kThreads) {
                 const int wi = i >> 2, c = i & 3;
-                const int cy = wy0 + wi / wnx, cxg = wx0 + wi - (wi / wnx) * wnx;
+                const int qy = wi / wnx;
+                const int cy = wy0 + qy, cxg = wx0 + wi - qy * wnx;
                 unsigned long long *g =
-                    reinterpret_cast<unsigned long long *>(a.acc) + ((size_t)cy * a.ns_c + cxg) * 6;
+                    reinterpret_cast<unsigned long long *>(fa.acc) + ((size_t)cy * ns_c + cxg) * 6;
                 if (c < 3) {
                     long long t = 0;
 #pragma unroll
-                    for (int q = 0; q < kWarps; ++q) t += (int)all[(size_t)q * a.win_max * 4 + i];
+                    for (int q = 0; q < kWarps; ++q) t += (int)wacc[(size_t)q * win_max * 4 + i];
                     if (t != 0) atomicAdd(&g[c], (unsigned long long)t);
                 } else {
                     long long xs = 0, ys = 0, n = 0;
 #pragma unroll
                     for (int q = 0; q < kWarps; ++q) {
-                        const unsigned pk = all[(size_t)q * a.win_max * 4 + i];
+                        const unsigned pk = wacc[(size_t)q * win_max * 4 + i];
                         xs += pk & 0xFFFu;
                         ys += (pk >> 12) & 0xFFFu;
                         n += pk >> 24;
@@ -498,8 +550,41 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_f
                 v[j][4] = y;
                 v[j][5] = 1;
             }
-            accumulate_runs(best, v, reinterpret_cast<unsigned long long *>(a.acc), wx0, wy0, wnx, a.ns_c);
+            accumulate_runs(best, v, reinterpret_cast<unsigned long long *>(fa.acc), wx0, wy0, wnx, ns_c);
         }
+    }
+}
+
+template <bool FIRST, bool LAST, bool SAME>
+__global__ void __launch_bounds__(kThreads, 3) k_assign(const __grid_constant__ FrameArgs a, int store_feat) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *lut = nullptr;
+    if (FIRST) {
+        lut = reinterpret_cast<float *>(smem_raw + smem_layout(a.win_max, false));
+        for (int i = threadIdx.x; i < 256; i += kThreads) lut[i] = g_lut[i];
+    }
+    assign_tile<FIRST, LAST, SAME>(a, blockIdx.x * kTileW, blockIdx.y * kTileH, store_feat, smem_raw, lut);
+}
+
+// Persistent batched pass: CTA b processes tiles b, b + gridDim.x, ... of
+// the concatenated tile lists of all frames (win_max: largest window of any
+// frame, which sizes the shared memory).
+template <bool FIRST, bool LAST, bool SAME>
+__global__ void __launch_bounds__(kThreads, 3) k_assign_batch(const FrameArgs *frames, int n_frames, int total_tiles,
+                                                              int win_max) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *lut = nullptr;
+    if (FIRST) {
+        lut = reinterpret_cast<float *>(smem_raw + smem_layout(win_max, false));
+        for (int i = threadIdx.x; i < 256; i += kThreads) lut[i] = g_lut[i];
+    }
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        const int f = find_frame<kTileBase>(frames, n_frames, tile);
+        const FrameArgs &a = frames[f];
+        const int local = tile - a.tile_base;
+        const int ty = local / a.tiles_x, tx = local - ty * a.tiles_x;
+        assign_tile<FIRST, LAST, SAME>(a, tx * kTileW, ty * kTileH, 0, smem_raw, lut);
+        __syncthreads();
     }
 }
 
@@ -507,13 +592,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign(FrameArgs a, int store_f
 // Update: centre = member mean; empty centre keeps position and colour.
 // ---------------------------------------------------------------------------
 
-__global__ void k_update(long long *acc, const float *centres_in, float *centres_out, int K, double fix_inv) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    long long *ak = acc + (size_t)k * 6;
+__device__ __forceinline__ void update_centre(long long *ak, const float *ci, float *co, double fix_inv) {
     const long long n = ak[5];
-    float *co = centres_out + (size_t)k * 6;
-    const float *ci = centres_in + (size_t)k * 6;
     if (n > 0) {
         const double inv = 1.0 / (double)n;
         co[0] = (float)((double)ak[0] * fix_inv * inv);
@@ -533,44 +613,60 @@ __global__ void k_update(long long *acc, const float *centres_in, float *centres
     for (int c = 0; c < 6; ++c) ak[c] = 0;
 }
 
-// Sums of the pixels of each label from an explicit label map (used for an
-// update from given labels, e.g. a learned warm start). One thread per
-// pixel; warp-aggregated global atomics.
+__global__ void k_update(long long *acc, const float *centres_in, float *centres_out, int K, double fix_inv) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    update_centre(acc + (size_t)k * 6, centres_in + (size_t)k * 6, centres_out + (size_t)k * 6, fix_inv);
+}
+
+__global__ void k_update_batch(const FrameArgs *frames, int n, int total) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int f = find_frame<kCentreBase>(frames, n, g);
+    const FrameArgs &a = frames[f];
+    const size_t k = (size_t)(g - a.centre_base) * 6;
+    update_centre(a.acc + k, a.centres_out + k, a.centres_out + k, 1.0 / (double)a.fix_scale);
+}
+
+// Sums of the pixels of each label from an explicit label map (an update
+// from given labels, e.g. a learned warm start). One thread per pixel;
+// warp-aggregated global atomics.
 __global__ void k_accumulate_labels(const float *feat, int W, int H, int P, const int32_t *labels, int K,
                                     long long *acc, float fs) {
     const int lane = threadIdx.x & 31;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int x = (int)(i % W), y = (int)(i / W);
-    int key = -1;
-    int v[6] = {0, 0, 0, 0, 0, 0};
-    if (i < (long long)W * H) {
-        const int k = labels[i];
-        if (k >= 0 && k < K) {
-            const size_t plane = (size_t)H * P, off = (size_t)y * P + x;
-            key = k;
-            v[0] = __float2int_rn(feat[off] * fs);
-            v[1] = __float2int_rn(feat[plane + off] * fs);
-            v[2] = __float2int_rn(feat[2 * plane + off] * fs);
-            v[3] = x;
-            v[4] = y;
-            v[5] = 1;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int y = blockIdx.y; y < H; y += gridDim.y) {
+        int key = -1;
+        int v[6] = {0, 0, 0, 0, 0, 0};
+        if (x < W) {
+            const int k = labels[(size_t)y * W + x];
+            if (k >= 0 && k < K) {
+                const size_t plane = (size_t)H * P, off = (size_t)y * P + x;
+                key = k;
+                v[0] = __float2int_rn(feat[off] * fs);
+                v[1] = __float2int_rn(feat[plane + off] * fs);
+                v[2] = __float2int_rn(feat[2 * plane + off] * fs);
+                v[3] = x;
+                v[4] = y;
+                v[5] = 1;
+            }
         }
-    }
-    unsigned pending = __ballot_sync(kFull, key >= 0);
-    while (pending) {
-        const int leader = __ffs(pending) - 1;
-        const int k = __shfl_sync(kFull, key, leader);
-        const bool mine = key == k;
-        const unsigned grp = __ballot_sync(kFull, mine);
-        int s[6];
+        unsigned pending = __ballot_sync(kFull, key >= 0);
+        while (pending) {
+            const int leader = __ffs(pending) - 1;
+            const int k = __shfl_sync(kFull, key, leader);
+            const bool mine = key == k;
+            const unsigned grp = __ballot_sync(kFull, mine);
+            int s[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) s[c] = __reduce_add_sync(kFull, mine ? v[c] : 0);
-        if (lane == leader) {
-            unsigned long long *g = reinterpret_cast<unsigned long long *>(acc) + (size_t)k * 6;
+            for (int c = 0; c < 6; ++c) s[c] = __reduce_add_sync(kFull, mine ? v[c] : 0);
+            if (lane == leader) {
+                unsigned long long *g = reinterpret_cast<unsigned long long *>(acc) + (size_t)k * 6;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) atomicAdd(&g[c], (unsigned long long)(long long)s[c]);
+                for (int c = 0; c < 6; ++c) atomicAdd(&g[c], (unsigned long long)(long long)s[c]);
+            }
+            pending &= ~grp;
         }
-        pending &= ~grp;
     }
 }
 
@@ -592,36 +688,93 @@ __global__ void k_convert(ConvConsts cc, const uint8_t *rgb, int W, int H, int C
 }
 
 // ---------------------------------------------------------------------------
-// Connectivity: one double-buffered pass.
+// Connectivity: one double-buffered pass, 4 pixels per thread.
 // ---------------------------------------------------------------------------
 
-__global__ void k_connectivity(const int32_t *__restrict__ in, int32_t *__restrict__ out, int W, int H) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= W) return;
-    for (int y = blockIdx.y; y < H; y += gridDim.y) {
-        const size_t i = (size_t)y * W + x;
-        const int32_t own = __ldg(in + i);
-        int32_t nb[4];
-        int n = 0;
-        if (x > 0) nb[n++] = __ldg(in + i - 1);
-        if (y > 0) nb[n++] = __ldg(in + i - W);
-        if (x < W - 1) nb[n++] = __ldg(in + i + 1);
-        if (y < H - 1) nb[n++] = __ldg(in + i + W);
-        bool all_differ = n > 0;
-        for (int j = 0; j < n; ++j) all_differ &= (nb[j] != own);
-        int32_t result = own;
-        if (all_differ) {
-            int best_count = 0;
-            for (int j = 0; j < n; ++j) {
-                int cnt = 0;
-                for (int q = 0; q < n; ++q) cnt += (nb[q] == nb[j]);
-                if (cnt > best_count) {
-                    best_count = cnt;
-                    result = nb[j];
-                }
-            }
+// Majority rule for one pixel: own label and its neighbours in the order
+// left, up, right, down, with in-image flags.
+__device__ __forceinline__ int32_t connect_rule(int32_t own, const int32_t (&nb)[4], const bool (&ok)[4]) {
+    bool any = false, all_differ = true;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        any |= ok[j];
+        all_differ &= !ok[j] || nb[j] != own;
+    }
+    if (!any || !all_differ) return own;
+    int32_t result = own;
+    int best_count = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (!ok[j]) continue;
+        int cnt = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cnt += (ok[q] && nb[q] == nb[j]) ? 1 : 0;
+        if (cnt > best_count) {
+            best_count = cnt;
+            result = nb[j];
         }
-        out[i] = result;
+    }
+    return result;
+}
+
+__device__ __forceinline__ void connect_row4(const int32_t *__restrict__ in, int32_t *__restrict__ out, int W, int H,
+                                             int x0, int y, bool vec) {
+    const size_t row = (size_t)y * W;
+    int32_t c[4] = {0, 0, 0, 0}, up[4] = {0, 0, 0, 0}, dn[4] = {0, 0, 0, 0};
+    if (vec) {
+        const int4 a = __ldg(reinterpret_cast<const int4 *>(in + row + x0));
+        c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+        if (y > 0) {
+            const int4 u = __ldg(reinterpret_cast<const int4 *>(in + row - W + x0));
+            up[0] = u.x; up[1] = u.y; up[2] = u.z; up[3] = u.w;
+        }
+        if (y < H - 1) {
+            const int4 d = __ldg(reinterpret_cast<const int4 *>(in + row + W + x0));
+            dn[0] = d.x; dn[1] = d.y; dn[2] = d.z; dn[3] = d.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool okx = x0 + j < W;
+            c[j] = okx ? __ldg(in + row + x0 + j) : 0;
+            up[j] = (okx && y > 0) ? __ldg(in + row - W + x0 + j) : 0;
+            dn[j] = (okx && y < H - 1) ? __ldg(in + row + W + x0 + j) : 0;
+        }
+    }
+    const int32_t left = x0 > 0 ? __ldg(in + row + x0 - 1) : 0;
+    const int32_t right = x0 + 4 < W ? __ldg(in + row + x0 + 4) : 0;
+    int32_t r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int x = x0 + j;
+        const int32_t nb[4] = {j > 0 ? c[j - 1] : left, up[j], j < 3 ? c[j + 1] : right, dn[j]};
+        const bool ok[4] = {x > 0, y > 0, x < W - 1, y < H - 1};
+        r[j] = connect_rule(c[j], nb, ok);
+    }
+    if (vec) {
+        *reinterpret_cast<int4 *>(out + row + x0) = make_int4(r[0], r[1], r[2], r[3]);
+    } else {
+        for (int j = 0; j < 4 && x0 + j < W; ++j) out[row + x0 + j] = r[j];
+    }
+}
+
+__global__ void k_connectivity(const int32_t *__restrict__ in, int32_t *__restrict__ out, int W, int H, int vec) {
+    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x0 >= W) return;
+    for (int y = blockIdx.y; y < H; y += gridDim.y) connect_row4(in, out, W, H, x0, y, vec != 0);
+}
+
+// pass 0: labels -> lbl_tmp; pass 1: lbl_tmp -> labels. blockIdx.y strides
+// over the concatenated rows of all frames.
+__global__ void k_connectivity_batch(const FrameArgs *frames, int n, int total_rows, int pass) {
+    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    for (int gr = blockIdx.y; gr < total_rows; gr += gridDim.y) {
+        const int f = find_frame<kRowBase>(frames, n, gr);
+        const FrameArgs &a = frames[f];
+        if (x0 >= a.W) continue;
+        const int32_t *in = pass == 0 ? a.labels : a.lbl_tmp;
+        int32_t *out = pass == 0 ? a.lbl_tmp : a.labels;
+        connect_row4(in, out, a.W, a.H, x0, gr - a.row_base, a.labels_vec != 0);
     }
 }
 
@@ -633,7 +786,9 @@ cudaError_t upload_lut(const float *lut256) { return cudaMemcpyToSymbol(g_lut, l
 
 template <bool F, bool L, bool SM>
 static cudaError_t set_smem(int bytes) {
-    return cudaFuncSetAttribute(k_assign<F, L, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_assign<F, L, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_assign_batch<F, L, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t configure_kernels(size_t max_smem) {
@@ -649,9 +804,14 @@ cudaError_t configure_kernels(size_t max_smem) {
     return set_smem<false, false, false>(b);
 }
 
-cudaError_t launch_init_from_rgb(const FrameArgs &a, float *centres, cudaStream_t s) {
+cudaError_t launch_init_from_rgb(const FrameArgs &a, cudaStream_t s) {
     const int K = a.ns_c * a.ns_r;
-    k_init_rgb<<<(K + 127) / 128, 128, 0, s>>>(a, centres, a.acc);
+    k_init_rgb<<<(K + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_batch(const FrameArgs *d_frames, int n, int total_centres, cudaStream_t s) {
+    k_init_batch<<<(total_centres + 127) / 128, 128, 0, s>>>(d_frames, n, total_centres);
     return cudaGetLastError();
 }
 
@@ -668,12 +828,10 @@ cudaError_t launch_zero_acc(long long *acc, int K, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_assign(const FrameArgs &a, bool first, bool last, bool store_feat, size_t smem,
-                          cudaStream_t s) {
+cudaError_t launch_assign(const FrameArgs &a, bool first, bool last, bool store_feat, size_t smem, cudaStream_t s) {
     const dim3 grid((a.W + kTileW - 1) / kTileW, (a.H + kTileH - 1) / kTileH);
     const int sf = store_feat ? 1 : 0;
-    const bool same = (a.S % kPPT) == 0;
-    if (same) {
+    if ((a.S % kPPT) == 0) {
         if (first && last) k_assign<true, true, true><<<grid, kThreads, smem, s>>>(a, sf);
         else if (first) k_assign<true, false, true><<<grid, kThreads, smem, s>>>(a, sf);
         else if (last) k_assign<false, true, true><<<grid, kThreads, smem, s>>>(a, sf);
@@ -687,29 +845,77 @@ cudaError_t launch_assign(const FrameArgs &a, bool first, bool last, bool store_
     return cudaGetLastError();
 }
 
+cudaError_t launch_assign_batch(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool first,
+                                bool last, size_t smem, int grid, cudaStream_t s) {
+    if (grid > total_tiles) grid = total_tiles;
+    if (grid < 1) grid = 1;
+    const int N = n, T = total_tiles, Wm = win_max;
+    if (same) {
+        if (first && last) k_assign_batch<true, true, true><<<grid, kThreads, smem, s>>>(d_frames, N, T, Wm);
+        else if (first) k_assign_batch<true, false, true><<<grid, kThreads, smem, s>>>(d_frames, N, T, Wm);
+        else if (last) k_assign_batch<false, true, true><<<grid, kThreads, smem, s>>>(d_frames, N, T, Wm);
+        else k_assign_batch<false, false, true><<<grid, kThreads, smem, s>>>(d_frames, N, T, Wm);
+    } else {
+        if (first && last) k_assign_batch<true, true, false><<<grid, kThreads, smem, s>>>(d_frames, N, T, Wm);
+        else if (first) k_assign_batch<true, false, false><<<grid, kThreads, smem, s>>>(d_frames, N, T, Wm);
+        else if (last) k_assign_batch<false, true, false><<<grid, kThreads, smem, s>>>(d_frames, N, T, Wm);
+        else k_assign_batch<false, false, false><<<grid, kThreads, smem, s>>>(d_frames, N, T, Wm);
+    }
+    return cudaGetLastError();
+}
+
+template <bool F, bool L, bool SM>
+static int occupancy_of(size_t smem) {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_assign_batch<F, L, SM>, kThreads, smem) !=
+        cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+int assign_batch_occupancy(bool same, size_t smem) {
+    // The four pass kinds share the same shape; take the smallest.
+    int b = same ? occupancy_of<false, false, true>(smem) : occupancy_of<false, false, false>(smem);
+    const int b2 = same ? occupancy_of<true, false, true>(smem) : occupancy_of<true, false, false>(smem);
+    return b2 < b ? b2 : b;
+}
+
 cudaError_t launch_update(long long *acc, const float *centres_in, float *centres_out, int K, double fix_inv,
                           cudaStream_t s) {
     k_update<<<(K + 127) / 128, 128, 0, s>>>(acc, centres_in, centres_out, K, fix_inv);
     return cudaGetLastError();
 }
 
-cudaError_t launch_accumulate_labels(const float *feat, int W, int H, int P, const int32_t *labels, int K,
-                                     long long *acc, float fix_scale, cudaStream_t s) {
-    const long long n = (long long)W * H;
-    k_accumulate_labels<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(feat, W, H, P, labels, K, acc, fix_scale);
+cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_centres, cudaStream_t s) {
+    k_update_batch<<<(total_centres + 127) / 128, 128, 0, s>>>(d_frames, n, total_centres);
     return cudaGetLastError();
 }
 
-static dim3 rows_grid(int W, int H, int bx) { return dim3((W + bx - 1) / bx, H < 65535 ? H : 65535); }
+static dim3 rows_grid(int W, int H, int bx, int ppt) {
+    return dim3((W + bx * ppt - 1) / (bx * ppt), H < 65535 ? H : 65535);
+}
+
+cudaError_t launch_accumulate_labels(const float *feat, int W, int H, int P, const int32_t *labels, int K,
+                                     long long *acc, float fix_scale, cudaStream_t s) {
+    k_accumulate_labels<<<rows_grid(W, H, 128, 1), 128, 0, s>>>(feat, W, H, P, labels, K, acc, fix_scale);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_convert(const ConvConsts &cc, const uint8_t *rgb, int W, int H, int C, float *feat, int P,
                            cudaStream_t s) {
-    k_convert<<<rows_grid(W, H, 128), 128, 0, s>>>(cc, rgb, W, H, C, feat, P);
+    k_convert<<<rows_grid(W, H, 128, 1), 128, 0, s>>>(cc, rgb, W, H, C, feat, P);
     return cudaGetLastError();
 }
 
 cudaError_t launch_connectivity(const int32_t *in, int32_t *out, int W, int H, cudaStream_t s) {
-    k_connectivity<<<rows_grid(W, H, 128), 128, 0, s>>>(in, out, W, H);
+    const int vec = ((W & 3) == 0 && ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0) ? 1 : 0;
+    k_connectivity<<<rows_grid(W, H, 64, 4), 64, 0, s>>>(in, out, W, H, vec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_connectivity_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w, int pass,
+                                      cudaStream_t s) {
+    k_connectivity_batch<<<rows_grid(max_w, total_rows, 64, 4), 64, 0, s>>>(d_frames, n, total_rows, pass);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,117 @@
+"""The batched path: per-frame results bit-identical to single-frame
+slic_segment (exact integer sums make them order-independent), mixed sizes,
+S and m in one batch, initial centres, the launch-shape autotuner and its
+cache, and the error paths of the batch API."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1509_04232_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _cuda(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _frames_mixed():
+    return [dict(width=320, height=240, S=16, m=10.0), dict(width=333, height=257, S=13, m=20.0),
+            dict(width=640, height=480, S=8, m=5.0), dict(width=97, height=61, K=50, m=10.0),
+            dict(width=128, height=96, S=32, m=10.0, color_space=1), dict(width=64, height=48, S=3, m=10.0)]
+
+
+@pytest.mark.parametrize("iterations,conn", [(5, True), (0, False), (3, False)])
+def test_batch_bit_identical_to_single_frames(slic_gpu, iterations, conn):
+    import torch
+    pkg = slic_gpu
+    frames = _frames_mixed()
+    imgs = [_cuda(synth.voronoi_frame(f["width"], f["height"], 30, 6.0, 100 + i)) for i, f in enumerate(frames)]
+    bs = pkg.BatchSegmenter(frames, iterations=iterations, enforce_connectivity=conn)
+    bs.bind(imgs)
+    labels, centres = bs.segment()
+    for i, f in enumerate(frames):
+        seg = pkg.Segmenter(f["width"], f["height"], S=f.get("S", 0), K=f.get("K", 0), m=f["m"],
+                            iterations=iterations, enforce_connectivity=conn, color_space=f.get("color_space", 0))
+        l1, c1 = seg.segment(imgs[i])
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(labels[i].cpu().numpy(), l1.cpu().numpy())
+        np.testing.assert_array_equal(centres[i].cpu().numpy(), c1.cpu().numpy())
+
+
+def test_batch_matches_oracle_on_mixed_batch(slic_gpu):
+    pkg = slic_gpu
+    frames = _frames_mixed()[:4]
+    host = [synth.voronoi_frame(f["width"], f["height"], 30, 6.0, 200 + i) for i, f in enumerate(frames)]
+    bs = pkg.BatchSegmenter(frames, iterations=5)
+    bs.bind([_cuda(h) for h in host])
+    labels, _ = bs.segment()
+    for i, f in enumerate(frames):
+        ref = oracle.slic(host[i], K=f.get("K", 0), S=f.get("S", 0), m=f["m"], iterations=5)
+        assert np.mean(labels[i].cpu().numpy() == ref["labels"]) >= 0.995
+
+
+def test_batch_repeatable_and_launch_count(slic_gpu):
+    import torch
+    pkg = slic_gpu
+    frames = [dict(width=320, height=240, S=16)] * 3
+    bs = pkg.BatchSegmenter(frames, iterations=4)
+    bs.bind([_cuda(synth.small_image(i)) for i in range(3)])
+    l1 = [t.clone() for t in bs.segment()[0]]
+    n0 = bs.info[1]
+    l2 = bs.segment()[0]
+    torch.cuda.synchronize()
+    assert bs.info[1] - n0 == 2 * 4 + 4      # independent of the number of frames
+    for a, b in zip(l1, l2):
+        assert torch.equal(a, b)
+
+
+def test_batch_initial_centres(slic_gpu):
+    """Frames with given initial centres start from them (video warm start)."""
+    pkg = slic_gpu
+    img = synth.small_image(7)
+    ref_prev = oracle.slic(img, K=300, m=10, iterations=3)
+    init = _cuda(ref_prev["centres"].astype(np.float32))
+    bs = pkg.BatchSegmenter([dict(width=320, height=240, K=300)] * 2, iterations=0, enforce_connectivity=False)
+    bs.bind([_cuda(img), _cuda(img)], init_centres=[init, None])
+    labels, centres = bs.segment()
+    want = oracle.slic(img, K=300, m=10, iterations=0, enforce_connectivity=False,
+                       init_centres=ref_prev["centres"].astype(np.float32).astype(float))
+    grid = oracle.slic(img, K=300, m=10, iterations=0, enforce_connectivity=False)
+    assert np.mean(labels[0].cpu().numpy() == want["labels"]) >= 0.999
+    assert np.mean(labels[1].cpu().numpy() == grid["labels"]) >= 0.999
+    np.testing.assert_array_equal(centres[0].cpu().numpy(), ref_prev["centres"].astype(np.float32))
+
+
+def test_autotune_writes_and_reuses_cache(slic_gpu, tmp_path):
+    pkg = slic_gpu
+    frames = [dict(width=640, height=480, S=16), dict(width=320, height=240, S=8)]
+    bs = pkg.BatchSegmenter(frames, iterations=2)
+    bs.bind([_cuda(synth.voronoi_frame(f["width"], f["height"], 20, 6.0, 5)) for f in frames])
+    cache = str(tmp_path / "tune.jsonl")
+    c1 = bs.autotune(cache)
+    assert c1 >= 1
+    line = json.loads(open(cache).read().splitlines()[0])
+    assert line["ctas_per_sm"] == c1 and "640x480s16" in line["key"]
+    bs.set_tuning(0)
+    assert bs.autotune(cache) == c1          # served from the cache
+    assert len(open(cache).read().splitlines()) == 1
+    assert bs.info[2] == c1
+
+
+def test_batch_errors(slic_gpu):
+    pkg = slic_gpu
+    from paper_1509_04232_gb300 import _binding
+    bad = [pkg.slic_params(64, 48, 0, 16, 10.0, 3, 0, 1, 3), pkg.slic_params(64, 48, 0, 16, 10.0, 4, 0, 1, 3)]
+    with pytest.raises(pkg.SlicError) as ei:
+        pkg.slic_batch_create(bad)
+    assert ei.value.status == _binding.SLIC_ERR_INVALID and "same iterations" in str(ei.value)
+    b = pkg.slic_batch_create(bad[:1])
+    with pytest.raises(pkg.SlicError) as ei:
+        pkg.slic_batch_segment(b)
+    assert ei.value.status == _binding.SLIC_ERR_STATE
+    pkg.slic_batch_destroy(b)
