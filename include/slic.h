@@ -187,6 +187,11 @@ slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stre
    (any may be NULL). */
 slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm);
 
+/* Wait for the device, then report whether a bounded wait inside the
+   batch's kernels gave up since the last call (SLIC_ERR_TIMEOUT; the
+   affected tiles' results are then incomplete). Clears the flag. */
+slic_status slic_batch_status(slic_batch b);
+
 /* Device time of the batch's assignment launches, as slic_profile_enable /
    slic_profile_read do for a handle. */
 slic_status slic_batch_profile_enable(slic_batch b, int enable);

@@ -12,6 +12,7 @@ from __future__ import annotations
 from ._binding import (SLIC_CIELAB, SLIC_RGB, SLIC_XYZ, SlicError, library_path, slic_assign,  # noqa: F401
                        slic_batch_autotune, slic_batch_create, slic_batch_destroy, slic_batch_info,
                        slic_batch_last_error, slic_batch_profile_enable, slic_batch_profile_read, slic_batch_segment, slic_batch_set_buffers, slic_batch_set_tuning,
+                       slic_batch_status,
                        slic_connectivity_pass, slic_convert, slic_create, slic_destroy, slic_grid,
                        slic_init_centres, slic_last_error, slic_launch_count, slic_params,
                        slic_profile_enable, slic_profile_read, slic_segment, slic_segment_noalloc,
@@ -153,6 +154,10 @@ class BatchSegmenter:
     @property
     def info(self):
         return slic_batch_info(self.handle)
+
+    def status(self):
+        """Raises SlicError(SLIC_ERR_TIMEOUT) if a bounded device wait gave up."""
+        slic_batch_status(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -61,6 +61,7 @@ _SIGNATURES = {
     "slic_batch_info": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                         ctypes.POINTER(_I)],
     "slic_batch_destroy": [_P],
+    "slic_batch_status": [_P],
     "slic_batch_profile_enable": [_P, _I],
     "slic_batch_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
 }
@@ -215,6 +216,11 @@ def slic_batch_info(b: int):
     px, n, c = ctypes.c_longlong(), ctypes.c_longlong(), _I()
     _bcheck(lib().slic_batch_info(b, ctypes.byref(px), ctypes.byref(n), ctypes.byref(c)), b)
     return px.value, n.value, c.value
+
+
+def slic_batch_status(b: int) -> None:
+    """Raise SlicError(SLIC_ERR_TIMEOUT) if a bounded device wait gave up."""
+    _bcheck(lib().slic_batch_status(b), b)
 
 
 def slic_batch_profile_enable(b: int, enable: bool) -> None:

@@ -6,6 +6,8 @@
 #include "slic.h"
 #include "slic_internal.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -31,9 +33,12 @@ struct slic_batch_ctx {
     int total_tiles = 0, total_centres = 0, total_rows = 0, max_w = 0, win_max = 0;
     long long total_pixels = 0;
     bool same = true;
+    bool pipe = false;       // passes after the first use the pipelined kernel
     bool buffers_set = false;
     size_t smem = 0;
     int occupancy = 0;
+    int max_ring = 0;
+    int *d_err = nullptr;    // device flag: a bounded wait timed out
     int ctas_per_sm = 0;  // 0: occupancy
     long long launches = 0;
     bool profiling = false;
@@ -55,6 +60,46 @@ slic_status bfail(slic_batch_ctx *b, slic_status st, const std::string &msg) {
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// cuTensorMapEncodeTiled from the driver, found once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor maps of one frame for the pipelined assignment: the features as a
+// [3][H][P] f32 tensor copied in 32x32x3 boxes, and the padded centre table
+// as a [ns_r+2][(ns_c+2)*8] f32 tensor copied in box_h x box_w*8 boxes.
+bool encode_maps(FrameArgs &a) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || a.box_w * 8 > 256 || a.box_h > 256) return false;
+    const cuuint64_t fdim[3] = {(cuuint64_t)a.P, (cuuint64_t)a.H, 3};
+    const cuuint64_t fstride[2] = {(cuuint64_t)a.P * 4, (cuuint64_t)a.P * a.H * 4};
+    const cuuint32_t fbox[3] = {(cuuint32_t)kTileW, (cuuint32_t)kTileH, 3};
+    const cuuint32_t ones[3] = {1, 1, 1};
+    if (enc(&a.feat_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.feat, fdim, fstride, fbox, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t cdim[2] = {(cuuint64_t)(a.ns_c + 2) * 8, (cuuint64_t)(a.ns_r + 2)};
+    const cuuint64_t cstride[1] = {(cuuint64_t)(a.ns_c + 2) * 32};
+    const cuuint32_t cbox[2] = {(cuuint32_t)a.box_w * 8, (cuuint32_t)a.box_h};
+    return enc(&a.ctab_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.ctab, cdim, cstride, cbox, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 bool valid_params(const slic_params &p, std::string &why) {
     if (p.width <= 0 || p.height <= 0 || p.width > (1 << 20) || p.height > (1 << 20) ||
@@ -145,7 +190,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
 
     // Geometry, bases and the scratch layout.
     size_t bytes = 0;
-    std::vector<size_t> off_feat(n_frames), off_acc(n_frames), off_lbl(n_frames);
+    std::vector<size_t> off_feat(n_frames), off_acc(n_frames), off_lbl(n_frames), off_ctab(n_frames);
     long long tiles = 0, centres = 0, rows = 0;
     for (int f = 0; f < n_frames; ++f) {
         const slic_params &p = params[f];
@@ -179,6 +224,11 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
             return bfail(nullptr, SLIC_ERR_INVALID, "batch too large (tiles, centres or rows exceed 2^31)");
         }
         b->win_max = std::max(b->win_max, assign_max_window(S, a.ns_c, a.ns_r));
+        {
+            const int span = (kTileW - 1) / S + 2, spanh = (kTileH - 1) / S + 2;
+            a.box_w = std::min(span, a.ns_c) + 2;
+            a.box_h = std::min(spanh, a.ns_r) + 2;
+        }
         b->max_w = std::max(b->max_w, p.width);
         b->same = b->same && (S % kPPT) == 0;
         b->total_pixels += (long long)p.width * p.height;
@@ -188,7 +238,12 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         bytes += align256(sizeof(long long) * 6 * (size_t)a.ns_c * a.ns_r);
         off_lbl[f] = bytes;
         bytes += align256(sizeof(int32_t) * (size_t)p.width * p.height);
+        off_ctab[f] = bytes;
+        bytes += align256(sizeof(float) * 8 * (size_t)(a.ns_c + 2) * (a.ns_r + 2));
+        b->max_ring = std::max(b->max_ring, 2 * (a.ns_c + 2) + 2 * a.ns_r);
     }
+    const size_t off_err = bytes;
+    bytes += 256;
     b->total_tiles = (int)tiles;
     b->total_centres = (int)centres;
     b->total_rows = (int)rows;
@@ -205,7 +260,9 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         delete b;
         return bfail(nullptr, SLIC_ERR_CUDA, std::string("CUDA set-up: ") + cudaGetErrorString(e));
     }
+    b->pipe = !assign_direct_acc(b->win_max);
     b->occupancy = std::max(1, assign_batch_occupancy(b->same, b->smem));
+    if (b->pipe) b->occupancy = std::max(1, std::min(b->occupancy, assign_pipe_occupancy(b->same, b->win_max)));
     if (cudaMalloc(&b->scratch, bytes) != cudaSuccess ||
         cudaMalloc(&b->d_frames, sizeof(FrameArgs) * n_frames) != cudaSuccess) {
         cudaGetLastError();
@@ -219,6 +276,13 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         a.feat = reinterpret_cast<float *>(b->scratch + off_feat[f]);
         a.acc = reinterpret_cast<long long *>(b->scratch + off_acc[f]);
         a.lbl_tmp = reinterpret_cast<int32_t *>(b->scratch + off_lbl[f]);
+        a.ctab = reinterpret_cast<float *>(b->scratch + off_ctab[f]);
+        if (b->pipe && !encode_maps(a)) b->pipe = false;  // then every pass uses k_assign_batch
+    }
+    b->d_err = reinterpret_cast<int *>(b->scratch + off_err);
+    if (cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess) {
+        slic_batch_destroy(b);
+        return bfail(nullptr, SLIC_ERR_CUDA, "clearing the error flag failed");
     }
     *out = b;
     return SLIC_OK;
@@ -257,6 +321,9 @@ slic_status slic_batch_set_buffers(slic_batch b, const uint8_t *const *d_images,
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_frames, b->frames.data(), sizeof(FrameArgs) * b->n, cudaMemcpyHostToDevice);
+    // Sentinel ring of the padded centre tables (geometry only).
+    if (e == cudaSuccess) e = launch_fill_ring(b->d_frames, b->n, b->max_ring, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("frame table upload: ") + cudaGetErrorString(e));
     b->buffers_set = true;
     return SLIC_OK;
@@ -287,8 +354,12 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
                 cudaEventRecordWithFlags(b->events[b->ev_used].first, s, cudaEventRecordExternal);
                 e1 = b->events[b->ev_used++].second;
             }
-            e = launch_assign_batch(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == 0,
-                                    pass == b->iterations, b->smem, grid, s);
+            if (pass > 0 && b->pipe)
+                e = launch_assign_pipe(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == b->iterations,
+                                       grid, b->d_err, s);
+            else
+                e = launch_assign_batch(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == 0,
+                                        pass == b->iterations, b->smem, grid, s);
             if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
             ++n_launch;
         }
@@ -380,6 +451,17 @@ slic_status slic_batch_profile_read(slic_batch b, double *assign_ms, long long *
     }
     *assign_ms = total;
     *assign_launches = (long long)b->ev_used;
+    return SLIC_OK;
+}
+
+slic_status slic_batch_status(slic_batch b) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    int flag = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && flag) e = cudaMemset(b->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+    if (flag) return bfail(b, SLIC_ERR_TIMEOUT, "a bounded wait inside the assignment kernel timed out");
     return SLIC_OK;
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace slicgb {
@@ -35,6 +36,8 @@ struct ConvConsts {
 // parameter for single-frame launches, an entry of a device-side table for
 // batched ones).
 struct FrameArgs {
+    CUtensorMap feat_map;   // features as a [3][H][P] f32 tensor, box 32x32x3 (batched path)
+    CUtensorMap ctab_map;   // padded centre table as [(ns_r+2)][(ns_c+2)*8] f32, box box_w*8 x box_h
     ConvConsts conv;
     const uint8_t *rgb;     // [H][W][C]
     float *feat;            // 3 planes [H][P]; plane stride H*P
@@ -44,6 +47,7 @@ struct FrameArgs {
     int32_t *labels;        // [H][W]
     int32_t *lbl_tmp;       // [H][W] connectivity ping-pong (batched path)
     const float *init;      // [K][6] initial centres instead of the grid (batched path)
+    float *ctab;            // [(ns_r+2)(ns_c+2)][8] centres with a sentinel ring (batched path)
     int W, H, P, C, S, ns_c, ns_r;
     float w;                // m / S
     int win_max;            // largest centre window of any tile (sizes shared memory)
@@ -56,6 +60,7 @@ struct FrameArgs {
     int tile_base;          // first tile / centre / row of this frame in the
     int centre_base;        // batch's concatenated lists (0 for a single
     int row_base;           // frame)
+    int box_w, box_h;       // window box of the centre-table copies (cells)
 };
 
 // Shared memory for one assignment CTA whose tile spans at most win_n cells.
@@ -87,6 +92,14 @@ cudaError_t launch_assign_batch(const FrameArgs *d_frames, int n, int total_tile
 cudaError_t launch_update(long long *acc, const float *centres_in, float *centres_out, int K, double fix_inv,
                           cudaStream_t s);
 cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_centres, cudaStream_t s);
+// Pipelined (TMA bulk copies, mbarrier) assignment for the passes after the
+// first, reading features and the padded centre table; *err is set on a
+// timed-out wait.
+cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool last,
+                               int grid, int *err, cudaStream_t s);
+size_t assign_pipe_smem_bytes(int win_n, bool last);
+int assign_pipe_occupancy(bool same, int win_n);
+cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cudaStream_t s);
 cudaError_t launch_accumulate_labels(const float *feat, int W, int H, int P, const int32_t *labels, int K,
                                      long long *acc, float fix_scale, cudaStream_t s);
 cudaError_t launch_convert(const ConvConsts &cc, const uint8_t *rgb, int W, int H, int C, float *feat, int P,

@@ -166,6 +166,30 @@ __global__ void k_init_batch(const FrameArgs *frames, int n, int total) {
     } else {
         init_centre(a, k);
     }
+    if (a.ctab) {
+        const int r = k / a.ns_c, c = k - (k / a.ns_c) * a.ns_c;
+        float *t = a.ctab + ((size_t)(r + 1) * (a.ns_c + 2) + c + 1) * 8;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) t[q] = a.centres_out[(size_t)k * 6 + q];
+    }
+}
+
+// Sentinel ring of the padded centre tables (ring index i of frame f).
+__global__ void k_fill_ring(const FrameArgs *frames, int n, int max_ring) {
+    const int f = blockIdx.y;
+    if (f >= n) return;
+    const FrameArgs &a = frames[f];
+    const int cw = a.ns_c + 2, ch = a.ns_r + 2;
+    const int ring = 2 * cw + 2 * (ch - 2);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ring && i < max_ring; i += gridDim.x * blockDim.x) {
+        int r, c;
+        if (i < cw) { r = 0; c = i; }
+        else if (i < 2 * cw) { r = ch - 1; c = i - cw; }
+        else { const int j = i - 2 * cw; r = 1 + (j >> 1); c = (j & 1) ? cw - 1 : 0; }
+        float *t = a.ctab + ((size_t)r * cw + c) * 8;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t[q] = 1e18f;
+    }
 }
 
 __global__ void k_init_feat(const float *feat, int W, int H, int P, int S, int ns_c, int ns_r, float *centres) {
@@ -589,6 +613,358 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_batch(const FrameArgs *f
 }
 
 // ---------------------------------------------------------------------------
+// Pipelined assignment for the passes after the first (batched path)
+// ---------------------------------------------------------------------------
+//
+// Persistent CTAs walk the batch's tiles with two shared-memory stages. While
+// the CTA evaluates tile i from stage s, one thread has already issued the
+// two tensor-map copies of tile i+1 into stage s^1 (cp.async.bulk.tensor,
+// completion counted on the stage's mbarrier): the 32x32x3 box of features
+// and the box of 32-byte centre records around the tile from the frame's
+// padded centre table (its sentinel ring makes every window in-bounds).
+// Warp w evaluates rows 4w..4w+3 of the tile, lane l the 4 pixels at column
+// 4*(l%8) of row l/8, so each quarter-warp reads one 128-byte row without
+// bank conflicts. One barrier per tile separates the accumulation into the
+// stage's private sums from their flush to the global sums.
+
+namespace {
+
+constexpr size_t kStageFeatBytes = (size_t)3 * kTileH * kTileW * 4;  // 12288
+constexpr unsigned kWaitPolls = 1u << 20;                         // x 1 us suspend hint: ~1 s bound
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Wait for the phase with the given parity to complete; gives up (returns
+// false) after kWaitPolls polls with a 1 us suspend hint each.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    for (unsigned i = 0; i < kWaitPolls; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity), "r"(1000u)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+struct TileGeom {
+    int tx0, ty0, wx0, wy0, wnx, wny;
+};
+
+__device__ __forceinline__ TileGeom tile_geom(const FrameArgs &a, int local) {
+    TileGeom g;
+    const int ty = local / a.tiles_x, tx = local - ty * a.tiles_x;
+    g.tx0 = tx * kTileW;
+    g.ty0 = ty * kTileH;
+    const int ccx0 = div_s(g.tx0, a.s_mul, a.S), ccx1 = div_s(min(g.tx0 + kTileW - 1, a.W - 1), a.s_mul, a.S);
+    const int ccy0 = div_s(g.ty0, a.s_mul, a.S), ccy1 = div_s(min(g.ty0 + kTileH - 1, a.H - 1), a.s_mul, a.S);
+    g.wx0 = ccx0 - 1;
+    g.wy0 = ccy0 - 1;
+    g.wnx = ccx1 - ccx0 + 3;
+    g.wny = ccy1 - ccy0 + 3;
+    return g;
+}
+
+// One thread: arm the stage's mbarrier with the byte count of both boxes
+// and issue the two tensor copies.
+__device__ __forceinline__ void issue_tile(const FrameArgs &a, const TileGeom &g, unsigned char *stage,
+                                           uint64_t *bar) {
+    const unsigned cen_bytes = (unsigned)a.box_w * (unsigned)a.box_h * 32u;
+    mbar_expect_tx(bar, (unsigned)kStageFeatBytes + cen_bytes);
+    tma_load_3d(stage, &a.feat_map, g.tx0, g.ty0, 0, bar);
+    tma_load_2d(stage + kStageFeatBytes, &a.ctab_map, (g.wx0 + 1) * 8, g.wy0 + 1, bar);
+}
+
+}  // namespace
+
+size_t assign_pipe_smem_bytes(int win_n, bool last) {
+    const size_t stage = kStageFeatBytes + (((size_t)win_n * 32 + 127) & ~(size_t)127);
+    const size_t acc = last ? 0 : (size_t)kWarps * win_n * 4 * sizeof(int);
+    return 2 * (stage + acc) + 64 + 128;  // + two mbarriers, the abort flag and base alignment
+}
+
+template <bool LAST, bool SAME>
+__global__ void __launch_bounds__(kThreads, 3) k_assign_pipe(const FrameArgs *frames, int n_frames, int total_tiles,
+                                                             int win_max, int *err) {
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    // Tensor copies want 128-byte aligned destinations.
+    unsigned char *smem_raw =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~(uintptr_t)127);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const size_t stage_bytes = kStageFeatBytes + (((size_t)win_max * 32 + 127) & ~(size_t)127);
+    const size_t acc_words = LAST ? 0 : (size_t)kWarps * win_max * 4;
+    unsigned *const wacc0 = reinterpret_cast<unsigned *>(smem_raw + 2 * stage_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + 2 * stage_bytes + 2 * acc_words * 4);
+    int *abort_flag = reinterpret_cast<int *>(bars + 2);
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
+    }
+    if (!LAST) {
+        for (int i = tid; i < (int)(2 * acc_words); i += kThreads) wacc0[i] = 0u;
+    }
+    __syncthreads();
+
+    int tile = blockIdx.x;
+    if (tile < total_tiles && tid == 0) {
+        const FrameArgs &a = frames[find_frame<kTileBase>(frames, n_frames, tile)];
+        issue_tile(a, tile_geom(a, tile - a.tile_base), smem_raw, &bars[0]);
+    }
+    unsigned parity = 0u;  // bit s: parity of the phase stage s completes next
+    const int lx = 4 * (lane & 7), ly = 4 * warp + (lane >> 3);
+    for (int it = 0; tile < total_tiles; ++it) {
+        const int s = it & 1;
+        unsigned char *const stage_s = smem_raw + (size_t)s * stage_bytes;
+        unsigned *const wacc_s = wacc0 + (size_t)s * acc_words;
+        const int next = tile + gridDim.x;
+        if (tid == 0 && next < total_tiles) {
+            const FrameArgs &an = frames[find_frame<kTileBase>(frames, n_frames, next)];
+            issue_tile(an, tile_geom(an, next - an.tile_base), smem_raw + (size_t)(s ^ 1) * stage_bytes,
+                       &bars[s ^ 1]);
+        }
+        const FrameArgs &a = frames[find_frame<kTileBase>(frames, n_frames, tile)];
+        const TileGeom g = tile_geom(a, tile - a.tile_base);
+        const int bw = a.box_w;
+        const bool ok_wait = mbar_wait(&bars[s], (parity >> s) & 1u);
+        parity ^= 1u << s;
+        if (!ok_wait) {
+            *abort_flag = 1;
+            atomicOr(err, 1);
+        }
+
+        const int W = a.W, H = a.H, S = a.S, ns_c = a.ns_c;
+        const unsigned s_mul = a.s_mul;
+        const float *feat = reinterpret_cast<const float *>(stage_s);
+        const float *cen = reinterpret_cast<const float *>(stage_s + kStageFeatBytes);
+        const int x = g.tx0 + lx, y = g.ty0 + ly;
+        const bool row_ok = ok_wait && (y < H) && (x < W);
+        float f0[kPPT] = {}, f1[kPPT] = {}, f2[kPPT] = {};
+        if (row_ok) {
+            const float4 v0 = *reinterpret_cast<const float4 *>(feat + (0 * kTileH + ly) * kTileW + lx);
+            const float4 v1 = *reinterpret_cast<const float4 *>(feat + (1 * kTileH + ly) * kTileW + lx);
+            const float4 v2 = *reinterpret_cast<const float4 *>(feat + (2 * kTileH + ly) * kTileW + lx);
+            f0[0] = v0.x; f0[1] = v0.y; f0[2] = v0.z; f0[3] = v0.w;
+            f1[0] = v1.x; f1[1] = v1.y; f1[2] = v1.z; f1[3] = v1.w;
+            f2[0] = v2.x; f2[1] = v2.y; f2[2] = v2.z; f2[3] = v2.w;
+        }
+        const int pcy = div_s(y, s_mul, S);
+        int cx[kPPT];
+        {
+            const int c0 = div_s(x, s_mul, S);
+            if (SAME) {
+#pragma unroll
+                for (int j = 0; j < kPPT; ++j) cx[j] = c0;
+            } else if (S >= kPPT) {
+                const int rem = x - c0 * S;
+#pragma unroll
+                for (int j = 0; j < kPPT; ++j) cx[j] = c0 + (rem + j >= S ? 1 : 0);
+            } else {
+#pragma unroll
+                for (int j = 0; j < kPPT; ++j) cx[j] = (x + j) / S;
+            }
+        }
+        // Eq. (1) over the nine window centres, as in assign_tile (window
+        // index = (cell row - wy0) * box_w + (cell column - wx0)).
+        unsigned bk[kPPT];
+#pragma unroll
+        for (int j = 0; j < kPPT; ++j) bk[j] = 0xFFFFFFFFu;
+        if (row_ok) {
+            const float w = a.w;
+            const float fy = (float)y;
+            float fxs[kPPT];
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) fxs[j] = (float)(x + j);
+            const int rowoff = (pcy - g.wy0) * bw - g.wx0;
+#pragma unroll
+            for (int jj = 0; jj < (SAME ? 1 : kPPT); ++jj) {
+                const int own = rowoff + cx[jj];
+#pragma unroll
+                for (int t = 0; t < 9; ++t) {
+                    const int wi = own + (t / 3 - 1) * bw + (t % 3 - 1);
+                    const float4 c = *reinterpret_cast<const float4 *>(cen + (size_t)wi * 8);
+                    const float ddy = cen[(size_t)wi * 8 + 4] - fy;
+                    const float ddy2 = ddy * ddy;
+#pragma unroll
+                    for (int j = (SAME ? 0 : jj); j < (SAME ? kPPT : jj + 1); ++j) {
+                        const float ddx = c.w - fxs[j];
+                        const float dl = c.x - f0[j], da = c.y - f1[j], db = c.z - f2[j];
+                        const float d_lab = fsqrt_approx(fmaf(dl, dl, fmaf(da, da, db * db)));
+                        const float D = fmaf(w, fsqrt_approx(fmaf(ddx, ddx, ddy2)), d_lab);
+                        bk[j] = min(bk[j], (__float_as_uint(D) & ~15u) | (unsigned)t);
+                    }
+                }
+            }
+        }
+        int best[kPPT];
+#pragma unroll
+        for (int j = 0; j < kPPT; ++j) {
+            const int t = (int)(bk[j] & 15u);
+            const int dy = t / 3 - 1, dx = t % 3 - 1;
+            const bool ok = row_ok && (x + j < W);
+            if (LAST)
+                best[j] = ok ? (pcy + dy) * ns_c + cx[j] + dx : -1;
+            else
+                best[j] = ok ? (pcy + dy - g.wy0) * bw + (cx[j] + dx - g.wx0) : -1;
+        }
+        if constexpr (LAST) {
+            if (row_ok) {
+                int32_t *out = a.labels + (size_t)y * W + x;
+                if (a.labels_vec) {
+                    *reinterpret_cast<int4 *>(out) = make_int4(best[0], best[1], best[2], best[3]);
+                } else {
+                    for (int j = 0; j < kPPT && x + j < W; ++j) out[j] = best[j];
+                }
+            }
+            __syncthreads();
+        } else {
+            const float fs = a.fix_scale;
+            unsigned v[kPPT][4];
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) {
+                v[j][0] = (unsigned)__float2int_rn(f0[j] * fs);
+                v[j][1] = (unsigned)__float2int_rn(f1[j] * fs);
+                v[j][2] = (unsigned)__float2int_rn(f2[j] * fs);
+                v[j][3] = (unsigned)(lx + j) + ((unsigned)ly << 12) + (1u << 24);
+            }
+#pragma unroll
+            for (int j = kPPT - 2; j >= 0; --j) {
+                if (best[j + 1] == best[j]) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) v[j][c] += v[j + 1][c];
+                }
+            }
+            unsigned *my = wacc_s + (size_t)warp * win_max * 4;
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) {
+                const int k = (j == 0 || best[j] != best[j - 1]) ? best[j] : -1;
+                if (k >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) atomicAdd(&my[k * 4 + c], v[j][c]);
+                }
+            }
+            __syncthreads();
+            // Flush this stage's private sums to the global sums and clear
+            // them for the tile after next (the next tile uses the other set).
+            for (int i = tid; i < g.wnx * g.wny * 4; i += kThreads) {
+                const int cell = i >> 2, c = i & 3;
+                const int qy = cell / g.wnx, qx = cell - qy * g.wnx;
+                const int idx = (qy * bw + qx) * 4 + c;
+                unsigned long long *gs =
+                    reinterpret_cast<unsigned long long *>(a.acc) + ((size_t)(g.wy0 + qy) * ns_c + g.wx0 + qx) * 6;
+                if (c < 3) {
+                    long long t = 0;
+#pragma unroll
+                    for (int q = 0; q < kWarps; ++q) {
+                        t += (int)wacc_s[(size_t)q * win_max * 4 + idx];
+                        wacc_s[(size_t)q * win_max * 4 + idx] = 0u;
+                    }
+                    if (t != 0) atomicAdd(&gs[c], (unsigned long long)t);
+                } else {
+                    long long xs = 0, ys = 0, n = 0;
+#pragma unroll
+                    for (int q = 0; q < kWarps; ++q) {
+                        const unsigned pk = wacc_s[(size_t)q * win_max * 4 + idx];
+                        wacc_s[(size_t)q * win_max * 4 + idx] = 0u;
+                        xs += pk & 0xFFFu;
+                        ys += (pk >> 12) & 0xFFFu;
+                        n += pk >> 24;
+                    }
+                    if (n != 0) {
+                        atomicAdd(&gs[3], (unsigned long long)(xs + n * g.tx0));
+                        atomicAdd(&gs[4], (unsigned long long)(ys + n * g.ty0));
+                        atomicAdd(&gs[5], (unsigned long long)n);
+                    }
+                }
+            }
+        }
+        if (*abort_flag) {
+            // A wait timed out: let the copies of the next tile land (bounded)
+            // before leaving, so none targets a CTA that has exited.
+            if (next < total_tiles) mbar_wait(&bars[s ^ 1], (parity >> (s ^ 1)) & 1u);
+            return;
+        }
+        tile = next;
+    }
+}
+
+template <bool L, bool SM>
+static int pipe_occupancy_of(size_t smem) {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_assign_pipe<L, SM>, kThreads, smem) != cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+int assign_pipe_occupancy(bool same, int win_n) {
+    const size_t sm = assign_pipe_smem_bytes(win_n, false);
+    return same ? pipe_occupancy_of<false, true>(sm) : pipe_occupancy_of<false, false>(sm);
+}
+
+cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool last,
+                               int grid, int *err, cudaStream_t s) {
+    if (grid > total_tiles) grid = total_tiles;
+    if (grid < 1) grid = 1;
+    const size_t smem = assign_pipe_smem_bytes(win_max, last);
+    cudaError_t e;
+    if (same) {
+        if (last) {
+            e = cudaFuncSetAttribute(k_assign_pipe<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_assign_pipe<true, true><<<grid, kThreads, smem, s>>>(d_frames, n, total_tiles, win_max, err);
+        } else {
+            e = cudaFuncSetAttribute(k_assign_pipe<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_assign_pipe<false, true><<<grid, kThreads, smem, s>>>(d_frames, n, total_tiles, win_max, err);
+        }
+    } else {
+        if (last) {
+            e = cudaFuncSetAttribute(k_assign_pipe<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_assign_pipe<true, false><<<grid, kThreads, smem, s>>>(d_frames, n, total_tiles, win_max, err);
+        } else {
+            e = cudaFuncSetAttribute(k_assign_pipe<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_assign_pipe<false, false><<<grid, kThreads, smem, s>>>(d_frames, n, total_tiles, win_max, err);
+        }
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cudaStream_t s) {
+    k_fill_ring<<<dim3((max_ring + 255) / 256, n), 256, 0, s>>>(d_frames, n, max_ring);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Update: centre = member mean; empty centre keeps position and colour.
 // ---------------------------------------------------------------------------
 
@@ -624,8 +1000,15 @@ __global__ void k_update_batch(const FrameArgs *frames, int n, int total) {
     if (g >= total) return;
     const int f = find_frame<kCentreBase>(frames, n, g);
     const FrameArgs &a = frames[f];
-    const size_t k = (size_t)(g - a.centre_base) * 6;
+    const int kk = g - a.centre_base;
+    const size_t k = (size_t)kk * 6;
     update_centre(a.acc + k, a.centres_out + k, a.centres_out + k, 1.0 / (double)a.fix_scale);
+    if (a.ctab) {
+        const int r = kk / a.ns_c, c = kk - r * a.ns_c;
+        float *t = a.ctab + ((size_t)(r + 1) * (a.ns_c + 2) + c + 1) * 8;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) t[q] = a.centres_out[k + q];
+    }
 }
 
 // Sums of the pixels of each label from an explicit label map (an update

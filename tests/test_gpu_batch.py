@@ -34,6 +34,7 @@ def test_batch_bit_identical_to_single_frames(slic_gpu, iterations, conn):
     bs = pkg.BatchSegmenter(frames, iterations=iterations, enforce_connectivity=conn)
     bs.bind(imgs)
     labels, centres = bs.segment()
+    bs.status()
     for i, f in enumerate(frames):
         seg = pkg.Segmenter(f["width"], f["height"], S=f.get("S", 0), K=f.get("K", 0), m=f["m"],
                             iterations=iterations, enforce_connectivity=conn, color_space=f.get("color_space", 0))
