@@ -678,6 +678,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
 
 struct TileGeom {
     int tx0, ty0, wx0, wy0, wnx, wny;
+    int f;                 // frame index
+    unsigned wnx_mul;      // ceil(2^32 / wnx): cell / wnx for the flush
 };
 
 __device__ __forceinline__ TileGeom tile_geom(const FrameArgs &a, int local) {
@@ -691,6 +693,7 @@ __device__ __forceinline__ TileGeom tile_geom(const FrameArgs &a, int local) {
     g.wy0 = ccy0 - 1;
     g.wnx = ccx1 - ccx0 + 3;
     g.wny = ccy1 - ccy0 + 3;
+    g.wnx_mul = (unsigned)((0x100000000ULL + (unsigned)g.wnx - 1) / (unsigned)g.wnx);
     return g;
 }
 
@@ -709,7 +712,8 @@ __device__ __forceinline__ void issue_tile(const FrameArgs &a, const TileGeom &g
 size_t assign_pipe_smem_bytes(int win_n, bool last) {
     const size_t stage = kStageFeatBytes + (((size_t)win_n * 32 + 127) & ~(size_t)127);
     const size_t acc = last ? 0 : (size_t)kWarps * win_n * 4 * sizeof(int);
-    return 2 * (stage + acc) + 64 + 128;  // + two mbarriers, the abort flag and base alignment
+    // + two mbarriers, the abort flag, two tile headers and base alignment
+    return 2 * (stage + acc) + 32 + 2 * sizeof(TileGeom) + 128;
 }
 
 template <bool LAST, bool SAME>
@@ -725,6 +729,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_pipe(const FrameArgs *fr
     unsigned *const wacc0 = reinterpret_cast<unsigned *>(smem_raw + 2 * stage_bytes);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + 2 * stage_bytes + 2 * acc_words * 4);
     int *abort_flag = reinterpret_cast<int *>(bars + 2);
+    TileGeom *hdr = reinterpret_cast<TileGeom *>(bars + 4);  // per stage, written by the issuing thread
 
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -739,9 +744,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_pipe(const FrameArgs *fr
 
     int tile = blockIdx.x;
     if (tile < total_tiles && tid == 0) {
-        const FrameArgs &a = frames[find_frame<kTileBase>(frames, n_frames, tile)];
-        issue_tile(a, tile_geom(a, tile - a.tile_base), smem_raw, &bars[0]);
+        const int f = find_frame<kTileBase>(frames, n_frames, tile);
+        TileGeom g = tile_geom(frames[f], tile - frames[f].tile_base);
+        g.f = f;
+        hdr[0] = g;
+        issue_tile(frames[f], g, smem_raw, &bars[0]);
     }
+    __syncthreads();
     unsigned parity = 0u;  // bit s: parity of the phase stage s completes next
     const int lx = 4 * (lane & 7), ly = 4 * warp + (lane >> 3);
     for (int it = 0; tile < total_tiles; ++it) {
@@ -749,13 +758,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_pipe(const FrameArgs *fr
         unsigned char *const stage_s = smem_raw + (size_t)s * stage_bytes;
         unsigned *const wacc_s = wacc0 + (size_t)s * acc_words;
         const int next = tile + gridDim.x;
+        const TileGeom g = hdr[s];
         if (tid == 0 && next < total_tiles) {
-            const FrameArgs &an = frames[find_frame<kTileBase>(frames, n_frames, next)];
-            issue_tile(an, tile_geom(an, next - an.tile_base), smem_raw + (size_t)(s ^ 1) * stage_bytes,
-                       &bars[s ^ 1]);
+            const int fn = find_frame<kTileBase>(frames, n_frames, next);
+            TileGeom gn = tile_geom(frames[fn], next - frames[fn].tile_base);
+            gn.f = fn;
+            hdr[s ^ 1] = gn;
+            issue_tile(frames[fn], gn, smem_raw + (size_t)(s ^ 1) * stage_bytes, &bars[s ^ 1]);
         }
-        const FrameArgs &a = frames[find_frame<kTileBase>(frames, n_frames, tile)];
-        const TileGeom g = tile_geom(a, tile - a.tile_base);
+        const FrameArgs &a = frames[g.f];
         const int bw = a.box_w;
         const bool ok_wait = mbar_wait(&bars[s], (parity >> s) & 1u);
         parity ^= 1u << s;
@@ -879,7 +890,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_pipe(const FrameArgs *fr
             // them for the tile after next (the next tile uses the other set).
             for (int i = tid; i < g.wnx * g.wny * 4; i += kThreads) {
                 const int cell = i >> 2, c = i & 3;
-                const int qy = cell / g.wnx, qx = cell - qy * g.wnx;
+                const int qy = (int)__umulhi((unsigned)cell, g.wnx_mul), qx = cell - qy * g.wnx;
                 const int idx = (qy * bw + qx) * 4 + c;
                 unsigned long long *gs =
                     reinterpret_cast<unsigned long long *>(a.acc) + ((size_t)(g.wy0 + qy) * ns_c + g.wx0 + qx) * 6;
