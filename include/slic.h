@@ -196,6 +196,10 @@ slic_status slic_batch_status(slic_batch b);
    slic_profile_read do for a handle. */
 slic_status slic_batch_profile_enable(slic_batch b, int enable);
 slic_status slic_batch_profile_read(slic_batch b, double *assign_ms, long long *assign_launches);
+/* The same records one by one, in enqueue order (pass 0, 1, ..., iterations
+   for each slic_batch_segment call): up to max_n durations (ms) into ms[],
+   their number into *n. */
+slic_status slic_batch_profile_times(slic_batch b, double *ms, int max_n, int *n);
 
 /* Release the batch (waits for the device first). NULL is accepted. */
 slic_status slic_batch_destroy(slic_batch b);

@@ -11,7 +11,8 @@ from __future__ import annotations
 
 from ._binding import (SLIC_CIELAB, SLIC_RGB, SLIC_XYZ, SlicError, library_path, slic_assign,  # noqa: F401
                        slic_batch_autotune, slic_batch_create, slic_batch_destroy, slic_batch_info,
-                       slic_batch_last_error, slic_batch_profile_enable, slic_batch_profile_read, slic_batch_segment, slic_batch_set_buffers, slic_batch_set_tuning,
+                       slic_batch_last_error, slic_batch_profile_enable, slic_batch_profile_read,
+                       slic_batch_profile_times, slic_batch_segment, slic_batch_set_buffers, slic_batch_set_tuning,
                        slic_batch_status,
                        slic_connectivity_pass, slic_convert, slic_create, slic_destroy, slic_grid,
                        slic_init_centres, slic_last_error, slic_launch_count, slic_params,

@@ -64,6 +64,7 @@ _SIGNATURES = {
     "slic_batch_status": [_P],
     "slic_batch_profile_enable": [_P, _I],
     "slic_batch_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
+    "slic_batch_profile_times": [_P, ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I)],
 }
 
 
@@ -231,6 +232,13 @@ def slic_batch_profile_read(b: int):
     ms, n = ctypes.c_double(), ctypes.c_longlong()
     _bcheck(lib().slic_batch_profile_read(b, ctypes.byref(ms), ctypes.byref(n)), b)
     return ms.value, n.value
+
+
+def slic_batch_profile_times(b: int, max_n: int = 4096):
+    buf = (ctypes.c_double * max_n)()
+    n = _I()
+    _bcheck(lib().slic_batch_profile_times(b, buf, max_n, ctypes.byref(n)), b)
+    return list(buf[:n.value])
 
 
 def slic_batch_destroy(b: int) -> None:

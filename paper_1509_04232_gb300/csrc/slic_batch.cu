@@ -465,6 +465,20 @@ slic_status slic_batch_status(slic_batch b) {
     return SLIC_OK;
 }
 
+slic_status slic_batch_profile_times(slic_batch b, double *ms, int max_n, int *n) {
+    if (!b || !n || (max_n > 0 && !ms)) return bfail(b, SLIC_ERR_INVALID, "NULL argument");
+    const int count = (int)std::min<size_t>(b->ev_used, (size_t)std::max(max_n, 0));
+    for (int i = 0; i < count; ++i) {
+        float t = 0.0f;
+        cudaError_t e = cudaEventSynchronize(b->events[i].second);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, b->events[i].first, b->events[i].second);
+        if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("profile event: ") + cudaGetErrorString(e));
+        ms[i] = t;
+    }
+    *n = count;
+    return SLIC_OK;
+}
+
 const char *slic_batch_last_error(slic_batch b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
 
 }  // extern "C"
