@@ -229,6 +229,56 @@ const char *slic_batch_last_error(slic_batch b);
 slic_status slic_segment_noalloc(const slic_params *params, const uint8_t *d_image, int32_t *d_labels,
                                  float *d_centres, void *stream);
 
+/* ---- Learned warm start ---------------------------------------------------
+   A 4-layer 3x3 convolutional network (5 -> 32 -> 32 -> 32 -> 9 channels,
+   ReLU between layers, zero padding; bfloat16 weights and stored
+   activations, FP32 accumulation on the tensor cores) that predicts, for
+   each pixel of an RGB image, logits over the 9 cells of its 3x3 cell
+   window (slot t = (dy+1)*3 + (dx+1), the scan order of the assignment).
+   Inputs per pixel: L/100, a/128, b/128, (x mod S)/S, (y mod S)/S. The
+   paper has no such network; it replaces the first k-means iterations
+   (its labels give initial centres through slic_update). Trained here by
+   softmax cross-entropy against the slots of reference labels, with Adam
+   (beta 0.9/0.999, eps 1e-8) on FP32 master weights. */
+typedef struct slic_net_ctx *slic_net;
+
+/* Network for batches of up to max_batch RGB images of width x height and
+   grid interval S; He-normal weights from `seed`, zero biases. Allocates the
+   activations of max_batch images. */
+slic_status slic_net_create(int max_batch, int width, int height, int S, unsigned long long seed, slic_net *out);
+slic_status slic_net_destroy(slic_net n);
+
+/* Number of parameters (real sizes): per layer W[3][3][Cin][Cout] then b[Cout]. */
+slic_status slic_net_param_count(slic_net n, size_t *count);
+
+/* Host copies of the FP32 master weights (which = 0) or of the gradients of
+   the last slic_net_gradients/slic_net_train_step (which = 1), in the order
+   of slic_net_param_count; `count` must equal it. Synchronous. */
+slic_status slic_net_get_params(slic_net n, int which, float *h_out, size_t count);
+/* Load master weights (e.g. a checkpoint); synchronous. */
+slic_status slic_net_set_params(slic_net n, const float *h_in, size_t count);
+
+/* Inference on `batch` images d_images uint8 [batch][H][W][3]: d_logits
+   float [batch][H][W][16] (first 9 used; may be NULL), d_labels int32
+   [batch][H][W] = the label of the highest-scoring in-grid slot (may be
+   NULL). */
+slic_status slic_net_forward(slic_net n, int batch, const uint8_t *d_images, float *d_logits, int32_t *d_labels,
+                             void *stream);
+
+/* Forward and backward for targets d_targets uint8 [batch][H][W] (slots
+   0..8, in-grid): gradients of the mean cross-entropy are kept for
+   slic_net_get_params(which = 1); d_stats (may be NULL) receives float [2] =
+   (sum of per-pixel losses, number of pixels whose argmax equals the
+   target). */
+slic_status slic_net_gradients(slic_net n, int batch, const uint8_t *d_images, const uint8_t *d_targets,
+                               float *d_stats, void *stream);
+
+/* slic_net_gradients, then one Adam step with learning rate lr. */
+slic_status slic_net_train_step(slic_net n, int batch, const uint8_t *d_images, const uint8_t *d_targets, float lr,
+                                float *d_stats, void *stream);
+
+const char *slic_net_last_error(slic_net n);
+
 /* Reason for the last failure on this handle (or of the last failed
    slic_create on this thread when h is NULL). Never NULL. */
 const char *slic_last_error(slic_handle h);

@@ -65,6 +65,14 @@ _SIGNATURES = {
     "slic_batch_profile_enable": [_P, _I],
     "slic_batch_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
     "slic_batch_profile_times": [_P, ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I)],
+    "slic_net_create": [_I, _I, _I, _I, ctypes.c_ulonglong, ctypes.POINTER(_P)],
+    "slic_net_destroy": [_P],
+    "slic_net_param_count": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "slic_net_get_params": [_P, _I, _P, ctypes.c_size_t],
+    "slic_net_set_params": [_P, _P, ctypes.c_size_t],
+    "slic_net_forward": [_P, _I, _P, _P, _P, _P],
+    "slic_net_gradients": [_P, _I, _P, _P, _P, _P],
+    "slic_net_train_step": [_P, _I, _P, _P, ctypes.c_float, _P, _P],
 }
 
 
@@ -89,6 +97,8 @@ def lib():
         L.slic_last_error.restype = ctypes.c_char_p
         L.slic_batch_last_error.argtypes = [_P]
         L.slic_batch_last_error.restype = ctypes.c_char_p
+        L.slic_net_last_error.argtypes = [_P]
+        L.slic_net_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -243,3 +253,58 @@ def slic_batch_profile_times(b: int, max_n: int = 4096):
 
 def slic_batch_destroy(b: int) -> None:
     _bcheck(lib().slic_batch_destroy(b), None)
+
+
+# --- learned warm start network ----------------------------------------------
+
+def slic_net_last_error(n) -> str:
+    return lib().slic_net_last_error(n).decode()
+
+
+def _ncheck(status: int, n):
+    if status != SLIC_OK:
+        raise SlicError(status, slic_net_last_error(n))
+
+
+def slic_net_create(max_batch: int, width: int, height: int, S: int, seed: int = 0) -> int:
+    n = _P()
+    _ncheck(lib().slic_net_create(max_batch, width, height, S, seed, ctypes.byref(n)), None)
+    return n.value
+
+
+def slic_net_destroy(n: int) -> None:
+    _ncheck(lib().slic_net_destroy(n), None)
+
+
+def slic_net_param_count(n: int) -> int:
+    c = ctypes.c_size_t()
+    _ncheck(lib().slic_net_param_count(n, ctypes.byref(c)), n)
+    return c.value
+
+
+def slic_net_get_params(n: int, which: int = 0):
+    import numpy as np
+    out = np.empty(slic_net_param_count(n), np.float32)
+    _ncheck(lib().slic_net_get_params(n, which, out.ctypes.data_as(_P), out.size), n)
+    return out
+
+
+def slic_net_set_params(n: int, params) -> None:
+    import numpy as np
+    arr = np.ascontiguousarray(params, dtype=np.float32)
+    _ncheck(lib().slic_net_set_params(n, arr.ctypes.data_as(_P), arr.size), n)
+
+
+def slic_net_forward(n: int, batch: int, d_images: int, d_logits: int | None, d_labels: int | None,
+                     stream: int = 0) -> None:
+    _ncheck(lib().slic_net_forward(n, batch, d_images, d_logits or None, d_labels or None, stream or None), n)
+
+
+def slic_net_gradients(n: int, batch: int, d_images: int, d_targets: int, d_stats: int | None,
+                       stream: int = 0) -> None:
+    _ncheck(lib().slic_net_gradients(n, batch, d_images, d_targets, d_stats or None, stream or None), n)
+
+
+def slic_net_train_step(n: int, batch: int, d_images: int, d_targets: int, lr: float, d_stats: int | None,
+                        stream: int = 0) -> None:
+    _ncheck(lib().slic_net_train_step(n, batch, d_images, d_targets, float(lr), d_stats or None, stream or None), n)

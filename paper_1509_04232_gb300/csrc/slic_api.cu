@@ -116,6 +116,7 @@ cudaError_t ensure_lut(int dev) {
 
 namespace slicgb {
 ConvConsts conv_consts(int color_space) { return make_conv(color_space); }
+void srgb_table(float lut[256]) { make_lut(lut); }
 cudaError_t device_setup(int dev, size_t smem) {
     cudaError_t e = ensure_lut(dev);
     if (e == cudaSuccess) e = ensure_smem(dev, smem);

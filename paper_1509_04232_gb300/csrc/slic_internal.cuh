@@ -32,6 +32,40 @@ struct ConvConsts {
     int color_space;  // 0 CIELAB, 1 RGB, 2 XYZ
 };
 
+#ifdef __CUDACC__
+static __device__ __forceinline__ float lab_f(const ConvConsts &cc, float t) {
+    return t > cc.eps ? cbrtf(t) : fmaf(cc.k_slope, t, cc.k_offset);
+}
+
+// Sec. 3 "Image space conversion" for one pixel. `lut` is the sRGB
+// linearisation table (shared or global memory).
+static __device__ __forceinline__ void convert_pixel(const ConvConsts &cc, unsigned r, unsigned g, unsigned b,
+                                              const float *lut, float &f0, float &f1, float &f2) {
+    if (cc.color_space == 1) {
+        f0 = (float)r;
+        f1 = (float)g;
+        f2 = (float)b;
+        return;
+    }
+    const float lr = lut[r], lg = lut[g], lb = lut[b];
+    const float *m = cc.m;
+    const float X = fmaf(m[0], lr, fmaf(m[1], lg, m[2] * lb));
+    const float Y = fmaf(m[3], lr, fmaf(m[4], lg, m[5] * lb));
+    const float Z = fmaf(m[6], lr, fmaf(m[7], lg, m[8] * lb));
+    if (cc.color_space == 2) {
+        f0 = X;
+        f1 = Y;
+        f2 = Z;
+        return;
+    }
+    const float fx = lab_f(cc, X), fy = lab_f(cc, Y), fz = lab_f(cc, Z);
+    f0 = fmaf(116.0f, fy, -16.0f);
+    f1 = 500.0f * (fx - fy);
+    f2 = 200.0f * (fy - fz);
+}
+
+#endif
+
 // One frame's geometry and buffers as seen by the kernels (a kernel
 // parameter for single-frame launches, an entry of a device-side table for
 // batched ones).
@@ -73,6 +107,7 @@ int assign_batch_occupancy(bool same, size_t smem);
 // Host helpers shared by the C-ABI files: colour constants of a feature
 // space, and the once-per-device set-up (sRGB table, shared-memory limit).
 ConvConsts conv_consts(int color_space);
+void srgb_table(float lut[256]);
 cudaError_t device_setup(int dev, size_t smem);
 
 cudaError_t upload_lut(const float *lut256);

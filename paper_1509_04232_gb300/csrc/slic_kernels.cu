@@ -47,37 +47,6 @@ __device__ __forceinline__ int div_s(int x, unsigned s_mul, int S) {
     return s_mul ? (int)__umulhi((unsigned)x, s_mul) : x / S;
 }
 
-__device__ __forceinline__ float lab_f(const ConvConsts &cc, float t) {
-    return t > cc.eps ? cbrtf(t) : fmaf(cc.k_slope, t, cc.k_offset);
-}
-
-// Sec. 3 "Image space conversion" for one pixel. `lut` is the sRGB
-// linearisation table (shared or global memory).
-__device__ __forceinline__ void convert_pixel(const ConvConsts &cc, unsigned r, unsigned g, unsigned b,
-                                              const float *lut, float &f0, float &f1, float &f2) {
-    if (cc.color_space == 1) {
-        f0 = (float)r;
-        f1 = (float)g;
-        f2 = (float)b;
-        return;
-    }
-    const float lr = lut[r], lg = lut[g], lb = lut[b];
-    const float *m = cc.m;
-    const float X = fmaf(m[0], lr, fmaf(m[1], lg, m[2] * lb));
-    const float Y = fmaf(m[3], lr, fmaf(m[4], lg, m[5] * lb));
-    const float Z = fmaf(m[6], lr, fmaf(m[7], lg, m[8] * lb));
-    if (cc.color_space == 2) {
-        f0 = X;
-        f1 = Y;
-        f2 = Z;
-        return;
-    }
-    const float fx = lab_f(cc, X), fy = lab_f(cc, Y), fz = lab_f(cc, Z);
-    f0 = fmaf(116.0f, fy, -16.0f);
-    f1 = 500.0f * (fx - fy);
-    f2 = 200.0f * (fy - fz);
-}
-
 // Index of the frame whose [base, next base) range holds `idx` (frames are
 // sorted by base; base of frame 0 is 0).
 enum BaseField { kTileBase, kCentreBase, kRowBase };

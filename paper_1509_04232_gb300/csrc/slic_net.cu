@@ -1,0 +1,783 @@
+// Learned warm start: a 4-layer 3x3 convolutional network (C0=5 -> 32 -> 32
+// -> 32 -> 9, ReLU between layers, zero padding) that predicts, for every
+// pixel, logits over the 9 cells of its 3x3 cell window (slot t = (dy+1)*3 +
+// (dx+1)). Weights and stored activations are bfloat16, every product sum is
+// accumulated in FP32 on the tensor cores (mma.sync m16n8k16 bf16). Training
+// (softmax cross-entropy against the slots of reference labels, Adam with
+// FP32 master weights) and inference run entirely in the kernels below;
+// the C ABI is at the end of this file and declared in include/slic.h.
+//
+// Layouts: activations NHWC bf16 with the channel count padded to a multiple
+// of 16 (layer-1 input 16, hidden 32, logits 16 in FP32). Weights per layer:
+// master FP32 and gradients [9][Cin_p][Cout_p] (tap = dy*3 + dx), a bf16
+// copy [9][Cout_p][Cin_p] for the forward pass and one [9][Cin_p][Cout_p]
+// for the input-gradient pass, so every mma operand pair is two adjacent
+// bf16 values in shared memory.
+#include "slic.h"
+#include "slic_internal.cuh"
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <random>
+#include <string>
+#include <utility>
+#include <vector>
+
+using namespace slicgb;
+
+namespace {
+
+__device__ float g_lut_net[256];  // sRGB byte -> linear (this file's copy)
+
+cudaError_t net_upload_lut() {
+    float t[256];
+    srgb_table(t);
+    return cudaMemcpyToSymbol(g_lut_net, t, sizeof t);
+}
+
+constexpr int kLayers = 4;
+constexpr int kCinReal[kLayers] = {5, 32, 32, 32};
+constexpr int kCoutReal[kLayers] = {32, 32, 32, 9};
+constexpr int kCinPad[kLayers] = {16, 32, 32, 32};
+constexpr int kCoutPad[kLayers] = {32, 32, 32, 16};
+constexpr int kTX = 16, kTY = 4;  // conv tile: 16 pixels x 4 rows, one warp per row
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+// Two bf16 that may not be 4-byte aligned.
+__device__ __forceinline__ uint32_t lds_pair(const __nv_bfloat16 *p) {
+    const uint32_t lo = *reinterpret_cast<const unsigned short *>(p);
+    const uint32_t hi = *reinterpret_cast<const unsigned short *>(p + 1);
+    return lo | (hi << 16);
+}
+
+// ---------------------------------------------------------------------------
+// Input channels: L/100, a/128, b/128, (x mod S)/S, (y mod S)/S, zero padding.
+// ---------------------------------------------------------------------------
+__global__ void k_net_prep(ConvConsts cc, const uint8_t *rgb, int W, int H, int C, int S, __nv_bfloat16 *x0) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, b = blockIdx.z;
+    if (x >= W) return;
+    const size_t px = ((size_t)b * H + y) * W + x;
+    const uint8_t *p = rgb + px * C;
+    float f0, f1, f2;
+    convert_pixel(cc, p[0], p[1], p[2], g_lut_net, f0, f1, f2);
+    uint32_t out[8];
+    out[0] = pack_bf16(f0 / 100.0f, f1 / 128.0f);
+    out[1] = pack_bf16(f2 / 128.0f, (float)(x % S) / (float)S);
+    out[2] = pack_bf16((float)(y % S) / (float)S, 0.0f);
+#pragma unroll
+    for (int i = 3; i < 8; ++i) out[i] = 0u;
+    uint4 *dst = reinterpret_cast<uint4 *>(x0 + px * 16);
+    dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
+    dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
+}
+
+// ---------------------------------------------------------------------------
+// Forward convolution (implicit GEMM): out[p][co] = b[co] + sum_{tap,ci}
+// in[p + tap - (1,1)][ci] w[tap][ci][co]. CTA = 4 warps, tile 16 x 4 pixels
+// of one image; warp w computes row w as an m16 x COUT block.
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT, bool RELU, bool OUTF32>
+__global__ void __launch_bounds__(128) k_conv_fwd(const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const float *bias,
+                                                  void *out, int W, int H) {
+    constexpr int CS = CIN + 8;   // padded channel stride of a shared-memory pixel (bank spread)
+    constexpr int WS = CIN + 8;   // padded ci stride of a weight row
+    __shared__ __align__(16) __nv_bfloat16 in_s[(kTY + 2) * (kTX + 2) * CS];
+    __shared__ __align__(16) __nv_bfloat16 w_s[9 * COUT * WS];
+    __shared__ float b_s[COUT];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, img = blockIdx.z;
+    const size_t base = (size_t)img * H * W;
+
+    // Stage the input tile with a 1-pixel halo (zeros outside the image) and
+    // the layer's weights, in 32-bit words.
+    for (int i = tid; i < (kTY + 2) * (kTX + 2) * (CIN / 2); i += 128) {
+        const int c2 = i % (CIN / 2), pix = i / (CIN / 2);
+        const int lx = pix % (kTX + 2), ly = pix / (kTX + 2);
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        uint32_t v = 0u;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H)
+            v = *reinterpret_cast<const uint32_t *>(in + (base + (size_t)gy * W + gx) * CIN + 2 * c2);
+        *reinterpret_cast<uint32_t *>(&in_s[pix * CS + 2 * c2]) = v;
+    }
+    for (int i = tid; i < 9 * COUT * (CIN / 2); i += 128) {
+        const int c2 = i % (CIN / 2), row = i / (CIN / 2);
+        *reinterpret_cast<uint32_t *>(&w_s[row * WS + 2 * c2]) =
+            *reinterpret_cast<const uint32_t *>(wf + (size_t)row * CIN + 2 * c2);
+    }
+    for (int i = tid; i < COUT; i += 128) b_s[i] = bias[i];
+    __syncthreads();
+
+    float acc[COUT / 8][4];
+#pragma unroll
+    for (int n = 0; n < COUT / 8; ++n)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[n][q] = 0.0f;
+
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+        const __nv_bfloat16 *arow = &in_s[((warp + dy) * (kTX + 2) + dx) * CS];
+#pragma unroll
+        for (int kb = 0; kb < CIN / 16; ++kb) {
+            uint32_t a[4];
+            a[0] = lds32(arow + gid * CS + kb * 16 + 2 * tig);
+            a[1] = lds32(arow + (gid + 8) * CS + kb * 16 + 2 * tig);
+            a[2] = lds32(arow + gid * CS + kb * 16 + 2 * tig + 8);
+            a[3] = lds32(arow + (gid + 8) * CS + kb * 16 + 2 * tig + 8);
+#pragma unroll
+            for (int n = 0; n < COUT / 8; ++n) {
+                const __nv_bfloat16 *brow = &w_s[(tap * COUT + n * 8 + gid) * WS + kb * 16 + 2 * tig];
+                mma16816(acc[n], a, lds32(brow), lds32(brow + 8));
+            }
+        }
+    }
+
+    const int y = y0 + warp;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int x = x0 + gid + 8 * half;
+        if (x >= W || y >= H) continue;
+        const size_t px = base + (size_t)y * W + x;
+#pragma unroll
+        for (int n = 0; n < COUT / 8; ++n) {
+            const int co = n * 8 + 2 * tig;
+            float v0 = acc[n][2 * half] + b_s[co], v1 = acc[n][2 * half + 1] + b_s[co + 1];
+            if (RELU) {
+                v0 = fmaxf(v0, 0.0f);
+                v1 = fmaxf(v1, 0.0f);
+            }
+            if (OUTF32) {
+                *reinterpret_cast<float2 *>(static_cast<float *>(out) + px * COUT + co) = make_float2(v0, v1);
+            } else {
+                *reinterpret_cast<uint32_t *>(static_cast<__nv_bfloat16 *>(out) + px * COUT + co) = pack_bf16(v0, v1);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Input gradient: dA[p][ci] = sum_{tap,co} dZ[p - tap + (1,1)][co] w[tap][ci][co],
+// then times the ReLU derivative of the previous layer (its stored output
+// a_prev > 0): the result is the previous layer's dZ.
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) k_conv_bwd_data(const __nv_bfloat16 *dz, const __nv_bfloat16 *wb,
+                                                       const __nv_bfloat16 *a_prev, __nv_bfloat16 *dz_prev, int W,
+                                                       int H) {
+    constexpr int CS = COUT + 8;
+    constexpr int WS = COUT + 8;
+    __shared__ __align__(16) __nv_bfloat16 g_s[(kTY + 2) * (kTX + 2) * CS];
+    __shared__ __align__(16) __nv_bfloat16 w_s[9 * CIN * WS];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, img = blockIdx.z;
+    const size_t base = (size_t)img * H * W;
+
+    for (int i = tid; i < (kTY + 2) * (kTX + 2) * (COUT / 2); i += 128) {
+        const int c2 = i % (COUT / 2), pix = i / (COUT / 2);
+        const int lx = pix % (kTX + 2), ly = pix / (kTX + 2);
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        uint32_t v = 0u;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H)
+            v = *reinterpret_cast<const uint32_t *>(dz + (base + (size_t)gy * W + gx) * COUT + 2 * c2);
+        *reinterpret_cast<uint32_t *>(&g_s[pix * CS + 2 * c2]) = v;
+    }
+    for (int i = tid; i < 9 * CIN * (COUT / 2); i += 128) {
+        const int c2 = i % (COUT / 2), row = i / (COUT / 2);
+        *reinterpret_cast<uint32_t *>(&w_s[row * WS + 2 * c2]) =
+            *reinterpret_cast<const uint32_t *>(wb + (size_t)row * COUT + 2 * c2);
+    }
+    __syncthreads();
+
+    float acc[CIN / 8][4];
+#pragma unroll
+    for (int n = 0; n < CIN / 8; ++n)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[n][q] = 0.0f;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+        // pixel (x0+i, y0+warp) reads dZ at (x0+i-dx+1, y0+warp-dy+1): tile row warp-dy+2, column i-dx+2
+        const __nv_bfloat16 *arow = &g_s[((warp - dy + 2) * (kTX + 2) + (2 - dx)) * CS];
+#pragma unroll
+        for (int kb = 0; kb < COUT / 16; ++kb) {
+            uint32_t a[4];
+            a[0] = lds32(arow + gid * CS + kb * 16 + 2 * tig);
+            a[1] = lds32(arow + (gid + 8) * CS + kb * 16 + 2 * tig);
+            a[2] = lds32(arow + gid * CS + kb * 16 + 2 * tig + 8);
+            a[3] = lds32(arow + (gid + 8) * CS + kb * 16 + 2 * tig + 8);
+#pragma unroll
+            for (int n = 0; n < CIN / 8; ++n) {
+                const __nv_bfloat16 *brow = &w_s[(tap * CIN + n * 8 + gid) * WS + kb * 16 + 2 * tig];
+                mma16816(acc[n], a, lds32(brow), lds32(brow + 8));
+            }
+        }
+    }
+    const int y = y0 + warp;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int x = x0 + gid + 8 * half;
+        if (x >= W || y >= H) continue;
+        const size_t px = base + (size_t)y * W + x;
+#pragma unroll
+        for (int n = 0; n < CIN / 8; ++n) {
+            const int ci = n * 8 + 2 * tig;
+            const __nv_bfloat162 ap = *reinterpret_cast<const __nv_bfloat162 *>(a_prev + px * CIN + ci);
+            const float v0 = __bfloat162float(ap.x) > 0.0f ? acc[n][2 * half] : 0.0f;
+            const float v1 = __bfloat162float(ap.y) > 0.0f ? acc[n][2 * half + 1] : 0.0f;
+            *reinterpret_cast<uint32_t *>(dz_prev + px * CIN + ci) = pack_bf16(v0, v1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient: dW[tap][ci][co] = sum_p a_in[p + tap - (1,1)][ci] dZ[p][co].
+// Persistent CTAs of 9 warps (warp = tap) walk 16x4-pixel tiles of the batch;
+// each warp accumulates a CIN x COUT block (k = pixels) and writes its
+// partial once; k_reduce_partials adds the CTAs' partials.
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(288) k_conv_bwd_weight(const __nv_bfloat16 *a_in, const __nv_bfloat16 *dz, int W,
+                                                         int H, int n_img, float *partial) {
+    constexpr int PS = (kTY + 2) * (kTX + 2) + 4;  // per-channel plane of the halo tile (pixels)
+    constexpr int GS = kTY * kTX + 8;             // per-channel plane of the dZ tile
+    __shared__ __align__(16) __nv_bfloat16 a_s[CIN * PS];
+    __shared__ __align__(16) __nv_bfloat16 g_s[COUT * GS];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int tiles_x = (W + kTX - 1) / kTX, tiles_y = (H + kTY - 1) / kTY;
+    const int total = tiles_x * tiles_y * n_img;
+    const int dy = warp / 3, dx = warp % 3;
+
+    float acc[CIN / 16][COUT / 8][4];
+#pragma unroll
+    for (int m = 0; m < CIN / 16; ++m)
+#pragma unroll
+        for (int n = 0; n < COUT / 8; ++n)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.0f;
+
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int img = t / (tiles_x * tiles_y), r = t % (tiles_x * tiles_y);
+        const int x0 = (r % tiles_x) * kTX, y0 = (r / tiles_x) * kTY;
+        const size_t base = (size_t)img * H * W;
+        __syncthreads();
+        // channel-major tiles: a_s[ci][pix] (halo), g_s[co][pix] (zeros outside the image)
+        for (int i = tid; i < (kTY + 2) * (kTX + 2) * CIN; i += 288) {
+            const int ci = i % CIN, pix = i / CIN;
+            const int gx = x0 + pix % (kTX + 2) - 1, gy = y0 + pix / (kTX + 2) - 1;
+            __nv_bfloat16 v = __float2bfloat16(0.0f);
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = a_in[(base + (size_t)gy * W + gx) * CIN + ci];
+            a_s[ci * PS + pix] = v;
+        }
+        for (int i = tid; i < kTY * kTX * COUT; i += 288) {
+            const int co = i % COUT, pix = i / COUT;
+            const int gx = x0 + pix % kTX, gy = y0 + pix / kTX;
+            __nv_bfloat16 v = __float2bfloat16(0.0f);
+            if (gx < W && gy < H) v = dz[(base + (size_t)gy * W + gx) * COUT + co];
+            g_s[co * GS + pix] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int row = 0; row < kTY; ++row) {
+            // k = the 16 pixels of tile row `row`; input pixel of tap (dy,dx): halo row row+dy, column i+dx
+            uint32_t a[CIN / 16][4];
+#pragma unroll
+            for (int m = 0; m < CIN / 16; ++m) {
+                const __nv_bfloat16 *p0 = &a_s[(m * 16 + gid) * PS + (row + dy) * (kTX + 2) + dx];
+                const __nv_bfloat16 *p8 = p0 + 8 * PS;
+                a[m][0] = lds_pair(p0 + 2 * tig);
+                a[m][1] = lds_pair(p8 + 2 * tig);
+                a[m][2] = lds_pair(p0 + 2 * tig + 8);
+                a[m][3] = lds_pair(p8 + 2 * tig + 8);
+            }
+#pragma unroll
+            for (int n = 0; n < COUT / 8; ++n) {
+                const __nv_bfloat16 *q = &g_s[(n * 8 + gid) * GS + row * kTX + 2 * tig];
+                const uint32_t b0 = lds32(q), b1 = lds32(q + 8);
+#pragma unroll
+                for (int m = 0; m < CIN / 16; ++m) mma16816(acc[m][n], a[m], b0, b1);
+            }
+        }
+    }
+    // partial[block][tap][ci][co]
+    float *dst = partial + ((size_t)blockIdx.x * 9 + warp) * CIN * COUT;
+#pragma unroll
+    for (int m = 0; m < CIN / 16; ++m)
+#pragma unroll
+        for (int n = 0; n < COUT / 8; ++n) {
+            const int ci = m * 16 + gid, co = n * 8 + 2 * tig;
+            dst[ci * COUT + co] = acc[m][n][0];
+            dst[ci * COUT + co + 1] = acc[m][n][1];
+            dst[(ci + 8) * COUT + co] = acc[m][n][2];
+            dst[(ci + 8) * COUT + co + 1] = acc[m][n][3];
+        }
+}
+
+__global__ void k_reduce_partials(const float *partial, int n_blocks, int n, float *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.0f;
+    for (int b = 0; b < n_blocks; ++b) s += partial[(size_t)b * n + i];
+    out[i] = s;
+}
+
+// Bias gradient: db[co] = sum_p dZ[p][co] (per-CTA sums, then atomics).
+template <int COUT>
+__global__ void k_bias_grad(const __nv_bfloat16 *dz, long long n_px, float *db) {
+    __shared__ float s[COUT];
+    if (threadIdx.x < COUT) s[threadIdx.x] = 0.0f;
+    __syncthreads();
+    const int co = threadIdx.x % COUT;
+    float acc = 0.0f;
+    for (long long p = (long long)blockIdx.x * (blockDim.x / COUT) + threadIdx.x / COUT; p < n_px;
+         p += (long long)gridDim.x * (blockDim.x / COUT))
+        acc += __bfloat162float(dz[p * COUT + co]);
+    atomicAdd(&s[co], acc);
+    __syncthreads();
+    if (threadIdx.x < COUT) atomicAdd(&db[threadIdx.x], s[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// Loss: masked softmax over the in-grid slots, cross-entropy against the
+// target slot; writes dL/dlogits = (p - onehot) / n_total as bf16 [p][16]
+// and accumulates the loss sum and the number of correct argmaxes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool slot_valid(int t, int cx, int cy, int ns_c, int ns_r) {
+    const int nx = cx + t % 3 - 1, ny = cy + t / 3 - 1;
+    return nx >= 0 && nx < ns_c && ny >= 0 && ny < ns_r;
+}
+
+__global__ void k_softmax_ce(const float *logits, const uint8_t *target, int W, int H, int n_img, int S,
+                             float inv_total, __nv_bfloat16 *dz, float *stats) {
+    const long long n_px = (long long)W * H * n_img;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float loss = 0.0f, correct = 0.0f;
+    if (p < n_px) {
+        const int x = (int)(p % W), y = (int)((p / W) % H);
+        const int cx = x / S, cy = y / S, ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
+        const float *l = logits + p * 16;
+        float mx = -INFINITY;
+        int arg = 0;
+        for (int t = 0; t < 9; ++t)
+            if (slot_valid(t, cx, cy, ns_c, ns_r) && l[t] > mx) {
+                mx = l[t];
+                arg = t;
+            }
+        float e[9], sum = 0.0f;
+        for (int t = 0; t < 9; ++t) {
+            e[t] = slot_valid(t, cx, cy, ns_c, ns_r) ? __expf(l[t] - mx) : 0.0f;
+            sum += e[t];
+        }
+        const int tg = target[p];
+        loss = -(l[tg] - mx - __logf(sum));
+        correct = (arg == tg) ? 1.0f : 0.0f;
+        uint32_t g[8];
+        for (int t = 0; t < 16; t += 2) {
+            const float g0 = t < 9 ? (e[t] / sum - (t == tg ? 1.0f : 0.0f)) * inv_total : 0.0f;
+            const float g1 = t + 1 < 9 ? (e[t + 1] / sum - (t + 1 == tg ? 1.0f : 0.0f)) * inv_total : 0.0f;
+            g[t / 2] = pack_bf16(g0, g1);
+        }
+        uint4 *d = reinterpret_cast<uint4 *>(dz + p * 16);
+        d[0] = make_uint4(g[0], g[1], g[2], g[3]);
+        d[1] = make_uint4(g[4], g[5], g[6], g[7]);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        loss += __shfl_xor_sync(0xFFFFFFFFu, loss, off);
+        correct += __shfl_xor_sync(0xFFFFFFFFu, correct, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&stats[0], loss);
+        atomicAdd(&stats[1], correct);
+    }
+}
+
+// Argmax over the in-grid slots -> label of the chosen cell.
+__global__ void k_net_labels(const float *logits, int W, int H, int n_img, int S, int32_t *labels) {
+    const long long n_px = (long long)W * H * n_img;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_px) return;
+    const int x = (int)(p % W), y = (int)((p / W) % H);
+    const int cx = x / S, cy = y / S, ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
+    const float *l = logits + p * 16;
+    float mx = -INFINITY;
+    int arg = 4;
+    for (int t = 0; t < 9; ++t)
+        if (slot_valid(t, cx, cy, ns_c, ns_r) && l[t] > mx) {
+            mx = l[t];
+            arg = t;
+        }
+    labels[p] = (cy + arg / 3 - 1) * ns_c + cx + arg % 3 - 1;
+}
+
+// Adam on the FP32 master weights of one layer (padded layout; padding stays
+// zero), refreshing both bf16 copies.
+__global__ void k_adam(float *w, float *m, float *v, const float *g, int cin_p, int cout_p, int cin_r, int cout_r,
+                       float lr, float b1, float b2, float eps, float c1, float c2, __nv_bfloat16 *wf,
+                       __nv_bfloat16 *wb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * cin_p * cout_p) return;
+    const int co = i % cout_p, ci = (i / cout_p) % cin_p, tap = i / (cout_p * cin_p);
+    float wi = w[i];
+    if (ci < cin_r && co < cout_r) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        wi -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+    }
+    const __nv_bfloat16 q = __float2bfloat16_rn(wi);
+    wb[i] = q;
+    wf[((size_t)tap * cout_p + co) * cin_p + ci] = q;
+}
+
+__global__ void k_adam_bias(float *b, float *m, float *v, const float *g, int cout_r, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    const int i = threadIdx.x;
+    if (i >= cout_r) return;
+    const float mi = b1 * m[i] + (1.0f - b1) * g[i];
+    const float vi = b2 * v[i] + (1.0f - b2) * g[i] * g[i];
+    m[i] = mi;
+    v[i] = vi;
+    b[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// bf16 copies from the FP32 master weights (after loading weights).
+__global__ void k_weight_copies(const float *w, int cin_p, int cout_p, __nv_bfloat16 *wf, __nv_bfloat16 *wb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * cin_p * cout_p) return;
+    const int co = i % cout_p, ci = (i / cout_p) % cin_p, tap = i / (cout_p * cin_p);
+    const __nv_bfloat16 q = __float2bfloat16_rn(w[i]);
+    wb[i] = q;
+    wf[((size_t)tap * cout_p + co) * cin_p + ci] = q;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+struct slic_net_ctx {
+    int max_batch = 0, H = 0, W = 0, S = 0, device = 0;
+    long long step = 0;
+    // per layer: master w [9][cin_p][cout_p], m, v, grad; bias (cout_p) + m, v, grad; bf16 copies
+    float *w[kLayers] = {}, *wm[kLayers] = {}, *wv[kLayers] = {}, *wg[kLayers] = {};
+    float *b[kLayers] = {}, *bm[kLayers] = {}, *bv[kLayers] = {}, *bg[kLayers] = {};
+    __nv_bfloat16 *wf[kLayers] = {}, *wb[kLayers] = {};
+    // activations for max_batch images: x0 (16 ch), a1..a3 (32 ch), logits (16 f32), dz buffers
+    __nv_bfloat16 *act[kLayers] = {};
+    float *logits = nullptr;
+    __nv_bfloat16 *dzA = nullptr, *dzB = nullptr;
+    float *partial = nullptr;
+    int partial_blocks = 0;
+    float *stats = nullptr;
+    ConvConsts conv{};
+    std::string err;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+thread_local std::string g_net_error = "no error";
+
+slic_status nfail(slic_net_ctx *n, slic_status st, const std::string &msg) {
+    if (n)
+        n->err = msg;
+    else
+        g_net_error = msg;
+    return st;
+}
+
+template <typename T>
+bool nalloc(slic_net_ctx *n, T **p, size_t count) {
+    void *q = nullptr;
+    if (cudaMalloc(&q, sizeof(T) * count) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    n->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return true;
+}
+
+size_t wcount(int l) { return (size_t)9 * kCinPad[l] * kCoutPad[l]; }
+
+cudaError_t conv_fwd(int l, const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const float *b, void *out, int W, int H,
+                     int n, cudaStream_t s) {
+    const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, n);
+    if (l == 0) k_conv_fwd<16, 32, true, false><<<grid, 128, 0, s>>>(in, wf, b, out, W, H);
+    else if (l < 3) k_conv_fwd<32, 32, true, false><<<grid, 128, 0, s>>>(in, wf, b, out, W, H);
+    else k_conv_fwd<32, 16, false, true><<<grid, 128, 0, s>>>(in, wf, b, out, W, H);
+    return cudaGetLastError();
+}
+
+slic_status forward_all(slic_net_ctx *n, int batch, const uint8_t *d_images, cudaStream_t s) {
+    const dim3 pg((n->W + 127) / 128, n->H, batch);
+    k_net_prep<<<pg, 128, 0, s>>>(n->conv, d_images, n->W, n->H, 3, n->S, n->act[0]);
+    cudaError_t e = cudaGetLastError();
+    for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
+        void *out = l < 3 ? static_cast<void *>(n->act[l + 1]) : static_cast<void *>(n->logits);
+        e = conv_fwd(l, n->act[l], n->wf[l], n->b[l], out, n->W, n->H, batch, s);
+    }
+    if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("network forward launch: ") + cudaGetErrorString(e));
+    return SLIC_OK;
+}
+
+// Gradients of the mean cross-entropy for the batch into wg/bg (after forward_all).
+slic_status backward_all(slic_net_ctx *n, int batch, const uint8_t *d_targets, cudaStream_t s) {
+    const int W = n->W, H = n->H;
+    const long long n_px = (long long)W * H * batch;
+    cudaError_t e = cudaMemsetAsync(n->stats, 0, 2 * sizeof(float), s);
+    if (e == cudaSuccess) {
+        k_softmax_ce<<<(unsigned)((n_px + 255) / 256), 256, 0, s>>>(n->logits, d_targets, W, H, batch, n->S,
+                                                                   1.0f / (float)n_px, n->dzA, n->stats);
+        e = cudaGetLastError();
+    }
+    __nv_bfloat16 *dz = n->dzA, *dz_prev = n->dzB;
+    const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, batch);
+    for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
+        const int cin = kCinPad[l], cout = kCoutPad[l];
+        // weight gradient of layer l from its input act[l] and dz
+        if (l == 0)
+            k_conv_bwd_weight<16, 32><<<n->partial_blocks, 288, 0, s>>>(n->act[0], dz, W, H, batch, n->partial);
+        else if (l < 3)
+            k_conv_bwd_weight<32, 32><<<n->partial_blocks, 288, 0, s>>>(n->act[l], dz, W, H, batch, n->partial);
+        else
+            k_conv_bwd_weight<32, 16><<<n->partial_blocks, 288, 0, s>>>(n->act[l], dz, W, H, batch, n->partial);
+        const int cnt = 9 * cin * cout;
+        k_reduce_partials<<<(cnt + 255) / 256, 256, 0, s>>>(n->partial, n->partial_blocks, cnt, n->wg[l]);
+        e = cudaMemsetAsync(n->bg[l], 0, sizeof(float) * cout, s);
+        if (e != cudaSuccess) break;
+        if (cout == 32)
+            k_bias_grad<32><<<n->partial_blocks, 256, 0, s>>>(dz, n_px, n->bg[l]);
+        else
+            k_bias_grad<16><<<n->partial_blocks, 256, 0, s>>>(dz, n_px, n->bg[l]);
+        if (l > 0) {
+            // dz of layer l-1 (its output act[l] is layer l's input)
+            if (l < 3)
+                k_conv_bwd_data<32, 32><<<grid, 128, 0, s>>>(dz, n->wb[l], n->act[l], dz_prev, W, H);
+            else
+                k_conv_bwd_data<32, 16><<<grid, 128, 0, s>>>(dz, n->wb[l], n->act[l], dz_prev, W, H);
+            std::swap(dz, dz_prev);
+        }
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("network backward launch: ") + cudaGetErrorString(e));
+    return SLIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+slic_status slic_net_create(int max_batch, int width, int height, int S, unsigned long long seed, slic_net *out) {
+    if (!out || max_batch <= 0 || width <= 0 || height <= 0 || S <= 0 || (long long)width * height * max_batch >= (1LL << 31))
+        return nfail(nullptr, SLIC_ERR_INVALID, "need out, max_batch, width, height, S > 0 and batch pixels < 2^31");
+    *out = nullptr;
+    slic_net_ctx *n = new (std::nothrow) slic_net_ctx;
+    if (!n) return nfail(nullptr, SLIC_ERR_NOMEM, "host allocation failed");
+    n->max_batch = max_batch;
+    n->W = width;
+    n->H = height;
+    n->S = S;
+    n->conv = conv_consts(SLIC_CIELAB);
+    cudaError_t e = cudaGetDevice(&n->device);
+    if (e == cudaSuccess) e = device_setup(n->device, 0);
+    if (e == cudaSuccess) e = net_upload_lut();
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, n->device);
+    if (e != cudaSuccess) {
+        delete n;
+        return nfail(nullptr, SLIC_ERR_CUDA, std::string("CUDA set-up: ") + cudaGetErrorString(e));
+    }
+    n->partial_blocks = 2 * sms;
+    const size_t px = (size_t)width * height * max_batch;
+    bool ok = true;
+    for (int l = 0; l < kLayers && ok; ++l) {
+        ok = nalloc(n, &n->w[l], wcount(l)) && nalloc(n, &n->wm[l], wcount(l)) && nalloc(n, &n->wv[l], wcount(l)) &&
+             nalloc(n, &n->wg[l], wcount(l)) && nalloc(n, &n->b[l], kCoutPad[l]) && nalloc(n, &n->bm[l], kCoutPad[l]) &&
+             nalloc(n, &n->bv[l], kCoutPad[l]) && nalloc(n, &n->bg[l], kCoutPad[l]) &&
+             nalloc(n, &n->wf[l], wcount(l)) && nalloc(n, &n->wb[l], wcount(l)) &&
+             nalloc(n, &n->act[l], px * kCinPad[l]);
+    }
+    ok = ok && nalloc(n, &n->logits, px * 16) && nalloc(n, &n->dzA, px * 32) && nalloc(n, &n->dzB, px * 32) &&
+         nalloc(n, &n->partial, (size_t)n->partial_blocks * 9 * 32 * 32) && nalloc(n, &n->stats, 2);
+    if (!ok) {
+        slic_net_destroy(n);
+        return nfail(nullptr, SLIC_ERR_NOMEM, "device allocation for the network failed");
+    }
+    // He-normal initialisation of the real weights (FP32 master), zero biases
+    // and moments; padding stays zero.
+    std::mt19937_64 rng(seed);
+    for (int l = 0; l < kLayers; ++l) {
+        std::normal_distribution<float> nd(0.0f, std::sqrt(2.0f / (9.0f * kCinReal[l])));
+        std::vector<float> hw(wcount(l), 0.0f);
+        for (int tap = 0; tap < 9; ++tap)
+            for (int ci = 0; ci < kCinReal[l]; ++ci)
+                for (int co = 0; co < kCoutReal[l]; ++co)
+                    hw[((size_t)tap * kCinPad[l] + ci) * kCoutPad[l] + co] = nd(rng);
+        e = cudaMemcpy(n->w[l], hw.data(), sizeof(float) * hw.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(n->wm[l], 0, sizeof(float) * wcount(l));
+        if (e == cudaSuccess) e = cudaMemset(n->wv[l], 0, sizeof(float) * wcount(l));
+        if (e == cudaSuccess) e = cudaMemset(n->b[l], 0, sizeof(float) * kCoutPad[l]);
+        if (e == cudaSuccess) e = cudaMemset(n->bm[l], 0, sizeof(float) * kCoutPad[l]);
+        if (e == cudaSuccess) e = cudaMemset(n->bv[l], 0, sizeof(float) * kCoutPad[l]);
+        if (e == cudaSuccess) {
+            k_weight_copies<<<(unsigned)((wcount(l) + 255) / 256), 256>>>(n->w[l], kCinPad[l], kCoutPad[l], n->wf[l],
+                                                                        n->wb[l]);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        slic_net_destroy(n);
+        return nfail(nullptr, SLIC_ERR_CUDA, std::string("network initialisation: ") + cudaGetErrorString(e));
+    }
+    *out = n;
+    return SLIC_OK;
+}
+
+slic_status slic_net_destroy(slic_net n) {
+    if (!n) return SLIC_OK;
+    cudaDeviceSynchronize();
+    for (void *p : n->allocs) cudaFree(p);
+    delete n;
+    return SLIC_OK;
+}
+
+slic_status slic_net_param_count(slic_net n, size_t *count) {
+    if (!n || !count) return nfail(n, SLIC_ERR_INVALID, "NULL argument");
+    size_t c = 0;
+    for (int l = 0; l < kLayers; ++l) c += (size_t)9 * kCinReal[l] * kCoutReal[l] + kCoutReal[l];
+    *count = c;
+    return SLIC_OK;
+}
+
+// Host <-> device parameters in the order layer by layer, W[dy][dx][ci][co]
+// then b[co], real (unpadded) sizes; FP32 master values. `which` 0 selects
+// the weights, 1 the last computed gradients.
+slic_status slic_net_get_params(slic_net n, int which, float *h_out, size_t count) {
+    size_t need = 0;
+    if (!n || !h_out || slic_net_param_count(n, &need) != SLIC_OK || count != need || (which != 0 && which != 1))
+        return nfail(n, SLIC_ERR_INVALID, "bad arguments (count must equal slic_net_param_count)");
+    cudaError_t e = cudaDeviceSynchronize();
+    size_t off = 0;
+    for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
+        std::vector<float> hw(wcount(l)), hb(kCoutPad[l]);
+        e = cudaMemcpy(hw.data(), which ? n->wg[l] : n->w[l], sizeof(float) * hw.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(hb.data(), which ? n->bg[l] : n->b[l], sizeof(float) * hb.size(), cudaMemcpyDeviceToHost);
+        for (int tap = 0; tap < 9; ++tap)
+            for (int ci = 0; ci < kCinReal[l]; ++ci)
+                for (int co = 0; co < kCoutReal[l]; ++co)
+                    h_out[off++] = hw[((size_t)tap * kCinPad[l] + ci) * kCoutPad[l] + co];
+        for (int co = 0; co < kCoutReal[l]; ++co) h_out[off++] = hb[co];
+    }
+    if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("parameter read: ") + cudaGetErrorString(e));
+    return SLIC_OK;
+}
+
+slic_status slic_net_set_params(slic_net n, const float *h_in, size_t count) {
+    size_t need = 0;
+    if (!n || !h_in || slic_net_param_count(n, &need) != SLIC_OK || count != need)
+        return nfail(n, SLIC_ERR_INVALID, "bad arguments (count must equal slic_net_param_count)");
+    cudaError_t e = cudaDeviceSynchronize();
+    size_t off = 0;
+    for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
+        std::vector<float> hw(wcount(l), 0.0f), hb(kCoutPad[l], 0.0f);
+        for (int tap = 0; tap < 9; ++tap)
+            for (int ci = 0; ci < kCinReal[l]; ++ci)
+                for (int co = 0; co < kCoutReal[l]; ++co)
+                    hw[((size_t)tap * kCinPad[l] + ci) * kCoutPad[l] + co] = h_in[off++];
+        for (int co = 0; co < kCoutReal[l]; ++co) hb[co] = h_in[off++];
+        e = cudaMemcpy(n->w[l], hw.data(), sizeof(float) * hw.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(n->b[l], hb.data(), sizeof(float) * hb.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            k_weight_copies<<<(unsigned)((wcount(l) + 255) / 256), 256>>>(n->w[l], kCinPad[l], kCoutPad[l], n->wf[l],
+                                                                        n->wb[l]);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("parameter write: ") + cudaGetErrorString(e));
+    return SLIC_OK;
+}
+
+slic_status slic_net_forward(slic_net n, int batch, const uint8_t *d_images, float *d_logits, int32_t *d_labels,
+                             void *stream) {
+    if (!n) return nfail(nullptr, SLIC_ERR_INVALID, "NULL network");
+    if (batch <= 0 || batch > n->max_batch || !d_images) return nfail(n, SLIC_ERR_INVALID, "bad batch or images");
+    cudaStream_t s = (cudaStream_t)stream;
+    slic_status st = forward_all(n, batch, d_images, s);
+    if (st != SLIC_OK) return st;
+    const long long n_px = (long long)n->W * n->H * batch;
+    cudaError_t e = cudaSuccess;
+    if (d_logits) e = cudaMemcpyAsync(d_logits, n->logits, sizeof(float) * 16 * n_px, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && d_labels) {
+        k_net_labels<<<(unsigned)((n_px + 255) / 256), 256, 0, s>>>(n->logits, n->W, n->H, batch, n->S, d_labels);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("network output: ") + cudaGetErrorString(e));
+    return SLIC_OK;
+}
+
+slic_status slic_net_gradients(slic_net n, int batch, const uint8_t *d_images, const uint8_t *d_targets,
+                               float *d_stats, void *stream) {
+    if (!n) return nfail(nullptr, SLIC_ERR_INVALID, "NULL network");
+    if (batch <= 0 || batch > n->max_batch || !d_images || !d_targets)
+        return nfail(n, SLIC_ERR_INVALID, "bad batch, images or targets");
+    cudaStream_t s = (cudaStream_t)stream;
+    slic_status st = forward_all(n, batch, d_images, s);
+    if (st == SLIC_OK) st = backward_all(n, batch, d_targets, s);
+    if (st == SLIC_OK && d_stats) {
+        cudaError_t e = cudaMemcpyAsync(d_stats, n->stats, 2 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("stats copy: ") + cudaGetErrorString(e));
+    }
+    return st;
+}
+
+slic_status slic_net_train_step(slic_net n, int batch, const uint8_t *d_images, const uint8_t *d_targets, float lr,
+                                float *d_stats, void *stream) {
+    slic_status st = slic_net_gradients(n, batch, d_images, d_targets, d_stats, stream);
+    if (st != SLIC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    n->step += 1;
+    const float c1 = 1.0f - std::pow(b1, (float)n->step), c2 = 1.0f - std::pow(b2, (float)n->step);
+    for (int l = 0; l < kLayers; ++l) {
+        k_adam<<<(unsigned)((wcount(l) + 255) / 256), 256, 0, s>>>(n->w[l], n->wm[l], n->wv[l], n->wg[l], kCinPad[l],
+                                                                  kCoutPad[l], kCinReal[l], kCoutReal[l], lr, b1, b2,
+                                                                  eps, c1, c2, n->wf[l], n->wb[l]);
+        k_adam_bias<<<1, 32, 0, s>>>(n->b[l], n->bm[l], n->bv[l], n->bg[l], kCoutReal[l], lr, b1, b2, eps, c1, c2);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("optimiser launch: ") + cudaGetErrorString(e));
+    return SLIC_OK;
+}
+
+const char *slic_net_last_error(slic_net n) { return n ? n->err.c_str() : g_net_error.c_str(); }
+
+}  // extern "C"

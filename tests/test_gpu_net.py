@@ -1,0 +1,116 @@
+"""The warm-start network's CUDA kernels against the FP64 network oracle.
+
+Tolerances (derived from the precision model: bf16 weights and stored
+activations, FP32 accumulation vs FP64 in the oracle):
+  logits     |gpu - oracle| <= 2e-2 * max(1, max |oracle|), and the argmax
+             slot agrees wherever the oracle's top two logits differ by > 2e-2
+  gradients  per layer, ||gpu - oracle|| <= 5e-2 * ||oracle|| (the device
+             back-propagates bf16 gradients)
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import net_oracle as NO
+from paper_1509_04232_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _split(flat):
+    out, off = [], 0
+    for cin, cout in NO.LAYERS:
+        w = flat[off:off + 9 * cin * cout].reshape(3, 3, cin, cout)
+        off += 9 * cin * cout
+        b = flat[off:off + cout]
+        off += cout
+        out.append((w.astype(np.float64), b.astype(np.float64)))
+    return out
+
+
+def _setup(slic_gpu, n=2, W=48, H=40, S=8, seed=3):
+    import torch
+    from paper_1509_04232_gb300.warmstart import WarmStartNet
+    net = WarmStartNet(W, H, S, max_batch=n, seed=seed)
+    host = np.stack([synth.voronoi_frame(W, H, 12, 8.0, 900 + i) for i in range(n)])
+    return net, host, torch.from_numpy(host).cuda()
+
+
+def _oracle_input(img, S):
+    return NO.input_channels(oracle.convert(img), S)
+
+
+def test_forward_matches_oracle(slic_gpu):
+    import torch
+    net, host, imgs = _setup(slic_gpu)
+    logits = torch.empty((2, 40, 48, 16), dtype=torch.float32, device="cuda")
+    labels = torch.empty((2, 40, 48), dtype=torch.int32, device="cuda")
+    net.forward(imgs, logits=logits, labels=labels)
+    torch.cuda.synchronize()
+    params = _split(net.params())
+    for i in range(2):
+        ref, _ = NO.forward(_oracle_input(host[i], 8), params, bf16=True)
+        got = logits[i].cpu().numpy()[..., :9]
+        scale = max(1.0, np.abs(ref).max())
+        assert np.max(np.abs(got - ref)) <= 2e-2 * scale
+        valid = NO.slot_mask(40, 48, 8)
+        z = np.where(valid, ref, -np.inf)
+        top2 = np.sort(z, axis=-1)[..., -2:]
+        clear = (top2[..., 1] - top2[..., 0]) > 2e-2 * scale
+        want = NO.labels_from_slots(np.argmax(z, axis=-1), 8)
+        assert np.all((labels[i].cpu().numpy() == want) | ~clear)
+        assert np.all(logits[i].cpu().numpy()[..., 9:] == 0.0)
+
+
+def test_gradients_match_oracle(slic_gpu):
+    import torch
+    net, host, imgs = _setup(slic_gpu)
+    rng = np.random.default_rng(0)
+    valid = NO.slot_mask(40, 48, 8)
+    target = np.zeros((2, 40, 48), np.uint8)
+    for i in range(2):
+        for y in range(40):
+            for x in range(48):
+                target[i, y, x] = rng.choice(np.flatnonzero(valid[y, x]))
+    stats = torch.zeros(2, dtype=torch.float32, device="cuda")
+    net.gradients(imgs, torch.from_numpy(target).cuda(), stats)
+    torch.cuda.synchronize()
+    g_gpu = _split(net.grads())
+    params = _split(net.params())
+    # the batch loss is the mean over both images: average the oracle's per-image gradients
+    g_ref = [(np.zeros_like(w), np.zeros_like(b)) for w, b in params]
+    loss_ref = 0.0
+    for i in range(2):
+        li, gi = NO.backward(_oracle_input(host[i], 8), params, target[i].astype(np.int64), valid, bf16=True)
+        loss_ref += li / 2
+        for l in range(4):
+            g_ref[l] = (g_ref[l][0] + gi[l][0] / 2, g_ref[l][1] + gi[l][1] / 2)
+    assert float(stats[0]) / (2 * 40 * 48) == pytest.approx(loss_ref, rel=1e-2)
+    for l in range(4):
+        for a, b in zip(g_gpu[l], g_ref[l]):
+            assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b), (l, np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_training_reduces_loss(slic_gpu):
+    import torch
+    from paper_1509_04232_gb300.warmstart import WarmStartNet, training_batch
+    net = WarmStartNet(256, 256, 16, max_batch=8, seed=1)
+    imgs, slots = training_batch(0, 8, torch.device("cuda"))
+    stats = torch.zeros(2, dtype=torch.float32, device="cuda")
+    losses = []
+    for step in range(60):
+        net.train_step(imgs, slots, 3e-3, stats)
+        losses.append(float(stats[0].item()) / (8 * 256 * 256))
+    assert losses[-1] < 0.7 * losses[0], losses[::10]
+
+
+def test_training_targets_agree_with_oracle(slic_gpu):
+    """The GPU full-iteration labels used as training targets agree with the
+    FP64 oracle's (before connectivity)."""
+    import torch
+    from paper_1509_04232_gb300.warmstart import reference_labels
+    host = np.stack([synth.train_image(i) for i in range(3)])
+    got = reference_labels(torch.from_numpy(host).cuda()).cpu().numpy()
+    for i in range(3):
+        ref = oracle.slic(host[i], S=16, m=10.0, iterations=10, enforce_connectivity=False)
+        assert np.mean(got[i] == ref["labels_pre"]) >= 0.995
