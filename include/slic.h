@@ -230,22 +230,26 @@ slic_status slic_segment_noalloc(const slic_params *params, const uint8_t *d_ima
                                  float *d_centres, void *stream);
 
 /* ---- Learned warm start ---------------------------------------------------
-   A 4-layer 3x3 convolutional network (5 -> 32 -> 32 -> 32 -> 9 channels,
+   A 4-layer 3x3 convolutional network (14 -> 32 -> 32 -> 32 -> 9 channels,
    ReLU between layers, zero padding; bfloat16 weights and stored
    activations, FP32 accumulation on the tensor cores) that predicts, for
    each pixel of an RGB image, logits over the 9 cells of its 3x3 cell
    window (slot t = (dy+1)*3 + (dx+1), the scan order of the assignment).
-   Inputs per pixel: L/100, a/128, b/128, (x mod S)/S, (y mod S)/S. The
+   Inputs per pixel (14): L/100, a/128, b/128, (x mod S)/S, (y mod S)/S and,
+   for each slot, D/100 = the Eq. (1) distance to that cell's
+   grid-initialised centre (2.0 off the grid). The
    paper has no such network; it replaces the first k-means iterations
    (its labels give initial centres through slic_update). Trained here by
    softmax cross-entropy against the slots of reference labels, with Adam
    (beta 0.9/0.999, eps 1e-8) on FP32 master weights. */
 typedef struct slic_net_ctx *slic_net;
 
-/* Network for batches of up to max_batch RGB images of width x height and
-   grid interval S; He-normal weights from `seed`, zero biases. Allocates the
-   activations of max_batch images. */
-slic_status slic_net_create(int max_batch, int width, int height, int S, unsigned long long seed, slic_net *out);
+/* Network for batches of up to max_batch RGB images of width x height, grid
+   interval S and compactness m (used by the distance inputs); He-normal
+   weights from `seed`, zero biases. Allocates the activations of max_batch
+   images. */
+slic_status slic_net_create(int max_batch, int width, int height, int S, float m, unsigned long long seed,
+                            slic_net *out);
 slic_status slic_net_destroy(slic_net n);
 
 /* Number of parameters (real sizes): per layer W[3][3][Cin][Cout] then b[Cout]. */

@@ -6,8 +6,10 @@ pixel's 3x3 cell window (slot t = (dy+1)*3 + (dx+1), scan order as in the
 assignment of Eq. 1). Four 3x3 convolutions with zero padding and ReLU
 between them: C0 -> 32 -> 32 -> 32 -> 9.
 
-Input channels (C0 = 5, zero-padded to 16 on the device): L/100, a/128,
-b/128, (x mod S)/S, (y mod S)/S.
+Input channels (C0 = 14, zero-padded to 16 on the device): L/100, a/128,
+b/128, (x mod S)/S, (y mod S)/S, and D_t/100 for t = 0..8, the Eq. (1)
+distance to the grid-initialised centre of slot t (2.0 for an off-grid
+slot) -- the information of the first assignment.
 
 Precision model of the device path, mirrored here when ``bf16=True``:
 weights and the activations stored between layers are rounded to bfloat16
@@ -21,7 +23,7 @@ from __future__ import annotations
 
 import numpy as np
 
-C0, C_HID, N_SLOTS = 5, 32, 9
+C0, C_HID, N_SLOTS = 14, 32, 9
 LAYERS = [(C0, C_HID), (C_HID, C_HID), (C_HID, C_HID), (C_HID, N_SLOTS)]
 
 
@@ -44,12 +46,35 @@ def init_params(seed: int = 0):
     return params
 
 
-def input_channels(lab: np.ndarray, S: int) -> np.ndarray:
-    """lab [H,W,3] -> network input [H,W,5]."""
+def grid_distances(lab: np.ndarray, S: int, m: float) -> np.ndarray:
+    """D[H,W,9]: Eq. (1) distance of each pixel to the grid-initialised centre
+    (Sec. 3 initialisation) of each slot of its 3x3 cell window; inf off-grid."""
+    H, W, _ = lab.shape
+    ns_c, ns_r = -(-W // S), -(-H // S)
+    ys, xs = np.mgrid[0:H, 0:W]
+    D = np.full((H, W, 9), np.inf)
+    for t in range(9):
+        cx = xs // S + t % 3 - 1
+        cy = ys // S + t // 3 - 1
+        ok = (cx >= 0) & (cx < ns_c) & (cy >= 0) & (cy < ns_r)
+        cxc, cyc = np.clip(cx, 0, ns_c - 1), np.clip(cy, 0, ns_r - 1)
+        xk = (cxc * S + np.minimum((cxc + 1) * S, W) - 1) / 2.0
+        yk = (cyc * S + np.minimum((cyc + 1) * S, H) - 1) / 2.0
+        ck = lab[np.floor(yk).astype(int), np.floor(xk).astype(int)]
+        d = np.sqrt(((lab - ck) ** 2).sum(-1)) + (m / S) * np.sqrt((xs - xk) ** 2 + (ys - yk) ** 2)
+        D[..., t] = np.where(ok, d, np.inf)
+    return D
+
+
+def input_channels(lab: np.ndarray, S: int, m: float = 10.0) -> np.ndarray:
+    """lab [H,W,3] -> network input [H,W,14]."""
     H, W, _ = lab.shape
     ys, xs = np.mgrid[0:H, 0:W]
-    return np.stack([lab[..., 0] / 100.0, lab[..., 1] / 128.0, lab[..., 2] / 128.0,
-                     (xs % S) / S, (ys % S) / S], axis=-1).astype(np.float64)
+    D = grid_distances(lab, S, m)
+    Dn = np.where(np.isfinite(D), D / 100.0, 2.0)
+    base = np.stack([lab[..., 0] / 100.0, lab[..., 1] / 128.0, lab[..., 2] / 128.0,
+                     (xs % S) / S, (ys % S) / S], axis=-1)
+    return np.concatenate([base, Dn], axis=-1).astype(np.float64)
 
 
 def slot_mask(H: int, W: int, S: int) -> np.ndarray:

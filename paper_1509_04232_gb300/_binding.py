@@ -65,7 +65,7 @@ _SIGNATURES = {
     "slic_batch_profile_enable": [_P, _I],
     "slic_batch_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
     "slic_batch_profile_times": [_P, ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I)],
-    "slic_net_create": [_I, _I, _I, _I, ctypes.c_ulonglong, ctypes.POINTER(_P)],
+    "slic_net_create": [_I, _I, _I, _I, ctypes.c_float, ctypes.c_ulonglong, ctypes.POINTER(_P)],
     "slic_net_destroy": [_P],
     "slic_net_param_count": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "slic_net_get_params": [_P, _I, _P, ctypes.c_size_t],
@@ -266,9 +266,9 @@ def _ncheck(status: int, n):
         raise SlicError(status, slic_net_last_error(n))
 
 
-def slic_net_create(max_batch: int, width: int, height: int, S: int, seed: int = 0) -> int:
+def slic_net_create(max_batch: int, width: int, height: int, S: int, m: float = 10.0, seed: int = 0) -> int:
     n = _P()
-    _ncheck(lib().slic_net_create(max_batch, width, height, S, seed, ctypes.byref(n)), None)
+    _ncheck(lib().slic_net_create(max_batch, width, height, S, float(m), seed, ctypes.byref(n)), None)
     return n.value
 
 

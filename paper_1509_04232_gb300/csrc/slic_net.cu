@@ -1,4 +1,4 @@
-// Learned warm start: a 4-layer 3x3 convolutional network (C0=5 -> 32 -> 32
+// Learned warm start: a 4-layer 3x3 convolutional network (C0=14 -> 32 -> 32
 // -> 32 -> 9, ReLU between layers, zero padding) that predicts, for every
 // pixel, logits over the 9 cells of its 3x3 cell window (slot t = (dy+1)*3 +
 // (dx+1)). Weights and stored activations are bfloat16, every product sum is
@@ -39,7 +39,7 @@ cudaError_t net_upload_lut() {
 }
 
 constexpr int kLayers = 4;
-constexpr int kCinReal[kLayers] = {5, 32, 32, 32};
+constexpr int kCinReal[kLayers] = {14, 32, 32, 32};
 constexpr int kCoutReal[kLayers] = {32, 32, 32, 9};
 constexpr int kCinPad[kLayers] = {16, 32, 32, 32};
 constexpr int kCoutPad[kLayers] = {32, 32, 32, 16};
@@ -68,22 +68,47 @@ __device__ __forceinline__ uint32_t lds_pair(const __nv_bfloat16 *p) {
 }
 
 // ---------------------------------------------------------------------------
-// Input channels: L/100, a/128, b/128, (x mod S)/S, (y mod S)/S, zero padding.
+// Input channels: L/100, a/128, b/128, (x mod S)/S, (y mod S)/S, then for the
+// 9 slots of the pixel's cell window the Eq. (1) distance D/100 to the
+// grid-initialised centre of that cell (2.0 off the grid), zero padding.
 // ---------------------------------------------------------------------------
-__global__ void k_net_prep(ConvConsts cc, const uint8_t *rgb, int W, int H, int C, int S, __nv_bfloat16 *x0) {
+__global__ void k_net_prep(ConvConsts cc, const uint8_t *rgb, int W, int H, int C, int S, float w,
+                           __nv_bfloat16 *x0) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, b = blockIdx.z;
     if (x >= W) return;
-    const size_t px = ((size_t)b * H + y) * W + x;
+    const size_t img = (size_t)b * H * W;
+    const size_t px = img + (size_t)y * W + x;
     const uint8_t *p = rgb + px * C;
     float f0, f1, f2;
     convert_pixel(cc, p[0], p[1], p[2], g_lut_net, f0, f1, f2);
-    uint32_t out[8];
-    out[0] = pack_bf16(f0 / 100.0f, f1 / 128.0f);
-    out[1] = pack_bf16(f2 / 128.0f, (float)(x % S) / (float)S);
-    out[2] = pack_bf16((float)(y % S) / (float)S, 0.0f);
+    float ch[16];
+    ch[0] = f0 / 100.0f;
+    ch[1] = f1 / 128.0f;
+    ch[2] = f2 / 128.0f;
+    ch[3] = (float)(x % S) / (float)S;
+    ch[4] = (float)(y % S) / (float)S;
+    const int cx = x / S, cy = y / S, ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
 #pragma unroll
-    for (int i = 3; i < 8; ++i) out[i] = 0u;
+    for (int t = 0; t < 9; ++t) {
+        const int nx = cx + t % 3 - 1, ny = cy + t / 3 - 1;
+        float d = 2.0f;
+        if (nx >= 0 && nx < ns_c && ny >= 0 && ny < ns_r) {
+            // grid initialisation of Sec. 3: midpoint of the in-image cell, colour under it
+            const int xf = nx * S, xl = min((nx + 1) * S, W) - 1, yf = ny * S, yl = min((ny + 1) * S, H) - 1;
+            const uint8_t *q = rgb + (img + (size_t)((yf + yl) >> 1) * W + ((xf + xl) >> 1)) * C;
+            float k0, k1, k2;
+            convert_pixel(cc, q[0], q[1], q[2], g_lut_net, k0, k1, k2);
+            const float dl = k0 - f0, da = k1 - f1, db = k2 - f2;
+            const float dx = 0.5f * (float)(xf + xl) - (float)x, dy = 0.5f * (float)(yf + yl) - (float)y;
+            d = (sqrtf(dl * dl + da * da + db * db) + w * sqrtf(dx * dx + dy * dy)) / 100.0f;
+        }
+        ch[5 + t] = d;
+    }
+    ch[14] = ch[15] = 0.0f;
+    uint32_t out[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) out[i] = pack_bf16(ch[2 * i], ch[2 * i + 1]);
     uint4 *dst = reinterpret_cast<uint4 *>(x0 + px * 16);
     dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
     dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
@@ -481,6 +506,7 @@ __global__ void k_weight_copies(const float *w, int cin_p, int cout_p, __nv_bflo
 
 struct slic_net_ctx {
     int max_batch = 0, H = 0, W = 0, S = 0, device = 0;
+    float m = 10.0f;
     long long step = 0;
     // per layer: master w [9][cin_p][cout_p], m, v, grad; bias (cout_p) + m, v, grad; bf16 copies
     float *w[kLayers] = {}, *wm[kLayers] = {}, *wv[kLayers] = {}, *wg[kLayers] = {};
@@ -535,7 +561,7 @@ cudaError_t conv_fwd(int l, const __nv_bfloat16 *in, const __nv_bfloat16 *wf, co
 
 slic_status forward_all(slic_net_ctx *n, int batch, const uint8_t *d_images, cudaStream_t s) {
     const dim3 pg((n->W + 127) / 128, n->H, batch);
-    k_net_prep<<<pg, 128, 0, s>>>(n->conv, d_images, n->W, n->H, 3, n->S, n->act[0]);
+    k_net_prep<<<pg, 128, 0, s>>>(n->conv, d_images, n->W, n->H, 3, n->S, n->m / (float)n->S, n->act[0]);
     cudaError_t e = cudaGetLastError();
     for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
         void *out = l < 3 ? static_cast<void *>(n->act[l + 1]) : static_cast<void *>(n->logits);
@@ -592,9 +618,11 @@ slic_status backward_all(slic_net_ctx *n, int batch, const uint8_t *d_targets, c
 
 extern "C" {
 
-slic_status slic_net_create(int max_batch, int width, int height, int S, unsigned long long seed, slic_net *out) {
-    if (!out || max_batch <= 0 || width <= 0 || height <= 0 || S <= 0 || (long long)width * height * max_batch >= (1LL << 31))
-        return nfail(nullptr, SLIC_ERR_INVALID, "need out, max_batch, width, height, S > 0 and batch pixels < 2^31");
+slic_status slic_net_create(int max_batch, int width, int height, int S, float m, unsigned long long seed,
+                            slic_net *out) {
+    if (!out || max_batch <= 0 || width <= 0 || height <= 0 || S <= 0 || !(m >= 0.0f) ||
+        (long long)width * height * max_batch >= (1LL << 31))
+        return nfail(nullptr, SLIC_ERR_INVALID, "need out, max_batch, width, height, S > 0, m >= 0 and batch pixels < 2^31");
     *out = nullptr;
     slic_net_ctx *n = new (std::nothrow) slic_net_ctx;
     if (!n) return nfail(nullptr, SLIC_ERR_NOMEM, "host allocation failed");
@@ -602,6 +630,7 @@ slic_status slic_net_create(int max_batch, int width, int height, int S, unsigne
     n->W = width;
     n->H = height;
     n->S = S;
+    n->m = m;
     n->conv = conv_consts(SLIC_CIELAB);
     cudaError_t e = cudaGetDevice(&n->device);
     if (e == cudaSuccess) e = device_setup(n->device, 0);

@@ -33,9 +33,9 @@ def slots_from_labels(labels: np.ndarray, S: int) -> np.ndarray:
 class WarmStartNet:
     """The network on one geometry (width x height, grid interval S)."""
 
-    def __init__(self, width: int, height: int, S: int = 16, max_batch: int = 64, seed: int = 0):
-        self.W, self.H, self.S, self.max_batch = width, height, S, max_batch
-        self.handle = B.slic_net_create(max_batch, width, height, S, seed)
+    def __init__(self, width: int, height: int, S: int = 16, max_batch: int = 64, seed: int = 0, m: float = 10.0):
+        self.W, self.H, self.S, self.m, self.max_batch = width, height, S, m, max_batch
+        self.handle = B.slic_net_create(max_batch, width, height, S, m, seed)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -160,5 +160,23 @@ def warm_start_segment(net: WarmStartNet, images_u8, iterations: int, m: float =
     bs = BatchSegmenter([dict(width=W, height=H, S=net.S, m=m)] * n, iterations=iterations - 1,
                         enforce_connectivity=enforce_connectivity, device=dev)
     bs.bind([images_u8[i] for i in range(n)], init_centres=init)
+    labels, centres = bs.segment()
+    return [l.clone() for l in labels], [c.clone() for c in centres]
+
+
+def agreement(a, b) -> float:
+    """Fraction of equal labels between two lists of int32 CUDA tensors."""
+    import torch
+    eq = sum(int((x == y).sum().item()) for x, y in zip(a, b))
+    return eq / sum(x.numel() for x in a)
+
+
+def plain_segment(images_u8, iterations: int, S: int = 16, m: float = 10.0, enforce_connectivity: bool = True):
+    """Plain batched SLIC (grid initialisation) on frames [n, H, W, 3]."""
+    from . import BatchSegmenter
+    n, H, W, _ = images_u8.shape
+    bs = BatchSegmenter([dict(width=W, height=H, S=S, m=m)] * n, iterations=iterations,
+                        enforce_connectivity=enforce_connectivity, device=images_u8.device)
+    bs.bind([images_u8[i] for i in range(n)])
     labels, centres = bs.segment()
     return [l.clone() for l in labels], [c.clone() for c in centres]

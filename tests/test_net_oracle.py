@@ -99,5 +99,19 @@ def test_input_channels():
     lab[..., 1] = 64.0
     lab[..., 2] = -128.0
     x = net.input_channels(lab, 4)
-    np.testing.assert_allclose(x[0, 0], [0.5, 0.5, -1.0, 0.0, 0.0])
-    np.testing.assert_allclose(x[2, 4], [0.5, 0.5, -1.0, 0.0, 0.5])
+    np.testing.assert_allclose(x[0, 0, :5], [0.5, 0.5, -1.0, 0.0, 0.0])
+    np.testing.assert_allclose(x[2, 4, :5], [0.5, 0.5, -1.0, 0.0, 0.5])
+
+
+def test_grid_distances_uniform_image():
+    """Uniform colour: D is (m/S) times the distance to each grid midpoint
+    (hand values for an 8x8 image, S=4, m=8: midpoints at 1.5 and 5.5)."""
+    lab = np.full((8, 8, 3), 42.0)
+    D = net.grid_distances(lab, 4, 8.0)
+    # pixel (0,0): own centre (1.5,1.5) -> 2*sqrt(4.5); right centre (5.5,1.5) -> 2*sqrt(32.5)
+    assert D[0, 0, 4] == pytest.approx(2 * np.sqrt(4.5))
+    assert D[0, 0, 5] == pytest.approx(2 * np.sqrt(32.5))
+    assert D[0, 0, 8] == pytest.approx(2 * np.sqrt(60.5))
+    assert np.isinf(D[0, 0, [0, 1, 2, 3, 6]]).all()
+    x = net.input_channels(lab, 4, 8.0)
+    assert x[0, 0, 5 + 0] == 2.0 and x[0, 0, 5 + 4] == pytest.approx(2 * np.sqrt(4.5) / 100)
