@@ -294,6 +294,11 @@ def run_ours(args):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
     e2e_value = world * B / (e2e_ms / 1e3)
 
+    # --- label agreement with the 10-iteration result and the learned path ---
+    quality = None
+    if not args.no_quality:
+        quality = quality_and_learned(args, pkg, images, B, stream, world, dev)
+
     # --- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N=1) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -320,6 +325,7 @@ def run_ours(args):
                                  "frac": achieved_gbs / peaks["hbm_gbs"], "unit": "GB/s",
                                  "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch}},
             "cpu_baseline": cpu,
+            "quality": quality,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clock_info,
@@ -331,6 +337,58 @@ def run_ours(args):
     return 0
 
 
+def quality_and_learned(args, pkg, images, B, stream, world, dev):
+    """Agreement of plain SLIC with n iterations and of the learned warm start
+    with k iterations against the 10-iteration labels (first 8 frames), and
+    the learned path's throughput on the whole batch (one CUDA graph per
+    step, same timing protocol as `value`). The network is trained first on
+    seeded 256x256 images (outside any timed region)."""
+    import torch
+    from paper_1509_04232_gb300 import warmstart as ws
+    q = min(8, B)
+    sub = images[:q]
+    ref, _ = ws.plain_segment(sub, 10)
+    plain = {}
+    for n in (0, 1, 2, 3, 5, 7, 9):
+        lab, _ = ws.plain_segment(sub, n)
+        plain[n] = round(ws.agreement(lab, ref), 5)
+    t0 = time.time()
+    small = ws.WarmStartNet(256, 256, S, max_batch=64, seed=0, m=M)
+    hist = ws.train(small, n_images=args.train_images, batch=64, epochs=args.train_epochs, lr=2e-3, log_every=50)
+    train_s = time.time() - t0
+    net = ws.WarmStartNet(W, H, S, max_batch=B, seed=0, m=M)
+    net.set_params(small.params())
+    learned, learned_fps = {}, {}
+    for k in (1, 2):
+        lab, _ = ws.warm_start_segment(net, sub, k)
+        learned[k] = round(ws.agreement(lab, ref), 5)
+        pipe = ws.WarmStartPipeline(net, [images[f] for f in range(B)], k)
+        with torch.cuda.stream(stream):
+            pipe.run(stream)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            pipe.run(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                g.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                g.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
+        learned_fps[k] = world * B / (ms / 1e3)
+    return {"reference": "plain SLIC, 10 iterations (same frames, connectivity on)", "frames": q,
+            "plain_agreement_by_iterations": plain, "learned_agreement_by_iterations": learned,
+            "learned_frames_per_s_by_iterations": learned_fps,
+            "learned_training": {"images": args.train_images, "epochs": args.train_epochs, "seconds": train_s,
+                                 "final_loss": hist[-1][1] if hist else None,
+                                 "final_pixel_accuracy": hist[-1][2] if hist else None}}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,7 +397,10 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=32, help="1080p frames per GPU per step")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-frames", type=int, default=6, help="frames in the oracle CPU-baseline sample")
+    ap.add_argument("--train-images", type=int, default=20000, help="training images for the learned leg")
+    ap.add_argument("--train-epochs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-quality", action="store_true", help="skip the agreement table and the learned path")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

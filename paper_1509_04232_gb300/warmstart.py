@@ -180,3 +180,43 @@ def plain_segment(images_u8, iterations: int, S: int = 16, m: float = 10.0, enfo
     bs.bind([images_u8[i] for i in range(n)])
     labels, centres = bs.segment()
     return [l.clone() for l in labels], [c.clone() for c in centres]
+
+
+class WarmStartPipeline:
+    """The learned path for a fixed set of frames, with every buffer
+    allocated up front so that `run` only enqueues kernels (and can be
+    captured into a CUDA graph): network labels -> member-mean centres per
+    frame -> `iterations` assignments of the batched path -> connectivity."""
+
+    def __init__(self, net: WarmStartNet, images, iterations: int, m: float = 10.0,
+                 enforce_connectivity: bool = True):
+        import torch
+        from . import BatchSegmenter, Segmenter
+        self.net = net
+        self.images = list(images)
+        n = len(self.images)
+        H, W, _ = self.images[0].shape
+        dev = self.images[0].device
+        self.stacked = torch.stack(self.images)
+        self.net_labels = torch.empty((n, H, W), dtype=torch.int32, device=dev)
+        self.seg = Segmenter(W, H, S=net.S, m=m, iterations=0)
+        self.feat = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+        self.c0 = torch.empty((self.seg.K_eff, 6), dtype=torch.float32, device=dev)
+        self.init = [torch.empty((self.seg.K_eff, 6), dtype=torch.float32, device=dev) for _ in range(n)]
+        self.bs = BatchSegmenter([dict(width=W, height=H, S=net.S, m=m)] * n, iterations=iterations - 1,
+                                 enforce_connectivity=enforce_connectivity, device=dev)
+        self.bs.bind(self.images, init_centres=self.init)
+
+    def run(self, stream=None):
+        import torch
+        s = int((stream if stream is not None else torch.cuda.current_stream()).cuda_stream)
+        B.slic_net_forward(self.net.handle, len(self.images), self.stacked.data_ptr(), None,
+                           self.net_labels.data_ptr(), s)
+        h = self.seg.handle
+        for i, img in enumerate(self.images):
+            B.slic_convert(h, img.data_ptr(), self.feat.data_ptr(), s)
+            B.slic_init_centres(h, self.feat.data_ptr(), self.c0.data_ptr(), s)
+            B.slic_update(h, self.feat.data_ptr(), self.net_labels[i].data_ptr(), self.c0.data_ptr(),
+                          self.init[i].data_ptr(), s)
+        B.slic_batch_segment(self.bs.handle, s)
+        return self.bs.labels, self.bs.centres
