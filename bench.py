@@ -200,7 +200,7 @@ def run_ours(args):
     bs = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=ITERS, device=dev)
     bs.bind([images[f] for f in range(B)])
     tune_cache = os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl")
-    ctas_per_sm = bs.autotune(tune_cache, stream=stream)
+    ctas_per_sm, stages = bs.autotune(tune_cache, stream=stream)
 
     def step():
         bs.segment(stream=stream)
@@ -316,7 +316,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world} (frames sharded, no collective)",
                        "l2": "inputs larger than L2 (B x 6.2 MB RGB + B x 8.3 MB labels per step)",
                        "graph": "one CUDA graph per step (one batched launch per stage)",
-                       "ctas_per_sm": ctas_per_sm},
+                       "ctas_per_sm": ctas_per_sm, "pipeline_stages": stages},
             "roofline": {"kernel": "k_assign_pipe<0,1> (middle assignment pass, all frames)", "bound": "alu",
                          "unit": "Tsqrt/s", "achieved": achieved_tops, "peak": xu_peak, "frac": achieved_tops / xu_peak,
                          "peak_source": "16 MUFU lanes/clk/SM x 152 SMs x max SM clock (recipe unit counts)",

@@ -170,22 +170,28 @@ slic_status slic_batch_set_buffers(slic_batch b, const uint8_t *const *d_images,
    SLIC_ERR_STATE before slic_batch_set_buffers. */
 slic_status slic_batch_segment(slic_batch b, void *stream);
 
-/* Launch shape of the persistent assignment kernel: resident CTAs per SM
-   (0 = as many as fit). */
-slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm);
+/* Launch shape of the persistent assignment kernels: resident CTAs per SM
+   (0 = as many as fit, capped by each kernel's occupancy) and the number of
+   TMA pipeline stages of the passes after the first (3 or 4; 0 keeps the
+   current value, default 4 where it fits). SLIC_ERR_INVALID for other
+   values or stages that do not fit in shared memory. */
+slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages);
 
 /* Autotuner: time slic_batch_segment on the bound buffers for every launch
    shape that fits (3 timed runs each, CUDA events on `stream`; this waits
    for the device), keep the fastest, and append it to the JSON-lines file
    cache_path (may be NULL) under a key of GPU name, frame count,
    iterations and the distinct (width, height, S). When the key is already
-   in the file its entry is used without timing. The chosen value is
-   returned in *ctas_per_sm (may be NULL). */
-slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm);
+   in the file its entry is used without timing. The search covers CTAs
+   per SM x pipeline stages; the choice is returned in *ctas_per_sm and
+   *stages (either may be NULL). */
+slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm, int *stages);
 
-/* Pixels of all frames, kernel launches enqueued so far, CTAs per SM in use
-   (any may be NULL). */
-slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm);
+/* Pixels of all frames, kernel launches enqueued so far, CTAs per SM
+   requested, pipeline stages in use (0 when the pipelined kernel is not
+   used); any pointer may be NULL. */
+slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm,
+                            int *stages);
 
 /* Wait for the device, then report whether a bounded wait inside the
    batch's kernels gave up since the last call (SLIC_ERR_TIMEOUT; the

@@ -146,11 +146,12 @@ class BatchSegmenter:
         slic_batch_segment(self.handle, _stream_handle(stream))
         return self.labels, self.centres
 
-    def autotune(self, cache_path=None, stream=None) -> int:
+    def autotune(self, cache_path=None, stream=None):
+        """Time the launch shapes that fit; -> (ctas_per_sm, stages) chosen."""
         return slic_batch_autotune(self.handle, cache_path, _stream_handle(stream))
 
-    def set_tuning(self, ctas_per_sm: int):
-        slic_batch_set_tuning(self.handle, ctas_per_sm)
+    def set_tuning(self, ctas_per_sm: int, stages: int = 0):
+        slic_batch_set_tuning(self.handle, ctas_per_sm, stages)
 
     @property
     def info(self):

@@ -153,6 +153,20 @@ FrameArgs frame_args(slic_ctx *h, const uint8_t *rgb, float *feat, int P, const 
     return a;
 }
 
+}  // namespace
+
+// Under stream capture a record must be external to become an event-record
+// node of the graph; outside capture it is a plain record.
+cudaError_t slicgb::record_profile_event(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecordWithFlags(ev, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                             : cudaEventRecordDefault);
+}
+
+namespace {
+
 slic_status assign_launch(slic_ctx *h, const FrameArgs &a, bool first, bool last, bool store_feat, cudaStream_t s) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->profiling) {
@@ -165,13 +179,13 @@ slic_status assign_launch(slic_ctx *h, const FrameArgs &a, bool first, bool last
         e0 = h->events[h->ev_used].first;
         e1 = h->events[h->ev_used].second;
         ++h->ev_used;
-        // External records become event-record nodes under stream capture.
-        cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+        if (record_profile_event(e0, s) != cudaSuccess) return fail(h, SLIC_ERR_CUDA, "profile event record failed");
     }
     cudaError_t e = launch_assign(a, first, last, store_feat, assign_smem_bytes(assign_max_window(h->S, h->ns_c, h->ns_r), first), s);
     if (e != cudaSuccess) return cuda_fail(h, e, "assignment kernel launch");
     ++h->launches;
-    if (h->profiling) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+    if (h->profiling && record_profile_event(e1, s) != cudaSuccess)
+        return fail(h, SLIC_ERR_CUDA, "profile event record failed");
     return SLIC_OK;
 }
 

@@ -36,10 +36,11 @@ struct slic_batch_ctx {
     bool pipe = false;       // passes after the first use the pipelined kernel
     bool buffers_set = false;
     size_t smem = 0;
-    int occupancy = 0;
+    int occupancy = 0;       // resident CTAs per SM of the first-pass kernel
     int max_ring = 0;
     int *d_err = nullptr;    // device flag: a bounded wait timed out
-    int ctas_per_sm = 0;  // 0: occupancy
+    int ctas_per_sm = 0;     // 0: as many as fit
+    int stages = 4;          // TMA pipeline stages of the later passes (3..4)
     long long launches = 0;
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
@@ -81,10 +82,12 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // Tensor maps of one frame for the pipelined assignment: the features as a
 // [3][H][P] f32 tensor copied in 32x32x3 boxes, and the padded centre table
-// as a [ns_r+2][(ns_c+2)*8] f32 tensor copied in box_h x box_w*8 boxes.
+// as a [ns_r+2][(ns_c+2)*kCtabRec] f32 tensor copied in box_h x box_w*kCtabRec
+// boxes (the innermost coordinate of a copy, (wx0+1)*kCtabRec floats, is a
+// multiple of 16 bytes).
 bool encode_maps(FrameArgs &a) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc || a.box_w * 8 > 256 || a.box_h > 256) return false;
+    if (!enc || a.box_w * kCtabRec > 256 || a.box_h > 256) return false;
     const cuuint64_t fdim[3] = {(cuuint64_t)a.P, (cuuint64_t)a.H, 3};
     const cuuint64_t fstride[2] = {(cuuint64_t)a.P * 4, (cuuint64_t)a.P * a.H * 4};
     const cuuint32_t fbox[3] = {(cuuint32_t)kTileW, (cuuint32_t)kTileH, 3};
@@ -93,9 +96,9 @@ bool encode_maps(FrameArgs &a) {
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
-    const cuuint64_t cdim[2] = {(cuuint64_t)(a.ns_c + 2) * 8, (cuuint64_t)(a.ns_r + 2)};
-    const cuuint64_t cstride[1] = {(cuuint64_t)(a.ns_c + 2) * 32};
-    const cuuint32_t cbox[2] = {(cuuint32_t)a.box_w * 8, (cuuint32_t)a.box_h};
+    const cuuint64_t cdim[2] = {(cuuint64_t)(a.ns_c + 2) * kCtabRec, (cuuint64_t)(a.ns_r + 2)};
+    const cuuint64_t cstride[1] = {(cuuint64_t)(a.ns_c + 2) * kCtabRec * 4};
+    const cuuint32_t cbox[2] = {(cuuint32_t)a.box_w * kCtabRec, (cuuint32_t)a.box_h};
     return enc(&a.ctab_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.ctab, cdim, cstride, cbox, ones,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -119,9 +122,15 @@ bool valid_params(const slic_params &p, std::string &why) {
     return true;
 }
 
-int grid_for(const slic_batch_ctx *b) {
-    const int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, b->occupancy) : b->occupancy;
+// Persistent grids: CTAs per SM requested (or all that fit), capped by the
+// occupancy of the kernel being launched.
+int grid_for(const slic_batch_ctx *b, int occ) {
+    const int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
     return std::max(1, per_sm) * b->sms;
+}
+
+int pipe_occ(const slic_batch_ctx *b, int stages) {
+    return std::max(1, assign_pipe_occupancy(b->same, b->win_max, stages));
 }
 
 std::string tune_key(const slic_batch_ctx *b) {
@@ -138,8 +147,8 @@ std::string tune_key(const slic_batch_ctx *b) {
     return key;
 }
 
-// Cache lines: {"key": "<key>", "ctas_per_sm": <int>, "ms": <float>}
-bool cache_lookup(const char *path, const std::string &key, int *ctas) {
+// Cache lines: {"key": "<key>", "ctas_per_sm": <int>, "stages": <int>, "ms": <float>}
+bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stages) {
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
     char line[4096];
@@ -148,9 +157,12 @@ bool cache_lookup(const char *path, const std::string &key, int *ctas) {
     while (std::fgets(line, sizeof line, f)) {
         if (std::strstr(line, needle.c_str())) {
             const char *q = std::strstr(line, "\"ctas_per_sm\":");
-            int v = 0;
-            if (q && std::sscanf(q + 14, "%d", &v) == 1 && v > 0) {
+            const char *r = std::strstr(line, "\"stages\":");
+            int v = 0, w = 0;
+            if (q && r && std::sscanf(q + 14, "%d", &v) == 1 && std::sscanf(r + 9, "%d", &w) == 1 && v > 0 &&
+                w >= 3 && w <= 4) {
                 *ctas = v;
+                *stages = w;
                 found = true;
             }
         }
@@ -159,10 +171,11 @@ bool cache_lookup(const char *path, const std::string &key, int *ctas) {
     return found;
 }
 
-void cache_store(const char *path, const std::string &key, int ctas, float ms) {
+void cache_store(const char *path, const std::string &key, int ctas, int stages, float ms) {
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"ms\": %.4f}\n", key.c_str(), ctas, ms);
+    std::fprintf(f, "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"stages\": %d, \"ms\": %.4f}\n", key.c_str(), ctas,
+                 stages, ms);
     std::fclose(f);
 }
 
@@ -239,7 +252,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         off_lbl[f] = bytes;
         bytes += align256(sizeof(int32_t) * (size_t)p.width * p.height);
         off_ctab[f] = bytes;
-        bytes += align256(sizeof(float) * 8 * (size_t)(a.ns_c + 2) * (a.ns_r + 2));
+        bytes += align256(sizeof(float) * kCtabRec * (size_t)(a.ns_c + 2) * (a.ns_r + 2));
         b->max_ring = std::max(b->max_ring, 2 * (a.ns_c + 2) + 2 * a.ns_r);
     }
     const size_t off_err = bytes;
@@ -260,9 +273,11 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         delete b;
         return bfail(nullptr, SLIC_ERR_CUDA, std::string("CUDA set-up: ") + cudaGetErrorString(e));
     }
-    b->pipe = !assign_direct_acc(b->win_max);
+    // The pipelined kernel needs private sums and its shared memory within
+    // the opt-in limit (at least with three stages).
+    b->pipe = !assign_direct_acc(b->win_max) && assign_pipe_occupancy(b->same, b->win_max, 3) > 0;
+    if (b->pipe && assign_pipe_occupancy(b->same, b->win_max, 4) == 0) b->stages = 3;
     b->occupancy = std::max(1, assign_batch_occupancy(b->same, b->smem));
-    if (b->pipe) b->occupancy = std::max(1, std::min(b->occupancy, assign_pipe_occupancy(b->same, b->win_max)));
     if (cudaMalloc(&b->scratch, bytes) != cudaSuccess ||
         cudaMalloc(&b->d_frames, sizeof(FrameArgs) * n_frames) != cudaSuccess) {
         cudaGetLastError();
@@ -333,7 +348,9 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
     cudaStream_t s = (cudaStream_t)stream;
-    const int grid = grid_for(b);
+    const int grid = grid_for(b, b->occupancy);
+    const int grid_pipe = b->pipe ? grid_for(b, pipe_occ(b, b->stages)) : grid;
+    const int pipe_per_sm = grid_pipe / std::max(1, b->sms);
     cudaError_t e = launch_init_batch(b->d_frames, b->n, b->total_centres, s);
     long long n_launch = 1;
     for (int pass = 0; e == cudaSuccess && pass <= b->iterations; ++pass) {
@@ -350,17 +367,17 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
                         return bfail(b, SLIC_ERR_CUDA, "cudaEventCreate failed");
                     b->events.emplace_back(x, y);
                 }
-                // External records become event-record nodes under stream capture.
-                cudaEventRecordWithFlags(b->events[b->ev_used].first, s, cudaEventRecordExternal);
+                e = record_profile_event(b->events[b->ev_used].first, s);
                 e1 = b->events[b->ev_used++].second;
             }
+            if (e != cudaSuccess) break;
             if (pass > 0 && b->pipe)
                 e = launch_assign_pipe(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == b->iterations,
-                                       grid, b->d_err, s);
+                                       b->stages, pipe_per_sm, grid_pipe, b->d_err, s);
             else
                 e = launch_assign_batch(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == 0,
                                         pass == b->iterations, b->smem, grid, s);
-            if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+            if (e1 && e == cudaSuccess) e = record_profile_event(e1, s);
             ++n_launch;
         }
     }
@@ -374,21 +391,27 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
     return SLIC_OK;
 }
 
-slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm) {
+slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (ctas_per_sm < 0) return bfail(b, SLIC_ERR_INVALID, "ctas_per_sm must be >= 0");
+    if (stages != 0 && (stages < 3 || stages > 4)) return bfail(b, SLIC_ERR_INVALID, "stages must be 0, 3 or 4");
+    if (stages && b->pipe && assign_pipe_occupancy(b->same, b->win_max, stages) == 0)
+        return bfail(b, SLIC_ERR_INVALID, "the pipeline stages do not fit in shared memory");
     b->ctas_per_sm = ctas_per_sm;
+    if (stages) b->stages = stages;
     return SLIC_OK;
 }
 
-slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm) {
+slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm, int *stages) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
     const std::string key = tune_key(b);
-    int best = 0;
-    if (cache_path && cache_lookup(cache_path, key, &best)) {
-        b->ctas_per_sm = std::min(best, b->occupancy);
-        if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    int best = 0, best_st = b->stages;
+    if (cache_path && cache_lookup(cache_path, key, &best, &best_st)) {
+        b->ctas_per_sm = best;
+        b->stages = best_st;
+        if (ctas_per_sm) *ctas_per_sm = best;
+        if (stages) *stages = best_st;
         return SLIC_OK;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -397,38 +420,50 @@ slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stre
         return bfail(b, SLIC_ERR_CUDA, "cudaEventCreate failed");
     float best_ms = 1e30f;
     slic_status st = SLIC_OK;
-    for (int c = 1; c <= b->occupancy && st == SLIC_OK; ++c) {
-        b->ctas_per_sm = c;
-        if ((st = slic_batch_segment(b, stream)) != SLIC_OK) break;  // warm-up
-        float total = 0.0f;
-        for (int rep = 0; rep < 3 && st == SLIC_OK; ++rep) {
-            cudaEventRecord(e0, s);
-            st = slic_batch_segment(b, stream);
-            cudaEventRecord(e1, s);
-            float ms = 0.0f;
-            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-                st = bfail(b, SLIC_ERR_CUDA, "autotune timing failed");
-            total += ms;
-        }
-        if (st == SLIC_OK && total / 3 < best_ms) {
-            best_ms = total / 3;
-            best = c;
+    // Search space: pipeline depth x resident CTAs per SM (up to what fits).
+    const int st_lo = b->pipe ? 3 : b->stages, st_hi = b->pipe ? 4 : b->stages;
+    for (int nst = st_lo; nst <= st_hi && st == SLIC_OK; ++nst) {
+        if (b->pipe && assign_pipe_occupancy(b->same, b->win_max, nst) == 0) continue;
+        const int occ = std::max(b->occupancy, b->pipe ? pipe_occ(b, nst) : 0);
+        for (int c = 1; c <= occ && st == SLIC_OK; ++c) {
+            b->ctas_per_sm = c;
+            b->stages = nst;
+            if ((st = slic_batch_segment(b, stream)) != SLIC_OK) break;  // warm-up
+            float total = 0.0f;
+            for (int rep = 0; rep < 3 && st == SLIC_OK; ++rep) {
+                cudaEventRecord(e0, s);
+                st = slic_batch_segment(b, stream);
+                cudaEventRecord(e1, s);
+                float ms = 0.0f;
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                    st = bfail(b, SLIC_ERR_CUDA, "autotune timing failed");
+                total += ms;
+            }
+            if (st == SLIC_OK && total / 3 < best_ms) {
+                best_ms = total / 3;
+                best = c;
+                best_st = nst;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != SLIC_OK) return st;
     b->ctas_per_sm = best;
-    if (cache_path) cache_store(cache_path, key, best, best_ms);
+    b->stages = best_st;
+    if (cache_path) cache_store(cache_path, key, best, best_st, best_ms);
     if (ctas_per_sm) *ctas_per_sm = best;
+    if (stages) *stages = best_st;
     return SLIC_OK;
 }
 
-slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm) {
+slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm,
+                            int *stages) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (total_pixels) *total_pixels = b->total_pixels;
     if (launches) *launches = b->launches;
-    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, b->occupancy) : b->occupancy;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : b->occupancy;
+    if (stages) *stages = b->pipe ? b->stages : 0;
     return SLIC_OK;
 }
 

@@ -22,6 +22,12 @@ constexpr int kTileH = 32;
 constexpr int kPPT = 4;
 constexpr int kThreads = (kTileW / kPPT) * kTileH;
 
+// Record of the padded centre table read by the pipelined assignment: every
+// field twice, (L, L, a, a, b, b, x, x, y, y, n, 0), so that the paired
+// (two pixels per instruction) FP32 arithmetic takes a centre field as one
+// 64-bit operand.
+constexpr int kCtabRec = 12;
+
 // Colour-conversion constants, computed on the host in double precision and
 // rounded to float (see slic_api.cu).
 struct ConvConsts {
@@ -71,7 +77,7 @@ static __device__ __forceinline__ void convert_pixel(const ConvConsts &cc, unsig
 // batched ones).
 struct FrameArgs {
     CUtensorMap feat_map;   // features as a [3][H][P] f32 tensor, box 32x32x3 (batched path)
-    CUtensorMap ctab_map;   // padded centre table as [(ns_r+2)][(ns_c+2)*8] f32, box box_w*8 x box_h
+    CUtensorMap ctab_map;   // padded centre table as [(ns_r+2)][(ns_c+2)*kCtabRec] f32, box box_w*kCtabRec x box_h
     ConvConsts conv;
     const uint8_t *rgb;     // [H][W][C]
     float *feat;            // 3 planes [H][P]; plane stride H*P
@@ -81,7 +87,7 @@ struct FrameArgs {
     int32_t *labels;        // [H][W]
     int32_t *lbl_tmp;       // [H][W] connectivity ping-pong (batched path)
     const float *init;      // [K][6] initial centres instead of the grid (batched path)
-    float *ctab;            // [(ns_r+2)(ns_c+2)][8] centres with a sentinel ring (batched path)
+    float *ctab;            // [(ns_r+2)(ns_c+2)][kCtabRec] centres with a sentinel ring (batched path)
     int W, H, P, C, S, ns_c, ns_r;
     float w;                // m / S
     int win_max;            // largest centre window of any tile (sizes shared memory)
@@ -130,10 +136,13 @@ cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_cent
 // Pipelined (TMA bulk copies, mbarrier) assignment for the passes after the
 // first, reading features and the padded centre table; *err is set on a
 // timed-out wait.
+// ctas_per_sm >= 4 selects the 64-register build.
 cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool last,
-                               int grid, int *err, cudaStream_t s);
-size_t assign_pipe_smem_bytes(int win_n, bool last);
-int assign_pipe_occupancy(bool same, int win_n);
+                               int nst, int ctas_per_sm, int grid, int *err, cudaStream_t s);
+// Shared memory and resident CTAs per SM of the pipelined kernel with nst
+// (2..4) stages.
+size_t assign_pipe_smem_bytes(int win_n, bool last, int nst);
+int assign_pipe_occupancy(bool same, int win_n, int nst);
 cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cudaStream_t s);
 cudaError_t launch_accumulate_labels(const float *feat, int W, int H, int P, const int32_t *labels, int K,
                                      long long *acc, float fix_scale, cudaStream_t s);
@@ -142,5 +151,7 @@ cudaError_t launch_convert(const ConvConsts &cc, const uint8_t *rgb, int W, int 
 cudaError_t launch_connectivity(const int32_t *in, int32_t *out, int W, int H, cudaStream_t s);
 cudaError_t launch_connectivity_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w, int pass,
                                       cudaStream_t s);
+// Event record for the profiling timers, valid inside and outside stream capture.
+cudaError_t record_profile_event(cudaEvent_t ev, cudaStream_t s);
 
 }  // namespace slicgb

@@ -35,6 +35,14 @@ constexpr int kWarps = kThreads / 32;
 constexpr float kSentinel = 1e18f;
 constexpr size_t kPrivateAccLimit = 64 * 1024;
 
+// One record of the padded centre table: each field twice (see kCtabRec).
+__device__ __forceinline__ void write_ctab(float *t, const float *c) {
+    float4 *t4 = reinterpret_cast<float4 *>(t);
+    t4[0] = make_float4(c[0], c[0], c[1], c[1]);
+    t4[1] = make_float4(c[2], c[2], c[3], c[3]);
+    t4[2] = make_float4(c[4], c[4], c[5], 0.0f);
+}
+
 __device__ __forceinline__ float fsqrt_approx(float x) {
     float r;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -137,9 +145,7 @@ __global__ void k_init_batch(const FrameArgs *frames, int n, int total) {
     }
     if (a.ctab) {
         const int r = k / a.ns_c, c = k - (k / a.ns_c) * a.ns_c;
-        float *t = a.ctab + ((size_t)(r + 1) * (a.ns_c + 2) + c + 1) * 8;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) t[q] = a.centres_out[(size_t)k * 6 + q];
+        write_ctab(a.ctab + ((size_t)(r + 1) * (a.ns_c + 2) + c + 1) * kCtabRec, a.centres_out + (size_t)k * 6);
     }
 }
 
@@ -155,9 +161,9 @@ __global__ void k_fill_ring(const FrameArgs *frames, int n, int max_ring) {
         if (i < cw) { r = 0; c = i; }
         else if (i < 2 * cw) { r = ch - 1; c = i - cw; }
         else { const int j = i - 2 * cw; r = 1 + (j >> 1); c = (j & 1) ? cw - 1 : 0; }
-        float *t = a.ctab + ((size_t)r * cw + c) * 8;
+        float4 *t = reinterpret_cast<float4 *>(a.ctab + ((size_t)r * cw + c) * kCtabRec);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) t[q] = 1e18f;
+        for (int q = 0; q < kCtabRec / 4; ++q) t[q] = make_float4(1e18f, 1e18f, 1e18f, 1e18f);
     }
 }
 
@@ -599,6 +605,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_batch(const FrameArgs *f
 namespace {
 
 constexpr size_t kStageFeatBytes = (size_t)3 * kTileH * kTileW * 4;  // 12288
+constexpr int kMaxStages = 4;
+constexpr int kAccSets = 3;    // accumulator sets in flight: fill, flush, reuse
+constexpr int kHdrSlots = 8;   // tile-header ring (>= stages + 2)
 constexpr unsigned kWaitPolls = 1u << 20;                         // x 1 us suspend hint: ~1 s bound
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -628,6 +637,10 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // Wait for the phase with the given parity to complete; gives up (returns
 // false) after kWaitPolls polls with a 1 us suspend hint each.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
@@ -645,14 +658,92 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
     return false;
 }
 
-struct TileGeom {
-    int tx0, ty0, wx0, wy0, wnx, wny;
-    int f;                 // frame index
+// Paired FP32 arithmetic: a 64-bit operand holds two floats (low, high);
+// each element is rounded exactly as the scalar instruction would be.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// min of two non-negative floats (a NaN operand loses), IEEE (no flush).
+__device__ __forceinline__ float fmin_nan(float a, float b) {
+    float r;
+    asm("min.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// Eq. (1) for two pixels (colour pairs l, a, b; column pair x) against one
+// centre record: d_lab = sqrt(dl^2 + da^2 + db^2), d_xy = sqrt(dx^2 + dy^2),
+// D = (m/S) d_xy + d_lab, then the index-carrying running minimum.
+__device__ __forceinline__ void eval_pair(const ulonglong2 &la, const ulonglong2 &bx, unsigned long long ddy2,
+                                          unsigned long long ww, unsigned long long l, unsigned long long a,
+                                          unsigned long long b, unsigned long long x, unsigned t, float &bk0,
+                                          float &bk1) {
+    const unsigned long long dl = sub2(la.x, l), da = sub2(la.y, a), db = sub2(bx.x, b);
+    const unsigned long long s = fma2(dl, dl, fma2(da, da, mul2(db, db)));
+    const unsigned long long dx = sub2(bx.y, x);
+    const unsigned long long q = fma2(dx, dx, ddy2);
+    float s0, s1, q0, q1;
+    unpack2(s, s0, s1);
+    unpack2(q, q0, q1);
+    const unsigned long long D = fma2(ww, pack2(fsqrt_approx(q0), fsqrt_approx(q1)),
+                                      pack2(fsqrt_approx(s0), fsqrt_approx(s1)));
+    float d0, d1;
+    unpack2(D, d0, d1);
+    bk0 = fmin_nan(bk0, __uint_as_float((__float_as_uint(d0) & ~15u) | t));
+    bk1 = fmin_nan(bk1, __uint_as_float((__float_as_uint(d1) & ~15u) | t));
+}
+
+// Tile header written by the tile's producer next to its stage: the tile's
+// geometry and the frame constants the consumers need, so that a warp reads
+// one shared-memory record per tile instead of the frame table in global
+// memory.
+struct __align__(16) TileGeom {
+    int tx0, ty0, wx0, wy0;
+    int wnx, wny;
     unsigned wnx_mul;      // ceil(2^32 / wnx): cell / wnx for the flush
+    int f;                 // frame index
+    int W, H, S, ns_c;
+    unsigned s_mul;
+    int box_w;
+    float w, fix_scale;
+    int32_t *labels;
+    long long *acc;
+    int labels_vec, pad;
 };
 
 __device__ __forceinline__ TileGeom tile_geom(const FrameArgs &a, int local) {
     TileGeom g;
+    g.W = a.W;
+    g.H = a.H;
+    g.S = a.S;
+    g.ns_c = a.ns_c;
+    g.s_mul = a.s_mul;
+    g.box_w = a.box_w;
+    g.w = a.w;
+    g.fix_scale = a.fix_scale;
+    g.labels = a.labels;
+    g.acc = a.acc;
+    g.labels_vec = a.labels_vec;
+    g.pad = 0;
     const int ty = local / a.tiles_x, tx = local - ty * a.tiles_x;
     g.tx0 = tx * kTileW;
     g.ty0 = ty * kTileH;
@@ -670,86 +761,167 @@ __device__ __forceinline__ TileGeom tile_geom(const FrameArgs &a, int local) {
 // and issue the two tensor copies.
 __device__ __forceinline__ void issue_tile(const FrameArgs &a, const TileGeom &g, unsigned char *stage,
                                            uint64_t *bar) {
-    const unsigned cen_bytes = (unsigned)a.box_w * (unsigned)a.box_h * 32u;
+    const unsigned cen_bytes = (unsigned)a.box_w * (unsigned)a.box_h * (unsigned)(kCtabRec * 4);
     mbar_expect_tx(bar, (unsigned)kStageFeatBytes + cen_bytes);
     tma_load_3d(stage, &a.feat_map, g.tx0, g.ty0, 0, bar);
-    tma_load_2d(stage + kStageFeatBytes, &a.ctab_map, (g.wx0 + 1) * 8, g.wy0 + 1, bar);
+    tma_load_2d(stage + kStageFeatBytes, &a.ctab_map, (g.wx0 + 1) * kCtabRec, g.wy0 + 1, bar);
+}
+
+// Add tile j's private sums (all warps' copies of accumulator set j % 3) to
+// the frame's global sums and clear them; warp w takes items w, w + 8, ...
+// of the window's (cell, word) items. Waits until every warp has filled the
+// set, and reports the set free afterwards. False when the wait timed out.
+__device__ __forceinline__ bool flush_tile(const TileGeom *hdr, unsigned *wacc0, size_t acc_words, int win_max,
+                                           uint64_t *acc_done, uint64_t *acc_free, int j, int warp, int lane) {
+    const int set = j % kAccSets;
+    if (!__all_sync(0xffffffffu, mbar_wait(&acc_done[set], (j / kAccSets) & 1))) return false;
+    const TileGeom &g = hdr[j % kHdrSlots];
+    const int bw = g.box_w, ns_c = g.ns_c, wnx = g.wnx, wny = g.wny, wx0 = g.wx0, wy0 = g.wy0, tx0 = g.tx0,
+              ty0 = g.ty0;
+    const unsigned wnx_mul = g.wnx_mul;
+    long long *const acc = g.acc;
+    unsigned *const ws = wacc0 + (size_t)set * acc_words;
+    const int n_items = wnx * wny * 4;
+    for (int i = warp + kWarps * lane; i < n_items; i += kWarps * 32) {
+        const int cell = i >> 2, c = i & 3;
+        const int qy = (int)__umulhi((unsigned)cell, wnx_mul), qx = cell - qy * wnx;
+        const int idx = (qy * bw + qx) * 4 + c;
+        unsigned long long *gs =
+            reinterpret_cast<unsigned long long *>(acc) + ((size_t)(wy0 + qy) * ns_c + wx0 + qx) * 6;
+        if (c < 3) {
+            long long t = 0;
+#pragma unroll
+            for (int q = 0; q < kWarps; ++q) {
+                t += (int)ws[(size_t)q * win_max * 4 + idx];
+                ws[(size_t)q * win_max * 4 + idx] = 0u;
+            }
+            if (t != 0) atomicAdd(&gs[c], (unsigned long long)t);
+        } else {
+            long long xs = 0, ys = 0, n = 0;
+#pragma unroll
+            for (int q = 0; q < kWarps; ++q) {
+                const unsigned pk = ws[(size_t)q * win_max * 4 + idx];
+                ws[(size_t)q * win_max * 4 + idx] = 0u;
+                xs += pk & 0xFFFu;
+                ys += (pk >> 12) & 0xFFFu;
+                n += pk >> 24;
+            }
+            if (n != 0) {
+                atomicAdd(&gs[3], (unsigned long long)(xs + n * tx0));
+                atomicAdd(&gs[4], (unsigned long long)(ys + n * ty0));
+                atomicAdd(&gs[5], (unsigned long long)n);
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&acc_free[set]);
+    return true;
 }
 
 }  // namespace
 
-size_t assign_pipe_smem_bytes(int win_n, bool last) {
-    const size_t stage = kStageFeatBytes + (((size_t)win_n * 32 + 127) & ~(size_t)127);
+size_t assign_pipe_smem_bytes(int win_n, bool last, int nst) {
+    const size_t stage = kStageFeatBytes + (((size_t)win_n * kCtabRec * 4 + 127) & ~(size_t)127);
     const size_t acc = last ? 0 : (size_t)kWarps * win_n * 4 * sizeof(int);
-    // + two mbarriers, the abort flag, two tile headers and base alignment
-    return 2 * (stage + acc) + 32 + 2 * sizeof(TileGeom) + 128;
+    // nst stages, the accumulator sets, the mbarriers, the header ring, two
+    // flags and base alignment
+    return (size_t)nst * stage + kAccSets * acc + (size_t)(2 * kMaxStages + 2 * kAccSets) * 8 +
+           (size_t)kHdrSlots * sizeof(TileGeom) + 16 + 128;
 }
 
-template <bool LAST, bool SAME>
-__global__ void __launch_bounds__(kThreads, 3) k_assign_pipe(const FrameArgs *frames, int n_frames, int total_tiles,
-                                                             int win_max, int *err) {
+template <bool LAST, bool SAME, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs *frames, int n_frames,
+                                                                int total_tiles, int win_max, int nst, int *err) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     // Tensor copies want 128-byte aligned destinations.
     unsigned char *smem_raw =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~(uintptr_t)127);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const size_t stage_bytes = kStageFeatBytes + (((size_t)win_max * 32 + 127) & ~(size_t)127);
+    const size_t stage_bytes = kStageFeatBytes + (((size_t)win_max * kCtabRec * 4 + 127) & ~(size_t)127);
     const size_t acc_words = LAST ? 0 : (size_t)kWarps * win_max * 4;
-    unsigned *const wacc0 = reinterpret_cast<unsigned *>(smem_raw + 2 * stage_bytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + 2 * stage_bytes + 2 * acc_words * 4);
-    int *abort_flag = reinterpret_cast<int *>(bars + 2);
-    TileGeom *hdr = reinterpret_cast<TileGeom *>(bars + 4);  // per stage, written by the issuing thread
+    unsigned *const wacc0 = reinterpret_cast<unsigned *>(smem_raw + (size_t)nst * stage_bytes);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)nst * stage_bytes + kAccSets * acc_words * 4);
+    uint64_t *empty = full + kMaxStages;       // stage released by every warp (count kWarps)
+    uint64_t *acc_done = empty + kMaxStages;   // accumulator set filled by every warp (count kWarps)
+    uint64_t *acc_free = acc_done + kAccSets;  // accumulator set flushed and cleared (count kWarps)
+    TileGeom *hdr = reinterpret_cast<TileGeom *>(acc_free + kAccSets);  // ring of kHdrSlots tile headers
+    int *flags = reinterpret_cast<int *>(hdr + kHdrSlots);              // [0] abort, [1] last tile issued
+    volatile int *abort_flag = flags;
+    const int ahead = nst - 3;  // tiles issued beyond the next one: stage reuse lags two tiles
 
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int q = 0; q < nst; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kWarps);
+        }
+        for (int q = 0; q < kAccSets; ++q) {
+            mbar_init(&acc_done[q], kWarps);
+            mbar_init(&acc_free[q], kWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *abort_flag = 0;
+        flags[0] = 0;
+        flags[1] = -1;
     }
     if (!LAST) {
-        for (int i = tid; i < (int)(2 * acc_words); i += kThreads) wacc0[i] = 0u;
+        for (int i = tid; i < (int)(kAccSets * acc_words); i += kThreads) wacc0[i] = 0u;
     }
     __syncthreads();
 
-    int tile = blockIdx.x;
-    if (tile < total_tiles && tid == 0) {
-        const int f = find_frame<kTileBase>(frames, n_frames, tile);
-        TileGeom g = tile_geom(frames[f], tile - frames[f].tile_base);
+    // Tile j of this CTA (global tile blockIdx.x + j * gridDim.x) goes to
+    // stage j % nst (its use j / nst of that stage) and header slot
+    // j % kHdrSlots. Its producer issues it at the top of iteration
+    // j - ahead - 1, once every warp has released the stage's previous tile
+    // j - nst (two iterations earlier); the producer role rotates over the
+    // warps. No CTA-wide barrier inside the loop: warps drift up to about two
+    // tiles apart, bounded by the mbarriers.
+    auto produce = [&](int j) -> bool {
+        const int t = blockIdx.x + j * gridDim.x;
+        if (t >= total_tiles) return true;
+        const int q = j % nst;
+        if (j >= nst && !mbar_wait(&empty[q], ((j / nst) - 1) & 1)) return false;
+        const int f = find_frame<kTileBase>(frames, n_frames, t);
+        TileGeom g = tile_geom(frames[f], t - frames[f].tile_base);
         g.f = f;
-        hdr[0] = g;
-        issue_tile(frames[f], g, smem_raw, &bars[0]);
+        hdr[j % kHdrSlots] = g;
+        issue_tile(frames[f], g, smem_raw + (size_t)q * stage_bytes, &full[q]);
+        atomicMax(&flags[1], j);
+        return true;
+    };
+    if (tid == 0) {
+        for (int j = 0; j <= ahead; ++j) produce(j);
     }
     __syncthreads();
-    unsigned parity = 0u;  // bit s: parity of the phase stage s completes next
+
     const int lx = 4 * (lane & 7), ly = 4 * warp + (lane >> 3);
-    for (int it = 0; tile < total_tiles; ++it) {
-        const int s = it & 1;
-        unsigned char *const stage_s = smem_raw + (size_t)s * stage_bytes;
-        unsigned *const wacc_s = wacc0 + (size_t)s * acc_words;
-        const int next = tile + gridDim.x;
-        const TileGeom g = hdr[s];
-        if (tid == 0 && next < total_tiles) {
-            const int fn = find_frame<kTileBase>(frames, n_frames, next);
-            TileGeom gn = tile_geom(frames[fn], next - frames[fn].tile_base);
-            gn.f = fn;
-            hdr[s ^ 1] = gn;
-            issue_tile(frames[fn], gn, smem_raw + (size_t)(s ^ 1) * stage_bytes, &bars[s ^ 1]);
+    int it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++it) {
+        if (*abort_flag) {
+            ok = false;
+            break;
         }
-        const FrameArgs &a = frames[g.f];
-        const int bw = a.box_w;
-        const bool ok_wait = mbar_wait(&bars[s], (parity >> s) & 1u);
-        parity ^= 1u << s;
-        if (!ok_wait) {
+        if (warp == (it & (kWarps - 1)) && lane == 0 && !produce(it + ahead + 1)) {
             *abort_flag = 1;
             atomicOr(err, 1);
         }
-
-        const int W = a.W, H = a.H, S = a.S, ns_c = a.ns_c;
-        const unsigned s_mul = a.s_mul;
+        const int s = it % nst;
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (it / nst) & 1))) {
+            if (lane == 0) {
+                *abort_flag = 1;
+                atomicOr(err, 1);
+            }
+            ok = false;
+            break;
+        }
+        unsigned char *const stage_s = smem_raw + (size_t)s * stage_bytes;
+        const TileGeom &g = hdr[it % kHdrSlots];
+        const int bw = g.box_w, tx0 = g.tx0, ty0 = g.ty0, wx0 = g.wx0, wy0 = g.wy0;
+        const int W = g.W, H = g.H, S = g.S, ns_c = g.ns_c;
+        const unsigned s_mul = g.s_mul;
         const float *feat = reinterpret_cast<const float *>(stage_s);
         const float *cen = reinterpret_cast<const float *>(stage_s + kStageFeatBytes);
-        const int x = g.tx0 + lx, y = g.ty0 + ly;
-        const bool row_ok = ok_wait && (y < H) && (x < W);
+        const int x = tx0 + lx, y = ty0 + ly;
+        const bool row_ok = (y < H) && (x < W);
         float f0[kPPT] = {}, f1[kPPT] = {}, f2[kPPT] = {};
         if (row_ok) {
             const float4 v0 = *reinterpret_cast<const float4 *>(feat + (0 * kTileH + ly) * kTileW + lx);
@@ -776,33 +948,54 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_pipe(const FrameArgs *fr
             }
         }
         // Eq. (1) over the nine window centres, as in assign_tile (window
-        // index = (cell row - wy0) * box_w + (cell column - wx0)).
-        unsigned bk[kPPT];
+        // index = (cell row - wy0) * box_w + (cell column - wx0)), with the
+        // same operations in the same order. The running minimum is a float
+        // whose low 4 mantissa bits carry the candidate index: non-negative
+        // floats order like their bit patterns, so this equals the integer
+        // minimum of (D & ~15) | t, scan order breaking ties.
+        float bk[kPPT];
 #pragma unroll
-        for (int j = 0; j < kPPT; ++j) bk[j] = 0xFFFFFFFFu;
+        for (int j = 0; j < kPPT; ++j) bk[j] = __int_as_float(0x7F800000);
         if (row_ok) {
-            const float w = a.w;
+            const float w = g.w;
             const float fy = (float)y;
-            float fxs[kPPT];
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j) fxs[j] = (float)(x + j);
-            const int rowoff = (pcy - g.wy0) * bw - g.wx0;
-#pragma unroll
-            for (int jj = 0; jj < (SAME ? 1 : kPPT); ++jj) {
-                const int own = rowoff + cx[jj];
+            const int rowoff = (pcy - wy0) * bw - wx0;
+            if (SAME) {
+                // The thread's 4 pixels share the window: pixels (0, 1) and
+                // (2, 3) go through paired FP32 instructions.
+                const unsigned long long ww = pack2(w, w), fyy = pack2(fy, fy);
+                const unsigned long long l01 = pack2(f0[0], f0[1]), l23 = pack2(f0[2], f0[3]);
+                const unsigned long long a01 = pack2(f1[0], f1[1]), a23 = pack2(f1[2], f1[3]);
+                const unsigned long long b01 = pack2(f2[0], f2[1]), b23 = pack2(f2[2], f2[3]);
+                const unsigned long long x01 = pack2((float)x, (float)(x + 1)), x23 = pack2((float)(x + 2), (float)(x + 3));
+                const int own = rowoff + cx[0];
 #pragma unroll
                 for (int t = 0; t < 9; ++t) {
-                    const int wi = own + (t / 3 - 1) * bw + (t % 3 - 1);
-                    const float4 c = *reinterpret_cast<const float4 *>(cen + (size_t)wi * 8);
-                    const float ddy = cen[(size_t)wi * 8 + 4] - fy;
-                    const float ddy2 = ddy * ddy;
+                    const float *r = cen + (size_t)(own + (t / 3 - 1) * bw + (t % 3 - 1)) * kCtabRec;
+                    const ulonglong2 la = *reinterpret_cast<const ulonglong2 *>(r);      // (L, L), (a, a)
+                    const ulonglong2 bx = *reinterpret_cast<const ulonglong2 *>(r + 4);  // (b, b), (x, x)
+                    const unsigned long long yy = *reinterpret_cast<const unsigned long long *>(r + 8);
+                    const unsigned long long ddy = sub2(yy, fyy);
+                    const unsigned long long ddy2 = mul2(ddy, ddy);
+                    eval_pair(la, bx, ddy2, ww, l01, a01, b01, x01, (unsigned)t, bk[0], bk[1]);
+                    eval_pair(la, bx, ddy2, ww, l23, a23, b23, x23, (unsigned)t, bk[2], bk[3]);
+                }
+            } else {
 #pragma unroll
-                    for (int j = (SAME ? 0 : jj); j < (SAME ? kPPT : jj + 1); ++j) {
-                        const float ddx = c.w - fxs[j];
-                        const float dl = c.x - f0[j], da = c.y - f1[j], db = c.z - f2[j];
+                for (int j = 0; j < kPPT; ++j) {
+                    const int own = rowoff + cx[j];
+                    const float fx = (float)(x + j);
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) {
+                        const float *r = cen + (size_t)(own + (t / 3 - 1) * bw + (t % 3 - 1)) * kCtabRec;
+                        const float4 la = *reinterpret_cast<const float4 *>(r);
+                        const float4 bx = *reinterpret_cast<const float4 *>(r + 4);
+                        const float ddy = r[8] - fy;
+                        const float ddx = bx.z - fx;
+                        const float dl = la.x - f0[j], da = la.z - f1[j], db = bx.x - f2[j];
                         const float d_lab = fsqrt_approx(fmaf(dl, dl, fmaf(da, da, db * db)));
-                        const float D = fmaf(w, fsqrt_approx(fmaf(ddx, ddx, ddy2)), d_lab);
-                        bk[j] = min(bk[j], (__float_as_uint(D) & ~15u) | (unsigned)t);
+                        const float D = fmaf(w, fsqrt_approx(fmaf(ddx, ddx, ddy * ddy)), d_lab);
+                        bk[j] = fmin_nan(bk[j], __uint_as_float((__float_as_uint(D) & ~15u) | (unsigned)t));
                     }
                 }
             }
@@ -810,26 +1003,28 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_pipe(const FrameArgs *fr
         int best[kPPT];
 #pragma unroll
         for (int j = 0; j < kPPT; ++j) {
-            const int t = (int)(bk[j] & 15u);
+            const int t = (int)(__float_as_uint(bk[j]) & 15u);
             const int dy = t / 3 - 1, dx = t % 3 - 1;
             const bool ok = row_ok && (x + j < W);
             if (LAST)
                 best[j] = ok ? (pcy + dy) * ns_c + cx[j] + dx : -1;
             else
-                best[j] = ok ? (pcy + dy - g.wy0) * bw + (cx[j] + dx - g.wx0) : -1;
+                best[j] = ok ? (pcy + dy - wy0) * bw + (cx[j] + dx - wx0) : -1;
         }
+        // Every read of the stage is done: release it to the producers.
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
         if constexpr (LAST) {
             if (row_ok) {
-                int32_t *out = a.labels + (size_t)y * W + x;
-                if (a.labels_vec) {
+                int32_t *out = g.labels + (size_t)y * W + x;
+                if (g.labels_vec) {
                     *reinterpret_cast<int4 *>(out) = make_int4(best[0], best[1], best[2], best[3]);
                 } else {
                     for (int j = 0; j < kPPT && x + j < W; ++j) out[j] = best[j];
                 }
             }
-            __syncthreads();
         } else {
-            const float fs = a.fix_scale;
+            const float fs = g.fix_scale;
             unsigned v[kPPT][4];
 #pragma unroll
             for (int j = 0; j < kPPT; ++j) {
@@ -845,7 +1040,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_pipe(const FrameArgs *fr
                     for (int c = 0; c < 4; ++c) v[j][c] += v[j + 1][c];
                 }
             }
-            unsigned *my = wacc_s + (size_t)warp * win_max * 4;
+            // Set it % 3 was flushed (tile it - 3) before it is reused.
+            const int set = it % kAccSets;
+            if (it >= kAccSets && !__all_sync(0xffffffffu, mbar_wait(&acc_free[set], ((it / kAccSets) - 1) & 1))) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    atomicOr(err, 1);
+                }
+                ok = false;
+                break;
+            }
+            unsigned *my = wacc0 + (size_t)set * acc_words + (size_t)warp * win_max * 4;
 #pragma unroll
             for (int j = 0; j < kPPT; ++j) {
                 const int k = (j == 0 || best[j] != best[j - 1]) ? best[j] : -1;
@@ -854,89 +1059,86 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_pipe(const FrameArgs *fr
                     for (int c = 0; c < 4; ++c) atomicAdd(&my[k * 4 + c], v[j][c]);
                 }
             }
-            __syncthreads();
-            // Flush this stage's private sums to the global sums and clear
-            // them for the tile after next (the next tile uses the other set).
-            for (int i = tid; i < g.wnx * g.wny * 4; i += kThreads) {
-                const int cell = i >> 2, c = i & 3;
-                const int qy = (int)__umulhi((unsigned)cell, g.wnx_mul), qx = cell - qy * g.wnx;
-                const int idx = (qy * bw + qx) * 4 + c;
-                unsigned long long *gs =
-                    reinterpret_cast<unsigned long long *>(a.acc) + ((size_t)(g.wy0 + qy) * ns_c + g.wx0 + qx) * 6;
-                if (c < 3) {
-                    long long t = 0;
-#pragma unroll
-                    for (int q = 0; q < kWarps; ++q) {
-                        t += (int)wacc_s[(size_t)q * win_max * 4 + idx];
-                        wacc_s[(size_t)q * win_max * 4 + idx] = 0u;
-                    }
-                    if (t != 0) atomicAdd(&gs[c], (unsigned long long)t);
-                } else {
-                    long long xs = 0, ys = 0, n = 0;
-#pragma unroll
-                    for (int q = 0; q < kWarps; ++q) {
-                        const unsigned pk = wacc_s[(size_t)q * win_max * 4 + idx];
-                        wacc_s[(size_t)q * win_max * 4 + idx] = 0u;
-                        xs += pk & 0xFFFu;
-                        ys += (pk >> 12) & 0xFFFu;
-                        n += pk >> 24;
-                    }
-                    if (n != 0) {
-                        atomicAdd(&gs[3], (unsigned long long)(xs + n * g.tx0));
-                        atomicAdd(&gs[4], (unsigned long long)(ys + n * g.ty0));
-                        atomicAdd(&gs[5], (unsigned long long)n);
-                    }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_done[set]);
+            // Flush the previous tile's sums (one slice per warp).
+            if (it > 0 && !flush_tile(hdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    atomicOr(err, 1);
                 }
+                ok = false;
+                break;
             }
         }
-        if (*abort_flag) {
-            // A wait timed out: let the copies of the next tile land (bounded)
-            // before leaving, so none targets a CTA that has exited.
-            if (next < total_tiles) mbar_wait(&bars[s ^ 1], (parity >> (s ^ 1)) & 1u);
-            return;
+    }
+    if (!LAST && ok && it > 0 &&
+        !flush_tile(hdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
+        if (lane == 0) {
+            *abort_flag = 1;
+            atomicOr(err, 1);
         }
-        tile = next;
+    }
+    __syncthreads();
+    if (tid == 0 && *abort_flag) {
+        // A wait timed out: let the copies already issued land (bounded)
+        // before the CTA exits, so none targets freed shared memory.
+        const int last = flags[1];
+        for (int j = max(0, last - nst + 1); j <= last; ++j) mbar_wait(&full[j % nst], (j / nst) & 1);
     }
 }
 
-template <bool L, bool SM>
+// Resident CTAs per SM of one instantiation (the query honours the
+// kernel's dynamic shared memory opt-in, so that is raised first).
+template <bool L, bool SM, int MINB>
 static int pipe_occupancy_of(size_t smem) {
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_assign_pipe<L, SM>, kThreads, smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_assign_pipe<L, SM, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_assign_pipe<L, SM, MINB>, kThreads, smem) !=
+            cudaSuccess)
         return 0;
     return blocks;
 }
 
-int assign_pipe_occupancy(bool same, int win_n) {
-    const size_t sm = assign_pipe_smem_bytes(win_n, false);
-    return same ? pipe_occupancy_of<false, true>(sm) : pipe_occupancy_of<false, false>(sm);
+int assign_pipe_occupancy(bool same, int win_n, int nst) {
+    const size_t sm = assign_pipe_smem_bytes(win_n, false, nst);
+    // The 4-CTA build (64 registers) where shared memory allows, else the 3-CTA build.
+    const int o4 = same ? pipe_occupancy_of<false, true, 4>(sm) : pipe_occupancy_of<false, false, 4>(sm);
+    const int o3 = same ? pipe_occupancy_of<false, true, 3>(sm) : pipe_occupancy_of<false, false, 3>(sm);
+    return o4 >= 4 ? o4 : o3;
+}
+
+template <bool L, bool SM, int MINB>
+static cudaError_t launch_pipe_as(const FrameArgs *d_frames, int n, int total_tiles, int win_max, int nst, int grid,
+                                  size_t smem, int *err, cudaStream_t s) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_assign_pipe<L, SM, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_assign_pipe<L, SM, MINB><<<grid, kThreads, smem, s>>>(d_frames, n, total_tiles, win_max, nst, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool last,
-                               int grid, int *err, cudaStream_t s) {
+                               int nst, int ctas_per_sm, int grid, int *err, cudaStream_t s) {
     if (grid > total_tiles) grid = total_tiles;
     if (grid < 1) grid = 1;
-    const size_t smem = assign_pipe_smem_bytes(win_max, last);
-    cudaError_t e;
+    if (nst < 3) nst = 3;
+    if (nst > kMaxStages) nst = kMaxStages;
+    const size_t smem = assign_pipe_smem_bytes(win_max, last, nst);
+    const bool wide = ctas_per_sm >= 4;  // 64-register build
     if (same) {
-        if (last) {
-            e = cudaFuncSetAttribute(k_assign_pipe<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_assign_pipe<true, true><<<grid, kThreads, smem, s>>>(d_frames, n, total_tiles, win_max, err);
-        } else {
-            e = cudaFuncSetAttribute(k_assign_pipe<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_assign_pipe<false, true><<<grid, kThreads, smem, s>>>(d_frames, n, total_tiles, win_max, err);
-        }
-    } else {
-        if (last) {
-            e = cudaFuncSetAttribute(k_assign_pipe<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_assign_pipe<true, false><<<grid, kThreads, smem, s>>>(d_frames, n, total_tiles, win_max, err);
-        } else {
-            e = cudaFuncSetAttribute(k_assign_pipe<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_assign_pipe<false, false><<<grid, kThreads, smem, s>>>(d_frames, n, total_tiles, win_max, err);
-        }
+        if (last)
+            return wide ? launch_pipe_as<true, true, 4>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
+                        : launch_pipe_as<true, true, 3>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
+        return wide ? launch_pipe_as<false, true, 4>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
+                    : launch_pipe_as<false, true, 3>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
     }
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
+    if (last)
+        return wide ? launch_pipe_as<true, false, 4>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
+                    : launch_pipe_as<true, false, 3>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
+    return wide ? launch_pipe_as<false, false, 4>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
+                : launch_pipe_as<false, false, 3>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
 }
 
 cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cudaStream_t s) {
@@ -985,9 +1187,7 @@ __global__ void k_update_batch(const FrameArgs *frames, int n, int total) {
     update_centre(a.acc + k, a.centres_out + k, a.centres_out + k, 1.0 / (double)a.fix_scale);
     if (a.ctab) {
         const int r = kk / a.ns_c, c = kk - r * a.ns_c;
-        float *t = a.ctab + ((size_t)(r + 1) * (a.ns_c + 2) + c + 1) * 8;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) t[q] = a.centres_out[k + q];
+        write_ctab(a.ctab + ((size_t)(r + 1) * (a.ns_c + 2) + c + 1) * kCtabRec, a.centres_out + k);
     }
 }
 
@@ -1230,8 +1430,10 @@ cudaError_t launch_assign_batch(const FrameArgs *d_frames, int n, int total_tile
 template <bool F, bool L, bool SM>
 static int occupancy_of(size_t smem) {
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_assign_batch<F, L, SM>, kThreads, smem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(k_assign_batch<F, L, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_assign_batch<F, L, SM>, kThreads, smem) !=
+            cudaSuccess)
         return 0;
     return blocks;
 }

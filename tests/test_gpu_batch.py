@@ -94,14 +94,42 @@ def test_autotune_writes_and_reuses_cache(slic_gpu, tmp_path):
     bs = pkg.BatchSegmenter(frames, iterations=2)
     bs.bind([_cuda(synth.voronoi_frame(f["width"], f["height"], 20, 6.0, 5)) for f in frames])
     cache = str(tmp_path / "tune.jsonl")
-    c1 = bs.autotune(cache)
-    assert c1 >= 1
+    c1, st1 = bs.autotune(cache)
+    assert c1 >= 1 and 3 <= st1 <= 4
     line = json.loads(open(cache).read().splitlines()[0])
-    assert line["ctas_per_sm"] == c1 and "640x480s16" in line["key"]
-    bs.set_tuning(0)
-    assert bs.autotune(cache) == c1          # served from the cache
+    assert line["ctas_per_sm"] == c1 and line["stages"] == st1 and "640x480s16" in line["key"]
+    bs.set_tuning(0, 3 if st1 != 3 else 4)
+    assert bs.autotune(cache) == (c1, st1)   # served from the cache
     assert len(open(cache).read().splitlines()) == 1
-    assert bs.info[2] == c1
+    assert bs.info[2] == c1 and bs.info[3] == st1
+
+
+@pytest.mark.parametrize("stages", [3, 4])
+def test_pipeline_depth_is_bit_exact(slic_gpu, stages):
+    """Every pipeline depth and launch shape gives the same labels and centres
+    (fixed-point update sums are order-independent)."""
+    import torch
+    pkg = slic_gpu
+    frames = [dict(width=1920, height=1080, S=16)] * 2 + [dict(width=333, height=211, S=12)]
+    imgs = [_cuda(synth.hd_image(3)), _cuda(synth.hd_image(4)),
+            _cuda(synth.voronoi_frame(333, 211, 15, 6.0, 9))]
+    ref = pkg.BatchSegmenter(frames, iterations=4)
+    ref.bind(imgs)
+    ref.set_tuning(1, 3)
+    want_l, want_c = [[t.clone() for t in x] for x in ref.segment()]
+    bs = pkg.BatchSegmenter(frames, iterations=4)
+    bs.bind(imgs)
+    for cps in (0, 1, 2):
+        bs.set_tuning(cps, stages)
+        labels, centres = bs.segment()
+        bs.status()
+        for a, b in zip(labels, want_l):
+            assert torch.equal(a, b)
+        for a, b in zip(centres, want_c):
+            assert torch.equal(a, b)
+    for bad in (2, 5):
+        with pytest.raises(pkg.SlicError):
+            bs.set_tuning(0, bad)
 
 
 def test_batch_errors(slic_gpu):
@@ -116,3 +144,16 @@ def test_batch_errors(slic_gpu):
         pkg.slic_batch_segment(b)
     assert ei.value.status == _binding.SLIC_ERR_STATE
     pkg.slic_batch_destroy(b)
+
+
+def test_profile_timers_outside_capture(slic_gpu):
+    """Per-launch timers work on a plain stream as well as under capture."""
+    pkg = slic_gpu
+    frames = [dict(width=640, height=480, S=16)] * 2
+    bs = pkg.BatchSegmenter(frames, iterations=3)
+    bs.bind([_cuda(synth.voronoi_frame(640, 480, 30, 6.0, s)) for s in (1, 2)])
+    pkg.slic_batch_profile_enable(bs.handle, True)
+    bs.segment()
+    times = pkg.slic_batch_profile_times(bs.handle)
+    assert len(times) == 4 and all(t > 0 for t in times)
+    bs.status()

@@ -262,3 +262,13 @@ def test_init_centres_override(slic_gpu):
     ref = oracle.slic(img, K=300, m=10, iterations=0, init_centres=ref1["centres"].astype(np.float32).astype(float))
     assert np.mean(_np(labels) == ref["labels"]) >= 0.999
     np.testing.assert_array_equal(_np(centres), ref1["centres"].astype(np.float32))
+
+
+def test_profile_timers_single_frame(slic_gpu):
+    """Assignment timers on a plain stream: one pair per assignment launch."""
+    img = synth.small_image(2)
+    seg = _seg(slic_gpu, 320, 240, K=300, iterations=4)
+    slic_gpu.slic_profile_enable(seg.handle, True)
+    seg.segment(_t(img))
+    ms, n = slic_gpu.slic_profile_read(seg.handle)
+    assert n == 5 and ms > 0
