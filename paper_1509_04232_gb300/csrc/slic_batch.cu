@@ -31,6 +31,7 @@ struct slic_batch_ctx {
     FrameArgs *d_frames = nullptr;    // device copy
     unsigned char *scratch = nullptr; // features, sums, connectivity labels of all frames
     int total_tiles = 0, total_centres = 0, total_rows = 0, max_w = 0, win_max = 0;
+    int total_units = 0;  // work units of the fused connectivity kernel
     long long total_pixels = 0;
     bool same = true;
     bool pipe = false;       // passes after the first use the pipelined kernel
@@ -243,6 +244,8 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
             a.box_h = std::min(spanh, a.ns_r) + 2;
         }
         b->max_w = std::max(b->max_w, p.width);
+        a.strip_base = b->total_units;
+        b->total_units += connectivity2_units(p.width, p.height, &a.strips_x);
         b->same = b->same && (S % kPPT) == 0;
         b->total_pixels += (long long)p.width * p.height;
         off_feat[f] = bytes;
@@ -331,6 +334,11 @@ slic_status slic_batch_set_buffers(slic_batch b, const uint8_t *const *d_images,
         a.init = d_init ? d_init[f] : nullptr;
         a.rgb_vec = ((a.W & 3) == 0 && ((uintptr_t)a.rgb & 15) == 0) ? 1 : 0;
         a.labels_vec = ((a.W & 3) == 0 && ((uintptr_t)a.labels & 15) == 0) ? 1 : 0;
+        // The pipelined last pass writes lbl_tmp when the fused connectivity
+        // kernel follows (it reads lbl_tmp and writes the labels).
+        const bool fused = b->pipe && b->connectivity;
+        a.assign_out = fused ? a.lbl_tmp : a.labels;
+        a.assign_vec = fused ? ((a.W & 3) == 0 ? 1 : 0) : a.labels_vec;
     }
     // Synchronous upload: the table must not change under queued work.
     cudaError_t e = cudaDeviceSynchronize();
@@ -351,8 +359,16 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
     const int grid = grid_for(b, b->occupancy);
     const int grid_pipe = b->pipe ? grid_for(b, pipe_occ(b, b->stages)) : grid;
     const int pipe_per_sm = grid_pipe / std::max(1, b->sms);
-    cudaError_t e = launch_init_batch(b->d_frames, b->n, b->total_centres, s);
-    long long n_launch = 1;
+    // With the pipelined kernel every pass reads features: a conversion
+    // pre-pass writes them, and the first pass is pipelined as well.
+    cudaError_t e = cudaSuccess;
+    long long n_launch = 0;
+    if (b->pipe) {
+        e = launch_convert_batch(b->d_frames, b->n, b->total_rows, b->max_w, s);
+        ++n_launch;
+    }
+    if (e == cudaSuccess) e = launch_init_batch(b->d_frames, b->n, b->total_centres, s);
+    ++n_launch;
     for (int pass = 0; e == cudaSuccess && pass <= b->iterations; ++pass) {
         if (pass > 0) {
             e = launch_update_batch(b->d_frames, b->n, b->total_centres, s);
@@ -371,7 +387,7 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
                 e1 = b->events[b->ev_used++].second;
             }
             if (e != cudaSuccess) break;
-            if (pass > 0 && b->pipe)
+            if (b->pipe)
                 e = launch_assign_pipe(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == b->iterations,
                                        b->stages, pipe_per_sm, grid_pipe, b->d_err, s);
             else
@@ -382,9 +398,14 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
         }
     }
     if (e == cudaSuccess && b->connectivity) {
-        e = launch_connectivity_batch(b->d_frames, b->n, b->total_rows, b->max_w, 0, s);
-        if (e == cudaSuccess) e = launch_connectivity_batch(b->d_frames, b->n, b->total_rows, b->max_w, 1, s);
-        n_launch += 2;
+        if (b->pipe) {
+            e = launch_connectivity2_batch(b->d_frames, b->n, b->total_units, b->sms * 8, s);
+            n_launch += 1;
+        } else {
+            e = launch_connectivity_batch(b->d_frames, b->n, b->total_rows, b->max_w, 0, s);
+            if (e == cudaSuccess) e = launch_connectivity_batch(b->d_frames, b->n, b->total_rows, b->max_w, 1, s);
+            n_launch += 2;
+        }
     }
     if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     b->launches += n_launch;

@@ -101,6 +101,10 @@ struct FrameArgs {
     int centre_base;        // batch's concatenated lists (0 for a single
     int row_base;           // frame)
     int box_w, box_h;       // window box of the centre-table copies (cells)
+    int32_t *assign_out;    // labels of the pipelined last pass (lbl_tmp when the
+    int assign_vec;         // fused connectivity follows); 1: 4-pixel vector stores
+    int strips_x;           // fused connectivity: strips per row and first
+    int strip_base;         // work unit (strip x row segment) of this frame
 };
 
 // Shared memory for one assignment CTA whose tile spans at most win_n cells.
@@ -143,6 +147,9 @@ cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles
 // (2..4) stages.
 size_t assign_pipe_smem_bytes(int win_n, bool last, int nst);
 int assign_pipe_occupancy(bool same, int win_n, int nst);
+// Batched RGB -> features pre-pass (the pipelined path's first pass reads
+// the features it writes).
+cudaError_t launch_convert_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w, cudaStream_t s);
 cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cudaStream_t s);
 cudaError_t launch_accumulate_labels(const float *feat, int W, int H, int P, const int32_t *labels, int K,
                                      long long *acc, float fix_scale, cudaStream_t s);
@@ -151,6 +158,11 @@ cudaError_t launch_convert(const ConvConsts &cc, const uint8_t *rgb, int W, int 
 cudaError_t launch_connectivity(const int32_t *in, int32_t *out, int W, int H, cudaStream_t s);
 cudaError_t launch_connectivity_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w, int pass,
                                       cudaStream_t s);
+// Both connectivity passes in one launch (a warp streams down a 120-column
+// strip of a row segment): reads lbl_tmp, writes labels. Units of a frame
+// (strips x segments) and its strips per row:
+int connectivity2_units(int W, int H, int *strips_x);
+cudaError_t launch_connectivity2_batch(const FrameArgs *d_frames, int n, int total_units, int grid, cudaStream_t s);
 // Event record for the profiling timers, valid inside and outside stream capture.
 cudaError_t record_profile_event(cudaEvent_t ev, cudaStream_t s);
 

@@ -57,10 +57,10 @@ __device__ __forceinline__ int div_s(int x, unsigned s_mul, int S) {
 
 // Index of the frame whose [base, next base) range holds `idx` (frames are
 // sorted by base; base of frame 0 is 0).
-enum BaseField { kTileBase, kCentreBase, kRowBase };
+enum BaseField { kTileBase, kCentreBase, kRowBase, kStripBase };
 template <BaseField F>
 __device__ __forceinline__ int base_of(const FrameArgs &a) {
-    return F == kTileBase ? a.tile_base : F == kCentreBase ? a.centre_base : a.row_base;
+    return F == kTileBase ? a.tile_base : F == kCentreBase ? a.centre_base : F == kRowBase ? a.row_base : a.strip_base;
 }
 template <BaseField F>
 __device__ __forceinline__ int find_frame(const FrameArgs *frames, int n, int idx) {
@@ -740,9 +740,9 @@ __device__ __forceinline__ TileGeom tile_geom(const FrameArgs &a, int local) {
     g.box_w = a.box_w;
     g.w = a.w;
     g.fix_scale = a.fix_scale;
-    g.labels = a.labels;
+    g.labels = a.assign_out;
     g.acc = a.acc;
-    g.labels_vec = a.labels_vec;
+    g.labels_vec = a.assign_vec;
     g.pad = 0;
     const int ty = local / a.tiles_x, tx = local - ty * a.tiles_x;
     g.tx0 = tx * kTileW;
@@ -1250,6 +1250,60 @@ __global__ void k_convert(ConvConsts cc, const uint8_t *rgb, int W, int H, int C
     }
 }
 
+// Batched conversion pre-pass (Sec. 4's colour conversion): RGB -> planar
+// features of every frame, 4 pixels per thread; blockIdx.y strides over the
+// concatenated rows of all frames. Feature rows have a pitch P that is a
+// multiple of 4, so each plane takes one 16-byte store per thread.
+__global__ void __launch_bounds__(128) k_convert_batch(const FrameArgs *frames, int n, int total_rows) {
+    __shared__ float lut[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = g_lut[i];
+    __syncthreads();
+    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    for (int gr = blockIdx.y; gr < total_rows; gr += gridDim.y) {
+        const int f = find_frame<kRowBase>(frames, n, gr);
+        const FrameArgs &a = frames[f];
+        const int W = a.W, C = a.C;
+        if (x0 >= W) continue;
+        const int y = gr - a.row_base;
+        // Constants in registers: the feature stores below could alias the
+        // frame table as far as the compiler knows.
+        const ConvConsts cc = a.conv;
+        const bool rgb_vec = a.rgb_vec != 0;
+        float *const feat = a.feat;
+        const size_t plane = (size_t)a.H * a.P, off = (size_t)y * a.P + x0;
+        const uint8_t *p = a.rgb + ((size_t)y * W + x0) * C;
+        unsigned r[kPPT], g[kPPT], b[kPPT];
+        if (rgb_vec && C == 3) {
+            const uint32_t *q = reinterpret_cast<const uint32_t *>(p);
+            const uint32_t w0 = __ldg(q), w1 = __ldg(q + 1), w2 = __ldg(q + 2);
+            r[0] = w0 & 255; g[0] = (w0 >> 8) & 255; b[0] = (w0 >> 16) & 255; r[1] = w0 >> 24;
+            g[1] = w1 & 255; b[1] = (w1 >> 8) & 255; r[2] = (w1 >> 16) & 255; g[2] = w1 >> 24;
+            b[2] = w2 & 255; r[3] = (w2 >> 8) & 255; g[3] = (w2 >> 16) & 255; b[3] = w2 >> 24;
+        } else if (rgb_vec) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
+            const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) {
+                r[j] = w[j] & 255; g[j] = (w[j] >> 8) & 255; b[j] = (w[j] >> 16) & 255;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) {
+                const bool ok = x0 + j < W;
+                r[j] = ok ? p[j * C + 0] : 0;
+                g[j] = ok ? p[j * C + 1] : 0;
+                b[j] = ok ? p[j * C + 2] : 0;
+            }
+        }
+        float f0[kPPT], f1[kPPT], f2[kPPT];
+#pragma unroll
+        for (int j = 0; j < kPPT; ++j) convert_pixel(cc, r[j], g[j], b[j], lut, f0[j], f1[j], f2[j]);
+        *reinterpret_cast<float4 *>(feat + off) = make_float4(f0[0], f0[1], f0[2], f0[3]);
+        *reinterpret_cast<float4 *>(feat + plane + off) = make_float4(f1[0], f1[1], f1[2], f1[3]);
+        *reinterpret_cast<float4 *>(feat + 2 * plane + off) = make_float4(f2[0], f2[1], f2[2], f2[3]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Connectivity: one double-buffered pass, 4 pixels per thread.
 // ---------------------------------------------------------------------------
@@ -1341,6 +1395,131 @@ __global__ void k_connectivity_batch(const FrameArgs *frames, int n, int total_r
     }
 }
 
+// Both connectivity passes fused, streaming down vertical strips. A warp
+// holds 128 columns [sx - 4, sx + 124) of one strip (lane l: columns
+// sx - 4 + 4l .. +3) and walks down a segment of rows with a rolling window
+// of input rows and first-pass rows in registers (horizontal neighbours by
+// shuffles): input row q + 2 gives the first pass at row q + 1, which gives
+// the second pass at row q. Lanes 1..30 write columns [sx, sx + 120); the
+// two outer lanes only supply neighbours. Every pixel sees exactly the
+// inputs of the two separate passes, so the result equals theirs.
+namespace {
+constexpr int kConnOut = 120;   // output columns per strip
+constexpr int kConnSeg = 64;    // output rows per segment
+
+__device__ __forceinline__ int4 conn_load_row(const int32_t *in, int W, int H, int y, int x0, bool vec) {
+    int4 v = make_int4(-1, -1, -1, -1);
+    if (y < 0 || y >= H) return v;
+    const int32_t *row = in + (size_t)y * W;
+    if (vec && x0 >= 0 && x0 + 3 < W) return __ldg(reinterpret_cast<const int4 *>(row + x0));
+    v.x = (x0 >= 0 && x0 < W) ? __ldg(row + x0) : -1;
+    v.y = (x0 + 1 >= 0 && x0 + 1 < W) ? __ldg(row + x0 + 1) : -1;
+    v.z = (x0 + 2 >= 0 && x0 + 2 < W) ? __ldg(row + x0 + 2) : -1;
+    v.w = (x0 + 3 >= 0 && x0 + 3 < W) ? __ldg(row + x0 + 3) : -1;
+    return v;
+}
+
+// Majority among the valid neighbours (left, up, right, down), the first of
+// the largest count winning, for a pixel none of whose valid neighbours
+// carries its label. Invalid neighbours hold distinct negative sentinels, so
+// they never match a label or each other; their count is 0.
+__device__ __forceinline__ int32_t conn_majority(int32_t l, int32_t u, int32_t r, int32_t d, bool okl, bool oku,
+                                                 bool okr, bool okd) {
+    const int elu = l == u, elr = l == r, eld = l == d, eur = u == r, eud = u == d, erd = r == d;
+    const int cl = okl ? 1 + elu + elr + eld : 0;
+    const int cu = oku ? 1 + elu + eur + eud : 0;
+    const int cr = okr ? 1 + elr + eur + erd : 0;
+    const int cd = okd ? 1 + eld + eud + erd : 0;
+    int32_t best = l;
+    int bc = cl;
+    if (cu > bc) { best = u; bc = cu; }
+    if (cr > bc) { best = r; bc = cr; }
+    if (cd > bc) best = d;
+    return best;
+}
+
+// One pass of the majority rule at row y for the lane's 4 pixels, from the
+// rows above, at and below y (left/right neighbours across lanes). A pixel
+// keeps its label when a valid neighbour shares it (the common case, no
+// counting); the counting runs only when some pixel of the warp needs it.
+// okx: bit j = pixel j has a left neighbour, bit 4 + j = a right neighbour.
+__device__ __forceinline__ int4 conn_rule4(const int4 &up, const int4 &c, const int4 &dn, int H, int y,
+                                           unsigned okx) {
+    const int32_t left = __shfl_up_sync(0xffffffffu, c.w, 1), right = __shfl_down_sync(0xffffffffu, c.x, 1);
+    const bool oku = y > 0, okd = y < H - 1;
+    const int32_t cc[4] = {c.x, c.y, c.z, c.w};
+    const int32_t uu[4] = {oku ? up.x : -2, oku ? up.y : -2, oku ? up.z : -2, oku ? up.w : -2};
+    const int32_t dd[4] = {okd ? dn.x : -4, okd ? dn.y : -4, okd ? dn.z : -4, okd ? dn.w : -4};
+    int32_t ll[4], rr[4];
+    bool need[4];
+    bool any_need = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        ll[j] = ((okx >> j) & 1u) ? (j > 0 ? cc[j - 1] : left) : -1;
+        rr[j] = ((okx >> (4 + j)) & 1u) ? (j < 3 ? cc[j + 1] : right) : -3;
+        const bool anyok = ((okx >> j) & 1u) || ((okx >> (4 + j)) & 1u) || oku || okd;
+        need[j] = anyok && ll[j] != cc[j] && uu[j] != cc[j] && rr[j] != cc[j] && dd[j] != cc[j];
+        any_need |= need[j];
+    }
+    int32_t r[4] = {cc[0], cc[1], cc[2], cc[3]};
+    if (__any_sync(0xffffffffu, any_need)) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (need[j])
+                r[j] = conn_majority(ll[j], uu[j], rr[j], dd[j], (okx >> j) & 1u, oku, (okx >> (4 + j)) & 1u, okd);
+    }
+    return make_int4(r[0], r[1], r[2], r[3]);
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256, 4) k_connectivity2_batch(const FrameArgs *frames, int n, int total_units) {
+    const int lane = threadIdx.x & 31;
+    const int warps = blockDim.x >> 5;
+    for (int unit = blockIdx.x * warps + (threadIdx.x >> 5); unit < total_units; unit += gridDim.x * warps) {
+        const int f = find_frame<kStripBase>(frames, n, unit);
+        const FrameArgs &a = frames[f];
+        const int W = a.W, H = a.H;
+        const int local = unit - a.strip_base, seg = local / a.strips_x, strip = local - seg * a.strips_x;
+        const int sx = strip * kConnOut, x0 = sx - 4 + 4 * lane;
+        const int ry0 = seg * kConnSeg, ry1 = min(ry0 + kConnSeg, H);
+        const bool vec = (W & 3) == 0;
+        const int32_t *in = a.lbl_tmp;
+        unsigned okx = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            okx |= (x0 + j > 0 ? 1u << j : 0u) | (x0 + j < W - 1 ? 1u << (4 + j) : 0u);
+        // Input rows q .. q + 3 and first-pass rows q - 1, q.
+        int4 a_m2 = conn_load_row(in, W, H, ry0 - 2, x0, vec), a_m1 = conn_load_row(in, W, H, ry0 - 1, x0, vec);
+        int4 a0 = conn_load_row(in, W, H, ry0, x0, vec), a1 = conn_load_row(in, W, H, ry0 + 1, x0, vec);
+        int4 a2 = conn_load_row(in, W, H, ry0 + 2, x0, vec);
+        int4 l_m1 = conn_rule4(a_m2, a_m1, a0, H, ry0 - 1, okx);
+        int4 l0 = conn_rule4(a_m1, a0, a1, H, ry0, okx);
+        const bool writer = lane >= 1 && lane <= 30;
+        const bool out_vec = vec && a.labels_vec && x0 >= 0 && x0 + 3 < W;
+        for (int q = ry0; q < ry1; ++q) {
+            const int4 a3 = conn_load_row(in, W, H, q + 3, x0, vec);  // one row ahead of its use
+            const int4 l1 = conn_rule4(a0, a1, a2, H, q + 1, okx);
+            const int4 o = conn_rule4(l_m1, l0, l1, H, q, okx);
+            if (writer) {
+                int32_t *out = a.labels + (size_t)q * W;
+                if (out_vec) {
+                    *reinterpret_cast<int4 *>(out + x0) = o;
+                } else {
+                    const int32_t ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (x0 + j >= 0 && x0 + j < W) out[x0 + j] = ov[j];
+                }
+            }
+            l_m1 = l0;
+            l0 = l1;
+            a0 = a1;
+            a1 = a2;
+            a2 = a3;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
@@ -1370,6 +1549,27 @@ cudaError_t configure_kernels(size_t max_smem) {
 cudaError_t launch_init_from_rgb(const FrameArgs &a, cudaStream_t s) {
     const int K = a.ns_c * a.ns_r;
     k_init_rgb<<<(K + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w, cudaStream_t s) {
+    const int threads = 128;
+    const dim3 grid((unsigned)((max_w + 4 * threads - 1) / (4 * threads)), (unsigned)std::min(total_rows, 4096));
+    k_convert_batch<<<grid, threads, 0, s>>>(d_frames, n, total_rows);
+    return cudaGetLastError();
+}
+
+int connectivity2_units(int W, int H, int *strips_x) {
+    *strips_x = (W + kConnOut - 1) / kConnOut;
+    return *strips_x * ((H + kConnSeg - 1) / kConnSeg);
+}
+
+cudaError_t launch_connectivity2_batch(const FrameArgs *d_frames, int n, int total_units, int grid, cudaStream_t s) {
+    const int per_block = 8;  // warps per 256-thread block, one unit each
+    const int need = (total_units + per_block - 1) / per_block;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    k_connectivity2_batch<<<grid, 32 * per_block, 0, s>>>(d_frames, n, total_units);
     return cudaGetLastError();
 }
 

@@ -66,7 +66,11 @@ def test_batch_repeatable_and_launch_count(slic_gpu):
     n0 = bs.info[1]
     l2 = bs.segment()[0]
     torch.cuda.synchronize()
-    assert bs.info[1] - n0 == 2 * 4 + 4      # independent of the number of frames
+    # conversion pre-pass, init, 5 assignments, 4 updates and one fused
+    # launch of both connectivity passes (pipelined kernel in use);
+    # independent of the number of frames
+    assert bs.info[3] in (3, 4)
+    assert bs.info[1] - n0 == 2 * 4 + 4
     for a, b in zip(l1, l2):
         assert torch.equal(a, b)
 
