@@ -768,11 +768,14 @@ __device__ __forceinline__ void issue_tile(const FrameArgs &a, const TileGeom &g
 }
 
 // Add tile j's private sums (all warps' copies of accumulator set j % 3) to
-// the frame's global sums and clear them; warp w takes items w, w + 8, ...
-// of the window's (cell, word) items. Waits until every warp has filled the
-// set, and reports the set free afterwards. False when the wait timed out.
+// the frame's global sums and clear them. One warp per tile does it (warp
+// j % 8, so the duty rotates), a lane per window cell reading the cell's
+// four words of every copy as one 16-byte load. The flushing warp waits
+// until every warp has filled the set and reports it free afterwards; the
+// others return at once. False when the wait timed out.
 __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, unsigned *wacc0, size_t acc_words, int win_max,
                                            uint64_t *acc_done, uint64_t *acc_free, int j, int warp, int lane) {
+    if (warp != (j & (kWarps - 1))) return true;
     const int set = j % kAccSets;
     if (!__all_sync(0xffffffffu, mbar_wait(&acc_done[set], (j / kAccSets) & 1))) return false;
     const TileGeom &g = hdr[j % kHdrSlots];
@@ -781,36 +784,33 @@ __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, unsigned *wacc0,
     const unsigned wnx_mul = g.wnx_mul;
     long long *const acc = g.acc;
     unsigned *const ws = wacc0 + (size_t)set * acc_words;
-    const int n_items = wnx * wny * 4;
-    for (int i = warp + kWarps * lane; i < n_items; i += kWarps * 32) {
-        const int cell = i >> 2, c = i & 3;
+    const int n_cells = wnx * wny;
+    for (int cell = lane; cell < n_cells; cell += 32) {
         const int qy = (int)__umulhi((unsigned)cell, wnx_mul), qx = cell - qy * wnx;
-        const int idx = (qy * bw + qx) * 4 + c;
-        unsigned long long *gs =
-            reinterpret_cast<unsigned long long *>(acc) + ((size_t)(wy0 + qy) * ns_c + wx0 + qx) * 6;
-        if (c < 3) {
-            long long t = 0;
+        const int idx = (qy * bw + qx) * 4;
+        long long l = 0, a = 0, b = 0;
+        unsigned xs = 0, ys = 0, n = 0;
 #pragma unroll
-            for (int q = 0; q < kWarps; ++q) {
-                t += (int)ws[(size_t)q * win_max * 4 + idx];
-                ws[(size_t)q * win_max * 4 + idx] = 0u;
-            }
-            if (t != 0) atomicAdd(&gs[c], (unsigned long long)t);
-        } else {
-            long long xs = 0, ys = 0, n = 0;
-#pragma unroll
-            for (int q = 0; q < kWarps; ++q) {
-                const unsigned pk = ws[(size_t)q * win_max * 4 + idx];
-                ws[(size_t)q * win_max * 4 + idx] = 0u;
-                xs += pk & 0xFFFu;
-                ys += (pk >> 12) & 0xFFFu;
-                n += pk >> 24;
-            }
-            if (n != 0) {
-                atomicAdd(&gs[3], (unsigned long long)(xs + n * tx0));
-                atomicAdd(&gs[4], (unsigned long long)(ys + n * ty0));
-                atomicAdd(&gs[5], (unsigned long long)n);
-            }
+        for (int q = 0; q < kWarps; ++q) {
+            uint4 *p = reinterpret_cast<uint4 *>(ws + (size_t)q * win_max * 4 + idx);
+            const uint4 v = *p;
+            *p = make_uint4(0u, 0u, 0u, 0u);
+            l += (int)v.x;
+            a += (int)v.y;
+            b += (int)v.z;
+            xs += v.w & 0xFFFu;
+            ys += (v.w >> 12) & 0xFFFu;
+            n += v.w >> 24;
+        }
+        if (n != 0) {
+            unsigned long long *gs =
+                reinterpret_cast<unsigned long long *>(acc) + ((size_t)(wy0 + qy) * ns_c + wx0 + qx) * 6;
+            atomicAdd(&gs[0], (unsigned long long)l);
+            atomicAdd(&gs[1], (unsigned long long)a);
+            atomicAdd(&gs[2], (unsigned long long)b);
+            atomicAdd(&gs[3], (unsigned long long)xs + (unsigned long long)n * tx0);
+            atomicAdd(&gs[4], (unsigned long long)ys + (unsigned long long)n * ty0);
+            atomicAdd(&gs[5], (unsigned long long)n);
         }
     }
     __syncwarp();
@@ -843,7 +843,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)nst * stage_bytes + kAccSets * acc_words * 4);
     uint64_t *empty = full + kMaxStages;       // stage released by every warp (count kWarps)
     uint64_t *acc_done = empty + kMaxStages;   // accumulator set filled by every warp (count kWarps)
-    uint64_t *acc_free = acc_done + kAccSets;  // accumulator set flushed and cleared (count kWarps)
+    uint64_t *acc_free = acc_done + kAccSets;  // accumulator set flushed and cleared (count 1)
     TileGeom *hdr = reinterpret_cast<TileGeom *>(acc_free + kAccSets);  // ring of kHdrSlots tile headers
     int *flags = reinterpret_cast<int *>(hdr + kHdrSlots);              // [0] abort, [1] last tile issued
     volatile int *abort_flag = flags;
@@ -856,7 +856,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
         }
         for (int q = 0; q < kAccSets; ++q) {
             mbar_init(&acc_done[q], kWarps);
-            mbar_init(&acc_free[q], kWarps);
+            mbar_init(&acc_free[q], 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         flags[0] = 0;
