@@ -9,11 +9,12 @@
 namespace slicgb {
 
 // Fixed-point scale for the centre-update sums: CIELAB and XYZ features
-// (|f| < 128) are rounded to multiples of 2^-16 before summation, RGB
+// (|f| < 128) are rounded to multiples of 2^-15 before summation, RGB
 // features are integers already (scale 1). Every partial sum is then an
 // exact integer, so the result does not depend on summation order, tiling
-// or batching.
-constexpr float kFixScaleFrac = 65536.0f;
+// or batching. |f| * 2^15 < 2^22 lets the pipelined kernel round on the FMA
+// pipe (fix_round); a centre moves by at most 2^-16 from the exact mean.
+constexpr float kFixScaleFrac = 32768.0f;
 
 // Assignment tile: 32 x 32 pixels, 256 threads, 4 horizontally adjacent
 // pixels per thread.
@@ -39,8 +40,19 @@ struct ConvConsts {
 };
 
 #ifdef __CUDACC__
+// Cube root of t > 0 from the identity t^(1/3) = 2^(log2(t) / 3), with the
+// hardware base-2 logarithm and exponential approximations (relative error
+// a few 1e-7 over CIELAB's range t in (216/24389, 1.1]).
+static __device__ __forceinline__ float cbrt_exp2(float t) {
+    float l, r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(t));
+    l *= (1.0f / 3.0f);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(l));
+    return r;
+}
+
 static __device__ __forceinline__ float lab_f(const ConvConsts &cc, float t) {
-    return t > cc.eps ? cbrtf(t) : fmaf(cc.k_slope, t, cc.k_offset);
+    return t > cc.eps ? cbrt_exp2(t) : fmaf(cc.k_slope, t, cc.k_offset);
 }
 
 // Sec. 3 "Image space conversion" for one pixel. `lut` is the sRGB

@@ -658,6 +658,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
     return false;
 }
 
+// round(x * fs) (nearest, ties to even) as a two's-complement word, on the
+// FMA pipe: with M = 1.5 * 2^23, x * fs + M lies in [2^23, 2^24) where the
+// float spacing is 1, so the one rounding of the fused multiply-add is the
+// rounding to an integer and the low mantissa bits are that integer + 2^22.
+// Exact for |x * fs| < 2^22 (features below 128 at the 2^15 colour scale,
+// 8-bit values at scale 1), and equal to __float2int_rn(x * fs) there since
+// fs is a power of two.
+__device__ __forceinline__ unsigned fix_round(float x, float fs) {
+    return (unsigned)(__float_as_int(fmaf(x, fs, 12582912.0f)) - 0x4B400000);
+}
+
 // Paired FP32 arithmetic: a 64-bit operand holds two floats (low, high);
 // each element is rounded exactly as the scalar instruction would be.
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
@@ -967,7 +978,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
                 const unsigned long long l01 = pack2(f0[0], f0[1]), l23 = pack2(f0[2], f0[3]);
                 const unsigned long long a01 = pack2(f1[0], f1[1]), a23 = pack2(f1[2], f1[3]);
                 const unsigned long long b01 = pack2(f2[0], f2[1]), b23 = pack2(f2[2], f2[3]);
-                const unsigned long long x01 = pack2((float)x, (float)(x + 1)), x23 = pack2((float)(x + 2), (float)(x + 3));
+                const float fx = (float)x;  // x + j exactly (x < 2^24)
+                const unsigned long long x01 = pack2(fx, fx + 1.0f), x23 = pack2(fx + 2.0f, fx + 3.0f);
                 const int own = rowoff + cx[0];
 #pragma unroll
                 for (int t = 0; t < 9; ++t) {
@@ -1028,9 +1040,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
             unsigned v[kPPT][4];
 #pragma unroll
             for (int j = 0; j < kPPT; ++j) {
-                v[j][0] = (unsigned)__float2int_rn(f0[j] * fs);
-                v[j][1] = (unsigned)__float2int_rn(f1[j] * fs);
-                v[j][2] = (unsigned)__float2int_rn(f2[j] * fs);
+                v[j][0] = fix_round(f0[j], fs);
+                v[j][1] = fix_round(f1[j], fs);
+                v[j][2] = fix_round(f2[j], fs);
                 v[j][3] = (unsigned)(lx + j) + ((unsigned)ly << 12) + (1u << 24);
             }
 #pragma unroll
@@ -1403,72 +1415,85 @@ __global__ void k_connectivity_batch(const FrameArgs *frames, int n, int total_r
 // the second pass at row q. Lanes 1..30 write columns [sx, sx + 120); the
 // two outer lanes only supply neighbours. Every pixel sees exactly the
 // inputs of the two separate passes, so the result equals theirs.
+//
+// Positions outside the image hold negative sentinels, one per side (left
+// -1, above -2, right -3, below -4): a sentinel never equals a label or
+// another side's sentinel, which is all the rule needs to skip missing
+// neighbours.
 namespace {
 constexpr int kConnOut = 120;   // output columns per strip
 constexpr int kConnSeg = 64;    // output rows per segment
 
+__device__ __forceinline__ int32_t conn_col_sentinel(int x, int W, int32_t v) {
+    return x < 0 ? -1 : (x >= W ? -3 : v);
+}
+
 __device__ __forceinline__ int4 conn_load_row(const int32_t *in, int W, int H, int y, int x0, bool vec) {
-    int4 v = make_int4(-1, -1, -1, -1);
-    if (y < 0 || y >= H) return v;
+    if (y < 0) return make_int4(-2, -2, -2, -2);
+    if (y >= H) return make_int4(-4, -4, -4, -4);
     const int32_t *row = in + (size_t)y * W;
     if (vec && x0 >= 0 && x0 + 3 < W) return __ldg(reinterpret_cast<const int4 *>(row + x0));
-    v.x = (x0 >= 0 && x0 < W) ? __ldg(row + x0) : -1;
-    v.y = (x0 + 1 >= 0 && x0 + 1 < W) ? __ldg(row + x0 + 1) : -1;
-    v.z = (x0 + 2 >= 0 && x0 + 2 < W) ? __ldg(row + x0 + 2) : -1;
-    v.w = (x0 + 3 >= 0 && x0 + 3 < W) ? __ldg(row + x0 + 3) : -1;
+    int4 v;
+    v.x = (x0 >= 0 && x0 < W) ? __ldg(row + x0) : conn_col_sentinel(x0, W, 0);
+    v.y = (x0 + 1 >= 0 && x0 + 1 < W) ? __ldg(row + x0 + 1) : conn_col_sentinel(x0 + 1, W, 0);
+    v.z = (x0 + 2 >= 0 && x0 + 2 < W) ? __ldg(row + x0 + 2) : conn_col_sentinel(x0 + 2, W, 0);
+    v.w = (x0 + 3 >= 0 && x0 + 3 < W) ? __ldg(row + x0 + 3) : conn_col_sentinel(x0 + 3, W, 0);
     return v;
 }
 
-// Majority among the valid neighbours (left, up, right, down), the first of
-// the largest count winning, for a pixel none of whose valid neighbours
-// carries its label. Invalid neighbours hold distinct negative sentinels, so
-// they never match a label or each other; their count is 0.
-__device__ __forceinline__ int32_t conn_majority(int32_t l, int32_t u, int32_t r, int32_t d, bool okl, bool oku,
-                                                 bool okr, bool okd) {
-    const int elu = l == u, elr = l == r, eld = l == d, eur = u == r, eud = u == d, erd = r == d;
-    const int cl = okl ? 1 + elu + elr + eld : 0;
-    const int cu = oku ? 1 + elu + eur + eud : 0;
-    const int cr = okr ? 1 + elr + eur + erd : 0;
-    const int cd = okd ? 1 + eld + eud + erd : 0;
-    int32_t best = l;
-    int bc = cl;
-    if (cu > bc) { best = u; bc = cu; }
-    if (cr > bc) { best = r; bc = cr; }
-    if (cd > bc) best = d;
-    return best;
+// Sentinels back into a first-pass row (its values outside the image are
+// meaningless): the whole row when y is outside, else the lane's columns
+// outside (edge lanes only).
+__device__ __forceinline__ int4 conn_mask_row(int4 v, int W, int H, int y, int x0, bool edge_lane) {
+    if (y < 0) return make_int4(-2, -2, -2, -2);
+    if (y >= H) return make_int4(-4, -4, -4, -4);
+    if (edge_lane) {
+        v.x = conn_col_sentinel(x0, W, v.x);
+        v.y = conn_col_sentinel(x0 + 1, W, v.y);
+        v.z = conn_col_sentinel(x0 + 2, W, v.z);
+        v.w = conn_col_sentinel(x0 + 3, W, v.w);
+    }
+    return v;
+}
+
+// The rule for a pixel none of whose neighbours (left, up, right, down;
+// sentinels for missing ones) carries its label: the neighbours' majority,
+// the first in that order among the largest counts. With at most four
+// values, the left one wins whenever it matches another; else the upper one
+// when it matches the right or lower one; else the right one when it matches
+// the lower one; else all are distinct and the first valid one wins. No
+// valid neighbour at all keeps the label.
+__device__ __forceinline__ int32_t conn_majority(int32_t own, int32_t l, int32_t u, int32_t r, int32_t d) {
+    const bool el = l == u || l == r || l == d, eu = u == r || u == d, er = r == d;
+    const int32_t fv = l >= 0 ? l : (u >= 0 ? u : (r >= 0 ? r : d));
+    const int32_t res = el ? l : (eu ? u : (er ? r : fv));
+    return res >= 0 ? res : own;
 }
 
 // One pass of the majority rule at row y for the lane's 4 pixels, from the
 // rows above, at and below y (left/right neighbours across lanes). A pixel
-// keeps its label when a valid neighbour shares it (the common case, no
-// counting); the counting runs only when some pixel of the warp needs it.
-// okx: bit j = pixel j has a left neighbour, bit 4 + j = a right neighbour.
-__device__ __forceinline__ int4 conn_rule4(const int4 &up, const int4 &c, const int4 &dn, int H, int y,
-                                           unsigned okx) {
+// keeps its label when a neighbour shares it (the common case); the
+// majority is evaluated only when some pixel of the warp needs it.
+__device__ __forceinline__ int4 conn_rule4(const int4 &up, const int4 &c, const int4 &dn) {
     const int32_t left = __shfl_up_sync(0xffffffffu, c.w, 1), right = __shfl_down_sync(0xffffffffu, c.x, 1);
-    const bool oku = y > 0, okd = y < H - 1;
-    const int32_t cc[4] = {c.x, c.y, c.z, c.w};
-    const int32_t uu[4] = {oku ? up.x : -2, oku ? up.y : -2, oku ? up.z : -2, oku ? up.w : -2};
-    const int32_t dd[4] = {okd ? dn.x : -4, okd ? dn.y : -4, okd ? dn.z : -4, okd ? dn.w : -4};
-    int32_t ll[4], rr[4];
+    const int32_t cc[4] = {c.x, c.y, c.z, c.w}, uu[4] = {up.x, up.y, up.z, up.w}, dd[4] = {dn.x, dn.y, dn.z, dn.w};
     bool need[4];
     bool any_need = false;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        ll[j] = ((okx >> j) & 1u) ? (j > 0 ? cc[j - 1] : left) : -1;
-        rr[j] = ((okx >> (4 + j)) & 1u) ? (j < 3 ? cc[j + 1] : right) : -3;
-        const bool anyok = ((okx >> j) & 1u) || ((okx >> (4 + j)) & 1u) || oku || okd;
-        need[j] = anyok && ll[j] != cc[j] && uu[j] != cc[j] && rr[j] != cc[j] && dd[j] != cc[j];
+        const int32_t l = j > 0 ? cc[j - 1] : left, r = j < 3 ? cc[j + 1] : right;
+        need[j] = l != cc[j] && uu[j] != cc[j] && r != cc[j] && dd[j] != cc[j];
         any_need |= need[j];
     }
-    int32_t r[4] = {cc[0], cc[1], cc[2], cc[3]};
+    int32_t res[4] = {cc[0], cc[1], cc[2], cc[3]};
     if (__any_sync(0xffffffffu, any_need)) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (need[j])
-                r[j] = conn_majority(ll[j], uu[j], rr[j], dd[j], (okx >> j) & 1u, oku, (okx >> (4 + j)) & 1u, okd);
+        for (int j = 0; j < 4; ++j) {
+            const int32_t l = j > 0 ? cc[j - 1] : left, r = j < 3 ? cc[j + 1] : right;
+            if (need[j]) res[j] = conn_majority(cc[j], l, uu[j], r, dd[j]);
+        }
     }
-    return make_int4(r[0], r[1], r[2], r[3]);
+    return make_int4(res[0], res[1], res[2], res[3]);
 }
 }  // namespace
 
@@ -1484,22 +1509,19 @@ __global__ void __launch_bounds__(256, 4) k_connectivity2_batch(const FrameArgs 
         const int ry0 = seg * kConnSeg, ry1 = min(ry0 + kConnSeg, H);
         const bool vec = (W & 3) == 0;
         const int32_t *in = a.lbl_tmp;
-        unsigned okx = 0u;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            okx |= (x0 + j > 0 ? 1u << j : 0u) | (x0 + j < W - 1 ? 1u << (4 + j) : 0u);
-        // Input rows q .. q + 3 and first-pass rows q - 1, q.
+        const bool edge_lane = x0 < 0 || x0 + 3 >= W;
+        // Input rows q .. q + 2 (q + 3 in flight) and first-pass rows q - 1, q.
         int4 a_m2 = conn_load_row(in, W, H, ry0 - 2, x0, vec), a_m1 = conn_load_row(in, W, H, ry0 - 1, x0, vec);
         int4 a0 = conn_load_row(in, W, H, ry0, x0, vec), a1 = conn_load_row(in, W, H, ry0 + 1, x0, vec);
         int4 a2 = conn_load_row(in, W, H, ry0 + 2, x0, vec);
-        int4 l_m1 = conn_rule4(a_m2, a_m1, a0, H, ry0 - 1, okx);
-        int4 l0 = conn_rule4(a_m1, a0, a1, H, ry0, okx);
+        int4 l_m1 = conn_mask_row(conn_rule4(a_m2, a_m1, a0), W, H, ry0 - 1, x0, edge_lane);
+        int4 l0 = conn_mask_row(conn_rule4(a_m1, a0, a1), W, H, ry0, x0, edge_lane);
         const bool writer = lane >= 1 && lane <= 30;
         const bool out_vec = vec && a.labels_vec && x0 >= 0 && x0 + 3 < W;
         for (int q = ry0; q < ry1; ++q) {
             const int4 a3 = conn_load_row(in, W, H, q + 3, x0, vec);  // one row ahead of its use
-            const int4 l1 = conn_rule4(a0, a1, a2, H, q + 1, okx);
-            const int4 o = conn_rule4(l_m1, l0, l1, H, q, okx);
+            const int4 l1 = conn_mask_row(conn_rule4(a0, a1, a2), W, H, q + 1, x0, edge_lane);
+            const int4 o = conn_rule4(l_m1, l0, l1);
             if (writer) {
                 int32_t *out = a.labels + (size_t)q * W;
                 if (out_vec) {
