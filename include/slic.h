@@ -170,6 +170,19 @@ slic_status slic_batch_set_buffers(slic_batch b, const uint8_t *const *d_images,
    SLIC_ERR_STATE before slic_batch_set_buffers. */
 slic_status slic_batch_segment(slic_batch b, void *stream);
 
+/* End to end with host buffers, on `stream`: copy each frame's image from
+   host_images[f] (uint8 [H][W][C]) into the bound device image, segment as
+   slic_batch_segment, then copy the bound labels and centres into
+   host_labels[f] (int32 [H][W]) and host_centres[f] (float [K_eff_f][6]).
+   host_labels or host_centres may be NULL to skip those copies. One
+   cudaMemcpyAsync per buffer; host memory must be page-locked for the copies
+   to overlap other work. Returns once everything is enqueued: synchronise the
+   stream before reading the outputs. Two batches bound to different device
+   buffers, driven on two streams, overlap one batch's copies with the
+   other's kernels. SLIC_ERR_STATE before slic_batch_set_buffers. */
+slic_status slic_batch_segment_host(slic_batch b, const uint8_t *const *host_images, int32_t *const *host_labels,
+                                    float *const *host_centres, void *stream);
+
 /* Launch shape of the persistent assignment kernels: resident CTAs per SM
    (0 = as many as fit, capped by each kernel's occupancy) and the number of
    TMA pipeline stages of the passes after the first (3 or 4; 0 keeps the

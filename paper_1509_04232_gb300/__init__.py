@@ -12,8 +12,8 @@ from __future__ import annotations
 from ._binding import (SLIC_CIELAB, SLIC_RGB, SLIC_XYZ, SlicError, library_path, slic_assign,  # noqa: F401
                        slic_batch_autotune, slic_batch_create, slic_batch_destroy, slic_batch_info,
                        slic_batch_last_error, slic_batch_profile_enable, slic_batch_profile_read,
-                       slic_batch_profile_times, slic_batch_segment, slic_batch_set_buffers, slic_batch_set_tuning,
-                       slic_batch_status,
+                       slic_batch_profile_times, slic_batch_segment, slic_batch_segment_host,
+                       slic_batch_set_buffers, slic_batch_set_tuning, slic_batch_status,
                        slic_connectivity_pass, slic_convert, slic_create, slic_destroy, slic_grid,
                        slic_init_centres, slic_last_error, slic_launch_count, slic_params,
                        slic_profile_enable, slic_profile_read, slic_segment, slic_segment_noalloc,
@@ -145,6 +145,15 @@ class BatchSegmenter:
     def segment(self, stream=None):
         slic_batch_segment(self.handle, _stream_handle(stream))
         return self.labels, self.centres
+
+    def segment_host(self, host_images, host_labels=None, host_centres=None, stream=None):
+        """End to end with host tensors (page-locked CPU tensors, one per
+        frame): images in, labels [H, W] int32 and centres [K_eff, 6] float32
+        out (either list may be None). Enqueued on `stream`; synchronise it
+        before reading the outputs."""
+        ptrs = lambda ts: [t.data_ptr() for t in ts] if ts is not None else None  # noqa: E731
+        slic_batch_segment_host(self.handle, ptrs(host_images), ptrs(host_labels), ptrs(host_centres),
+                                _stream_handle(stream))
 
     def autotune(self, cache_path=None, stream=None):
         """Time the launch shapes that fit; -> (ctas_per_sm, stages) chosen."""

@@ -56,6 +56,7 @@ _SIGNATURES = {
     "slic_batch_create": [ctypes.POINTER(slic_params), _I, ctypes.POINTER(_P)],
     "slic_batch_set_buffers": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)],
     "slic_batch_segment": [_P, _P],
+    "slic_batch_segment_host": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
     "slic_batch_set_tuning": [_P, _I, _I],
     "slic_batch_autotune": [_P, ctypes.c_char_p, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "slic_batch_info": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
@@ -210,6 +211,17 @@ def slic_batch_set_buffers(b: int, d_images, d_labels, d_centres, d_init=None) -
 
 def slic_batch_segment(b: int, stream: int = 0) -> None:
     _bcheck(lib().slic_batch_segment(b, stream or None), b)
+
+
+def slic_batch_segment_host(b: int, host_images, host_labels=None, host_centres=None, stream: int = 0) -> None:
+    """host_* are sequences of host addresses (page-locked memory), one per frame."""
+    n = len(host_images)
+
+    def arr(ptrs):
+        return (_P * n)(*[p or None for p in ptrs]) if ptrs is not None else None
+
+    _bcheck(lib().slic_batch_segment_host(b, arr(host_images), arr(host_labels), arr(host_centres),
+                                          stream or None), b)
 
 
 def slic_batch_set_tuning(b: int, ctas_per_sm: int, stages: int = 0) -> None:

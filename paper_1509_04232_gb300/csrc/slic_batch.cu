@@ -412,6 +412,34 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
     return SLIC_OK;
 }
 
+slic_status slic_batch_segment_host(slic_batch b, const uint8_t *const *host_images, int32_t *const *host_labels,
+                                    float *const *host_centres, void *stream) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (!host_images) return bfail(b, SLIC_ERR_INVALID, "NULL host image array");
+    if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int f = 0; f < b->n; ++f) {
+        const FrameArgs &a = b->frames[f];
+        if (!host_images[f]) return bfail(b, SLIC_ERR_INVALID, "NULL host image for frame " + std::to_string(f));
+        const cudaError_t e = cudaMemcpyAsync(const_cast<uint8_t *>(a.rgb), host_images[f],
+                                              (size_t)a.W * a.H * a.C, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("image copy: ") + cudaGetErrorString(e));
+    }
+    const slic_status st = slic_batch_segment(b, stream);
+    if (st != SLIC_OK) return st;
+    for (int f = 0; f < b->n; ++f) {
+        const FrameArgs &a = b->frames[f];
+        cudaError_t e = cudaSuccess;
+        if (host_labels && host_labels[f])
+            e = cudaMemcpyAsync(host_labels[f], a.labels, sizeof(int32_t) * a.W * a.H, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && host_centres && host_centres[f])
+            e = cudaMemcpyAsync(host_centres[f], a.centres_out, sizeof(float) * 6 * (size_t)a.ns_c * a.ns_r,
+                                cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
+    }
+    return SLIC_OK;
+}
+
 slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (ctas_per_sm < 0) return bfail(b, SLIC_ERR_INVALID, "ctas_per_sm must be >= 0");

@@ -161,3 +161,30 @@ def test_profile_timers_outside_capture(slic_gpu):
     times = pkg.slic_batch_profile_times(bs.handle)
     assert len(times) == 4 and all(t > 0 for t in times)
     bs.status()
+
+
+def test_segment_host_matches_device_path(slic_gpu):
+    """Host buffers in and out (page-locked) give the device path's results."""
+    import torch
+    pkg = slic_gpu
+    frames = [dict(width=320, height=240, S=16), dict(width=333, height=211, S=12)]
+    imgs = [synth.small_image(3), synth.voronoi_frame(333, 211, 15, 6.0, 4)]
+    ref = pkg.BatchSegmenter(frames, iterations=3)
+    ref.bind([_cuda(i) for i in imgs])
+    want_l, want_c = [[t.cpu() for t in x] for x in ref.segment()]
+    bs = pkg.BatchSegmenter(frames, iterations=3)
+    bs.bind([torch.empty(i.shape, dtype=torch.uint8, device="cuda") for i in imgs])
+    h_img = [torch.from_numpy(np.ascontiguousarray(i)).pin_memory() for i in imgs]
+    h_lab = [torch.empty(t.shape, dtype=torch.int32).pin_memory() for t in want_l]
+    h_cen = [torch.empty(t.shape, dtype=torch.float32).pin_memory() for t in want_c]
+    stream = torch.cuda.Stream()
+    bs.segment_host(h_img, h_lab, h_cen, stream=stream)
+    stream.synchronize()
+    for a, b in zip(h_lab, want_l):
+        assert torch.equal(a, b)
+    for a, b in zip(h_cen, want_c):
+        assert torch.equal(a, b)
+    h_lab2 = [torch.zeros(t.shape, dtype=torch.int32).pin_memory() for t in want_l]
+    bs.segment_host(h_img, h_lab2, None, stream=stream)   # centres copy skipped
+    stream.synchronize()
+    assert torch.equal(h_lab2[0], want_l[0])
