@@ -33,7 +33,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 W, H, S, M, ITERS = 1920, 1080, 16, 10.0, 5
-METRIC = "1080p SLIC frames/s (S=16, m=10, 5 iterations, connectivity on)"
+METRIC = "1080p SLIC frames/s (batched+learned vs plain GPU) at \u226599% label agreement"
 UNIT = "frames/s"
 
 
@@ -328,8 +328,11 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{B} x 1920x1080 RGB frames per GPU per step (400 Voronoi regions, "
-                                   f"noise 6); S=16 (K_eff 8160), m=10, 5 iterations, CIELAB, connectivity",
+            "config": {"workload": f"plain SLIC throughput: {B} x 1920x1080 RGB frames per GPU per step (400 "
+                                   f"Voronoi regions, noise 6); S=16 (K_eff 8160), m=10, {ITERS} iterations, CIELAB, "
+                                   f"connectivity; agreement with 10 iterations and the learned warm start in "
+                                   f"'quality'",
+                       "iterations": ITERS,
                        "global_batch": world * B, "frames_per_gpu": B, "megapixels_per_s": value * N / 1e6,
                        "parallelism": f"replicas x{world} (frames sharded, no collective)",
                        "l2": "inputs larger than L2 (B x 6.2 MB RGB + B x 8.3 MB labels per step)",
@@ -356,6 +359,23 @@ def run_ours(args):
     return 0
 
 
+def _graph_ms(graph, stream, args, world, dev):
+    """Milliseconds per replay of a captured step: warm-up replays, then
+    `steps` replays between CUDA events on the replay stream."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
+
+
 def quality_and_learned(args, pkg, images, B, stream, world, dev):
     """Agreement of plain SLIC with n iterations and of the learned warm start
     with k iterations against the 10-iteration labels (first 8 frames), and
@@ -371,6 +391,18 @@ def quality_and_learned(args, pkg, images, B, stream, world, dev):
     for n in (0, 1, 2, 3, 5, 7, 9):
         lab, _ = ws.plain_segment(sub, n)
         plain[n] = round(ws.agreement(lab, ref), 5)
+    # The plain path at the iteration count that reaches >= 99 % agreement by
+    # definition (the 10-iteration reference itself), timed like `value`.
+    plain10 = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=10, device=dev)
+    plain10.bind([images[f] for f in range(B)])
+    with torch.cuda.stream(stream):
+        plain10.segment(stream)
+    torch.cuda.synchronize()
+    g10 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g10, stream=stream):
+        plain10.segment(stream)
+    plain10_fps = world * B / (_graph_ms(g10, stream, args, world, dev) / 1e3)
+    plain10.close()
     t0 = time.time()
     small = ws.WarmStartNet(256, 256, S, max_batch=64, seed=0, m=M)
     hist = ws.train(small, n_images=args.train_images, batch=64, epochs=args.train_epochs, lr=2e-3, log_every=50)
@@ -388,21 +420,12 @@ def quality_and_learned(args, pkg, images, B, stream, world, dev):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
             pipe.run(stream)
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                g.replay()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.steps):
-                g.replay()
-            e1.record(stream)
-        torch.cuda.synchronize()
-        ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
-        learned_fps[k] = world * B / (ms / 1e3)
+        learned_fps[k] = world * B / (_graph_ms(g, stream, args, world, dev) / 1e3)
     return {"reference": "plain SLIC, 10 iterations (same frames, connectivity on)", "frames": q,
             "plain_agreement_by_iterations": plain, "learned_agreement_by_iterations": learned,
+            "plain_frames_per_s_at_10_iterations": plain10_fps,
             "learned_frames_per_s_by_iterations": learned_fps,
+            "learned_reaches_99_percent": any(v >= 0.99 for v in learned.values()),
             "learned_training": {"images": args.train_images, "epochs": args.train_epochs, "seconds": train_s,
                                  "final_loss": hist[-1][1] if hist else None,
                                  "final_pixel_accuracy": hist[-1][2] if hist else None}}
@@ -411,7 +434,7 @@ def quality_and_learned(args, pkg, images, B, stream, world, dev):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--batch", type=int, default=32, help="1080p frames per GPU per step")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
