@@ -312,6 +312,11 @@ def run_ours(args):
     e2e_value = world * B / (e2e_ms / 1e3)
     bs2.close()
 
+    # --- the mixed-resolution batch (256 frames, four sizes, S and m mixed) ---
+    mixed = None
+    if rank == 0 and not args.no_mixed:
+        mixed = mixed_batch_throughput(args, pkg, stream, dev)
+
     # --- label agreement with the 10-iteration result and the learned path ---
     quality = None
     if not args.no_quality:
@@ -348,6 +353,7 @@ def run_ours(args):
                                  "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch}},
             "cpu_baseline": cpu,
             "quality": quality,
+            "mixed_batch": mixed,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clock_info,
@@ -357,6 +363,45 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def mixed_batch_throughput(args, pkg, stream, dev):
+    """The 256-frame mixed batch (64 each of 640x480, 1280x720, 1920x1080,
+    3840x2160; S in {8,16,32}, m in {5,10,20}; 5 iterations): one captured
+    graph per step, autotuned, inputs resident; rank 0 only (a context line,
+    not the headline)."""
+    import torch
+    from paper_1509_04232_gb300 import synth
+    specs = synth.mixed_batch_specs(256)
+    frames = [dict(width=w, height=h, S=s_, m=m_) for (w, h, s_, m_) in specs]
+    imgs = [torch.from_numpy(synth.mixed_batch_frame(f, w, h)).to(dev) for f, (w, h, _, _) in enumerate(specs)]
+    bs = pkg.BatchSegmenter(frames, iterations=ITERS, device=dev)
+    bs.bind(imgs)
+    ctas, stages = bs.autotune(os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl"), stream=stream)
+    with torch.cuda.stream(stream):
+        bs.segment(stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        bs.segment(stream)
+    steps = max(3, min(args.steps, 20))
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            g.replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    bs.status()
+    px = sum(w * h for (w, h, _, _) in specs)
+    bs.close()
+    return {"frames": len(specs), "megapixels": px / 1e6, "ms_per_step": ms, "frames_per_s": len(specs) / (ms / 1e3),
+            "megapixels_per_s": px / 1e6 / (ms / 1e3), "steps": steps, "ctas_per_sm": ctas, "pipeline_stages": stages,
+            "iterations": ITERS}
 
 
 def _graph_ms(graph, stream, args, world, dev):
@@ -443,6 +488,7 @@ def main(argv=None):
     ap.add_argument("--train-epochs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true", help="skip the agreement table and the learned path")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 256-frame mixed-resolution batch")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
