@@ -200,7 +200,7 @@ def run_ours(args):
     bs = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=ITERS, device=dev)
     bs.bind([images[f] for f in range(B)])
     tune_cache = os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl")
-    ctas_per_sm, stages = bs.autotune(tune_cache, stream=stream)
+    ctas_per_sm, stages, rows = bs.autotune(tune_cache, stream=stream)
 
     def step():
         bs.segment(stream=stream)
@@ -284,7 +284,7 @@ def run_ours(args):
     d2h = B * H * W * 4 + B * K_EFF * 6 * 4
     bs2 = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=ITERS, device=dev)
     bs2.bind([torch.empty_like(images[f]) for f in range(B)])
-    bs2.set_tuning(ctas_per_sm, stages)
+    bs2.set_tuning(ctas_per_sm, stages, rows)
     pair = [(bs, stream, host_labels, host_centres),
             (bs2, torch.cuda.Stream(device=dev), torch.empty_like(host_labels).pin_memory(),
              torch.empty_like(host_centres).pin_memory())]
@@ -342,9 +342,9 @@ def run_ours(args):
                        "parallelism": f"replicas x{world} (frames sharded, no collective)",
                        "l2": "inputs larger than L2 (B x 6.2 MB RGB + B x 8.3 MB labels per step)",
                        "graph": "one CUDA graph per step (one batched launch per stage)",
-                       "ctas_per_sm": ctas_per_sm, "pipeline_stages": stages},
-            "roofline": {"kernel": f"k_assign_pipe<0,1,{4 if ctas_per_sm >= 4 else 3}> (middle assignment pass, "
-                                   f"all frames)", "bound": "alu",
+                       "ctas_per_sm": ctas_per_sm, "pipeline_stages": stages, "row_groups_per_warp": rows},
+            "roofline": {"kernel": f"k_assign_pipe<0,1,{4 if (rows == 2 or ctas_per_sm >= 4) else 3},{rows}> "
+                                   f"(middle assignment pass, all frames)", "bound": "alu",
                          "unit": "Tsqrt/s", "achieved": achieved_tops, "peak": xu_peak, "frac": achieved_tops / xu_peak,
                          "peak_source": "16 MUFU lanes/clk/SM x 152 SMs x max SM clock (recipe unit counts)",
                          "traffic": traffic, "avg_launch_us": mid_ms * 1e3, "launches_timed": len(mid),
@@ -377,7 +377,7 @@ def mixed_batch_throughput(args, pkg, stream, dev):
     imgs = [torch.from_numpy(synth.mixed_batch_frame(f, w, h)).to(dev) for f, (w, h, _, _) in enumerate(specs)]
     bs = pkg.BatchSegmenter(frames, iterations=ITERS, device=dev)
     bs.bind(imgs)
-    ctas, stages = bs.autotune(os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl"), stream=stream)
+    ctas, stages, rows = bs.autotune(os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl"), stream=stream)
     with torch.cuda.stream(stream):
         bs.segment(stream)
     torch.cuda.synchronize()
@@ -401,6 +401,7 @@ def mixed_batch_throughput(args, pkg, stream, dev):
     bs.close()
     return {"frames": len(specs), "megapixels": px / 1e6, "ms_per_step": ms, "frames_per_s": len(specs) / (ms / 1e3),
             "megapixels_per_s": px / 1e6 / (ms / 1e3), "steps": steps, "ctas_per_sm": ctas, "pipeline_stages": stages,
+            "row_groups_per_warp": rows,
             "iterations": ITERS}
 
 

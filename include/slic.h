@@ -184,27 +184,30 @@ slic_status slic_batch_segment_host(slic_batch b, const uint8_t *const *host_ima
                                     float *const *host_centres, void *stream);
 
 /* Launch shape of the persistent assignment kernels: resident CTAs per SM
-   (0 = as many as fit, capped by each kernel's occupancy) and the number of
-   TMA pipeline stages of the passes after the first (3 or 4; 0 keeps the
-   current value, default 4 where it fits). SLIC_ERR_INVALID for other
-   values or stages that do not fit in shared memory. */
-slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages);
+   (0 = as many as fit, capped by each kernel's occupancy), the number of
+   TMA pipeline stages (3 or 4; 0 keeps the current value, default 4 where it
+   fits) and the row groups per warp (1: 256 threads, 4 pixels per thread;
+   2: 128 threads, 8 pixels per thread, only when every frame's S is a
+   multiple of 8; 0 keeps the current value, default 1). SLIC_ERR_INVALID
+   for other values or shapes that do not fit in shared memory. */
+slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages, int rows);
 
 /* Autotuner: time slic_batch_segment on the bound buffers for every launch
    shape that fits (3 timed runs each, CUDA events on `stream`; this waits
    for the device), keep the fastest, and append it to the JSON-lines file
    cache_path (may be NULL) under a key of GPU name, frame count,
    iterations and the distinct (width, height, S). When the key is already
-   in the file its entry is used without timing. The search covers CTAs
-   per SM x pipeline stages; the choice is returned in *ctas_per_sm and
-   *stages (either may be NULL). */
-slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm, int *stages);
+   in the file its entry is used without timing. The search covers row
+   groups per warp x pipeline stages x CTAs per SM; the choice is returned in
+   *ctas_per_sm, *stages and *rows (any may be NULL). */
+slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm, int *stages,
+                               int *rows);
 
 /* Pixels of all frames, kernel launches enqueued so far, CTAs per SM
-   requested, pipeline stages in use (0 when the pipelined kernel is not
-   used); any pointer may be NULL. */
+   requested, pipeline stages and row groups per warp in use (0 when the
+   pipelined kernel is not used); any pointer may be NULL. */
 slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm,
-                            int *stages);
+                            int *stages, int *rows);
 
 /* Wait for the device, then report whether a bounded wait inside the
    batch's kernels gave up since the last call (SLIC_ERR_TIMEOUT; the

@@ -156,11 +156,11 @@ class BatchSegmenter:
                                 _stream_handle(stream))
 
     def autotune(self, cache_path=None, stream=None):
-        """Time the launch shapes that fit; -> (ctas_per_sm, stages) chosen."""
+        """Time the launch shapes that fit; -> (ctas_per_sm, stages, rows) chosen."""
         return slic_batch_autotune(self.handle, cache_path, _stream_handle(stream))
 
-    def set_tuning(self, ctas_per_sm: int, stages: int = 0):
-        slic_batch_set_tuning(self.handle, ctas_per_sm, stages)
+    def set_tuning(self, ctas_per_sm: int, stages: int = 0, rows: int = 0):
+        slic_batch_set_tuning(self.handle, ctas_per_sm, stages, rows)
 
     @property
     def info(self):

@@ -57,10 +57,10 @@ _SIGNATURES = {
     "slic_batch_set_buffers": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)],
     "slic_batch_segment": [_P, _P],
     "slic_batch_segment_host": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
-    "slic_batch_set_tuning": [_P, _I, _I],
-    "slic_batch_autotune": [_P, ctypes.c_char_p, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "slic_batch_set_tuning": [_P, _I, _I, _I],
+    "slic_batch_autotune": [_P, ctypes.c_char_p, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "slic_batch_info": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
-                        ctypes.POINTER(_I), ctypes.POINTER(_I)],
+                        ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "slic_batch_destroy": [_P],
     "slic_batch_status": [_P],
     "slic_batch_profile_enable": [_P, _I],
@@ -224,23 +224,25 @@ def slic_batch_segment_host(b: int, host_images, host_labels=None, host_centres=
                                           stream or None), b)
 
 
-def slic_batch_set_tuning(b: int, ctas_per_sm: int, stages: int = 0) -> None:
-    _bcheck(lib().slic_batch_set_tuning(b, int(ctas_per_sm), int(stages)), b)
+def slic_batch_set_tuning(b: int, ctas_per_sm: int, stages: int = 0, rows: int = 0) -> None:
+    _bcheck(lib().slic_batch_set_tuning(b, int(ctas_per_sm), int(stages), int(rows)), b)
 
 
 def slic_batch_autotune(b: int, cache_path: str | None = None, stream: int = 0):
-    """-> (ctas_per_sm, stages) chosen."""
-    c, st = _I(), _I()
+    """-> (ctas_per_sm, stages, rows) chosen."""
+    c, st, rw = _I(), _I(), _I()
     path = cache_path.encode() if cache_path else None
-    _bcheck(lib().slic_batch_autotune(b, path, stream or None, ctypes.byref(c), ctypes.byref(st)), b)
-    return c.value, st.value
+    _bcheck(lib().slic_batch_autotune(b, path, stream or None, ctypes.byref(c), ctypes.byref(st), ctypes.byref(rw)),
+            b)
+    return c.value, st.value, rw.value
 
 
 def slic_batch_info(b: int):
-    """-> (total_pixels, launches, ctas_per_sm, stages)."""
-    px, n, c, st = ctypes.c_longlong(), ctypes.c_longlong(), _I(), _I()
-    _bcheck(lib().slic_batch_info(b, ctypes.byref(px), ctypes.byref(n), ctypes.byref(c), ctypes.byref(st)), b)
-    return px.value, n.value, c.value, st.value
+    """-> (total_pixels, launches, ctas_per_sm, stages, rows)."""
+    px, n, c, st, rw = ctypes.c_longlong(), ctypes.c_longlong(), _I(), _I(), _I()
+    _bcheck(lib().slic_batch_info(b, ctypes.byref(px), ctypes.byref(n), ctypes.byref(c), ctypes.byref(st),
+                                  ctypes.byref(rw)), b)
+    return px.value, n.value, c.value, st.value, rw.value
 
 
 def slic_batch_status(b: int) -> None:

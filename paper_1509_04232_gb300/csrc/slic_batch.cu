@@ -33,7 +33,8 @@ struct slic_batch_ctx {
     int total_tiles = 0, total_centres = 0, total_rows = 0, max_w = 0, win_max = 0;
     int total_units = 0;  // work units of the fused connectivity kernel
     long long total_pixels = 0;
-    bool same = true;
+    bool same = true;        // every frame's S a multiple of 4 (4-pixel groups share a cell)
+    bool same8 = true;       // every frame's S a multiple of 8 (two row groups share a cell row)
     bool pipe = false;       // passes after the first use the pipelined kernel
     bool buffers_set = false;
     size_t smem = 0;
@@ -41,7 +42,8 @@ struct slic_batch_ctx {
     int max_ring = 0;
     int *d_err = nullptr;    // device flag: a bounded wait timed out
     int ctas_per_sm = 0;     // 0: as many as fit
-    int stages = 4;          // TMA pipeline stages of the later passes (3..4)
+    int stages = 4;          // TMA pipeline stages of the pipelined kernel (3..4)
+    int rows = 1;            // row groups per warp of the pipelined kernel (1, or 2 when same8)
     long long launches = 0;
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
@@ -130,8 +132,8 @@ int grid_for(const slic_batch_ctx *b, int occ) {
     return std::max(1, per_sm) * b->sms;
 }
 
-int pipe_occ(const slic_batch_ctx *b, int stages) {
-    return std::max(1, assign_pipe_occupancy(b->same, b->win_max, stages));
+int pipe_occ(const slic_batch_ctx *b, int stages, int rows) {
+    return std::max(1, assign_pipe_occupancy(b->same, b->win_max, stages, rows));
 }
 
 std::string tune_key(const slic_batch_ctx *b) {
@@ -148,8 +150,8 @@ std::string tune_key(const slic_batch_ctx *b) {
     return key;
 }
 
-// Cache lines: {"key": "<key>", "ctas_per_sm": <int>, "stages": <int>, "ms": <float>}
-bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stages) {
+// Cache lines: {"key": "<key>", "ctas_per_sm": <int>, "stages": <int>, "rows": <int>, "ms": <float>}
+bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stages, int *rows) {
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
     char line[4096];
@@ -159,11 +161,13 @@ bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stag
         if (std::strstr(line, needle.c_str())) {
             const char *q = std::strstr(line, "\"ctas_per_sm\":");
             const char *r = std::strstr(line, "\"stages\":");
-            int v = 0, w = 0;
-            if (q && r && std::sscanf(q + 14, "%d", &v) == 1 && std::sscanf(r + 9, "%d", &w) == 1 && v > 0 &&
-                w >= 3 && w <= 4) {
+            const char *o = std::strstr(line, "\"rows\":");
+            int v = 0, w = 0, u = 0;
+            if (q && r && o && std::sscanf(q + 14, "%d", &v) == 1 && std::sscanf(r + 9, "%d", &w) == 1 &&
+                std::sscanf(o + 7, "%d", &u) == 1 && v > 0 && w >= 3 && w <= 4 && (u == 1 || u == 2)) {
                 *ctas = v;
                 *stages = w;
+                *rows = u;
                 found = true;
             }
         }
@@ -172,11 +176,11 @@ bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stag
     return found;
 }
 
-void cache_store(const char *path, const std::string &key, int ctas, int stages, float ms) {
+void cache_store(const char *path, const std::string &key, int ctas, int stages, int rows, float ms) {
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"stages\": %d, \"ms\": %.4f}\n", key.c_str(), ctas,
-                 stages, ms);
+    std::fprintf(f, "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"stages\": %d, \"rows\": %d, \"ms\": %.4f}\n",
+                 key.c_str(), ctas, stages, rows, ms);
     std::fclose(f);
 }
 
@@ -247,6 +251,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         a.strip_base = b->total_units;
         b->total_units += connectivity2_units(p.width, p.height, &a.strips_x);
         b->same = b->same && (S % kPPT) == 0;
+        b->same8 = b->same8 && (S % 8) == 0;
         b->total_pixels += (long long)p.width * p.height;
         off_feat[f] = bytes;
         bytes += align256(sizeof(float) * 3 * (size_t)p.height * a.P);
@@ -278,8 +283,9 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
     }
     // The pipelined kernel needs private sums and its shared memory within
     // the opt-in limit (at least with three stages).
-    b->pipe = !assign_direct_acc(b->win_max) && assign_pipe_occupancy(b->same, b->win_max, 3) > 0;
-    if (b->pipe && assign_pipe_occupancy(b->same, b->win_max, 4) == 0) b->stages = 3;
+    b->same8 = b->same8 && b->same;
+    b->pipe = !assign_direct_acc(b->win_max) && assign_pipe_occupancy(b->same, b->win_max, 3, 1) > 0;
+    if (b->pipe && assign_pipe_occupancy(b->same, b->win_max, 4, 1) == 0) b->stages = 3;
     b->occupancy = std::max(1, assign_batch_occupancy(b->same, b->smem));
     if (cudaMalloc(&b->scratch, bytes) != cudaSuccess ||
         cudaMalloc(&b->d_frames, sizeof(FrameArgs) * n_frames) != cudaSuccess) {
@@ -357,7 +363,7 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
     if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
     cudaStream_t s = (cudaStream_t)stream;
     const int grid = grid_for(b, b->occupancy);
-    const int grid_pipe = b->pipe ? grid_for(b, pipe_occ(b, b->stages)) : grid;
+    const int grid_pipe = b->pipe ? grid_for(b, pipe_occ(b, b->stages, b->rows)) : grid;
     const int pipe_per_sm = grid_pipe / std::max(1, b->sms);
     // With the pipelined kernel every pass reads features: a conversion
     // pre-pass writes them, and the first pass is pipelined as well.
@@ -389,7 +395,7 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
             if (e != cudaSuccess) break;
             if (b->pipe)
                 e = launch_assign_pipe(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == b->iterations,
-                                       b->stages, pipe_per_sm, grid_pipe, b->d_err, s);
+                                       b->stages, b->rows, pipe_per_sm, grid_pipe, b->d_err, s);
             else
                 e = launch_assign_batch(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == 0,
                                         pass == b->iterations, b->smem, grid, s);
@@ -440,27 +446,35 @@ slic_status slic_batch_segment_host(slic_batch b, const uint8_t *const *host_ima
     return SLIC_OK;
 }
 
-slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages) {
+slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages, int rows) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (ctas_per_sm < 0) return bfail(b, SLIC_ERR_INVALID, "ctas_per_sm must be >= 0");
     if (stages != 0 && (stages < 3 || stages > 4)) return bfail(b, SLIC_ERR_INVALID, "stages must be 0, 3 or 4");
-    if (stages && b->pipe && assign_pipe_occupancy(b->same, b->win_max, stages) == 0)
+    if (rows != 0 && rows != 1 && rows != 2) return bfail(b, SLIC_ERR_INVALID, "rows must be 0, 1 or 2");
+    if (rows == 2 && !(b->pipe && b->same8))
+        return bfail(b, SLIC_ERR_INVALID, "two row groups need every frame's S to be a multiple of 8");
+    const int st = stages ? stages : b->stages, rw = rows ? rows : b->rows;
+    if ((stages || rows) && b->pipe && assign_pipe_occupancy(b->same, b->win_max, st, rw) == 0)
         return bfail(b, SLIC_ERR_INVALID, "the pipeline stages do not fit in shared memory");
     b->ctas_per_sm = ctas_per_sm;
-    if (stages) b->stages = stages;
+    b->stages = st;
+    b->rows = rw;
     return SLIC_OK;
 }
 
-slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm, int *stages) {
+slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm, int *stages,
+                               int *rows) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
     const std::string key = tune_key(b);
-    int best = 0, best_st = b->stages;
-    if (cache_path && cache_lookup(cache_path, key, &best, &best_st)) {
+    int best = 0, best_st = b->stages, best_rw = b->rows;
+    if (cache_path && cache_lookup(cache_path, key, &best, &best_st, &best_rw) && (best_rw == 1 || b->same8)) {
         b->ctas_per_sm = best;
         b->stages = best_st;
+        b->rows = best_rw;
         if (ctas_per_sm) *ctas_per_sm = best;
         if (stages) *stages = best_st;
+        if (rows) *rows = best_rw;
         return SLIC_OK;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -469,29 +483,35 @@ slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stre
         return bfail(b, SLIC_ERR_CUDA, "cudaEventCreate failed");
     float best_ms = 1e30f;
     slic_status st = SLIC_OK;
-    // Search space: pipeline depth x resident CTAs per SM (up to what fits).
+    // Search space: row groups per warp x pipeline stages x resident CTAs
+    // per SM (up to what fits).
     const int st_lo = b->pipe ? 3 : b->stages, st_hi = b->pipe ? 4 : b->stages;
-    for (int nst = st_lo; nst <= st_hi && st == SLIC_OK; ++nst) {
-        if (b->pipe && assign_pipe_occupancy(b->same, b->win_max, nst) == 0) continue;
-        const int occ = std::max(b->occupancy, b->pipe ? pipe_occ(b, nst) : 0);
-        for (int c = 1; c <= occ && st == SLIC_OK; ++c) {
-            b->ctas_per_sm = c;
-            b->stages = nst;
-            if ((st = slic_batch_segment(b, stream)) != SLIC_OK) break;  // warm-up
-            float total = 0.0f;
-            for (int rep = 0; rep < 3 && st == SLIC_OK; ++rep) {
-                cudaEventRecord(e0, s);
-                st = slic_batch_segment(b, stream);
-                cudaEventRecord(e1, s);
-                float ms = 0.0f;
-                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-                    st = bfail(b, SLIC_ERR_CUDA, "autotune timing failed");
-                total += ms;
-            }
-            if (st == SLIC_OK && total / 3 < best_ms) {
-                best_ms = total / 3;
-                best = c;
-                best_st = nst;
+    const int rw_hi = (b->pipe && b->same8) ? 2 : 1;
+    for (int rw = 1; rw <= rw_hi && st == SLIC_OK; ++rw) {
+        for (int nst = st_lo; nst <= st_hi && st == SLIC_OK; ++nst) {
+            if (b->pipe && assign_pipe_occupancy(b->same, b->win_max, nst, rw) == 0) continue;
+            const int occ = std::max(b->occupancy, b->pipe ? pipe_occ(b, nst, rw) : 0);
+            for (int c = 1; c <= occ && st == SLIC_OK; ++c) {
+                b->ctas_per_sm = c;
+                b->stages = nst;
+                b->rows = rw;
+                if ((st = slic_batch_segment(b, stream)) != SLIC_OK) break;  // warm-up
+                float total = 0.0f;
+                for (int rep = 0; rep < 3 && st == SLIC_OK; ++rep) {
+                    cudaEventRecord(e0, s);
+                    st = slic_batch_segment(b, stream);
+                    cudaEventRecord(e1, s);
+                    float ms = 0.0f;
+                    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                        st = bfail(b, SLIC_ERR_CUDA, "autotune timing failed");
+                    total += ms;
+                }
+                if (st == SLIC_OK && total / 3 < best_ms) {
+                    best_ms = total / 3;
+                    best = c;
+                    best_st = nst;
+                    best_rw = rw;
+                }
             }
         }
     }
@@ -500,19 +520,22 @@ slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stre
     if (st != SLIC_OK) return st;
     b->ctas_per_sm = best;
     b->stages = best_st;
-    if (cache_path) cache_store(cache_path, key, best, best_st, best_ms);
+    b->rows = best_rw;
+    if (cache_path) cache_store(cache_path, key, best, best_st, best_rw, best_ms);
     if (ctas_per_sm) *ctas_per_sm = best;
     if (stages) *stages = best_st;
+    if (rows) *rows = best_rw;
     return SLIC_OK;
 }
 
 slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm,
-                            int *stages) {
+                            int *stages, int *rows) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (total_pixels) *total_pixels = b->total_pixels;
     if (launches) *launches = b->launches;
     if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : b->occupancy;
     if (stages) *stages = b->pipe ? b->stages : 0;
+    if (rows) *rows = b->pipe ? b->rows : 0;
     return SLIC_OK;
 }
 

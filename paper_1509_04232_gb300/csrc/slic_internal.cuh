@@ -152,13 +152,15 @@ cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_cent
 // Pipelined (TMA bulk copies, mbarrier) assignment for the passes after the
 // first, reading features and the padded centre table; *err is set on a
 // timed-out wait.
-// ctas_per_sm >= 4 selects the 64-register build.
+// rows = 1: 256 threads, 4 pixels per thread (ctas_per_sm >= 4 selects the
+// 64-register build); rows = 2: 128 threads, 8 pixels per thread (two row
+// groups in one cell row: every frame's S a multiple of 8, `same` set).
 cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool last,
-                               int nst, int ctas_per_sm, int grid, int *err, cudaStream_t s);
+                               int nst, int rows, int ctas_per_sm, int grid, int *err, cudaStream_t s);
 // Shared memory and resident CTAs per SM of the pipelined kernel with nst
-// (2..4) stages.
-size_t assign_pipe_smem_bytes(int win_n, bool last, int nst);
-int assign_pipe_occupancy(bool same, int win_n, int nst);
+// (3..4) stages and 1 or 2 row groups per warp.
+size_t assign_pipe_smem_bytes(int win_n, bool last, int nst, int rows);
+int assign_pipe_occupancy(bool same, int win_n, int nst, int rows);
 // Batched RGB -> features pre-pass (the pipelined path's first pass reads
 // the features it writes).
 cudaError_t launch_convert_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w, cudaStream_t s);

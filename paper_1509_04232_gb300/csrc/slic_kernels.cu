@@ -778,15 +778,16 @@ __device__ __forceinline__ void issue_tile(const FrameArgs &a, const TileGeom &g
     tma_load_2d(stage + kStageFeatBytes, &a.ctab_map, (g.wx0 + 1) * kCtabRec, g.wy0 + 1, bar);
 }
 
-// Add tile j's private sums (all warps' copies of accumulator set j % 3) to
-// the frame's global sums and clear them. One warp per tile does it (warp
-// j % 8, so the duty rotates), a lane per window cell reading the cell's
+// Add tile j's private sums (the 8 copies of accumulator set j % 3, one per
+// 128 pixels) to the frame's global sums and clear them. One of the NW warps
+// per tile does it (warp j % NW, so the duty rotates), a lane per window cell reading the cell's
 // four words of every copy as one 16-byte load. The flushing warp waits
 // until every warp has filled the set and reports it free afterwards; the
 // others return at once. False when the wait timed out.
+template <int NW>
 __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, unsigned *wacc0, size_t acc_words, int win_max,
                                            uint64_t *acc_done, uint64_t *acc_free, int j, int warp, int lane) {
-    if (warp != (j & (kWarps - 1))) return true;
+    if (warp != j % NW) return true;
     const int set = j % kAccSets;
     if (!__all_sync(0xffffffffu, mbar_wait(&acc_done[set], (j / kAccSets) & 1))) return false;
     const TileGeom &g = hdr[j % kHdrSlots];
@@ -831,7 +832,8 @@ __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, unsigned *wacc0,
 
 }  // namespace
 
-size_t assign_pipe_smem_bytes(int win_n, bool last, int nst) {
+size_t assign_pipe_smem_bytes(int win_n, bool last, int nst, int rows) {
+    (void)rows;  // the sums keep one copy per 128 pixels whatever the warp count
     const size_t stage = kStageFeatBytes + (((size_t)win_n * kCtabRec * 4 + 127) & ~(size_t)127);
     const size_t acc = last ? 0 : (size_t)kWarps * win_n * 4 * sizeof(int);
     // nst stages, the accumulator sets, the mbarriers, the header ring, two
@@ -840,20 +842,29 @@ size_t assign_pipe_smem_bytes(int win_n, bool last, int nst) {
            (size_t)kHdrSlots * sizeof(TileGeom) + 16 + 128;
 }
 
-template <bool LAST, bool SAME, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs *frames, int n_frames,
-                                                                int total_tiles, int win_max, int nst, int *err) {
+template <bool LAST, bool SAME, int MINB, int ROWS>
+__global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const FrameArgs *frames, int n_frames,
+                                                                       int total_tiles, int win_max, int nst,
+                                                                       int *err) {
+    // ROWS = 1: 8 warps, warp w evaluates rows 4w..4w+3 of the tile.
+    // ROWS = 2: 4 warps, warp w evaluates rows 8w..8w+3 and 8w+4..8w+7 (the
+    // same cell row when S is a multiple of 8), sharing the centre loads and
+    // the per-tile work between 8 pixels per thread.
+    static_assert(ROWS == 1 || (ROWS == 2 && SAME), "two row groups need cell-aligned 4-pixel groups");
+    constexpr int NW = kWarps / ROWS, NT = NW * 32;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     // Tensor copies want 128-byte aligned destinations.
     unsigned char *smem_raw =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~(uintptr_t)127);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t stage_bytes = kStageFeatBytes + (((size_t)win_max * kCtabRec * 4 + 127) & ~(size_t)127);
+    // One private copy of the sums per 128 pixels (per warp and row group),
+    // so a copy's packed x / y / count fields cannot overflow.
     const size_t acc_words = LAST ? 0 : (size_t)kWarps * win_max * 4;
     unsigned *const wacc0 = reinterpret_cast<unsigned *>(smem_raw + (size_t)nst * stage_bytes);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)nst * stage_bytes + kAccSets * acc_words * 4);
-    uint64_t *empty = full + kMaxStages;       // stage released by every warp (count kWarps)
-    uint64_t *acc_done = empty + kMaxStages;   // accumulator set filled by every warp (count kWarps)
+    uint64_t *empty = full + kMaxStages;       // stage released by every warp (count NW)
+    uint64_t *acc_done = empty + kMaxStages;   // accumulator set filled by every warp (count NW)
     uint64_t *acc_free = acc_done + kAccSets;  // accumulator set flushed and cleared (count 1)
     TileGeom *hdr = reinterpret_cast<TileGeom *>(acc_free + kAccSets);  // ring of kHdrSlots tile headers
     int *flags = reinterpret_cast<int *>(hdr + kHdrSlots);              // [0] abort, [1] last tile issued
@@ -863,10 +874,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
     if (tid == 0) {
         for (int q = 0; q < nst; ++q) {
             mbar_init(&full[q], 1);
-            mbar_init(&empty[q], kWarps);
+            mbar_init(&empty[q], NW);
         }
         for (int q = 0; q < kAccSets; ++q) {
-            mbar_init(&acc_done[q], kWarps);
+            mbar_init(&acc_done[q], NW);
             mbar_init(&acc_free[q], 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -874,7 +885,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
         flags[1] = -1;
     }
     if (!LAST) {
-        for (int i = tid; i < (int)(kAccSets * acc_words); i += kThreads) wacc0[i] = 0u;
+        for (int i = tid; i < (int)(kAccSets * acc_words); i += NT) wacc0[i] = 0u;
     }
     __syncthreads();
 
@@ -903,7 +914,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
     }
     __syncthreads();
 
-    const int lx = 4 * (lane & 7), ly = 4 * warp + (lane >> 3);
+    const int lx = 4 * (lane & 7), ly0 = 4 * ROWS * warp + (lane >> 3);
     int it = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++it) {
@@ -911,7 +922,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
             ok = false;
             break;
         }
-        if (warp == (it & (kWarps - 1)) && lane == 0 && !produce(it + ahead + 1)) {
+        if (warp == it % NW && lane == 0 && !produce(it + ahead + 1)) {
             *abort_flag = 1;
             atomicOr(err, 1);
         }
@@ -931,18 +942,26 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
         const unsigned s_mul = g.s_mul;
         const float *feat = reinterpret_cast<const float *>(stage_s);
         const float *cen = reinterpret_cast<const float *>(stage_s + kStageFeatBytes);
-        const int x = tx0 + lx, y = ty0 + ly;
-        const bool row_ok = (y < H) && (x < W);
-        float f0[kPPT] = {}, f1[kPPT] = {}, f2[kPPT] = {};
-        if (row_ok) {
-            const float4 v0 = *reinterpret_cast<const float4 *>(feat + (0 * kTileH + ly) * kTileW + lx);
-            const float4 v1 = *reinterpret_cast<const float4 *>(feat + (1 * kTileH + ly) * kTileW + lx);
-            const float4 v2 = *reinterpret_cast<const float4 *>(feat + (2 * kTileH + ly) * kTileW + lx);
-            f0[0] = v0.x; f0[1] = v0.y; f0[2] = v0.z; f0[3] = v0.w;
-            f1[0] = v1.x; f1[1] = v1.y; f1[2] = v1.z; f1[3] = v1.w;
-            f2[0] = v2.x; f2[1] = v2.y; f2[2] = v2.z; f2[3] = v2.w;
+        const int x = tx0 + lx;
+        int y[ROWS];
+        bool row_ok[ROWS];
+        float f0[ROWS][kPPT] = {}, f1[ROWS][kPPT] = {}, f2[ROWS][kPPT] = {};
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const int ly = ly0 + 4 * r;
+            y[r] = ty0 + ly;
+            row_ok[r] = (y[r] < H) && (x < W);
+            if (row_ok[r]) {
+                const float4 v0 = *reinterpret_cast<const float4 *>(feat + (0 * kTileH + ly) * kTileW + lx);
+                const float4 v1 = *reinterpret_cast<const float4 *>(feat + (1 * kTileH + ly) * kTileW + lx);
+                const float4 v2 = *reinterpret_cast<const float4 *>(feat + (2 * kTileH + ly) * kTileW + lx);
+                f0[r][0] = v0.x; f0[r][1] = v0.y; f0[r][2] = v0.z; f0[r][3] = v0.w;
+                f1[r][0] = v1.x; f1[r][1] = v1.y; f1[r][2] = v1.z; f1[r][3] = v1.w;
+                f2[r][0] = v2.x; f2[r][1] = v2.y; f2[r][2] = v2.z; f2[r][3] = v2.w;
+            }
         }
-        const int pcy = div_s(y, s_mul, S);
+        // Both row groups share the cell row (ROWS = 2 needs S % 8 == 0).
+        const int pcy = div_s(y[0], s_mul, S);
         int cx[kPPT];
         {
             const int c0 = div_s(x, s_mul, S);
@@ -964,94 +983,102 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
         // whose low 4 mantissa bits carry the candidate index: non-negative
         // floats order like their bit patterns, so this equals the integer
         // minimum of (D & ~15) | t, scan order breaking ties.
-        float bk[kPPT];
+        float bk[ROWS][kPPT];
 #pragma unroll
-        for (int j = 0; j < kPPT; ++j) bk[j] = __int_as_float(0x7F800000);
-        if (row_ok) {
+        for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) bk[r][j] = __int_as_float(0x7F800000);
+        bool any_row = false;
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) any_row |= row_ok[r];
+        if (any_row) {
             const float w = g.w;
-            const float fy = (float)y;
             const int rowoff = (pcy - wy0) * bw - wx0;
             if (SAME) {
-                // The thread's 4 pixels share the window: pixels (0, 1) and
-                // (2, 3) go through paired FP32 instructions.
-                const unsigned long long ww = pack2(w, w), fyy = pack2(fy, fy);
-                const unsigned long long l01 = pack2(f0[0], f0[1]), l23 = pack2(f0[2], f0[3]);
-                const unsigned long long a01 = pack2(f1[0], f1[1]), a23 = pack2(f1[2], f1[3]);
-                const unsigned long long b01 = pack2(f2[0], f2[1]), b23 = pack2(f2[2], f2[3]);
+                // The thread's pixels share the window: pixels (0, 1) and
+                // (2, 3) of each row group go through paired FP32 instructions.
+                const unsigned long long ww = pack2(w, w);
+                unsigned long long fyy[ROWS], l01[ROWS], l23[ROWS], a01[ROWS], a23[ROWS], b01[ROWS], b23[ROWS];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    const float fy = (float)y[r];
+                    fyy[r] = pack2(fy, fy);
+                    l01[r] = pack2(f0[r][0], f0[r][1]);
+                    l23[r] = pack2(f0[r][2], f0[r][3]);
+                    a01[r] = pack2(f1[r][0], f1[r][1]);
+                    a23[r] = pack2(f1[r][2], f1[r][3]);
+                    b01[r] = pack2(f2[r][0], f2[r][1]);
+                    b23[r] = pack2(f2[r][2], f2[r][3]);
+                }
                 const float fx = (float)x;  // x + j exactly (x < 2^24)
                 const unsigned long long x01 = pack2(fx, fx + 1.0f), x23 = pack2(fx + 2.0f, fx + 3.0f);
                 const int own = rowoff + cx[0];
 #pragma unroll
                 for (int t = 0; t < 9; ++t) {
-                    const float *r = cen + (size_t)(own + (t / 3 - 1) * bw + (t % 3 - 1)) * kCtabRec;
-                    const ulonglong2 la = *reinterpret_cast<const ulonglong2 *>(r);      // (L, L), (a, a)
-                    const ulonglong2 bx = *reinterpret_cast<const ulonglong2 *>(r + 4);  // (b, b), (x, x)
-                    const unsigned long long yy = *reinterpret_cast<const unsigned long long *>(r + 8);
-                    const unsigned long long ddy = sub2(yy, fyy);
-                    const unsigned long long ddy2 = mul2(ddy, ddy);
-                    eval_pair(la, bx, ddy2, ww, l01, a01, b01, x01, (unsigned)t, bk[0], bk[1]);
-                    eval_pair(la, bx, ddy2, ww, l23, a23, b23, x23, (unsigned)t, bk[2], bk[3]);
+                    const float *rp = cen + (size_t)(own + (t / 3 - 1) * bw + (t % 3 - 1)) * kCtabRec;
+                    const ulonglong2 la = *reinterpret_cast<const ulonglong2 *>(rp);      // (L, L), (a, a)
+                    const ulonglong2 bx = *reinterpret_cast<const ulonglong2 *>(rp + 4);  // (b, b), (x, x)
+                    const unsigned long long yy = *reinterpret_cast<const unsigned long long *>(rp + 8);
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) {
+                        const unsigned long long ddy = sub2(yy, fyy[r]);
+                        const unsigned long long ddy2 = mul2(ddy, ddy);
+                        eval_pair(la, bx, ddy2, ww, l01[r], a01[r], b01[r], x01, (unsigned)t, bk[r][0], bk[r][1]);
+                        eval_pair(la, bx, ddy2, ww, l23[r], a23[r], b23[r], x23, (unsigned)t, bk[r][2], bk[r][3]);
+                    }
                 }
             } else {
+                const float fy = (float)y[0];
 #pragma unroll
                 for (int j = 0; j < kPPT; ++j) {
                     const int own = rowoff + cx[j];
                     const float fx = (float)(x + j);
 #pragma unroll
                     for (int t = 0; t < 9; ++t) {
-                        const float *r = cen + (size_t)(own + (t / 3 - 1) * bw + (t % 3 - 1)) * kCtabRec;
-                        const float4 la = *reinterpret_cast<const float4 *>(r);
-                        const float4 bx = *reinterpret_cast<const float4 *>(r + 4);
-                        const float ddy = r[8] - fy;
+                        const float *rp = cen + (size_t)(own + (t / 3 - 1) * bw + (t % 3 - 1)) * kCtabRec;
+                        const float4 la = *reinterpret_cast<const float4 *>(rp);
+                        const float4 bx = *reinterpret_cast<const float4 *>(rp + 4);
+                        const float ddy = rp[8] - fy;
                         const float ddx = bx.z - fx;
-                        const float dl = la.x - f0[j], da = la.z - f1[j], db = bx.x - f2[j];
+                        const float dl = la.x - f0[0][j], da = la.z - f1[0][j], db = bx.x - f2[0][j];
                         const float d_lab = fsqrt_approx(fmaf(dl, dl, fmaf(da, da, db * db)));
                         const float D = fmaf(w, fsqrt_approx(fmaf(ddx, ddx, ddy * ddy)), d_lab);
-                        bk[j] = fmin_nan(bk[j], __uint_as_float((__float_as_uint(D) & ~15u) | (unsigned)t));
+                        bk[0][j] = fmin_nan(bk[0][j], __uint_as_float((__float_as_uint(D) & ~15u) | (unsigned)t));
                     }
                 }
             }
         }
-        int best[kPPT];
+        int best[ROWS][kPPT];
 #pragma unroll
-        for (int j = 0; j < kPPT; ++j) {
-            const int t = (int)(__float_as_uint(bk[j]) & 15u);
-            const int dy = t / 3 - 1, dx = t % 3 - 1;
-            const bool ok = row_ok && (x + j < W);
-            if (LAST)
-                best[j] = ok ? (pcy + dy) * ns_c + cx[j] + dx : -1;
-            else
-                best[j] = ok ? (pcy + dy - wy0) * bw + (cx[j] + dx - wx0) : -1;
+        for (int r = 0; r < ROWS; ++r) {
+#pragma unroll
+            for (int j = 0; j < kPPT; ++j) {
+                const int t = (int)(__float_as_uint(bk[r][j]) & 15u);
+                const int dy = t / 3 - 1, dx = t % 3 - 1;
+                const bool okp = row_ok[r] && (x + j < W);
+                if (LAST)
+                    best[r][j] = okp ? (pcy + dy) * ns_c + cx[j] + dx : -1;
+                else
+                    best[r][j] = okp ? (pcy + dy - wy0) * bw + (cx[j] + dx - wx0) : -1;
+            }
         }
         // Every read of the stage is done: release it to the producers.
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         if constexpr (LAST) {
-            if (row_ok) {
-                int32_t *out = g.labels + (size_t)y * W + x;
-                if (g.labels_vec) {
-                    *reinterpret_cast<int4 *>(out) = make_int4(best[0], best[1], best[2], best[3]);
-                } else {
-                    for (int j = 0; j < kPPT && x + j < W; ++j) out[j] = best[j];
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                if (row_ok[r]) {
+                    int32_t *out = g.labels + (size_t)y[r] * W + x;
+                    if (g.labels_vec) {
+                        *reinterpret_cast<int4 *>(out) = make_int4(best[r][0], best[r][1], best[r][2], best[r][3]);
+                    } else {
+                        for (int j = 0; j < kPPT && x + j < W; ++j) out[j] = best[r][j];
+                    }
                 }
             }
         } else {
             const float fs = g.fix_scale;
-            unsigned v[kPPT][4];
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j) {
-                v[j][0] = fix_round(f0[j], fs);
-                v[j][1] = fix_round(f1[j], fs);
-                v[j][2] = fix_round(f2[j], fs);
-                v[j][3] = (unsigned)(lx + j) + ((unsigned)ly << 12) + (1u << 24);
-            }
-#pragma unroll
-            for (int j = kPPT - 2; j >= 0; --j) {
-                if (best[j + 1] == best[j]) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) v[j][c] += v[j + 1][c];
-                }
-            }
             // Set it % 3 was flushed (tile it - 3) before it is reused.
             const int set = it % kAccSets;
             if (it >= kAccSets && !__all_sync(0xffffffffu, mbar_wait(&acc_free[set], ((it / kAccSets) - 1) & 1))) {
@@ -1062,19 +1089,38 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
                 ok = false;
                 break;
             }
-            unsigned *my = wacc0 + (size_t)set * acc_words + (size_t)warp * win_max * 4;
 #pragma unroll
-            for (int j = 0; j < kPPT; ++j) {
-                const int k = (j == 0 || best[j] != best[j - 1]) ? best[j] : -1;
-                if (k >= 0) {
+            for (int r = 0; r < ROWS; ++r) {
+                const int ly = ly0 + 4 * r;
+                unsigned *my = wacc0 + (size_t)set * acc_words + (size_t)(warp * ROWS + r) * win_max * 4;
+                unsigned v[kPPT][4];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) atomicAdd(&my[k * 4 + c], v[j][c]);
+                for (int j = 0; j < kPPT; ++j) {
+                    v[j][0] = fix_round(f0[r][j], fs);
+                    v[j][1] = fix_round(f1[r][j], fs);
+                    v[j][2] = fix_round(f2[r][j], fs);
+                    v[j][3] = (unsigned)(lx + j) + ((unsigned)ly << 12) + (1u << 24);
+                }
+#pragma unroll
+                for (int j = kPPT - 2; j >= 0; --j) {
+                    if (best[r][j + 1] == best[r][j]) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) v[j][c] += v[j + 1][c];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kPPT; ++j) {
+                    const int k = (j == 0 || best[r][j] != best[r][j - 1]) ? best[r][j] : -1;
+                    if (k >= 0) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) atomicAdd(&my[k * 4 + c], v[j][c]);
+                    }
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_done[set]);
-            // Flush the previous tile's sums (one slice per warp).
-            if (it > 0 && !flush_tile(hdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
+            // Flush the previous tile's sums (one warp per tile).
+            if (it > 0 && !flush_tile<NW>(hdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
                 if (lane == 0) {
                     *abort_flag = 1;
                     atomicOr(err, 1);
@@ -1085,7 +1131,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
         }
     }
     if (!LAST && ok && it > 0 &&
-        !flush_tile(hdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
+        !flush_tile<NW>(hdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
         if (lane == 0) {
             *abort_flag = 1;
             atomicOr(err, 1);
@@ -1102,55 +1148,60 @@ __global__ void __launch_bounds__(kThreads, MINB) k_assign_pipe(const FrameArgs 
 
 // Resident CTAs per SM of one instantiation (the query honours the
 // kernel's dynamic shared memory opt-in, so that is raised first).
-template <bool L, bool SM, int MINB>
+template <bool L, bool SM, int MINB, int ROWS>
 static int pipe_occupancy_of(size_t smem) {
     int blocks = 0;
-    if (cudaFuncSetAttribute(k_assign_pipe<L, SM, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_assign_pipe<L, SM, MINB>, kThreads, smem) !=
-            cudaSuccess)
+    if (cudaFuncSetAttribute(k_assign_pipe<L, SM, MINB, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_assign_pipe<L, SM, MINB, ROWS>, kThreads / ROWS,
+                                                      smem) != cudaSuccess)
         return 0;
     return blocks;
 }
 
-int assign_pipe_occupancy(bool same, int win_n, int nst) {
-    const size_t sm = assign_pipe_smem_bytes(win_n, false, nst);
+int assign_pipe_occupancy(bool same, int win_n, int nst, int rows) {
+    const size_t sm = assign_pipe_smem_bytes(win_n, false, nst, rows);
+    if (rows == 2) return same ? pipe_occupancy_of<false, true, 4, 2>(sm) : 0;
     // The 4-CTA build (64 registers) where shared memory allows, else the 3-CTA build.
-    const int o4 = same ? pipe_occupancy_of<false, true, 4>(sm) : pipe_occupancy_of<false, false, 4>(sm);
-    const int o3 = same ? pipe_occupancy_of<false, true, 3>(sm) : pipe_occupancy_of<false, false, 3>(sm);
+    const int o4 = same ? pipe_occupancy_of<false, true, 4, 1>(sm) : pipe_occupancy_of<false, false, 4, 1>(sm);
+    const int o3 = same ? pipe_occupancy_of<false, true, 3, 1>(sm) : pipe_occupancy_of<false, false, 3, 1>(sm);
     return o4 >= 4 ? o4 : o3;
 }
 
-template <bool L, bool SM, int MINB>
+template <bool L, bool SM, int MINB, int ROWS>
 static cudaError_t launch_pipe_as(const FrameArgs *d_frames, int n, int total_tiles, int win_max, int nst, int grid,
                                   size_t smem, int *err, cudaStream_t s) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_assign_pipe<L, SM, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_assign_pipe<L, SM, MINB, ROWS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_assign_pipe<L, SM, MINB><<<grid, kThreads, smem, s>>>(d_frames, n, total_tiles, win_max, nst, err);
+    k_assign_pipe<L, SM, MINB, ROWS><<<grid, kThreads / ROWS, smem, s>>>(d_frames, n, total_tiles, win_max, nst, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool last,
-                               int nst, int ctas_per_sm, int grid, int *err, cudaStream_t s) {
+                               int nst, int rows, int ctas_per_sm, int grid, int *err, cudaStream_t s) {
     if (grid > total_tiles) grid = total_tiles;
     if (grid < 1) grid = 1;
     if (nst < 3) nst = 3;
     if (nst > kMaxStages) nst = kMaxStages;
-    const size_t smem = assign_pipe_smem_bytes(win_max, last, nst);
+    if (rows == 2 && !same) return cudaErrorInvalidValue;
+    const size_t smem = assign_pipe_smem_bytes(win_max, last, nst, rows);
+    if (rows == 2)
+        return last ? launch_pipe_as<true, true, 4, 2>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
+                    : launch_pipe_as<false, true, 4, 2>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
     const bool wide = ctas_per_sm >= 4;  // 64-register build
     if (same) {
         if (last)
-            return wide ? launch_pipe_as<true, true, 4>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
-                        : launch_pipe_as<true, true, 3>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
-        return wide ? launch_pipe_as<false, true, 4>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
-                    : launch_pipe_as<false, true, 3>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
+            return wide ? launch_pipe_as<true, true, 4, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
+                        : launch_pipe_as<true, true, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
+        return wide ? launch_pipe_as<false, true, 4, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
+                    : launch_pipe_as<false, true, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
     }
     if (last)
-        return wide ? launch_pipe_as<true, false, 4>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
-                    : launch_pipe_as<true, false, 3>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
-    return wide ? launch_pipe_as<false, false, 4>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
-                : launch_pipe_as<false, false, 3>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
+        return wide ? launch_pipe_as<true, false, 4, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
+                    : launch_pipe_as<true, false, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
+    return wide ? launch_pipe_as<false, false, 4, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
+                : launch_pipe_as<false, false, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
 }
 
 cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cudaStream_t s) {
