@@ -694,6 +694,15 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
+// fix_round for two values with one paired fused multiply-add.
+__device__ __forceinline__ void fix_round2(float x0, float x1, float fs, unsigned &r0, unsigned &r1) {
+    const unsigned long long m = fma2(pack2(x0, x1), pack2(fs, fs), pack2(12582912.0f, 12582912.0f));
+    float m0, m1;
+    unpack2(m, m0, m1);
+    r0 = (unsigned)(__float_as_int(m0) - 0x4B400000);
+    r1 = (unsigned)(__float_as_int(m1) - 0x4B400000);
+}
+
 // min of two non-negative floats (a NaN operand loses), IEEE (no flush).
 __device__ __forceinline__ float fmin_nan(float a, float b) {
     float r;
@@ -1048,18 +1057,22 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
                 }
             }
         }
+        // Winner t -> its cell: row offset t/3 - 1, column offset t%3 - 1, so
+        // index = base + t + (t/3)*(stride - 3) with base = own - stride - 1
+        // (stride: box_w for the window index of the sums, ns_c for the label).
         int best[ROWS][kPPT];
-#pragma unroll
-        for (int r = 0; r < ROWS; ++r) {
+        {
+            const int stride = LAST ? ns_c : bw;
 #pragma unroll
             for (int j = 0; j < kPPT; ++j) {
-                const int t = (int)(__float_as_uint(bk[r][j]) & 15u);
-                const int dy = t / 3 - 1, dx = t % 3 - 1;
-                const bool okp = row_ok[r] && (x + j < W);
-                if (LAST)
-                    best[r][j] = okp ? (pcy + dy) * ns_c + cx[j] + dx : -1;
-                else
-                    best[r][j] = okp ? (pcy + dy - wy0) * bw + (cx[j] + dx - wx0) : -1;
+                const int base = (LAST ? pcy * ns_c + cx[j] : (pcy - wy0) * bw + cx[j] - wx0) - stride - 1;
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    const unsigned t = __float_as_uint(bk[r][j]) & 15u;
+                    const int q = (int)__umulhi(t, 0x55555556u);  // t / 3 for t < 9
+                    const bool okp = row_ok[r] && (x + j < W);
+                    best[r][j] = okp ? base + (int)t + q * (stride - 3) : -1;
+                }
             }
         }
         // Every read of the stage is done: release it to the producers.
@@ -1094,12 +1107,14 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
                 const int ly = ly0 + 4 * r;
                 unsigned *my = wacc0 + (size_t)set * acc_words + (size_t)(warp * ROWS + r) * win_max * 4;
                 unsigned v[kPPT][4];
+                const unsigned xyn = (unsigned)lx + ((unsigned)ly << 12) + (1u << 24);
 #pragma unroll
-                for (int j = 0; j < kPPT; ++j) {
-                    v[j][0] = fix_round(f0[r][j], fs);
-                    v[j][1] = fix_round(f1[r][j], fs);
-                    v[j][2] = fix_round(f2[r][j], fs);
-                    v[j][3] = (unsigned)(lx + j) + ((unsigned)ly << 12) + (1u << 24);
+                for (int j = 0; j < kPPT; j += 2) {
+                    fix_round2(f0[r][j], f0[r][j + 1], fs, v[j][0], v[j + 1][0]);
+                    fix_round2(f1[r][j], f1[r][j + 1], fs, v[j][1], v[j + 1][1]);
+                    fix_round2(f2[r][j], f2[r][j + 1], fs, v[j][2], v[j + 1][2]);
+                    v[j][3] = xyn + (unsigned)j;
+                    v[j + 1][3] = xyn + (unsigned)(j + 1);
                 }
 #pragma unroll
                 for (int j = kPPT - 2; j >= 0; --j) {
