@@ -905,11 +905,12 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
     // j - nst (two iterations earlier); the producer role rotates over the
     // warps. No CTA-wide barrier inside the loop: warps drift up to about two
     // tiles apart, bounded by the mbarriers.
-    auto produce = [&](int j) -> bool {
+    // q = j % nst and use = j / nst are passed in (kept incrementally: a
+    // division by the run-time stage count costs tens of instructions).
+    auto produce = [&](int j, int q, int use) -> bool {
         const int t = blockIdx.x + j * gridDim.x;
         if (t >= total_tiles) return true;
-        const int q = j % nst;
-        if (j >= nst && !mbar_wait(&empty[q], ((j / nst) - 1) & 1)) return false;
+        if (use > 0 && !mbar_wait(&empty[q], (use - 1) & 1)) return false;
         const int f = find_frame<kTileBase>(frames, n_frames, t);
         TileGeom g = tile_geom(frames[f], t - frames[f].tile_base);
         g.f = f;
@@ -919,24 +920,40 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
         return true;
     };
     if (tid == 0) {
-        for (int j = 0; j <= ahead; ++j) produce(j);
+        for (int j = 0; j <= ahead; ++j) produce(j, j, 0);
     }
     __syncthreads();
+    // Stage and phase of this iteration's tile, and of the tile its producer
+    // issues (ahead + 1 later), advanced without division.
+    int s = 0, ph = 0, sp = ahead + 1, usep = 0;
+    if (sp == nst) {
+        sp = 0;
+        usep = 1;
+    }
 
     const int lx = 4 * (lane & 7), ly0 = 4 * ROWS * warp + (lane >> 3);
     int it = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++it) {
+    auto advance = [&]() {
+        if (++s == nst) {
+            s = 0;
+            ph ^= 1;
+        }
+        if (++sp == nst) {
+            sp = 0;
+            ++usep;
+        }
+    };
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++it, advance()) {
         if (*abort_flag) {
             ok = false;
             break;
         }
-        if (warp == it % NW && lane == 0 && !produce(it + ahead + 1)) {
+        if (warp == it % NW && lane == 0 && !produce(it + ahead + 1, sp, usep)) {
             *abort_flag = 1;
             atomicOr(err, 1);
         }
-        const int s = it % nst;
-        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (it / nst) & 1))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], ph & 1))) {
             if (lane == 0) {
                 *abort_flag = 1;
                 atomicOr(err, 1);
