@@ -606,7 +606,7 @@ namespace {
 
 constexpr size_t kStageFeatBytes = (size_t)3 * kTileH * kTileW * 4;  // 12288
 constexpr int kMaxStages = 4;
-constexpr int kAccSets = 3;    // accumulator sets in flight: fill, flush, reuse
+constexpr int kAccSets = 2;    // accumulator sets in flight: one filled while the other is flushed
 constexpr int kHdrSlots = 8;   // tile-header ring (>= stages + 2)
 constexpr unsigned kWaitPolls = 1u << 20;                         // x 1 us suspend hint: ~1 s bound
 
@@ -787,7 +787,7 @@ __device__ __forceinline__ void issue_tile(const FrameArgs &a, const TileGeom &g
     tma_load_2d(stage + kStageFeatBytes, &a.ctab_map, (g.wx0 + 1) * kCtabRec, g.wy0 + 1, bar);
 }
 
-// Add tile j's private sums (the 8 copies of accumulator set j % 3, one per
+// Add tile j's private sums (the 8 copies of accumulator set j % 2, one per
 // 128 pixels) to the frame's global sums and clear them. One of the NW warps
 // per tile does it (warp j % NW, so the duty rotates), a lane per window cell reading the cell's
 // four words of every copy as one 16-byte load. The flushing warp waits
@@ -1109,7 +1109,7 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
             }
         } else {
             const float fs = g.fix_scale;
-            // Set it % 3 was flushed (tile it - 3) before it is reused.
+            // Set it % 2 was flushed (tile it - 2) before it is reused.
             const int set = it % kAccSets;
             if (it >= kAccSets && !__all_sync(0xffffffffu, mbar_wait(&acc_free[set], ((it / kAccSets) - 1) & 1))) {
                 if (lane == 0) {
