@@ -305,7 +305,7 @@ slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_label
     ++h->launches;
     for (int pass = 0; pass <= n; ++pass) {
         if (pass > 0) {
-            e = launch_update(h->acc, d_centres, d_centres, h->K, 1.0 / h->fix_scale, s);
+            e = launch_update(h->acc, d_centres, d_centres, h->K, 1.0f / h->fix_scale, s);
             if (e != cudaSuccess) return cuda_fail(h, e, "update kernel launch");
             ++h->launches;
         }
@@ -360,7 +360,7 @@ slic_status slic_update(slic_handle h, const float *d_features, const int32_t *d
     if (e == cudaSuccess)
         e = launch_accumulate_labels(d_features, h->p.width, h->p.height, h->p.width, d_labels, h->K, h->acc,
                                      h->fix_scale, s);
-    if (e == cudaSuccess) e = launch_update(h->acc, d_centres_in, d_centres_out, h->K, 1.0 / h->fix_scale, s);
+    if (e == cudaSuccess) e = launch_update(h->acc, d_centres_in, d_centres_out, h->K, 1.0f / h->fix_scale, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "update kernel launch");
     h->launches += 3;
     return SLIC_OK;
@@ -522,7 +522,7 @@ extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uin
     // sums left in the shared array by the previous call.
     e = launch_init_from_rgb(a, s);
     for (int pass = 0; e == cudaSuccess && pass <= p.iterations; ++pass) {
-        if (pass > 0) e = launch_update(a.acc, d_centres, d_centres, (int)K, 1.0 / a.fix_scale, s);
+        if (pass > 0) e = launch_update(a.acc, d_centres, d_centres, (int)K, 1.0f / a.fix_scale, s);
         if (e == cudaSuccess) e = launch_assign(a, pass == 0, pass == p.iterations, false, smem, s);
     }
     if (e == cudaSuccess && p.enforce_connectivity) {

@@ -146,7 +146,7 @@ cudaError_t launch_assign(const FrameArgs &a, bool first, bool last, bool store_
                           cudaStream_t s);
 cudaError_t launch_assign_batch(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool first,
                                 bool last, size_t smem, int grid, cudaStream_t s);
-cudaError_t launch_update(long long *acc, const float *centres_in, float *centres_out, int K, double fix_inv,
+cudaError_t launch_update(long long *acc, const float *centres_in, float *centres_out, int K, float fix_inv,
                           cudaStream_t s);
 cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_centres, cudaStream_t s);
 // Pipelined (TMA bulk copies, mbarrier) assignment for the passes after the

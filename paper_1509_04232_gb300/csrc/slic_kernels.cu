@@ -132,7 +132,10 @@ __global__ void k_init_rgb(const __grid_constant__ FrameArgs a) {
 __global__ void k_init_batch(const FrameArgs *frames, int n, int total) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= total) return;
-    const int f = find_frame<kCentreBase>(frames, n, g);
+    // one frame lookup per warp, a lane's own only across a frame boundary
+    const int g0 = __shfl_sync(__activemask(), g, 0);
+    int f = find_frame<kCentreBase>(frames, n, g0);
+    if (f + 1 < n && g >= frames[f + 1].centre_base) f = find_frame<kCentreBase>(frames, n, g);
     const FrameArgs &a = frames[f];
     const int k = g - a.centre_base;
     if (a.init) {
@@ -1245,16 +1248,23 @@ cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cud
 // Update: centre = member mean; empty centre keeps position and colour.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void update_centre(long long *ak, const float *ci, float *co, double fix_inv) {
-    const long long n = ak[5];
+// Member mean from the exact integer sums, in FP32 (this GPU's FP64 rate is
+// a small fraction of its FP32 rate): the sum rounded to float, scaled by the
+// power of two fix_inv (exact) and divided by the count (correctly rounded),
+// so within about one unit in the last place of the exact mean.
+__device__ __forceinline__ void update_centre(long long *ak, const float *ci, float *co, float fix_inv) {
+    const longlong2 s01 = *reinterpret_cast<const longlong2 *>(ak);
+    const longlong2 s23 = *reinterpret_cast<const longlong2 *>(ak + 2);
+    const longlong2 s45 = *reinterpret_cast<const longlong2 *>(ak + 4);
+    const long long n = s45.y;
     if (n > 0) {
-        const double inv = 1.0 / (double)n;
-        co[0] = (float)((double)ak[0] * fix_inv * inv);
-        co[1] = (float)((double)ak[1] * fix_inv * inv);
-        co[2] = (float)((double)ak[2] * fix_inv * inv);
-        co[3] = (float)((double)ak[3] * inv);
-        co[4] = (float)((double)ak[4] * inv);
-        co[5] = (float)n;
+        const float fn = (float)n;
+        co[0] = __fdiv_rn((float)s01.x * fix_inv, fn);
+        co[1] = __fdiv_rn((float)s01.y * fix_inv, fn);
+        co[2] = __fdiv_rn((float)s23.x * fix_inv, fn);
+        co[3] = __fdiv_rn((float)s23.y, fn);
+        co[4] = __fdiv_rn((float)s45.x, fn);
+        co[5] = fn;
     } else {
         if (co != ci) {
 #pragma unroll
@@ -1262,11 +1272,13 @@ __device__ __forceinline__ void update_centre(long long *ak, const float *ci, fl
         }
         co[5] = 0.0f;
     }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) ak[c] = 0;
+    longlong2 *az = reinterpret_cast<longlong2 *>(ak);
+    az[0] = make_longlong2(0, 0);
+    az[1] = make_longlong2(0, 0);
+    az[2] = make_longlong2(0, 0);
 }
 
-__global__ void k_update(long long *acc, const float *centres_in, float *centres_out, int K, double fix_inv) {
+__global__ void k_update(long long *acc, const float *centres_in, float *centres_out, int K, float fix_inv) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     update_centre(acc + (size_t)k * 6, centres_in + (size_t)k * 6, centres_out + (size_t)k * 6, fix_inv);
@@ -1275,11 +1287,16 @@ __global__ void k_update(long long *acc, const float *centres_in, float *centres
 __global__ void k_update_batch(const FrameArgs *frames, int n, int total) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= total) return;
-    const int f = find_frame<kCentreBase>(frames, n, g);
+    // Consecutive centres share a frame: one lookup per warp (its first
+    // lane's frame, correct for every lane below the next frame's base),
+    // a lane's own search only across a frame boundary.
+    const int g0 = __shfl_sync(__activemask(), g, 0);
+    int f = find_frame<kCentreBase>(frames, n, g0);
+    if (f + 1 < n && g >= frames[f + 1].centre_base) f = find_frame<kCentreBase>(frames, n, g);
     const FrameArgs &a = frames[f];
     const int kk = g - a.centre_base;
     const size_t k = (size_t)kk * 6;
-    update_centre(a.acc + k, a.centres_out + k, a.centres_out + k, 1.0 / (double)a.fix_scale);
+    update_centre(a.acc + k, a.centres_out + k, a.centres_out + k, 1.0f / a.fix_scale);
     if (a.ctab) {
         const int r = kk / a.ns_c, c = kk - r * a.ns_c;
         write_ctab(a.ctab + ((size_t)(r + 1) * (a.ns_c + 2) + c + 1) * kCtabRec, a.centres_out + k);
@@ -1750,7 +1767,7 @@ int assign_batch_occupancy(bool same, size_t smem) {
     return b2 < b ? b2 : b;
 }
 
-cudaError_t launch_update(long long *acc, const float *centres_in, float *centres_out, int K, double fix_inv,
+cudaError_t launch_update(long long *acc, const float *centres_in, float *centres_out, int K, float fix_inv,
                           cudaStream_t s) {
     k_update<<<(K + 127) / 128, 128, 0, s>>>(acc, centres_in, centres_out, K, fix_inv);
     return cudaGetLastError();
