@@ -486,6 +486,27 @@ def quality_and_learned(args, pkg, images, B, stream, world, dev):
     train_s = time.time() - t0
     net = ws.WarmStartNet(W, H, S, max_batch=B, seed=0, m=M)
     net.set_params(small.params())
+    # The network alone (input channels, four convolutions, labels) on the
+    # whole batch, against the bf16 tensor roofline: the algorithmic work is
+    # 2 * 9 * (14*32 + 32*32 + 32*32 + 32*9) FLOP per pixel.
+    stacked = torch.stack([images[f] for f in range(B)])
+    net_labels = torch.empty((B, H, W), dtype=torch.int32, device=dev)
+    s_handle = int(stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        net.forward(stacked, labels=net_labels, stream=s_handle)
+    torch.cuda.synchronize()
+    gn = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gn, stream=stream):
+        net.forward(stacked, labels=net_labels, stream=s_handle)
+    net_ms = _graph_ms(gn, stream, args, world, dev)
+    flop = 2.0 * 9 * (14 * 32 + 32 * 32 + 32 * 32 + 32 * 9) * B * W * H
+    peaks, peak_kind = measured_peaks()
+    net_tflops = flop / (net_ms / 1e3) / 1e12
+    net_roof = {"ms_per_batch": net_ms, "frames_per_s": B / (net_ms / 1e3), "achieved": net_tflops,
+                "unit": "TFLOP/s", "bound": "tensor", "peak": peaks.get("bf16_tflops"),
+                "frac": net_tflops / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None,
+                "peak_kind": peak_kind, "flop_per_pixel": flop / (B * W * H),
+                "kernels": "mma.sync m16n8k16 bf16 implicit GEMM"}
     learned, learned_fps = {}, {}
     for k in (1, 2):
         lab, _ = ws.warm_start_segment(net, sub, k)
@@ -502,6 +523,7 @@ def quality_and_learned(args, pkg, images, B, stream, world, dev):
             "plain_agreement_by_iterations": plain, "learned_agreement_by_iterations": learned,
             "plain_frames_per_s_at_10_iterations": plain10_fps,
             "learned_frames_per_s_by_iterations": learned_fps,
+            "network_forward": net_roof,
             "learned_reaches_99_percent": any(v >= 0.99 for v in learned.values()),
             "learned_training": {"images": args.train_images, "epochs": args.train_epochs, "seconds": train_s,
                                  "final_loss": hist[-1][1] if hist else None,
