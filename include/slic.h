@@ -303,6 +303,12 @@ slic_status slic_net_gradients(slic_net n, int batch, const uint8_t *d_images, c
 slic_status slic_net_train_step(slic_net n, int batch, const uint8_t *d_images, const uint8_t *d_targets, float lr,
                                 float *d_stats, void *stream);
 
+/* Wait for the device, then report whether a bounded wait inside the
+   network's tensor-core kernels gave up since the last call
+   (SLIC_ERR_TIMEOUT; that forward pass's outputs are then incomplete).
+   Clears the flag. */
+slic_status slic_net_status(slic_net n);
+
 const char *slic_net_last_error(slic_net n);
 
 /* Reason for the last failure on this handle (or of the last failed

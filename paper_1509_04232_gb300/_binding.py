@@ -74,6 +74,7 @@ _SIGNATURES = {
     "slic_net_forward": [_P, _I, _P, _P, _P, _P],
     "slic_net_gradients": [_P, _I, _P, _P, _P, _P],
     "slic_net_train_step": [_P, _I, _P, _P, ctypes.c_float, _P, _P],
+    "slic_net_status": [_P],
 }
 
 
@@ -319,6 +320,11 @@ def slic_net_forward(n: int, batch: int, d_images: int, d_logits: int | None, d_
 def slic_net_gradients(n: int, batch: int, d_images: int, d_targets: int, d_stats: int | None,
                        stream: int = 0) -> None:
     _ncheck(lib().slic_net_gradients(n, batch, d_images, d_targets, d_stats or None, stream or None), n)
+
+
+def slic_net_status(n: int) -> None:
+    """Raises SlicError(SLIC_ERR_TIMEOUT) if a bounded device wait of the network gave up."""
+    _ncheck(lib().slic_net_status(n), n)
 
 
 def slic_net_train_step(n: int, batch: int, d_images: int, d_targets: int, lr: float, d_stats: int | None,

@@ -2,7 +2,9 @@
 // -> 32 -> 9, ReLU between layers, zero padding) that predicts, for every
 // pixel, logits over the 9 cells of its 3x3 cell window (slot t = (dy+1)*3 +
 // (dx+1)). Weights and stored activations are bfloat16, every product sum is
-// accumulated in FP32 on the tensor cores (mma.sync m16n8k16 bf16). Training
+// accumulated in FP32 on the tensor cores: the forward convolutions on
+// tcgen05.mma with tensor-memory accumulators, the backward ones on
+// mma.sync m16n8k16 bf16. Training
 // (softmax cross-entropy against the slots of reference labels, Adam with
 // FP32 master weights) and inference run entirely in the kernels below;
 // the C ABI is at the end of this file and declared in include/slic.h.
@@ -115,88 +117,219 @@ __global__ void k_net_prep(ConvConsts cc, const uint8_t *rgb, int W, int H, int 
 }
 
 // ---------------------------------------------------------------------------
-// Forward convolution (implicit GEMM): out[p][co] = b[co] + sum_{tap,ci}
-// in[p + tap - (1,1)][ci] w[tap][ci][co]. CTA = 4 warps, tile 16 x 4 pixels
-// of one image; warp w computes row w as an m16 x COUT block.
+// Forward convolution on the 5th-generation tensor cores (tcgen05.mma, FP32
+// accumulators in tensor memory). Persistent CTAs of 4 warps; a work tile is
+// 128 consecutive pixels of one image row (the MMA's M = 128), N = COUT
+// output channels, and the K loop runs over the 9 taps x CIN/16 channel
+// chunks of 16 (one MMA each, M128 x N x K16, bf16 x bf16 -> f32).
+//
+// Shared-memory operands use the K-major, unswizzled canonical layout: an
+// 8-row x 16-byte core matrix holds 8 consecutive rows (pixels, or output
+// channels for the weights) of 8 channels. The input tile (3 rows x 130
+// pixels with the 1-pixel halo, zeros outside the image) is stored as planes
+// of 8 channels, pixel after pixel (16 bytes each), so the A operand of tap
+// (dy, dx) is the same layout started (dy * 130 + dx) pixels in: the shift
+// is a 16-byte-aligned start address. Leading-dimension offset (next 8
+// channels) = one plane, stride offset (next 8 pixels) = 128 bytes. The
+// weights [tap][co][ci] are stored the same way, once per CTA.
 // ---------------------------------------------------------------------------
-template <int CIN, int COUT, bool RELU, bool OUTF32>
-__global__ void __launch_bounds__(128) k_conv_fwd(const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const float *bias,
-                                                  void *out, int W, int H) {
-    constexpr int CS = CIN + 8;   // padded channel stride of a shared-memory pixel (bank spread)
-    constexpr int WS = CIN + 8;   // padded ci stride of a weight row
-    __shared__ __align__(16) __nv_bfloat16 in_s[(kTY + 2) * (kTX + 2) * CS];
-    __shared__ __align__(16) __nv_bfloat16 w_s[9 * COUT * WS];
-    __shared__ float b_s[COUT];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int gid = lane >> 2, tig = lane & 3;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, img = blockIdx.z;
-    const size_t base = (size_t)img * H * W;
+constexpr int kTcM = 128;                 // pixels per tile (MMA M)
+constexpr int kTcRow = kTcM + 2;          // staged pixels per input row
+constexpr int kTcPlane = 3 * kTcRow * 16; // bytes of one 8-channel plane of the input tile
+constexpr unsigned kTcWaitPolls = 1u << 20;
 
-    // Stage the input tile with a 1-pixel halo (zeros outside the image) and
-    // the layer's weights, in 32-bit words.
-    for (int i = tid; i < (kTY + 2) * (kTX + 2) * (CIN / 2); i += 128) {
-        const int c2 = i % (CIN / 2), pix = i / (CIN / 2);
-        const int lx = pix % (kTX + 2), ly = pix / (kTX + 2);
-        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        uint32_t v = 0u;
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H)
-            v = *reinterpret_cast<const uint32_t *>(in + (base + (size_t)gy * W + gx) * CIN + 2 * c2);
-        *reinterpret_cast<uint32_t *>(&in_s[pix * CS + 2 * c2]) = v;
+__device__ __forceinline__ unsigned tc_smem(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading
+// (K-direction) and stride (M/N-direction) byte offsets, each >> 4 in 14
+// bits, descriptor version 1 at bit 46, no swizzle.
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr & 0x3FFFFu) >> 4) | ((unsigned long long)((lbo & 0x3FFFFu) >> 4) << 16) |
+           ((unsigned long long)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 D, bf16 A and B (both K-major),
+// N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr unsigned tc_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(unsigned long long *bar, unsigned parity) {
+    for (unsigned i = 0; i < kTcWaitPolls; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(tc_smem(bar)), "r"(parity), "r"(1000u)
+            : "memory");
+        if (done) return true;
     }
-    for (int i = tid; i < 9 * COUT * (CIN / 2); i += 128) {
-        const int c2 = i % (CIN / 2), row = i / (CIN / 2);
-        *reinterpret_cast<uint32_t *>(&w_s[row * WS + 2 * c2]) =
-            *reinterpret_cast<const uint32_t *>(wf + (size_t)row * CIN + 2 * c2);
+    return false;
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (NCOL = 16 or 32).
+template <int NCOL>
+__device__ __forceinline__ void tc_load(unsigned taddr, float (&v)[32]) {
+    unsigned r[32];
+    if constexpr (NCOL == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < NCOL; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int CIN, int COUT, bool RELU, bool OUTF32>
+__global__ void __launch_bounds__(128) k_conv_fwd_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wf,
+                                                     const float *bias, void *out, int W, int H, int n_img,
+                                                     int *err) {
+    constexpr int NP = CIN / 8;                         // input planes of 8 channels
+    constexpr int KC = CIN / 16;                        // K chunks per tap
+    constexpr int IN_BYTES = NP * kTcPlane;
+    constexpr int W_PLANE = COUT * 16;                  // bytes of one 8-channel weight plane
+    constexpr int W_BYTES = 9 * NP * W_PLANE;
+    extern __shared__ __align__(16) unsigned char tc_dyn[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_dyn) + 127) & ~(uintptr_t)127);
+    unsigned char *in_s = sm;
+    unsigned char *w_s = sm + IN_BYTES;
+    float *b_s = reinterpret_cast<float *>(w_s + W_BYTES);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(b_s + COUT);
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // Weights once per CTA: B[tap][co][ci] -> plane (tap * NP + ci / 8), row co.
+    for (int i = tid; i < 9 * COUT * NP; i += 128) {
+        const int pl = i % NP, row = i / NP;  // row = tap * COUT + co
+        const int tap = row / COUT, co = row - tap * COUT;
+        const uint4 v = *reinterpret_cast<const uint4 *>(wf + (size_t)row * CIN + pl * 8);
+        *reinterpret_cast<uint4 *>(w_s + (tap * NP + pl) * W_PLANE + co * 16) = v;
     }
     for (int i = tid; i < COUT; i += 128) b_s[i] = bias[i];
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(tc_smem(tmem_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = *tmem_slot;
+    const unsigned idesc = tc_idesc(kTcM, COUT);
 
-    float acc[COUT / 8][4];
-#pragma unroll
-    for (int n = 0; n < COUT / 8; ++n)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[n][q] = 0.0f;
-
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
-        const __nv_bfloat16 *arow = &in_s[((warp + dy) * (kTX + 2) + dx) * CS];
-#pragma unroll
-        for (int kb = 0; kb < CIN / 16; ++kb) {
-            uint32_t a[4];
-            a[0] = lds32(arow + gid * CS + kb * 16 + 2 * tig);
-            a[1] = lds32(arow + (gid + 8) * CS + kb * 16 + 2 * tig);
-            a[2] = lds32(arow + gid * CS + kb * 16 + 2 * tig + 8);
-            a[3] = lds32(arow + (gid + 8) * CS + kb * 16 + 2 * tig + 8);
-#pragma unroll
-            for (int n = 0; n < COUT / 8; ++n) {
-                const __nv_bfloat16 *brow = &w_s[(tap * COUT + n * 8 + gid) * WS + kb * 16 + 2 * tig];
-                mma16816(acc[n], a, lds32(brow), lds32(brow + 8));
-            }
+    const int tiles_x = (W + kTcM - 1) / kTcM;
+    const long long total = (long long)n_img * H * tiles_x;
+    unsigned phase = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int tx = (int)(t % tiles_x);
+        const long long ry = t / tiles_x;
+        const int y = (int)(ry % H), img = (int)(ry / H);
+        const int x0 = tx * kTcM;
+        const size_t base = (size_t)img * H * W;
+        // Stage rows y-1..y+1, columns x0-1..x0+128: one 16-byte chunk (8
+        // channels of one pixel) per plane entry.
+        for (int i = tid; i < 3 * kTcRow * NP; i += 128) {
+            const int pl = i % NP, pix = i / NP;
+            const int r = pix / kTcRow, c = pix - r * kTcRow;
+            const int gx = x0 + c - 1, gy = y + r - 1;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H)
+                v = *reinterpret_cast<const uint4 *>(in + (base + (size_t)gy * W + gx) * CIN + pl * 8);
+            *reinterpret_cast<uint4 *>(in_s + pl * kTcPlane + pix * 16) = v;
         }
-    }
-
-    const int y = y0 + warp;
+        // generic-proxy stores -> visible to the tensor core
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const unsigned a0 = tc_smem(in_s), b0 = tc_smem(w_s);
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int x = x0 + gid + 8 * half;
-        if (x >= W || y >= H) continue;
-        const size_t px = base + (size_t)y * W + x;
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
-        for (int n = 0; n < COUT / 8; ++n) {
-            const int co = n * 8 + 2 * tig;
-            float v0 = acc[n][2 * half] + b_s[co], v1 = acc[n][2 * half + 1] + b_s[co + 1];
-            if (RELU) {
-                v0 = fmaxf(v0, 0.0f);
-                v1 = fmaxf(v1, 0.0f);
+                for (int kc = 0; kc < KC; ++kc) {
+                    const unsigned long long ad =
+                        tc_desc(a0 + kc * 2 * kTcPlane + (dy * kTcRow + dx) * 16, kTcPlane, 128);
+                    const unsigned long long bd = tc_desc(b0 + (tap * NP + 2 * kc) * W_PLANE, W_PLANE, 128);
+                    const unsigned acc = (tap | kc) != 0 ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
             }
-            if (OUTF32) {
-                *reinterpret_cast<float2 *>(static_cast<float *>(out) + px * COUT + co) = make_float2(v0, v1);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tc_smem(bar))
+                         : "memory");
+        }
+        const bool done = __all_sync(0xffffffffu, tc_wait(bar, phase));
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float v[32];
+        if (done) tc_load<COUT>(tmem + ((unsigned)(warp * 32) << 16), v);
+        // TMEM and the input tile are free for the next tile once every warp
+        // has read; the barrier also makes a timed-out wait CTA-uniform.
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (!__syncthreads_and(done ? 1 : 0)) {
+            if (tid == 0) atomicOr(err, 1);
+            ok = false;
+            break;
+        }
+        const int x = x0 + warp * 32 + lane;
+        if (done && x < W) {
+            const size_t px = base + (size_t)y * W + x;
+            if constexpr (OUTF32) {
+                float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + px * COUT);
+#pragma unroll
+                for (int q = 0; q < COUT / 4; ++q) {
+                    float4 f = make_float4(v[4 * q] + b_s[4 * q], v[4 * q + 1] + b_s[4 * q + 1],
+                                           v[4 * q + 2] + b_s[4 * q + 2], v[4 * q + 3] + b_s[4 * q + 3]);
+                    if (RELU) {
+                        f.x = fmaxf(f.x, 0.0f); f.y = fmaxf(f.y, 0.0f); f.z = fmaxf(f.z, 0.0f); f.w = fmaxf(f.w, 0.0f);
+                    }
+                    o[q] = f;
+                }
             } else {
-                *reinterpret_cast<uint32_t *>(static_cast<__nv_bfloat16 *>(out) + px * COUT + co) = pack_bf16(v0, v1);
+                uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + px * COUT);
+#pragma unroll
+                for (int q = 0; q < COUT / 8; ++q) {
+                    uint32_t w4[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        float lo = v[8 * q + 2 * h] + b_s[8 * q + 2 * h], hi = v[8 * q + 2 * h + 1] + b_s[8 * q + 2 * h + 1];
+                        if (RELU) {
+                            lo = fmaxf(lo, 0.0f);
+                            hi = fmaxf(hi, 0.0f);
+                        }
+                        w4[h] = pack_bf16(lo, hi);
+                    }
+                    o[q] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                }
             }
         }
     }
+    if (!ok) tc_wait(bar, phase ^ 1u);  // a timed-out MMA batch: wait (bounded) once more before freeing TMEM
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
 }
 
 // ---------------------------------------------------------------------------
@@ -519,6 +652,8 @@ struct slic_net_ctx {
     float *partial = nullptr;
     int partial_blocks = 0;
     float *stats = nullptr;
+    int *tc_err = nullptr;   // set by a timed-out wait of the tensor-core convolution
+    int sms = 0;
     ConvConsts conv{};
     std::string err;
     std::vector<void *> allocs;
@@ -550,13 +685,26 @@ bool nalloc(slic_net_ctx *n, T **p, size_t count) {
 
 size_t wcount(int l) { return (size_t)9 * kCinPad[l] * kCoutPad[l]; }
 
-cudaError_t conv_fwd(int l, const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const float *b, void *out, int W, int H,
-                     int n, cudaStream_t s) {
-    const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, n);
-    if (l == 0) k_conv_fwd<16, 32, true, false><<<grid, 128, 0, s>>>(in, wf, b, out, W, H);
-    else if (l < 3) k_conv_fwd<32, 32, true, false><<<grid, 128, 0, s>>>(in, wf, b, out, W, H);
-    else k_conv_fwd<32, 16, false, true><<<grid, 128, 0, s>>>(in, wf, b, out, W, H);
+template <int CIN, int COUT, bool RELU, bool OUTF32>
+cudaError_t conv_fwd_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const float *b, void *out, int W, int H,
+                        int n, int *err, int grid, cudaStream_t s) {
+    const size_t smem = (size_t)(CIN / 8) * kTcPlane + (size_t)9 * (CIN / 8) * COUT * 16 + COUT * 4 + 16 + 128;
+    cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc<CIN, COUT, RELU, OUTF32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)n * H * ((W + kTcM - 1) / kTcM);
+    if (grid > tiles) grid = (int)tiles;
+    k_conv_fwd_tc<CIN, COUT, RELU, OUTF32><<<grid, 128, smem, s>>>(in, wf, b, out, W, H, n, err);
     return cudaGetLastError();
+}
+
+// Layer l of the forward pass on the tensor cores (persistent grid: 4 CTAs per SM).
+cudaError_t conv_fwd(const slic_net_ctx *nc, int l, const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const float *b,
+                     void *out, int W, int H, int n, cudaStream_t s) {
+    const int grid = 4 * nc->sms;
+    if (l == 0) return conv_fwd_tc<16, 32, true, false>(in, wf, b, out, W, H, n, nc->tc_err, grid, s);
+    if (l < 3) return conv_fwd_tc<32, 32, true, false>(in, wf, b, out, W, H, n, nc->tc_err, grid, s);
+    return conv_fwd_tc<32, 16, false, true>(in, wf, b, out, W, H, n, nc->tc_err, grid, s);
 }
 
 slic_status forward_all(slic_net_ctx *n, int batch, const uint8_t *d_images, cudaStream_t s) {
@@ -565,7 +713,7 @@ slic_status forward_all(slic_net_ctx *n, int batch, const uint8_t *d_images, cud
     cudaError_t e = cudaGetLastError();
     for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
         void *out = l < 3 ? static_cast<void *>(n->act[l + 1]) : static_cast<void *>(n->logits);
-        e = conv_fwd(l, n->act[l], n->wf[l], n->b[l], out, n->W, n->H, batch, s);
+        e = conv_fwd(n, l, n->act[l], n->wf[l], n->b[l], out, n->W, n->H, batch, s);
     }
     if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("network forward launch: ") + cudaGetErrorString(e));
     return SLIC_OK;
@@ -642,6 +790,7 @@ slic_status slic_net_create(int max_batch, int width, int height, int S, float m
         return nfail(nullptr, SLIC_ERR_CUDA, std::string("CUDA set-up: ") + cudaGetErrorString(e));
     }
     n->partial_blocks = 2 * sms;
+    n->sms = sms;
     const size_t px = (size_t)width * height * max_batch;
     bool ok = true;
     for (int l = 0; l < kLayers && ok; ++l) {
@@ -652,7 +801,8 @@ slic_status slic_net_create(int max_batch, int width, int height, int S, float m
              nalloc(n, &n->act[l], px * kCinPad[l]);
     }
     ok = ok && nalloc(n, &n->logits, px * 16) && nalloc(n, &n->dzA, px * 32) && nalloc(n, &n->dzB, px * 32) &&
-         nalloc(n, &n->partial, (size_t)n->partial_blocks * 9 * 32 * 32) && nalloc(n, &n->stats, 2);
+         nalloc(n, &n->partial, (size_t)n->partial_blocks * 9 * 32 * 32) && nalloc(n, &n->stats, 2) &&
+         nalloc(n, &n->tc_err, 1) && cudaMemset(n->tc_err, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {
         slic_net_destroy(n);
         return nfail(nullptr, SLIC_ERR_NOMEM, "device allocation for the network failed");
@@ -702,6 +852,17 @@ slic_status slic_net_param_count(slic_net n, size_t *count) {
     size_t c = 0;
     for (int l = 0; l < kLayers; ++l) c += (size_t)9 * kCinReal[l] * kCoutReal[l] + kCoutReal[l];
     *count = c;
+    return SLIC_OK;
+}
+
+slic_status slic_net_status(slic_net n) {
+    if (!n) return nfail(nullptr, SLIC_ERR_INVALID, "NULL network");
+    int flag = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && flag) e = cudaMemset(n->tc_err, 0, sizeof(int));
+    if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+    if (flag) return nfail(n, SLIC_ERR_TIMEOUT, "a bounded wait in the tensor-core convolution timed out");
     return SLIC_OK;
 }
 

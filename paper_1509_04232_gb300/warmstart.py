@@ -77,6 +77,10 @@ class WarmStartNet:
         B.slic_net_gradients(self.handle, images.shape[0], images.data_ptr(), targets.data_ptr(),
                              stats.data_ptr() if stats is not None else None, stream)
 
+    def status(self):
+        """Raises SlicError(SLIC_ERR_TIMEOUT) if a bounded wait of the tensor-core kernels gave up."""
+        B.slic_net_status(self.handle)
+
     def train_step(self, images, targets, lr: float, stats=None, stream: int = 0):
         B.slic_net_train_step(self.handle, images.shape[0], images.data_ptr(), targets.data_ptr(), lr,
                               stats.data_ptr() if stats is not None else None, stream)

@@ -47,6 +47,7 @@ def test_forward_matches_oracle(slic_gpu):
     labels = torch.empty((2, 40, 48), dtype=torch.int32, device="cuda")
     net.forward(imgs, logits=logits, labels=labels)
     torch.cuda.synchronize()
+    net.status()
     params = _split(net.params())
     for i in range(2):
         ref, _ = NO.forward(_oracle_input(host[i], 8), params, bf16=True)
@@ -60,6 +61,22 @@ def test_forward_matches_oracle(slic_gpu):
         want = NO.labels_from_slots(np.argmax(z, axis=-1), 8)
         assert np.all((labels[i].cpu().numpy() == want) | ~clear)
         assert np.all(logits[i].cpu().numpy()[..., 9:] == 0.0)
+
+
+def test_forward_spans_several_tensor_core_tiles(slic_gpu):
+    """A 300-pixel-wide image: rows of three 128-pixel tensor-core tiles, the
+    last one ragged, in a batch of two."""
+    import torch
+    net, host, imgs = _setup(slic_gpu, n=2, W=300, H=21, S=12, seed=5)
+    logits = torch.empty((2, 21, 300, 16), dtype=torch.float32, device="cuda")
+    net.forward(imgs, logits=logits)
+    torch.cuda.synchronize()
+    net.status()
+    params = _split(net.params())
+    for i in range(2):
+        ref, _ = NO.forward(_oracle_input(host[i], 12), params, bf16=True)
+        got = logits[i].cpu().numpy()[..., :9]
+        assert np.max(np.abs(got - ref)) <= 2e-2 * max(1.0, np.abs(ref).max())
 
 
 def test_gradients_match_oracle(slic_gpu):
