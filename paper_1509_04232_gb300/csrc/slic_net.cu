@@ -74,35 +74,55 @@ __device__ __forceinline__ uint32_t lds_pair(const __nv_bfloat16 *p) {
 // 9 slots of the pixel's cell window the Eq. (1) distance D/100 to the
 // grid-initialised centre of that cell (2.0 off the grid), zero padding.
 // ---------------------------------------------------------------------------
-__global__ void k_net_prep(ConvConsts cc, const uint8_t *rgb, int W, int H, int C, int S, float w,
-                           __nv_bfloat16 *x0) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, b = blockIdx.z;
-    if (x >= W) return;
+__global__ void __launch_bounds__(128) k_net_prep(ConvConsts cc, const uint8_t *rgb, int W, int H, int C, int S,
+                                                  float w, __nv_bfloat16 *x0) {
+    // A block covers 128 pixels of one row; the grid centres of the cells its
+    // pixels see (three cell rows, the covered cell columns +- 1) are
+    // converted once into shared memory instead of once per pixel and slot.
+    constexpr int kMaxCols = 128 + 3;
+    __shared__ float cen[3][kMaxCols][5];  // L, a, b, x, y of a grid centre (x < 0: off the grid)
+    const int x0p = blockIdx.x * blockDim.x, y = blockIdx.y, b = blockIdx.z;
     const size_t img = (size_t)b * H * W;
-    const size_t px = img + (size_t)y * W + x;
-    const uint8_t *p = rgb + px * C;
-    float f0, f1, f2;
-    convert_pixel(cc, p[0], p[1], p[2], g_lut_net, f0, f1, f2);
-    float ch[16];
-    ch[0] = f0 / 100.0f;
-    ch[1] = f1 / 128.0f;
-    ch[2] = f2 / 128.0f;
-    ch[3] = (float)(x % S) / (float)S;
-    ch[4] = (float)(y % S) / (float)S;
-    const int cx = x / S, cy = y / S, ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        const int nx = cx + t % 3 - 1, ny = cy + t / 3 - 1;
-        float d = 2.0f;
+    const int ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
+    const int cy = y / S, cx_lo = x0p / S - 1;
+    const int cx_hi = min(x0p + (int)blockDim.x - 1, W - 1) / S + 1;
+    const int ncols = cx_hi - cx_lo + 1;
+    for (int i = threadIdx.x; i < 3 * ncols; i += blockDim.x) {
+        const int r = i / ncols, c = i - r * ncols;
+        const int nx = cx_lo + c, ny = cy + r - 1;
+        float *e = cen[r][c];
         if (nx >= 0 && nx < ns_c && ny >= 0 && ny < ns_r) {
             // grid initialisation of Sec. 3: midpoint of the in-image cell, colour under it
             const int xf = nx * S, xl = min((nx + 1) * S, W) - 1, yf = ny * S, yl = min((ny + 1) * S, H) - 1;
             const uint8_t *q = rgb + (img + (size_t)((yf + yl) >> 1) * W + ((xf + xl) >> 1)) * C;
-            float k0, k1, k2;
-            convert_pixel(cc, q[0], q[1], q[2], g_lut_net, k0, k1, k2);
-            const float dl = k0 - f0, da = k1 - f1, db = k2 - f2;
-            const float dx = 0.5f * (float)(xf + xl) - (float)x, dy = 0.5f * (float)(yf + yl) - (float)y;
+            convert_pixel(cc, q[0], q[1], q[2], g_lut_net, e[0], e[1], e[2]);
+            e[3] = 0.5f * (float)(xf + xl);
+            e[4] = 0.5f * (float)(yf + yl);
+        } else {
+            e[3] = -1.0f;
+        }
+    }
+    __syncthreads();
+    const int x = x0p + threadIdx.x;
+    if (x >= W) return;
+    const size_t px = img + (size_t)y * W + x;
+    const uint8_t *p = rgb + px * C;
+    float f0, f1, f2;
+    convert_pixel(cc, p[0], p[1], p[2], g_lut_net, f0, f1, f2);
+    const int cx = x / S;
+    float ch[16];
+    ch[0] = f0 / 100.0f;
+    ch[1] = f1 / 128.0f;
+    ch[2] = f2 / 128.0f;
+    ch[3] = (float)(x - cx * S) / (float)S;
+    ch[4] = (float)(y - cy * S) / (float)S;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        const float *e = cen[t / 3][cx + t % 3 - 1 - cx_lo];
+        float d = 2.0f;
+        if (e[3] >= 0.0f) {
+            const float dl = e[0] - f0, da = e[1] - f1, db = e[2] - f2;
+            const float dx = e[3] - (float)x, dy = e[4] - (float)y;
             d = (sqrtf(dl * dl + da * da + db * db) + w * sqrtf(dx * dx + dy * dy)) / 100.0f;
         }
         ch[5 + t] = d;
@@ -194,10 +214,20 @@ __device__ __forceinline__ void tc_load(unsigned taddr, float (&v)[32]) {
     for (int i = 0; i < NCOL; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int CIN, int COUT, bool RELU, bool OUTF32>
+// ---------------------------------------------------------------------------
+// Loss: masked softmax over the in-grid slots, cross-entropy against the
+// target slot; writes dL/dlogits = (p - onehot) / n_total as bf16 [p][16]
+// and accumulates the loss sum and the number of correct argmaxes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool slot_valid(int t, int cx, int cy, int ns_c, int ns_r) {
+    const int nx = cx + t % 3 - 1, ny = cy + t / 3 - 1;
+    return nx >= 0 && nx < ns_c && ny >= 0 && ny < ns_r;
+}
+
+template <int CIN, int COUT, bool RELU, bool OUTF32, bool LABELS>
 __global__ void __launch_bounds__(128) k_conv_fwd_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wf,
                                                      const float *bias, void *out, int W, int H, int n_img,
-                                                     int *err) {
+                                                     int S, int *err) {
     constexpr int NP = CIN / 8;                         // input planes of 8 channels
     constexpr int KC = CIN / 16;                        // K chunks per tap
     constexpr int IN_BYTES = NP * kTcPlane;
@@ -297,7 +327,22 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(const __nv_bfloat16 *in, co
         const int x = x0 + warp * 32 + lane;
         if (done && x < W) {
             const size_t px = base + (size_t)y * W + x;
-            if constexpr (OUTF32) {
+            if constexpr (LABELS) {
+                // argmax of the valid slots' logits (first maximum in slot
+                // order), as the stand-alone label kernel on stored logits
+                const int cx = x / S, cy = y / S, ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
+                float mx = -INFINITY;
+                int arg = 4;
+#pragma unroll
+                for (int t = 0; t < 9; ++t) {
+                    const float l = v[t] + b_s[t];
+                    if (slot_valid(t, cx, cy, ns_c, ns_r) && l > mx) {
+                        mx = l;
+                        arg = t;
+                    }
+                }
+                static_cast<int32_t *>(out)[px] = (cy + arg / 3 - 1) * ns_c + cx + arg % 3 - 1;
+            } else if constexpr (OUTF32) {
                 float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + px * COUT);
 #pragma unroll
                 for (int q = 0; q < COUT / 4; ++q) {
@@ -515,15 +560,6 @@ __global__ void k_bias_grad(const __nv_bfloat16 *dz, long long n_px, float *db) 
     if (threadIdx.x < COUT) atomicAdd(&db[threadIdx.x], s[threadIdx.x]);
 }
 
-// ---------------------------------------------------------------------------
-// Loss: masked softmax over the in-grid slots, cross-entropy against the
-// target slot; writes dL/dlogits = (p - onehot) / n_total as bf16 [p][16]
-// and accumulates the loss sum and the number of correct argmaxes.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool slot_valid(int t, int cx, int cy, int ns_c, int ns_r) {
-    const int nx = cx + t % 3 - 1, ny = cy + t / 3 - 1;
-    return nx >= 0 && nx < ns_c && ny >= 0 && ny < ns_r;
-}
 
 __global__ void k_softmax_ce(const float *logits, const uint8_t *target, int W, int H, int n_img, int S,
                              float inv_total, __nv_bfloat16 *dz, float *stats) {
@@ -685,35 +721,41 @@ bool nalloc(slic_net_ctx *n, T **p, size_t count) {
 
 size_t wcount(int l) { return (size_t)9 * kCinPad[l] * kCoutPad[l]; }
 
-template <int CIN, int COUT, bool RELU, bool OUTF32>
+template <int CIN, int COUT, bool RELU, bool OUTF32, bool LABELS>
 cudaError_t conv_fwd_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const float *b, void *out, int W, int H,
-                        int n, int *err, int grid, cudaStream_t s) {
+                        int n, int S, int *err, int grid, cudaStream_t s) {
     const size_t smem = (size_t)(CIN / 8) * kTcPlane + (size_t)9 * (CIN / 8) * COUT * 16 + COUT * 4 + 16 + 128;
-    cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc<CIN, COUT, RELU, OUTF32>,
+    cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc<CIN, COUT, RELU, OUTF32, LABELS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)n * H * ((W + kTcM - 1) / kTcM);
     if (grid > tiles) grid = (int)tiles;
-    k_conv_fwd_tc<CIN, COUT, RELU, OUTF32><<<grid, 128, smem, s>>>(in, wf, b, out, W, H, n, err);
+    k_conv_fwd_tc<CIN, COUT, RELU, OUTF32, LABELS><<<grid, 128, smem, s>>>(in, wf, b, out, W, H, n, S, err);
     return cudaGetLastError();
 }
 
-// Layer l of the forward pass on the tensor cores (persistent grid: 4 CTAs per SM).
+// Layer l of the forward pass on the tensor cores (persistent grid: 4 CTAs
+// per SM). With `labels`, the last layer writes each pixel's label (argmax
+// of its valid slots) instead of its logits.
 cudaError_t conv_fwd(const slic_net_ctx *nc, int l, const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const float *b,
-                     void *out, int W, int H, int n, cudaStream_t s) {
+                     void *out, int W, int H, int n, bool labels, cudaStream_t s) {
     const int grid = 4 * nc->sms;
-    if (l == 0) return conv_fwd_tc<16, 32, true, false>(in, wf, b, out, W, H, n, nc->tc_err, grid, s);
-    if (l < 3) return conv_fwd_tc<32, 32, true, false>(in, wf, b, out, W, H, n, nc->tc_err, grid, s);
-    return conv_fwd_tc<32, 16, false, true>(in, wf, b, out, W, H, n, nc->tc_err, grid, s);
+    if (l == 0) return conv_fwd_tc<16, 32, true, false, false>(in, wf, b, out, W, H, n, nc->S, nc->tc_err, grid, s);
+    if (l < 3) return conv_fwd_tc<32, 32, true, false, false>(in, wf, b, out, W, H, n, nc->S, nc->tc_err, grid, s);
+    if (labels) return conv_fwd_tc<32, 16, false, false, true>(in, wf, b, out, W, H, n, nc->S, nc->tc_err, grid, s);
+    return conv_fwd_tc<32, 16, false, true, false>(in, wf, b, out, W, H, n, nc->S, nc->tc_err, grid, s);
 }
 
-slic_status forward_all(slic_net_ctx *n, int batch, const uint8_t *d_images, cudaStream_t s) {
+// Forward pass into n->logits, or, with labels_out, straight to labels.
+slic_status forward_all(slic_net_ctx *n, int batch, const uint8_t *d_images, cudaStream_t s,
+                        int32_t *labels_out = nullptr) {
     const dim3 pg((n->W + 127) / 128, n->H, batch);
     k_net_prep<<<pg, 128, 0, s>>>(n->conv, d_images, n->W, n->H, 3, n->S, n->m / (float)n->S, n->act[0]);
     cudaError_t e = cudaGetLastError();
     for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
-        void *out = l < 3 ? static_cast<void *>(n->act[l + 1]) : static_cast<void *>(n->logits);
-        e = conv_fwd(n, l, n->act[l], n->wf[l], n->b[l], out, n->W, n->H, batch, s);
+        void *out = l < 3 ? static_cast<void *>(n->act[l + 1])
+                          : (labels_out ? static_cast<void *>(labels_out) : static_cast<void *>(n->logits));
+        e = conv_fwd(n, l, n->act[l], n->wf[l], n->b[l], out, n->W, n->H, batch, labels_out != nullptr, s);
     }
     if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("network forward launch: ") + cudaGetErrorString(e));
     return SLIC_OK;
@@ -921,6 +963,7 @@ slic_status slic_net_forward(slic_net n, int batch, const uint8_t *d_images, flo
     if (!n) return nfail(nullptr, SLIC_ERR_INVALID, "NULL network");
     if (batch <= 0 || batch > n->max_batch || !d_images) return nfail(n, SLIC_ERR_INVALID, "bad batch or images");
     cudaStream_t s = (cudaStream_t)stream;
+    if (d_labels && !d_logits) return forward_all(n, batch, d_images, s, d_labels);  // labels fused into the last layer
     slic_status st = forward_all(n, batch, d_images, s);
     if (st != SLIC_OK) return st;
     const long long n_px = (long long)n->W * n->H * batch;

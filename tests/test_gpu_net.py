@@ -79,6 +79,21 @@ def test_forward_spans_several_tensor_core_tiles(slic_gpu):
         assert np.max(np.abs(got - ref)) <= 2e-2 * max(1.0, np.abs(ref).max())
 
 
+def test_fused_labels_equal_labels_from_logits(slic_gpu):
+    """The labels-only forward (argmax fused into the last tensor-core layer)
+    gives the labels computed from the stored logits."""
+    import torch
+    net, host, imgs = _setup(slic_gpu, n=2, W=300, H=37, S=12, seed=6)
+    logits = torch.empty((2, 37, 300, 16), dtype=torch.float32, device="cuda")
+    want = torch.empty((2, 37, 300), dtype=torch.int32, device="cuda")
+    got = torch.empty_like(want)
+    net.forward(imgs, logits=logits, labels=want)
+    net.forward(imgs, labels=got)
+    torch.cuda.synchronize()
+    net.status()
+    assert torch.equal(got, want)
+
+
 def test_gradients_match_oracle(slic_gpu):
     import torch
     net, host, imgs = _setup(slic_gpu)
