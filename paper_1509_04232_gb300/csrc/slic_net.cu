@@ -230,16 +230,16 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(const __nv_bfloat16 *in, co
                                                      int S, int *err) {
     constexpr int NP = CIN / 8;                         // input planes of 8 channels
     constexpr int KC = CIN / 16;                        // K chunks per tap
-    constexpr int IN_BYTES = NP * kTcPlane;
+    constexpr int IN_BYTES = NP * kTcPlane;             // one input stage
     constexpr int W_PLANE = COUT * 16;                  // bytes of one 8-channel weight plane
     constexpr int W_BYTES = 9 * NP * W_PLANE;
     extern __shared__ __align__(16) unsigned char tc_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_dyn) + 127) & ~(uintptr_t)127);
-    unsigned char *in_s = sm;
-    unsigned char *w_s = sm + IN_BYTES;
+    unsigned char *in_s = sm;                           // two stages
+    unsigned char *w_s = sm + 2 * IN_BYTES;
     float *b_s = reinterpret_cast<float *>(w_s + W_BYTES);
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(b_s + COUT);
-    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bar + 1);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(b_s + COUT);  // [2]: MMAs of a TMEM buffer done
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bar + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // Weights once per CTA: B[tap][co][ci] -> plane (tap * NP + ci / 8), row co.
@@ -251,11 +251,14 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(const __nv_bfloat16 *in, co
     }
     for (int i = tid; i < COUT; i += 128) b_s[i] = bias[i];
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&bar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(tc_smem(tmem_slot)));
+        // two accumulator buffers of 32 columns: the MMAs of one tile run while
+        // the previous tile's accumulators are read out
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(tc_smem(tmem_slot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -263,118 +266,168 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(const __nv_bfloat16 *in, co
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tmem_slot;
     const unsigned idesc = tc_idesc(kTcM, COUT);
-
     const int tiles_x = (W + kTcM - 1) / kTcM;
     const long long total = (long long)n_img * H * tiles_x;
-    unsigned phase = 0;
-    bool ok = true;
-    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+
+    // Asynchronous copy of tile t's input (rows y-1..y+1, columns x0-1..x0+128,
+    // zeros outside the image) into a stage: one 16-byte chunk (8 channels of
+    // one pixel) per plane entry.
+    auto load_tile = [&](long long t, unsigned char *dst) {
         const int tx = (int)(t % tiles_x);
         const long long ry = t / tiles_x;
         const int y = (int)(ry % H), img = (int)(ry / H);
         const int x0 = tx * kTcM;
         const size_t base = (size_t)img * H * W;
-        // Stage rows y-1..y+1, columns x0-1..x0+128: one 16-byte chunk (8
-        // channels of one pixel) per plane entry.
         for (int i = tid; i < 3 * kTcRow * NP; i += 128) {
             const int pl = i % NP, pix = i / NP;
             const int r = pix / kTcRow, c = pix - r * kTcRow;
             const int gx = x0 + c - 1, gy = y + r - 1;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H)
-                v = *reinterpret_cast<const uint4 *>(in + (base + (size_t)gy * W + gx) * CIN + pl * 8);
-            *reinterpret_cast<uint4 *>(in_s + pl * kTcPlane + pix * 16) = v;
+            const bool inside = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            const __nv_bfloat16 *src = inside ? in + (base + (size_t)gy * W + gx) * CIN + pl * 8 : in;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc_smem(dst + pl * kTcPlane + pix * 16)),
+                         "l"(src), "r"(inside ? 16 : 0)
+                         : "memory");
         }
-        // generic-proxy stores -> visible to the tensor core
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // Nine taps x KC chunks of M128 x N x K16 into accumulator buffer `buf`,
+    // completion on bar[buf].
+    auto issue_mma = [&](const unsigned char *src, int buf) {
+        const unsigned a0 = tc_smem(src), b0 = tc_smem(w_s), d = tmem + (unsigned)(buf * 32);
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+            for (int kc = 0; kc < KC; ++kc) {
+                const unsigned long long ad = tc_desc(a0 + kc * 2 * kTcPlane + (dy * kTcRow + dx) * 16, kTcPlane, 128);
+                const unsigned long long bd = tc_desc(b0 + (tap * NP + 2 * kc) * W_PLANE, W_PLANE, 128);
+                const unsigned acc = (tap | kc) != 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         tc_smem(&bar[buf]))
+                     : "memory");
+    };
+    // Bias, activation and store of tile t from accumulator buffer `buf`
+    // (already loaded into v by this warp: its 32 pixels).
+    auto store_tile = [&](long long t, const float (&v)[32]) {
+        const int tx = (int)(t % tiles_x);
+        const long long ry = t / tiles_x;
+        const int y = (int)(ry % H), img = (int)(ry / H);
+        const int x = tx * kTcM + warp * 32 + lane;
+        if (x >= W) return;
+        const size_t px = (size_t)img * H * W + (size_t)y * W + x;
+        if constexpr (LABELS) {
+            // argmax of the valid slots' logits (first maximum in slot
+            // order), as the stand-alone label kernel on stored logits
+            const int cx = x / S, cy = y / S, ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
+            float mx = -INFINITY;
+            int arg = 4;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const float l = v[q] + b_s[q];
+                if (slot_valid(q, cx, cy, ns_c, ns_r) && l > mx) {
+                    mx = l;
+                    arg = q;
+                }
+            }
+            static_cast<int32_t *>(out)[px] = (cy + arg / 3 - 1) * ns_c + cx + arg % 3 - 1;
+        } else if constexpr (OUTF32) {
+            float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + px * COUT);
+#pragma unroll
+            for (int q = 0; q < COUT / 4; ++q) {
+                float4 f = make_float4(v[4 * q] + b_s[4 * q], v[4 * q + 1] + b_s[4 * q + 1],
+                                       v[4 * q + 2] + b_s[4 * q + 2], v[4 * q + 3] + b_s[4 * q + 3]);
+                if (RELU) {
+                    f.x = fmaxf(f.x, 0.0f); f.y = fmaxf(f.y, 0.0f); f.z = fmaxf(f.z, 0.0f); f.w = fmaxf(f.w, 0.0f);
+                }
+                o[q] = f;
+            }
+        } else {
+            uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + px * COUT);
+#pragma unroll
+            for (int q = 0; q < COUT / 8; ++q) {
+                uint32_t w4[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    float lo = v[8 * q + 2 * h] + b_s[8 * q + 2 * h], hi = v[8 * q + 2 * h + 1] + b_s[8 * q + 2 * h + 1];
+                    if (RELU) {
+                        lo = fmaxf(lo, 0.0f);
+                        hi = fmaxf(hi, 0.0f);
+                    }
+                    w4[h] = pack_bf16(lo, hi);
+                }
+                o[q] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
+        }
+    };
+
+    // Tile j (global tile blockIdx.x + j * gridDim.x) uses input stage j & 1
+    // and accumulator buffer j & 1. Iteration j: wait for its input, issue
+    // its MMAs, wait for tile j-1's MMAs, start loading tile j+1 into the
+    // stage tile j-1 used, then read out and store tile j-1.
+    unsigned phase = 0;    // bit b: parity of bar[b]'s next completion
+    unsigned pending = 0;  // bit b: MMAs committed to bar[b] not yet waited for
+    bool ok = true;
+    const long long t0 = blockIdx.x;
+    if (t0 < total) load_tile(t0, in_s);
+    int j = 0;
+    for (long long t = t0; t < total; t += gridDim.x, ++j) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // copies -> visible to the tensor core
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-            const unsigned a0 = tc_smem(in_s), b0 = tc_smem(w_s);
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap % 3;
-#pragma unroll
-                for (int kc = 0; kc < KC; ++kc) {
-                    const unsigned long long ad =
-                        tc_desc(a0 + kc * 2 * kTcPlane + (dy * kTcRow + dx) * 16, kTcPlane, 128);
-                    const unsigned long long bd = tc_desc(b0 + (tap * NP + 2 * kc) * W_PLANE, W_PLANE, 128);
-                    const unsigned acc = (tap | kc) != 0 ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             tc_smem(bar))
-                         : "memory");
-        }
-        const bool done = __all_sync(0xffffffffu, tc_wait(bar, phase));
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) issue_mma(in_s + (j & 1) * IN_BYTES, j & 1);
+        pending |= 1u << (j & 1);
         float v[32];
-        if (done) tc_load<COUT>(tmem + ((unsigned)(warp * 32) << 16), v);
-        // TMEM and the input tile are free for the next tile once every warp
-        // has read; the barrier also makes a timed-out wait CTA-uniform.
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (!__syncthreads_and(done ? 1 : 0)) {
+        bool have_prev = false;
+        if (j > 0) {
+            const int pb = (j - 1) & 1;
+            const bool done = __all_sync(0xffffffffu, tc_wait(&bar[pb], (phase >> pb) & 1u));
+            if (!__syncthreads_and(done ? 1 : 0)) {
+                if (tid == 0) atomicOr(err, 1);
+                ok = false;
+                break;
+            }
+            phase ^= 1u << pb;
+            pending &= ~(1u << pb);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_load<COUT>(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(pb * 32), v);
+            have_prev = true;
+        }
+        if (t + gridDim.x < total) load_tile(t + gridDim.x, in_s + ((j + 1) & 1) * IN_BYTES);
+        if (have_prev) store_tile(t - gridDim.x, v);
+    }
+    // the last tile
+    if (ok && j > 0) {
+        const int pb = (j - 1) & 1;
+        const bool done = __all_sync(0xffffffffu, tc_wait(&bar[pb], (phase >> pb) & 1u));
+        if (__syncthreads_and(done ? 1 : 0)) {
+            phase ^= 1u << pb;
+            pending &= ~(1u << pb);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float v[32];
+            tc_load<COUT>(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(pb * 32), v);
+            store_tile(t0 + (long long)(j - 1) * gridDim.x, v);
+        } else {
             if (tid == 0) atomicOr(err, 1);
             ok = false;
-            break;
-        }
-        const int x = x0 + warp * 32 + lane;
-        if (done && x < W) {
-            const size_t px = base + (size_t)y * W + x;
-            if constexpr (LABELS) {
-                // argmax of the valid slots' logits (first maximum in slot
-                // order), as the stand-alone label kernel on stored logits
-                const int cx = x / S, cy = y / S, ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
-                float mx = -INFINITY;
-                int arg = 4;
-#pragma unroll
-                for (int t = 0; t < 9; ++t) {
-                    const float l = v[t] + b_s[t];
-                    if (slot_valid(t, cx, cy, ns_c, ns_r) && l > mx) {
-                        mx = l;
-                        arg = t;
-                    }
-                }
-                static_cast<int32_t *>(out)[px] = (cy + arg / 3 - 1) * ns_c + cx + arg % 3 - 1;
-            } else if constexpr (OUTF32) {
-                float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + px * COUT);
-#pragma unroll
-                for (int q = 0; q < COUT / 4; ++q) {
-                    float4 f = make_float4(v[4 * q] + b_s[4 * q], v[4 * q + 1] + b_s[4 * q + 1],
-                                           v[4 * q + 2] + b_s[4 * q + 2], v[4 * q + 3] + b_s[4 * q + 3]);
-                    if (RELU) {
-                        f.x = fmaxf(f.x, 0.0f); f.y = fmaxf(f.y, 0.0f); f.z = fmaxf(f.z, 0.0f); f.w = fmaxf(f.w, 0.0f);
-                    }
-                    o[q] = f;
-                }
-            } else {
-                uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + px * COUT);
-#pragma unroll
-                for (int q = 0; q < COUT / 8; ++q) {
-                    uint32_t w4[4];
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        float lo = v[8 * q + 2 * h] + b_s[8 * q + 2 * h], hi = v[8 * q + 2 * h + 1] + b_s[8 * q + 2 * h + 1];
-                        if (RELU) {
-                            lo = fmaxf(lo, 0.0f);
-                            hi = fmaxf(hi, 0.0f);
-                        }
-                        w4[h] = pack_bf16(lo, hi);
-                    }
-                    o[q] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-                }
-            }
         }
     }
-    if (!ok) tc_wait(bar, phase ^ 1u);  // a timed-out MMA batch: wait (bounded) once more before freeing TMEM
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!ok) {
+        // a timed-out MMA batch: wait (bounded) once more before freeing TMEM
+        if (pending & 1u) tc_wait(&bar[0], phase & 1u);
+        if (pending & 2u) tc_wait(&bar[1], (phase >> 1) & 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
 }
 
 // ---------------------------------------------------------------------------
@@ -724,7 +777,7 @@ size_t wcount(int l) { return (size_t)9 * kCinPad[l] * kCoutPad[l]; }
 template <int CIN, int COUT, bool RELU, bool OUTF32, bool LABELS>
 cudaError_t conv_fwd_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const float *b, void *out, int W, int H,
                         int n, int S, int *err, int grid, cudaStream_t s) {
-    const size_t smem = (size_t)(CIN / 8) * kTcPlane + (size_t)9 * (CIN / 8) * COUT * 16 + COUT * 4 + 16 + 128;
+    const size_t smem = (size_t)2 * (CIN / 8) * kTcPlane + (size_t)9 * (CIN / 8) * COUT * 16 + COUT * 4 + 24 + 128;
     cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc<CIN, COUT, RELU, OUTF32, LABELS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -734,12 +787,12 @@ cudaError_t conv_fwd_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const 
     return cudaGetLastError();
 }
 
-// Layer l of the forward pass on the tensor cores (persistent grid: 4 CTAs
-// per SM). With `labels`, the last layer writes each pixel's label (argmax
+// Layer l of the forward pass on the tensor cores (persistent grid: 3 CTAs
+// per SM, as the two input stages allow). With `labels`, the last layer writes each pixel's label (argmax
 // of its valid slots) instead of its logits.
 cudaError_t conv_fwd(const slic_net_ctx *nc, int l, const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const float *b,
                      void *out, int W, int H, int n, bool labels, cudaStream_t s) {
-    const int grid = 4 * nc->sms;
+    const int grid = 3 * nc->sms;
     if (l == 0) return conv_fwd_tc<16, 32, true, false, false>(in, wf, b, out, W, H, n, nc->S, nc->tc_err, grid, s);
     if (l < 3) return conv_fwd_tc<32, 32, true, false, false>(in, wf, b, out, W, H, n, nc->S, nc->tc_err, grid, s);
     if (labels) return conv_fwd_tc<32, 16, false, false, true>(in, wf, b, out, W, H, n, nc->S, nc->tc_err, grid, s);
