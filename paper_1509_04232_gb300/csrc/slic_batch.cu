@@ -65,8 +65,10 @@ slic_status bfail(slic_batch_ctx *b, slic_status st, const std::string &msg) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+}  // namespace
+
 // cuTensorMapEncodeTiled from the driver, found once through the runtime.
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+PFN_cuTensorMapEncodeTiled_v12000 slicgb::tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static bool tried = false;
     if (!tried) {
@@ -82,6 +84,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     }
     return fn;
 }
+
+namespace {
 
 // Tensor maps of one frame for the pipelined assignment: the features as a
 // [3][H][P] f32 tensor copied in 32x32x3 boxes, and the padded centre table

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 namespace slicgb {
@@ -125,6 +126,10 @@ int assign_max_window(int S, int ns_c, int ns_r);
 bool assign_direct_acc(int win_n);
 // Resident CTAs per SM of the batched assignment kernel.
 int assign_batch_occupancy(bool same, size_t smem);
+
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point
+// query, once); nullptr if the driver does not provide it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 // Host helpers shared by the C-ABI files: colour constants of a feature
 // space, and the once-per-device set-up (sRGB table, shared-memory limit).

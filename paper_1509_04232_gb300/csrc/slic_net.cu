@@ -60,6 +60,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+// max(lo, 0) and max(hi, 0) rounded to bf16 in one conversion (hi in the
+// upper half).
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 __device__ __forceinline__ uint32_t lds32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
 // Two bf16 that may not be 4-byte aligned.
@@ -138,24 +146,31 @@ __global__ void __launch_bounds__(128) k_net_prep(ConvConsts cc, const uint8_t *
 
 // ---------------------------------------------------------------------------
 // Forward convolution on the 5th-generation tensor cores (tcgen05.mma, FP32
-// accumulators in tensor memory). Persistent CTAs of 4 warps; a work tile is
-// 128 consecutive pixels of one image row (the MMA's M = 128), N = COUT
-// output channels, and the K loop runs over the 9 taps x CIN/16 channel
-// chunks of 16 (one MMA each, M128 x N x K16, bf16 x bf16 -> f32).
+// accumulators in tensor memory), warp-specialised: one warp copies input
+// tiles with the tensor-memory accelerator (TMA), one issues the MMAs, and
+// the epilogue warps read the accumulators out (bias, activation, store).
+// The roles meet on mbarrier rings: NS input stages (full / empty) and two
+// accumulator buffers (full / empty).
 //
-// Shared-memory operands use the K-major, unswizzled canonical layout: an
-// 8-row x 16-byte core matrix holds 8 consecutive rows (pixels, or output
-// channels for the weights) of 8 channels. The input tile (3 rows x 130
-// pixels with the 1-pixel halo, zeros outside the image) is stored as planes
-// of 8 channels, pixel after pixel (16 bytes each), so the A operand of tap
-// (dy, dx) is the same layout started (dy * 130 + dx) pixels in: the shift
-// is a 16-byte-aligned start address. Leading-dimension offset (next 8
-// channels) = one plane, stride offset (next 8 pixels) = 128 bytes. The
-// weights [tap][co][ci] are stored the same way, once per CTA.
+// A work tile is 120 output pixels of one image row, 30 per TMEM lane
+// quarter (epilogue warp q % 4). Quarter q's 32 MMA rows (positions) are
+// x0-1+30q .. x0+30+30q, so the 30 outputs of a quarter need only its own
+// rows; all CIN channels of a position form one row of CIN*2 bytes, copied
+// with the 32-byte (CIN 16) or 64-byte (CIN 32) swizzle, zeros outside the
+// image (the zero padding). For each kernel row dy one MMA chunk (M 128
+// positions x N 3*COUT x K16) takes all three horizontal taps at once:
+// column dx*COUT + co of the accumulator row of position q holds
+// sum_dy,ci in[y+dy-1][q][ci] * w[dy][dx][co][ci], and the output at x is
+// the sum over dx of column block dx at position x-1+dx (neighbouring lanes
+// of one warp: two shuffles). Three times the N of a tap-by-tap loop, so
+// each A row read from shared memory feeds three times the MACs. Weights
+// [dy][dx*COUT+co][ci] use the K-major unswizzled canonical layout (8-row x
+// 16-byte core matrices, leading offset = one 8-channel plane), staged once
+// per CTA.
 // ---------------------------------------------------------------------------
-constexpr int kTcM = 128;                 // pixels per tile (MMA M)
-constexpr int kTcRow = kTcM + 2;          // staged pixels per input row
-constexpr int kTcPlane = 3 * kTcRow * 16; // bytes of one 8-channel plane of the input tile
+constexpr int kTcOut = 120;               // output pixels per tile
+constexpr int kTcIn = 128;                // MMA rows (positions) per tile
+constexpr int kTcSeg = 30;                // outputs per lane quarter
 constexpr unsigned kTcWaitPolls = 1u << 20;
 
 __device__ __forceinline__ unsigned tc_smem(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -166,6 +181,14 @@ __device__ __forceinline__ unsigned tc_smem(const void *p) { return (unsigned)__
 __device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo) {
     return (unsigned long long)((addr & 0x3FFFFu) >> 4) | ((unsigned long long)((lbo & 0x3FFFFu) >> 4) << 16) |
            ((unsigned long long)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+
+// The same for a K-major operand whose rows (CIN*2 bytes) carry the 32- or
+// 64-byte swizzle (layout type at bit 61: 6 or 4); the leading offset is
+// unused there (one MMA's 32 bytes of K lie within a row).
+__device__ __forceinline__ unsigned long long tc_desc_sw(unsigned addr, unsigned sbo, unsigned long long layout) {
+    return (unsigned long long)((addr & 0x3FFFFu) >> 4) | (1ull << 16) |
+           ((unsigned long long)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46) | (layout << 61);
 }
 
 // kind::f16 instruction descriptor: FP32 D, bf16 A and B (both K-major),
@@ -189,9 +212,10 @@ __device__ __forceinline__ bool tc_wait(unsigned long long *bar, unsigned parity
     return false;
 }
 
-// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (NCOL = 16 or 32).
+// NCOL (16 or 32) consecutive FP32 columns of this warp's 32 TMEM lanes,
+// without the wait (tcgen05.wait::ld follows a batch of these).
 template <int NCOL>
-__device__ __forceinline__ void tc_load(unsigned taddr, float (&v)[32]) {
+__device__ __forceinline__ void tc_ld_cols(unsigned taddr, float *v) {
     unsigned r[32];
     if constexpr (NCOL == 32) {
         asm volatile(
@@ -209,7 +233,6 @@ __device__ __forceinline__ void tc_load(unsigned taddr, float (&v)[32]) {
               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
             : "r"(taddr));
     }
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < NCOL; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -224,210 +247,294 @@ __device__ __forceinline__ bool slot_valid(int t, int cx, int cy, int ns_c, int 
     return nx >= 0 && nx < ns_c && ny >= 0 && ny < ns_r;
 }
 
-template <int CIN, int COUT, bool RELU, bool OUTF32, bool LABELS>
-__global__ void __launch_bounds__(128) k_conv_fwd_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wf,
-                                                     const float *bias, void *out, int W, int H, int n_img,
-                                                     int S, int *err) {
-    constexpr int NP = CIN / 8;                         // input planes of 8 channels
-    constexpr int KC = CIN / 16;                        // K chunks per tap
-    constexpr int IN_BYTES = NP * kTcPlane;             // one input stage
-    constexpr int W_PLANE = COUT * 16;                  // bytes of one 8-channel weight plane
-    constexpr int W_BYTES = 9 * NP * W_PLANE;
+// Shared memory of one forward-convolution CTA (plus 1 KB for aligning the
+// stages to the swizzle pattern), its TMEM columns and epilogue warps (each
+// takes 16 output channels of one lane quarter).
+__host__ __device__ constexpr int tc_box_bytes(int cin) { return 3 * kTcIn * cin * 2; }
+__host__ __device__ constexpr int tc_buf_cols(int cout) { return 3 * cout <= 64 ? 64 : 128; }
+__host__ __device__ constexpr int tc_epi_warps(int cout) { return cout / 16 * 4; }
+__host__ __device__ constexpr int tc_smem_bytes(int cin, int cout, bool staged, int ns) {
+    return 1024 + ns * tc_box_bytes(cin) + 3 * (cin / 8) * 3 * cout * 16 + (staged ? tc_epi_warps(cout) * 32 * 32 : 0) +
+           (2 * ns + 5) * 8 + 16;
+}
+
+// Bounded mbarrier wait that also gives up once another role has aborted.
+__device__ __forceinline__ bool tc_wait_ab(unsigned long long *bar, unsigned parity, const volatile int *abort) {
+    for (unsigned i = 0; i < kTcWaitPolls; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(tc_smem(bar)), "r"(parity), "r"(1000u)
+            : "memory");
+        if (done) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem(bar)) : "memory");
+}
+
+template <int CIN, int COUT, bool RELU, bool OUTF32, bool LABELS, int NS>
+__global__ void __launch_bounds__((tc_epi_warps(COUT) + 2) * 32) k_conv_fwd_tc(
+    const __grid_constant__ CUtensorMap in_map, const __nv_bfloat16 *wf, const float *bias, void *out, int W, int H,
+    int n_img, int S, int *err) {
+    constexpr int NP = CIN / 8;                   // 8-channel planes
+    constexpr int KC = CIN / 16;                  // K chunks per kernel row
+    constexpr int ROWB = CIN * 2;                 // bytes of one staged position
+    constexpr unsigned BOX = tc_box_bytes(CIN);   // bytes of one stage (12 copies of 32 positions)
+    constexpr int NN = 3 * COUT;                  // MMA N: three horizontal taps x COUT
+    constexpr int W_PLANE = NN * 16;              // bytes of one 8-channel weight plane
+    constexpr int W_BYTES = 3 * NP * W_PLANE;
+    constexpr unsigned long long LAYOUT = CIN == 32 ? 4ull : 6ull;  // 64- or 32-byte swizzle
+    constexpr bool STAGED = !OUTF32 && !LABELS;   // bf16 activations leave through shared memory
+    constexpr int BUFC = tc_buf_cols(COUT);       // TMEM columns per accumulator buffer
+    constexpr int EW = tc_epi_warps(COUT);        // epilogue warps: 16 channels x one lane quarter each
+    constexpr int NT = (EW + 2) * 32;
+    constexpr int PRODUCER = EW, ISSUER = EW + 1; // warp roles
+    static_assert(BOX % 1024 == 0, "stages must keep the swizzle pattern aligned");
+    static_assert(!STAGED || COUT == 32, "staged stores assume 64-byte output pixels");
     extern __shared__ __align__(16) unsigned char tc_dyn[];
-    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_dyn) + 127) & ~(uintptr_t)127);
-    unsigned char *in_s = sm;                           // two stages
-    unsigned char *w_s = sm + 2 * IN_BYTES;
-    float *b_s = reinterpret_cast<float *>(w_s + W_BYTES);
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(b_s + COUT);  // [2]: MMAs of a TMEM buffer done
-    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bar + 2);
+    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_dyn) + 1023) & ~(uintptr_t)1023);
+    unsigned char *in_s = sm;                     // [NS][dy][128 positions][ROWB]
+    unsigned char *w_s = in_s + NS * BOX;
+    unsigned char *o_s = w_s + W_BYTES;           // [EW][32 pixels][32 bytes] when STAGED
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(o_s + (STAGED ? EW * 32 * 32 : 0));
+    unsigned long long *empty = full + NS;
+    unsigned long long *tfull = empty + NS;       // [2] accumulators ready
+    unsigned long long *tempty = tfull + 2;       // [2] accumulators read out (EW warps)
+    unsigned long long *done = tempty + 2;        // every MMA of this CTA complete
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(done + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // Weights once per CTA: B[tap][co][ci] -> plane (tap * NP + ci / 8), row co.
-    for (int i = tid; i < 9 * COUT * NP; i += 128) {
-        const int pl = i % NP, row = i / NP;  // row = tap * COUT + co
-        const int tap = row / COUT, co = row - tap * COUT;
-        const uint4 v = *reinterpret_cast<const uint4 *>(wf + (size_t)row * CIN + pl * 8);
-        *reinterpret_cast<uint4 *>(w_s + (tap * NP + pl) * W_PLANE + co * 16) = v;
+    // Weights once per CTA: plane (dy, ci / 8), row dx * COUT + co holds
+    // w[dy][dx][co][ci .. ci+7] (global [tap][co][ci], tap = dy * 3 + dx).
+    for (int i = tid; i < 3 * NN * NP; i += NT) {
+        const int pl = i % NP, r = i / NP;  // r = dy * NN + dx * COUT + co
+        const int dy = r / NN, n = r - dy * NN;
+        const uint4 v = *reinterpret_cast<const uint4 *>(wf + (size_t)r * CIN + pl * 8);
+        *reinterpret_cast<uint4 *>(w_s + (dy * NP + pl) * W_PLANE + n * 16) = v;
     }
-    for (int i = tid; i < COUT; i += 128) b_s[i] = bias[i];
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&bar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&bar[1])));
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&in_map)) : "memory");
+        for (int i = 0; i < 2 * NS; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&full[i])));
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&tfull[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&tempty[i])), "n"(EW));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(done)));
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
-        // two accumulator buffers of 32 columns: the MMAs of one tile run while
-        // the previous tile's accumulators are read out
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(tc_smem(tmem_slot)));
+    if (warp == ISSUER) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(tmem_slot)),
+                     "n"(2 * BUFC));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    // generic-proxy writes (weights) -> visible to the tensor core
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tmem_slot;
-    const unsigned idesc = tc_idesc(kTcM, COUT);
-    const int tiles_x = (W + kTcM - 1) / kTcM;
-    const long long total = (long long)n_img * H * tiles_x;
+    const unsigned tiles_x = (unsigned)((W + kTcOut - 1) / kTcOut);
+    const unsigned total = (unsigned)n_img * (unsigned)H * tiles_x;  // < 2^31 (pixels < 2^31)
+    const unsigned G = gridDim.x;
+    auto fail = [&]() {
+        *abort = 1;
+        atomicOr(err, 1);
+    };
 
-    // Asynchronous copy of tile t's input (rows y-1..y+1, columns x0-1..x0+128,
-    // zeros outside the image) into a stage: one 16-byte chunk (8 channels of
-    // one pixel) per plane entry.
-    auto load_tile = [&](long long t, unsigned char *dst) {
-        const int tx = (int)(t % tiles_x);
-        const long long ry = t / tiles_x;
-        const int y = (int)(ry % H), img = (int)(ry / H);
-        const int x0 = tx * kTcM;
-        const size_t base = (size_t)img * H * W;
-        for (int i = tid; i < 3 * kTcRow * NP; i += 128) {
-            const int pl = i % NP, pix = i / NP;
-            const int r = pix / kTcRow, c = pix - r * kTcRow;
-            const int gx = x0 + c - 1, gy = y + r - 1;
-            const bool inside = gx >= 0 && gx < W && gy >= 0 && gy < H;
-            const __nv_bfloat16 *src = inside ? in + (base + (size_t)gy * W + gx) * CIN + pl * 8 : in;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc_smem(dst + pl * kTcPlane + pix * 16)),
-                         "l"(src), "r"(inside ? 16 : 0)
-                         : "memory");
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    // Nine taps x KC chunks of M128 x N x K16 into accumulator buffer `buf`,
-    // completion on bar[buf].
-    auto issue_mma = [&](const unsigned char *src, int buf) {
-        const unsigned a0 = tc_smem(src), b0 = tc_smem(w_s), d = tmem + (unsigned)(buf * 32);
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int dy = tap / 3, dx = tap % 3;
-#pragma unroll
-            for (int kc = 0; kc < KC; ++kc) {
-                const unsigned long long ad = tc_desc(a0 + kc * 2 * kTcPlane + (dy * kTcRow + dx) * 16, kTcPlane, 128);
-                const unsigned long long bd = tc_desc(b0 + (tap * NP + 2 * kc) * W_PLANE, W_PLANE, 128);
-                const unsigned acc = (tap | kc) != 0 ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         tc_smem(&bar[buf]))
-                     : "memory");
-    };
-    // Bias, activation and store of tile t from accumulator buffer `buf`
-    // (already loaded into v by this warp: its 32 pixels).
-    auto store_tile = [&](long long t, const float (&v)[32]) {
-        const int tx = (int)(t % tiles_x);
-        const long long ry = t / tiles_x;
-        const int y = (int)(ry % H), img = (int)(ry / H);
-        const int x = tx * kTcM + warp * 32 + lane;
-        if (x >= W) return;
-        const size_t px = (size_t)img * H * W + (size_t)y * W + x;
-        if constexpr (LABELS) {
-            // argmax of the valid slots' logits (first maximum in slot
-            // order), as the stand-alone label kernel on stored logits
-            const int cx = x / S, cy = y / S, ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
-            float mx = -INFINITY;
-            int arg = 4;
-#pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                const float l = v[q] + b_s[q];
-                if (slot_valid(q, cx, cy, ns_c, ns_r) && l > mx) {
-                    mx = l;
-                    arg = q;
+    if (warp == PRODUCER) {
+        // ---- producer: 12 tensor-map copies (4 quarters x 3 rows) per stage ----
+        if (lane == 0) {
+            int s = 0;
+            unsigned u = 0;       // completed rounds of the ring
+            unsigned issued = 0;  // bit s: a copy was issued into stage s
+            unsigned lastpar = 0; // bit s: parity of that copy's completion
+            for (unsigned t = blockIdx.x; t < total; t += G) {
+                if (u > 0 && !tc_wait_ab(&empty[s], (u - 1) & 1u, abort)) {
+                    fail();
+                    break;
                 }
-            }
-            static_cast<int32_t *>(out)[px] = (cy + arg / 3 - 1) * ns_c + cx + arg % 3 - 1;
-        } else if constexpr (OUTF32) {
-            float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + px * COUT);
+                const unsigned tx = t % tiles_x, ry = t / tiles_x;
+                const int y = (int)(ry % (unsigned)H), img = (int)(ry / (unsigned)H);
+                const unsigned b = tc_smem(&full[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(BOX) : "memory");
+                const unsigned dst0 = tc_smem(in_s + s * BOX);
 #pragma unroll
-            for (int q = 0; q < COUT / 4; ++q) {
-                float4 f = make_float4(v[4 * q] + b_s[4 * q], v[4 * q + 1] + b_s[4 * q + 1],
-                                       v[4 * q + 2] + b_s[4 * q + 2], v[4 * q + 3] + b_s[4 * q + 3]);
-                if (RELU) {
-                    f.x = fmaxf(f.x, 0.0f); f.y = fmaxf(f.y, 0.0f); f.z = fmaxf(f.z, 0.0f); f.w = fmaxf(f.w, 0.0f);
-                }
-                o[q] = f;
-            }
-        } else {
-            uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + px * COUT);
+                for (int dy = 0; dy < 3; ++dy) {
 #pragma unroll
-            for (int q = 0; q < COUT / 8; ++q) {
-                uint32_t w4[4];
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    float lo = v[8 * q + 2 * h] + b_s[8 * q + 2 * h], hi = v[8 * q + 2 * h + 1] + b_s[8 * q + 2 * h + 1];
-                    if (RELU) {
-                        lo = fmaxf(lo, 0.0f);
-                        hi = fmaxf(hi, 0.0f);
+                    for (int q = 0; q < 4; ++q) {
+                        asm volatile(
+                            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+                            "{%2, %3, %4, %5}], [%6];" ::"r"(dst0 + (unsigned)((dy * kTcIn + 32 * q) * ROWB)),
+                            "l"(reinterpret_cast<uint64_t>(&in_map)), "r"(0),
+                            "r"((int)tx * kTcOut - 1 + kTcSeg * q), "r"(y + dy - 1), "r"(img), "r"(b)
+                            : "memory");
                     }
-                    w4[h] = pack_bf16(lo, hi);
                 }
-                o[q] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                issued |= 1u << s;
+                lastpar = (lastpar & ~(1u << s)) | ((u & 1u) << s);
+                if (++s == NS) {
+                    s = 0;
+                    ++u;
+                }
             }
+            // every copy lands before the shared memory is released
+            for (int k = 0; k < NS; ++k)
+                if (issued & (1u << k)) tc_wait(&full[k], (lastpar >> k) & 1u);
         }
-    };
-
-    // Tile j (global tile blockIdx.x + j * gridDim.x) uses input stage j & 1
-    // and accumulator buffer j & 1. Iteration j: wait for its input, issue
-    // its MMAs, wait for tile j-1's MMAs, start loading tile j+1 into the
-    // stage tile j-1 used, then read out and store tile j-1.
-    unsigned phase = 0;    // bit b: parity of bar[b]'s next completion
-    unsigned pending = 0;  // bit b: MMAs committed to bar[b] not yet waited for
-    bool ok = true;
-    const long long t0 = blockIdx.x;
-    if (t0 < total) load_tile(t0, in_s);
-    int j = 0;
-    for (long long t = t0; t < total; t += gridDim.x, ++j) {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // copies -> visible to the tensor core
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) issue_mma(in_s + (j & 1) * IN_BYTES, j & 1);
-        pending |= 1u << (j & 1);
-        float v[32];
-        bool have_prev = false;
-        if (j > 0) {
-            const int pb = (j - 1) & 1;
-            const bool done = __all_sync(0xffffffffu, tc_wait(&bar[pb], (phase >> pb) & 1u));
-            if (!__syncthreads_and(done ? 1 : 0)) {
-                if (tid == 0) atomicOr(err, 1);
-                ok = false;
+    } else if (warp == ISSUER) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            const unsigned idesc = tc_idesc(kTcIn, NN);
+            int s = 0;
+            unsigned u = 0, j = 0;
+            for (unsigned t = blockIdx.x; t < total; t += G, ++j) {
+                const int bf = (int)(j & 1u);
+                if (!tc_wait_ab(&full[s], u & 1u, abort) ||
+                    (j >= 2 && !tc_wait_ab(&tempty[bf], ((j >> 1) - 1) & 1u, abort))) {
+                    fail();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned a0 = tc_smem(in_s + s * BOX), b0 = tc_smem(w_s), d = tmem + (unsigned)(bf * BUFC);
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) {
+#pragma unroll
+                    for (int kc = 0; kc < KC; ++kc) {
+                        const unsigned long long ad = tc_desc_sw(a0 + dy * kTcIn * ROWB + kc * 32, 8 * ROWB, LAYOUT);
+                        const unsigned long long bd = tc_desc(b0 + (dy * NP + 2 * kc) * W_PLANE, W_PLANE, 128);
+                        const unsigned acc = (dy | kc) != 0 ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 tc_smem(&tfull[bf]))
+                             : "memory");
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 tc_smem(&empty[s]))
+                             : "memory");
+                if (++s == NS) {
+                    s = 0;
+                    ++u;
+                }
+            }
+            // all MMAs (and their commits) complete before TMEM is released
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tc_smem(done))
+                         : "memory");
+            tc_wait(done, 0);
+        }
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31, channels 16*(w/4) .. +15 ----
+        const int quarter = warp & 3, c0 = (warp >> 2) * 16;
+        float bv[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) bv[c] = c0 + c < COUT ? bias[c0 + c] : 0.0f;
+        unsigned j = 0;
+        for (unsigned t = blockIdx.x; t < total; t += G, ++j) {
+            const int bf = (int)(j & 1u);
+            if (!__all_sync(0xffffffffu, tc_wait_ab(&tfull[bf], (j >> 1) & 1u, abort))) {
+                if (lane == 0) fail();
                 break;
             }
-            phase ^= 1u << pb;
-            pending &= ~(1u << pb);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            tc_load<COUT>(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(pb * 32), v);
-            have_prev = true;
+            float d0[32], d1[32], d2[32];
+            const unsigned ta = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(bf * BUFC + c0);
+            tc_ld_cols<16>(ta, d0);
+            tc_ld_cols<16>(ta + COUT, d1);
+            tc_ld_cols<16>(ta + 2 * COUT, d2);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tc_arrive(&tempty[bf]);
+            // output of lane l (l < 30): positions l, l+1, l+2 of this quarter
+            float v[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                v[c] = (d0[c] + bv[c]) + __shfl_down_sync(0xffffffffu, d1[c], 1) +
+                       __shfl_down_sync(0xffffffffu, d2[c], 2);
+
+            const unsigned tx = t % tiles_x, ry = t / tiles_x;
+            const int y = (int)(ry % (unsigned)H), img = (int)(ry / (unsigned)H);
+            const int xw = (int)tx * kTcOut + kTcSeg * quarter;  // output pixel of lane 0
+            const size_t row0 = (size_t)img * H * W + (size_t)y * W;
+            if constexpr (STAGED) {
+                // Each lane packs its pixel's 32 bytes (16 channels) into the
+                // warp's staging rows (16-byte chunks swizzled by pixel
+                // group, conflict-free); then each store instruction writes
+                // 16 whole 32-byte sectors.
+                unsigned char *ow = o_s + warp * (32 * 32);
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    uint32_t w4[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) w4[h] = RELU ? pack_bf16_relu(v[8 * k + 2 * h], v[8 * k + 2 * h + 1])
+                                                             : pack_bf16(v[8 * k + 2 * h], v[8 * k + 2 * h + 1]);
+                    *reinterpret_cast<uint4 *>(ow + lane * 32 + ((k ^ ((lane >> 2) & 1)) << 4)) =
+                        make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                }
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int pp = i * 16 + (lane >> 1), k = lane & 1;
+                    const uint4 c = *reinterpret_cast<const uint4 *>(ow + pp * 32 + ((k ^ ((pp >> 2) & 1)) << 4));
+                    if (pp < kTcSeg && xw + pp < W)
+                        *reinterpret_cast<uint4 *>(static_cast<unsigned char *>(out) + (row0 + xw + pp) * 64 + c0 * 2 +
+                                                   k * 16) = c;
+                }
+                __syncwarp();
+            } else {
+                const int x = xw + lane;
+                if (lane < kTcSeg && x < W) {
+                    const size_t px = row0 + x;
+                    if constexpr (LABELS) {
+                        // argmax of the valid slots' logits (first maximum in
+                        // slot order), as the stand-alone label kernel on
+                        // stored logits
+                        const int cx = x / S, cy = y / S, ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
+                        float mx = -INFINITY;
+                        int arg = 4;
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) {
+                            if (slot_valid(q, cx, cy, ns_c, ns_r) && v[q] > mx) {
+                                mx = v[q];
+                                arg = q;
+                            }
+                        }
+                        static_cast<int32_t *>(out)[px] = (cy + arg / 3 - 1) * ns_c + cx + arg % 3 - 1;
+                    } else {
+                        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + px * COUT + c0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float4 f = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                            if (RELU) {
+                                f.x = fmaxf(f.x, 0.0f); f.y = fmaxf(f.y, 0.0f); f.z = fmaxf(f.z, 0.0f); f.w = fmaxf(f.w, 0.0f);
+                            }
+                            o[q] = f;
+                        }
+                    }
+                }
+            }
         }
-        if (t + gridDim.x < total) load_tile(t + gridDim.x, in_s + ((j + 1) & 1) * IN_BYTES);
-        if (have_prev) store_tile(t - gridDim.x, v);
-    }
-    // the last tile
-    if (ok && j > 0) {
-        const int pb = (j - 1) & 1;
-        const bool done = __all_sync(0xffffffffu, tc_wait(&bar[pb], (phase >> pb) & 1u));
-        if (__syncthreads_and(done ? 1 : 0)) {
-            phase ^= 1u << pb;
-            pending &= ~(1u << pb);
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            float v[32];
-            tc_load<COUT>(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(pb * 32), v);
-            store_tile(t0 + (long long)(j - 1) * gridDim.x, v);
-        } else {
-            if (tid == 0) atomicOr(err, 1);
-            ok = false;
-        }
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (!ok) {
-        // a timed-out MMA batch: wait (bounded) once more before freeing TMEM
-        if (pending & 1u) tc_wait(&bar[0], phase & 1u);
-        if (pending & 2u) tc_wait(&bar[1], (phase >> 1) & 1u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == ISSUER) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(2 * BUFC));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -742,6 +849,9 @@ struct slic_net_ctx {
     int partial_blocks = 0;
     float *stats = nullptr;
     int *tc_err = nullptr;   // set by a timed-out wait of the tensor-core convolution
+    // act[l] as a [max_batch][H][W][Cin_p] bf16 tensor, copied in 32 x Cin_p boxes
+    // (32- or 64-byte swizzle) by the forward convolution of layer l
+    CUtensorMap in_map[kLayers] = {};
     int sms = 0;
     ConvConsts conv{};
     std::string err;
@@ -774,29 +884,37 @@ bool nalloc(slic_net_ctx *n, T **p, size_t count) {
 
 size_t wcount(int l) { return (size_t)9 * kCinPad[l] * kCoutPad[l]; }
 
-template <int CIN, int COUT, bool RELU, bool OUTF32, bool LABELS>
-cudaError_t conv_fwd_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const float *b, void *out, int W, int H,
-                        int n, int S, int *err, int grid, cudaStream_t s) {
-    const size_t smem = (size_t)2 * (CIN / 8) * kTcPlane + (size_t)9 * (CIN / 8) * COUT * 16 + COUT * 4 + 24 + 128;
-    cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc<CIN, COUT, RELU, OUTF32, LABELS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int CIN, int COUT, bool RELU, bool OUTF32, bool LABELS, int NS>
+cudaError_t conv_fwd_tc(const CUtensorMap &in_map, const __nv_bfloat16 *wf, const float *b, void *out, int W, int H,
+                        int n, int S, int *err, int sms, cudaStream_t s) {
+    auto kern = k_conv_fwd_tc<CIN, COUT, RELU, OUTF32, LABELS, NS>;
+    const int smem = tc_smem_bytes(CIN, COUT, !OUTF32 && !LABELS, NS);
+    const int threads = (tc_epi_warps(COUT) + 2) * 32;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return e;
-    const long long tiles = (long long)n * H * ((W + kTcM - 1) / kTcM);
-    if (grid > tiles) grid = (int)tiles;
-    k_conv_fwd_tc<CIN, COUT, RELU, OUTF32, LABELS><<<grid, 128, smem, s>>>(in, wf, b, out, W, H, n, S, err);
+    // persistent grid: as many CTAs as fit, TMEM (512 columns per SM) included
+    const int tmem_cap = 512 / (2 * tc_buf_cols(COUT));
+    per_sm = per_sm < 1 ? 1 : (per_sm > tmem_cap ? tmem_cap : per_sm);
+    const long long tiles = (long long)n * H * ((W + kTcOut - 1) / kTcOut);
+    const int grid = (int)(tiles < (long long)per_sm * sms ? tiles : (long long)per_sm * sms);
+    kern<<<grid, threads, smem, s>>>(in_map, wf, b, out, W, H, n, S, err);
     return cudaGetLastError();
 }
 
-// Layer l of the forward pass on the tensor cores (persistent grid: 3 CTAs
-// per SM, as the two input stages allow). With `labels`, the last layer writes each pixel's label (argmax
-// of its valid slots) instead of its logits.
-cudaError_t conv_fwd(const slic_net_ctx *nc, int l, const __nv_bfloat16 *in, const __nv_bfloat16 *wf, const float *b,
-                     void *out, int W, int H, int n, bool labels, cudaStream_t s) {
-    const int grid = 3 * nc->sms;
-    if (l == 0) return conv_fwd_tc<16, 32, true, false, false>(in, wf, b, out, W, H, n, nc->S, nc->tc_err, grid, s);
-    if (l < 3) return conv_fwd_tc<32, 32, true, false, false>(in, wf, b, out, W, H, n, nc->S, nc->tc_err, grid, s);
-    if (labels) return conv_fwd_tc<32, 16, false, false, true>(in, wf, b, out, W, H, n, nc->S, nc->tc_err, grid, s);
-    return conv_fwd_tc<32, 16, false, true, false>(in, wf, b, out, W, H, n, nc->S, nc->tc_err, grid, s);
+// Layer l of the forward pass on the tensor cores, reading its input through
+// the layer's tensor map. With `labels`, the last layer writes each pixel's
+// label (argmax of its valid slots) instead of its logits.
+cudaError_t conv_fwd(const slic_net_ctx *nc, int l, const __nv_bfloat16 *wf, const float *b, void *out, int W, int H,
+                     int n, bool labels, cudaStream_t s) {
+    const CUtensorMap &m = nc->in_map[l];
+    if (l == 0) return conv_fwd_tc<16, 32, true, false, false, 4>(m, wf, b, out, W, H, n, nc->S, nc->tc_err, nc->sms, s);
+    if (l < 3) return conv_fwd_tc<32, 32, true, false, false, 3>(m, wf, b, out, W, H, n, nc->S, nc->tc_err, nc->sms, s);
+    if (labels)
+        return conv_fwd_tc<32, 16, false, false, true, 3>(m, wf, b, out, W, H, n, nc->S, nc->tc_err, nc->sms, s);
+    return conv_fwd_tc<32, 16, false, true, false, 3>(m, wf, b, out, W, H, n, nc->S, nc->tc_err, nc->sms, s);
 }
 
 // Forward pass into n->logits, or, with labels_out, straight to labels.
@@ -808,7 +926,7 @@ slic_status forward_all(slic_net_ctx *n, int batch, const uint8_t *d_images, cud
     for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
         void *out = l < 3 ? static_cast<void *>(n->act[l + 1])
                           : (labels_out ? static_cast<void *>(labels_out) : static_cast<void *>(n->logits));
-        e = conv_fwd(n, l, n->act[l], n->wf[l], n->b[l], out, n->W, n->H, batch, labels_out != nullptr, s);
+        e = conv_fwd(n, l, n->wf[l], n->b[l], out, n->W, n->H, batch, labels_out != nullptr, s);
     }
     if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("network forward launch: ") + cudaGetErrorString(e));
     return SLIC_OK;
@@ -901,6 +1019,21 @@ slic_status slic_net_create(int max_batch, int width, int height, int S, float m
     if (!ok) {
         slic_net_destroy(n);
         return nfail(nullptr, SLIC_ERR_NOMEM, "device allocation for the network failed");
+    }
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    for (int l = 0; l < kLayers && ok; ++l) {
+        const cuuint64_t c = (cuuint64_t)kCinPad[l];
+        const cuuint64_t dims[4] = {c, (cuuint64_t)width, (cuuint64_t)height, (cuuint64_t)max_batch};
+        const cuuint64_t strides[3] = {c * 2, c * 2 * width, c * 2 * width * height};
+        const cuuint32_t box[4] = {(cuuint32_t)c, 32, 1, 1};
+        const cuuint32_t ones[4] = {1, 1, 1, 1};
+        ok = enc && enc(&n->in_map[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, n->act[l], dims, strides, box, ones,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, c == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    if (!ok) {
+        slic_net_destroy(n);
+        return nfail(nullptr, SLIC_ERR_CUDA, "tensor maps of the network activations could not be encoded");
     }
     // He-normal initialisation of the real weights (FP32 master), zero biases
     // and moments; padding stays zero.
