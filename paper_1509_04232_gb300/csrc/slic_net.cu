@@ -20,6 +20,7 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -892,12 +893,24 @@ cudaError_t conv_fwd_tc(const CUtensorMap &in_map, const __nv_bfloat16 *wf, cons
     const int threads = (tc_epi_warps(COUT) + 2) * 32;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    int per_sm = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    // Persistent grid: as many CTAs per SM as registers (256-register warp
+    // granules), shared memory (with the per-CTA reservation), warps and
+    // TMEM (512 columns) allow.
+    cudaFuncAttributes fa{};
+    int dev = 0, smem_sm = 0, smem_res = 0, regs_sm = 0, warps_sm = 0;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&warps_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
     if (e != cudaSuccess) return e;
-    // persistent grid: as many CTAs as fit, TMEM (512 columns per SM) included
-    const int tmem_cap = 512 / (2 * tc_buf_cols(COUT));
-    per_sm = per_sm < 1 ? 1 : (per_sm > tmem_cap ? tmem_cap : per_sm);
+    const int warps = threads / 32, warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+    int per_sm = 512 / (2 * tc_buf_cols(COUT));
+    per_sm = std::min(per_sm, smem_sm / (smem + smem_res));
+    per_sm = std::min(per_sm, regs_sm / (warp_regs * warps));
+    per_sm = std::min(per_sm, warps_sm / 32 / warps);
+    per_sm = std::max(per_sm, 1);
     const long long tiles = (long long)n * H * ((W + kTcOut - 1) / kTcOut);
     const int grid = (int)(tiles < (long long)per_sm * sms ? tiles : (long long)per_sm * sms);
     kern<<<grid, threads, smem, s>>>(in_map, wf, b, out, W, H, n, S, err);
