@@ -78,6 +78,14 @@ __device__ __forceinline__ uint32_t lds_pair(const __nv_bfloat16 *p) {
     return lo | (hi << 16);
 }
 
+// Square root on the hardware approximation (relative error ~2^-22, far
+// below the bf16 rounding of the channels).
+__device__ __forceinline__ float sqrt_fast(float v) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // Input channels: L/100, a/128, b/128, (x mod S)/S, (y mod S)/S, then for the
 // 9 slots of the pixel's cell window the Eq. (1) distance D/100 to the
@@ -89,7 +97,8 @@ __global__ void __launch_bounds__(128) k_net_prep(ConvConsts cc, const uint8_t *
     // pixels see (three cell rows, the covered cell columns +- 1) are
     // converted once into shared memory instead of once per pixel and slot.
     constexpr int kMaxCols = 128 + 3;
-    __shared__ float cen[3][kMaxCols][5];  // L, a, b, x, y of a grid centre (x < 0: off the grid)
+    __shared__ float4 cen_lab[3][kMaxCols];  // L, a, b, x of a grid centre
+    __shared__ float cen_y[3][kMaxCols];     // y (< 0: off the grid)
     const int x0p = blockIdx.x * blockDim.x, y = blockIdx.y, b = blockIdx.z;
     const size_t img = (size_t)b * H * W;
     const int ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
@@ -99,16 +108,17 @@ __global__ void __launch_bounds__(128) k_net_prep(ConvConsts cc, const uint8_t *
     for (int i = threadIdx.x; i < 3 * ncols; i += blockDim.x) {
         const int r = i / ncols, c = i - r * ncols;
         const int nx = cx_lo + c, ny = cy + r - 1;
-        float *e = cen[r][c];
         if (nx >= 0 && nx < ns_c && ny >= 0 && ny < ns_r) {
             // grid initialisation of Sec. 3: midpoint of the in-image cell, colour under it
             const int xf = nx * S, xl = min((nx + 1) * S, W) - 1, yf = ny * S, yl = min((ny + 1) * S, H) - 1;
             const uint8_t *q = rgb + (img + (size_t)((yf + yl) >> 1) * W + ((xf + xl) >> 1)) * C;
-            convert_pixel(cc, q[0], q[1], q[2], g_lut_net, e[0], e[1], e[2]);
-            e[3] = 0.5f * (float)(xf + xl);
-            e[4] = 0.5f * (float)(yf + yl);
+            float l, a2, b2;
+            convert_pixel(cc, q[0], q[1], q[2], g_lut_net, l, a2, b2);
+            cen_lab[r][c] = make_float4(l, a2, b2, 0.5f * (float)(xf + xl));
+            cen_y[r][c] = 0.5f * (float)(yf + yl);
         } else {
-            e[3] = -1.0f;
+            cen_lab[r][c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            cen_y[r][c] = -1.0f;
         }
     }
     __syncthreads();
@@ -119,20 +129,24 @@ __global__ void __launch_bounds__(128) k_net_prep(ConvConsts cc, const uint8_t *
     float f0, f1, f2;
     convert_pixel(cc, p[0], p[1], p[2], g_lut_net, f0, f1, f2);
     const int cx = x / S;
+    const float inv_s = 1.0f / (float)S;
     float ch[16];
-    ch[0] = f0 / 100.0f;
-    ch[1] = f1 / 128.0f;
-    ch[2] = f2 / 128.0f;
-    ch[3] = (float)(x - cx * S) / (float)S;
-    ch[4] = (float)(y - cy * S) / (float)S;
+    ch[0] = f0 * 0.01f;
+    ch[1] = f1 * (1.0f / 128.0f);
+    ch[2] = f2 * (1.0f / 128.0f);
+    ch[3] = (float)(x - cx * S) * inv_s;
+    ch[4] = (float)(y - cy * S) * inv_s;
+    const float fx = (float)x, fy = (float)y;
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
-        const float *e = cen[t / 3][cx + t % 3 - 1 - cx_lo];
+        const int col = cx + t % 3 - 1 - cx_lo;
+        const float4 e = cen_lab[t / 3][col];
+        const float ey = cen_y[t / 3][col];
         float d = 2.0f;
-        if (e[3] >= 0.0f) {
-            const float dl = e[0] - f0, da = e[1] - f1, db = e[2] - f2;
-            const float dx = e[3] - (float)x, dy = e[4] - (float)y;
-            d = (sqrtf(dl * dl + da * da + db * db) + w * sqrtf(dx * dx + dy * dy)) / 100.0f;
+        if (ey >= 0.0f) {
+            const float dl = e.x - f0, da = e.y - f1, db = e.z - f2;
+            const float dx = e.w - fx, dy = ey - fy;
+            d = (sqrt_fast(fmaf(dl, dl, fmaf(da, da, db * db))) + w * sqrt_fast(fmaf(dx, dx, dy * dy))) * 0.01f;
         }
         ch[5 + t] = d;
     }
