@@ -174,3 +174,77 @@ def test_trained_network_beats_grid_start_at_equal_iterations(slic_gpu, tmp_path
     net.forward(imgs, labels=l1)
     net2.forward(imgs, labels=l2)
     assert torch.equal(l1, l2)
+
+
+@pytest.mark.parametrize("W,H,n", [(1920, 48, 2), (1000, 41, 3)])
+def test_forward_several_tiles_per_cta(slic_gpu, W, H, n):
+    """Enough 120-pixel tiles that every persistent CTA takes several, so the
+    input-stage ring and both accumulator buffers are reused (1536 and 1080
+    tiles over the 2-CTA-per-SM grid); the second size has a ragged last
+    tile. Logits of the whole batch against the oracle, and the fused
+    labels-only path against the oracle's argmax."""
+    import torch
+    S = 16
+    net, host, imgs = _setup(slic_gpu, n=n, W=W, H=H, S=S, seed=11)
+    logits = torch.empty((n, H, W, 16), dtype=torch.float32, device="cuda")
+    labels = torch.empty((n, H, W), dtype=torch.int32, device="cuda")
+    net.forward(imgs, logits=logits)
+    net.forward(imgs, labels=labels)
+    torch.cuda.synchronize()
+    net.status()
+    params = _split(net.params())
+    valid = NO.slot_mask(H, W, S)
+    for i in range(n):
+        ref, _ = NO.forward(_oracle_input(host[i], S), params, bf16=True)
+        scale = max(1.0, np.abs(ref).max())
+        got = logits[i].cpu().numpy()
+        assert np.max(np.abs(got[..., :9] - ref)) <= 2e-2 * scale
+        z = np.where(valid, ref, -np.inf)
+        top2 = np.sort(z, axis=-1)[..., -2:]
+        clear = (top2[..., 1] - top2[..., 0]) > 2e-2 * scale
+        want = NO.labels_from_slots(np.argmax(z, axis=-1), S)
+        assert np.all((labels[i].cpu().numpy() == want) | ~clear)
+
+
+def test_forward_full_hd_batch_sampled(slic_gpu):
+    """The bench's network launch configuration: 8 frames of 1920x1080,
+    S=16 (three of them checked). The oracle evaluates sampled pixels one by
+    one on the 9x9 window
+    that determines them (four 3x3 layers), cut from its input channels of
+    the whole frame and clipped at the image border, where every layer's zero
+    padding then falls as on the device."""
+    import torch
+    W, H, S, n = 1920, 1080, 16, 8
+    from paper_1509_04232_gb300.warmstart import WarmStartNet
+    net = WarmStartNet(W, H, S, max_batch=n, seed=7)
+    host = np.stack([synth.hd_image(40 + i, W, H) for i in range(n)])
+    imgs = torch.from_numpy(host).cuda()
+    logits = torch.empty((n, H, W, 16), dtype=torch.float32, device="cuda")
+    labels = torch.empty((n, H, W), dtype=torch.int32, device="cuda")
+    net.forward(imgs, logits=logits)
+    net.forward(imgs, labels=labels)
+    torch.cuda.synchronize()
+    net.status()
+    params = _split(net.params())
+    rng = np.random.default_rng(5)
+    ns_c, ns_r = -(-W // S), -(-H // S)
+    fixed = [(0, 0), (0, W - 1), (H - 1, 0), (H - 1, W - 1), (1, 119), (2, 120), (540, 239), (541, 240),
+             (H - 2, 1799), (H - 1, 1800), (7, W - 2), (H // 2, 1)]
+    for i in (0, 4, 7):  # the oracle's input channels take seconds per 1080p frame
+        x0 = _oracle_input(host[i], S)
+        pts = fixed + [(int(rng.integers(0, H)), int(rng.integers(0, W))) for _ in range(36)]
+        got_l = logits[i].cpu().numpy()
+        got_lab = labels[i].cpu().numpy()
+        for y, x in pts:
+            r0, r1, c0, c1 = max(0, y - 4), min(H, y + 5), max(0, x - 4), min(W, x + 5)
+            ref_win, _ = NO.forward(x0[r0:r1, c0:c1], params, bf16=True)
+            ref = ref_win[y - r0, x - c0]
+            scale = max(1.0, np.abs(ref).max())
+            assert np.max(np.abs(got_l[y, x, :9] - ref)) <= 2e-2 * scale, (i, y, x)
+            cx, cy = x // S, y // S
+            ok = [0 <= cx + t % 3 - 1 < ns_c and 0 <= cy + t // 3 - 1 < ns_r for t in range(9)]
+            z = np.where(ok, ref, -np.inf)
+            top2 = np.sort(z)[-2:]
+            if top2[1] - top2[0] > 2e-2 * scale:
+                t = int(np.argmax(z))
+                assert got_lab[y, x] == (cy + t // 3 - 1) * ns_c + cx + t % 3 - 1, (i, y, x)
