@@ -8,10 +8,15 @@ than the 129 MB L2, so no flush is needed between steps.
 
 Prints ONE JSON line (rank 0). Keys beyond the base contract:
   roofline      the assignment kernel (the dominant one) against its bound
-  cpu_baseline  the FP64 CPU oracle timed on a bounded sample, 1 thread
+  cpu_baseline  the FP64 CPU oracle timed on a bounded sample over all host
+                cores (one process per core), with a one-core figure beside it
   e2e           the same metric through the public API with host buffers
   gpu_launches  kernel launches of this library inside the timed region
   clocks        SM clocks sampled by nvidia-smi during the timed region
+  quality       label agreement with 10 iterations, the plain path at 10
+                iterations, the learned warm start and the network forward
+                against the bf16 tensor roofline
+  mixed_batch   the 256-frame mixed-resolution batch (context line)
 
 ``--impl reference`` times the FP64 CPU oracle itself (the only reference
 implementation of the method in this repository) on the same workload.
