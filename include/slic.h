@@ -64,6 +64,19 @@ typedef struct {
     int color_space;          /* slic_color_space */
     int enforce_connectivity; /* 0 or 1 */
     int in_channels;          /* 3 or 4 */
+    /* Sec. 2 steps of the original SLIC that the paper's GPU steps omit
+       (both off by default, i.e. zero-initialised): */
+    int perturb_seeds;        /* 0 or 1: move each grid seed to the pixel of
+                                 lowest gradient G = |I(x+1,y)-I(x-1,y)|^2 +
+                                 |I(x,y+1)-I(x,y-1)|^2 (features; neighbours
+                                 clamped at the border) in the 3x3 pixels
+                                 around it; it moves only to a strictly lower
+                                 G, the first in scan order (dy, then dx) */
+    float convergence;        /* >= 0, finite: stop after the first iteration
+                                 whose update moved the centres by a mean L1
+                                 distance (|dx| + |dy| in pixels, over all
+                                 K_eff centres) below this; `iterations` is
+                                 then the maximum. 0: fixed iterations */
 } slic_params;
 
 /* Create a handle for one image geometry; allocates the handle's device

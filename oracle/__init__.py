@@ -12,6 +12,8 @@ marshals numpy arrays through ctypes. Function-level citations:
 ``grid``               Sec. 2, S = sqrt(N/K); integer S, ceil grid
 ``convert``            Sec. 2 (CIELAB) and Sec. 3 "Image space conversion"
 ``init_centres``       Sec. 3 "Cluster center initialisation"
+``perturb_seeds``      Sec. 2, centres moved to the lowest-gradient pixel nearby
+``residual``           Sec. 2, L1 change of the centres (the stopping test)
 ``assign``             Eq. (1) and Sec. 3 "Finding the cluster associations"
 ``update``             Sec. 3 "Updating the cluster center"
 ``connectivity_pass``  Sec. 3 "Enforce connectivity" (one of the two passes)
@@ -67,9 +69,12 @@ def _load():
         lib.oracle_assign.argtypes = [P, I, I, I, D, P, P, P]
         lib.oracle_update.argtypes = [P, I, I, P, I, P]
         lib.oracle_connectivity_pass.argtypes = [P, I, I, P]
-        lib.oracle_slic.argtypes = [P, I, I, I, I, I, D, I, I, I, P, P, P, P, P]
+        lib.oracle_slic.argtypes = [P, I, I, I, I, I, D, I, I, I, P, I, D, P, P, P, P, P]
+        lib.oracle_perturb_seeds.argtypes = [P, I, I, I, P, P, P]
+        lib.oracle_residual.argtypes = [P, P, I]
+        lib.oracle_residual.restype = D
         for f in (lib.oracle_grid, lib.oracle_convert, lib.oracle_init_centres, lib.oracle_assign,
-                  lib.oracle_update, lib.oracle_connectivity_pass, lib.oracle_slic):
+                  lib.oracle_update, lib.oracle_connectivity_pass, lib.oracle_slic, lib.oracle_perturb_seeds):
             f.restype = I
         _lib = lib
     return _lib
@@ -110,6 +115,26 @@ def init_centres(feat: np.ndarray, S: int) -> np.ndarray:
     return out
 
 
+def perturb_seeds(feat: np.ndarray, S: int, centres: np.ndarray):
+    """Seed perturbation of grid-initialised centres. Returns (centres,
+    g_best [K_eff], margin [K_eff]): the gradient at each chosen pixel and
+    the relative gap to the next-lowest candidate."""
+    feat = np.ascontiguousarray(feat, dtype=np.float64)
+    out = np.array(centres, dtype=np.float64, copy=True, order="C")
+    H, W, _ = feat.shape
+    g = np.empty(out.shape[0], np.float64)
+    mg = np.empty(out.shape[0], np.float64)
+    _check(_load().oracle_perturb_seeds(_ptr(feat), W, H, S, _ptr(out), _ptr(g), _ptr(mg)), "perturb_seeds")
+    return out, g, mg
+
+
+def residual(prev: np.ndarray, cur: np.ndarray) -> float:
+    """Mean L1 move of the centre positions between two centre sets."""
+    prev = np.ascontiguousarray(prev, dtype=np.float64)
+    cur = np.ascontiguousarray(cur, dtype=np.float64)
+    return float(_load().oracle_residual(_ptr(prev), _ptr(cur), prev.shape[0]))
+
+
 def assign(feat: np.ndarray, S: int, m: float, centres: np.ndarray):
     """One assignment pass. Returns (labels int32 [H,W], margin float64 [H,W])."""
     feat = np.ascontiguousarray(feat, dtype=np.float64)
@@ -143,12 +168,14 @@ def connectivity_pass(labels: np.ndarray) -> np.ndarray:
 
 def slic(rgb: np.ndarray, K: int = 0, S: int = 0, m: float = 10.0, iterations: int = 10,
          color_space: int = CIELAB, enforce_connectivity: bool = True,
-         init_centres: np.ndarray | None = None) -> dict:
+         init_centres: np.ndarray | None = None, perturb_seeds: bool = False,
+         convergence: float = 0.0) -> dict:
     """Whole SLIC run in the order of the paper's Perform_Segmentation.
 
     Returns a dict with ``labels`` (after connectivity), ``labels_pre``
     (before it), ``centres`` (the ones the final labels were assigned
-    against), ``margin`` (tie margin of the final assignment) and the grid.
+    against), ``margin`` (tie margin of the final assignment),
+    ``iterations_run`` (updates performed) and the grid.
     """
     rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
     H, W, C = rgb.shape
@@ -162,8 +189,10 @@ def slic(rgb: np.ndarray, K: int = 0, S: int = 0, m: float = 10.0, iterations: i
         ic = np.ascontiguousarray(init_centres, dtype=np.float64)
         if ic.shape != centres.shape:
             raise ValueError("init_centres has the wrong shape")
+    run = ctypes.c_int(0)
     _check(_load().oracle_slic(_ptr(rgb), W, H, C, K, S, float(m), iterations, color_space,
-                               int(bool(enforce_connectivity)), _ptr(ic), _ptr(labels),
-                               _ptr(centres), _ptr(pre), _ptr(margin)), "slic")
+                               int(bool(enforce_connectivity)), _ptr(ic), int(bool(perturb_seeds)),
+                               float(convergence), _ptr(labels), _ptr(centres), _ptr(pre), _ptr(margin),
+                               ctypes.byref(run)), "slic")
     return {"labels": labels, "labels_pre": pre, "centres": centres, "margin": margin,
-            "S": s, "ns_c": ns_c, "ns_r": ns_r}
+            "iterations_run": run.value, "S": s, "ns_c": ns_c, "ns_r": ns_r}

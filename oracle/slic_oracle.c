@@ -13,6 +13,8 @@
  *   colour convert  Sec. 2 (CIELAB), Sec. 3 "Image space conversion"
  *                                                           oracle_convert
  *   init            Sec. 3 "Cluster center initialisation"  oracle_init_centres
+ *   seed perturbation  Sec. 2 (original SLIC's first step)  oracle_perturb_seeds
+ *   stopping test   Sec. 2 (L1 change of the centres)       oracle_residual
  *   assign          Eq. (1), Sec. 3 "Finding the cluster associations"
  *                                                           oracle_assign
  *   update          Sec. 3 "Updating the cluster center"    oracle_update
@@ -147,6 +149,90 @@ int oracle_init_centres(const double *feat, int W, int H, int S, double *centres
     return 0;
 }
 
+/* Sec. 2, first step of the original SLIC: "the cluster centers are
+   perturbed to the lowest gradient position from a local neighborhood".
+   Readings (the paper names neither the gradient nor the neighbourhood):
+   the neighbourhood is the 3x3 pixels around the seed pixel
+   (floor(x_k), floor(y_k)); the gradient is the squared central
+   differences of the features, G(x,y) = |I(x+1,y) - I(x-1,y)|^2 +
+   |I(x,y+1) - I(x,y-1)|^2, with coordinates clamped into the image. The
+   seed pixel is the first candidate and a later one (dy outer, dx inner,
+   each -1..1, in-image only) replaces the best only when its G is strictly
+   lower; a seed that moves takes that pixel's features and integer
+   coordinates, one that stays keeps its initial centre. */
+static double gradient_G(const double *feat, int W, int H, int x, int y) {
+    int xl = x > 0 ? x - 1 : 0, xr = x < W - 1 ? x + 1 : W - 1;
+    int yu = y > 0 ? y - 1 : 0, yd = y < H - 1 ? y + 1 : H - 1;
+    double g = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        double gx = feat[3 * ((long)y * W + xr) + c] - feat[3 * ((long)y * W + xl) + c];
+        double gy = feat[3 * ((long)yd * W + x) + c] - feat[3 * ((long)yu * W + x) + c];
+        g += gx * gx + gy * gy;
+    }
+    return g;
+}
+
+/* Applies the perturbation to grid-initialised centres in place.
+   g_best [K_eff] (optional): G at the chosen pixel; margin [K_eff]
+   (optional): (smallest G among the other candidates - g_best) /
+   max(g_best, 1e-12), +inf with a single candidate. */
+int oracle_perturb_seeds(const double *feat, int W, int H, int S, double *centres, double *g_best,
+                         double *margin) {
+    if (W <= 0 || H <= 0 || S <= 0) return -1;
+    int ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
+    for (int k = 0; k < ns_c * ns_r; ++k) {
+        double *ck = centres + 6 * (long)k;
+        int px = (int)floor(ck[3]), py = (int)floor(ck[4]);
+        int bx = px, by = py;
+        const double g0 = gradient_G(feat, W, H, px, py);
+        double best = g0;
+        double gv[9];
+        int gx[9], gy[9], n = 0;
+        for (int dy = -1; dy <= 1; ++dy) {
+            for (int dx = -1; dx <= 1; ++dx) {
+                int x = px + dx, y = py + dy;
+                if (x < 0 || x >= W || y < 0 || y >= H) continue;
+                double g = (dx == 0 && dy == 0) ? g0 : gradient_G(feat, W, H, x, y);
+                gv[n] = g;
+                gx[n] = x;
+                gy[n] = y;
+                ++n;
+                if (!(dx == 0 && dy == 0) && g < best) {
+                    best = g;
+                    bx = x;
+                    by = y;
+                }
+            }
+        }
+        if (g_best) g_best[k] = best;
+        if (margin) {
+            double second = INFINITY;
+            for (int i = 0; i < n; ++i)
+                if (!(gx[i] == bx && gy[i] == by) && gv[i] < second) second = gv[i];
+            margin[k] = isinf(second) ? INFINITY : (second - best) / (best > 1e-12 ? best : 1e-12);
+        }
+        if (bx != px || by != py) {
+            const double *f = feat + 3 * ((long)by * W + bx);
+            ck[0] = f[0];
+            ck[1] = f[1];
+            ck[2] = f[2];
+            ck[3] = bx;
+            ck[4] = by;
+        }
+    }
+    return 0;
+}
+
+/* Sec. 2: the iteration stops "when the cluster centers stabilise", the
+   L1 distance between centres of consecutive iterations falling below a
+   threshold. Reading: E = (1/K_eff) sum_k (|x_k - x'_k| + |y_k - y'_k|),
+   the mean L1 move of the centre positions over one update. */
+double oracle_residual(const double *prev, const double *cur, int K_eff) {
+    double e = 0.0;
+    for (int k = 0; k < K_eff; ++k) e += fabs(cur[6 * k + 3] - prev[6 * k + 3]) + fabs(cur[6 * k + 4] - prev[6 * k + 4]);
+    return K_eff > 0 ? e / K_eff : 0.0;
+}
+
 /* Eq. (1): D_s = d_lab + (m/S) d_xy for pixel i against centre k. */
 static double distance_Ds(const double *fi, double xi, double yi, const double *ck, double m, int S) {
     double dl = ck[0] - fi[0], da = ck[1] - fi[1], db = ck[2] - fi[2];
@@ -267,35 +353,50 @@ int oracle_connectivity_pass(const int32_t *in, int W, int H, int32_t *out) {
 
 /*
  * Sec. 4, Perform_Segmentation: convert; initialise centres (or take
- * init_centres when given, e.g. the previous video frame's); assign; then
- * `iterations` times {update; assign}; then, if enabled, two connectivity
- * passes.
+ * init_centres when given, e.g. the previous video frame's), perturbed
+ * when perturb_seeds is set (Sec. 2); assign; then up to `iterations` times
+ * {update; assign}, ending after the first iteration whose update moved
+ * the centres by E < convergence (Sec. 2; convergence 0: never); then, if
+ * enabled, two connectivity passes.
  *   labels   [H*W]      final labels
  *   centres  [K_eff*6]  centres the final labels were assigned against
  *   labels_pre [H*W]    optional: labels before connectivity
  *   margin   [H*W]      optional: tie margin of the final assignment
+ *   iterations_run      optional: updates performed
  * Returns 0, -1 on invalid arguments, -2 on allocation failure.
  */
 int oracle_slic(const uint8_t *rgb, int W, int H, int C, int K, int S_in, double m, int iterations,
-                int color_space, int enforce_connectivity, const double *init_centres,
-                int32_t *labels, double *centres, int32_t *labels_pre, double *margin) {
+                int color_space, int enforce_connectivity, const double *init_centres, int perturb_seeds,
+                double convergence, int32_t *labels, double *centres, int32_t *labels_pre, double *margin,
+                int *iterations_run) {
     int S, ns_c, ns_r;
-    if (oracle_grid(W, H, K, S_in, &S, &ns_c, &ns_r) != 0 || iterations < 0 || !(m >= 0.0)) return -1;
+    if (oracle_grid(W, H, K, S_in, &S, &ns_c, &ns_r) != 0 || iterations < 0 || !(m >= 0.0) ||
+        !(convergence >= 0.0))
+        return -1;
     int K_eff = ns_c * ns_r;
     long N = (long)W * H;
     double *feat = (double *)malloc(sizeof(double) * 3 * N);
     int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * N);
-    if (!feat || !tmp) { free(feat); free(tmp); return -2; }
-    if (oracle_convert(rgb, W, H, C, color_space, feat) != 0) { free(feat); free(tmp); return -1; }
-    if (init_centres)
+    double *prev = (double *)malloc(sizeof(double) * 6 * K_eff);
+    if (!feat || !tmp || !prev) { free(feat); free(tmp); free(prev); return -2; }
+    if (oracle_convert(rgb, W, H, C, color_space, feat) != 0) { free(feat); free(tmp); free(prev); return -1; }
+    if (init_centres) {
         memcpy(centres, init_centres, sizeof(double) * 6 * K_eff);
-    else
+    } else {
         oracle_init_centres(feat, W, H, S, centres);
+        if (perturb_seeds) oracle_perturb_seeds(feat, W, H, S, centres, NULL, NULL);
+    }
     oracle_assign(feat, W, H, S, m, centres, labels, margin);
+    int done = 0;
     for (int it = 0; it < iterations; ++it) {
+        memcpy(prev, centres, sizeof(double) * 6 * K_eff);
         oracle_update(feat, W, H, labels, K_eff, centres);
         oracle_assign(feat, W, H, S, m, centres, labels, margin);
+        ++done;
+        if (convergence > 0.0 && oracle_residual(prev, centres, K_eff) < convergence) break;
     }
+    if (iterations_run) *iterations_run = done;
+    free(prev);
     if (labels_pre) memcpy(labels_pre, labels, sizeof(int32_t) * N);
     if (enforce_connectivity) {
         oracle_connectivity_pass(labels, W, H, tmp);

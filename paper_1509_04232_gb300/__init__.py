@@ -27,14 +27,16 @@ def _stream_handle(stream) -> int:
 
 
 class Segmenter:
-    """One image geometry and parameter set (Sec. 2: K or S, m; Sec. 4:
-    colour space, iterations, connectivity), owning a library handle."""
+    """One image geometry and parameter set (Sec. 2: K or S, m, and the
+    optional seed perturbation and convergence threshold; Sec. 4: colour
+    space, iterations, connectivity), owning a library handle."""
 
     def __init__(self, width: int, height: int, *, K: int = 0, S: int = 0, m: float = 10.0,
                  iterations: int = 10, color_space: int = SLIC_CIELAB, enforce_connectivity: bool = True,
-                 in_channels: int = 3):
+                 in_channels: int = 3, perturb_seeds: bool = False, convergence: float = 0.0):
         self.params = slic_params(width, height, K, S, float(m), iterations, color_space,
-                                  int(bool(enforce_connectivity)), in_channels)
+                                  int(bool(enforce_connectivity)), in_channels, int(bool(perturb_seeds)),
+                                  float(convergence))
         self.handle = slic_create(self.params)
         self.S, self.ns_c, self.ns_r = slic_grid(self.handle)
         self.K_eff = self.ns_c * self.ns_r
@@ -110,15 +112,18 @@ class Segmenter:
 class BatchSegmenter:
     """Many frames (uneven size, S or K, m) segmented by one set of launches
     per pass. ``frames`` is a sequence of dicts with keys width, height and
-    K or S, optionally m, color_space, in_channels; ``iterations`` and
-    ``enforce_connectivity`` are shared. Output tensors are allocated here
-    (``labels[f]`` int32 [H, W], ``centres[f]`` float32 [K_eff, 6])."""
+    K or S, optionally m, color_space, in_channels, perturb_seeds and
+    convergence (per frame: a converged frame skips its remaining middle
+    passes); ``iterations`` and ``enforce_connectivity`` are shared. Output
+    tensors are allocated here (``labels[f]`` int32 [H, W], ``centres[f]``
+    float32 [K_eff, 6])."""
 
     def __init__(self, frames, *, iterations: int = 5, enforce_connectivity: bool = True, device=None):
         import torch
         self.params = [slic_params(f["width"], f["height"], f.get("K", 0), f.get("S", 0), float(f.get("m", 10.0)),
                                    iterations, f.get("color_space", SLIC_CIELAB), int(bool(enforce_connectivity)),
-                                   f.get("in_channels", 3)) for f in frames]
+                                   f.get("in_channels", 3), int(bool(f.get("perturb_seeds", False))),
+                                   float(f.get("convergence", 0.0))) for f in frames]
         self.handle = slic_batch_create(self.params)
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.labels, self.centres, self.K_eff = [], [], []

@@ -30,7 +30,8 @@ class SlicError(RuntimeError):
 class slic_params(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("K", ctypes.c_int), ("S", ctypes.c_int),
                 ("m", ctypes.c_float), ("iterations", ctypes.c_int), ("color_space", ctypes.c_int),
-                ("enforce_connectivity", ctypes.c_int), ("in_channels", ctypes.c_int)]
+                ("enforce_connectivity", ctypes.c_int), ("in_channels", ctypes.c_int),
+                ("perturb_seeds", ctypes.c_int), ("convergence", ctypes.c_float)]
 
 
 _lib = None

@@ -207,6 +207,10 @@ slic_status slic_create(const slic_params *params, slic_handle *out) {
     if (p.in_channels != 3 && p.in_channels != 4) return fail(nullptr, SLIC_ERR_INVALID, "in_channels must be 3 or 4");
     if (p.enforce_connectivity != 0 && p.enforce_connectivity != 1)
         return fail(nullptr, SLIC_ERR_INVALID, "enforce_connectivity must be 0 or 1");
+    if (p.perturb_seeds != 0 && p.perturb_seeds != 1)
+        return fail(nullptr, SLIC_ERR_INVALID, "perturb_seeds must be 0 or 1");
+    if (!(p.convergence >= 0.0f) || !std::isfinite(p.convergence))
+        return fail(nullptr, SLIC_ERR_INVALID, "convergence must be finite and >= 0");
 
     slic_ctx *h = new (std::nothrow) slic_ctx;
     if (!h) return fail(nullptr, SLIC_ERR_NOMEM, "host allocation failed");
@@ -466,6 +470,10 @@ extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uin
     if (p.in_channels != 3 && p.in_channels != 4) return fail(nullptr, SLIC_ERR_INVALID, "in_channels must be 3 or 4");
     if (p.enforce_connectivity != 0 && p.enforce_connectivity != 1)
         return fail(nullptr, SLIC_ERR_INVALID, "enforce_connectivity must be 0 or 1");
+    if (p.perturb_seeds != 0 && p.perturb_seeds != 1)
+        return fail(nullptr, SLIC_ERR_INVALID, "perturb_seeds must be 0 or 1");
+    if (!(p.convergence >= 0.0f) || !std::isfinite(p.convergence))
+        return fail(nullptr, SLIC_ERR_INVALID, "convergence must be finite and >= 0");
     int S = p.S;
     if (S == 0) {
         S = (int)std::lround(std::sqrt((double)p.width * (double)p.height / (double)p.K));

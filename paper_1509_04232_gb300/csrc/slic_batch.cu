@@ -126,6 +126,11 @@ bool valid_params(const slic_params &p, std::string &why) {
         why = "enforce_connectivity must be 0 or 1";
         return false;
     }
+    if (p.perturb_seeds != 0 && p.perturb_seeds != 1) { why = "perturb_seeds must be 0 or 1"; return false; }
+    if (!(p.convergence >= 0.0f) || !std::isfinite(p.convergence)) {
+        why = "convergence must be finite and >= 0";
+        return false;
+    }
     return true;
 }
 

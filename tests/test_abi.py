@@ -54,6 +54,10 @@ def test_binding_covers_every_declared_symbol():
     (dict(in_channels=2), "in_channels"),
     (dict(enforce_connectivity=2), "enforce_connectivity"),
     (dict(width=1 << 21), "width"),
+    (dict(perturb_seeds=2), "perturb_seeds"),
+    (dict(convergence=-0.5), "convergence"),
+    (dict(convergence=float("inf")), "convergence"),
+    (dict(convergence=float("nan")), "convergence"),
 ])
 def test_invalid_params_rejected_without_cuda(lib, kw, msg):
     base = dict(width=64, height=48, K=12, S=0, m=10.0, iterations=3, color_space=0,
