@@ -150,6 +150,7 @@ FrameArgs frame_args(slic_ctx *h, const uint8_t *rgb, float *feat, int P, const 
     a.rgb_vec = (rgb && (h->p.width & 3) == 0 && ((uintptr_t)rgb & 15) == 0) ? 1 : 0;
     a.labels_vec = (labels && (h->p.width & 3) == 0 && ((uintptr_t)labels & 15) == 0) ? 1 : 0;
     a.fix_scale = h->fix_scale;
+    a.perturb = h->p.perturb_seeds;
     return a;
 }
 
@@ -339,7 +340,7 @@ slic_status slic_init_centres(slic_handle h, const float *d_features, float *d_c
     if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
     if (!d_features || !d_centres) return fail(h, SLIC_ERR_INVALID, "NULL buffer");
     cudaError_t e = launch_init_from_feat(d_features, h->p.width, h->p.height, h->p.width, h->S, h->ns_c, h->ns_r,
-                                          d_centres, (cudaStream_t)stream);
+                                          h->p.perturb_seeds, d_centres, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "initialisation kernel launch");
     ++h->launches;
     return SLIC_OK;
@@ -522,6 +523,7 @@ extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uin
     a.fix_scale = p.color_space == SLIC_RGB ? 1.0f : kFixScaleFrac;
     a.s_mul = S <= 2048 ? (unsigned)((0x100000000ULL + (unsigned)S - 1) / (unsigned)S) : 0u;
     a.tiles_x = (p.width + kTileW - 1) / kTileW;
+    a.perturb = p.perturb_seeds;
     int32_t *lbl_tmp = reinterpret_cast<int32_t *>(base + feat_b + acc_b);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t smem = assign_smem_bytes(win, true);

@@ -240,6 +240,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         a.fix_scale = p.color_space == SLIC_RGB ? 1.0f : kFixScaleFrac;
         a.s_mul = S <= 2048 ? (unsigned)((0x100000000ULL + (unsigned)S - 1) / (unsigned)S) : 0u;
         a.tiles_x = (p.width + kTileW - 1) / kTileW;
+        a.perturb = p.perturb_seeds;
         a.tile_base = (int)tiles;
         a.centre_base = (int)centres;
         a.row_base = (int)rows;

@@ -118,6 +118,7 @@ struct FrameArgs {
     int assign_vec;         // fused connectivity follows); 1: 4-pixel vector stores
     int strips_x;           // fused connectivity: strips per row and first
     int strip_base;         // work unit (strip x row segment) of this frame
+    int perturb;            // 1: grid seeds move to the lowest-gradient pixel nearby (Sec. 2)
 };
 
 // Shared memory for one assignment CTA whose tile spans at most win_n cells.
@@ -142,7 +143,7 @@ cudaError_t configure_kernels(size_t max_smem);
 
 cudaError_t launch_init_from_rgb(const FrameArgs &a, cudaStream_t s);
 cudaError_t launch_init_batch(const FrameArgs *d_frames, int n, int total_centres, cudaStream_t s);
-cudaError_t launch_init_from_feat(const float *feat, int W, int H, int P, int S, int ns_c, int ns_r,
+cudaError_t launch_init_from_feat(const float *feat, int W, int H, int P, int S, int ns_c, int ns_r, int perturb,
                                   float *centres, cudaStream_t s);
 cudaError_t launch_zero_acc(long long *acc, int K, cudaStream_t s);
 // first: convert from RGB (and store features unless last); last: write labels

@@ -103,17 +103,79 @@ __device__ __forceinline__ void init_centre_position(int k, int W, int H, int S,
     py = (y_first + y_last) >> 1;
 }
 
+// Seed perturbation (Sec. 2, the original SLIC's first step): the pixel of
+// lowest gradient G = |I(x+1,y) - I(x-1,y)|^2 + |I(x,y+1) - I(x,y-1)|^2
+// (features, neighbours clamped into the image) among the 3x3 pixels around
+// the seed pixel (px, py). The seed pixel is the first candidate; a later
+// one (dy outer, dx inner, in-image only) wins only with a strictly lower G.
+// fetch(x, y, f) gives the features of an in-image pixel. Returns whether the
+// seed moved, with the chosen pixel and its features.
+template <typename Fetch>
+__device__ __forceinline__ bool perturb_seed(const Fetch &fetch, int W, int H, int px, int py, int &bx, int &by,
+                                             float (&fb)[3]) {
+    float f[5][5][3];  // features of the 5x5 block around (px, py), clamped; corners unused
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            if ((i == 0 || i == 4) && (j == 0 || j == 4)) continue;
+            fetch(min(max(px - 2 + i, 0), W - 1), min(max(py - 2 + j, 0), H - 1), f[j][i]);
+        }
+    }
+    auto grad = [&](int i, int j) {
+        float g = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float gx = f[j][i + 1][c] - f[j][i - 1][c], gy = f[j + 1][i][c] - f[j - 1][i][c];
+            g += gx * gx + gy * gy;
+        }
+        return g;
+    };
+    float best = grad(2, 2);
+    int bi = 2, bj = 2;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            if ((dx == 0 && dy == 0) || px + dx < 0 || px + dx >= W || py + dy < 0 || py + dy >= H) continue;
+            const float g = grad(2 + dx, 2 + dy);
+            if (g < best) {
+                best = g;
+                bi = 2 + dx;
+                bj = 2 + dy;
+            }
+        }
+    }
+    bx = px + bi - 2;
+    by = py + bj - 2;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) fb[c] = f[bj][bi][c];
+    return bi != 2 || bj != 2;
+}
+
 __device__ __forceinline__ void init_centre(const FrameArgs &a, int k) {
     float xk, yk;
     int px, py;
     init_centre_position(k, a.W, a.H, a.S, a.ns_c, xk, yk, px, py);
-    const uint8_t *p = a.rgb + ((size_t)py * a.W + px) * a.C;
-    float f0, f1, f2;
-    convert_pixel(a.conv, p[0], p[1], p[2], g_lut, f0, f1, f2);
+    float fv[3];
+    if (a.perturb) {
+        int bx, by;
+        auto fetch = [&](int x, int y, float (&o)[3]) {
+            const uint8_t *q = a.rgb + ((size_t)y * a.W + x) * a.C;
+            convert_pixel(a.conv, q[0], q[1], q[2], g_lut, o[0], o[1], o[2]);
+        };
+        if (perturb_seed(fetch, a.W, a.H, px, py, bx, by, fv)) {
+            xk = (float)bx;
+            yk = (float)by;
+        }
+    } else {
+        const uint8_t *p = a.rgb + ((size_t)py * a.W + px) * a.C;
+        convert_pixel(a.conv, p[0], p[1], p[2], g_lut, fv[0], fv[1], fv[2]);
+    }
     float *ck = a.centres_out + (size_t)k * 6;
-    ck[0] = f0;
-    ck[1] = f1;
-    ck[2] = f2;
+    ck[0] = fv[0];
+    ck[1] = fv[1];
+    ck[2] = fv[2];
     ck[3] = xk;
     ck[4] = yk;
     ck[5] = 0.0f;
@@ -170,18 +232,33 @@ __global__ void k_fill_ring(const FrameArgs *frames, int n, int max_ring) {
     }
 }
 
-__global__ void k_init_feat(const float *feat, int W, int H, int P, int S, int ns_c, int ns_r, float *centres) {
+__global__ void k_init_feat(const float *feat, int W, int H, int P, int S, int ns_c, int ns_r, int perturb,
+                            float *centres) {
     const int K = ns_c * ns_r;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     float xk, yk;
     int px, py;
     init_centre_position(k, W, H, S, ns_c, xk, yk, px, py);
-    const size_t plane = (size_t)H * P, off = (size_t)py * P + px;
+    const size_t plane = (size_t)H * P;
+    auto fetch = [&](int x, int y, float (&o)[3]) {
+        const size_t off = (size_t)y * P + x;
+        o[0] = feat[off];
+        o[1] = feat[plane + off];
+        o[2] = feat[2 * plane + off];
+    };
+    float fv[3];
+    int bx, by;
+    if (perturb && perturb_seed(fetch, W, H, px, py, bx, by, fv)) {
+        xk = (float)bx;
+        yk = (float)by;
+    } else {
+        fetch(px, py, fv);
+    }
     float *ck = centres + (size_t)k * 6;
-    ck[0] = feat[off];
-    ck[1] = feat[plane + off];
-    ck[2] = feat[2 * plane + off];
+    ck[0] = fv[0];
+    ck[1] = fv[1];
+    ck[2] = fv[2];
     ck[3] = xk;
     ck[4] = yk;
     ck[5] = 0.0f;
@@ -1700,10 +1777,10 @@ cudaError_t launch_init_batch(const FrameArgs *d_frames, int n, int total_centre
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_from_feat(const float *feat, int W, int H, int P, int S, int ns_c, int ns_r,
+cudaError_t launch_init_from_feat(const float *feat, int W, int H, int P, int S, int ns_c, int ns_r, int perturb,
                                   float *centres, cudaStream_t s) {
     const int K = ns_c * ns_r;
-    k_init_feat<<<(K + 127) / 128, 128, 0, s>>>(feat, W, H, P, S, ns_c, ns_r, centres);
+    k_init_feat<<<(K + 127) / 128, 128, 0, s>>>(feat, W, H, P, S, ns_c, ns_r, perturb, centres);
     return cudaGetLastError();
 }
 
