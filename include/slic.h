@@ -109,6 +109,14 @@ slic_status slic_grid(slic_handle h, int *S, int *ns_c, int *ns_r);
 slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_labels, float *d_centres,
                          void *stream);
 
+/* Wait for the device, then report how many centre updates the last
+   slic_segment call performed: params.iterations, or fewer when the
+   stopping test (params.convergence > 0) ended the run early. A run that
+   stops skips its remaining updates and middle assignment passes; its last
+   assignment pass (labels against the final centres) and connectivity
+   always run. */
+slic_status slic_iterations_run(slic_handle h, int *out);
+
 /* Use d_init [K_eff][6] (e.g. the previous video frame's centres) instead of
    the grid initialisation on the next slic_segment call. The buffer is read
    when that call's work runs. Pass NULL to disarm. */
@@ -226,6 +234,12 @@ slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *la
    batch's kernels gave up since the last call (SLIC_ERR_TIMEOUT; the
    affected tiles' results are then incomplete). Clears the flag. */
 slic_status slic_batch_status(slic_batch b);
+
+/* Wait for the device, then write each frame's number of centre updates in
+   the last slic_batch_segment call to out[0 .. n_frames-1] (the stopping
+   test is per frame: a frame that passed it skips its tiles in the
+   remaining middle passes while the others go on). */
+slic_status slic_batch_iterations_run(slic_batch b, int *out);
 
 /* Device time of the batch's assignment launches, as slic_profile_enable /
    slic_profile_read do for a handle. */

@@ -11,11 +11,12 @@ from __future__ import annotations
 
 from ._binding import (SLIC_CIELAB, SLIC_RGB, SLIC_XYZ, SlicError, library_path, slic_assign,  # noqa: F401
                        slic_batch_autotune, slic_batch_create, slic_batch_destroy, slic_batch_info,
-                       slic_batch_last_error, slic_batch_profile_enable, slic_batch_profile_read,
+                       slic_batch_iterations_run, slic_batch_last_error, slic_batch_profile_enable,
+                       slic_batch_profile_read,
                        slic_batch_profile_times, slic_batch_segment, slic_batch_segment_host,
                        slic_batch_set_buffers, slic_batch_set_tuning, slic_batch_status,
                        slic_connectivity_pass, slic_convert, slic_create, slic_destroy, slic_grid,
-                       slic_init_centres, slic_last_error, slic_launch_count, slic_params,
+                       slic_init_centres, slic_iterations_run, slic_last_error, slic_launch_count, slic_params,
                        slic_profile_enable, slic_profile_read, slic_segment, slic_segment_noalloc,
                        slic_set_init_centres, slic_update)
 
@@ -108,6 +109,12 @@ class Segmenter:
     def launches(self) -> int:
         return slic_launch_count(self.handle)
 
+    @property
+    def iterations_run(self) -> int:
+        """Centre updates the last run performed (fewer than ``iterations``
+        when the stopping test ended it; waits for the device)."""
+        return slic_iterations_run(self.handle)
+
 
 class BatchSegmenter:
     """Many frames (uneven size, S or K, m) segmented by one set of launches
@@ -174,6 +181,11 @@ class BatchSegmenter:
     def status(self):
         """Raises SlicError(SLIC_ERR_TIMEOUT) if a bounded device wait gave up."""
         slic_batch_status(self.handle)
+
+    @property
+    def iterations_run(self):
+        """Per frame, the centre updates of the last run (waits for the device)."""
+        return slic_batch_iterations_run(self.handle, len(self.params))
 
     def close(self):
         if getattr(self, "handle", None):

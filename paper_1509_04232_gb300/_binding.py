@@ -64,6 +64,8 @@ _SIGNATURES = {
                         ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "slic_batch_destroy": [_P],
     "slic_batch_status": [_P],
+    "slic_batch_iterations_run": [_P, ctypes.POINTER(_I)],
+    "slic_iterations_run": [_P, ctypes.POINTER(_I)],
     "slic_batch_profile_enable": [_P, _I],
     "slic_batch_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
     "slic_batch_profile_times": [_P, ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I)],
@@ -245,6 +247,20 @@ def slic_batch_info(b: int):
     _bcheck(lib().slic_batch_info(b, ctypes.byref(px), ctypes.byref(n), ctypes.byref(c), ctypes.byref(st),
                                   ctypes.byref(rw)), b)
     return px.value, n.value, c.value, st.value, rw.value
+
+
+def slic_iterations_run(h: int) -> int:
+    """Centre updates performed by the handle's last run (waits for the device)."""
+    n = _I()
+    _check(lib().slic_iterations_run(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def slic_batch_iterations_run(b: int, n_frames: int) -> list:
+    """Centre updates each frame's last run performed (waits for the device)."""
+    out = (_I * n_frames)()
+    _bcheck(lib().slic_batch_iterations_run(b, out), b)
+    return list(out)
 
 
 def slic_batch_status(b: int) -> None:

@@ -26,6 +26,7 @@ struct slic_ctx {
     float *feat = nullptr;        // 3 planes [H][P]
     long long *acc = nullptr;     // [K][6]
     int32_t *lbl_tmp = nullptr;   // [H][W] connectivity ping-pong
+    ConvState *cstate = nullptr;  // stopping-test state of the current run
     float fix_scale = 0.0f;
     size_t smem_max = 0;
     ConvConsts conv{};
@@ -242,11 +243,14 @@ slic_status slic_create(const slic_params *params, slic_handle *out) {
     const size_t npix = (size_t)p.width * p.height;
     if (cudaMalloc(&h->feat, sizeof(float) * 3 * (size_t)p.height * h->P) != cudaSuccess ||
         cudaMalloc(&h->acc, sizeof(long long) * 6 * (size_t)h->K) != cudaSuccess ||
-        cudaMalloc(&h->lbl_tmp, sizeof(int32_t) * npix) != cudaSuccess) {
+        cudaMalloc(&h->lbl_tmp, sizeof(int32_t) * npix) != cudaSuccess ||
+        cudaMalloc(&h->cstate, sizeof(ConvState)) != cudaSuccess ||
+        cudaMemset(h->cstate, 0, sizeof(ConvState)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(h->feat);
         cudaFree(h->acc);
         cudaFree(h->lbl_tmp);
+        cudaFree(h->cstate);
         delete h;
         return fail(nullptr, SLIC_ERR_NOMEM, "device allocation of scratch failed");
     }
@@ -266,6 +270,7 @@ slic_status slic_destroy(slic_handle h) {
     cudaFree(h->feat);
     cudaFree(h->acc);
     cudaFree(h->lbl_tmp);
+    cudaFree(h->cstate);
     for (auto &ev : h->events) {
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
@@ -282,6 +287,16 @@ slic_status slic_grid(slic_handle h, int *S, int *ns_c, int *ns_r) {
     return SLIC_OK;
 }
 
+slic_status slic_iterations_run(slic_handle h, int *out) {
+    if (!h || !out) return fail(h, SLIC_ERR_INVALID, "NULL argument");
+    ConvState cs{};
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&cs, h->cstate, sizeof(ConvState), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reading the stopping-test state");
+    *out = cs.iters;
+    return SLIC_OK;
+}
+
 slic_status slic_set_init_centres(slic_handle h, const float *d_init) {
     if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
     h->init_centres = d_init;
@@ -294,6 +309,8 @@ slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_label
     cudaStream_t s = (cudaStream_t)stream;
     const int n = h->p.iterations;
     FrameArgs a = frame_args(h, d_image, h->feat, h->P, d_centres, d_labels);
+    a.cstate = h->cstate;
+    a.conv_eps = h->p.convergence;
     cudaError_t e;
     if (h->init_centres) {
         if (h->init_centres != d_centres) {
@@ -303,6 +320,8 @@ slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_label
         }
         h->init_centres = nullptr;
         e = launch_zero_acc(h->acc, h->K, s);
+        // (the grid initialisation resets the stopping-test state itself)
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->cstate, 0, sizeof(ConvState), s);
     } else {
         e = launch_init_from_rgb(a, s);
     }
@@ -310,7 +329,8 @@ slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_label
     ++h->launches;
     for (int pass = 0; pass <= n; ++pass) {
         if (pass > 0) {
-            e = launch_update(h->acc, d_centres, d_centres, h->K, 1.0f / h->fix_scale, s);
+            e = launch_update(h->acc, d_centres, d_centres, h->K, 1.0f / h->fix_scale, h->cstate, h->p.convergence,
+                              pass, s);
             if (e != cudaSuccess) return cuda_fail(h, e, "update kernel launch");
             ++h->launches;
         }
@@ -365,7 +385,8 @@ slic_status slic_update(slic_handle h, const float *d_features, const int32_t *d
     if (e == cudaSuccess)
         e = launch_accumulate_labels(d_features, h->p.width, h->p.height, h->p.width, d_labels, h->K, h->acc,
                                      h->fix_scale, s);
-    if (e == cudaSuccess) e = launch_update(h->acc, d_centres_in, d_centres_out, h->K, 1.0f / h->fix_scale, s);
+    if (e == cudaSuccess)
+        e = launch_update(h->acc, d_centres_in, d_centres_out, h->K, 1.0f / h->fix_scale, nullptr, 0.0f, 1, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "update kernel launch");
     h->launches += 3;
     return SLIC_OK;
@@ -483,13 +504,16 @@ extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uin
     const int ns_c = (p.width + S - 1) / S, ns_r = (p.height + S - 1) / S;
     const long long K = (long long)ns_c * ns_r;
     const int P = (p.width + 3) & ~3;
-    // Scratch layout: features [3][H][P] f32 | sums [K][6] i64 | labels [H][W] i32.
+    // Scratch layout: features [3][H][P] f32 | sums [K][6] i64 | labels [H][W] i32
+    // | stopping-test state.
     const size_t feat_b = align256(sizeof(float) * 3 * (size_t)p.height * P);
     const size_t acc_b = align256(sizeof(long long) * 6 * (size_t)K);
     const size_t lbl_b = align256(sizeof(int32_t) * (size_t)p.width * p.height);
-    if (feat_b + acc_b + lbl_b > kStaticScratchBytes)
+    const size_t cs_b = align256(sizeof(ConvState));
+    if (feat_b + acc_b + lbl_b + cs_b > kStaticScratchBytes)
         return fail(nullptr, SLIC_ERR_INVALID,
-                    "image too large for the static scratch: needs " + std::to_string(feat_b + acc_b + lbl_b) +
+                    "image too large for the static scratch: needs " +
+                        std::to_string(feat_b + acc_b + lbl_b + cs_b) +
                         " bytes, the limit is " + std::to_string(kStaticScratchBytes) + " (32 MiB)");
 
     int dev = 0;
@@ -524,6 +548,8 @@ extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uin
     a.s_mul = S <= 2048 ? (unsigned)((0x100000000ULL + (unsigned)S - 1) / (unsigned)S) : 0u;
     a.tiles_x = (p.width + kTileW - 1) / kTileW;
     a.perturb = p.perturb_seeds;
+    a.cstate = reinterpret_cast<ConvState *>(base + feat_b + acc_b + lbl_b);
+    a.conv_eps = p.convergence;
     int32_t *lbl_tmp = reinterpret_cast<int32_t *>(base + feat_b + acc_b);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t smem = assign_smem_bytes(win, true);
@@ -532,7 +558,8 @@ extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uin
     // sums left in the shared array by the previous call.
     e = launch_init_from_rgb(a, s);
     for (int pass = 0; e == cudaSuccess && pass <= p.iterations; ++pass) {
-        if (pass > 0) e = launch_update(a.acc, d_centres, d_centres, (int)K, 1.0f / a.fix_scale, s);
+        if (pass > 0)
+            e = launch_update(a.acc, d_centres, d_centres, (int)K, 1.0f / a.fix_scale, a.cstate, a.conv_eps, pass, s);
         if (e == cudaSuccess) e = launch_assign(a, pass == 0, pass == p.iterations, false, smem, s);
     }
     if (e == cudaSuccess && p.enforce_connectivity) {

@@ -217,7 +217,8 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
 
     // Geometry, bases and the scratch layout.
     size_t bytes = 0;
-    std::vector<size_t> off_feat(n_frames), off_acc(n_frames), off_lbl(n_frames), off_ctab(n_frames);
+    std::vector<size_t> off_feat(n_frames), off_acc(n_frames), off_lbl(n_frames), off_ctab(n_frames),
+        off_cs(n_frames);
     long long tiles = 0, centres = 0, rows = 0;
     for (int f = 0; f < n_frames; ++f) {
         const slic_params &p = params[f];
@@ -241,6 +242,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         a.s_mul = S <= 2048 ? (unsigned)((0x100000000ULL + (unsigned)S - 1) / (unsigned)S) : 0u;
         a.tiles_x = (p.width + kTileW - 1) / kTileW;
         a.perturb = p.perturb_seeds;
+        a.conv_eps = p.convergence;
         a.tile_base = (int)tiles;
         a.centre_base = (int)centres;
         a.row_base = (int)rows;
@@ -271,6 +273,8 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         bytes += align256(sizeof(int32_t) * (size_t)p.width * p.height);
         off_ctab[f] = bytes;
         bytes += align256(sizeof(float) * kCtabRec * (size_t)(a.ns_c + 2) * (a.ns_r + 2));
+        off_cs[f] = bytes;
+        bytes += align256(sizeof(ConvState));
         b->max_ring = std::max(b->max_ring, 2 * (a.ns_c + 2) + 2 * a.ns_r);
     }
     const size_t off_err = bytes;
@@ -311,6 +315,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         a.acc = reinterpret_cast<long long *>(b->scratch + off_acc[f]);
         a.lbl_tmp = reinterpret_cast<int32_t *>(b->scratch + off_lbl[f]);
         a.ctab = reinterpret_cast<float *>(b->scratch + off_ctab[f]);
+        a.cstate = reinterpret_cast<ConvState *>(b->scratch + off_cs[f]);
         if (b->pipe && !encode_maps(a)) b->pipe = false;  // then every pass uses k_assign_batch
     }
     b->d_err = reinterpret_cast<int *>(b->scratch + off_err);
@@ -387,7 +392,7 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
     ++n_launch;
     for (int pass = 0; e == cudaSuccess && pass <= b->iterations; ++pass) {
         if (pass > 0) {
-            e = launch_update_batch(b->d_frames, b->n, b->total_centres, s);
+            e = launch_update_batch(b->d_frames, b->n, b->total_centres, pass, s);
             ++n_launch;
         }
         if (e == cudaSuccess) {
@@ -579,6 +584,18 @@ slic_status slic_batch_status(slic_batch b) {
     if (e == cudaSuccess && flag) e = cudaMemset(b->d_err, 0, sizeof(int));
     if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
     if (flag) return bfail(b, SLIC_ERR_TIMEOUT, "a bounded wait inside the assignment kernel timed out");
+    return SLIC_OK;
+}
+
+slic_status slic_batch_iterations_run(slic_batch b, int *out) {
+    if (!b || !out) return bfail(b, SLIC_ERR_INVALID, "NULL argument");
+    cudaError_t e = cudaDeviceSynchronize();
+    for (int f = 0; f < b->n && e == cudaSuccess; ++f) {
+        ConvState cs{};
+        e = cudaMemcpy(&cs, b->frames[f].cstate, sizeof(ConvState), cudaMemcpyDeviceToHost);
+        out[f] = cs.iters;
+    }
+    if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("state read: ") + cudaGetErrorString(e));
     return SLIC_OK;
 }
 

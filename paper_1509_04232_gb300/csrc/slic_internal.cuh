@@ -85,6 +85,18 @@ static __device__ __forceinline__ void convert_pixel(const ConvConsts &cc, unsig
 
 #endif
 
+// Per-frame state of the stopping test (Sec. 2: the iteration ends once
+// the centres stabilise, read as the mean L1 move of their positions): the
+// sums of |dx| + |dy| over the centres in fixed point (scale kResidScale,
+// so the sums are exact whatever the order) for three consecutive updates
+// (slot = update index mod 3), the stop flag and the updates performed.
+struct ConvState {
+    long long resid[3];
+    int done;
+    int iters;
+};
+constexpr float kResidScale = 65536.0f;
+
 // One frame's geometry and buffers as seen by the kernels (a kernel
 // parameter for single-frame launches, an entry of a device-side table for
 // batched ones).
@@ -119,6 +131,8 @@ struct FrameArgs {
     int strips_x;           // fused connectivity: strips per row and first
     int strip_base;         // work unit (strip x row segment) of this frame
     int perturb;            // 1: grid seeds move to the lowest-gradient pixel nearby (Sec. 2)
+    float conv_eps;         // stopping threshold on the mean L1 move (0: fixed iterations)
+    ConvState *cstate;      // the frame's stopping-test state (reset by the initialisation)
 };
 
 // Shared memory for one assignment CTA whose tile spans at most win_n cells.
@@ -152,9 +166,12 @@ cudaError_t launch_assign(const FrameArgs &a, bool first, bool last, bool store_
                           cudaStream_t s);
 cudaError_t launch_assign_batch(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool first,
                                 bool last, size_t smem, int grid, cudaStream_t s);
+// Update `it` (1-based) of a run; with cstate (and eps > 0) it applies the
+// stopping test first and records its move (cstate may be null: a plain
+// update, as the stage-by-stage API does).
 cudaError_t launch_update(long long *acc, const float *centres_in, float *centres_out, int K, float fix_inv,
-                          cudaStream_t s);
-cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_centres, cudaStream_t s);
+                          ConvState *cstate, float eps, int it, cudaStream_t s);
+cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_centres, int it, cudaStream_t s);
 // Pipelined (TMA bulk copies, mbarrier) assignment for the passes after the
 // first, reading features and the padded centre table; *err is set on a
 // timed-out wait.

@@ -184,9 +184,18 @@ __device__ __forceinline__ void init_centre(const FrameArgs &a, int k) {
     for (int c = 0; c < 6; ++c) ak[c] = 0;
 }
 
+__device__ __forceinline__ void reset_conv(ConvState *cs) {
+    if (cs) {
+        cs->resid[0] = cs->resid[1] = cs->resid[2] = 0;
+        cs->done = 0;
+        cs->iters = 0;
+    }
+}
+
 __global__ void k_init_rgb(const __grid_constant__ FrameArgs a) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < a.ns_c * a.ns_r) init_centre(a, k);
+    if (k == 0) reset_conv(a.cstate);
 }
 
 // Batched initialisation; a frame with `init` set copies those centres
@@ -208,6 +217,7 @@ __global__ void k_init_batch(const FrameArgs *frames, int n, int total) {
     } else {
         init_centre(a, k);
     }
+    if (k == 0) reset_conv(a.cstate);
     if (a.ctab) {
         const int r = k / a.ns_c, c = k - (k / a.ns_c) * a.ns_c;
         write_ctab(a.ctab + ((size_t)(r + 1) * (a.ns_c + 2) + c + 1) * kCtabRec, a.centres_out + (size_t)k * 6);
@@ -634,8 +644,15 @@ __device__ __forceinline__ void assign_tile(const FrameArgs &fa, int tx0, int ty
     }
 }
 
+// A middle pass (it accumulates the next update's sums) has nothing to do
+// for a frame that passed its stopping test; the last pass always runs.
+__device__ __forceinline__ bool frame_stopped(const FrameArgs &a) {
+    return a.cstate && a.conv_eps > 0.0f && *reinterpret_cast<const volatile int *>(&a.cstate->done);
+}
+
 template <bool FIRST, bool LAST, bool SAME>
 __global__ void __launch_bounds__(kThreads, 3) k_assign(const __grid_constant__ FrameArgs a, int store_feat) {
+    if (!LAST && frame_stopped(a)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *lut = nullptr;
     if (FIRST) {
@@ -660,6 +677,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_batch(const FrameArgs *f
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
         const int f = find_frame<kTileBase>(frames, n_frames, tile);
         const FrameArgs &a = frames[f];
+        if (!LAST && frame_stopped(a)) continue;  // CTA-uniform
         const int local = tile - a.tile_base;
         const int ty = local / a.tiles_x, tx = local - ty * a.tiles_x;
         assign_tile<FIRST, LAST, SAME>(a, tx * kTileW, ty * kTileH, 0, smem_raw, lut);
@@ -827,7 +845,8 @@ struct __align__(16) TileGeom {
     float w, fix_scale;
     int32_t *labels;
     long long *acc;
-    int labels_vec, pad;
+    int labels_vec;
+    int skip;              // 1: the frame passed its stopping test (no copy was issued)
 };
 
 __device__ __forceinline__ TileGeom tile_geom(const FrameArgs &a, int local) {
@@ -843,7 +862,7 @@ __device__ __forceinline__ TileGeom tile_geom(const FrameArgs &a, int local) {
     g.labels = a.assign_out;
     g.acc = a.acc;
     g.labels_vec = a.assign_vec;
-    g.pad = 0;
+    g.skip = 0;
     const int ty = local / a.tiles_x, tx = local - ty * a.tiles_x;
     g.tx0 = tx * kTileW;
     g.ty0 = ty * kTileH;
@@ -994,8 +1013,12 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
         const int f = find_frame<kTileBase>(frames, n_frames, t);
         TileGeom g = tile_geom(frames[f], t - frames[f].tile_base);
         g.f = f;
+        g.skip = !LAST && frame_stopped(frames[f]) ? 1 : 0;
         hdr[j % kHdrSlots] = g;
-        issue_tile(frames[f], g, smem_raw + (size_t)q * stage_bytes, &full[q]);
+        if (g.skip)
+            mbar_arrive(&full[q]);  // a stopped frame's tile: no copy, the stage completes at once
+        else
+            issue_tile(frames[f], g, smem_raw + (size_t)q * stage_bytes, &full[q]);
         atomicMax(&flags[1], j);
         return true;
     };
@@ -1056,7 +1079,7 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
         for (int r = 0; r < ROWS; ++r) {
             const int ly = ly0 + 4 * r;
             y[r] = ty0 + ly;
-            row_ok[r] = (y[r] < H) && (x < W);
+            row_ok[r] = (y[r] < H) && (x < W) && !g.skip;
             if (row_ok[r]) {
                 const float4 v0 = *reinterpret_cast<const float4 *>(feat + (0 * kTileH + ly) * kTileW + lx);
                 const float4 v1 = *reinterpret_cast<const float4 *>(feat + (1 * kTileH + ly) * kTileW + lx);
@@ -1329,19 +1352,24 @@ cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cud
 // a small fraction of its FP32 rate): the sum rounded to float, scaled by the
 // power of two fix_inv (exact) and divided by the count (correctly rounded),
 // so within about one unit in the last place of the exact mean.
-__device__ __forceinline__ void update_centre(long long *ak, const float *ci, float *co, float fix_inv) {
+// Returns the centre's move |dx| + |dy| (0 for an empty cluster).
+__device__ __forceinline__ float update_centre(long long *ak, const float *ci, float *co, float fix_inv) {
     const longlong2 s01 = *reinterpret_cast<const longlong2 *>(ak);
     const longlong2 s23 = *reinterpret_cast<const longlong2 *>(ak + 2);
     const longlong2 s45 = *reinterpret_cast<const longlong2 *>(ak + 4);
     const long long n = s45.y;
+    float move = 0.0f;
     if (n > 0) {
         const float fn = (float)n;
+        const float x0 = ci[3], y0 = ci[4];
         co[0] = __fdiv_rn((float)s01.x * fix_inv, fn);
         co[1] = __fdiv_rn((float)s01.y * fix_inv, fn);
         co[2] = __fdiv_rn((float)s23.x * fix_inv, fn);
-        co[3] = __fdiv_rn((float)s23.y, fn);
-        co[4] = __fdiv_rn((float)s45.x, fn);
+        const float xn = __fdiv_rn((float)s23.y, fn), yn = __fdiv_rn((float)s45.x, fn);
+        co[3] = xn;
+        co[4] = yn;
         co[5] = fn;
+        move = fabsf(xn - x0) + fabsf(yn - y0);
     } else {
         if (co != ci) {
 #pragma unroll
@@ -1353,30 +1381,86 @@ __device__ __forceinline__ void update_centre(long long *ak, const float *ci, fl
     az[0] = make_longlong2(0, 0);
     az[1] = make_longlong2(0, 0);
     az[2] = make_longlong2(0, 0);
+    return move;
 }
 
-__global__ void k_update(long long *acc, const float *centres_in, float *centres_out, int K, float fix_inv) {
+// Stopping test before update `it` (1-based): the frame stops when it has
+// stopped already or update it-1 moved its K centres by a mean L1 distance
+// below eps (so update it-1 and its assignment were the last). Every thread
+// decides from the same stored values.
+__device__ __forceinline__ bool conv_stop(const ConvState *cs, float eps, int K, int it) {
+    if (!cs || !(eps > 0.0f)) return false;
+    if (*reinterpret_cast<const volatile int *>(&cs->done)) return true;
+    return it >= 2 && (double)cs->resid[(it - 1) % 3] < (double)eps * (double)kResidScale * (double)K;
+}
+
+// After update `it`: the sum of this warp's moves into the frame's slot
+// it % 3 (one atomic per warp when all its lanes belong to `cs`'s frame),
+// and, from the frame's first centre, the update count and the cleared slot
+// of update it+1.
+__device__ __forceinline__ void conv_record(ConvState *cs, bool uniform, float move, bool first, int it) {
+    long long v = (long long)__float2ll_rn(move * kResidScale);
+    if (uniform) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v != 0)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&cs->resid[it % 3]), (unsigned long long)v);
+    } else if (cs && v != 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&cs->resid[it % 3]), (unsigned long long)v);
+    }
+    if (cs && first) {
+        cs->resid[(it + 1) % 3] = 0;
+        cs->iters = it;
+    }
+}
+
+__global__ void k_update(long long *acc, const float *centres_in, float *centres_out, int K, float fix_inv,
+                         ConvState *cs, float eps, int it) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    update_centre(acc + (size_t)k * 6, centres_in + (size_t)k * 6, centres_out + (size_t)k * 6, fix_inv);
+    if (conv_stop(cs, eps, K, it)) {
+        if (k == 0) cs->done = 1;
+        return;
+    }
+    float move = 0.0f;
+    if (k < K)
+        move = update_centre(acc + (size_t)k * 6, centres_in + (size_t)k * 6, centres_out + (size_t)k * 6, fix_inv);
+    if (cs) conv_record(cs, __all_sync(0xffffffffu, k < K), move, k == 0, it);
 }
 
-__global__ void k_update_batch(const FrameArgs *frames, int n, int total) {
+__global__ void k_update_batch(const FrameArgs *frames, int n, int total, int it) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= total) return;
+    const bool valid = g < total;
     // Consecutive centres share a frame: one lookup per warp (its first
     // lane's frame, correct for every lane below the next frame's base),
     // a lane's own search only across a frame boundary.
-    const int g0 = __shfl_sync(__activemask(), g, 0);
-    int f = find_frame<kCentreBase>(frames, n, g0);
-    if (f + 1 < n && g >= frames[f + 1].centre_base) f = find_frame<kCentreBase>(frames, n, g);
+    const int g0 = __shfl_sync(0xffffffffu, g, 0);
+    int f = find_frame<kCentreBase>(frames, n, min(g0, total - 1));
+    if (valid && f + 1 < n && g >= frames[f + 1].centre_base) f = find_frame<kCentreBase>(frames, n, g);
+    const int f_lane0 = __shfl_sync(0xffffffffu, f, 0);  // (every lane takes part in each warp primitive)
+    const bool uniform = __all_sync(0xffffffffu, valid && f == f_lane0);
     const FrameArgs &a = frames[f];
     const int kk = g - a.centre_base;
-    const size_t k = (size_t)kk * 6;
-    update_centre(a.acc + k, a.centres_out + k, a.centres_out + k, 1.0f / a.fix_scale);
-    if (a.ctab) {
-        const int r = kk / a.ns_c, c = kk - r * a.ns_c;
-        write_ctab(a.ctab + ((size_t)(r + 1) * (a.ns_c + 2) + c + 1) * kCtabRec, a.centres_out + k);
+    float move = 0.0f;
+    bool stop = true;
+    if (valid) {
+        stop = conv_stop(a.cstate, a.conv_eps, a.ns_c * a.ns_r, it);
+        if (stop) {
+            if (kk == 0) a.cstate->done = 1;
+        } else {
+            const size_t k = (size_t)kk * 6;
+            move = update_centre(a.acc + k, a.centres_out + k, a.centres_out + k, 1.0f / a.fix_scale);
+            if (a.ctab) {
+                const int r = kk / a.ns_c, c = kk - r * a.ns_c;
+                write_ctab(a.ctab + ((size_t)(r + 1) * (a.ns_c + 2) + c + 1) * kCtabRec, a.centres_out + k);
+            }
+        }
+    }
+    // (a stopped frame stops for all its centres, so a uniform warp is all
+    // stopped or all running)
+    if (uniform) {
+        if (!stop && a.cstate) conv_record(a.cstate, true, move, kk == 0, it);
+    } else if (valid && !stop && a.cstate) {
+        conv_record(a.cstate, false, move, kk == 0, it);
     }
 }
 
@@ -1845,13 +1929,13 @@ int assign_batch_occupancy(bool same, size_t smem) {
 }
 
 cudaError_t launch_update(long long *acc, const float *centres_in, float *centres_out, int K, float fix_inv,
-                          cudaStream_t s) {
-    k_update<<<(K + 127) / 128, 128, 0, s>>>(acc, centres_in, centres_out, K, fix_inv);
+                          ConvState *cstate, float eps, int it, cudaStream_t s) {
+    k_update<<<(K + 127) / 128, 128, 0, s>>>(acc, centres_in, centres_out, K, fix_inv, cstate, eps, it);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_centres, cudaStream_t s) {
-    k_update_batch<<<(total_centres + 127) / 128, 128, 0, s>>>(d_frames, n, total_centres);
+cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_centres, int it, cudaStream_t s) {
+    k_update_batch<<<(total_centres + 127) / 128, 128, 0, s>>>(d_frames, n, total_centres, it);
     return cudaGetLastError();
 }
 

@@ -102,3 +102,95 @@ def test_batch_with_perturbation_bit_identical_to_single_frames(slic_gpu):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(labels[i].cpu().numpy(), l1.cpu().numpy())
         np.testing.assert_array_equal(centres[i].cpu().numpy(), c1.cpu().numpy())
+
+
+# --- stopping test (L1 move of the centres) -------------------------------------
+
+def _threshold_between(img, stop_after, **kw):
+    """A threshold halfway between the oracle's E of update `stop_after` and
+    the smallest E before it (both several percent away, where FP32 and FP64
+    differ by ~1e-6 relative, so both decide alike), or None when E does not
+    drop there by at least 5 %."""
+    runs = [oracle.slic(img, iterations=i, enforce_connectivity=False, **kw) for i in range(stop_after + 1)]
+    E = [None] + [oracle.residual(runs[i - 1]["centres"], runs[i]["centres"]) for i in range(1, stop_after + 1)]
+    before = min(E[1:stop_after])
+    if not E[stop_after] < 0.95 * before:
+        return None
+    return 0.5 * (E[stop_after] + before)
+
+
+def test_stopping_matches_oracle_and_fixed_runs(slic_gpu):
+    img = synth.voronoi_frame(320, 240, 40, 8.0, 41)
+    eps = _threshold_between(img, 3, S=16)
+    assert eps is not None
+    ref = oracle.slic(img, S=16, iterations=10, convergence=eps)
+    assert ref["iterations_run"] == 3
+    seg = slic_gpu.Segmenter(320, 240, S=16, iterations=10, convergence=eps)
+    labels, centres = seg.segment(_t(img))
+    assert seg.iterations_run == 3
+    assert np.mean(_np(labels) == ref["labels"]) >= AGREE_MIN
+    fixed = slic_gpu.Segmenter(320, 240, S=16, iterations=3)
+    l3, c3 = fixed.segment(_t(img))
+    np.testing.assert_array_equal(_np(labels), _np(l3))   # the same updates, then the last pass
+    np.testing.assert_array_equal(_np(centres), _np(c3))
+    # and again on the same handle: the state is reset by the initialisation
+    labels2, _ = seg.segment(_t(img))
+    assert seg.iterations_run == 3
+    np.testing.assert_array_equal(_np(labels2), _np(l3))
+
+
+def test_stopping_uniform_image_after_one_update(slic_gpu):
+    img = np.full((48, 64, 3), 77, np.uint8)
+    seg = slic_gpu.Segmenter(64, 48, S=16, iterations=8, convergence=1e-6)
+    seg.segment(_t(img))
+    assert seg.iterations_run == 1
+    plain = slic_gpu.Segmenter(64, 48, S=16, iterations=8)
+    plain.segment(_t(img))
+    assert plain.iterations_run == 8
+
+
+def test_stopping_is_per_frame_in_a_batch(slic_gpu):
+    """Frames that stop after 2, 3 and 4 updates and one that never stops,
+    in one batch (pipelined path): per-frame update counts, and results
+    bit-identical to single-frame runs with the same threshold."""
+    import torch
+    pkg = slic_gpu
+    specs = [(320, 240, 2, 51), (640, 480, 3, 52), (333, 256, 4, 53), (256, 192, 0, 54)]
+    frames, imgs, want = [], [], []
+    for W, H, stop, seed in specs:
+        img = synth.voronoi_frame(W, H, 40, 8.0, seed)
+        eps = 0.0
+        if stop:
+            eps = _threshold_between(img, stop, S=16)
+            assert eps is not None, (W, H, stop)
+        frames.append(dict(width=W, height=H, S=16, convergence=eps))
+        imgs.append(_t(img))
+        want.append(stop if stop else 6)
+    bs = pkg.BatchSegmenter(frames, iterations=6)
+    bs.bind(imgs)
+    labels, centres = bs.segment()
+    bs.status()
+    assert bs.iterations_run == want
+    for i, f in enumerate(frames):
+        seg = pkg.Segmenter(f["width"], f["height"], S=16, iterations=6, convergence=f["convergence"])
+        l1, c1 = seg.segment(imgs[i])
+        torch.cuda.synchronize()
+        assert seg.iterations_run == want[i]
+        np.testing.assert_array_equal(labels[i].cpu().numpy(), l1.cpu().numpy())
+        np.testing.assert_array_equal(centres[i].cpu().numpy(), c1.cpu().numpy())
+
+
+def test_stopping_in_the_allocation_free_path(slic_gpu):
+    import torch
+    from paper_1509_04232_gb300 import _binding
+    img = synth.voronoi_frame(320, 240, 40, 8.0, 41)
+    eps = _threshold_between(img, 3, S=16)
+    seg = slic_gpu.Segmenter(320, 240, S=16, iterations=10, convergence=eps)
+    want_l, want_c = seg.segment(_t(img))
+    labels = torch.empty((240, 320), dtype=torch.int32, device="cuda")
+    centres = torch.empty((seg.K_eff, 6), dtype=torch.float32, device="cuda")
+    p = _binding.slic_params(320, 240, 0, 16, 10.0, 10, 0, 1, 3, 0, float(eps))
+    _binding.slic_segment_noalloc(p, _t(img).data_ptr(), labels.data_ptr(), centres.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream)
+    np.testing.assert_array_equal(_np(labels), _np(want_l))
+    np.testing.assert_array_equal(_np(centres), _np(want_c))
