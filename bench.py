@@ -16,6 +16,7 @@ Prints ONE JSON line (rank 0). Keys beyond the base contract:
   quality       label agreement with 10 iterations, the plain path at 10
                 iterations, the learned warm start and the network forward
                 against the bf16 tensor roofline
+  sec2_options  the stopping test with early exit and the seed perturbation
   mixed_batch   the 256-frame mixed-resolution batch (context line)
 
 ``--impl reference`` times the FP64 CPU oracle itself (the only reference
@@ -352,6 +353,11 @@ def run_ours(args):
     if not args.no_quality:
         quality = quality_and_learned(args, pkg, images, B, stream, world, dev)
 
+    # --- the Sec. 2 options: stopping test with early exit, seed perturbation ---
+    options = None
+    if not args.no_options:
+        options = sec2_options(args, pkg, images, B, stream, world, dev, (ctas_per_sm, stages, rows))
+
     # --- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N=1) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -390,6 +396,7 @@ def run_ours(args):
                                  "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch}},
             "cpu_baseline": cpu,
             "quality": quality,
+            "sec2_options": options,
             "mixed_batch": mixed,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
@@ -457,6 +464,51 @@ def _graph_ms(graph, stream, args, world, dev):
         e1.record(stream)
     torch.cuda.synchronize()
     return max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
+
+
+def sec2_options(args, pkg, images, B, stream, world, dev, tuning):
+    """The two optional steps of Sec. 2 on the bench frames, in the tuned
+    launch shape, one CUDA graph per step timed like `value`: the stopping
+    test (mean L1 move of the centres below a threshold, per-frame early
+    exit, at most 10 iterations) at three thresholds, and the seed
+    perturbation (5 iterations). Agreement is measured on the first 8
+    frames against the 10-iteration labels (with perturbed seeds for the
+    perturbed run)."""
+    import torch
+    q = min(8, B)
+
+    def run(cfg, iterations):
+        bs = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M, **cfg)] * B, iterations=iterations, device=dev)
+        bs.bind([images[f] for f in range(B)])
+        bs.set_tuning(*tuning)
+        with torch.cuda.stream(stream):
+            bs.segment(stream)
+        torch.cuda.synchronize()
+        labels = [bs.labels[f].clone() for f in range(q)]
+        its = bs.iterations_run
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            bs.segment(stream)
+        ms = _graph_ms(g, stream, args, world, dev)
+        bs.close()
+        return labels, its, world * B / (ms / 1e3)
+
+    def agreement(a, b):
+        return float(np.mean([torch.eq(x, y).float().mean().item() for x, y in zip(a, b)]))
+
+    ref, _, fps10 = run({}, 10)
+    stopping = []
+    for eps in (0.5, 0.3, 0.2):
+        lab, its, fps = run(dict(convergence=eps), 10)
+        stopping.append({"threshold_px": eps, "frames_per_s": fps, "mean_updates": float(np.mean(its)),
+                         "agreement_with_10_iterations": round(agreement(lab, ref), 5)})
+    pref, _, _ = run(dict(perturb_seeds=True), 10)
+    plab, _, pfps = run(dict(perturb_seeds=True), ITERS)
+    _, _, fps5 = run({}, ITERS)
+    return {"frames": q, "plain_frames_per_s_at_10_iterations": fps10,
+            "stopping_test_max_10_iterations": stopping,
+            "seed_perturbation": {"iterations": ITERS, "frames_per_s": pfps, "plain_frames_per_s": fps5,
+                                  "agreement_with_own_10_iterations": round(agreement(plab, pref), 5)}}
 
 
 def quality_and_learned(args, pkg, images, B, stream, world, dev):
@@ -553,6 +605,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true", help="skip the agreement table and the learned path")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 256-frame mixed-resolution batch")
+    ap.add_argument("--no-options", action="store_true",
+                    help="skip the Sec. 2 options (stopping test, seed perturbation)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -89,9 +89,12 @@ static __device__ __forceinline__ void convert_pixel(const ConvConsts &cc, unsig
 // the centres stabilise, read as the mean L1 move of their positions): the
 // sums of |dx| + |dy| over the centres in fixed point (scale kResidScale,
 // so the sums are exact whatever the order) for three consecutive updates
-// (slot = update index mod 3), the stop flag and the updates performed.
+// (slot = update index mod 3), each spread over kResidLanes counters so
+// that a frame's warps do not all add to one address, the stop flag and the
+// updates performed.
+constexpr int kResidLanes = 8;
 struct ConvState {
-    long long resid[3];
+    long long resid[3][kResidLanes];
     int done;
     int iters;
 };

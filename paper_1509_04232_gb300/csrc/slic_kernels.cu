@@ -186,7 +186,8 @@ __device__ __forceinline__ void init_centre(const FrameArgs &a, int k) {
 
 __device__ __forceinline__ void reset_conv(ConvState *cs) {
     if (cs) {
-        cs->resid[0] = cs->resid[1] = cs->resid[2] = 0;
+#pragma unroll
+        for (int i = 0; i < 3 * kResidLanes; ++i) (&cs->resid[0][0])[i] = 0;
         cs->done = 0;
         cs->iters = 0;
     }
@@ -1014,6 +1015,7 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
         TileGeom g = tile_geom(frames[f], t - frames[f].tile_base);
         g.f = f;
         g.skip = !LAST && frame_stopped(frames[f]) ? 1 : 0;
+        if (g.skip) g.H = 0;  // no pixel of the tile is evaluated or summed
         hdr[j % kHdrSlots] = g;
         if (g.skip)
             mbar_arrive(&full[q]);  // a stopped frame's tile: no copy, the stage completes at once
@@ -1079,7 +1081,7 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
         for (int r = 0; r < ROWS; ++r) {
             const int ly = ly0 + 4 * r;
             y[r] = ty0 + ly;
-            row_ok[r] = (y[r] < H) && (x < W) && !g.skip;
+            row_ok[r] = (y[r] < H) && (x < W);  // (H = 0 in a skipped tile's header)
             if (row_ok[r]) {
                 const float4 v0 = *reinterpret_cast<const float4 *>(feat + (0 * kTileH + ly) * kTileW + lx);
                 const float4 v1 = *reinterpret_cast<const float4 *>(feat + (1 * kTileH + ly) * kTileW + lx);
@@ -1391,25 +1393,36 @@ __device__ __forceinline__ float update_centre(long long *ak, const float *ci, f
 __device__ __forceinline__ bool conv_stop(const ConvState *cs, float eps, int K, int it) {
     if (!cs || !(eps > 0.0f)) return false;
     if (*reinterpret_cast<const volatile int *>(&cs->done)) return true;
-    return it >= 2 && (double)cs->resid[(it - 1) % 3] < (double)eps * (double)kResidScale * (double)K;
+    if (it < 2) return false;
+    long long e = 0;
+#pragma unroll
+    for (int i = 0; i < kResidLanes; ++i) e += cs->resid[(it - 1) % 3][i];
+    return (double)e < (double)eps * (double)kResidScale * (double)K;
 }
 
-// After update `it`: the sum of this warp's moves into the frame's slot
-// it % 3 (one atomic per warp when all its lanes belong to `cs`'s frame),
-// and, from the frame's first centre, the update count and the cleared slot
-// of update it+1.
-__device__ __forceinline__ void conv_record(ConvState *cs, bool uniform, float move, bool first, int it) {
-    long long v = (long long)__float2ll_rn(move * kResidScale);
-    if (uniform) {
+// After update `it`: with the stopping test on, the sum of this warp's
+// moves into one of the frame's counters of slot it % 3 (one atomic per
+// warp when all its lanes belong to `cs`'s frame); from the frame's first
+// centre, the update count and the cleared slot of update it+1.
+__device__ __forceinline__ void conv_record(ConvState *cs, bool uniform, bool test_on, float move, bool first,
+                                            int it) {
+    if (test_on) {
+        long long v = (long long)__float2ll_rn(move * kResidScale);
+        const int lane_slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % kResidLanes;
+        if (uniform) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0 && v != 0)
-            atomicAdd(reinterpret_cast<unsigned long long *>(&cs->resid[it % 3]), (unsigned long long)v);
-    } else if (cs && v != 0) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(&cs->resid[it % 3]), (unsigned long long)v);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0 && v != 0)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&cs->resid[it % 3][lane_slot]), (unsigned long long)v);
+        } else if (v != 0) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&cs->resid[it % 3][lane_slot]), (unsigned long long)v);
+        }
     }
-    if (cs && first) {
-        cs->resid[(it + 1) % 3] = 0;
+    if (first) {
+        if (test_on) {
+#pragma unroll
+            for (int i = 0; i < kResidLanes; ++i) cs->resid[(it + 1) % 3][i] = 0;
+        }
         cs->iters = it;
     }
 }
@@ -1424,7 +1437,7 @@ __global__ void k_update(long long *acc, const float *centres_in, float *centres
     float move = 0.0f;
     if (k < K)
         move = update_centre(acc + (size_t)k * 6, centres_in + (size_t)k * 6, centres_out + (size_t)k * 6, fix_inv);
-    if (cs) conv_record(cs, __all_sync(0xffffffffu, k < K), move, k == 0, it);
+    if (cs) conv_record(cs, __all_sync(0xffffffffu, k < K), eps > 0.0f, move, k == 0, it);
 }
 
 __global__ void k_update_batch(const FrameArgs *frames, int n, int total, int it) {
@@ -1458,9 +1471,9 @@ __global__ void k_update_batch(const FrameArgs *frames, int n, int total, int it
     // (a stopped frame stops for all its centres, so a uniform warp is all
     // stopped or all running)
     if (uniform) {
-        if (!stop && a.cstate) conv_record(a.cstate, true, move, kk == 0, it);
+        if (!stop && a.cstate) conv_record(a.cstate, true, a.conv_eps > 0.0f, move, kk == 0, it);
     } else if (valid && !stop && a.cstate) {
-        conv_record(a.cstate, false, move, kk == 0, it);
+        conv_record(a.cstate, false, a.conv_eps > 0.0f, move, kk == 0, it);
     }
 }
 
