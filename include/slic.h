@@ -173,8 +173,10 @@ slic_status slic_profile_read(slic_handle h, double *assign_ms, long long *assig
 typedef struct slic_batch_ctx *slic_batch;
 
 /* params[f] describes frame f (same rules as slic_create); all frames need
-   the same iterations and enforce_connectivity. Allocates the batch's device
-   scratch (12*H*P + 48*K_eff + 4*W*H bytes per frame, 256-aligned parts). */
+   the same iterations and enforce_connectivity, while perturb_seeds and
+   convergence may differ per frame. Allocates the batch's device scratch
+   (12*H*P + 48*K_eff + 4*W*H + 48*(ns_c+2)*(ns_r+2) bytes per frame plus a
+   256-byte state record, 256-aligned parts). */
 slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batch *out);
 
 /* Bind the frames' buffers: host arrays of n device pointers, as in
