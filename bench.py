@@ -473,13 +473,15 @@ def sec2_options(args, pkg, images, B, stream, world, dev, tuning):
     exit, at most 10 iterations) at three thresholds, and the seed
     perturbation (5 iterations). Agreement is measured on the first 8
     frames against the 10-iteration labels (with perturbed seeds for the
-    perturbed run)."""
+    perturbed run). Also the input variants at the bench's iterations:
+    4-channel RGBA input and the raw-RGB and XYZ feature spaces."""
     import torch
     q = min(8, B)
 
-    def run(cfg, iterations):
+    def run(cfg, iterations, frames=None):
         bs = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M, **cfg)] * B, iterations=iterations, device=dev)
-        bs.bind([images[f] for f in range(B)])
+        src = frames if frames is not None else images
+        bs.bind([src[f] for f in range(B)])
         bs.set_tuning(*tuning)
         with torch.cuda.stream(stream):
             bs.segment(stream)
@@ -505,10 +507,18 @@ def sec2_options(args, pkg, images, B, stream, world, dev, tuning):
     pref, _, _ = run(dict(perturb_seeds=True), 10)
     plab, _, pfps = run(dict(perturb_seeds=True), ITERS)
     _, _, fps5 = run({}, ITERS)
+    # Input variants (scope row f3): 4-channel RGBA input, raw RGB and XYZ
+    # feature spaces, same frames and iterations as `value`.
+    rgba = [torch.cat([images[f], torch.full_like(images[f][..., :1], 255)], dim=-1).contiguous() for f in range(B)]
+    variants = {}
+    for name, cfg, frames in (("rgba_cielab", dict(in_channels=4), rgba), ("rgb_features", dict(color_space=1), None),
+                              ("xyz_features", dict(color_space=2), None)):
+        variants[name] = run(cfg, ITERS, frames)[2]
     return {"frames": q, "plain_frames_per_s_at_10_iterations": fps10,
             "stopping_test_max_10_iterations": stopping,
             "seed_perturbation": {"iterations": ITERS, "frames_per_s": pfps, "plain_frames_per_s": fps5,
-                                  "agreement_with_own_10_iterations": round(agreement(plab, pref), 5)}}
+                                  "agreement_with_own_10_iterations": round(agreement(plab, pref), 5)},
+            "input_variants_frames_per_s": variants}
 
 
 def quality_and_learned(args, pkg, images, B, stream, world, dev):

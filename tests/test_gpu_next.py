@@ -194,3 +194,30 @@ def test_stopping_in_the_allocation_free_path(slic_gpu):
                                   torch.cuda.current_stream().cuda_stream)
     np.testing.assert_array_equal(_np(labels), _np(want_l))
     np.testing.assert_array_equal(_np(centres), _np(want_c))
+
+
+# --- input variants (scope row f3) ---------------------------------------------
+
+def test_batch_rgba_and_feature_spaces_bit_identical_to_single_frames(slic_gpu):
+    """4-channel input (alpha ignored) and the RGB / XYZ feature spaces in one
+    pipelined batch: bit-identical to single-frame runs, and the RGBA frame
+    equal to its 3-channel twin."""
+    import torch
+    pkg = slic_gpu
+    rgb = [synth.voronoi_frame(256, 192, 30, 6.0, 60 + i) for i in range(3)]
+    rgba0 = np.concatenate([rgb[0], np.full(rgb[0].shape[:2] + (1,), 17, np.uint8)], axis=-1)
+    frames = [dict(width=256, height=192, S=16, in_channels=4), dict(width=256, height=192, S=16, color_space=1),
+              dict(width=256, height=192, S=16, color_space=2), dict(width=256, height=192, S=16)]
+    imgs = [_t(rgba0), _t(rgb[1]), _t(rgb[2]), _t(rgb[0])]
+    bs = pkg.BatchSegmenter(frames, iterations=5)
+    bs.bind(imgs)
+    labels, centres = bs.segment()
+    bs.status()
+    for i, f in enumerate(frames):
+        seg = pkg.Segmenter(256, 192, S=16, iterations=5, color_space=f.get("color_space", 0),
+                            in_channels=f.get("in_channels", 3))
+        l1, c1 = seg.segment(imgs[i])
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(labels[i].cpu().numpy(), l1.cpu().numpy())
+        np.testing.assert_array_equal(centres[i].cpu().numpy(), c1.cpu().numpy())
+    np.testing.assert_array_equal(labels[0].cpu().numpy(), labels[3].cpu().numpy())
