@@ -17,6 +17,7 @@ marshals numpy arrays through ctypes. Function-level citations:
 ``assign``             Eq. (1) and Sec. 3 "Finding the cluster associations"
 ``update``             Sec. 3 "Updating the cluster center"
 ``connectivity_pass``  Sec. 3 "Enforce connectivity" (one of the two passes)
+``connectivity_components``  Sec. 2, the original SLIC's component-based connectivity
 ``slic``               Sec. 4, the Perform_Segmentation stage order
 =====================  ==========================================================
 """
@@ -71,6 +72,8 @@ def _load():
         lib.oracle_connectivity_pass.argtypes = [P, I, I, P]
         lib.oracle_slic.argtypes = [P, I, I, I, I, I, D, I, I, I, P, I, D, P, P, P, P, P]
         lib.oracle_perturb_seeds.argtypes = [P, I, I, I, P, P, P]
+        lib.oracle_connectivity_components.argtypes = [P, I, I, I, P]
+        lib.oracle_connectivity_components.restype = I
         lib.oracle_residual.argtypes = [P, P, I]
         lib.oracle_residual.restype = D
         for f in (lib.oracle_grid, lib.oracle_convert, lib.oracle_init_centres, lib.oracle_assign,
@@ -166,8 +169,20 @@ def connectivity_pass(labels: np.ndarray) -> np.ndarray:
     return out
 
 
+def connectivity_components(labels: np.ndarray, min_size: int):
+    """Component-based relabelling (original SLIC's connectivity). Returns
+    (new labels int32 [H,W], number of segments kept)."""
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    H, W = labels.shape
+    out = np.empty_like(labels)
+    n = _load().oracle_connectivity_components(_ptr(labels), W, H, int(min_size), _ptr(out))
+    if n < 0:
+        raise ValueError("oracle connectivity_components failed")
+    return out, n
+
+
 def slic(rgb: np.ndarray, K: int = 0, S: int = 0, m: float = 10.0, iterations: int = 10,
-         color_space: int = CIELAB, enforce_connectivity: bool = True,
+         color_space: int = CIELAB, enforce_connectivity: int = 1,
          init_centres: np.ndarray | None = None, perturb_seeds: bool = False,
          convergence: float = 0.0) -> dict:
     """Whole SLIC run in the order of the paper's Perform_Segmentation.
@@ -190,8 +205,9 @@ def slic(rgb: np.ndarray, K: int = 0, S: int = 0, m: float = 10.0, iterations: i
         if ic.shape != centres.shape:
             raise ValueError("init_centres has the wrong shape")
     run = ctypes.c_int(0)
+    conn = int(enforce_connectivity)  # 0 off, 1 (True) the paper's local rule, 2 components
     _check(_load().oracle_slic(_ptr(rgb), W, H, C, K, S, float(m), iterations, color_space,
-                               int(bool(enforce_connectivity)), _ptr(ic), int(bool(perturb_seeds)),
+                               conn, _ptr(ic), int(bool(perturb_seeds)),
                                float(convergence), _ptr(labels), _ptr(centres), _ptr(pre), _ptr(margin),
                                ctypes.byref(run)), "slic")
     return {"labels": labels, "labels_pre": pre, "centres": centres, "margin": margin,

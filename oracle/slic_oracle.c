@@ -19,6 +19,7 @@
  *                                                           oracle_assign
  *   update          Sec. 3 "Updating the cluster center"    oracle_update
  *   connectivity    Sec. 3 "Enforce connectivity"           oracle_connectivity_pass
+ *   connectivity, original SLIC's components (Sec. 2)      oracle_connectivity_components
  *   driver          Sec. 4 Perform_Segmentation order       oracle_slic
  *
  * Readings where the paper is silent or garbled (each one is listed in the
@@ -351,13 +352,69 @@ int oracle_connectivity_pass(const int32_t *in, int W, int H, int32_t *out) {
     return 0;
 }
 
+/* Component-based connectivity, the original SLIC's notion of "connectivity
+ * is enforced" (Sec. 2), offered as an alternative to the paper's local rule.
+ * Readings: a segment is a 4-connected set of pixels with equal labels;
+ * segments are visited in scan order of their first pixel; one of at most
+ * min_size pixels (the caller passes S*S/4) is merged into the segment of
+ * its first pixel's left neighbour, or of its upper neighbour in column 0,
+ * taking that segment's final label; the segment of pixel (0, 0) is always
+ * kept; kept segments are numbered 0, 1, ... in the order visited.
+ * out[H*W] receives the new labels. Returns the number of segments kept,
+ * -1 on invalid arguments, -2 on allocation failure. */
+int oracle_connectivity_components(const int32_t *in, int W, int H, int min_size, int32_t *out) {
+    if (W <= 0 || H <= 0 || min_size < 0) return -1;
+    long N = (long)W * H;
+    long *queue = (long *)malloc(sizeof(long) * N);
+    if (!queue) return -2;
+    for (long i = 0; i < N; ++i) out[i] = -1;
+    int kept = 0;
+    for (long start = 0; start < N; ++start) {
+        if (out[start] >= 0) continue;
+        /* breadth-first search of the segment, marking its pixels with a
+           provisional label (kept) */
+        long head = 0, tail = 0;
+        queue[tail++] = start;
+        out[start] = kept;
+        while (head < tail) {
+            long i = queue[head++];
+            int x = (int)(i % W), y = (int)(i / W);
+            long nb[4];
+            int n = 0;
+            if (x > 0) nb[n++] = i - 1;
+            if (y > 0) nb[n++] = i - W;
+            if (x < W - 1) nb[n++] = i + 1;
+            if (y < H - 1) nb[n++] = i + W;
+            for (int j = 0; j < n; ++j) {
+                if (out[nb[j]] < 0 && in[nb[j]] == in[start]) {
+                    out[nb[j]] = kept;
+                    queue[tail++] = nb[j];
+                }
+            }
+        }
+        long size = tail;
+        int sx = (int)(start % W);
+        long adj = start == 0 ? -1 : (sx > 0 ? start - 1 : start - W);
+        if (size <= min_size && adj >= 0) {
+            /* merged: the neighbour's segment was visited earlier, so its
+               final label is already written */
+            for (long q = 0; q < size; ++q) out[queue[q]] = out[adj];
+        } else {
+            ++kept;
+        }
+    }
+    free(queue);
+    return kept;
+}
+
 /*
  * Sec. 4, Perform_Segmentation: convert; initialise centres (or take
  * init_centres when given, e.g. the previous video frame's), perturbed
  * when perturb_seeds is set (Sec. 2); assign; then up to `iterations` times
  * {update; assign}, ending after the first iteration whose update moved
- * the centres by E < convergence (Sec. 2; convergence 0: never); then, if
- * enabled, two connectivity passes.
+ * the centres by E < convergence (Sec. 2; convergence 0: never); then, with
+ * enforce_connectivity 1, two connectivity passes, or with 2 the
+ * component-based relabelling (minimum size S*S/4).
  *   labels   [H*W]      final labels
  *   centres  [K_eff*6]  centres the final labels were assigned against
  *   labels_pre [H*W]    optional: labels before connectivity
@@ -398,9 +455,16 @@ int oracle_slic(const uint8_t *rgb, int W, int H, int C, int K, int S_in, double
     if (iterations_run) *iterations_run = done;
     free(prev);
     if (labels_pre) memcpy(labels_pre, labels, sizeof(int32_t) * N);
-    if (enforce_connectivity) {
+    if (enforce_connectivity == 1) {
         oracle_connectivity_pass(labels, W, H, tmp);
         oracle_connectivity_pass(tmp, W, H, labels);
+    } else if (enforce_connectivity == 2) {
+        memcpy(tmp, labels, sizeof(int32_t) * N);
+        if (oracle_connectivity_components(tmp, W, H, S * S / 4, labels) < 0) {
+            free(feat);
+            free(tmp);
+            return -2;
+        }
     }
     free(feat);
     free(tmp);

@@ -125,3 +125,88 @@ def test_stopping_iteration_matches_fixed_runs():
 def test_convergence_zero_runs_every_iteration():
     img = synth.voronoi_frame(64, 48, 8, 6.0, 3)
     assert oracle.slic(img, S=16, iterations=4)["iterations_run"] == 4
+
+
+# --- component-based connectivity (the original SLIC's, scope row f4) ------------
+
+def _first_occurrence_order(lab):
+    """Labels in raster order of their first pixel."""
+    _, idx = np.unique(lab.ravel(), return_index=True)
+    return lab.ravel()[np.sort(idx)]
+
+
+def test_components_small_island_joins_its_left_neighbour():
+    lab = np.zeros((6, 6), np.int32)
+    lab[2, 2:4] = 1                       # 2 pixels <= 16/4: merged into the left pixel's segment
+    out, n = oracle.connectivity_components(lab, 4)
+    assert n == 1 and np.all(out == 0)
+
+
+def test_components_segment_at_the_origin_is_kept():
+    lab = np.zeros((6, 6), np.int32)
+    lab[0, 0:2] = 5                       # first segment in scan order, small but kept
+    out, n = oracle.connectivity_components(lab, 4)
+    want = np.ones((6, 6), np.int32)
+    want[0, 0:2] = 0
+    assert n == 2 and np.array_equal(out, want)
+
+
+def test_components_chain_of_small_segments():
+    """Row 0: R R A A B R ... (A, B small). A's first pixel has R on its left;
+    B's has A: B joins A's final segment, which is R's."""
+    lab = np.full((5, 8), 7, np.int32)
+    lab[0, 2:4] = 1
+    lab[0, 4] = 2
+    out, n = oracle.connectivity_components(lab, 4)
+    assert n == 1 and np.all(out == 0)
+
+
+def test_components_column_zero_uses_the_upper_neighbour():
+    lab = np.zeros((6, 6), np.int32)
+    lab[:3, 3:] = 3                       # a large second segment (9 pixels)
+    lab[4, 0] = 9                         # small, in column 0: joins the segment above
+    out, n = oracle.connectivity_components(lab, 4)
+    want = np.zeros((6, 6), np.int32)
+    want[:3, 3:] = 1
+    assert n == 2 and np.array_equal(out, want)
+
+
+def test_components_disconnected_label_is_two_segments():
+    lab = np.zeros((8, 8), np.int32)
+    lab[:, 3:5] = 1                       # splits label 0 into two large parts
+    out, n = oracle.connectivity_components(lab, 4)
+    assert n == 3
+    assert list(_first_occurrence_order(out)) == [0, 1, 2]
+    assert np.all(out[:, :3] == 0) and np.all(out[:, 3:5] == 1) and np.all(out[:, 5:] == 2)
+
+
+def test_components_huge_minimum_merges_everything_into_the_first():
+    lab = np.random.default_rng(2).integers(0, 6, (20, 30)).astype(np.int32)
+    out, n = oracle.connectivity_components(lab, 10**9)
+    assert n == 1 and np.all(out == 0)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_components_without_merging_is_connected_component_labelling(seed):
+    """min_size 0: every 4-connected component of each label is one segment,
+    as scipy.ndimage.label finds them, numbered in scan order."""
+    from scipy import ndimage
+    rng = np.random.default_rng(seed)
+    lab = rng.integers(0, 4, (23, 31)).astype(np.int32)
+    lab = np.repeat(np.repeat(lab, 2, axis=0), 3, axis=1)[:40, :70]  # blocky, with thin joins
+    out, n = oracle.connectivity_components(lab, 0)
+    total = 0
+    for v in np.unique(lab):
+        comp, k = ndimage.label(lab == v)   # default structure: 4-connectivity
+        total += k
+        for c in range(1, k + 1):
+            assert len(np.unique(out[comp == c])) == 1
+    assert n == total and len(np.unique(out)) == total
+    assert list(_first_occurrence_order(out)) == list(range(total))
+
+
+def test_whole_run_component_mode_applies_the_relabelling():
+    img = synth.voronoi_frame(96, 64, 12, 8.0, 19)
+    r = oracle.slic(img, S=8, iterations=3, enforce_connectivity=2)
+    want, _ = oracle.connectivity_components(r["labels_pre"], 8 * 8 // 4)
+    assert np.array_equal(r["labels"], want)
