@@ -62,7 +62,16 @@ typedef struct {
     float m;                  /* compactness, >= 0 (Eq. 1) */
     int iterations;           /* >= 0: centre updates after the first assignment */
     int color_space;          /* slic_color_space */
-    int enforce_connectivity; /* 0 or 1 */
+    int enforce_connectivity; /* 0: none; 1: the paper's two-pass local rule
+                                 (Sec. 3); 2: the original SLIC's components
+                                 (Sec. 2): 4-connected segments of equal
+                                 labels, one of at most S*S/4 pixels joins
+                                 the segment of its first pixel's left (in
+                                 column 0: upper) neighbour, the segment of
+                                 pixel 0 is kept, and the kept segments are
+                                 renumbered 0, 1, ... in scan order of their
+                                 first pixels (labels then no longer index
+                                 the centres) */
     int in_channels;          /* 3 or 4 */
     /* Sec. 2 steps of the original SLIC that the paper's GPU steps omit
        (both off by default, i.e. zero-initialised): */
@@ -108,6 +117,17 @@ slic_status slic_grid(slic_handle h, int *S, int *ns_c, int *ns_r);
    initialisation for this call only. */
 slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_labels, float *d_centres,
                          void *stream);
+
+/* Component-based connectivity (enforce_connectivity = 2) on its own:
+   d_in -> d_out label maps of the handle's size (they may be the same
+   buffer). SLIC_ERR_STATE unless the handle was created with mode 2 (it
+   owns the scratch: 16 bytes per pixel). */
+slic_status slic_connectivity_components(slic_handle h, const int32_t *d_in, int32_t *d_out, void *stream);
+
+/* Wait for the device, then report whether a bounded device loop of the
+   handle's component connectivity gave up since the last call
+   (SLIC_ERR_TIMEOUT; the labels are then incomplete). Clears the flag. */
+slic_status slic_status_check(slic_handle h);
 
 /* Wait for the device, then report how many centre updates the last
    slic_segment call performed: params.iterations, or fewer when the

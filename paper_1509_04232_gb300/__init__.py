@@ -15,7 +15,8 @@ from ._binding import (SLIC_CIELAB, SLIC_RGB, SLIC_XYZ, SlicError, library_path,
                        slic_batch_profile_read,
                        slic_batch_profile_times, slic_batch_segment, slic_batch_segment_host,
                        slic_batch_set_buffers, slic_batch_set_tuning, slic_batch_status,
-                       slic_connectivity_pass, slic_convert, slic_create, slic_destroy, slic_grid,
+                       slic_connectivity_components, slic_connectivity_pass, slic_convert, slic_create,
+                       slic_destroy, slic_grid, slic_status_check,
                        slic_init_centres, slic_iterations_run, slic_last_error, slic_launch_count, slic_params,
                        slic_profile_enable, slic_profile_read, slic_segment, slic_segment_noalloc,
                        slic_set_init_centres, slic_update)
@@ -33,10 +34,11 @@ class Segmenter:
     space, iterations, connectivity), owning a library handle."""
 
     def __init__(self, width: int, height: int, *, K: int = 0, S: int = 0, m: float = 10.0,
-                 iterations: int = 10, color_space: int = SLIC_CIELAB, enforce_connectivity: bool = True,
+                 iterations: int = 10, color_space: int = SLIC_CIELAB, enforce_connectivity: int = 1,
                  in_channels: int = 3, perturb_seeds: bool = False, convergence: float = 0.0):
+        # enforce_connectivity: 0 / False none, 1 / True the paper's rule, 2 components
         self.params = slic_params(width, height, K, S, float(m), iterations, color_space,
-                                  int(bool(enforce_connectivity)), in_channels, int(bool(perturb_seeds)),
+                                  int(enforce_connectivity), in_channels, int(bool(perturb_seeds)),
                                   float(convergence))
         self.handle = slic_create(self.params)
         self.S, self.ns_c, self.ns_r = slic_grid(self.handle)
@@ -99,6 +101,17 @@ class Segmenter:
                     _stream_handle(stream))
         return out
 
+    def connectivity_components(self, labels, stream=None):
+        """Component-based relabelling (handles created with enforce_connectivity=2)."""
+        import torch
+        out = torch.empty_like(labels)
+        slic_connectivity_components(self.handle, labels.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def status(self):
+        """Raises SlicError(SLIC_ERR_TIMEOUT) if a bounded device loop gave up."""
+        slic_status_check(self.handle)
+
     def connectivity_pass(self, labels, stream=None):
         import torch
         out = torch.empty_like(labels)
@@ -125,10 +138,10 @@ class BatchSegmenter:
     tensors are allocated here (``labels[f]`` int32 [H, W], ``centres[f]``
     float32 [K_eff, 6])."""
 
-    def __init__(self, frames, *, iterations: int = 5, enforce_connectivity: bool = True, device=None):
+    def __init__(self, frames, *, iterations: int = 5, enforce_connectivity: int = 1, device=None):
         import torch
         self.params = [slic_params(f["width"], f["height"], f.get("K", 0), f.get("S", 0), float(f.get("m", 10.0)),
-                                   iterations, f.get("color_space", SLIC_CIELAB), int(bool(enforce_connectivity)),
+                                   iterations, f.get("color_space", SLIC_CIELAB), int(enforce_connectivity),
                                    f.get("in_channels", 3), int(bool(f.get("perturb_seeds", False))),
                                    float(f.get("convergence", 0.0))) for f in frames]
         self.handle = slic_batch_create(self.params)

@@ -66,6 +66,8 @@ _SIGNATURES = {
     "slic_batch_status": [_P],
     "slic_batch_iterations_run": [_P, ctypes.POINTER(_I)],
     "slic_iterations_run": [_P, ctypes.POINTER(_I)],
+    "slic_connectivity_components": [_P, _P, _P, _P],
+    "slic_status_check": [_P],
     "slic_batch_profile_enable": [_P, _I],
     "slic_batch_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
     "slic_batch_profile_times": [_P, ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(_I)],
@@ -247,6 +249,15 @@ def slic_batch_info(b: int):
     _bcheck(lib().slic_batch_info(b, ctypes.byref(px), ctypes.byref(n), ctypes.byref(c), ctypes.byref(st),
                                   ctypes.byref(rw)), b)
     return px.value, n.value, c.value, st.value, rw.value
+
+
+def slic_connectivity_components(h: int, d_in: int, d_out: int, stream: int = 0) -> None:
+    _check(lib().slic_connectivity_components(h, d_in, d_out, stream or None), h)
+
+
+def slic_status_check(h: int) -> None:
+    """Raise SlicError(SLIC_ERR_TIMEOUT) if a bounded device loop gave up."""
+    _check(lib().slic_status_check(h), h)
 
 
 def slic_iterations_run(h: int) -> int:

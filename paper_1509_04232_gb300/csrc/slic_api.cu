@@ -27,6 +27,8 @@ struct slic_ctx {
     long long *acc = nullptr;     // [K][6]
     int32_t *lbl_tmp = nullptr;   // [H][W] connectivity ping-pong
     ConvState *cstate = nullptr;  // stopping-test state of the current run
+    int *ccl = nullptr;           // component connectivity scratch (mode 2), and its error flag
+    int *ccl_err = nullptr;
     float fix_scale = 0.0f;
     size_t smem_max = 0;
     ConvConsts conv{};
@@ -207,8 +209,8 @@ slic_status slic_create(const slic_params *params, slic_handle *out) {
     if (p.iterations < 0) return fail(nullptr, SLIC_ERR_INVALID, "iterations must be >= 0");
     if (p.color_space < 0 || p.color_space > 2) return fail(nullptr, SLIC_ERR_INVALID, "unknown color_space");
     if (p.in_channels != 3 && p.in_channels != 4) return fail(nullptr, SLIC_ERR_INVALID, "in_channels must be 3 or 4");
-    if (p.enforce_connectivity != 0 && p.enforce_connectivity != 1)
-        return fail(nullptr, SLIC_ERR_INVALID, "enforce_connectivity must be 0 or 1");
+    if (p.enforce_connectivity < 0 || p.enforce_connectivity > 2)
+        return fail(nullptr, SLIC_ERR_INVALID, "enforce_connectivity must be 0, 1 or 2");
     if (p.perturb_seeds != 0 && p.perturb_seeds != 1)
         return fail(nullptr, SLIC_ERR_INVALID, "perturb_seeds must be 0 or 1");
     if (!(p.convergence >= 0.0f) || !std::isfinite(p.convergence))
@@ -245,12 +247,16 @@ slic_status slic_create(const slic_params *params, slic_handle *out) {
         cudaMalloc(&h->acc, sizeof(long long) * 6 * (size_t)h->K) != cudaSuccess ||
         cudaMalloc(&h->lbl_tmp, sizeof(int32_t) * npix) != cudaSuccess ||
         cudaMalloc(&h->cstate, sizeof(ConvState)) != cudaSuccess ||
-        cudaMemset(h->cstate, 0, sizeof(ConvState)) != cudaSuccess) {
+        cudaMemset(h->cstate, 0, sizeof(ConvState)) != cudaSuccess || cudaMalloc(&h->ccl_err, sizeof(int)) != cudaSuccess ||
+        cudaMemset(h->ccl_err, 0, sizeof(int)) != cudaSuccess ||
+        (p.enforce_connectivity == 2 && cudaMalloc(&h->ccl, sizeof(int) * ccl_scratch_ints((long long)npix)) != cudaSuccess)) {
         cudaGetLastError();
         cudaFree(h->feat);
         cudaFree(h->acc);
         cudaFree(h->lbl_tmp);
         cudaFree(h->cstate);
+        cudaFree(h->ccl_err);
+        cudaFree(h->ccl);
         delete h;
         return fail(nullptr, SLIC_ERR_NOMEM, "device allocation of scratch failed");
     }
@@ -271,6 +277,8 @@ slic_status slic_destroy(slic_handle h) {
     cudaFree(h->acc);
     cudaFree(h->lbl_tmp);
     cudaFree(h->cstate);
+    cudaFree(h->ccl);
+    cudaFree(h->ccl_err);
     for (auto &ev : h->events) {
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
@@ -337,11 +345,16 @@ slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_label
         slic_status st = assign_launch(h, a, pass == 0, pass == n, pass != n, s);
         if (st != SLIC_OK) return st;
     }
-    if (h->p.enforce_connectivity) {
+    if (h->p.enforce_connectivity == 1) {
         e = launch_connectivity(d_labels, h->lbl_tmp, h->p.width, h->p.height, s);
         if (e == cudaSuccess) e = launch_connectivity(h->lbl_tmp, d_labels, h->p.width, h->p.height, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "connectivity kernel launch");
         h->launches += 2;
+    } else if (h->p.enforce_connectivity == 2) {
+        e = launch_connectivity_components(d_labels, d_labels, h->p.width, h->p.height, h->S * h->S / 4, h->ccl,
+                                           h->ccl_err, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "component connectivity launch");
+        h->launches += 9;
     }
     return SLIC_OK;
 }
@@ -398,6 +411,28 @@ slic_status slic_connectivity_pass(slic_handle h, const int32_t *d_in, int32_t *
     cudaError_t e = launch_connectivity(d_in, d_out, h->p.width, h->p.height, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "connectivity kernel launch");
     ++h->launches;
+    return SLIC_OK;
+}
+
+slic_status slic_connectivity_components(slic_handle h, const int32_t *d_in, int32_t *d_out, void *stream) {
+    if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    if (!d_in || !d_out) return fail(h, SLIC_ERR_INVALID, "NULL buffer");
+    if (!h->ccl) return fail(h, SLIC_ERR_STATE, "the handle was not created with enforce_connectivity = 2");
+    cudaError_t e = launch_connectivity_components(d_in, d_out, h->p.width, h->p.height, h->S * h->S / 4, h->ccl,
+                                                   h->ccl_err, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "component connectivity launch");
+    h->launches += 9;
+    return SLIC_OK;
+}
+
+slic_status slic_status_check(slic_handle h) {
+    if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    int flag = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, h->ccl_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && flag) e = cudaMemset(h->ccl_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+    if (flag) return fail(h, SLIC_ERR_TIMEOUT, "a bounded device loop gave up");
     return SLIC_OK;
 }
 
@@ -490,8 +525,8 @@ extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uin
     if (p.iterations < 0) return fail(nullptr, SLIC_ERR_INVALID, "iterations must be >= 0");
     if (p.color_space < 0 || p.color_space > 2) return fail(nullptr, SLIC_ERR_INVALID, "unknown color_space");
     if (p.in_channels != 3 && p.in_channels != 4) return fail(nullptr, SLIC_ERR_INVALID, "in_channels must be 3 or 4");
-    if (p.enforce_connectivity != 0 && p.enforce_connectivity != 1)
-        return fail(nullptr, SLIC_ERR_INVALID, "enforce_connectivity must be 0 or 1");
+    if (p.enforce_connectivity < 0 || p.enforce_connectivity > 2)
+        return fail(nullptr, SLIC_ERR_INVALID, "enforce_connectivity must be 0, 1 or 2");
     if (p.perturb_seeds != 0 && p.perturb_seeds != 1)
         return fail(nullptr, SLIC_ERR_INVALID, "perturb_seeds must be 0 or 1");
     if (!(p.convergence >= 0.0f) || !std::isfinite(p.convergence))
@@ -509,11 +544,13 @@ extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uin
     const size_t feat_b = align256(sizeof(float) * 3 * (size_t)p.height * P);
     const size_t acc_b = align256(sizeof(long long) * 6 * (size_t)K);
     const size_t lbl_b = align256(sizeof(int32_t) * (size_t)p.width * p.height);
-    const size_t cs_b = align256(sizeof(ConvState));
-    if (feat_b + acc_b + lbl_b + cs_b > kStaticScratchBytes)
+    const size_t cs_b = align256(sizeof(ConvState) + sizeof(int));
+    const size_t ccl_b =
+        p.enforce_connectivity == 2 ? align256(sizeof(int) * ccl_scratch_ints((long long)p.width * p.height)) : 0;
+    if (feat_b + acc_b + lbl_b + cs_b + ccl_b > kStaticScratchBytes)
         return fail(nullptr, SLIC_ERR_INVALID,
                     "image too large for the static scratch: needs " +
-                        std::to_string(feat_b + acc_b + lbl_b + cs_b) +
+                        std::to_string(feat_b + acc_b + lbl_b + cs_b + ccl_b) +
                         " bytes, the limit is " + std::to_string(kStaticScratchBytes) + " (32 MiB)");
 
     int dev = 0;
@@ -562,9 +599,16 @@ extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uin
             e = launch_update(a.acc, d_centres, d_centres, (int)K, 1.0f / a.fix_scale, a.cstate, a.conv_eps, pass, s);
         if (e == cudaSuccess) e = launch_assign(a, pass == 0, pass == p.iterations, false, smem, s);
     }
-    if (e == cudaSuccess && p.enforce_connectivity) {
+    if (e == cudaSuccess && p.enforce_connectivity == 1) {
         e = launch_connectivity(d_labels, lbl_tmp, p.width, p.height, s);
         if (e == cudaSuccess) e = launch_connectivity(lbl_tmp, d_labels, p.width, p.height, s);
+    } else if (e == cudaSuccess && p.enforce_connectivity == 2) {
+        int *ccl_err = reinterpret_cast<int *>(base + feat_b + acc_b + lbl_b + sizeof(ConvState));
+        e = cudaMemsetAsync(ccl_err, 0, sizeof(int), s);
+        if (e == cudaSuccess)
+            e = launch_connectivity_components(d_labels, d_labels, p.width, p.height, S * S / 4,
+                                               reinterpret_cast<int *>(base + feat_b + acc_b + lbl_b + cs_b), ccl_err,
+                                               s);
     }
     if (e != cudaSuccess) return fail(nullptr, SLIC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return SLIC_OK;

@@ -30,6 +30,7 @@ struct slic_batch_ctx {
     std::vector<FrameArgs> frames;    // host copy of the descriptor table
     FrameArgs *d_frames = nullptr;    // device copy
     unsigned char *scratch = nullptr; // features, sums, connectivity labels of all frames
+    std::vector<int *> ccl;           // per frame: component connectivity scratch (mode 2)
     int total_tiles = 0, total_centres = 0, total_rows = 0, max_w = 0, win_max = 0;
     int total_units = 0;  // work units of the fused connectivity kernel
     long long total_pixels = 0;
@@ -122,8 +123,8 @@ bool valid_params(const slic_params &p, std::string &why) {
     if (p.iterations < 0) { why = "iterations must be >= 0"; return false; }
     if (p.color_space < 0 || p.color_space > 2) { why = "unknown color_space"; return false; }
     if (p.in_channels != 3 && p.in_channels != 4) { why = "in_channels must be 3 or 4"; return false; }
-    if (p.enforce_connectivity != 0 && p.enforce_connectivity != 1) {
-        why = "enforce_connectivity must be 0 or 1";
+    if (p.enforce_connectivity < 0 || p.enforce_connectivity > 2) {
+        why = "enforce_connectivity must be 0, 1 or 2";
         return false;
     }
     if (p.perturb_seeds != 0 && p.perturb_seeds != 1) { why = "perturb_seeds must be 0 or 1"; return false; }
@@ -218,7 +219,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
     // Geometry, bases and the scratch layout.
     size_t bytes = 0;
     std::vector<size_t> off_feat(n_frames), off_acc(n_frames), off_lbl(n_frames), off_ctab(n_frames),
-        off_cs(n_frames);
+        off_cs(n_frames), off_ccl(n_frames);
     long long tiles = 0, centres = 0, rows = 0;
     for (int f = 0; f < n_frames; ++f) {
         const slic_params &p = params[f];
@@ -275,6 +276,9 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         bytes += align256(sizeof(float) * kCtabRec * (size_t)(a.ns_c + 2) * (a.ns_r + 2));
         off_cs[f] = bytes;
         bytes += align256(sizeof(ConvState));
+        off_ccl[f] = bytes;
+        if (params[0].enforce_connectivity == 2)
+            bytes += align256(sizeof(int) * ccl_scratch_ints((long long)p.width * p.height));
         b->max_ring = std::max(b->max_ring, 2 * (a.ns_c + 2) + 2 * a.ns_r);
     }
     const size_t off_err = bytes;
@@ -316,6 +320,8 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         a.lbl_tmp = reinterpret_cast<int32_t *>(b->scratch + off_lbl[f]);
         a.ctab = reinterpret_cast<float *>(b->scratch + off_ctab[f]);
         a.cstate = reinterpret_cast<ConvState *>(b->scratch + off_cs[f]);
+        b->ccl.push_back(params[0].enforce_connectivity == 2 ? reinterpret_cast<int *>(b->scratch + off_ccl[f])
+                                                            : nullptr);
         if (b->pipe && !encode_maps(a)) b->pipe = false;  // then every pass uses k_assign_batch
     }
     b->d_err = reinterpret_cast<int *>(b->scratch + off_err);
@@ -357,7 +363,7 @@ slic_status slic_batch_set_buffers(slic_batch b, const uint8_t *const *d_images,
         a.labels_vec = ((a.W & 3) == 0 && ((uintptr_t)a.labels & 15) == 0) ? 1 : 0;
         // The pipelined last pass writes lbl_tmp when the fused connectivity
         // kernel follows (it reads lbl_tmp and writes the labels).
-        const bool fused = b->pipe && b->connectivity;
+        const bool fused = b->pipe && b->connectivity == 1;
         a.assign_out = fused ? a.lbl_tmp : a.labels;
         a.assign_vec = fused ? ((a.W & 3) == 0 ? 1 : 0) : a.labels_vec;
     }
@@ -418,7 +424,14 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
             ++n_launch;
         }
     }
-    if (e == cudaSuccess && b->connectivity) {
+    if (e == cudaSuccess && b->connectivity == 2) {
+        // component-based connectivity, frame by frame, in place on the labels
+        for (int f = 0; f < b->n && e == cudaSuccess; ++f) {
+            const FrameArgs &a = b->frames[f];
+            e = launch_connectivity_components(a.labels, a.labels, a.W, a.H, a.S * a.S / 4, b->ccl[f], b->d_err, s);
+            n_launch += 9;
+        }
+    } else if (e == cudaSuccess && b->connectivity) {
         if (b->pipe) {
             e = launch_connectivity2_batch(b->d_frames, b->n, b->total_units, b->sms * 8, s);
             n_launch += 1;

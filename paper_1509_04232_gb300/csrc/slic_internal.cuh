@@ -203,6 +203,13 @@ cudaError_t launch_connectivity_batch(const FrameArgs *d_frames, int n, int tota
 // (strips x segments) and its strips per row:
 int connectivity2_units(int W, int H, int *strips_x);
 cudaError_t launch_connectivity2_batch(const FrameArgs *d_frames, int n, int total_units, int grid, cudaStream_t s);
+// Component-based connectivity (connectivity mode 2): in -> out over a W x H
+// label map (out may equal in), segments of at most min_size pixels joined
+// to a neighbour. scratch holds ccl_scratch_ints(W*H) ints; a bounded walk
+// that gives up sets bit 1 of *err.
+size_t ccl_scratch_ints(long long N);
+cudaError_t launch_connectivity_components(const int32_t *in, int32_t *out, int W, int H, int min_size,
+                                           int *scratch, int *err, cudaStream_t s);
 // Event record for the profiling timers, valid inside and outside stream capture.
 cudaError_t record_profile_event(cudaEvent_t ev, cudaStream_t s);
 

@@ -1817,6 +1817,185 @@ __global__ void __launch_bounds__(256, 4) k_connectivity2_batch(const FrameArgs 
 }
 
 // ---------------------------------------------------------------------------
+// Component-based connectivity (the original SLIC's notion of enforcing
+// connectivity, Sec. 2), an alternative to the paper's local rule: the
+// 4-connected segments of equal labels, in scan order of their first pixel;
+// a segment of at most min_size pixels joins the segment of its first
+// pixel's left neighbour (its upper one in column 0), the segment of pixel 0
+// is kept, and kept segments are numbered 0, 1, ... in scan order.
+//
+// Union-find over pixel indices: a pixel's parent always has a smaller
+// index, so each component's root is its first pixel in scan order. Every
+// walk is bounded; a walk that gives up sets bit 1 of *err.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr unsigned kCclSteps = 1u << 22;
+constexpr int kScanThreads = 256, kScanPer = 8, kScanBlock = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int ccl_find(const int *parent, int i, int *err) {
+    for (unsigned n = 0; n < kCclSteps; ++n) {
+        const int p = __ldcg(parent + i);
+        if (p == i) return i;
+        i = p;
+    }
+    atomicOr(err, 2);
+    return i;
+}
+
+// Link the trees of a and b: the larger root takes the smaller as parent
+// (atomicMin; a root changed meanwhile is followed and the link retried).
+__device__ __forceinline__ void ccl_union(int *parent, int a, int b, int *err) {
+    for (unsigned n = 0; n < kCclSteps; ++n) {
+        a = ccl_find(parent, a, err);
+        b = ccl_find(parent, b, err);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicMin(parent + a, b);
+        if (old == a) return;
+        a = old;
+    }
+    atomicOr(err, 2);
+}
+}  // namespace
+
+// Parent = the first pixel of the pixel's horizontal run within the warp's
+// 32 pixels, or the pixel before the warp when the run comes from there.
+__global__ void k_ccl_init(const int32_t *lab, int N, int W, int *parent) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+    const bool valid = i < N;
+    const int32_t v = valid ? lab[i] : 0;
+    const int32_t left = __shfl_up_sync(kFull, v, 1);
+    bool same_left = false;
+    if (valid && i % W > 0) same_left = lane == 0 ? lab[i - 1] == v : left == v;
+    const unsigned starts = __ballot_sync(kFull, !same_left) & (kFull >> (31 - lane));
+    if (valid) parent[i] = starts ? i - lane + (31 - __clz(starts)) : i - lane - 1;
+}
+
+// Vertical links; a pixel whose left neighbour is in its run and has the same
+// link above needs none of its own.
+__global__ void k_ccl_merge(const int32_t *lab, int N, int W, int *parent, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N || i < W) return;
+    const int32_t v = lab[i];
+    if (lab[i - W] != v) return;
+    if (i % W > 0 && lab[i - 1] == v && lab[i - W - 1] == v) return;
+    ccl_union(parent, i, i - W, err);
+}
+
+__global__ void k_ccl_compress(int N, int *parent, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) parent[i] = ccl_find(parent, i, err);
+}
+
+// Segment sizes (count zeroed beforehand), one atomic per root per warp.
+__global__ void k_ccl_count(int N, const int *parent, int *count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+    const int r = i < N ? parent[i] : -1;
+    const unsigned peers = __match_any_sync(kFull, r);
+    if (r >= 0 && lane == __ffs(peers) - 1) atomicAdd(count + r, __popc(peers));
+}
+
+// Per root: itself when kept, else the root of its first pixel's left (or,
+// in column 0, upper) neighbour.
+__global__ void k_ccl_decide(int N, int W, int min_size, const int *parent, const int *count, int *target) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N || parent[i] != i) return;
+    int t = i;
+    if (i != 0 && count[i] <= min_size) t = parent[i % W > 0 ? i - 1 : i - W];
+    target[i] = t;
+}
+
+// Per root: follow the joins to the kept segment (chains point to smaller
+// indices and end at a kept root; in place, every value written stays on
+// the chain).
+__global__ void k_ccl_resolve(int N, const int *parent, int *target, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N || parent[i] != i) return;
+    int t = target[i];
+    unsigned n = 0;
+    for (; n < kCclSteps; ++n) {
+        const int u = __ldcg(target + t);
+        if (u == t) break;
+        t = u;
+    }
+    if (n == kCclSteps) atomicOr(err, 2);
+    target[i] = t;
+}
+
+// Exclusive scan of the kept-root flags, block by block (kScanBlock pixels):
+// rank[i] within the block, totals[block] the block's count.
+__global__ void __launch_bounds__(kScanThreads) k_ccl_scan_block(int N, const int *parent, const int *target,
+                                                                  int *rank, int *totals) {
+    __shared__ int warp_sum[kScanThreads / 32];
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int f[kScanPer], sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+        const int i = base + j;
+        f[j] = (i < N && parent[i] == i && target[i] == i) ? 1 : 0;
+        sum += f[j];
+    }
+    int incl = sum;  // inclusive scan of the thread sums within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += warp_sum[w];
+    int run = before + incl - sum;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+        const int i = base + j;
+        if (i < N) rank[i] = run;
+        run += f[j];
+    }
+    if (threadIdx.x == kScanThreads - 1) totals[blockIdx.x] = run;
+}
+
+// Exclusive scan of the block totals, in place (one block).
+__global__ void __launch_bounds__(1024) k_ccl_scan_totals(int nb, int *totals) {
+    __shared__ int warp_sum[32];
+    __shared__ int carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nb; c0 += 1024) {
+        const int i = c0 + threadIdx.x;
+        const int v = i < nb ? totals[i] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
+        __syncthreads();
+        int before = carry;
+        for (int w = 0; w < warp; ++w) before += warp_sum[w];
+        if (i < nb) totals[i] = before + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = before + incl;
+        __syncthreads();
+    }
+}
+
+__global__ void k_ccl_relabel(int N, const int *parent, const int *target, const int *rank, const int *totals,
+                              int32_t *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int f = target[parent[i]];
+    out[i] = rank[f] + totals[f / kScanBlock];
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
 
@@ -1971,6 +2150,29 @@ cudaError_t launch_convert(const ConvConsts &cc, const uint8_t *rgb, int W, int 
 cudaError_t launch_connectivity(const int32_t *in, int32_t *out, int W, int H, cudaStream_t s) {
     const int vec = ((W & 3) == 0 && ((uintptr_t)in & 15) == 0 && ((uintptr_t)out & 15) == 0) ? 1 : 0;
     k_connectivity<<<rows_grid(W, H, 64, 4), 64, 0, s>>>(in, out, W, H, vec);
+    return cudaGetLastError();
+}
+
+size_t ccl_scratch_ints(long long N) {
+    return (size_t)N * 4 + (size_t)((N + kScanBlock - 1) / kScanBlock) + 64;
+}
+
+cudaError_t launch_connectivity_components(const int32_t *in, int32_t *out, int W, int H, int min_size,
+                                           int *scratch, int *err, cudaStream_t s) {
+    const int N = W * H, nb = (N + kScanBlock - 1) / kScanBlock, g = (N + 255) / 256;
+    int *parent = scratch, *count = scratch + N, *target = scratch + 2 * (size_t)N, *rank = scratch + 3 * (size_t)N;
+    int *totals = scratch + 4 * (size_t)N;
+    k_ccl_init<<<g, 256, 0, s>>>(in, N, W, parent);
+    k_ccl_merge<<<g, 256, 0, s>>>(in, N, W, parent, err);
+    k_ccl_compress<<<g, 256, 0, s>>>(N, parent, err);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)N, s);
+    if (e != cudaSuccess) return e;
+    k_ccl_count<<<g, 256, 0, s>>>(N, parent, count);
+    k_ccl_decide<<<g, 256, 0, s>>>(N, W, min_size, parent, count, target);
+    k_ccl_resolve<<<g, 256, 0, s>>>(N, parent, target, err);
+    k_ccl_scan_block<<<nb, kScanThreads, 0, s>>>(N, parent, target, rank, totals);
+    k_ccl_scan_totals<<<1, 1024, 0, s>>>(nb, totals);
+    k_ccl_relabel<<<g, 256, 0, s>>>(N, parent, target, rank, totals, out);
     return cudaGetLastError();
 }
 

@@ -52,7 +52,7 @@ def test_binding_covers_every_declared_symbol():
     (dict(iterations=-1), "iterations"),
     (dict(color_space=7), "color_space"),
     (dict(in_channels=2), "in_channels"),
-    (dict(enforce_connectivity=2), "enforce_connectivity"),
+    (dict(enforce_connectivity=3), "enforce_connectivity"),
     (dict(width=1 << 21), "width"),
     (dict(perturb_seeds=2), "perturb_seeds"),
     (dict(convergence=-0.5), "convergence"),

@@ -221,3 +221,69 @@ def test_batch_rgba_and_feature_spaces_bit_identical_to_single_frames(slic_gpu):
         np.testing.assert_array_equal(labels[i].cpu().numpy(), l1.cpu().numpy())
         np.testing.assert_array_equal(centres[i].cpu().numpy(), c1.cpu().numpy())
     np.testing.assert_array_equal(labels[0].cpu().numpy(), labels[3].cpu().numpy())
+
+
+# --- component-based connectivity (scope row f4) --------------------------------
+
+def _blocky(seed, H, W, k=4):
+    rng = np.random.default_rng(seed)
+    lab = rng.integers(0, k, (H // 2 + 1, W // 3 + 1)).astype(np.int32)
+    return np.ascontiguousarray(np.repeat(np.repeat(lab, 2, axis=0), 3, axis=1)[:H, :W])
+
+
+@pytest.mark.parametrize("W,H,S,kind", [(64, 48, 8, "blocky"), (333, 257, 13, "blocky"), (1, 37, 2, "blocky"),
+                                        (37, 1, 3, "blocky"), (5, 3, 1, "noise"), (200, 150, 16, "noise"),
+                                        (1920, 1080, 16, "slic"), (640, 480, 4, "slic")])
+def test_components_stage_matches_oracle(slic_gpu, W, H, S, kind):
+    if kind == "blocky":
+        lab = _blocky(W + H, H, W)
+    elif kind == "noise":
+        lab = np.random.default_rng(W).integers(0, 3, (H, W)).astype(np.int32)
+    else:  # pre-connectivity labels of a GPU run: the maps the mode sees in practice
+        img = synth.voronoi_frame(W, H, 60, 8.0, 5)
+        lab = _np(slic_gpu.Segmenter(W, H, S=S, iterations=3, enforce_connectivity=0).segment(_t(img))[0])
+    seg = slic_gpu.Segmenter(W, H, S=S, enforce_connectivity=2)
+    got = _np(seg.connectivity_components(_t(lab)))
+    seg.status()
+    want, n = oracle.connectivity_components(lab, S * S // 4)
+    np.testing.assert_array_equal(got, want)
+    assert got.max() == n - 1
+
+
+def test_components_whole_run_and_paths(slic_gpu):
+    """A whole run in mode 2 equals the oracle's relabelling of the same
+    run's pre-connectivity labels; the batch and the allocation-free paths
+    give the same labels bit for bit."""
+    import torch
+    from paper_1509_04232_gb300 import _binding
+    pkg = slic_gpu
+    W, H, S = 640, 480, 16
+    imgs = [synth.voronoi_frame(W, H, 60, 8.0, 70 + i) for i in range(3)]
+    outs = []
+    for img in imgs:
+        pre = _np(pkg.Segmenter(W, H, S=S, iterations=5, enforce_connectivity=0).segment(_t(img))[0])
+        seg = pkg.Segmenter(W, H, S=S, iterations=5, enforce_connectivity=2)
+        lab, _ = seg.segment(_t(img))
+        seg.status()
+        want, _ = oracle.connectivity_components(pre, S * S // 4)
+        np.testing.assert_array_equal(_np(lab), want)
+        outs.append(_np(lab))
+    bs = pkg.BatchSegmenter([dict(width=W, height=H, S=S)] * 3, iterations=5, enforce_connectivity=2)
+    dev = [_t(x) for x in imgs]
+    bs.bind(dev)
+    labels, _ = bs.segment()
+    bs.status()
+    for i in range(3):
+        np.testing.assert_array_equal(labels[i].cpu().numpy(), outs[i])
+    lab = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    cen = torch.empty(((W // S) * (H // S), 6), dtype=torch.float32, device="cuda")
+    p = _binding.slic_params(W, H, 0, S, 10.0, 5, 0, 2, 3)
+    _binding.slic_segment_noalloc(p, dev[0].data_ptr(), lab.data_ptr(), cen.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream)
+    np.testing.assert_array_equal(_np(lab), outs[0])
+
+
+def test_components_stage_needs_mode_two(slic_gpu):
+    seg = slic_gpu.Segmenter(32, 32, S=8)
+    with pytest.raises(slic_gpu.SlicError):
+        seg.connectivity_components(_t(np.zeros((32, 32), np.int32)))
