@@ -474,12 +474,14 @@ def sec2_options(args, pkg, images, B, stream, world, dev, tuning):
     perturbation (5 iterations). Agreement is measured on the first 8
     frames against the 10-iteration labels (with perturbed seeds for the
     perturbed run). Also the input variants at the bench's iterations:
-    4-channel RGBA input and the raw-RGB and XYZ feature spaces."""
+    4-channel RGBA input and the raw-RGB and XYZ feature spaces, and the
+    component-based connectivity mode."""
     import torch
     q = min(8, B)
 
-    def run(cfg, iterations, frames=None):
-        bs = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M, **cfg)] * B, iterations=iterations, device=dev)
+    def run(cfg, iterations, frames=None, connectivity=1):
+        bs = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M, **cfg)] * B, iterations=iterations, device=dev,
+                                enforce_connectivity=connectivity)
         src = frames if frames is not None else images
         bs.bind([src[f] for f in range(B)])
         bs.set_tuning(*tuning)
@@ -514,11 +516,15 @@ def sec2_options(args, pkg, images, B, stream, world, dev, tuning):
     for name, cfg, frames in (("rgba_cielab", dict(in_channels=4), rgba), ("rgb_features", dict(color_space=1), None),
                               ("xyz_features", dict(color_space=2), None)):
         variants[name] = run(cfg, ITERS, frames)[2]
+    # Component-based connectivity (the original SLIC's; scope row f4) in
+    # place of the paper's two-pass rule, same frames and iterations.
+    comp_fps = run({}, ITERS, None, 2)[2]
     return {"frames": q, "plain_frames_per_s_at_10_iterations": fps10,
             "stopping_test_max_10_iterations": stopping,
             "seed_perturbation": {"iterations": ITERS, "frames_per_s": pfps, "plain_frames_per_s": fps5,
                                   "agreement_with_own_10_iterations": round(agreement(plab, pref), 5)},
-            "input_variants_frames_per_s": variants}
+            "input_variants_frames_per_s": variants,
+            "component_connectivity_frames_per_s": comp_fps}
 
 
 def quality_and_learned(args, pkg, images, B, stream, world, dev):
