@@ -14,7 +14,7 @@ namespace slicgb {
 // features are integers already (scale 1). Every partial sum is then an
 // exact integer, so the result does not depend on summation order, tiling
 // or batching. |f| * 2^15 < 2^22 lets the pipelined kernel round on the FMA
-// pipe (fix_round); a centre moves by at most 2^-16 from the exact mean.
+// pipe (fix_round2); a centre moves by at most 2^-16 from the exact mean.
 constexpr float kFixScaleFrac = 32768.0f;
 
 // Assignment tile: 32 x 32 pixels, 256 threads, 4 horizontally adjacent

@@ -757,16 +757,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
     return false;
 }
 
-// round(x * fs) (nearest, ties to even) as a two's-complement word, on the
-// FMA pipe: with M = 1.5 * 2^23, x * fs + M lies in [2^23, 2^24) where the
-// float spacing is 1, so the one rounding of the fused multiply-add is the
-// rounding to an integer and the low mantissa bits are that integer + 2^22.
-// Exact for |x * fs| < 2^22 (features below 128 at the 2^15 colour scale,
-// 8-bit values at scale 1), and equal to __float2int_rn(x * fs) there since
-// fs is a power of two.
-__device__ __forceinline__ unsigned fix_round(float x, float fs) {
-    return (unsigned)(__float_as_int(fmaf(x, fs, 12582912.0f)) - 0x4B400000);
-}
 
 // Paired FP32 arithmetic: a 64-bit operand holds two floats (low, high);
 // each element is rounded exactly as the scalar instruction would be.
@@ -793,7 +783,14 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
-// fix_round for two values with one paired fused multiply-add.
+// round(x * fs) (nearest, ties to even) as a two's-complement word, for
+// two values with one paired fused multiply-add on the FMA pipe: with
+// M = 1.5 * 2^23, x * fs + M lies in [2^23, 2^24) where the float spacing is
+// 1, so the one rounding of the fused multiply-add is the rounding to an
+// integer and the low mantissa bits are that integer + 2^22. Exact for
+// |x * fs| < 2^22 (features below 128 at the 2^15 colour scale, 8-bit
+// values at scale 1), and equal to __float2int_rn(x * fs) there since fs is
+// a power of two.
 __device__ __forceinline__ void fix_round2(float x0, float x1, float fs, unsigned &r0, unsigned &r1) {
     const unsigned long long m = fma2(pack2(x0, x1), pack2(fs, fs), pack2(12582912.0f, 12582912.0f));
     float m0, m1;
