@@ -31,6 +31,7 @@ struct slic_batch_ctx {
     FrameArgs *d_frames = nullptr;    // device copy
     unsigned char *scratch = nullptr; // features, sums, connectivity labels of all frames
     std::vector<int *> ccl;           // per frame: component connectivity scratch (mode 2)
+    bool any_conv = false;            // some frame has a stopping threshold
     int total_tiles = 0, total_centres = 0, total_rows = 0, max_w = 0, win_max = 0;
     int total_units = 0;  // work units of the fused connectivity kernel
     long long total_pixels = 0;
@@ -244,6 +245,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         a.tiles_x = (p.width + kTileW - 1) / kTileW;
         a.perturb = p.perturb_seeds;
         a.conv_eps = p.convergence;
+        b->any_conv = b->any_conv || p.convergence > 0.0f;
         a.tile_base = (int)tiles;
         a.centre_base = (int)centres;
         a.row_base = (int)rows;
@@ -416,7 +418,7 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
             if (e != cudaSuccess) break;
             if (b->pipe)
                 e = launch_assign_pipe(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == b->iterations,
-                                       b->stages, b->rows, pipe_per_sm, grid_pipe, b->d_err, s);
+                                       b->stages, b->rows, pipe_per_sm, grid_pipe, b->d_err, b->any_conv ? 1 : 0, s);
             else
                 e = launch_assign_batch(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == 0,
                                         pass == b->iterations, b->smem, grid, s);

@@ -181,8 +181,11 @@ cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_cent
 // rows = 1: 256 threads, 4 pixels per thread (ctas_per_sm >= 4 selects the
 // 64-register build); rows = 2: 128 threads, 8 pixels per thread (two row
 // groups in one cell row: every frame's S a multiple of 8, `same` set).
+// check_stop: some frame has a stopping threshold (its tiles are then skipped
+// once it has stopped).
 cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool last,
-                               int nst, int rows, int ctas_per_sm, int grid, int *err, cudaStream_t s);
+                               int nst, int rows, int ctas_per_sm, int grid, int *err, int check_stop,
+                               cudaStream_t s);
 // Shared memory and resident CTAs per SM of the pipelined kernel with nst
 // (3..4) stages and 1 or 2 row groups per warp.
 size_t assign_pipe_smem_bytes(int win_n, bool last, int nst, int rows);

@@ -951,7 +951,7 @@ size_t assign_pipe_smem_bytes(int win_n, bool last, int nst, int rows) {
 template <bool LAST, bool SAME, int MINB, int ROWS>
 __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const FrameArgs *frames, int n_frames,
                                                                        int total_tiles, int win_max, int nst,
-                                                                       int *err) {
+                                                                       int *err, int check_stop) {
     // ROWS = 1: 8 warps, warp w evaluates rows 4w..4w+3 of the tile.
     // ROWS = 2: 4 warps, warp w evaluates rows 8w..8w+3 and 8w+4..8w+7 (the
     // same cell row when S is a multiple of 8), sharing the centre loads and
@@ -1011,7 +1011,7 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
         const int f = find_frame<kTileBase>(frames, n_frames, t);
         TileGeom g = tile_geom(frames[f], t - frames[f].tile_base);
         g.f = f;
-        g.skip = !LAST && frame_stopped(frames[f]) ? 1 : 0;
+        g.skip = !LAST && check_stop && frame_stopped(frames[f]) ? 1 : 0;
         if (g.skip) g.H = 0;  // no pixel of the tile is evaluated or summed
         hdr[j % kHdrSlots] = g;
         if (g.skip)
@@ -1304,16 +1304,18 @@ int assign_pipe_occupancy(bool same, int win_n, int nst, int rows) {
 
 template <bool L, bool SM, int MINB, int ROWS>
 static cudaError_t launch_pipe_as(const FrameArgs *d_frames, int n, int total_tiles, int win_max, int nst, int grid,
-                                  size_t smem, int *err, cudaStream_t s) {
+                                  size_t smem, int *err, int check_stop, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_assign_pipe<L, SM, MINB, ROWS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_assign_pipe<L, SM, MINB, ROWS><<<grid, kThreads / ROWS, smem, s>>>(d_frames, n, total_tiles, win_max, nst, err);
+    k_assign_pipe<L, SM, MINB, ROWS><<<grid, kThreads / ROWS, smem, s>>>(d_frames, n, total_tiles, win_max, nst, err,
+                                                                           check_stop);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool last,
-                               int nst, int rows, int ctas_per_sm, int grid, int *err, cudaStream_t s) {
+                               int nst, int rows, int ctas_per_sm, int grid, int *err, int check_stop,
+                               cudaStream_t s) {
     if (grid > total_tiles) grid = total_tiles;
     if (grid < 1) grid = 1;
     if (nst < 3) nst = 3;
@@ -1321,21 +1323,21 @@ cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles
     if (rows == 2 && !same) return cudaErrorInvalidValue;
     const size_t smem = assign_pipe_smem_bytes(win_max, last, nst, rows);
     if (rows == 2)
-        return last ? launch_pipe_as<true, true, 4, 2>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
-                    : launch_pipe_as<false, true, 4, 2>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
+        return last ? launch_pipe_as<true, true, 4, 2>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s)
+                    : launch_pipe_as<false, true, 4, 2>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s);
     const bool wide = ctas_per_sm >= 4;  // 64-register build
     if (same) {
         if (last)
-            return wide ? launch_pipe_as<true, true, 4, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
-                        : launch_pipe_as<true, true, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
-        return wide ? launch_pipe_as<false, true, 4, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
-                    : launch_pipe_as<false, true, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
+            return wide ? launch_pipe_as<true, true, 4, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s)
+                        : launch_pipe_as<true, true, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s);
+        return wide ? launch_pipe_as<false, true, 4, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s)
+                    : launch_pipe_as<false, true, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s);
     }
     if (last)
-        return wide ? launch_pipe_as<true, false, 4, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
-                    : launch_pipe_as<true, false, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
-    return wide ? launch_pipe_as<false, false, 4, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s)
-                : launch_pipe_as<false, false, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, s);
+        return wide ? launch_pipe_as<true, false, 4, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s)
+                    : launch_pipe_as<true, false, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s);
+    return wide ? launch_pipe_as<false, false, 4, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s)
+                : launch_pipe_as<false, false, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s);
 }
 
 cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cudaStream_t s) {
@@ -1351,8 +1353,10 @@ cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cud
 // a small fraction of its FP32 rate): the sum rounded to float, scaled by the
 // power of two fix_inv (exact) and divided by the count (correctly rounded),
 // so within about one unit in the last place of the exact mean.
-// Returns the centre's move |dx| + |dy| (0 for an empty cluster).
-__device__ __forceinline__ float update_centre(long long *ak, const float *ci, float *co, float fix_inv) {
+// Returns the centre's move |dx| + |dy| (0 for an empty cluster, or when
+// want_move is false: the old position is then not read).
+__device__ __forceinline__ float update_centre(long long *ak, const float *ci, float *co, float fix_inv,
+                                               bool want_move) {
     const longlong2 s01 = *reinterpret_cast<const longlong2 *>(ak);
     const longlong2 s23 = *reinterpret_cast<const longlong2 *>(ak + 2);
     const longlong2 s45 = *reinterpret_cast<const longlong2 *>(ak + 4);
@@ -1360,7 +1364,7 @@ __device__ __forceinline__ float update_centre(long long *ak, const float *ci, f
     float move = 0.0f;
     if (n > 0) {
         const float fn = (float)n;
-        const float x0 = ci[3], y0 = ci[4];
+        const float x0 = want_move ? ci[3] : 0.0f, y0 = want_move ? ci[4] : 0.0f;
         co[0] = __fdiv_rn((float)s01.x * fix_inv, fn);
         co[1] = __fdiv_rn((float)s01.y * fix_inv, fn);
         co[2] = __fdiv_rn((float)s23.x * fix_inv, fn);
@@ -1368,7 +1372,7 @@ __device__ __forceinline__ float update_centre(long long *ak, const float *ci, f
         co[3] = xn;
         co[4] = yn;
         co[5] = fn;
-        move = fabsf(xn - x0) + fabsf(yn - y0);
+        if (want_move) move = fabsf(xn - x0) + fabsf(yn - y0);
     } else {
         if (co != ci) {
 #pragma unroll
@@ -1433,7 +1437,8 @@ __global__ void k_update(long long *acc, const float *centres_in, float *centres
     }
     float move = 0.0f;
     if (k < K)
-        move = update_centre(acc + (size_t)k * 6, centres_in + (size_t)k * 6, centres_out + (size_t)k * 6, fix_inv);
+        move = update_centre(acc + (size_t)k * 6, centres_in + (size_t)k * 6, centres_out + (size_t)k * 6, fix_inv,
+                             eps > 0.0f);
     if (cs) conv_record(cs, __all_sync(0xffffffffu, k < K), eps > 0.0f, move, k == 0, it);
 }
 
@@ -1458,7 +1463,8 @@ __global__ void k_update_batch(const FrameArgs *frames, int n, int total, int it
             if (kk == 0) a.cstate->done = 1;
         } else {
             const size_t k = (size_t)kk * 6;
-            move = update_centre(a.acc + k, a.centres_out + k, a.centres_out + k, 1.0f / a.fix_scale);
+            move = update_centre(a.acc + k, a.centres_out + k, a.centres_out + k, 1.0f / a.fix_scale,
+                                 a.conv_eps > 0.0f);
             if (a.ctab) {
                 const int r = kk / a.ns_c, c = kk - r * a.ns_c;
                 write_ctab(a.ctab + ((size_t)(r + 1) * (a.ns_c + 2) + c + 1) * kCtabRec, a.centres_out + k);
