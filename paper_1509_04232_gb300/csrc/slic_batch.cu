@@ -30,7 +30,9 @@ struct slic_batch_ctx {
     std::vector<FrameArgs> frames;    // host copy of the descriptor table
     FrameArgs *d_frames = nullptr;    // device copy
     unsigned char *scratch = nullptr; // features, sums, connectivity labels of all frames
-    std::vector<int *> ccl;           // per frame: component connectivity scratch (mode 2)
+    int *ccl = nullptr;               // component connectivity (mode 2): scratch over all frames' pixels,
+    CclFrame *d_ccl = nullptr;        // the frames' table (device) and its host copy
+    std::vector<CclFrame> ccl_frames;
     bool any_conv = false;            // some frame has a stopping threshold
     int total_tiles = 0, total_centres = 0, total_rows = 0, max_w = 0, win_max = 0;
     int total_units = 0;  // work units of the fused connectivity kernel
@@ -220,7 +222,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
     // Geometry, bases and the scratch layout.
     size_t bytes = 0;
     std::vector<size_t> off_feat(n_frames), off_acc(n_frames), off_lbl(n_frames), off_ctab(n_frames),
-        off_cs(n_frames), off_ccl(n_frames);
+        off_cs(n_frames);
     long long tiles = 0, centres = 0, rows = 0;
     for (int f = 0; f < n_frames; ++f) {
         const slic_params &p = params[f];
@@ -278,13 +280,22 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         bytes += align256(sizeof(float) * kCtabRec * (size_t)(a.ns_c + 2) * (a.ns_r + 2));
         off_cs[f] = bytes;
         bytes += align256(sizeof(ConvState));
-        off_ccl[f] = bytes;
-        if (params[0].enforce_connectivity == 2)
-            bytes += align256(sizeof(int) * ccl_scratch_ints((long long)p.width * p.height));
         b->max_ring = std::max(b->max_ring, 2 * (a.ns_c + 2) + 2 * a.ns_r);
     }
     const size_t off_err = bytes;
     bytes += 256;
+    // component connectivity: one scratch over all frames' pixels and the table
+    size_t off_ccl = 0, off_ccl_table = 0;
+    if (b->connectivity == 2) {
+        if (b->total_pixels >= (1LL << 31)) {
+            delete b;
+            return bfail(nullptr, SLIC_ERR_INVALID, "component connectivity needs fewer than 2^31 pixels per batch");
+        }
+        off_ccl = bytes;
+        bytes += align256(sizeof(int) * ccl_scratch_ints(b->total_pixels));
+        off_ccl_table = bytes;
+        bytes += align256(sizeof(CclFrame) * (size_t)n_frames);
+    }
     b->total_tiles = (int)tiles;
     b->total_centres = (int)centres;
     b->total_rows = (int)rows;
@@ -322,11 +333,13 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         a.lbl_tmp = reinterpret_cast<int32_t *>(b->scratch + off_lbl[f]);
         a.ctab = reinterpret_cast<float *>(b->scratch + off_ctab[f]);
         a.cstate = reinterpret_cast<ConvState *>(b->scratch + off_cs[f]);
-        b->ccl.push_back(params[0].enforce_connectivity == 2 ? reinterpret_cast<int *>(b->scratch + off_ccl[f])
-                                                            : nullptr);
         if (b->pipe && !encode_maps(a)) b->pipe = false;  // then every pass uses k_assign_batch
     }
     b->d_err = reinterpret_cast<int *>(b->scratch + off_err);
+    if (b->connectivity == 2) {
+        b->ccl = reinterpret_cast<int *>(b->scratch + off_ccl);
+        b->d_ccl = reinterpret_cast<CclFrame *>(b->scratch + off_ccl_table);
+    }
     if (cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess) {
         slic_batch_destroy(b);
         return bfail(nullptr, SLIC_ERR_CUDA, "clearing the error flag failed");
@@ -369,10 +382,21 @@ slic_status slic_batch_set_buffers(slic_batch b, const uint8_t *const *d_images,
         a.assign_out = fused ? a.lbl_tmp : a.labels;
         a.assign_vec = fused ? ((a.W & 3) == 0 ? 1 : 0) : a.labels_vec;
     }
-    // Synchronous upload: the table must not change under queued work.
+    if (b->connectivity == 2) {
+        b->ccl_frames.assign(b->n, CclFrame{});
+        int base = 0;
+        for (int f = 0; f < b->n; ++f) {
+            const FrameArgs &a = b->frames[f];
+            b->ccl_frames[f] = CclFrame{a.labels, a.labels, a.W, a.S * a.S / 4, base};
+            base += a.W * a.H;
+        }
+    }
+    // Synchronous upload: the tables must not change under queued work.
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_frames, b->frames.data(), sizeof(FrameArgs) * b->n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b->connectivity == 2)
+        e = cudaMemcpy(b->d_ccl, b->ccl_frames.data(), sizeof(CclFrame) * b->n, cudaMemcpyHostToDevice);
     // Sentinel ring of the padded centre tables (geometry only).
     if (e == cudaSuccess) e = launch_fill_ring(b->d_frames, b->n, b->max_ring, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -427,12 +451,10 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
         }
     }
     if (e == cudaSuccess && b->connectivity == 2) {
-        // component-based connectivity, frame by frame, in place on the labels
-        for (int f = 0; f < b->n && e == cudaSuccess; ++f) {
-            const FrameArgs &a = b->frames[f];
-            e = launch_connectivity_components(a.labels, a.labels, a.W, a.H, a.S * a.S / 4, b->ccl[f], b->d_err, s);
-            n_launch += 9;
-        }
+        // component-based connectivity over all frames at once, in place on the labels
+        e = launch_connectivity_components(b->d_ccl, b->ccl_frames[0], b->n, (int)b->total_pixels, b->ccl, b->d_err,
+                                           s);
+        n_launch += 9;
     } else if (e == cudaSuccess && b->connectivity) {
         if (b->pipe) {
             e = launch_connectivity2_batch(b->d_frames, b->n, b->total_units, b->sms * 8, s);

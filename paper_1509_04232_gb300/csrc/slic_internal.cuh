@@ -213,6 +213,19 @@ cudaError_t launch_connectivity2_batch(const FrameArgs *d_frames, int n, int tot
 size_t ccl_scratch_ints(long long N);
 cudaError_t launch_connectivity_components(const int32_t *in, int32_t *out, int W, int H, int min_size,
                                            int *scratch, int *err, cudaStream_t s);
+// Several frames at once: d_table[n] (device) describes each frame, base =
+// its first index in the concatenation of all frames' pixels (G in total,
+// below 2^31); scratch holds ccl_scratch_ints(G) ints. For n == 1, `one`
+// is used and d_table may be null.
+struct CclFrame {
+    const int32_t *in;
+    int32_t *out;
+    int W;
+    int min_size;
+    int base;
+};
+cudaError_t launch_connectivity_components(const CclFrame *d_table, const CclFrame &one, int n, int G, int *scratch,
+                                           int *err, cudaStream_t s);
 // Event record for the profiling timers, valid inside and outside stream capture.
 cudaError_t record_profile_event(cudaEvent_t ev, cudaStream_t s);
 

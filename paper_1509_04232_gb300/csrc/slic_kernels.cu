@@ -1865,28 +1865,60 @@ __device__ __forceinline__ void ccl_union(int *parent, int a, int b, int *err) {
 }
 }  // namespace
 
+// The frames of a call: pixels of all frames form one index space (frame f
+// holds base_f .. base_f + W_f*H_f - 1), so parents and roots are global
+// indices and a pixel's left / upper neighbour is g - 1 / g - W_f. One frame
+// travels in the launch itself, several in a device table.
+struct CclFrames {
+    const CclFrame *table;
+    CclFrame one;
+    int n;
+};
+
+__device__ __forceinline__ CclFrame ccl_frame_of(const CclFrames &fr, int g) {
+    if (fr.n == 1) return fr.one;
+    int lo = 0, hi = fr.n - 1;
+    while (lo < hi) {  // last frame whose base <= g
+        const int mid = (lo + hi + 1) >> 1;
+        if (fr.table[mid].base <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return fr.table[lo];
+}
+
 // Parent = the first pixel of the pixel's horizontal run within the warp's
-// 32 pixels, or the pixel before the warp when the run comes from there.
-__global__ void k_ccl_init(const int32_t *lab, int N, int W, int *parent) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
-    const bool valid = i < N;
-    const int32_t v = valid ? lab[i] : 0;
+// 32 pixels, or the pixel before the warp when the run comes from there (a
+// run never crosses a row, hence never a frame).
+__global__ void k_ccl_init(CclFrames fr, int G, int *parent) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+    const bool valid = g < G;
+    CclFrame f{};
+    int32_t v = 0;
+    int i = 0;
+    if (valid) {
+        f = ccl_frame_of(fr, g);
+        i = g - f.base;
+        v = f.in[i];
+    }
     const int32_t left = __shfl_up_sync(kFull, v, 1);
     bool same_left = false;
-    if (valid && i % W > 0) same_left = lane == 0 ? lab[i - 1] == v : left == v;
+    if (valid && i % f.W > 0) same_left = lane == 0 ? f.in[i - 1] == v : left == v;
     const unsigned starts = __ballot_sync(kFull, !same_left) & (kFull >> (31 - lane));
-    if (valid) parent[i] = starts ? i - lane + (31 - __clz(starts)) : i - lane - 1;
+    if (valid) parent[g] = starts ? g - lane + (31 - __clz(starts)) : g - lane - 1;
 }
 
 // Vertical links; a pixel whose left neighbour is in its run and has the same
 // link above needs none of its own.
-__global__ void k_ccl_merge(const int32_t *lab, int N, int W, int *parent, int *err) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N || i < W) return;
-    const int32_t v = lab[i];
-    if (lab[i - W] != v) return;
-    if (i % W > 0 && lab[i - 1] == v && lab[i - W - 1] == v) return;
-    ccl_union(parent, i, i - W, err);
+__global__ void k_ccl_merge(CclFrames fr, int G, int *parent, int *err) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const CclFrame f = ccl_frame_of(fr, g);
+    const int i = g - f.base, W = f.W;
+    if (i < W) return;
+    const int32_t v = f.in[i];
+    if (f.in[i - W] != v) return;
+    if (i % W > 0 && f.in[i - 1] == v && f.in[i - W - 1] == v) return;
+    ccl_union(parent, g, g - W, err);
 }
 
 __global__ void k_ccl_compress(int N, int *parent, int *err) {
@@ -1903,13 +1935,15 @@ __global__ void k_ccl_count(int N, const int *parent, int *count) {
 }
 
 // Per root: itself when kept, else the root of its first pixel's left (or,
-// in column 0, upper) neighbour.
-__global__ void k_ccl_decide(int N, int W, int min_size, const int *parent, const int *count, int *target) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N || parent[i] != i) return;
-    int t = i;
-    if (i != 0 && count[i] <= min_size) t = parent[i % W > 0 ? i - 1 : i - W];
-    target[i] = t;
+// in column 0, upper) neighbour; a frame's first pixel is always kept.
+__global__ void k_ccl_decide(CclFrames fr, int G, const int *parent, const int *count, int *target) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G || parent[g] != g) return;
+    const CclFrame f = ccl_frame_of(fr, g);
+    const int i = g - f.base;
+    int t = g;
+    if (i != 0 && count[g] <= f.min_size) t = parent[i % f.W > 0 ? g - 1 : g - f.W];
+    target[g] = t;
 }
 
 // Per root: follow the joins to the kept segment (chains point to smaller
@@ -1990,12 +2024,15 @@ __global__ void __launch_bounds__(1024) k_ccl_scan_totals(int nb, int *totals) {
     }
 }
 
-__global__ void k_ccl_relabel(int N, const int *parent, const int *target, const int *rank, const int *totals,
-                              int32_t *out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int f = target[parent[i]];
-    out[i] = rank[f] + totals[f / kScanBlock];
+// New label: the kept root's rank among all kept roots, less the number of
+// kept roots of the earlier frames (the rank at the frame's base).
+__global__ void k_ccl_relabel(CclFrames fr, int G, const int *parent, const int *target, const int *rank,
+                              const int *totals) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const CclFrame f = ccl_frame_of(fr, g);
+    const int r = target[parent[g]];
+    f.out[g - f.base] = rank[r] + totals[r / kScanBlock] - (rank[f.base] + totals[f.base / kScanBlock]);
 }
 
 // ---------------------------------------------------------------------------
@@ -2160,23 +2197,33 @@ size_t ccl_scratch_ints(long long N) {
     return (size_t)N * 4 + (size_t)((N + kScanBlock - 1) / kScanBlock) + 64;
 }
 
+cudaError_t launch_connectivity_components(const CclFrame *d_table, const CclFrame &one, int n, int G, int *scratch,
+                                           int *err, cudaStream_t s) {
+    CclFrames fr;
+    fr.table = d_table;
+    fr.one = one;
+    fr.n = n;
+    const int nb = (G + kScanBlock - 1) / kScanBlock, g = (G + 255) / 256;
+    int *parent = scratch, *count = scratch + G, *target = scratch + 2 * (size_t)G, *rank = scratch + 3 * (size_t)G;
+    int *totals = scratch + 4 * (size_t)G;
+    k_ccl_init<<<g, 256, 0, s>>>(fr, G, parent);
+    k_ccl_merge<<<g, 256, 0, s>>>(fr, G, parent, err);
+    k_ccl_compress<<<g, 256, 0, s>>>(G, parent, err);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)G, s);
+    if (e != cudaSuccess) return e;
+    k_ccl_count<<<g, 256, 0, s>>>(G, parent, count);
+    k_ccl_decide<<<g, 256, 0, s>>>(fr, G, parent, count, target);
+    k_ccl_resolve<<<g, 256, 0, s>>>(G, parent, target, err);
+    k_ccl_scan_block<<<nb, kScanThreads, 0, s>>>(G, parent, target, rank, totals);
+    k_ccl_scan_totals<<<1, 1024, 0, s>>>(nb, totals);
+    k_ccl_relabel<<<g, 256, 0, s>>>(fr, G, parent, target, rank, totals);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_connectivity_components(const int32_t *in, int32_t *out, int W, int H, int min_size,
                                            int *scratch, int *err, cudaStream_t s) {
-    const int N = W * H, nb = (N + kScanBlock - 1) / kScanBlock, g = (N + 255) / 256;
-    int *parent = scratch, *count = scratch + N, *target = scratch + 2 * (size_t)N, *rank = scratch + 3 * (size_t)N;
-    int *totals = scratch + 4 * (size_t)N;
-    k_ccl_init<<<g, 256, 0, s>>>(in, N, W, parent);
-    k_ccl_merge<<<g, 256, 0, s>>>(in, N, W, parent, err);
-    k_ccl_compress<<<g, 256, 0, s>>>(N, parent, err);
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)N, s);
-    if (e != cudaSuccess) return e;
-    k_ccl_count<<<g, 256, 0, s>>>(N, parent, count);
-    k_ccl_decide<<<g, 256, 0, s>>>(N, W, min_size, parent, count, target);
-    k_ccl_resolve<<<g, 256, 0, s>>>(N, parent, target, err);
-    k_ccl_scan_block<<<nb, kScanThreads, 0, s>>>(N, parent, target, rank, totals);
-    k_ccl_scan_totals<<<1, 1024, 0, s>>>(nb, totals);
-    k_ccl_relabel<<<g, 256, 0, s>>>(N, parent, target, rank, totals, out);
-    return cudaGetLastError();
+    CclFrame one{in, out, W, min_size, 0};
+    return launch_connectivity_components(nullptr, one, 1, W * H, scratch, err, s);
 }
 
 cudaError_t launch_connectivity_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w, int pass,
