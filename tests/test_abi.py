@@ -82,3 +82,23 @@ def test_library_has_no_torch_dependency(lib):
     import subprocess
     out = subprocess.run(["nm", "-D", "--undefined-only", build.SLIC_LIB], capture_output=True, text=True).stdout
     assert "c10" not in out and "torch" not in out
+
+
+def test_params_struct_matches_the_header():
+    """The ctypes mirror of slic_params has the header's fields, in order and
+    with matching C types (a mismatch would shift every later field)."""
+    text = open(os.path.join(ROOT, "include", "slic.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} slic_params;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, names = decl.split(None, 1)
+        fields += [(n.strip(), ctype) for n in names.split(",")]
+    want = {"int": ctypes.c_int, "float": ctypes.c_float}
+    got = [(n, t) for n, t in _binding.slic_params._fields_]
+    assert [n for n, _ in fields] == [n for n, _ in got]
+    for (n, ctype), (_, t) in zip(fields, got):
+        assert want[ctype] is t, n
