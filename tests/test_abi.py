@@ -102,3 +102,24 @@ def test_params_struct_matches_the_header():
     assert [n for n, _ in fields] == [n for n, _ in got]
     for (n, ctype), (_, t) in zip(fields, got):
         assert want[ctype] is t, n
+
+
+@pytest.mark.parametrize("second,msg", [
+    (dict(iterations=4), "same iterations"),
+    (dict(enforce_connectivity=2), "same iterations and connectivity"),
+    (dict(convergence=-1.0), "convergence"),
+    (dict(perturb_seeds=5), "perturb_seeds"),
+    (dict(enforce_connectivity=7), "enforce_connectivity"),
+    (dict(width=0), "width"),
+])
+def test_invalid_batches_rejected_without_cuda(lib, second, msg):
+    """Per-frame options may differ within a batch, iterations and the
+    connectivity mode may not; every frame is validated before any CUDA call."""
+    base = dict(width=64, height=48, K=0, S=16, m=10.0, iterations=3, color_space=0,
+                enforce_connectivity=1, in_channels=3)
+    other = dict(base)
+    other.update(second)
+    with pytest.raises(pkg.SlicError) as ei:
+        pkg.slic_batch_create([_binding.slic_params(**base), _binding.slic_params(**other)])
+    assert ei.value.status == _binding.SLIC_ERR_INVALID
+    assert msg in str(ei.value)
