@@ -19,7 +19,8 @@
  *  - Images are 8-bit R,G,B (in_channels = 3) or R,G,B,A (in_channels = 4,
  *    alpha ignored), row-major, rows of width*in_channels bytes.
  *  - Labels are int32 [height][width]; label k = r*ns_c + c names the grid
- *    cell (column c, row r) the centre started in.
+ *    cell (column c, row r) the centre started in (except with
+ *    enforce_connectivity = 2, which renumbers the segments 0, 1, ...).
  *  - Centres are float [K_eff][6] = (f0, f1, f2, x, y, count) where
  *    (f0,f1,f2) = (L*, a*, b*) for SLIC_CIELAB, K_eff = ns_c*ns_r.
  *  - Features are float [3][height][width] (planar).
