@@ -24,6 +24,9 @@
  *  - Centres are float [K_eff][6] = (f0, f1, f2, x, y, count) where
  *    (f0,f1,f2) = (L*, a*, b*) for SLIC_CIELAB, K_eff = ns_c*ns_r.
  *  - Features are float [3][height][width] (planar).
+ *  - The library keeps per-device state (the sRGB table, kernel attributes,
+ *    fault-injection words) from its first use on a device: do not use it
+ *    after cudaDeviceReset on that device.
  */
 #ifndef SLIC_H
 #define SLIC_H
@@ -253,6 +256,11 @@ slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stre
 slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm,
                             int *stages, int *rows);
 
+/* Grid of frame `frame` (Sec. 2): its S and ns_c x ns_r cells, K_eff =
+   ns_c*ns_r centres (any pointer may be NULL); SLIC_ERR_INVALID for a frame
+   index outside [0, n_frames). */
+slic_status slic_batch_grid(slic_batch b, int frame, int *S, int *ns_c, int *ns_r);
+
 /* Wait for the device, then report whether a bounded wait inside the
    batch's kernels gave up since the last call (SLIC_ERR_TIMEOUT; the
    affected tiles' results are then incomplete). Clears the flag. */
@@ -288,18 +296,58 @@ const char *slic_batch_last_error(slic_batch b);
    takes the parameters directly (no handle) and the same image, label and
    centre buffers, calls no cudaMalloc/cudaFree, and keeps its scratch in a
    32 MiB array in device memory that each GPU loading this library holds
-   until the process exits. Images whose scratch (12*height*P + 48*K_eff +
-   4*width*height bytes, P = width rounded up to 4, each part rounded up to
-   256) exceeds 32 MiB are rejected with SLIC_ERR_INVALID; that admits e.g.
-   1280x720 or 1024x1024 at S >= 4. The first call on each device does a
-   one-time set-up (sRGB table upload, kernel attributes, device address of
-   the array) and should come before any stream capture. All calls share the
-   one array: calls whose work overlaps on the GPU (different streams, or
-   several host threads) race and corrupt each other's results; serialise
-   them. The sums left by the previous call are cleared by each call.
-   Errors are reported through slic_last_error(NULL). */
+   until the process exits. Images whose scratch exceeds 32 MiB are rejected
+   with SLIC_ERR_INVALID; the scratch is 256 + 12*height*P + 48*K_eff +
+   4*width*height bytes (P = width rounded up to 4), plus
+   16*width*height + 4*ceil(width*height/2048) + 256 with
+   enforce_connectivity = 2, each part rounded up to 256 (plus a 256-byte
+   state record). That
+   admits e.g. 1280x720 or 1024x1024 at S >= 4 with connectivity mode 0 or
+   1, and 1280x720 in mode 2; 1024x1024 in mode 2 and 1920x1080 in any mode
+   do not fit. The first call on each device does a one-time set-up (sRGB
+   table upload, kernel attributes) and should come before any stream
+   capture. All calls share the one array: calls whose work overlaps on the
+   GPU (different streams, or several host threads) race and corrupt each
+   other's results; serialise them. The sums left by the previous call are
+   cleared by each call. Errors are reported through slic_last_error(NULL);
+   a bounded loop of component connectivity that gives up is reported by
+   slic_noalloc_status_check. */
 slic_status slic_segment_noalloc(const slic_params *params, const uint8_t *d_image, int32_t *d_labels,
                                  float *d_centres, void *stream);
+
+/* Wait for the current device, then report whether a bounded loop of the
+   allocation-free path's component connectivity (enforce_connectivity = 2)
+   gave up since the last check on this device (SLIC_ERR_TIMEOUT: those
+   labels are incomplete). Clears the flag. */
+slic_status slic_noalloc_status_check(void);
+
+/* ---- Fault injection, for tests of failure detection ----------------------
+   (The paper has none.) Process-wide switches that make the library's own
+   failure paths run without faulting the GPU:
+     SLIC_FAULT_ALLOC         the value-th device allocation the library
+                              makes from now on fails (that call frees what
+                              it allocated before and returns
+                              SLIC_ERR_NOMEM); 0 clears.
+     SLIC_FAULT_WALK_LIMIT    component connectivity's bounded walks give up
+                              after `value` steps instead of 2^22 (0 restores
+                              it): deeper trees then report SLIC_ERR_TIMEOUT
+                              through slic_status_check, slic_batch_status or
+                              slic_noalloc_status_check.
+     SLIC_FAULT_ABORT_COPIES  value != 0: the pipelined assignment kernel's
+                              producers issue no further tile copy (checked
+                              before each copy, so none is in flight when a
+                              CTA gives up); the consumers' bounded waits run
+                              out after about a second per launch and
+                              slic_batch_status reports SLIC_ERR_TIMEOUT.
+                              0 clears.
+   The device words apply to the current device. SLIC_ERR_INVALID for an
+   unknown kind or a negative value. */
+typedef enum {
+    SLIC_FAULT_ALLOC = 1,
+    SLIC_FAULT_WALK_LIMIT = 2,
+    SLIC_FAULT_ABORT_COPIES = 3
+} slic_fault;
+slic_status slic_fault_inject(int kind, long long value);
 
 /* ---- Learned warm start ---------------------------------------------------
    A 4-layer 3x3 convolutional network (14 -> 32 -> 32 -> 32 -> 9 channels,
@@ -352,6 +400,34 @@ slic_status slic_net_gradients(slic_net n, int batch, const uint8_t *d_images, c
 /* slic_net_gradients, then one Adam step with learning rate lr. */
 slic_status slic_net_train_step(slic_net n, int batch, const uint8_t *d_images, const uint8_t *d_targets, float lr,
                                 float *d_stats, void *stream);
+
+/* Training targets from labels: d_labels int32 [batch][H][W] (labels of
+   the network's geometry, e.g. full-iteration SLIC labels before
+   connectivity) -> d_slots uint8 [batch][H][W], the slot (dy+1)*3 + (dx+1)
+   of each label's cell relative to the pixel's own cell. A label outside the
+   pixel's 3x3 cell window gets slot 255 and adds 1 to *d_bad (a device int
+   the caller clears; may be NULL). Enqueued on `stream`. */
+slic_status slic_net_slots(slic_net n, int batch, const int32_t *d_labels, uint8_t *d_slots, int *d_bad,
+                           void *stream);
+
+/* Learned warm start of a segmentation (the paper has none; it replaces the
+   first k-means iterations). Once armed with a network (NULL disarms), each
+   slic_segment / slic_batch_segment call runs, after the colour conversion
+   and the initialisation: the network's labels for the frame, then one
+   update from them (Sec. 3 "Updating the cluster center": each centre
+   becomes the mean of the pixels the network gave its cell; a cell given no
+   pixel keeps its initial centre, from the grid or from
+   slic_set_init_centres / d_init), then the usual passes: assignment,
+   `iterations` x {update, assignment}, connectivity. The network must have
+   been created for the frames' width, height, S and m (else
+   SLIC_ERR_INVALID); it is read by every later call and must outlive the
+   arming. Its forward runs in chunks of its max_batch images; frames may
+   have 3 or 4 channels (all frames of a batch the same). The batch form
+   waits for the device and allocates the network's label maps (4 bytes per
+   pixel) the first time it is armed; the per-frame results equal those of
+   the armed single-frame handle bit for bit. */
+slic_status slic_set_warmstart(slic_handle h, slic_net net);
+slic_status slic_batch_set_warmstart(slic_batch b, slic_net net);
 
 /* Wait for the device, then report whether a bounded wait inside the
    network's tensor-core kernels gave up since the last call

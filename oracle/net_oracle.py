@@ -16,8 +16,12 @@ weights and the activations stored between layers are rounded to bfloat16
 (round to nearest even); every sum is exact (FP64 here, FP32 accumulation
 on the device). The loss is the mean softmax cross-entropy over pixels, with
 off-grid slots excluded from the softmax. Gradients (``backward``) are the
-plain FP64 chain rule of that loss (no rounding), pinned by central finite
-differences in the tests.
+plain FP64 chain rule of that loss, pinned by central finite differences in
+the tests. With ``bf16_grad=True`` the loss gradient of every layer's
+pre-activation (dL/dz: the softmax gradient, and each propagated gradient
+after the ReLU mask) is rounded to bfloat16 where the device stores it
+between its backward kernels; the weight and bias gradients are exact sums
+of those stored values.
 """
 from __future__ import annotations
 
@@ -149,18 +153,24 @@ def loss(logits: np.ndarray, target: np.ndarray, valid: np.ndarray) -> float:
     return float(-np.mean(np.take_along_axis(lp, target[..., None], axis=-1)))
 
 
-def backward(x0: np.ndarray, params, target: np.ndarray, valid: np.ndarray, bf16: bool = True):
-    """Loss and its gradients [(dW, db), ...] by the chain rule in FP64."""
+def backward(x0: np.ndarray, params, target: np.ndarray, valid: np.ndarray, bf16: bool = True,
+             bf16_grad: bool = False, return_dz: bool = False):
+    """Loss and its gradients [(dW, db), ...] by the chain rule in FP64
+    (dL/dz rounded to bfloat16 at each layer when ``bf16_grad``); with
+    ``return_dz`` also each layer's dL/dz [H,W,Cout] and its input [H,W,Cin]."""
+    stored = bf16_round if bf16_grad else (lambda v: v)
     logits, cache = forward(x0, params, bf16)
     H, W, _ = logits.shape
     lp = masked_log_softmax(logits, valid)
     p = np.where(valid, np.exp(lp), 0.0)
     onehot = np.zeros_like(p)
     np.put_along_axis(onehot, target[..., None], 1.0, axis=-1)
-    dz = (p - onehot) / (H * W)
+    dz = stored((p - onehot) / (H * W))
     grads = [None] * len(params)
+    dzs = [None] * len(params)
     for li in range(len(params) - 1, -1, -1):
         a_in, wq, z = cache[li]
+        dzs[li] = (dz, a_in)
         # dW[dy,dx,i,o] = sum_{y,x} a_in[y+dy-1, x+dx-1, i] dz[y,x,o]
         ap = np.pad(a_in, ((1, 1), (1, 1), (0, 0)))
         dw = np.zeros(wq.shape)
@@ -176,5 +186,7 @@ def backward(x0: np.ndarray, params, target: np.ndarray, valid: np.ndarray, bf16
                 for dx in range(3):
                     da += dzp[2 - dy:2 - dy + H, 2 - dx:2 - dx + W, :] @ wq[dy, dx].T
             z_prev = cache[li - 1][2]
-            dz = da * (z_prev > 0)
+            dz = stored(da * (z_prev > 0))
+    if return_dz:
+        return loss(logits, target, valid), grads, dzs
     return loss(logits, target, valid), grads

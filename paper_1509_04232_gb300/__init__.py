@@ -9,9 +9,13 @@ raise.
 """
 from __future__ import annotations
 
-from ._binding import (SLIC_CIELAB, SLIC_RGB, SLIC_XYZ, SlicError, library_path, slic_assign,  # noqa: F401
+from ._binding import (SLIC_CIELAB, SLIC_ERR_CUDA, SLIC_ERR_INVALID, SLIC_ERR_NOMEM,  # noqa: F401
+                       SLIC_ERR_STATE, SLIC_ERR_TIMEOUT, SLIC_FAULT_ABORT_COPIES, SLIC_FAULT_ALLOC,
+                       SLIC_FAULT_WALK_LIMIT, SLIC_OK, SLIC_RGB, SLIC_XYZ, SlicError, library_path, slic_assign,
+                       slic_fault_inject, slic_noalloc_status_check,
                        slic_batch_autotune, slic_batch_create, slic_batch_destroy, slic_batch_info,
-                       slic_batch_iterations_run, slic_batch_last_error, slic_batch_profile_enable,
+                       slic_batch_grid, slic_batch_iterations_run, slic_batch_last_error,
+                       slic_batch_profile_enable, slic_batch_set_warmstart, slic_set_warmstart,
                        slic_batch_profile_read,
                        slic_batch_profile_times, slic_batch_segment, slic_batch_segment_host,
                        slic_batch_set_buffers, slic_batch_set_tuning, slic_batch_status,
@@ -75,6 +79,13 @@ class Segmenter:
             slic_set_init_centres(self.handle, init_centres.data_ptr())
         slic_segment(self.handle, image.data_ptr(), labels.data_ptr(), centres.data_ptr(), _stream_handle(stream))
         return labels, centres
+
+    def set_warmstart(self, net):
+        """Arm the learned warm start with a network (an object with a
+        ``handle`` or a raw slic_net handle), or disarm it with None. The
+        network must outlive the arming."""
+        self._net = net
+        slic_set_warmstart(self.handle, getattr(net, "handle", net) if net is not None else None)
 
     def convert(self, image, stream=None):
         import torch
@@ -147,9 +158,9 @@ class BatchSegmenter:
         self.handle = slic_batch_create(self.params)
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.labels, self.centres, self.K_eff = [], [], []
-        for p in self.params:
-            S = p.S if p.S > 0 else max(1, int(round((p.width * p.height / p.K) ** 0.5)))
-            k = (-(-p.width // S)) * (-(-p.height // S))
+        for f, p in enumerate(self.params):
+            _, ns_c, ns_r = slic_batch_grid(self.handle, f)
+            k = ns_c * ns_r
             self.K_eff.append(k)
             self.labels.append(torch.empty((p.height, p.width), dtype=torch.int32, device=dev))
             self.centres.append(torch.empty((k, 6), dtype=torch.float32, device=dev))
@@ -170,6 +181,13 @@ class BatchSegmenter:
     def segment(self, stream=None):
         slic_batch_segment(self.handle, _stream_handle(stream))
         return self.labels, self.centres
+
+    def set_warmstart(self, net):
+        """Arm the learned warm start with a network (an object with a
+        ``handle``, e.g. warmstart.WarmStartNet, or a raw slic_net handle),
+        or disarm it with None. The network must outlive the arming."""
+        self._net = net
+        slic_batch_set_warmstart(self.handle, getattr(net, "handle", net) if net is not None else None)
 
     def segment_host(self, host_images, host_labels=None, host_centres=None, stream=None):
         """End to end with host tensors (page-locked CPU tensors, one per

@@ -16,6 +16,7 @@ from . import build as _build
 
 SLIC_OK, SLIC_ERR_INVALID, SLIC_ERR_NOMEM, SLIC_ERR_CUDA, SLIC_ERR_TIMEOUT, SLIC_ERR_STATE = 0, -1, -2, -3, -4, -5
 SLIC_CIELAB, SLIC_RGB, SLIC_XYZ = 0, 1, 2
+SLIC_FAULT_ALLOC, SLIC_FAULT_WALK_LIMIT, SLIC_FAULT_ABORT_COPIES = 1, 2, 3
 
 _STATUS_NAMES = {0: "SLIC_OK", -1: "SLIC_ERR_INVALID", -2: "SLIC_ERR_NOMEM", -3: "SLIC_ERR_CUDA",
                  -4: "SLIC_ERR_TIMEOUT", -5: "SLIC_ERR_STATE"}
@@ -80,6 +81,12 @@ _SIGNATURES = {
     "slic_net_gradients": [_P, _I, _P, _P, _P, _P],
     "slic_net_train_step": [_P, _I, _P, _P, ctypes.c_float, _P, _P],
     "slic_net_status": [_P],
+    "slic_net_slots": [_P, _I, _P, _P, _P, _P],
+    "slic_set_warmstart": [_P, _P],
+    "slic_batch_set_warmstart": [_P, _P],
+    "slic_batch_grid": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "slic_noalloc_status_check": [],
+    "slic_fault_inject": [_I, ctypes.c_longlong],
 }
 
 
@@ -143,6 +150,11 @@ def slic_set_init_centres(h: int, d_init: int | None) -> None:
     _check(lib().slic_set_init_centres(h, d_init or None), h)
 
 
+def slic_set_warmstart(h: int, net: int | None) -> None:
+    """Arm (or, with None, disarm) the learned warm start of the handle."""
+    _check(lib().slic_set_warmstart(h, net or None), h)
+
+
 def slic_convert(h: int, d_image: int, d_features: int, stream: int = 0) -> None:
     _check(lib().slic_convert(h, d_image, d_features, stream or None), h)
 
@@ -184,6 +196,17 @@ def slic_segment_noalloc(params: slic_params, d_image: int, d_labels: int, d_cen
     """Whole segmentation without any device allocation (scratch in a static
     32 MiB device array shared by all calls; see include/slic.h)."""
     _check(lib().slic_segment_noalloc(ctypes.byref(params), d_image, d_labels, d_centres, stream or None), None)
+
+
+def slic_noalloc_status_check() -> None:
+    """Raise SlicError(SLIC_ERR_TIMEOUT) if a bounded loop of the
+    allocation-free path gave up since the last check (waits for the device)."""
+    _check(lib().slic_noalloc_status_check(), None)
+
+
+def slic_fault_inject(kind: int, value: int) -> None:
+    """Fault injection for tests of failure detection (include/slic.h)."""
+    _check(lib().slic_fault_inject(int(kind), int(value)), None)
 
 
 # --- batches ---------------------------------------------------------------
@@ -296,6 +319,18 @@ def slic_batch_profile_times(b: int, max_n: int = 4096):
     return list(buf[:n.value])
 
 
+def slic_batch_grid(b: int, frame: int):
+    """-> (S, ns_c, ns_r) of one frame of the batch."""
+    s, c, r = _I(), _I(), _I()
+    _bcheck(lib().slic_batch_grid(b, int(frame), ctypes.byref(s), ctypes.byref(c), ctypes.byref(r)), b)
+    return s.value, c.value, r.value
+
+
+def slic_batch_set_warmstart(b: int, net: int | None) -> None:
+    """Arm (or, with None, disarm) the learned warm start of every frame."""
+    _bcheck(lib().slic_batch_set_warmstart(b, net or None), b)
+
+
 def slic_batch_destroy(b: int) -> None:
     _bcheck(lib().slic_batch_destroy(b), None)
 
@@ -358,3 +393,7 @@ def slic_net_status(n: int) -> None:
 def slic_net_train_step(n: int, batch: int, d_images: int, d_targets: int, lr: float, d_stats: int | None,
                         stream: int = 0) -> None:
     _ncheck(lib().slic_net_train_step(n, batch, d_images, d_targets, float(lr), d_stats or None, stream or None), n)
+
+
+def slic_net_slots(n: int, batch: int, d_labels: int, d_slots: int, d_bad: int | None, stream: int = 0) -> None:
+    _ncheck(lib().slic_net_slots(n, batch, d_labels, d_slots, d_bad or None, stream or None), n)

@@ -8,6 +8,7 @@
 #include "slic.h"
 #include "slic_internal.cuh"
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -33,6 +34,7 @@ struct slic_ctx {
     size_t smem_max = 0;
     ConvConsts conv{};
     const float *init_centres = nullptr;
+    slic_net net = nullptr;       // learned warm start (slic_set_warmstart)
     long long launches = 0;
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
@@ -117,7 +119,23 @@ cudaError_t ensure_lut(int dev) {
 
 }  // namespace
 
+namespace {
+// Fault injection (SLIC_FAULT_ALLOC): the device allocation that takes this
+// countdown from 1 to 0 fails; 0 means none.
+std::atomic<long long> g_fail_allocs{0};
+}  // namespace
+
 namespace slicgb {
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    long long n = g_fail_allocs.load();
+    while (n > 0 && !g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 ConvConsts conv_consts(int color_space) { return make_conv(color_space); }
 void srgb_table(float lut[256]) { make_lut(lut); }
 cudaError_t device_setup(int dev, size_t smem) {
@@ -243,13 +261,13 @@ slic_status slic_create(const slic_params *params, slic_handle *out) {
         return fail(nullptr, SLIC_ERR_CUDA, std::string("CUDA initialisation: ") + cudaGetErrorString(e));
     }
     const size_t npix = (size_t)p.width * p.height;
-    if (cudaMalloc(&h->feat, sizeof(float) * 3 * (size_t)p.height * h->P) != cudaSuccess ||
-        cudaMalloc(&h->acc, sizeof(long long) * 6 * (size_t)h->K) != cudaSuccess ||
-        cudaMalloc(&h->lbl_tmp, sizeof(int32_t) * npix) != cudaSuccess ||
-        cudaMalloc(&h->cstate, sizeof(ConvState)) != cudaSuccess ||
-        cudaMemset(h->cstate, 0, sizeof(ConvState)) != cudaSuccess || cudaMalloc(&h->ccl_err, sizeof(int)) != cudaSuccess ||
+    if (dev_alloc(&h->feat, sizeof(float) * 3 * (size_t)p.height * h->P) != cudaSuccess ||
+        dev_alloc(&h->acc, sizeof(long long) * 6 * (size_t)h->K) != cudaSuccess ||
+        dev_alloc(&h->lbl_tmp, sizeof(int32_t) * npix) != cudaSuccess ||
+        dev_alloc(&h->cstate, sizeof(ConvState)) != cudaSuccess ||
+        cudaMemset(h->cstate, 0, sizeof(ConvState)) != cudaSuccess || dev_alloc(&h->ccl_err, sizeof(int)) != cudaSuccess ||
         cudaMemset(h->ccl_err, 0, sizeof(int)) != cudaSuccess ||
-        (p.enforce_connectivity == 2 && cudaMalloc(&h->ccl, sizeof(int) * ccl_scratch_ints((long long)npix)) != cudaSuccess)) {
+        (p.enforce_connectivity == 2 && dev_alloc(&h->ccl, sizeof(int) * ccl_scratch_ints((long long)npix)) != cudaSuccess)) {
         cudaGetLastError();
         cudaFree(h->feat);
         cudaFree(h->acc);
@@ -320,7 +338,34 @@ slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_label
     a.cstate = h->cstate;
     a.conv_eps = h->p.convergence;
     cudaError_t e;
-    if (h->init_centres) {
+    const bool warm = h->net != nullptr;
+    if (warm) {
+        // Learned warm start: features first, the grid (or armed) initial
+        // centres, then the member means of the network's labels (written to
+        // lbl_tmp, free until connectivity) by one plain update.
+        e = launch_convert(h->conv, d_image, h->p.width, h->p.height, h->p.in_channels, h->feat, h->P, s);
+        if (e == cudaSuccess) {
+            if (h->init_centres)
+                e = h->init_centres == d_centres
+                        ? cudaSuccess
+                        : cudaMemcpyAsync(d_centres, h->init_centres, sizeof(float) * 6 * (size_t)h->K,
+                                          cudaMemcpyDeviceToDevice, s);
+            else
+                e = launch_init_from_feat(h->feat, h->p.width, h->p.height, h->P, h->S, h->ns_c, h->ns_r,
+                                          h->p.perturb_seeds, d_centres, s);
+        }
+        h->init_centres = nullptr;
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->cstate, 0, sizeof(ConvState), s);
+        if (e == cudaSuccess) e = launch_zero_acc(h->acc, h->K, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "warm-start set-up");
+        if (net_forward_labels(h->net, 1, d_image, nullptr, h->p.in_channels, h->lbl_tmp, s) != cudaSuccess)
+            return fail(h, SLIC_ERR_CUDA, std::string("network forward: ") + slic_net_last_error(h->net));
+        e = launch_accumulate_labels(h->feat, h->p.width, h->p.height, h->P, h->lbl_tmp, h->K, h->acc, h->fix_scale, s);
+        if (e == cudaSuccess)
+            e = launch_update(h->acc, d_centres, d_centres, h->K, 1.0f / h->fix_scale, nullptr, 0.0f, 0, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "warm-start update");
+        h->launches += 4;
+    } else if (h->init_centres) {
         if (h->init_centres != d_centres) {
             e = cudaMemcpyAsync(d_centres, h->init_centres, sizeof(float) * 6 * (size_t)h->K,
                                 cudaMemcpyDeviceToDevice, s);
@@ -342,7 +387,7 @@ slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_label
             if (e != cudaSuccess) return cuda_fail(h, e, "update kernel launch");
             ++h->launches;
         }
-        slic_status st = assign_launch(h, a, pass == 0, pass == n, pass != n, s);
+        slic_status st = assign_launch(h, a, pass == 0 && !warm, pass == n, pass != n, s);
         if (st != SLIC_OK) return st;
     }
     if (h->p.enforce_connectivity == 1) {
@@ -356,6 +401,19 @@ slic_status slic_segment(slic_handle h, const uint8_t *d_image, int32_t *d_label
         if (e != cudaSuccess) return cuda_fail(h, e, "component connectivity launch");
         h->launches += 9;
     }
+    return SLIC_OK;
+}
+
+slic_status slic_set_warmstart(slic_handle h, slic_net net) {
+    if (!h) return fail(nullptr, SLIC_ERR_INVALID, "NULL handle");
+    if (net) {
+        int W = 0, H = 0, S = 0, max_batch = 0;
+        float m = 0.0f;
+        net_geometry(net, &W, &H, &S, &m, &max_batch);
+        if (W != h->p.width || H != h->p.height || S != h->S || m != h->p.m)
+            return fail(h, SLIC_ERR_INVALID, "the network was made for another width, height, S or m");
+    }
+    h->net = net;
     return SLIC_OK;
 }
 
@@ -464,6 +522,31 @@ slic_status slic_profile_read(slic_handle h, double *assign_ms, long long *assig
     return SLIC_OK;
 }
 
+slic_status slic_fault_inject(int kind, long long value) {
+    if (value < 0) return fail(nullptr, SLIC_ERR_INVALID, "fault injection value must be >= 0");
+    static std::mutex mu;
+    static unsigned steps = 0;
+    static int abort_copies = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    switch (kind) {
+    case SLIC_FAULT_ALLOC:
+        g_fail_allocs.store(value);
+        return SLIC_OK;
+    case SLIC_FAULT_WALK_LIMIT:
+        if (value > (long long)ccl_default_steps()) return fail(nullptr, SLIC_ERR_INVALID, "walk limit above the default");
+        steps = (unsigned)value;
+        break;
+    case SLIC_FAULT_ABORT_COPIES:
+        abort_copies = value != 0;
+        break;
+    default:
+        return fail(nullptr, SLIC_ERR_INVALID, "unknown fault kind");
+    }
+    const cudaError_t e = set_fault_words(steps ? steps : ccl_default_steps(), abort_copies);
+    if (e != cudaSuccess) return fail(nullptr, SLIC_ERR_CUDA, std::string("fault words: ") + cudaGetErrorString(e));
+    return SLIC_OK;
+}
+
 const char *slic_last_error(slic_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 }  // extern "C"
@@ -483,31 +566,26 @@ namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB per device
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mu;
-unsigned char *g_static_addr[kMaxDevices] = {};
+// The first 256 bytes are a control block at a fixed place: the timeout flag
+// of component connectivity (bit 1), read and cleared by
+// slic_noalloc_status_check. Device memory of a module starts zeroed.
+constexpr size_t kStaticCtrlBytes = 256;
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Once per device, with that device current: the sRGB table, the kernels'
-// shared-memory limit and the device address of the static scratch (the
-// symbol itself is only a host-side stand-in).
+// With the device current: the sRGB table and the kernels' shared-memory
+// limit (once per device), and the device address of the static scratch,
+// taken afresh on every call (the symbol itself is only a host-side stand-in).
 slic_status static_setup(int dev, size_t smem, unsigned char **addr) {
-    if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, SLIC_ERR_INVALID, "device ordinal out of range");
     cudaError_t e = ensure_lut(dev);
     if (e == cudaSuccess) e = ensure_smem(dev, smem);
     if (e != cudaSuccess) return fail(nullptr, SLIC_ERR_CUDA, std::string("set-up: ") + cudaGetErrorString(e));
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(nullptr, SLIC_ERR_CUDA,
-                        std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
-        g_static_addr[dev] = static_cast<unsigned char *>(p);
-    }
-    *addr = g_static_addr[dev];
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(nullptr, SLIC_ERR_CUDA,
+                    std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
+    *addr = static_cast<unsigned char *>(p);
     return SLIC_OK;
 }
 
@@ -539,27 +617,28 @@ extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uin
     const int ns_c = (p.width + S - 1) / S, ns_r = (p.height + S - 1) / S;
     const long long K = (long long)ns_c * ns_r;
     const int P = (p.width + 3) & ~3;
-    // Scratch layout: features [3][H][P] f32 | sums [K][6] i64 | labels [H][W] i32
-    // | stopping-test state.
+    // Scratch layout: control block | features [3][H][P] f32 | sums [K][6] i64
+    // | labels [H][W] i32 | stopping-test state | component scratch (mode 2).
     const size_t feat_b = align256(sizeof(float) * 3 * (size_t)p.height * P);
     const size_t acc_b = align256(sizeof(long long) * 6 * (size_t)K);
     const size_t lbl_b = align256(sizeof(int32_t) * (size_t)p.width * p.height);
-    const size_t cs_b = align256(sizeof(ConvState) + sizeof(int));
+    const size_t cs_b = align256(sizeof(ConvState));
     const size_t ccl_b =
         p.enforce_connectivity == 2 ? align256(sizeof(int) * ccl_scratch_ints((long long)p.width * p.height)) : 0;
-    if (feat_b + acc_b + lbl_b + cs_b + ccl_b > kStaticScratchBytes)
+    const size_t need = kStaticCtrlBytes + feat_b + acc_b + lbl_b + cs_b + ccl_b;
+    if (need > kStaticScratchBytes)
         return fail(nullptr, SLIC_ERR_INVALID,
-                    "image too large for the static scratch: needs " +
-                        std::to_string(feat_b + acc_b + lbl_b + cs_b + ccl_b) +
+                    "image too large for the static scratch: needs " + std::to_string(need) +
                         " bytes, the limit is " + std::to_string(kStaticScratchBytes) + " (32 MiB)");
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(nullptr, SLIC_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     const int win = assign_max_window(S, ns_c, ns_r);
-    unsigned char *base = nullptr;
-    slic_status st = static_setup(dev, assign_smem_bytes(win, true), &base);
+    unsigned char *ctrl = nullptr;
+    slic_status st = static_setup(dev, assign_smem_bytes(win, true), &ctrl);
     if (st != SLIC_OK) return st;
+    unsigned char *const base = ctrl + kStaticCtrlBytes;
 
     FrameArgs a{};
     a.conv = make_conv(p.color_space);
@@ -603,13 +682,24 @@ extern "C" slic_status slic_segment_noalloc(const slic_params *params, const uin
         e = launch_connectivity(d_labels, lbl_tmp, p.width, p.height, s);
         if (e == cudaSuccess) e = launch_connectivity(lbl_tmp, d_labels, p.width, p.height, s);
     } else if (e == cudaSuccess && p.enforce_connectivity == 2) {
-        int *ccl_err = reinterpret_cast<int *>(base + feat_b + acc_b + lbl_b + sizeof(ConvState));
-        e = cudaMemsetAsync(ccl_err, 0, sizeof(int), s);
-        if (e == cudaSuccess)
-            e = launch_connectivity_components(d_labels, d_labels, p.width, p.height, S * S / 4,
-                                               reinterpret_cast<int *>(base + feat_b + acc_b + lbl_b + cs_b), ccl_err,
-                                               s);
+        e = launch_connectivity_components(d_labels, d_labels, p.width, p.height, S * S / 4,
+                                           reinterpret_cast<int *>(base + feat_b + acc_b + lbl_b + cs_b),
+                                           reinterpret_cast<int *>(ctrl), s);
     }
     if (e != cudaSuccess) return fail(nullptr, SLIC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return SLIC_OK;
+}
+
+extern "C" slic_status slic_noalloc_status_check(void) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_static_scratch);
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && flag) e = cudaMemset(p, 0, sizeof(int));
+    if (e != cudaSuccess) return fail(nullptr, SLIC_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+    if (flag) return fail(nullptr, SLIC_ERR_TIMEOUT, "a bounded device loop of the allocation-free path gave up");
     return SLIC_OK;
 }

@@ -49,6 +49,12 @@ struct slic_batch_ctx {
     int stages = 4;          // TMA pipeline stages of the pipelined kernel (3..4)
     int rows = 1;            // row groups per warp of the pipelined kernel (1, or 2 when same8)
     long long launches = 0;
+    // learned warm start (slic_batch_set_warmstart): the network, its labels
+    // [n][H][W] and the device table of the frames' image pointers
+    slic_net net = nullptr;
+    int32_t *net_labels = nullptr;
+    const uint8_t **d_img_table = nullptr;
+    int net_C = 3;
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     size_t ev_used = 0;
@@ -318,8 +324,8 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
     b->pipe = !assign_direct_acc(b->win_max) && assign_pipe_occupancy(b->same, b->win_max, 3, 1) > 0;
     if (b->pipe && assign_pipe_occupancy(b->same, b->win_max, 4, 1) == 0) b->stages = 3;
     b->occupancy = std::max(1, assign_batch_occupancy(b->same, b->smem));
-    if (cudaMalloc(&b->scratch, bytes) != cudaSuccess ||
-        cudaMalloc(&b->d_frames, sizeof(FrameArgs) * n_frames) != cudaSuccess) {
+    if (dev_alloc(&b->scratch, bytes) != cudaSuccess ||
+        dev_alloc(&b->d_frames, sizeof(FrameArgs) * n_frames) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(b->scratch);
         cudaFree(b->d_frames);
@@ -353,6 +359,8 @@ slic_status slic_batch_destroy(slic_batch b) {
     cudaDeviceSynchronize();
     cudaFree(b->scratch);
     cudaFree(b->d_frames);
+    cudaFree(b->net_labels);
+    cudaFree(b->d_img_table);
     for (auto &ev : b->events) {
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
@@ -397,6 +405,8 @@ slic_status slic_batch_set_buffers(slic_batch b, const uint8_t *const *d_images,
         e = cudaMemcpy(b->d_frames, b->frames.data(), sizeof(FrameArgs) * b->n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && b->connectivity == 2)
         e = cudaMemcpy(b->d_ccl, b->ccl_frames.data(), sizeof(CclFrame) * b->n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b->net)
+        e = cudaMemcpy(b->d_img_table, d_images, sizeof(const uint8_t *) * b->n, cudaMemcpyHostToDevice);
     // Sentinel ring of the padded centre tables (geometry only).
     if (e == cudaSuccess) e = launch_fill_ring(b->d_frames, b->n, b->max_ring, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -422,6 +432,22 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
     }
     if (e == cudaSuccess) e = launch_init_batch(b->d_frames, b->n, b->total_centres, s);
     ++n_launch;
+    const bool warm = b->net != nullptr;
+    if (warm) {
+        // Learned warm start: the network's labels, their member sums (from
+        // the features of the pre-pass) and one update without the stopping
+        // test's bookkeeping (update 0) turn them into the initial centres.
+        if (e == cudaSuccess && !b->pipe) {
+            e = launch_convert_batch(b->d_frames, b->n, b->total_rows, b->max_w, s);
+            ++n_launch;
+        }
+        if (e == cudaSuccess && net_forward_labels(b->net, b->n, nullptr, b->d_img_table, b->net_C, b->net_labels,
+                                                   s) != cudaSuccess)
+            return bfail(b, SLIC_ERR_CUDA, std::string("network forward: ") + slic_net_last_error(b->net));
+        if (e == cudaSuccess) e = launch_accumulate_labels_batch(b->d_frames, b->n, b->total_rows, b->max_w, s);
+        if (e == cudaSuccess) e = launch_update_batch(b->d_frames, b->n, b->total_centres, 0, s);
+        n_launch += 2;
+    }
     for (int pass = 0; e == cudaSuccess && pass <= b->iterations; ++pass) {
         if (pass > 0) {
             e = launch_update_batch(b->d_frames, b->n, b->total_centres, pass, s);
@@ -444,7 +470,7 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
                 e = launch_assign_pipe(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == b->iterations,
                                        b->stages, b->rows, pipe_per_sm, grid_pipe, b->d_err, b->any_conv ? 1 : 0, s);
             else
-                e = launch_assign_batch(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == 0,
+                e = launch_assign_batch(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == 0 && !warm,
                                         pass == b->iterations, b->smem, grid, s);
             if (e1 && e == cudaSuccess) e = record_profile_event(e1, s);
             ++n_launch;
@@ -647,6 +673,63 @@ slic_status slic_batch_profile_times(slic_batch b, double *ms, int max_n, int *n
         ms[i] = t;
     }
     *n = count;
+    return SLIC_OK;
+}
+
+slic_status slic_batch_grid(slic_batch b, int frame, int *S, int *ns_c, int *ns_r) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (frame < 0 || frame >= b->n) return bfail(b, SLIC_ERR_INVALID, "frame index out of range");
+    const FrameArgs &a = b->frames[frame];
+    if (S) *S = a.S;
+    if (ns_c) *ns_c = a.ns_c;
+    if (ns_r) *ns_r = a.ns_r;
+    return SLIC_OK;
+}
+
+slic_status slic_batch_set_warmstart(slic_batch b, slic_net net) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (net) {
+        int W = 0, H = 0, S = 0, max_batch = 0;
+        float m = 0.0f;
+        net_geometry(net, &W, &H, &S, &m, &max_batch);
+        for (int f = 0; f < b->n; ++f) {
+            const FrameArgs &a = b->frames[f];
+            if (a.W != W || a.H != H || a.S != S || b->params[f].m != m)
+                return bfail(b, SLIC_ERR_INVALID,
+                             "frame " + std::to_string(f) + " differs from the network's width, height, S or m");
+            if (a.C != b->frames[0].C) return bfail(b, SLIC_ERR_INVALID, "the frames' channel counts differ");
+        }
+    }
+    // Queued work may still read the tables: wait, then change them.
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && net && !b->net_labels) {
+        if (dev_alloc(&b->net_labels, sizeof(int32_t) * (size_t)b->total_pixels) != cudaSuccess ||
+            dev_alloc(&b->d_img_table, sizeof(const uint8_t *) * b->n) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(b->net_labels);
+            cudaFree(b->d_img_table);
+            b->net_labels = nullptr;
+            b->d_img_table = nullptr;
+            return bfail(b, SLIC_ERR_NOMEM, "device allocation of the warm-start labels failed");
+        }
+    }
+    if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("device wait: ") + cudaGetErrorString(e));
+    b->net = net;
+    b->net_C = b->frames[0].C;
+    std::vector<const uint8_t *> imgs(b->n);
+    size_t off = 0;
+    for (int f = 0; f < b->n; ++f) {
+        FrameArgs &a = b->frames[f];
+        a.init_labels = net ? b->net_labels + off : nullptr;
+        off += (size_t)a.W * a.H;
+        imgs[f] = a.rgb;
+    }
+    if (b->buffers_set) {
+        e = cudaMemcpy(b->d_frames, b->frames.data(), sizeof(FrameArgs) * b->n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && net)
+            e = cudaMemcpy(b->d_img_table, imgs.data(), sizeof(const uint8_t *) * b->n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
+    }
     return SLIC_OK;
 }
 

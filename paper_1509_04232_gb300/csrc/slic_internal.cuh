@@ -7,6 +7,8 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include "slic.h"
+
 namespace slicgb {
 
 // Fixed-point scale for the centre-update sums: CIELAB and XYZ features
@@ -136,6 +138,8 @@ struct FrameArgs {
     int perturb;            // 1: grid seeds move to the lowest-gradient pixel nearby (Sec. 2)
     float conv_eps;         // stopping threshold on the mean L1 move (0: fixed iterations)
     ConvState *cstate;      // the frame's stopping-test state (reset by the initialisation)
+    const int32_t *init_labels;  // [H][W] labels whose member means replace the grid
+                                 // centres (learned warm start), or null
 };
 
 // Shared memory for one assignment CTA whose tile spans at most win_n cells.
@@ -156,6 +160,18 @@ void srgb_table(float lut[256]);
 cudaError_t device_setup(int dev, size_t smem);
 
 cudaError_t upload_lut(const float *lut256);
+
+// Device allocations of the library go through dev_malloc, so that fault
+// injection (slic_fault_inject, SLIC_FAULT_ALLOC) can make them fail.
+cudaError_t dev_malloc(void **p, size_t bytes);
+template <typename T>
+cudaError_t dev_alloc(T **p, size_t bytes) {
+    return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+// The device words of fault injection on the current device: the step limit
+// of component connectivity's walks and the pipelined assignment's copy stop.
+cudaError_t set_fault_words(unsigned ccl_steps, int abort_copies);
+unsigned ccl_default_steps();
 cudaError_t configure_kernels(size_t max_smem);
 
 cudaError_t launch_init_from_rgb(const FrameArgs &a, cudaStream_t s);
@@ -196,6 +212,10 @@ cudaError_t launch_convert_batch(const FrameArgs *d_frames, int n, int total_row
 cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cudaStream_t s);
 cudaError_t launch_accumulate_labels(const float *feat, int W, int H, int P, const int32_t *labels, int K,
                                      long long *acc, float fix_scale, cudaStream_t s);
+// Member sums of every frame's init_labels map (frames without one are
+// skipped); the sums must be zero before (the initialisation clears them).
+cudaError_t launch_accumulate_labels_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w,
+                                           cudaStream_t s);
 cudaError_t launch_convert(const ConvConsts &cc, const uint8_t *rgb, int W, int H, int C, float *feat, int P,
                            cudaStream_t s);
 cudaError_t launch_connectivity(const int32_t *in, int32_t *out, int W, int H, cudaStream_t s);
@@ -226,6 +246,14 @@ struct CclFrame {
 };
 cudaError_t launch_connectivity_components(const CclFrame *d_table, const CclFrame &one, int n, int G, int *scratch,
                                            int *err, cudaStream_t s);
+// The learned warm start's network (slic_net.cu) as seen by the segmentation
+// drivers: its geometry, and the labels of `batch` images (uint8 [H][W][C],
+// C = 3 or 4; given by a device table of image pointers, or contiguous in
+// d_images when d_table is null) into labels [batch][H][W], forward passes
+// of at most max_batch images (on failure slic_net_last_error tells why).
+bool net_geometry(const slic_net_ctx *n, int *W, int *H, int *S, float *m, int *max_batch);
+cudaError_t net_forward_labels(slic_net_ctx *n, int batch, const uint8_t *d_images, const uint8_t *const *d_table,
+                               int C, int32_t *labels, cudaStream_t s);
 // Event record for the profiling timers, valid inside and outside stream capture.
 cudaError_t record_profile_event(cudaEvent_t ev, cudaStream_t s);
 

@@ -740,6 +740,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// Fault injection for tests of the timeout reporting: while non-zero, the
+// pipelined assignment's producers issue no further copy (checked before
+// each one, so a CTA that gives up has none in flight); the consumers'
+// bounded waits then run out.
+__device__ int g_abort_copies = 0;
+
 // Wait for the phase with the given parity to complete; gives up (returns
 // false) after kWaitPolls polls with a 1 us suspend hint each.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
@@ -1007,6 +1013,7 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
     auto produce = [&](int j, int q, int use) -> bool {
         const int t = blockIdx.x + j * gridDim.x;
         if (t >= total_tiles) return true;
+        if (*reinterpret_cast<volatile int *>(&g_abort_copies)) return false;
         if (use > 0 && !mbar_wait(&empty[q], (use - 1) & 1)) return false;
         const int f = find_frame<kTileBase>(frames, n_frames, t);
         TileGeom g = tile_geom(frames[f], t - frames[f].tile_base);
@@ -1480,45 +1487,72 @@ __global__ void k_update_batch(const FrameArgs *frames, int n, int total, int it
     }
 }
 
+// Adds each lane's pixel (fixed-point features, x, y, 1 in v) to the sums
+// of its label `key` (< 0: nothing to add), one global atomic per (label,
+// component) for all lanes of the warp with that label. Every lane of the
+// warp must call it.
+__device__ __forceinline__ void add_pixel_sums(long long *acc, int key, const int (&v)[6]) {
+    const int lane = threadIdx.x & 31;
+    unsigned pending = __ballot_sync(kFull, key >= 0);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int k = __shfl_sync(kFull, key, leader);
+        const bool mine = key == k;
+        const unsigned grp = __ballot_sync(kFull, mine);
+        int s[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s[c] = __reduce_add_sync(kFull, mine ? v[c] : 0);
+        if (lane == leader) {
+            unsigned long long *g = reinterpret_cast<unsigned long long *>(acc) + (size_t)k * 6;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) atomicAdd(&g[c], (unsigned long long)(long long)s[c]);
+        }
+        pending &= ~grp;
+    }
+}
+
+// The fixed-point features, coordinates and count of pixel (x, y) when its
+// label k lies in [0, K): returns k, else -1.
+__device__ __forceinline__ int pixel_sums(const float *feat, int H, int P, const int32_t *labels, int W, int K,
+                                          float fs, int x, int y, int (&v)[6]) {
+    const int k = labels[(size_t)y * W + x];
+    if (k < 0 || k >= K) return -1;
+    const size_t plane = (size_t)H * P, off = (size_t)y * P + x;
+    v[0] = __float2int_rn(feat[off] * fs);
+    v[1] = __float2int_rn(feat[plane + off] * fs);
+    v[2] = __float2int_rn(feat[2 * plane + off] * fs);
+    v[3] = x;
+    v[4] = y;
+    v[5] = 1;
+    return k;
+}
+
 // Sums of the pixels of each label from an explicit label map (an update
 // from given labels, e.g. a learned warm start). One thread per pixel;
 // warp-aggregated global atomics.
 __global__ void k_accumulate_labels(const float *feat, int W, int H, int P, const int32_t *labels, int K,
                                     long long *acc, float fs) {
-    const int lane = threadIdx.x & 31;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     for (int y = blockIdx.y; y < H; y += gridDim.y) {
-        int key = -1;
         int v[6] = {0, 0, 0, 0, 0, 0};
-        if (x < W) {
-            const int k = labels[(size_t)y * W + x];
-            if (k >= 0 && k < K) {
-                const size_t plane = (size_t)H * P, off = (size_t)y * P + x;
-                key = k;
-                v[0] = __float2int_rn(feat[off] * fs);
-                v[1] = __float2int_rn(feat[plane + off] * fs);
-                v[2] = __float2int_rn(feat[2 * plane + off] * fs);
-                v[3] = x;
-                v[4] = y;
-                v[5] = 1;
-            }
-        }
-        unsigned pending = __ballot_sync(kFull, key >= 0);
-        while (pending) {
-            const int leader = __ffs(pending) - 1;
-            const int k = __shfl_sync(kFull, key, leader);
-            const bool mine = key == k;
-            const unsigned grp = __ballot_sync(kFull, mine);
-            int s[6];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) s[c] = __reduce_add_sync(kFull, mine ? v[c] : 0);
-            if (lane == leader) {
-                unsigned long long *g = reinterpret_cast<unsigned long long *>(acc) + (size_t)k * 6;
-#pragma unroll
-                for (int c = 0; c < 6; ++c) atomicAdd(&g[c], (unsigned long long)(long long)s[c]);
-            }
-            pending &= ~grp;
-        }
+        const int key = x < W ? pixel_sums(feat, H, P, labels, W, K, fs, x, y, v) : -1;
+        add_pixel_sums(acc, key, v);
+    }
+}
+
+// The same for every frame of a batch that has an initial label map
+// (init_labels, e.g. a network's prediction), over the rows of all frames in
+// one index space; the first update then takes the member means.
+__global__ void __launch_bounds__(128) k_accumulate_labels_batch(const FrameArgs *frames, int n, int total_rows) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int gr = blockIdx.y; gr < total_rows; gr += gridDim.y) {
+        const FrameArgs &a = frames[find_frame<kRowBase>(frames, n, gr)];
+        if (!a.init_labels) continue;  // (the same for the whole block)
+        int v[6] = {0, 0, 0, 0, 0, 0};
+        const int key = x < a.W ? pixel_sums(a.feat, a.H, a.P, a.init_labels, a.W, a.ns_c * a.ns_r, a.fix_scale, x,
+                                             gr - a.row_base, v)
+                                : -1;
+        add_pixel_sums(a.acc, key, v);
     }
 }
 
@@ -1834,9 +1868,16 @@ __global__ void __launch_bounds__(256, 4) k_connectivity2_batch(const FrameArgs 
 namespace {
 constexpr unsigned kCclSteps = 1u << 22;
 constexpr int kScanThreads = 256, kScanPer = 8, kScanBlock = kScanThreads * kScanPer;
+}  // namespace
 
+// Step limit of every walk below (kCclSteps; lowered only by fault
+// injection, to make walks give up in tests of the timeout reporting).
+__device__ unsigned g_ccl_steps = kCclSteps;
+
+namespace {
 __device__ __forceinline__ int ccl_find(const int *parent, int i, int *err) {
-    for (unsigned n = 0; n < kCclSteps; ++n) {
+    const unsigned lim = g_ccl_steps;
+    for (unsigned n = 0; n < lim; ++n) {
         const int p = __ldcg(parent + i);
         if (p == i) return i;
         i = p;
@@ -1848,7 +1889,8 @@ __device__ __forceinline__ int ccl_find(const int *parent, int i, int *err) {
 // Link the trees of a and b: the larger root takes the smaller as parent
 // (atomicMin; a root changed meanwhile is followed and the link retried).
 __device__ __forceinline__ void ccl_union(int *parent, int a, int b, int *err) {
-    for (unsigned n = 0; n < kCclSteps; ++n) {
+    const unsigned lim = g_ccl_steps;
+    for (unsigned n = 0; n < lim; ++n) {
         a = ccl_find(parent, a, err);
         b = ccl_find(parent, b, err);
         if (a == b) return;
@@ -1948,18 +1990,25 @@ __global__ void k_ccl_decide(CclFrames fr, int G, const int *parent, const int *
 
 // Per root: follow the joins to the kept segment (chains point to smaller
 // indices and end at a kept root; in place, every value written stays on
-// the chain).
+// the chain). After a walk of an earlier stage gave up, a chain may reach
+// an entry no stage wrote: every step is checked to stay in [0, N), and one
+// that would leave it ends the walk with the error bit set.
 __global__ void k_ccl_resolve(int N, const int *parent, int *target, int *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N || parent[i] != i) return;
     int t = target[i];
     unsigned n = 0;
-    for (; n < kCclSteps; ++n) {
+    const unsigned lim = g_ccl_steps;
+    for (; n < lim; ++n) {
         const int u = __ldcg(target + t);
         if (u == t) break;
+        if ((unsigned)u >= (unsigned)N) {
+            n = lim;
+            break;
+        }
         t = u;
     }
-    if (n == kCclSteps) atomicOr(err, 2);
+    if (n == lim) atomicOr(err, 2);
     target[i] = t;
 }
 
@@ -2031,7 +2080,10 @@ __global__ void k_ccl_relabel(CclFrames fr, int G, const int *parent, const int 
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G) return;
     const CclFrame f = ccl_frame_of(fr, g);
-    const int r = target[parent[g]];
+    int r = target[parent[g]];
+    // (out of range only after a walk gave up, which set the error flag:
+    // the label is then wrong, the access still in bounds)
+    if ((unsigned)r >= (unsigned)G) r = f.base;
     f.out[g - f.base] = rank[r] + totals[r / kScanBlock] - (rank[f.base] + totals[f.base / kScanBlock]);
 }
 
@@ -2040,6 +2092,14 @@ __global__ void k_ccl_relabel(CclFrames fr, int G, const int *parent, const int 
 // ---------------------------------------------------------------------------
 
 cudaError_t upload_lut(const float *lut256) { return cudaMemcpyToSymbol(g_lut, lut256, 256 * sizeof(float)); }
+
+cudaError_t set_fault_words(unsigned ccl_steps, int abort_copies) {
+    cudaError_t e = cudaMemcpyToSymbol(g_ccl_steps, &ccl_steps, sizeof ccl_steps);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_abort_copies, &abort_copies, sizeof abort_copies);
+    return e;
+}
+
+unsigned ccl_default_steps() { return kCclSteps; }
 
 template <bool F, bool L, bool SM>
 static cudaError_t set_smem(int bytes) {
@@ -2178,6 +2238,13 @@ static dim3 rows_grid(int W, int H, int bx, int ppt) {
 cudaError_t launch_accumulate_labels(const float *feat, int W, int H, int P, const int32_t *labels, int K,
                                      long long *acc, float fix_scale, cudaStream_t s) {
     k_accumulate_labels<<<rows_grid(W, H, 128, 1), 128, 0, s>>>(feat, W, H, P, labels, K, acc, fix_scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate_labels_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w,
+                                           cudaStream_t s) {
+    const dim3 grid((unsigned)((max_w + 127) / 128), (unsigned)std::min(total_rows, 8192));
+    k_accumulate_labels_batch<<<grid, 128, 0, s>>>(d_frames, n, total_rows);
     return cudaGetLastError();
 }
 

@@ -91,8 +91,8 @@ __device__ __forceinline__ float sqrt_fast(float v) {
 // 9 slots of the pixel's cell window the Eq. (1) distance D/100 to the
 // grid-initialised centre of that cell (2.0 off the grid), zero padding.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_net_prep(ConvConsts cc, const uint8_t *rgb, int W, int H, int C, int S,
-                                                  float w, __nv_bfloat16 *x0) {
+__global__ void __launch_bounds__(128) k_net_prep(ConvConsts cc, const uint8_t *rgb, const uint8_t *const *table,
+                                                  int W, int H, int C, int S, float w, __nv_bfloat16 *x0) {
     // A block covers 128 pixels of one row; the grid centres of the cells its
     // pixels see (three cell rows, the covered cell columns +- 1) are
     // converted once into shared memory instead of once per pixel and slot.
@@ -101,6 +101,8 @@ __global__ void __launch_bounds__(128) k_net_prep(ConvConsts cc, const uint8_t *
     __shared__ float cen_y[3][kMaxCols];     // y (< 0: off the grid)
     const int x0p = blockIdx.x * blockDim.x, y = blockIdx.y, b = blockIdx.z;
     const size_t img = (size_t)b * H * W;
+    // image b: entry b of the pointer table, else the b-th of a contiguous stack
+    const uint8_t *const src = table ? table[b] : rgb + img * C;
     const int ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
     const int cy = y / S, cx_lo = x0p / S - 1;
     const int cx_hi = min(x0p + (int)blockDim.x - 1, W - 1) / S + 1;
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(128) k_net_prep(ConvConsts cc, const uint8_t *
         if (nx >= 0 && nx < ns_c && ny >= 0 && ny < ns_r) {
             // grid initialisation of Sec. 3: midpoint of the in-image cell, colour under it
             const int xf = nx * S, xl = min((nx + 1) * S, W) - 1, yf = ny * S, yl = min((ny + 1) * S, H) - 1;
-            const uint8_t *q = rgb + (img + (size_t)((yf + yl) >> 1) * W + ((xf + xl) >> 1)) * C;
+            const uint8_t *q = src + ((size_t)((yf + yl) >> 1) * W + ((xf + xl) >> 1)) * C;
             float l, a2, b2;
             convert_pixel(cc, q[0], q[1], q[2], g_lut_net, l, a2, b2);
             cen_lab[r][c] = make_float4(l, a2, b2, 0.5f * (float)(xf + xl));
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(128) k_net_prep(ConvConsts cc, const uint8_t *
     const int x = x0p + threadIdx.x;
     if (x >= W) return;
     const size_t px = img + (size_t)y * W + x;
-    const uint8_t *p = rgb + px * C;
+    const uint8_t *p = src + ((size_t)y * W + x) * C;
     float f0, f1, f2;
     convert_pixel(cc, p[0], p[1], p[2], g_lut_net, f0, f1, f2);
     const int cx = x / S;
@@ -798,6 +800,22 @@ __global__ void k_net_labels(const float *logits, int W, int H, int n_img, int S
     labels[p] = (cy + arg / 3 - 1) * ns_c + cx + arg % 3 - 1;
 }
 
+// Training targets: the slot (dy+1)*3 + (dx+1) of each pixel's label
+// relative to its own cell; 255 (and a count in *bad) for a label outside
+// the pixel's 3x3 cell window.
+__global__ void k_net_slots(const int32_t *labels, int W, int H, int n_img, int S, uint8_t *slots, int *bad) {
+    const long long n_px = (long long)W * H * n_img;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_px) return;
+    const int x = (int)(p % W), y = (int)((p / W) % H);
+    const int ns_c = (W + S - 1) / S, ns_r = (H + S - 1) / S;
+    const int k = labels[p];
+    const int dx = k % ns_c - x / S, dy = k / ns_c - y / S;
+    const bool ok = k >= 0 && k < ns_c * ns_r && dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1;
+    slots[p] = ok ? (uint8_t)((dy + 1) * 3 + dx + 1) : (uint8_t)255;
+    if (!ok && bad) atomicAdd(bad, 1);
+}
+
 // Adam on the FP32 master weights of one layer (padded layout; padding stays
 // zero), refreshing both bf16 copies.
 __global__ void k_adam(float *w, float *m, float *v, const float *g, int cin_p, int cout_p, int cin_r, int cout_r,
@@ -888,7 +906,7 @@ slic_status nfail(slic_net_ctx *n, slic_status st, const std::string &msg) {
 template <typename T>
 bool nalloc(slic_net_ctx *n, T **p, size_t count) {
     void *q = nullptr;
-    if (cudaMalloc(&q, sizeof(T) * count) != cudaSuccess) {
+    if (dev_alloc(&q, sizeof(T) * count) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -946,9 +964,9 @@ cudaError_t conv_fwd(const slic_net_ctx *nc, int l, const __nv_bfloat16 *wf, con
 
 // Forward pass into n->logits, or, with labels_out, straight to labels.
 slic_status forward_all(slic_net_ctx *n, int batch, const uint8_t *d_images, cudaStream_t s,
-                        int32_t *labels_out = nullptr) {
+                        int32_t *labels_out = nullptr, const uint8_t *const *d_table = nullptr, int C = 3) {
     const dim3 pg((n->W + 127) / 128, n->H, batch);
-    k_net_prep<<<pg, 128, 0, s>>>(n->conv, d_images, n->W, n->H, 3, n->S, n->m / (float)n->S, n->act[0]);
+    k_net_prep<<<pg, 128, 0, s>>>(n->conv, d_images, d_table, n->W, n->H, C, n->S, n->m / (float)n->S, n->act[0]);
     cudaError_t e = cudaGetLastError();
     for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
         void *out = l < 3 ? static_cast<void *>(n->act[l + 1])
@@ -1003,6 +1021,33 @@ slic_status backward_all(slic_net_ctx *n, int batch, const uint8_t *d_targets, c
 }
 
 }  // namespace
+
+// The network as seen by the segmentation drivers (the learned warm start
+// of slic_batch_set_warmstart / slic_set_warmstart).
+bool slicgb::net_geometry(const slic_net_ctx *n, int *W, int *H, int *S, float *m, int *max_batch) {
+    if (!n) return false;
+    *W = n->W;
+    *H = n->H;
+    *S = n->S;
+    *m = n->m;
+    *max_batch = n->max_batch;
+    return true;
+}
+
+// Labels of `batch` images into labels [batch][H][W], max_batch images per
+// forward pass: image i is entry i of the device table d_table when given,
+// else the i-th of the contiguous stack d_images (uint8 [H][W][C] each).
+cudaError_t slicgb::net_forward_labels(slic_net_ctx *n, int batch, const uint8_t *d_images,
+                                       const uint8_t *const *d_table, int C, int32_t *labels, cudaStream_t s) {
+    const size_t px = (size_t)n->W * n->H;
+    for (int b0 = 0; b0 < batch; b0 += n->max_batch) {
+        const int nb = std::min(n->max_batch, batch - b0);
+        const uint8_t *imgs = d_table ? nullptr : d_images + (size_t)b0 * px * C;
+        if (forward_all(n, nb, imgs, s, labels + (size_t)b0 * px, d_table ? d_table + b0 : nullptr, C) != SLIC_OK)
+            return cudaErrorLaunchFailure;
+    }
+    return cudaSuccess;
+}
 
 extern "C" {
 
@@ -1221,6 +1266,19 @@ slic_status slic_net_train_step(slic_net n, int batch, const uint8_t *d_images, 
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("optimiser launch: ") + cudaGetErrorString(e));
+    return SLIC_OK;
+}
+
+slic_status slic_net_slots(slic_net n, int batch, const int32_t *d_labels, uint8_t *d_slots, int *d_bad,
+                           void *stream) {
+    if (!n) return nfail(nullptr, SLIC_ERR_INVALID, "NULL network");
+    if (batch <= 0 || !d_labels || !d_slots) return nfail(n, SLIC_ERR_INVALID, "bad batch, labels or slots");
+    const long long n_px = (long long)n->W * n->H * batch;
+    if (n_px >= (1LL << 40)) return nfail(n, SLIC_ERR_INVALID, "batch too large");
+    k_net_slots<<<(unsigned)((n_px + 255) / 256), 256, 0, (cudaStream_t)stream>>>(d_labels, n->W, n->H, batch, n->S,
+                                                                                 d_slots, d_bad);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("slot kernel launch: ") + cudaGetErrorString(e));
     return SLIC_OK;
 }
 

@@ -1,13 +1,14 @@
 """Learned warm start: a small convolutional network predicts each pixel's
 cell among the 9 of its 3x3 cell window; its labels give initial centres
-(member means), after which one or two SLIC iterations replace the usual
-five to ten. The network, its training (forward, backward, Adam) and its
-inference are the library's own CUDA kernels (``slic_net_*`` in
-include/slic.h); this module only drives them.
+(member means), after which a few SLIC iterations replace the usual five
+to ten. The network, its training (forward, backward, Adam), its inference
+and the warm-started segmentation (``slic_batch_set_warmstart``) are the
+library's own CUDA kernels behind include/slic.h; this module only drives
+them (data, the learning-rate schedule, the order of the calls).
 
 Training targets are the slots of full-iteration SLIC labels (S=16, m=10,
 10 iterations, before connectivity) computed by this library's batched GPU
-path on seeded synthetic 256x256 images.
+path on seeded synthetic 256x256 images (``slic_net_slots``).
 """
 from __future__ import annotations
 
@@ -15,19 +16,6 @@ import numpy as np
 
 from . import _binding as B
 from . import synth
-
-
-def slots_from_labels(labels: np.ndarray, S: int) -> np.ndarray:
-    """Slot (dy+1)*3 + (dx+1) of each pixel's label relative to its own cell
-    (labels [..., H, W] must lie in the 3x3 cell window, as assignment labels do)."""
-    H, W = labels.shape[-2:]
-    ns_c = -(-W // S)
-    ys, xs = np.mgrid[0:H, 0:W]
-    dx = labels % ns_c - xs // S
-    dy = labels // ns_c - ys // S
-    if np.any(np.abs(dx) > 1) or np.any(np.abs(dy) > 1):
-        raise ValueError("labels outside the 3x3 cell window")
-    return ((dy + 1) * 3 + (dx + 1)).astype(np.uint8)
 
 
 class WarmStartNet:
@@ -102,14 +90,29 @@ def reference_labels(images_u8, S: int = 16, m: float = 10.0, iterations: int = 
     return out
 
 
-def training_batch(first: int, count: int, device, S: int = 16, m: float = 10.0, iterations: int = 10):
-    """Seeded 256x256 training images first..first+count-1 and their target slots."""
+def target_slots(net: "WarmStartNet", labels_i32):
+    """Slots (dy+1)*3 + (dx+1) of labels int32 CUDA [n, H, W] relative to
+    each pixel's own cell (the library's slic_net_slots), as uint8 CUDA
+    [n, H, W]; raises if a label lies outside its pixel's 3x3 cell window."""
+    import torch
+    n = labels_i32.shape[0]
+    slots = torch.empty(labels_i32.shape, dtype=torch.uint8, device=labels_i32.device)
+    bad = torch.zeros(1, dtype=torch.int32, device=labels_i32.device)
+    s = int(torch.cuda.current_stream().cuda_stream)
+    B.slic_net_slots(net.handle, n, labels_i32.data_ptr(), slots.data_ptr(), bad.data_ptr(), s)
+    if int(bad.item()) != 0:
+        raise ValueError(f"{int(bad.item())} labels outside the 3x3 cell window")
+    return slots
+
+
+def training_batch(net: "WarmStartNet", first: int, count: int, device, m: float = 10.0, iterations: int = 10):
+    """Seeded 256x256 training images first..first+count-1 and their target
+    slots (the network's geometry: width, height and S)."""
     import torch
     host = np.stack([synth.train_image(i) for i in range(first, first + count)])
     imgs = torch.from_numpy(host).to(device)
-    labels = reference_labels(imgs, S, m, iterations).cpu().numpy()
-    slots = slots_from_labels(labels, S)
-    return imgs, torch.from_numpy(slots).to(device)
+    labels = reference_labels(imgs, net.S, m, iterations)
+    return imgs, target_slots(net, labels.contiguous())
 
 
 def train(net: WarmStartNet, n_images: int, batch: int = 32, epochs: int = 1, lr: float = 2e-3,
@@ -125,7 +128,7 @@ def train(net: WarmStartNet, n_images: int, batch: int = 32, epochs: int = 1, lr
     for _ in range(epochs):
         for c0 in range(first_image, first_image + n_images, chunk):
             cn = min(chunk, first_image + n_images - c0)
-            imgs, slots = training_batch(c0, cn, dev, net.S)
+            imgs, slots = training_batch(net, c0, cn, dev, net.m)
             order = torch.randperm(cn, device=dev)
             for b0 in range(0, cn - batch + 1, batch):
                 idx = order[b0:b0 + batch]
@@ -145,27 +148,21 @@ def train(net: WarmStartNet, n_images: int, batch: int = 32, epochs: int = 1, lr
 
 def warm_start_segment(net: WarmStartNet, images_u8, iterations: int, m: float = 10.0,
                        enforce_connectivity: bool = True):
-    """Segment frames [n, H, W, 3] starting from the network's labels: centres
-    are the member means of the predicted labels (slic_update), then
-    `iterations` assignments (iterations - 1 updates between them) and
+    """Segment frames [n, H, W, 3] from the network's labels (the library's
+    warm start: member means of the predicted labels replace the grid
+    centres), then an assignment, `iterations` x {update, assignment} and
     connectivity. Returns (labels list, centres list)."""
-    import torch
-    from . import BatchSegmenter, Segmenter
+    from . import BatchSegmenter
     n, H, W, _ = images_u8.shape
-    dev = images_u8.device
-    net_labels = torch.empty((n, H, W), dtype=torch.int32, device=dev)
-    net.forward(images_u8, labels=net_labels)
-    seg = Segmenter(W, H, S=net.S, m=m, iterations=0)
-    init = []
-    for i in range(n):
-        feat = seg.convert(images_u8[i])
-        c0 = seg.init_centres(feat)
-        init.append(seg.update(feat, net_labels[i], c0))
-    bs = BatchSegmenter([dict(width=W, height=H, S=net.S, m=m)] * n, iterations=iterations - 1,
-                        enforce_connectivity=enforce_connectivity, device=dev)
-    bs.bind([images_u8[i] for i in range(n)], init_centres=init)
+    bs = BatchSegmenter([dict(width=W, height=H, S=net.S, m=m)] * n, iterations=iterations,
+                        enforce_connectivity=enforce_connectivity, device=images_u8.device)
+    bs.bind([images_u8[i] for i in range(n)])
+    bs.set_warmstart(net)
     labels, centres = bs.segment()
-    return [l.clone() for l in labels], [c.clone() for c in centres]
+    out = [l.clone() for l in labels], [c.clone() for c in centres]
+    bs.status()
+    bs.close()
+    return out
 
 
 def agreement(a, b) -> float:
@@ -187,40 +184,24 @@ def plain_segment(images_u8, iterations: int, S: int = 16, m: float = 10.0, enfo
 
 
 class WarmStartPipeline:
-    """The learned path for a fixed set of frames, with every buffer
-    allocated up front so that `run` only enqueues kernels (and can be
-    captured into a CUDA graph): network labels -> member-mean centres per
-    frame -> `iterations` assignments of the batched path -> connectivity."""
+    """The learned path for a fixed set of frames: one warm-started batch
+    (network labels -> member-mean centres -> assignment, `iterations` x
+    {update, assignment} -> connectivity, all enqueued by one library call),
+    so `run` can be captured into a CUDA graph."""
 
     def __init__(self, net: WarmStartNet, images, iterations: int, m: float = 10.0,
                  enforce_connectivity: bool = True):
-        import torch
-        from . import BatchSegmenter, Segmenter
+        from . import BatchSegmenter
         self.net = net
         self.images = list(images)
-        n = len(self.images)
         H, W, _ = self.images[0].shape
-        dev = self.images[0].device
-        self.stacked = torch.stack(self.images)
-        self.net_labels = torch.empty((n, H, W), dtype=torch.int32, device=dev)
-        self.seg = Segmenter(W, H, S=net.S, m=m, iterations=0)
-        self.feat = torch.empty((3, H, W), dtype=torch.float32, device=dev)
-        self.c0 = torch.empty((self.seg.K_eff, 6), dtype=torch.float32, device=dev)
-        self.init = [torch.empty((self.seg.K_eff, 6), dtype=torch.float32, device=dev) for _ in range(n)]
-        self.bs = BatchSegmenter([dict(width=W, height=H, S=net.S, m=m)] * n, iterations=iterations - 1,
-                                 enforce_connectivity=enforce_connectivity, device=dev)
-        self.bs.bind(self.images, init_centres=self.init)
+        self.bs = BatchSegmenter([dict(width=W, height=H, S=net.S, m=m)] * len(self.images), iterations=iterations,
+                                 enforce_connectivity=enforce_connectivity, device=self.images[0].device)
+        self.bs.bind(self.images)
+        self.bs.set_warmstart(net)
 
     def run(self, stream=None):
-        import torch
-        s = int((stream if stream is not None else torch.cuda.current_stream()).cuda_stream)
-        B.slic_net_forward(self.net.handle, len(self.images), self.stacked.data_ptr(), None,
-                           self.net_labels.data_ptr(), s)
-        h = self.seg.handle
-        for i, img in enumerate(self.images):
-            B.slic_convert(h, img.data_ptr(), self.feat.data_ptr(), s)
-            B.slic_init_centres(h, self.feat.data_ptr(), self.c0.data_ptr(), s)
-            B.slic_update(h, self.feat.data_ptr(), self.net_labels[i].data_ptr(), self.c0.data_ptr(),
-                          self.init[i].data_ptr(), s)
-        B.slic_batch_segment(self.bs.handle, s)
-        return self.bs.labels, self.bs.centres
+        return self.bs.segment(stream)
+
+    def close(self):
+        self.bs.close()

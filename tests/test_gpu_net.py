@@ -4,8 +4,10 @@ Tolerances (derived from the precision model: bf16 weights and stored
 activations, FP32 accumulation vs FP64 in the oracle):
   logits     |gpu - oracle| <= 2e-2 * max(1, max |oracle|), and the argmax
              slot agrees wherever the oracle's top two logits differ by > 2e-2
-  gradients  per layer, ||gpu - oracle|| <= 5e-2 * ||oracle|| (the device
-             back-propagates bf16 gradients)
+  gradients  per element, |gpu - oracle| <= 2^-6 |oracle| + 2^-8 T + 2^-14 T1
+             against the oracle with the device's bf16 gradient storage, T =
+             the sum of the absolute values of the element's terms, T1 that
+             of their FP32 summation scale
 """
 import numpy as np
 import pytest
@@ -94,40 +96,104 @@ def test_fused_labels_equal_labels_from_logits(slic_gpu):
     assert torch.equal(got, want)
 
 
+def _term_magnitudes(dzs, params):
+    """Per layer (Tw, Tb, T1w, T1b). Tw, Tb: for every gradient element the
+    sum of the absolute values of its terms, |a_in dz| (dW) and |dz| (db),
+    with the oracle's stored dL/dz of the layer. T1w, T1b: the same with dz
+    replaced by the scale of its own FP32 summation -- sum |dz_next| |w| over
+    the next layer's taps for a hidden layer, 1/(H W) for the softmax
+    gradient -- against which FP32-vs-FP64 noise of a near-cancelling dz is
+    measured."""
+    out = []
+    L = len(dzs)
+    for l, (dz, a_in) in enumerate(dzs):
+        H, W, _ = dz.shape
+        if l == L - 1:
+            scale = np.full(dz.shape, 1.0 / (H * W))
+        else:
+            nxt = np.pad(np.abs(dzs[l + 1][0]), ((1, 1), (1, 1), (0, 0)))
+            wq = np.abs(NO.bf16_round(params[l + 1][0]))
+            scale = np.zeros(dz.shape)
+            for dy in range(3):
+                for dx in range(3):
+                    scale += nxt[2 - dy:2 - dy + H, 2 - dx:2 - dx + W, :] @ wq[dy, dx].T
+        ap = np.pad(np.abs(a_in), ((1, 1), (1, 1), (0, 0)))
+        tw = np.zeros((3, 3, a_in.shape[2], dz.shape[2]))
+        t1 = np.zeros_like(tw)
+        for dy in range(3):
+            for dx in range(3):
+                win = ap[dy:dy + H, dx:dx + W, :]
+                tw[dy, dx] = np.einsum("yxi,yxo->io", win, np.abs(dz))
+                t1[dy, dx] = np.einsum("yxi,yxo->io", win, scale)
+        out.append((tw, np.abs(dz).sum(axis=(0, 1)), t1, scale.sum(axis=(0, 1))))
+    return out
+
+
 def test_gradients_match_oracle(slic_gpu):
+    """Every weight and bias gradient element against the FP64 oracle with
+    dL/dz rounded to bf16 where the device stores it (bf16_grad). Two 160x80
+    images: 400 weight-gradient tiles of 16x4 pixels, more than the 304
+    persistent CTAs, so CTAs accumulate several tiles. What remains is FP32
+    against FP64 summation and stored values that land on the other side of
+    a bf16 rounding boundary: in the forward pass a few activations, whose
+    one-step (2^-8 relative) changes move the logits and so every softmax
+    gradient a little, each of which can again round either way. Each term
+    is then off by at most about one bf16 step, so per element
+        |gpu - oracle| <= 2^-6 |oracle| + 2^-8 T + 2^-14 T1,
+    T = the sum of the absolute values of the element's terms (|a_in dz|
+    over the pixels, with the oracle's stored dz) and T1 the same with dz
+    replaced by the scale of the FP32 sum that produced it (a dz that nearly
+    cancels carries FP32 noise of about 2^-24 times that scale per term). A
+    wrong tap, channel or sign in one element moves it by about |g|, which
+    is typically a tenth of T or more here (random targets): ten times the
+    bound or more."""
     import torch
-    net, host, imgs = _setup(slic_gpu)
+    n, W, H, S = 2, 160, 80, 8
+    net, host, imgs = _setup(slic_gpu, n=n, W=W, H=H, S=S)
     rng = np.random.default_rng(0)
-    valid = NO.slot_mask(40, 48, 8)
-    target = np.zeros((2, 40, 48), np.uint8)
-    for i in range(2):
-        for y in range(40):
-            for x in range(48):
+    valid = NO.slot_mask(H, W, S)
+    target = np.zeros((n, H, W), np.uint8)
+    for i in range(n):
+        for y in range(H):
+            for x in range(W):
                 target[i, y, x] = rng.choice(np.flatnonzero(valid[y, x]))
     stats = torch.zeros(2, dtype=torch.float32, device="cuda")
     net.gradients(imgs, torch.from_numpy(target).cuda(), stats)
     torch.cuda.synchronize()
     g_gpu = _split(net.grads())
     params = _split(net.params())
-    # the batch loss is the mean over both images: average the oracle's per-image gradients
+    # the batch loss is the mean over the images: average the oracle's per-image gradients
     g_ref = [(np.zeros_like(w), np.zeros_like(b)) for w, b in params]
+    t_ref = [(np.zeros_like(w), np.zeros_like(b)) for w, b in params]
+    t1_ref = [(np.zeros_like(w), np.zeros_like(b)) for w, b in params]
     loss_ref = 0.0
-    for i in range(2):
-        li, gi = NO.backward(_oracle_input(host[i], 8), params, target[i].astype(np.int64), valid, bf16=True)
-        loss_ref += li / 2
+    for i in range(n):
+        x0 = _oracle_input(host[i], S)
+        ti = target[i].astype(np.int64)
+        li, gi, dzs = NO.backward(x0, params, ti, valid, bf16=True, bf16_grad=True, return_dz=True)
+        mi = _term_magnitudes(dzs, params)
+        loss_ref += li / n
         for l in range(4):
-            g_ref[l] = (g_ref[l][0] + gi[l][0] / 2, g_ref[l][1] + gi[l][1] / 2)
-    assert float(stats[0]) / (2 * 40 * 48) == pytest.approx(loss_ref, rel=1e-2)
+            g_ref[l] = (g_ref[l][0] + gi[l][0] / n, g_ref[l][1] + gi[l][1] / n)
+            t_ref[l] = (t_ref[l][0] + mi[l][0] / n, t_ref[l][1] + mi[l][1] / n)
+            t1_ref[l] = (t1_ref[l][0] + mi[l][2] / n, t1_ref[l][1] + mi[l][3] / n)
+    assert float(stats[0]) / (n * W * H) == pytest.approx(loss_ref, rel=1e-2)
+    worst = []
     for l in range(4):
-        for a, b in zip(g_gpu[l], g_ref[l]):
-            assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b), (l, np.linalg.norm(a - b) / np.linalg.norm(b))
+        for a, b, t, t1 in zip(g_gpu[l], g_ref[l], t_ref[l], t1_ref[l]):
+            bound = 2.0 ** -6 * np.abs(b) + 2.0 ** -8 * t + 2.0 ** -14 * t1
+            bad = np.abs(a - b) > bound
+            worst.append(float(np.max(np.abs(a - b) / np.maximum(bound, 1e-30))))
+            assert not bad.any(), (l, np.argwhere(bad)[:5].tolist(), a[bad][:5], b[bad][:5], t[bad][:5])
+    print("gradient elements, worst |gpu - oracle| / bound per layer (weights, bias):",
+          " ".join(f"{w:.3g}" for w in worst))
 
 
 def test_training_reduces_loss(slic_gpu):
     import torch
     from paper_1509_04232_gb300.warmstart import WarmStartNet, training_batch
     net = WarmStartNet(256, 256, 16, max_batch=8, seed=1)
-    imgs, slots = training_batch(0, 8, torch.device("cuda"))
+    imgs, slots = training_batch(net, 0, 8, torch.device("cuda"))
     stats = torch.zeros(2, dtype=torch.float32, device="cuda")
     losses = []
     for step in range(60):
@@ -160,7 +226,7 @@ def test_trained_network_beats_grid_start_at_equal_iterations(slic_gpu, tmp_path
     imgs = torch.from_numpy(np.stack([synth.train_image(50_000 + i) for i in range(16)])).cuda()
     ref, _ = ws.plain_segment(imgs, 10)
     grid1, _ = ws.plain_segment(imgs, 0)
-    warm1, _ = ws.warm_start_segment(net, imgs, 1)
+    warm1, _ = ws.warm_start_segment(net, imgs, 0)
     a_grid, a_warm = ws.agreement(grid1, ref), ws.agreement(warm1, ref)
     print(f"agreement with 10 iterations after one assignment: grid start {a_grid:.4f}, "
           f"network start {a_warm:.4f} (gain {a_warm - a_grid:+.4f})")

@@ -115,3 +115,119 @@ def test_grid_distances_uniform_image():
     assert np.isinf(D[0, 0, [0, 1, 2, 3, 6]]).all()
     x = net.input_channels(lab, 4, 8.0)
     assert x[0, 0, 5 + 0] == 2.0 and x[0, 0, 5 + 4] == pytest.approx(2 * np.sqrt(4.5) / 100)
+
+
+# --- hand-worked forward cases (values below are worked out by hand) ------------
+
+def _taps(cin, cout, centre, left=None, right=None, other=0.0):
+    """A [3,3,cin,cout] kernel: `centre`, `left` (input x-1) and `right`
+    (input x+1) taps of the middle kernel row as {(ci, co): value}; every
+    other tap set to `other`."""
+    w = np.full((3, 3, cin, cout), other)
+    w[1, :, :, :] = 0.0 if other == 0.0 else other
+    w[1, 0] = 0.0
+    w[1, 1] = 0.0
+    w[1, 2] = 0.0
+    for dx, taps in ((0, left), (1, centre), (2, right)):
+        for (ci, co), v in (taps or {}).items():
+            w[1, dx, ci, co] = v
+    return w
+
+
+def test_forward_two_layers_relu_between_not_on_logits():
+    """A 1x2 image through two layers. Layer 1 (1 -> 2 channels):
+    z1 = (x[p] + 0.5 x[p+1] - 1.5, -x[p] + 0.5); with x = (1, 2):
+    z1(0) = (1 + 1 - 1.5, -1 + 0.5) = (0.5, -0.5), z1(1) = (2 + 0 - 1.5, -2 + 0.5) = (0.5, -1.5),
+    ReLU -> a1(0) = a1(1) = (0.5, 0). Layer 2 (2 -> 2): logit0 = a1_0[p] + 3 a1_1[p]
+    + 2 a1_0[p-1] + 0.25, logit1 = -2 a1_0[p]:
+    logits(0) = (0.5 + 0 + 0 + 0.25, -1) = (0.75, -1), logits(1) = (0.5 + 0 + 1 + 0.25, -1) = (1.75, -1).
+    Without the ReLU logit0(0) would be 0.5 - 1.5 + 0.25 = -0.75; a ReLU on
+    the logits would make logit1 zero."""
+    x0 = np.array([[[1.0], [2.0]]])
+    w1 = _taps(1, 2, centre={(0, 0): 1.0, (0, 1): -1.0}, right={(0, 0): 0.5})
+    w2 = _taps(2, 2, centre={(0, 0): 1.0, (1, 0): 3.0, (0, 1): -2.0}, left={(0, 0): 2.0})
+    params = [(w1, np.array([-1.5, 0.5])), (w2, np.array([0.25, 0.0]))]
+    for bf16 in (False, True):  # every value here is a bfloat16 number
+        logits, _ = net.forward(x0, params, bf16=bf16)
+        np.testing.assert_array_equal(logits, [[[0.75, -1.0], [1.75, -1.0]]])
+
+
+def test_forward_four_layers_relu_after_each_hidden_layer():
+    """A 1x1 image (only centre taps see data: the other taps, set to 7, see
+    the zero padding) through four layers 1 -> 2 -> 2 -> 2 -> 1:
+    z1 = (a0, -a0) = (1, -1) -> a1 = (1, 0);
+    z2 = (a1_0 + a1_1, a1_0 + 2 a1_1 - 3) = (1, -2) -> a2 = (1, 0);
+    z3 = (a2_0 + a2_1 - 0.5, -a2_0) = (0.5, -1) -> a3 = (0.5, 0);
+    logit = a3_0 + a3_1 - 1 = -0.5.
+    Dropping the ReLU after layer 1, 2 or 3 gives -1, -1 or -1.5; a ReLU on
+    the logit gives 0."""
+    x0 = np.array([[[1.0]]])
+    params = [
+        (_taps(1, 2, centre={(0, 0): 1.0, (0, 1): -1.0}, other=7.0), np.array([0.0, 0.0])),
+        (_taps(2, 2, centre={(0, 0): 1.0, (1, 0): 1.0, (0, 1): 1.0, (1, 1): 2.0}, other=7.0), np.array([0.0, -3.0])),
+        (_taps(2, 2, centre={(0, 0): 1.0, (1, 0): 1.0, (0, 1): -1.0}, other=7.0), np.array([-0.5, 0.0])),
+        (_taps(2, 1, centre={(0, 0): 1.0, (1, 0): 1.0}, other=7.0), np.array([-1.0])),
+    ]
+    for bf16 in (False, True):
+        logits, _ = net.forward(x0, params, bf16=bf16)
+        assert logits.shape == (1, 1, 1) and logits[0, 0, 0] == -0.5
+
+
+def test_forward_bf16_rounding_points():
+    """Where the precision model rounds to bfloat16 (8 significant bits; the
+    spacing above 1 is 2^-7): the input channels, the weights and the
+    activations stored between layers, but neither the biases nor the
+    logits. v = 1 + 3*2^-9 = 1.005859375 lies 3/4 of a spacing above 1, so it
+    rounds to 1 + 2^-7 = 1.0078125. On a 1x1 image with one channel:
+      input v, weight 1, bias 0          -> logit 1.0078125 (input rounded)
+      input 1, weight v, bias 0          -> logit 1.0078125 (weight rounded)
+      input 1, weight 1, bias 3*2^-9, then a second layer of weight 1
+                                         -> logit 1.0078125 (activation rounded)
+      input 1, weight 1, bias 3*2^-9     -> logit 1.005859375 (bias, logit kept)"""
+    v = 1.0 + 3 * 2.0 ** -9
+    one = lambda w: _taps(1, 1, centre={(0, 0): w})  # noqa: E731
+    cases = [
+        (v, [(one(1.0), np.array([0.0]))], 1.0078125),
+        (1.0, [(one(v), np.array([0.0]))], 1.0078125),
+        (1.0, [(one(1.0), np.array([3 * 2.0 ** -9])), (one(1.0), np.array([0.0]))], 1.0078125),
+        (1.0, [(one(1.0), np.array([3 * 2.0 ** -9]))], 1.005859375),
+    ]
+    for x, params, want in cases:
+        got, _ = net.forward(np.array([[[x]]]), params, bf16=True)
+        assert got[0, 0, 0] == want
+        exact, _ = net.forward(np.array([[[x]]]), params, bf16=False)
+        assert exact[0, 0, 0] == pytest.approx(1.005859375, abs=1e-15)
+
+
+def test_backward_bf16_gradient_rounding_points():
+    """The stored dL/dz of the bf16_grad model, on a 1x2 image with S = 1
+    (two cells): pixel 0 may take slots 4 (own) and 5 (right), pixel 1 slots
+    3 (left) and 4. Layer 1 gives hidden channel 0 the constant activation 1
+    (bias 1); layer 2 has weight 1.25 from it to slot 5 (centre tap) and
+    biases ln 2 on slot 3 and ln 2 - 1.25 on slot 5, so the logits are ln 2
+    on slots 3 and 5 and 0 elsewhere. Targets: slot 4 at both pixels.
+    Softmax: pixel 0 has p4 = 1/3, p5 = 2/3; pixel 1 has p3 = 2/3, p4 = 1/3.
+    Mean-loss gradients (two pixels): dz4 = (1/3 - 1)/2 = -1/3, dz5 = dz3 = 1/3.
+    1/3 in bfloat16 is 0.333984375 (1.0101011b x 2^-2), so the last layer's
+    bias gradient is (1/3, -2/3, 1/3) exactly and (0.333984375, -0.66796875,
+    0.333984375) with rounding. Hidden gradient at pixel 0: 1.25 dz5 =
+    0.41666.. exactly; 1.25 x 0.333984375 = 0.41748046875 rounds to
+    0.41796875 (1.671875 x 2^-2); pixel 1 has none (p5 = 0 there). So the
+    first layer's bias gradient is 0.41666.. / 0.41796875."""
+    x0 = np.zeros((1, 2, 1))
+    w1 = _taps(1, 1, centre={})
+    w2 = _taps(1, net.N_SLOTS, centre={(0, 5): 1.25})
+    b2 = np.zeros(net.N_SLOTS)
+    b2[3] = np.log(2.0)
+    b2[5] = np.log(2.0) - 1.25
+    params = [(w1, np.array([1.0])), (w2, b2)]
+    valid = net.slot_mask(1, 2, 1)
+    assert valid[0, 0].tolist() == [False] * 4 + [True, True] + [False] * 3
+    assert valid[0, 1].tolist() == [False] * 3 + [True, True] + [False] * 4
+    target = np.array([[4, 4]])
+    _, g = net.backward(x0, params, target, valid, bf16=True, bf16_grad=False)
+    np.testing.assert_allclose(g[1][1][3:6], [1 / 3, -2 / 3, 1 / 3], rtol=1e-12)
+    assert g[0][1][0] == pytest.approx(1.25 / 3, rel=1e-12)
+    _, g = net.backward(x0, params, target, valid, bf16=True, bf16_grad=True)
+    np.testing.assert_array_equal(g[1][1][3:6], [0.333984375, -0.66796875, 0.333984375])
+    assert g[0][1][0] == 0.41796875
