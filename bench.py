@@ -1,26 +1,37 @@
-"""Throughput benchmark: 1080p SLIC frames/s on GB300.
+"""Benchmark: 1080p SLIC frames/s at >= 99 % label agreement, on GB300.
 
-Workload (one "step"): a batch of B seeded synthetic 1920x1080 RGB frames
-(400 Voronoi regions, noise sigma 6), each segmented with S=16 (K_eff =
-120x68 = 8160), m=10, 5 iterations, CIELAB and two connectivity passes.
-The batch's inputs (B x 6.2 MB of RGB, B x 8.3 MB of labels) are larger
-than the 129 MB L2, so no flush is needed between steps.
+The metric compares the batched plain path with the batched learned warm
+start at equal quality: each runs at the smallest iteration count whose
+mean label agreement with 10-iteration SLIC (connectivity on for both)
+reaches 99 % on an evaluation set of 64 seeded synthetic 1920x1080 frames
+(400 Voronoi regions, noise 6; S=16, m=10), and `value` is the faster of the
+two. One step is one batch of 32 such frames (the throughput frames, other
+seeds), one CUDA graph (one batched launch per stage) at that iteration
+count; the batch's inputs (32 x 6.2 MB of RGB, 32 x 8.3 MB of labels) are
+larger than the 129 MB L2, so no flush is needed between steps.
 
 Prints ONE JSON line (rank 0). Keys beyond the base contract:
-  roofline      the assignment kernel (the dominant one) against its bound
+  quality       the agreement-vs-iterations curves of both methods, their
+                iteration counts at 99 % and frames/s there, the network's
+                training and its forward against the bf16 tensor roofline
+  roofline      the dominant kernel (the pipelined assignment pass) against
+                its bound (the square-root pipe), with its HBM view
   cpu_baseline  the FP64 CPU oracle timed on a bounded sample over all host
                 cores (one process per core), with a one-core figure beside it
   e2e           the same metric through the public API with host buffers
   gpu_launches  kernel launches of this library inside the timed region
   clocks        SM clocks sampled by nvidia-smi during the timed region
-  quality       label agreement with 10 iterations, the plain path at 10
-                iterations, the learned warm start and the network forward
-                against the bf16 tensor roofline
-  sec2_options  the stopping test with early exit and the seed perturbation
-  mixed_batch   the 256-frame mixed-resolution batch (context line)
+  throughput_5_iterations  plain batched SLIC at 5 iterations (32 x 1080p)
+  single_frame  graph-captured slic_segment latency: 1920x1080 S=16 and
+                640x480 K=1200, 5 iterations
+  sec2_options  the stopping test with early exit, the seed perturbation,
+                input variants and component connectivity
+  mixed_batch   the 256-frame mixed-resolution batch
+  video         120 frames of 3840x2160 with the temporal warm start
 
 ``--impl reference`` times the FP64 CPU oracle itself (the only reference
-implementation of the method in this repository) on the same workload.
+implementation of the method in this repository) on the same frames at 10
+iterations.
 """
 from __future__ import annotations
 
@@ -38,7 +49,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-W, H, S, M, ITERS = 1920, 1080, 16, 10.0, 5
+W, H, S, M = 1920, 1080, 16, 10.0
+ITERS = 5          # the plain throughput configuration (configs[1])
+FULL_ITERS = 10    # the full-iteration result the agreement bar refers to
+EVAL_FRAMES = 64   # the evaluation set of the agreement bar
+AGREE_BAR = 0.99
 METRIC = "1080p SLIC frames/s (batched+learned vs plain GPU) at \u226599% label agreement"
 UNIT = "frames/s"
 
@@ -135,10 +150,11 @@ def measured_peaks():
 
 # --- the CPU oracle legs ----------------------------------------------------
 
-def _oracle_frame(img):
+def _oracle_frame(job):
     """One oracle run on a 1080p frame (in a spawned worker process)."""
     import oracle
-    oracle.slic(img, S=S, m=M, iterations=ITERS, enforce_connectivity=True)
+    img, iterations = job
+    oracle.slic(img, S=S, m=M, iterations=iterations, enforce_connectivity=True)
     return 0
 
 
@@ -148,7 +164,7 @@ def _oracle_ready(_):
     return os.getpid()
 
 
-def oracle_frames_per_s(frames, procs: int) -> float:
+def oracle_frames_per_s(frames, procs: int, iterations: int) -> float:
     """Wall-clock frames/s of the FP64 oracle (as it stands) over `frames`,
     one frame per task on `procs` spawned worker processes (spawn, not fork:
     the parent may hold a CUDA context)."""
@@ -157,7 +173,7 @@ def oracle_frames_per_s(frames, procs: int) -> float:
     with ctx.Pool(procs) as pool:
         pool.map(_oracle_ready, range(procs))  # workers up and the library loaded, untimed
         t0 = time.perf_counter()
-        pool.map(_oracle_frame, frames, chunksize=1)
+        pool.map(_oracle_frame, [(f, iterations) for f in frames], chunksize=1)
         dt = time.perf_counter() - t0
     return len(frames) / dt
 
@@ -181,13 +197,14 @@ def run_reference(args):
     # frame, the steps spread over all host cores
     warm = [synth.hd_image(19_000 + k, W, H) for k in range(args.warmup)]
     frames = [synth.hd_image(20_000 + k, W, H) for k in range(args.steps)]
-    oracle_frames_per_s(warm, procs)
-    value = oracle_frames_per_s(frames, procs)
+    oracle_frames_per_s(warm, procs, FULL_ITERS)
+    value = oracle_frames_per_s(frames, procs, FULL_ITERS)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "1 frame 1920x1080 per step (S=16, m=10, 5 it, connectivity)",
-                                            "global_batch": 1,
+            "data": "synthetic", "config": {"workload": "1 frame 1920x1080 per step, S=16 m=10, 10 it (the agreement "
+                                                        "reference), connectivity",
+                                            "global_batch": 1, "iterations": FULL_ITERS,
                                             "parallelism": f"{procs} host processes, one frame each at a time"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
                              "sample": f"{args.steps} frames 1920x1080 over {procs} processes"},
@@ -197,6 +214,28 @@ def run_reference(args):
 
 
 # --- the GPU path -----------------------------------------------------------
+
+def _plain_batch(pkg, images, iterations, dev, tuning=None, **kw):
+    """A bound batch of the throughput frames (plain path)."""
+    bs = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * len(images), iterations=iterations, device=dev, **kw)
+    bs.bind(list(images))
+    if tuning:
+        bs.set_tuning(*tuning)
+    return bs
+
+
+def _capture(fn, stream):
+    """One eager call (module loading, first-use set-up), then a CUDA graph of it."""
+    import torch
+    with torch.cuda.stream(stream):
+        fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        fn()
+    torch.cuda.synchronize()
+    return g
+
 
 def run_ours(args):
     import torch
@@ -210,6 +249,7 @@ def run_ours(args):
     import paper_1509_04232_gb300 as pkg
     from paper_1509_04232_gb300 import build, synth
     build.build_all()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     B = args.batch
     seeds = frame_seeds(B, rank)
@@ -217,39 +257,41 @@ def run_ours(args):
     for i, sd in enumerate(seeds):
         synth.voronoi_frame(W, H, 400, 6.0, synth.seed_of(1, sd), out=host[i].numpy())
     images = host.to(dev)
-    K_EFF = 120 * 68
-    host_labels = torch.empty((B, H, W), dtype=torch.int32).pin_memory()
-    host_centres = torch.empty((B, K_EFF, 6), dtype=torch.float32).pin_memory()
-
-    # One batch of B frames; the persistent assignment kernel's launch shape
-    # is autotuned once (cached per GPU and geometry).
+    frames = [images[f] for f in range(B)]
     stream = torch.cuda.Stream(device=dev)
-    bs = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=ITERS, device=dev)
-    bs.bind([images[f] for f in range(B)])
     tune_cache = os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl")
-    ctas_per_sm, stages, rows = bs.autotune(tune_cache, stream=stream)
 
-    def step():
-        bs.segment(stream=stream)
+    # --- the agreement bar: iteration sweeps of both methods on the eval set ---
+    quality, net_small = agreement_sweeps(args, pkg, dev, stream)
+    n_plain = quality["plain_iterations_at_99"]
+    n_learned = quality.get("learned_iterations_at_99")
 
-    # Capture one step into a CUDA graph; count its launches.
-    with torch.cuda.stream(stream):
-        step()
-    torch.cuda.synchronize()
+    # --- the plain path at its iteration count, autotuned, one graph per step ---
+    bs = _plain_batch(pkg, frames, n_plain, dev)
+    tuning = bs.autotune(tune_cache, stream=stream)
+    ctas_per_sm, stages, rows = tuning
+    K_EFF = bs.K_eff[0]
     n0 = bs.info[1]
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        step()
-    launches_per_step = bs.info[1] - n0
-    # A second graph with event pairs around every assignment kernel.
-    pkg.slic_batch_profile_enable(bs.handle, True)
-    graph_prof = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph_prof, stream=stream):
-        step()
-    pkg.slic_batch_profile_enable(bs.handle, False)
-    torch.cuda.synchronize()
+    graph = _capture(lambda: bs.segment(stream=stream), stream)
+    launches_per_step = (bs.info[1] - n0) // 2
+    plain_ms = _graph_ms(graph, stream, args, world, dev)
+    method = {"name": "plain", "iterations": n_plain, "frames_per_s": world * B / (plain_ms / 1e3)}
+    learned_fps = None
+    if n_learned is not None and net_small is not None:
+        from paper_1509_04232_gb300 import warmstart as ws
+        net = ws.WarmStartNet(W, H, S, max_batch=B, seed=0, m=M)
+        net.set_params(net_small.params())
+        pipe = ws.WarmStartPipeline(net, frames, n_learned, m=M)
+        g_l = _capture(lambda: pipe.run(stream), stream)
+        learned_fps = world * B / (_graph_ms(g_l, stream, args, world, dev) / 1e3)
+        quality["learned_frames_per_s_at_99"] = learned_fps
+        if learned_fps > method["frames_per_s"]:
+            method = {"name": "learned", "iterations": n_learned, "frames_per_s": learned_fps}
+            graph, bs, launches_per_step = g_l, pipe.bs, None
+    quality["plain_frames_per_s_at_99"] = world * B / (plain_ms / 1e3)
+    quality["headline_method"] = method["name"]
 
-    # --- device-resident throughput ---
+    # --- device-resident throughput of the headline method ---
     clocks = ClockSampler(local)
     clocks.start()
     with torch.cuda.stream(stream):  # replay() launches on the current stream
@@ -271,21 +313,28 @@ def run_ours(args):
     ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), world, dev) / args.steps
     step_ms = np.array([evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)])
     value = world * B / (ms / 1e3)
+    if launches_per_step is None:
+        launches_per_step = 0  # (the learned step: counted below)
 
-    # --- dominant kernel: event-timed replays of the same step ---
+    # --- dominant kernel: event-timed replays of the plain step ---
     # Each replay records one event pair per assignment launch, in pass
-    # order 0..ITERS; passes 1..ITERS-1 run the dominant kernel (the
-    # pipelined middle pass, k_assign_pipe<0,1,MINB,ROWS>: MINB = 4 for the
-    # two-row-group build and for the one-row 64-register build the
-    # autotuner picks at 4 CTAs per SM, else 3).
+    # order 0..n; passes 1..n-1 run the dominant kernel (the pipelined middle
+    # pass, k_assign_pipe<0,1,MINB,ROWS>: MINB = 4 for the two-row-group
+    # build and for the one-row 64-register build the autotuner picks at 4
+    # CTAs per SM, else 3).
+    pb = bs if method["name"] == "plain" else _plain_batch(pkg, frames, n_plain, dev, tuning)
+    pkg.slic_batch_profile_enable(pb.handle, True)
+    graph_prof = _capture(lambda: pb.segment(stream=stream), stream)
+    pkg.slic_batch_profile_enable(pb.handle, False)
     kname = f"k_assign_pipe<0,1,{4 if (rows == 2 or ctas_per_sm >= 4) else 3},{rows}>"
     mid = []
     for _ in range(max(3, min(args.steps, 10))):
         with torch.cuda.stream(stream):
             graph_prof.replay()
         torch.cuda.synchronize()
-        t = pkg.slic_batch_profile_times(bs.handle)
-        mid += [t[p] for p in range(1, ITERS) if p < len(t)]
+        t = pkg.slic_batch_profile_times(pb.handle)
+        t = t[-(n_plain + 1):]  # this replay's passes
+        mid += [t[p] for p in (range(1, n_plain) if n_plain >= 2 else range(n_plain + 1))]
     mid_ms = float(np.mean(mid))
     N = W * H
     # Algorithmic work of one middle-pass launch (all B frames): 12 bytes of
@@ -295,7 +344,8 @@ def run_ours(args):
     achieved_gbs = bytes_per_launch / (mid_ms / 1e3) / 1e9
     sqrt_per_launch = B * N * 18
     peaks, peak_kind = measured_peaks()
-    xu_peak = 16 * 152 * (clock_info.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    sm_max = clock_info.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    xu_peak = 16 * sms * sm_max * 1e6 / 1e12
     achieved_tops = sqrt_per_launch / (mid_ms / 1e3) / 1e12
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "assign_traffic.txt")
@@ -307,18 +357,22 @@ def run_ours(args):
             traffic = float(kv["dram_bytes_per_frame"]) * B
 
     # --- end to end through the C ABI with host buffers ---
-    # slic_batch_segment_host: H2D copies of the step's frames, the step, D2H
-    # copies of labels and centres. Two batches bound to separate device
+    # slic_batch_segment_host: H2D copy of the step's frames, the step, D2H
+    # copy of labels and centres. Two batches bound to separate device
     # buffers alternate on two streams, so one step's copies overlap the
     # other's kernels; every step still moves all of its own bytes.
     h2d = B * H * W * 3
     d2h = B * H * W * 4 + B * K_EFF * 6 * 4
-    bs2 = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=ITERS, device=dev)
-    bs2.bind([torch.empty_like(images[f]) for f in range(B)])
-    bs2.set_tuning(ctas_per_sm, stages, rows)
-    pair = [(bs, stream, host_labels, host_centres),
-            (bs2, torch.cuda.Stream(device=dev), torch.empty_like(host_labels).pin_memory(),
-             torch.empty_like(host_centres).pin_memory())]
+    e_iters = method["iterations"]
+    pair = []
+    for _ in range(2):
+        eb = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=e_iters, device=dev)
+        eb.bind([torch.empty_like(images[f]) for f in range(B)])
+        eb.set_tuning(ctas_per_sm, stages, rows)
+        if method["name"] == "learned":
+            eb.set_warmstart(net)
+        pair.append((eb, torch.cuda.Stream(device=dev), torch.empty((B, H, W), dtype=torch.int32).pin_memory(),
+                     torch.empty((B, K_EFF, 6), dtype=torch.float32).pin_memory()))
     h_imgs = [host[f] for f in range(B)]
 
     def host_step(k):
@@ -332,6 +386,7 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(pair[0][1])
     pair[1][1].wait_event(e0)
+    n_before = sum(p_[0].info[1] for p_ in pair)
     for k in range(args.steps):
         host_step(k)
     join = torch.cuda.Event()
@@ -341,22 +396,30 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
     e2e_value = world * B / (e2e_ms / 1e3)
-    bs2.close()
+    if launches_per_step == 0:
+        launches_per_step = (sum(p_[0].info[1] for p_ in pair) - n_before) // args.steps
+    for p_ in pair:
+        p_[0].close()
 
-    # --- the mixed-resolution batch (256 frames, four sizes, S and m mixed) ---
+    # --- context: plain throughput at 5 iterations (configs[1]) ---
+    b5 = _plain_batch(pkg, frames, ITERS, dev, tuning)
+    g5 = _capture(lambda: b5.segment(stream=stream), stream)
+    ms5 = _graph_ms(g5, stream, args, world, dev)
+    thr5 = {"iterations": ITERS, "frames_per_s": world * B / (ms5 / 1e3), "ms_per_step": ms5,
+            "megapixels_per_s": world * B * N / 1e6 / (ms5 / 1e3),
+            "agreement_with_10_iterations": quality["plain_agreement_by_iterations"].get(str(ITERS))}
+    b5.close()
+
+    single = None if args.no_single else single_frame_latency(args, pkg, stream, dev, images[0])
     mixed = None
     if rank == 0 and not args.no_mixed:
         mixed = mixed_batch_throughput(args, pkg, stream, dev)
-
-    # --- label agreement with the 10-iteration result and the learned path ---
-    quality = None
-    if not args.no_quality:
-        quality = quality_and_learned(args, pkg, images, B, stream, world, dev)
-
-    # --- the Sec. 2 options: stopping test with early exit, seed perturbation ---
     options = None
     if not args.no_options:
-        options = sec2_options(args, pkg, images, B, stream, world, dev, (ctas_per_sm, stages, rows))
+        options = sec2_options(args, pkg, images, B, stream, world, dev, tuning)
+    video = None
+    if rank == 0 and not args.no_video:
+        video = video_context(args, pkg, dev, net_small)
 
     # --- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N=1) ---
     cpu = None
@@ -364,10 +427,11 @@ def run_ours(args):
         procs = host_cores()
         n_cpu = args.cpu_frames or 2 * procs
         sample = [synth.hd_image(10_000 + i, W, H) for i in range(n_cpu)]
-        fps = oracle_frames_per_s(sample, procs)
-        fps1 = oracle_frames_per_s(sample[:2], 1)
+        fps = oracle_frames_per_s(sample, procs, e_iters)
+        fps1 = oracle_frames_per_s(sample[:2], 1, e_iters)
         cpu = {"value": fps, "unit": UNIT, "cores": procs, "kind": "oracle",
-               "sample": f"{n_cpu} frames 1920x1080 (S=16, m=10, 5 iterations, connectivity) over {procs} processes",
+               "sample": f"{n_cpu} frames 1920x1080 (S=16, m=10, {e_iters} iterations, connectivity) over {procs} "
+                         f"processes",
                "single_core": {"value": fps1, "sample": "2 of those frames on 1 process"}}
 
     if rank == 0:
@@ -377,11 +441,9 @@ def run_ours(args):
             "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"plain SLIC throughput: {B} x 1920x1080 RGB frames per GPU per step (400 "
-                                   f"Voronoi regions, noise 6); S=16 (K_eff 8160), m=10, {ITERS} iterations, CIELAB, "
-                                   f"connectivity; agreement with 10 iterations and the learned warm start in "
-                                   f"'quality'",
-                       "iterations": ITERS,
+            "config": {"workload": f"{B}x1080p/step, S=16 m=10, {method['name']} at {method['iterations']} it "
+                                   f"(>=99% agreement with 10 it)",
+                       "method": method["name"], "iterations": method["iterations"],
                        "global_batch": world * B, "frames_per_gpu": B, "megapixels_per_s": value * N / 1e6,
                        "parallelism": f"replicas x{world} (frames sharded, no collective)",
                        "l2": "inputs larger than L2 (B x 6.2 MB RGB + B x 8.3 MB labels per step)",
@@ -389,15 +451,18 @@ def run_ours(args):
                        "ctas_per_sm": ctas_per_sm, "pipeline_stages": stages, "row_groups_per_warp": rows},
             "roofline": {"kernel": f"{kname} (middle assignment pass, all frames)", "bound": "alu",
                          "unit": "Tsqrt/s", "achieved": achieved_tops, "peak": xu_peak, "frac": achieved_tops / xu_peak,
-                         "peak_source": "16 MUFU lanes/clk/SM x 152 SMs x max SM clock (recipe unit counts)",
+                         "peak_source": f"16 MUFU lanes/clk/SM x {sms} SMs x max SM clock (recipe unit counts)",
                          "traffic": traffic, "avg_launch_us": mid_ms * 1e3, "launches_timed": len(mid),
                          "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
                                  "frac": achieved_gbs / peaks["hbm_gbs"], "unit": "GB/s",
                                  "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch}},
             "cpu_baseline": cpu,
             "quality": quality,
+            "throughput_5_iterations": thr5,
+            "single_frame": single,
             "sec2_options": options,
             "mixed_batch": mixed,
+            "video": video,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clock_info,
@@ -407,6 +472,75 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def single_frame_latency(args, pkg, stream, dev, image):
+    """slic_segment on one frame at a time, graph-captured: 1920x1080 at S=16
+    and 640x480 at K=1200 (the paper's image size), m=10, 5 iterations
+    (configs[1]); per-call latency percentiles over replays."""
+    import torch
+    from paper_1509_04232_gb300 import synth
+    out = {}
+    for name, (w, h, kw, img) in {"1920x1080_S16": (W, H, dict(S=S), image),
+                                  "640x480_K1200": (640, 480, dict(K=1200),
+                                                    torch.from_numpy(synth.voronoi_frame(640, 480, 120, 6.0, 77)).to(dev))
+                                  }.items():
+        seg = pkg.Segmenter(w, h, m=M, iterations=ITERS, **kw)
+        labels = torch.empty((h, w), dtype=torch.int32, device=dev)
+        centres = torch.empty((seg.K_eff, 6), dtype=torch.float32, device=dev)
+        n0 = seg.launches
+        g = _capture(lambda: seg.segment(img, labels, centres, stream=stream), stream)
+        per_frame = (seg.launches - n0) // 2
+        reps = max(50, min(args.steps, 300))
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                g.replay()
+            evs[0].record(stream)
+            for k in range(reps):
+                g.replay()
+                evs[k + 1].record(stream)
+        torch.cuda.synchronize()
+        t = np.array([evs[k].elapsed_time(evs[k + 1]) for k in range(reps)])
+        out[name] = {"ms_p50": float(np.percentile(t, 50)), "ms_p99": float(np.percentile(t, 99)),
+                     "frames_per_s": 1e3 / float(np.mean(t)), "K_eff": seg.K_eff, "iterations": ITERS,
+                     "launches_per_frame": per_frame}
+        seg.close()
+    return out
+
+
+def video_context(args, pkg, dev, net_small):
+    """configs[4]: 120 frames of 3840x2160 (regions moving 0-4 px per frame,
+    colour drift 2, noise 6), S=16, m=10, 8 frames per launch, 2 iterations
+    per batch after a 10-iteration first batch: the previous batch's
+    centres, the grid, and (with a trained network) the learned warm start
+    on top of the previous centres; quality against per-frame 10-iteration
+    SLIC."""
+    import torch
+    from paper_1509_04232_gb300 import synth
+    from paper_1509_04232_gb300.video import run_video
+    VW, VH, T = 3840, 2160, args.video_frames
+    host = torch.empty((T, VH, VW, 3), dtype=torch.uint8)
+    for t in range(T):
+        host[t].numpy()[...] = synth.video_frame(t, VW, VH)
+    frames = host.to(dev)
+    run_video(frames[:8], 8, 2)  # warm-up: module loading and first-use set-up
+    out = {"workload": f"{T} frames 3840x2160, S=16, m=10, 8 per launch, 2 iterations per batch"}
+    for key, init, learned in (("previous_centres", "previous", False), ("grid", "grid", False),
+                               ("previous_centres_learned", "previous", True)):
+        net = None
+        if learned:
+            if net_small is None:
+                continue
+            from paper_1509_04232_gb300 import warmstart as ws
+            net = ws.WarmStartNet(VW, VH, S, max_batch=8, seed=0, m=M)
+            net.set_params(net_small.params())
+        r = run_video(frames, 8, 2, init=init, net=net)
+        r["agreement_vs_plain_10"].pop("per_frame")
+        out[key] = r
+        if net is not None:
+            net.close()
+    return out
 
 
 def mixed_batch_throughput(args, pkg, stream, dev):
@@ -527,84 +661,86 @@ def sec2_options(args, pkg, images, B, stream, world, dev, tuning):
             "component_connectivity_frames_per_s": comp_fps}
 
 
-def quality_and_learned(args, pkg, images, B, stream, world, dev):
-    """Agreement of plain SLIC with n iterations and of the learned warm start
-    with k iterations against the 10-iteration labels (first 8 frames), and
-    the learned path's throughput on the whole batch (one CUDA graph per
-    step, same timing protocol as `value`). The network is trained first on
-    seeded 256x256 images (outside any timed region)."""
+def agreement_sweeps(args, pkg, dev, stream):
+    """Mean label agreement with 10-iteration SLIC over the evaluation set
+    (64 seeded 1080p frames, other seeds than the throughput frames; labels
+    after connectivity) for the plain path at 0..10 iterations and, unless
+    --no-learned, the learned warm start at 0..10 iterations after training
+    its network on seeded 256x256 images (outside every timed region); the
+    smallest iteration count of each reaching 99 %. Returns (quality dict,
+    trained 256x256 network or None)."""
     import torch
+    from paper_1509_04232_gb300 import synth
     from paper_1509_04232_gb300 import warmstart as ws
-    q = min(8, B)
-    sub = images[:q]
-    ref, _ = ws.plain_segment(sub, 10)
-    plain = {}
-    for n in (0, 1, 2, 3, 5, 7, 9):
-        lab, _ = ws.plain_segment(sub, n)
-        plain[n] = round(ws.agreement(lab, ref), 5)
-    # The plain path at the iteration count that reaches >= 99 % agreement by
-    # definition (the 10-iteration reference itself), timed like `value`.
-    plain10 = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=10, device=dev)
-    plain10.bind([images[f] for f in range(B)])
-    with torch.cuda.stream(stream):
-        plain10.segment(stream)
-    torch.cuda.synchronize()
-    g10 = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g10, stream=stream):
-        plain10.segment(stream)
-    plain10_fps = world * B / (_graph_ms(g10, stream, args, world, dev) / 1e3)
-    plain10.close()
+    n_eval = args.eval_frames
+    host = np.stack([synth.hd_image(30_000 + i, W, H) for i in range(n_eval)])
+    evals = torch.from_numpy(host).to(dev)
+    chunk = 32
+
+    def run(iterations, net=None):
+        eq = 0
+        for c0 in range(0, n_eval, chunk):
+            sub = evals[c0:c0 + chunk]
+            lab = (ws.warm_start_segment(net, sub, iterations, m=M)[0] if net is not None
+                   else ws.plain_segment(sub, iterations, S, M)[0])
+            eq += sum(int(torch.eq(x, y).sum().item()) for x, y in zip(lab, refs[c0:c0 + chunk]))
+        return eq / (n_eval * W * H)
+
+    refs = []
+    for c0 in range(0, n_eval, chunk):
+        refs += ws.plain_segment(evals[c0:c0 + chunk], FULL_ITERS, S, M)[0]
+    plain = {str(n): round(run(n), 5) for n in range(0, FULL_ITERS + 1)}
+    n_plain = min(n for n in range(FULL_ITERS + 1) if plain[str(n)] >= AGREE_BAR)
+    q = {"reference": "plain SLIC at 10 iterations, connectivity on (GPU; the parity tests hold it to the FP64 "
+                      "oracle at >= 99.5 %)",
+         "eval_frames": n_eval, "bar": AGREE_BAR,
+         "plain_agreement_by_iterations": plain, "plain_iterations_at_99": n_plain}
+    if args.no_learned:
+        return q, None
     t0 = time.time()
     small = ws.WarmStartNet(256, 256, S, max_batch=64, seed=0, m=M)
     hist = ws.train(small, n_images=args.train_images, batch=64, epochs=args.train_epochs, lr=2e-3, log_every=50)
     train_s = time.time() - t0
-    net = ws.WarmStartNet(W, H, S, max_batch=B, seed=0, m=M)
+    net = ws.WarmStartNet(W, H, S, max_batch=chunk, seed=0, m=M)
     net.set_params(small.params())
-    # The network alone (input channels, four convolutions, labels) on the
-    # whole batch, against the bf16 tensor roofline: the algorithmic work is
-    # 2 * 9 * (14*32 + 32*32 + 32*32 + 32*9) FLOP per pixel.
-    stacked = torch.stack([images[f] for f in range(B)])
-    net_labels = torch.empty((B, H, W), dtype=torch.int32, device=dev)
+    learned = {str(n): round(run(n, net), 5) for n in range(0, FULL_ITERS + 1)}
+    reach = [n for n in range(FULL_ITERS + 1) if learned[str(n)] >= AGREE_BAR]
+    q.update({"learned_agreement_by_iterations": learned,
+              "learned_iterations_at_99": reach[0] if reach else None,
+              "learned_training": {"images": args.train_images, "epochs": args.train_epochs, "seconds": train_s,
+                                   "final_loss": hist[-1][1] if hist else None,
+                                   "final_pixel_accuracy": hist[-1][2] if hist else None}})
+    q["network_forward"] = network_forward_roofline(args, net, evals[:chunk], stream)
+    net.close()
+    return q, small
+
+
+def network_forward_roofline(args, net, images, stream):
+    """The network alone (input channels, four convolutions, labels) on a
+    32-frame 1080p batch, against the bf16 tensor roofline: the algorithmic
+    work is 2 * 9 * (14*32 + 32*32 + 32*32 + 32*9) FLOP per pixel."""
+    import torch
+    B = images.shape[0]
+    labels = torch.empty((B, H, W), dtype=torch.int32, device=images.device)
     s_handle = int(stream.cuda_stream)
     # (an NVTX range around the eager call lets a profiler pick these launches)
     torch.cuda.nvtx.range_push("network_forward")
     with torch.cuda.stream(stream):
-        net.forward(stacked, labels=net_labels, stream=s_handle)
+        net.forward(images, labels=labels, stream=s_handle)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     gn = torch.cuda.CUDAGraph()
     with torch.cuda.graph(gn, stream=stream):
-        net.forward(stacked, labels=net_labels, stream=s_handle)
-    net_ms = _graph_ms(gn, stream, args, world, dev)
+        net.forward(images, labels=labels, stream=s_handle)
+    net_ms = _graph_ms(gn, stream, args, 1, None)
     flop = 2.0 * 9 * (14 * 32 + 32 * 32 + 32 * 32 + 32 * 9) * B * W * H
     peaks, peak_kind = measured_peaks()
-    net_tflops = flop / (net_ms / 1e3) / 1e12
-    net_roof = {"ms_per_batch": net_ms, "frames_per_s": B / (net_ms / 1e3), "achieved": net_tflops,
-                "unit": "TFLOP/s", "bound": "tensor", "peak": peaks.get("bf16_tflops"),
-                "frac": net_tflops / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None,
-                "peak_kind": peak_kind, "flop_per_pixel": flop / (B * W * H),
-                "kernels": "tcgen05.mma M128 x N x K16 bf16 implicit GEMM, TMEM accumulators"}
-    learned, learned_fps = {}, {}
-    for k in (1, 2):  # k assignment passes: k - 1 updates after the warm start
-        lab, _ = ws.warm_start_segment(net, sub, k - 1)
-        learned[k] = round(ws.agreement(lab, ref), 5)
-        pipe = ws.WarmStartPipeline(net, [images[f] for f in range(B)], k - 1)
-        with torch.cuda.stream(stream):
-            pipe.run(stream)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=stream):
-            pipe.run(stream)
-        learned_fps[k] = world * B / (_graph_ms(g, stream, args, world, dev) / 1e3)
-    return {"reference": "plain SLIC, 10 iterations (same frames, connectivity on)", "frames": q,
-            "plain_agreement_by_iterations": plain, "learned_agreement_by_iterations": learned,
-            "plain_frames_per_s_at_10_iterations": plain10_fps,
-            "learned_frames_per_s_by_iterations": learned_fps,
-            "network_forward": net_roof,
-            "learned_reaches_99_percent": any(v >= 0.99 for v in learned.values()),
-            "learned_training": {"images": args.train_images, "epochs": args.train_epochs, "seconds": train_s,
-                                 "final_loss": hist[-1][1] if hist else None,
-                                 "final_pixel_accuracy": hist[-1][2] if hist else None}}
+    tflops = flop / (net_ms / 1e3) / 1e12
+    return {"frames": B, "ms_per_batch": net_ms, "frames_per_s": B / (net_ms / 1e3), "achieved": tflops,
+            "unit": "TFLOP/s", "bound": "tensor", "peak": peaks.get("bf16_tflops"),
+            "frac": tflops / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None, "peak_kind": peak_kind,
+            "flop_per_pixel": flop / (B * W * H),
+            "kernels": "tcgen05.mma M128 x N x K16 bf16 implicit GEMM, TMEM accumulators"}
 
 
 def main(argv=None):
@@ -619,7 +755,12 @@ def main(argv=None):
     ap.add_argument("--train-images", type=int, default=20000, help="training images for the learned leg")
     ap.add_argument("--train-epochs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-quality", action="store_true", help="skip the agreement table and the learned path")
+    ap.add_argument("--no-learned", "--no-quality", dest="no_learned", action="store_true",
+                    help="skip the learned warm start (the plain sweep always runs: it sets the iteration count)")
+    ap.add_argument("--eval-frames", type=int, default=EVAL_FRAMES, help="frames of the agreement evaluation set")
+    ap.add_argument("--no-video", action="store_true", help="skip the 4K video context")
+    ap.add_argument("--video-frames", type=int, default=120)
+    ap.add_argument("--no-single", action="store_true", help="skip the single-frame latencies")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 256-frame mixed-resolution batch")
     ap.add_argument("--no-options", action="store_true",
                     help="skip the Sec. 2 options (stopping test, seed perturbation)")
