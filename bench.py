@@ -367,7 +367,8 @@ def run_ours(args):
     pair = []
     for _ in range(2):
         eb = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=e_iters, device=dev)
-        eb.bind([torch.empty_like(images[f]) for f in range(B)])
+        eb.dimg = torch.empty_like(images)  # one allocation: the step's frames move with one copy
+        eb.bind([eb.dimg[f] for f in range(B)])
         eb.set_tuning(ctas_per_sm, stages, rows)
         if method["name"] == "learned":
             eb.set_warmstart(net)

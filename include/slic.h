@@ -213,6 +213,19 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
 slic_status slic_batch_set_buffers(slic_batch b, const uint8_t *const *d_images, int32_t *const *d_labels,
                                    float *const *d_centres, const float *const *d_init);
 
+/* Bind other buffers (same arguments as slic_batch_set_buffers) without
+   waiting for the device: the batch keeps two copies of its frame tables,
+   and this call fills the one not in use from page-locked staging memory
+   with one cudaMemcpyAsync on `stream`; slic_batch_segment calls enqueued
+   afterwards use it. Work already enqueued keeps the tables it was given
+   (a CUDA graph captured earlier keeps using its copy, which the rebind
+   after next overwrites). Calls that use the batch must be ordered on
+   `stream` (or synchronised with it). SLIC_ERR_STATE before the first
+   slic_batch_set_buffers. It waits only if the staging copy it needs is
+   still being uploaded from the rebind before last. */
+slic_status slic_batch_rebind(slic_batch b, const uint8_t *const *d_images, int32_t *const *d_labels,
+                              float *const *d_centres, const float *const *d_init, void *stream);
+
 /* Segment every frame of the batch (Sec. 4 stage order, as slic_segment);
    SLIC_ERR_STATE before slic_batch_set_buffers. */
 slic_status slic_batch_segment(slic_batch b, void *stream);
@@ -222,8 +235,10 @@ slic_status slic_batch_segment(slic_batch b, void *stream);
    slic_batch_segment, then copy the bound labels and centres into
    host_labels[f] (int32 [H][W]) and host_centres[f] (float [K_eff_f][6]).
    host_labels or host_centres may be NULL to skip those copies. One
-   cudaMemcpyAsync per buffer; host memory must be page-locked for the copies
-   to overlap other work. Returns once everything is enqueued: synchronise the
+   cudaMemcpyAsync per run of frames whose buffers lie back to back both on
+   the host and on the device (a batch held in one host and one device
+   allocation moves with one copy per direction and buffer kind); host
+   memory must be page-locked for the copies to overlap other work. Returns once everything is enqueued: synchronise the
    stream before reading the outputs. Two batches bound to different device
    buffers, driven on two streams, overlap one batch's copies with the
    other's kernels. SLIC_ERR_STATE before slic_batch_set_buffers. */

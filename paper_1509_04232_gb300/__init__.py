@@ -18,7 +18,7 @@ from ._binding import (SLIC_CIELAB, SLIC_ERR_CUDA, SLIC_ERR_INVALID, SLIC_ERR_NO
                        slic_batch_profile_enable, slic_batch_set_warmstart, slic_set_warmstart,
                        slic_batch_profile_read,
                        slic_batch_profile_times, slic_batch_segment, slic_batch_segment_host,
-                       slic_batch_set_buffers, slic_batch_set_tuning, slic_batch_status,
+                       slic_batch_rebind, slic_batch_set_buffers, slic_batch_set_tuning, slic_batch_status,
                        slic_connectivity_components, slic_connectivity_pass, slic_convert, slic_create,
                        slic_destroy, slic_grid, slic_status_check,
                        slic_init_centres, slic_iterations_run, slic_last_error, slic_launch_count, slic_params,
@@ -157,26 +157,44 @@ class BatchSegmenter:
                                    float(f.get("convergence", 0.0))) for f in frames]
         self.handle = slic_batch_create(self.params)
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
-        self.labels, self.centres, self.K_eff = [], [], []
-        for f, p in enumerate(self.params):
+        self.K_eff = []
+        for f in range(len(self.params)):
             _, ns_c, ns_r = slic_batch_grid(self.handle, f)
-            k = ns_c * ns_r
-            self.K_eff.append(k)
-            self.labels.append(torch.empty((p.height, p.width), dtype=torch.int32, device=dev))
-            self.centres.append(torch.empty((k, 6), dtype=torch.float32, device=dev))
+            self.K_eff.append(ns_c * ns_r)
+        # one allocation each for all frames' labels and centres, frame after
+        # frame, so that host copies of the whole batch are single copies
+        px = [p.height * p.width for p in self.params]
+        self._labels_flat = torch.empty(sum(px), dtype=torch.int32, device=dev)
+        self._centres_flat = torch.empty(6 * sum(self.K_eff), dtype=torch.float32, device=dev)
+        self.labels, self.centres = [], []
+        lo = co = 0
+        for p, n, k in zip(self.params, px, self.K_eff):
+            self.labels.append(self._labels_flat[lo:lo + n].view(p.height, p.width))
+            self.centres.append(self._centres_flat[co:co + 6 * k].view(k, 6))
+            lo += n
+            co += 6 * k
         self.images = None
 
-    def bind(self, images, init_centres=None):
-        """Bind input tensors (uint8 [H, W, C] CUDA, one per frame); keep them alive while in use."""
+    def bind(self, images, init_centres=None, stream=None):
+        """Bind input tensors (uint8 [H, W, C] CUDA, one per frame); keep them
+        alive while in use. The first binding waits for the device; later
+        ones are ordered on `stream` (the current stream by default) and do
+        not wait (slic_batch_rebind)."""
         for img, p in zip(images, self.params):
             if not img.is_cuda or not img.is_contiguous() or tuple(img.shape) != (p.height, p.width, p.in_channels):
                 raise ValueError("each image must be a contiguous uint8 CUDA tensor of its frame's shape")
+        first = self.images is None
         self.images = list(images)
         init = None
         if init_centres is not None:
             init = [t.data_ptr() if t is not None else None for t in init_centres]
-        slic_batch_set_buffers(self.handle, [t.data_ptr() for t in self.images], [t.data_ptr() for t in self.labels],
-                               [t.data_ptr() for t in self.centres], init)
+        args = ([t.data_ptr() for t in self.images], [t.data_ptr() for t in self.labels],
+                [t.data_ptr() for t in self.centres], init)
+        if first:
+            slic_batch_set_buffers(self.handle, *args)
+        else:
+            self._init_refs = init_centres  # (kept alive until the next binding)
+            slic_batch_rebind(self.handle, *args, _stream_handle(stream))
 
     def segment(self, stream=None):
         slic_batch_segment(self.handle, _stream_handle(stream))
@@ -192,9 +210,10 @@ class BatchSegmenter:
     def segment_host(self, host_images, host_labels=None, host_centres=None, stream=None):
         """End to end with host tensors (page-locked CPU tensors, one per
         frame): images in, labels [H, W] int32 and centres [K_eff, 6] float32
-        out (either list may be None). Enqueued on `stream`; synchronise it
-        before reading the outputs."""
-        ptrs = lambda ts: [t.data_ptr() for t in ts] if ts is not None else None  # noqa: E731
+        out (either list, or an entry of it, may be None: that copy is
+        skipped). Enqueued on `stream`; synchronise it before reading the
+        outputs."""
+        ptrs = lambda ts: [t.data_ptr() if t is not None else None for t in ts] if ts is not None else None  # noqa: E731
         slic_batch_segment_host(self.handle, ptrs(host_images), ptrs(host_labels), ptrs(host_centres),
                                 _stream_handle(stream))
 

@@ -57,6 +57,7 @@ _SIGNATURES = {
     "slic_segment_noalloc": [ctypes.POINTER(slic_params), _P, _P, _P, _P],
     "slic_batch_create": [ctypes.POINTER(slic_params), _I, ctypes.POINTER(_P)],
     "slic_batch_set_buffers": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)],
+    "slic_batch_rebind": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
     "slic_batch_segment": [_P, _P],
     "slic_batch_segment_host": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
     "slic_batch_set_tuning": [_P, _I, _I, _I],
@@ -236,6 +237,13 @@ def slic_batch_set_buffers(b: int, d_images, d_labels, d_centres, d_init=None) -
     init = _ptr_array(d_init) if d_init is not None else None
     _bcheck(lib().slic_batch_set_buffers(b, _ptr_array(d_images), _ptr_array(d_labels), _ptr_array(d_centres),
                                          init), b)
+
+
+def slic_batch_rebind(b: int, d_images, d_labels, d_centres, d_init=None, stream: int = 0) -> None:
+    """Stream-ordered rebinding (no device-wide wait); see include/slic.h."""
+    init = _ptr_array(d_init) if d_init is not None else None
+    _bcheck(lib().slic_batch_rebind(b, _ptr_array(d_images), _ptr_array(d_labels), _ptr_array(d_centres), init,
+                                    stream or None), b)
 
 
 def slic_batch_segment(b: int, stream: int = 0) -> None:

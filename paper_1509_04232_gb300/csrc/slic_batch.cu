@@ -28,11 +28,20 @@ struct slic_batch_ctx {
     int sms = 0;
     std::vector<slic_params> params;
     std::vector<FrameArgs> frames;    // host copy of the descriptor table
-    FrameArgs *d_frames = nullptr;    // device copy
+    // Device tables read by the kernels: the frame descriptors, the
+    // component-connectivity frames and the image pointers of the warm
+    // start, in two copies (a rebind fills the other one, stream-ordered,
+    // from its own page-locked staging copy); d_* point into the current one.
+    unsigned char *tables = nullptr, *staging = nullptr;
+    size_t tbl_bytes = 0, tbl_ccl = 0, tbl_img = 0;
+    int tbl_cur = 0;
+    cudaEvent_t staged[2] = {nullptr, nullptr};  // the staging copy's last upload
+    FrameArgs *d_frames = nullptr;
     unsigned char *scratch = nullptr; // features, sums, connectivity labels of all frames
-    int *ccl = nullptr;               // component connectivity (mode 2): scratch over all frames' pixels,
-    CclFrame *d_ccl = nullptr;        // the frames' table (device) and its host copy
+    int *ccl = nullptr;               // component connectivity (mode 2): scratch over all frames' pixels
+    CclFrame *d_ccl = nullptr;
     std::vector<CclFrame> ccl_frames;
+    std::vector<const uint8_t *> images;
     bool any_conv = false;            // some frame has a stopping threshold
     int total_tiles = 0, total_centres = 0, total_rows = 0, max_w = 0, win_max = 0;
     int total_units = 0;  // work units of the fused connectivity kernel
@@ -53,7 +62,7 @@ struct slic_batch_ctx {
     // [n][H][W] and the device table of the frames' image pointers
     slic_net net = nullptr;
     int32_t *net_labels = nullptr;
-    const uint8_t **d_img_table = nullptr;
+    const uint8_t *const *d_img_table = nullptr;  // (in the tables block)
     int net_C = 3;
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
@@ -203,6 +212,57 @@ void cache_store(const char *path, const std::string &key, int ctas, int stages,
     std::fclose(f);
 }
 
+// The frames' buffers into the host tables (frame descriptors,
+// component-connectivity frames).
+void bind_frames(slic_batch_ctx *b, const uint8_t *const *d_images, int32_t *const *d_labels, float *const *d_centres,
+                 const float *const *d_init) {
+    for (int f = 0; f < b->n; ++f) {
+        FrameArgs &a = b->frames[f];
+        b->images[f] = d_images[f];
+        a.rgb = d_images[f];
+        a.labels = d_labels[f];
+        a.centres = d_centres[f];
+        a.centres_out = d_centres[f];
+        a.init = d_init ? d_init[f] : nullptr;
+        a.rgb_vec = ((a.W & 3) == 0 && ((uintptr_t)a.rgb & 15) == 0) ? 1 : 0;
+        a.labels_vec = ((a.W & 3) == 0 && ((uintptr_t)a.labels & 15) == 0) ? 1 : 0;
+        // The pipelined last pass writes lbl_tmp when the fused connectivity
+        // kernel follows (it reads lbl_tmp and writes the labels).
+        const bool fused = b->pipe && b->connectivity == 1;
+        a.assign_out = fused ? a.lbl_tmp : a.labels;
+        a.assign_vec = fused ? ((a.W & 3) == 0 ? 1 : 0) : a.labels_vec;
+    }
+    if (b->connectivity == 2) {
+        b->ccl_frames.assign(b->n, CclFrame{});
+        int base = 0;
+        for (int f = 0; f < b->n; ++f) {
+            const FrameArgs &a = b->frames[f];
+            b->ccl_frames[f] = CclFrame{a.labels, a.labels, a.W, a.S * a.S / 4, base};
+            base += a.W * a.H;
+        }
+    }
+}
+
+// Upload the host tables into device copy k, ordered on stream s (the
+// staging copy k is reused only after its previous upload completed), and
+// make it the current one; then the sentinel ring of the centre tables.
+cudaError_t upload_tables(slic_batch_ctx *b, int k, cudaStream_t s) {
+    cudaError_t e = cudaEventSynchronize(b->staged[k]);
+    if (e != cudaSuccess) return e;
+    unsigned char *h = b->staging + (size_t)k * b->tbl_bytes, *d = b->tables + (size_t)k * b->tbl_bytes;
+    std::memcpy(h, b->frames.data(), sizeof(FrameArgs) * b->n);
+    if (b->connectivity == 2) std::memcpy(h + b->tbl_ccl, b->ccl_frames.data(), sizeof(CclFrame) * b->n);
+    std::memcpy(h + b->tbl_img, b->images.data(), sizeof(const uint8_t *) * b->n);
+    e = cudaMemcpyAsync(d, h, b->tbl_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->staged[k], s);
+    if (e != cudaSuccess) return e;
+    b->tbl_cur = k;
+    b->d_frames = reinterpret_cast<FrameArgs *>(d);
+    b->d_ccl = reinterpret_cast<CclFrame *>(d + b->tbl_ccl);
+    b->d_img_table = reinterpret_cast<const uint8_t *const *>(d + b->tbl_img);
+    return launch_fill_ring(b->d_frames, b->n, b->max_ring, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -291,7 +351,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
     const size_t off_err = bytes;
     bytes += 256;
     // component connectivity: one scratch over all frames' pixels and the table
-    size_t off_ccl = 0, off_ccl_table = 0;
+    size_t off_ccl = 0;
     if (b->connectivity == 2) {
         if (b->total_pixels >= (1LL << 31)) {
             delete b;
@@ -299,9 +359,10 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         }
         off_ccl = bytes;
         bytes += align256(sizeof(int) * ccl_scratch_ints(b->total_pixels));
-        off_ccl_table = bytes;
-        bytes += align256(sizeof(CclFrame) * (size_t)n_frames);
     }
+    b->tbl_ccl = align256(sizeof(FrameArgs) * (size_t)n_frames);
+    b->tbl_img = b->tbl_ccl + align256(sizeof(CclFrame) * (size_t)n_frames);
+    b->tbl_bytes = b->tbl_img + align256(sizeof(const uint8_t *) * (size_t)n_frames);
     b->total_tiles = (int)tiles;
     b->total_centres = (int)centres;
     b->total_rows = (int)rows;
@@ -324,14 +385,22 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
     b->pipe = !assign_direct_acc(b->win_max) && assign_pipe_occupancy(b->same, b->win_max, 3, 1) > 0;
     if (b->pipe && assign_pipe_occupancy(b->same, b->win_max, 4, 1) == 0) b->stages = 3;
     b->occupancy = std::max(1, assign_batch_occupancy(b->same, b->smem));
-    if (dev_alloc(&b->scratch, bytes) != cudaSuccess ||
-        dev_alloc(&b->d_frames, sizeof(FrameArgs) * n_frames) != cudaSuccess) {
+    if (dev_alloc(&b->scratch, bytes) != cudaSuccess || dev_alloc(&b->tables, 2 * b->tbl_bytes) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void **>(&b->staging), 2 * b->tbl_bytes, cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(b->scratch);
-        cudaFree(b->d_frames);
+        cudaFree(b->tables);
         delete b;
-        return bfail(nullptr, SLIC_ERR_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+        return bfail(nullptr, SLIC_ERR_NOMEM, "allocation of " + std::to_string(bytes) + " device bytes failed");
     }
+    if (cudaEventCreateWithFlags(&b->staged[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->staged[1], cudaEventDisableTiming) != cudaSuccess) {
+        slic_batch_destroy(b);
+        return bfail(nullptr, SLIC_ERR_CUDA, "cudaEventCreate failed");
+    }
+    b->images.assign(n_frames, nullptr);
+    b->d_frames = reinterpret_cast<FrameArgs *>(b->tables);
+    b->d_ccl = reinterpret_cast<CclFrame *>(b->tables + b->tbl_ccl);
     for (int f = 0; f < n_frames; ++f) {
         FrameArgs &a = b->frames[f];
         a.feat = reinterpret_cast<float *>(b->scratch + off_feat[f]);
@@ -342,10 +411,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         if (b->pipe && !encode_maps(a)) b->pipe = false;  // then every pass uses k_assign_batch
     }
     b->d_err = reinterpret_cast<int *>(b->scratch + off_err);
-    if (b->connectivity == 2) {
-        b->ccl = reinterpret_cast<int *>(b->scratch + off_ccl);
-        b->d_ccl = reinterpret_cast<CclFrame *>(b->scratch + off_ccl_table);
-    }
+    if (b->connectivity == 2) b->ccl = reinterpret_cast<int *>(b->scratch + off_ccl);
     if (cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess) {
         slic_batch_destroy(b);
         return bfail(nullptr, SLIC_ERR_CUDA, "clearing the error flag failed");
@@ -358,9 +424,11 @@ slic_status slic_batch_destroy(slic_batch b) {
     if (!b) return SLIC_OK;
     cudaDeviceSynchronize();
     cudaFree(b->scratch);
-    cudaFree(b->d_frames);
+    cudaFree(b->tables);
+    cudaFreeHost(b->staging);
+    for (cudaEvent_t ev : b->staged)
+        if (ev) cudaEventDestroy(ev);
     cudaFree(b->net_labels);
-    cudaFree(b->d_img_table);
     for (auto &ev : b->events) {
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
@@ -373,45 +441,32 @@ slic_status slic_batch_set_buffers(slic_batch b, const uint8_t *const *d_images,
                                    float *const *d_centres, const float *const *d_init) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (!d_images || !d_labels || !d_centres) return bfail(b, SLIC_ERR_INVALID, "NULL pointer array");
-    for (int f = 0; f < b->n; ++f) {
+    for (int f = 0; f < b->n; ++f)
         if (!d_images[f] || !d_labels[f] || !d_centres[f])
             return bfail(b, SLIC_ERR_INVALID, "NULL buffer for frame " + std::to_string(f));
-        FrameArgs &a = b->frames[f];
-        a.rgb = d_images[f];
-        a.labels = d_labels[f];
-        a.centres = d_centres[f];
-        a.centres_out = d_centres[f];
-        a.init = d_init ? d_init[f] : nullptr;
-        a.rgb_vec = ((a.W & 3) == 0 && ((uintptr_t)a.rgb & 15) == 0) ? 1 : 0;
-        a.labels_vec = ((a.W & 3) == 0 && ((uintptr_t)a.labels & 15) == 0) ? 1 : 0;
-        // The pipelined last pass writes lbl_tmp when the fused connectivity
-        // kernel follows (it reads lbl_tmp and writes the labels).
-        const bool fused = b->pipe && b->connectivity == 1;
-        a.assign_out = fused ? a.lbl_tmp : a.labels;
-        a.assign_vec = fused ? ((a.W & 3) == 0 ? 1 : 0) : a.labels_vec;
-    }
-    if (b->connectivity == 2) {
-        b->ccl_frames.assign(b->n, CclFrame{});
-        int base = 0;
-        for (int f = 0; f < b->n; ++f) {
-            const FrameArgs &a = b->frames[f];
-            b->ccl_frames[f] = CclFrame{a.labels, a.labels, a.W, a.S * a.S / 4, base};
-            base += a.W * a.H;
-        }
-    }
-    // Synchronous upload: the tables must not change under queued work.
+    // Synchronous: the tables must not change under queued work.
     cudaError_t e = cudaDeviceSynchronize();
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_frames, b->frames.data(), sizeof(FrameArgs) * b->n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && b->connectivity == 2)
-        e = cudaMemcpy(b->d_ccl, b->ccl_frames.data(), sizeof(CclFrame) * b->n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && b->net)
-        e = cudaMemcpy(b->d_img_table, d_images, sizeof(const uint8_t *) * b->n, cudaMemcpyHostToDevice);
-    // Sentinel ring of the padded centre tables (geometry only).
-    if (e == cudaSuccess) e = launch_fill_ring(b->d_frames, b->n, b->max_ring, nullptr);
+    if (e == cudaSuccess) {
+        bind_frames(b, d_images, d_labels, d_centres, d_init);
+        e = upload_tables(b, b->tbl_cur, nullptr);
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("frame table upload: ") + cudaGetErrorString(e));
     b->buffers_set = true;
+    return SLIC_OK;
+}
+
+slic_status slic_batch_rebind(slic_batch b, const uint8_t *const *d_images, int32_t *const *d_labels,
+                              float *const *d_centres, const float *const *d_init, void *stream) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
+    if (!d_images || !d_labels || !d_centres) return bfail(b, SLIC_ERR_INVALID, "NULL pointer array");
+    for (int f = 0; f < b->n; ++f)
+        if (!d_images[f] || !d_labels[f] || !d_centres[f])
+            return bfail(b, SLIC_ERR_INVALID, "NULL buffer for frame " + std::to_string(f));
+    bind_frames(b, d_images, d_labels, d_centres, d_init);
+    const cudaError_t e = upload_tables(b, b->tbl_cur ^ 1, (cudaStream_t)stream);
+    if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("frame table upload: ") + cudaGetErrorString(e));
     return SLIC_OK;
 }
 
@@ -496,31 +551,69 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
     return SLIC_OK;
 }
 
+namespace {
+// Copies of equal direction for frames 0..n-1 (host[f], device[f], bytes[f];
+// a NULL host pointer skips the frame), one cudaMemcpyAsync for each run of
+// frames that lie back to back in both host and device memory.
+cudaError_t copy_runs(int n, const std::vector<const void *> &src, const std::vector<void *> &dst,
+                      const std::vector<size_t> &bytes, cudaMemcpyKind kind, cudaStream_t s) {
+    int f = 0;
+    while (f < n) {
+        if (!src[f]) {
+            ++f;
+            continue;
+        }
+        size_t len = bytes[f];
+        int g = f + 1;
+        while (g < n && src[g] && static_cast<const char *>(src[g]) == static_cast<const char *>(src[f]) + len &&
+               static_cast<char *>(dst[g]) == static_cast<char *>(dst[f]) + len) {
+            len += bytes[g];
+            ++g;
+        }
+        const cudaError_t e = cudaMemcpyAsync(dst[f], src[f], len, kind, s);
+        if (e != cudaSuccess) return e;
+        f = g;
+    }
+    return cudaSuccess;
+}
+}  // namespace
+
 slic_status slic_batch_segment_host(slic_batch b, const uint8_t *const *host_images, int32_t *const *host_labels,
                                     float *const *host_centres, void *stream) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (!host_images) return bfail(b, SLIC_ERR_INVALID, "NULL host image array");
     if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
     cudaStream_t s = (cudaStream_t)stream;
-    for (int f = 0; f < b->n; ++f) {
+    const int n = b->n;
+    std::vector<const void *> src(n);
+    std::vector<void *> dst(n);
+    std::vector<size_t> len(n);
+    for (int f = 0; f < n; ++f) {
         const FrameArgs &a = b->frames[f];
         if (!host_images[f]) return bfail(b, SLIC_ERR_INVALID, "NULL host image for frame " + std::to_string(f));
-        const cudaError_t e = cudaMemcpyAsync(const_cast<uint8_t *>(a.rgb), host_images[f],
-                                              (size_t)a.W * a.H * a.C, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("image copy: ") + cudaGetErrorString(e));
+        src[f] = host_images[f];
+        dst[f] = const_cast<uint8_t *>(a.rgb);
+        len[f] = (size_t)a.W * a.H * a.C;
     }
+    cudaError_t e = copy_runs(n, src, dst, len, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("image copy: ") + cudaGetErrorString(e));
     const slic_status st = slic_batch_segment(b, stream);
     if (st != SLIC_OK) return st;
-    for (int f = 0; f < b->n; ++f) {
-        const FrameArgs &a = b->frames[f];
-        cudaError_t e = cudaSuccess;
-        if (host_labels && host_labels[f])
-            e = cudaMemcpyAsync(host_labels[f], a.labels, sizeof(int32_t) * a.W * a.H, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess && host_centres && host_centres[f])
-            e = cudaMemcpyAsync(host_centres[f], a.centres_out, sizeof(float) * 6 * (size_t)a.ns_c * a.ns_r,
-                                cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+        int32_t *const *hl = host_labels;
+        float *const *hc = host_centres;
+        if (pass == 0 && !hl) continue;
+        if (pass == 1 && !hc) continue;
+        for (int f = 0; f < n; ++f) {
+            const FrameArgs &a = b->frames[f];
+            src[f] = pass == 0 ? static_cast<const void *>(a.labels) : static_cast<const void *>(a.centres_out);
+            dst[f] = pass == 0 ? static_cast<void *>(hl[f]) : static_cast<void *>(hc[f]);
+            len[f] = pass == 0 ? sizeof(int32_t) * a.W * a.H : sizeof(float) * 6 * (size_t)a.ns_c * a.ns_r;
+            if (!dst[f]) src[f] = nullptr;
+        }
+        e = copy_runs(n, src, dst, len, cudaMemcpyDeviceToHost, s);
     }
+    if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
     return SLIC_OK;
 }
 
@@ -703,31 +796,24 @@ slic_status slic_batch_set_warmstart(slic_batch b, slic_net net) {
     // Queued work may still read the tables: wait, then change them.
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess && net && !b->net_labels) {
-        if (dev_alloc(&b->net_labels, sizeof(int32_t) * (size_t)b->total_pixels) != cudaSuccess ||
-            dev_alloc(&b->d_img_table, sizeof(const uint8_t *) * b->n) != cudaSuccess) {
+        if (dev_alloc(&b->net_labels, sizeof(int32_t) * (size_t)b->total_pixels) != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(b->net_labels);
-            cudaFree(b->d_img_table);
             b->net_labels = nullptr;
-            b->d_img_table = nullptr;
             return bfail(b, SLIC_ERR_NOMEM, "device allocation of the warm-start labels failed");
         }
     }
     if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("device wait: ") + cudaGetErrorString(e));
     b->net = net;
     b->net_C = b->frames[0].C;
-    std::vector<const uint8_t *> imgs(b->n);
     size_t off = 0;
     for (int f = 0; f < b->n; ++f) {
         FrameArgs &a = b->frames[f];
         a.init_labels = net ? b->net_labels + off : nullptr;
         off += (size_t)a.W * a.H;
-        imgs[f] = a.rgb;
     }
     if (b->buffers_set) {
-        e = cudaMemcpy(b->d_frames, b->frames.data(), sizeof(FrameArgs) * b->n, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && net)
-            e = cudaMemcpy(b->d_img_table, imgs.data(), sizeof(const uint8_t *) * b->n, cudaMemcpyHostToDevice);
+        e = upload_tables(b, b->tbl_cur, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
     }
     return SLIC_OK;

@@ -117,7 +117,8 @@ def run_video(frames, batch: int = 8, iterations: int = 2, S: int = 16, m: float
             if net is not None and prev is not None:
                 segs[key].set_warmstart(net)
         bs = segs[key]
-        bs.bind([frames[i] for i in range(f0, f1)], init_centres=[prev] * n if prev is not None else None)
+        bs.bind([frames[i] for i in range(f0, f1)], init_centres=[prev] * n if prev is not None else None,
+                stream=stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
             e0.record(stream)

@@ -215,3 +215,63 @@ def test_segment_host_matches_device_path(slic_gpu):
     bs.segment_host(h_img, h_lab2, None, stream=stream)   # centres copy skipped
     stream.synchronize()
     assert torch.equal(h_lab2[0], want_l[0])
+
+
+def test_segment_host_with_contiguous_buffers(slic_gpu):
+    """The whole batch in one host and one device allocation (the copies
+    merge into one per direction and kind): same results as the device
+    path, and a host label array skipped for one frame stays untouched."""
+    import torch
+    pkg = slic_gpu
+    W, H, n = 320, 240, 3
+    host = torch.from_numpy(np.stack([synth.small_image(10 + i) for i in range(n)])).pin_memory()
+    ref = pkg.BatchSegmenter([dict(width=W, height=H, S=16)] * n, iterations=3)
+    ref.bind([host[i].cuda() for i in range(n)])
+    want_l, want_c = [[t.cpu() for t in x] for x in ref.segment()]
+    bs = pkg.BatchSegmenter([dict(width=W, height=H, S=16)] * n, iterations=3)
+    dev = torch.empty_like(host, device="cuda")
+    bs.bind([dev[i] for i in range(n)])
+    h_lab = torch.full((n, H, W), -5, dtype=torch.int32).pin_memory()
+    h_cen = torch.empty((n, bs.K_eff[0], 6), dtype=torch.float32).pin_memory()
+    stream = torch.cuda.Stream()
+    bs.segment_host([host[i] for i in range(n)], [h_lab[0], None, h_lab[2]], [h_cen[i] for i in range(n)],
+                    stream=stream)
+    stream.synchronize()
+    assert torch.equal(h_lab[0], want_l[0]) and torch.equal(h_lab[2], want_l[2])
+    assert bool((h_lab[1] == -5).all())
+    for i in range(n):
+        assert torch.equal(h_cen[i], want_c[i])
+
+
+def test_rebind_is_stream_ordered(slic_gpu):
+    """Rebinding without a device-wide wait: frames A, then B and A again
+    on one stream, each result equal to a batch bound to those frames only;
+    with initial centres on the rebind as well."""
+    import torch
+    pkg = slic_gpu
+    W, H = 320, 240
+    A = [_cuda(synth.small_image(20 + i)) for i in range(2)]
+    B = [_cuda(synth.small_image(30 + i)) for i in range(2)]
+
+    def fresh(imgs, init=None):
+        r = pkg.BatchSegmenter([dict(width=W, height=H, S=16)] * 2, iterations=2)
+        r.bind(imgs, init_centres=init)
+        return [[t.clone() for t in x] for x in r.segment()]
+
+    want_a, want_b = fresh(A), fresh(B)
+    bs = pkg.BatchSegmenter([dict(width=W, height=H, S=16)] * 2, iterations=2)
+    bs.bind(A)
+    stream = torch.cuda.Stream()
+    got = []
+    with torch.cuda.stream(stream):
+        for imgs in (B, A, B):
+            bs.bind(imgs, stream=stream)
+            got.append([[t.clone() for t in x] for x in bs.segment(stream=stream)])
+        init = [want_a[1][0].clone(), None]
+        bs.bind(B, init_centres=init, stream=stream)
+        got.append([[t.clone() for t in x] for x in bs.segment(stream=stream)])
+    stream.synchronize()
+    want_bi = fresh(B, init)
+    for g, w in zip(got, (want_b, want_a, want_b, want_bi)):
+        for x, y in zip(g[0] + g[1], w[0] + w[1]):
+            assert torch.equal(x, y)
