@@ -269,7 +269,7 @@ def run_ours(args):
     # --- the plain path at its iteration count, autotuned, one graph per step ---
     bs = _plain_batch(pkg, frames, n_plain, dev)
     tuning = bs.autotune(tune_cache, stream=stream)
-    ctas_per_sm, stages, rows = tuning
+    ctas_per_sm, stages, rows, tile_h = tuning
     K_EFF = bs.K_eff[0]
     n0 = bs.info[1]
     graph = _capture(lambda: bs.segment(stream=stream), stream)
@@ -326,7 +326,8 @@ def run_ours(args):
     pkg.slic_batch_profile_enable(pb.handle, True)
     graph_prof = _capture(lambda: pb.segment(stream=stream), stream)
     pkg.slic_batch_profile_enable(pb.handle, False)
-    kname = f"k_assign_pipe<0,1,{4 if (rows == 2 or ctas_per_sm >= 4) else 3},{rows}>"
+    minb = 2 if tile_h == 64 else (4 if (rows == 2 or ctas_per_sm >= 4) else 3)
+    kname = f"k_assign_pipe<0,1,{minb},{rows},{tile_h}>"
     mid = []
     for _ in range(max(3, min(args.steps, 10))):
         with torch.cuda.stream(stream):
@@ -369,7 +370,7 @@ def run_ours(args):
         eb = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=e_iters, device=dev)
         eb.dimg = torch.empty_like(images)  # one allocation: the step's frames move with one copy
         eb.bind([eb.dimg[f] for f in range(B)])
-        eb.set_tuning(ctas_per_sm, stages, rows)
+        eb.set_tuning(ctas_per_sm, stages, rows, tile_h)
         if method["name"] == "learned":
             eb.set_warmstart(net)
         pair.append((eb, torch.cuda.Stream(device=dev), torch.empty((B, H, W), dtype=torch.int32).pin_memory(),
@@ -449,7 +450,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world} (frames sharded, no collective)",
                        "l2": "inputs larger than L2 (B x 6.2 MB RGB + B x 8.3 MB labels per step)",
                        "graph": "one CUDA graph per step (one batched launch per stage)",
-                       "ctas_per_sm": ctas_per_sm, "pipeline_stages": stages, "row_groups_per_warp": rows},
+                       "ctas_per_sm": ctas_per_sm, "pipeline_stages": stages, "row_groups_per_warp": rows,
+                       "tile": f"32x{tile_h}"},
             "roofline": {"kernel": f"{kname} (middle assignment pass, all frames)", "bound": "alu",
                          "unit": "Tsqrt/s", "achieved": achieved_tops, "peak": xu_peak, "frac": achieved_tops / xu_peak,
                          "peak_source": f"16 MUFU lanes/clk/SM x {sms} SMs x max SM clock (recipe unit counts)",
@@ -556,7 +558,8 @@ def mixed_batch_throughput(args, pkg, stream, dev):
     imgs = [torch.from_numpy(synth.mixed_batch_frame(f, w, h)).to(dev) for f, (w, h, _, _) in enumerate(specs)]
     bs = pkg.BatchSegmenter(frames, iterations=ITERS, device=dev)
     bs.bind(imgs)
-    ctas, stages, rows = bs.autotune(os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl"), stream=stream)
+    ctas, stages, rows, tile_h = bs.autotune(os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl"),
+                                             stream=stream)
     with torch.cuda.stream(stream):
         bs.segment(stream)
     torch.cuda.synchronize()
@@ -580,7 +583,7 @@ def mixed_batch_throughput(args, pkg, stream, dev):
     bs.close()
     return {"frames": len(specs), "megapixels": px / 1e6, "ms_per_step": ms, "frames_per_s": len(specs) / (ms / 1e3),
             "megapixels_per_s": px / 1e6 / (ms / 1e3), "steps": steps, "ctas_per_sm": ctas, "pipeline_stages": stages,
-            "row_groups_per_warp": rows,
+            "row_groups_per_warp": rows, "tile": f"32x{tile_h}",
             "iterations": ITERS}
 
 

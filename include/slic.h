@@ -248,28 +248,34 @@ slic_status slic_batch_segment_host(slic_batch b, const uint8_t *const *host_ima
 /* Launch shape of the persistent assignment kernels: resident CTAs per SM
    (0 = as many as fit, capped by each kernel's occupancy), the number of
    TMA pipeline stages (3 or 4; 0 keeps the current value, default 4 where it
-   fits) and the row groups per warp (1: 256 threads, 4 pixels per thread;
-   2: 128 threads, 8 pixels per thread, only when every frame's S is a
-   multiple of 8; 0 keeps the current value, default 1). SLIC_ERR_INVALID
-   for other values or shapes that do not fit in shared memory. */
-slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages, int rows);
+   fits), the row groups per warp (1: 256 threads, 4 pixels per thread;
+   2: 128 threads per 32 tile rows, 8 pixels per thread, only when every
+   frame's S is a multiple of 8; 0 keeps the current value, default 1) and
+   the tile shape (tile_h = 32: 32x32-pixel tiles; 64: 32x64-pixel tiles,
+   256 threads, two row groups only; 0 keeps the current value, default 32).
+   SLIC_ERR_INVALID for other values or shapes that do not fit in shared
+   memory. */
+slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages, int rows, int tile_h);
 
 /* Autotuner: time slic_batch_segment on the bound buffers for every launch
    shape that fits (3 timed runs each, CUDA events on `stream`; this waits
    for the device), keep the fastest, and append it to the JSON-lines file
    cache_path (may be NULL) under a key of GPU name, frame count,
    iterations and the distinct (width, height, S). When the key is already
-   in the file its entry is used without timing. The search covers row
-   groups per warp x pipeline stages x CTAs per SM; the choice is returned in
-   *ctas_per_sm, *stages and *rows (any may be NULL). */
+   in the file its entry is used without timing. The search covers tile
+   shapes x row groups per warp x pipeline stages x CTAs per SM; the choice
+   is returned in *ctas_per_sm, *stages, *rows and *tile_h (any may be
+   NULL). */
 slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm, int *stages,
-                               int *rows);
+                               int *rows, int *tile_h);
 
-/* Pixels of all frames, kernel launches enqueued so far, CTAs per SM
-   requested, pipeline stages and row groups per warp in use (0 when the
-   pipelined kernel is not used); any pointer may be NULL. */
+/* Pixels of all frames, kernel launches enqueued so far, and the launch
+   shape of the assignment passes: CTAs per SM (as requested, capped by what
+   fits), pipeline stages, row groups per warp and tile rows
+   (stages and rows 0, tile rows 32, when the pipelined kernel is not used);
+   any pointer may be NULL. */
 slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm,
-                            int *stages, int *rows);
+                            int *stages, int *rows, int *tile_h);
 
 /* Grid of frame `frame` (Sec. 2): its S and ns_c x ns_r cells, K_eff =
    ns_c*ns_r centres (any pointer may be NULL); SLIC_ERR_INVALID for a frame

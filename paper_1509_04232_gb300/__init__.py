@@ -218,11 +218,11 @@ class BatchSegmenter:
                                 _stream_handle(stream))
 
     def autotune(self, cache_path=None, stream=None):
-        """Time the launch shapes that fit; -> (ctas_per_sm, stages, rows) chosen."""
+        """Time the launch shapes that fit; -> (ctas_per_sm, stages, rows, tile_h) chosen."""
         return slic_batch_autotune(self.handle, cache_path, _stream_handle(stream))
 
-    def set_tuning(self, ctas_per_sm: int, stages: int = 0, rows: int = 0):
-        slic_batch_set_tuning(self.handle, ctas_per_sm, stages, rows)
+    def set_tuning(self, ctas_per_sm: int, stages: int = 0, rows: int = 0, tile_h: int = 0):
+        slic_batch_set_tuning(self.handle, ctas_per_sm, stages, rows, tile_h)
 
     @property
     def info(self):

@@ -60,10 +60,11 @@ _SIGNATURES = {
     "slic_batch_rebind": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
     "slic_batch_segment": [_P, _P],
     "slic_batch_segment_host": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
-    "slic_batch_set_tuning": [_P, _I, _I, _I],
-    "slic_batch_autotune": [_P, ctypes.c_char_p, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "slic_batch_set_tuning": [_P, _I, _I, _I, _I],
+    "slic_batch_autotune": [_P, ctypes.c_char_p, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                            ctypes.POINTER(_I)],
     "slic_batch_info": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
-                        ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+                        ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "slic_batch_destroy": [_P],
     "slic_batch_status": [_P],
     "slic_batch_iterations_run": [_P, ctypes.POINTER(_I)],
@@ -261,25 +262,25 @@ def slic_batch_segment_host(b: int, host_images, host_labels=None, host_centres=
                                           stream or None), b)
 
 
-def slic_batch_set_tuning(b: int, ctas_per_sm: int, stages: int = 0, rows: int = 0) -> None:
-    _bcheck(lib().slic_batch_set_tuning(b, int(ctas_per_sm), int(stages), int(rows)), b)
+def slic_batch_set_tuning(b: int, ctas_per_sm: int, stages: int = 0, rows: int = 0, tile_h: int = 0) -> None:
+    _bcheck(lib().slic_batch_set_tuning(b, int(ctas_per_sm), int(stages), int(rows), int(tile_h)), b)
 
 
 def slic_batch_autotune(b: int, cache_path: str | None = None, stream: int = 0):
-    """-> (ctas_per_sm, stages, rows) chosen."""
-    c, st, rw = _I(), _I(), _I()
+    """-> (ctas_per_sm, stages, rows, tile_h) chosen."""
+    c, st, rw, th = _I(), _I(), _I(), _I()
     path = cache_path.encode() if cache_path else None
-    _bcheck(lib().slic_batch_autotune(b, path, stream or None, ctypes.byref(c), ctypes.byref(st), ctypes.byref(rw)),
-            b)
-    return c.value, st.value, rw.value
+    _bcheck(lib().slic_batch_autotune(b, path, stream or None, ctypes.byref(c), ctypes.byref(st), ctypes.byref(rw),
+                                      ctypes.byref(th)), b)
+    return c.value, st.value, rw.value, th.value
 
 
 def slic_batch_info(b: int):
-    """-> (total_pixels, launches, ctas_per_sm, stages, rows)."""
-    px, n, c, st, rw = ctypes.c_longlong(), ctypes.c_longlong(), _I(), _I(), _I()
+    """-> (total_pixels, launches, ctas_per_sm, stages, rows, tile_h)."""
+    px, n, c, st, rw, th = ctypes.c_longlong(), ctypes.c_longlong(), _I(), _I(), _I(), _I()
     _bcheck(lib().slic_batch_info(b, ctypes.byref(px), ctypes.byref(n), ctypes.byref(c), ctypes.byref(st),
-                                  ctypes.byref(rw)), b)
-    return px.value, n.value, c.value, st.value, rw.value
+                                  ctypes.byref(rw), ctypes.byref(th)), b)
+    return px.value, n.value, c.value, st.value, rw.value, th.value
 
 
 def slic_connectivity_components(h: int, d_in: int, d_out: int, stream: int = 0) -> None:

@@ -44,6 +44,7 @@ struct slic_batch_ctx {
     std::vector<const uint8_t *> images;
     bool any_conv = false;            // some frame has a stopping threshold
     int total_tiles = 0, total_centres = 0, total_rows = 0, max_w = 0, win_max = 0;
+    int total_tiles64 = 0, win_max64 = 0;  // the same for 32x64 tiles
     int total_units = 0;  // work units of the fused connectivity kernel
     long long total_pixels = 0;
     bool same = true;        // every frame's S a multiple of 4 (4-pixel groups share a cell)
@@ -57,6 +58,7 @@ struct slic_batch_ctx {
     int ctas_per_sm = 0;     // 0: as many as fit
     int stages = 4;          // TMA pipeline stages of the pipelined kernel (3..4)
     int rows = 1;            // row groups per warp of the pipelined kernel (1, or 2 when same8)
+    int tile_h = 32;         // tile rows of the pipelined kernel (32, or 64 with rows = 2)
     long long launches = 0;
     // learned warm start (slic_batch_set_warmstart): the network, its labels
     // [n][H][W] and the device table of the frames' image pointers
@@ -107,13 +109,13 @@ PFN_cuTensorMapEncodeTiled_v12000 slicgb::tensor_map_encoder() {
 namespace {
 
 // Tensor maps of one frame for the pipelined assignment: the features as a
-// [3][H][P] f32 tensor copied in 32x32x3 boxes, and the padded centre table
-// as a [ns_r+2][(ns_c+2)*kCtabRec] f32 tensor copied in box_h x box_w*kCtabRec
-// boxes (the innermost coordinate of a copy, (wx0+1)*kCtabRec floats, is a
-// multiple of 16 bytes).
+// [3][H][P] f32 tensor copied in 32x32x3 (or 32x64x3) boxes, and the padded
+// centre table as a [ns_r+2][(ns_c+2)*kCtabRec] f32 tensor copied in
+// box_h x box_w*kCtabRec (or box_h64 x box_w*kCtabRec) boxes (the innermost
+// coordinate of a copy, (wx0+1)*kCtabRec floats, is a multiple of 16 bytes).
 bool encode_maps(FrameArgs &a) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc || a.box_w * kCtabRec > 256 || a.box_h > 256) return false;
+    if (!enc || a.box_w * kCtabRec > 256 || a.box_h64 > 256) return false;
     const cuuint64_t fdim[3] = {(cuuint64_t)a.P, (cuuint64_t)a.H, 3};
     const cuuint64_t fstride[2] = {(cuuint64_t)a.P * 4, (cuuint64_t)a.P * a.H * 4};
     const cuuint32_t fbox[3] = {(cuuint32_t)kTileW, (cuuint32_t)kTileH, 3};
@@ -125,7 +127,17 @@ bool encode_maps(FrameArgs &a) {
     const cuuint64_t cdim[2] = {(cuuint64_t)(a.ns_c + 2) * kCtabRec, (cuuint64_t)(a.ns_r + 2)};
     const cuuint64_t cstride[1] = {(cuuint64_t)(a.ns_c + 2) * kCtabRec * 4};
     const cuuint32_t cbox[2] = {(cuuint32_t)a.box_w * kCtabRec, (cuuint32_t)a.box_h};
-    return enc(&a.ctab_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.ctab, cdim, cstride, cbox, ones,
+    if (enc(&a.ctab_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.ctab, cdim, cstride, cbox, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    // 32x64 tiles: a box twice as high, and the taller window of centres
+    const cuuint32_t fbox64[3] = {(cuuint32_t)kTileW, (cuuint32_t)(2 * kTileH), 3};
+    const cuuint32_t cbox64[2] = {(cuuint32_t)a.box_w * kCtabRec, (cuuint32_t)a.box_h64};
+    return enc(&a.feat_map64, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.feat, fdim, fstride, fbox64, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
+           enc(&a.ctab_map64, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.ctab, cdim, cstride, cbox64, ones,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -160,8 +172,17 @@ int grid_for(const slic_batch_ctx *b, int occ) {
     return std::max(1, per_sm) * b->sms;
 }
 
-int pipe_occ(const slic_batch_ctx *b, int stages, int rows) {
-    return std::max(1, assign_pipe_occupancy(b->same, b->win_max, stages, rows));
+int pipe_occ(const slic_batch_ctx *b, int stages, int rows, int tile_h) {
+    return std::max(1, assign_pipe_occupancy(b->same, tile_h == 64 ? b->win_max64 : b->win_max, stages, rows, tile_h));
+}
+
+// Whether a launch shape of the pipelined kernel fits (shared memory) and is
+// allowed for the batch.
+bool shape_fits(const slic_batch_ctx *b, int stages, int rows, int tile_h) {
+    if (!b->pipe) return rows == 1 && tile_h == 32;
+    if ((rows == 2 || tile_h == 64) && !b->same8) return false;
+    if (tile_h == 64 && rows != 2) return false;
+    return assign_pipe_occupancy(b->same, tile_h == 64 ? b->win_max64 : b->win_max, stages, rows, tile_h) > 0;
 }
 
 std::string tune_key(const slic_batch_ctx *b) {
@@ -178,8 +199,9 @@ std::string tune_key(const slic_batch_ctx *b) {
     return key;
 }
 
-// Cache lines: {"key": "<key>", "ctas_per_sm": <int>, "stages": <int>, "rows": <int>, "ms": <float>}
-bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stages, int *rows) {
+// Cache lines: {"key": "<key>", "ctas_per_sm": <int>, "stages": <int>, "rows": <int>, "tile_h": <int>,
+// "ms": <float>}
+bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stages, int *rows, int *tile_h) {
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
     char line[4096];
@@ -190,12 +212,15 @@ bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stag
             const char *q = std::strstr(line, "\"ctas_per_sm\":");
             const char *r = std::strstr(line, "\"stages\":");
             const char *o = std::strstr(line, "\"rows\":");
-            int v = 0, w = 0, u = 0;
-            if (q && r && o && std::sscanf(q + 14, "%d", &v) == 1 && std::sscanf(r + 9, "%d", &w) == 1 &&
-                std::sscanf(o + 7, "%d", &u) == 1 && v > 0 && w >= 3 && w <= 4 && (u == 1 || u == 2)) {
+            const char *t = std::strstr(line, "\"tile_h\":");
+            int v = 0, w = 0, u = 0, h = 0;
+            if (q && r && o && t && std::sscanf(q + 14, "%d", &v) == 1 && std::sscanf(r + 9, "%d", &w) == 1 &&
+                std::sscanf(o + 7, "%d", &u) == 1 && std::sscanf(t + 9, "%d", &h) == 1 && v > 0 && w >= 3 &&
+                w <= 4 && (u == 1 || u == 2) && (h == 32 || h == 64)) {
                 *ctas = v;
                 *stages = w;
                 *rows = u;
+                *tile_h = h;
                 found = true;
             }
         }
@@ -204,11 +229,11 @@ bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stag
     return found;
 }
 
-void cache_store(const char *path, const std::string &key, int ctas, int stages, int rows, float ms) {
+void cache_store(const char *path, const std::string &key, int ctas, int stages, int rows, int tile_h, float ms) {
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"stages\": %d, \"rows\": %d, \"ms\": %.4f}\n",
-                 key.c_str(), ctas, stages, rows, ms);
+    std::fprintf(f, "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"stages\": %d, \"rows\": %d, \"tile_h\": %d, \"ms\": %.4f}\n",
+                 key.c_str(), ctas, stages, rows, tile_h, ms);
     std::fclose(f);
 }
 
@@ -289,7 +314,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
     size_t bytes = 0;
     std::vector<size_t> off_feat(n_frames), off_acc(n_frames), off_lbl(n_frames), off_ctab(n_frames),
         off_cs(n_frames);
-    long long tiles = 0, centres = 0, rows = 0;
+    long long tiles = 0, tiles64 = 0, centres = 0, rows = 0;
     for (int f = 0; f < n_frames; ++f) {
         const slic_params &p = params[f];
         FrameArgs &a = b->frames[f];
@@ -317,7 +342,9 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         a.tile_base = (int)tiles;
         a.centre_base = (int)centres;
         a.row_base = (int)rows;
+        a.tile_base64 = (int)tiles64;
         tiles += (long long)a.tiles_x * ((p.height + kTileH - 1) / kTileH);
+        tiles64 += (long long)a.tiles_x * ((p.height + 2 * kTileH - 1) / (2 * kTileH));
         centres += (long long)a.ns_c * a.ns_r;
         rows += p.height;
         if (tiles >= (1LL << 31) || centres >= (1LL << 31) || rows >= (1LL << 31)) {
@@ -325,10 +352,12 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
             return bfail(nullptr, SLIC_ERR_INVALID, "batch too large (tiles, centres or rows exceed 2^31)");
         }
         b->win_max = std::max(b->win_max, assign_max_window(S, a.ns_c, a.ns_r));
+        b->win_max64 = std::max(b->win_max64, assign_max_window(S, a.ns_c, a.ns_r, 2 * kTileH));
         {
-            const int span = (kTileW - 1) / S + 2, spanh = (kTileH - 1) / S + 2;
+            const int span = (kTileW - 1) / S + 2, spanh = (kTileH - 1) / S + 2, spanh64 = (2 * kTileH - 1) / S + 2;
             a.box_w = std::min(span, a.ns_c) + 2;
             a.box_h = std::min(spanh, a.ns_r) + 2;
+            a.box_h64 = std::min(spanh64, a.ns_r) + 2;
         }
         b->max_w = std::max(b->max_w, p.width);
         a.strip_base = b->total_units;
@@ -364,6 +393,7 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
     b->tbl_img = b->tbl_ccl + align256(sizeof(CclFrame) * (size_t)n_frames);
     b->tbl_bytes = b->tbl_img + align256(sizeof(const uint8_t *) * (size_t)n_frames);
     b->total_tiles = (int)tiles;
+    b->total_tiles64 = (int)tiles64;
     b->total_centres = (int)centres;
     b->total_rows = (int)rows;
     for (FrameArgs &a : b->frames) {
@@ -475,7 +505,7 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
     if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
     cudaStream_t s = (cudaStream_t)stream;
     const int grid = grid_for(b, b->occupancy);
-    const int grid_pipe = b->pipe ? grid_for(b, pipe_occ(b, b->stages, b->rows)) : grid;
+    const int grid_pipe = b->pipe ? grid_for(b, pipe_occ(b, b->stages, b->rows, b->tile_h)) : grid;
     const int pipe_per_sm = grid_pipe / std::max(1, b->sms);
     // With the pipelined kernel every pass reads features: a conversion
     // pre-pass writes them, and the first pass is pipelined as well.
@@ -522,8 +552,10 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
             }
             if (e != cudaSuccess) break;
             if (b->pipe)
-                e = launch_assign_pipe(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == b->iterations,
-                                       b->stages, b->rows, pipe_per_sm, grid_pipe, b->d_err, b->any_conv ? 1 : 0, s);
+                e = launch_assign_pipe(b->d_frames, b->n, b->tile_h == 64 ? b->total_tiles64 : b->total_tiles,
+                                       b->tile_h == 64 ? b->win_max64 : b->win_max, b->same, pass == b->iterations,
+                                       b->stages, b->rows, b->tile_h, pipe_per_sm, grid_pipe, b->d_err,
+                                       b->any_conv ? 1 : 0, s);
             else
                 e = launch_assign_batch(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == 0 && !warm,
                                         pass == b->iterations, b->smem, grid, s);
@@ -617,35 +649,44 @@ slic_status slic_batch_segment_host(slic_batch b, const uint8_t *const *host_ima
     return SLIC_OK;
 }
 
-slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages, int rows) {
+slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages, int rows, int tile_h) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (ctas_per_sm < 0) return bfail(b, SLIC_ERR_INVALID, "ctas_per_sm must be >= 0");
     if (stages != 0 && (stages < 3 || stages > 4)) return bfail(b, SLIC_ERR_INVALID, "stages must be 0, 3 or 4");
     if (rows != 0 && rows != 1 && rows != 2) return bfail(b, SLIC_ERR_INVALID, "rows must be 0, 1 or 2");
-    if (rows == 2 && !(b->pipe && b->same8))
-        return bfail(b, SLIC_ERR_INVALID, "two row groups need every frame's S to be a multiple of 8");
-    const int st = stages ? stages : b->stages, rw = rows ? rows : b->rows;
-    if ((stages || rows) && b->pipe && assign_pipe_occupancy(b->same, b->win_max, st, rw) == 0)
+    if (tile_h != 0 && tile_h != 32 && tile_h != 64) return bfail(b, SLIC_ERR_INVALID, "tile_h must be 0, 32 or 64");
+    if ((rows == 2 || tile_h == 64) && !(b->pipe && b->same8))
+        return bfail(b, SLIC_ERR_INVALID, "two row groups and 32x64 tiles need every frame's S to be a multiple of 8");
+    const int st = stages ? stages : b->stages, rw = rows ? rows : b->rows, th = tile_h ? tile_h : b->tile_h;
+    if (th == 64 && rw != 2) return bfail(b, SLIC_ERR_INVALID, "32x64 tiles need two row groups per warp");
+    if ((stages || rows || tile_h) && b->pipe && !shape_fits(b, st, rw, th))
         return bfail(b, SLIC_ERR_INVALID, "the pipeline stages do not fit in shared memory");
     b->ctas_per_sm = ctas_per_sm;
     b->stages = st;
     b->rows = rw;
+    b->tile_h = th;
     return SLIC_OK;
 }
 
 slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm, int *stages,
-                               int *rows) {
+                               int *rows, int *tile_h) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
     const std::string key = tune_key(b);
-    int best = 0, best_st = b->stages, best_rw = b->rows;
-    if (cache_path && cache_lookup(cache_path, key, &best, &best_st, &best_rw) && (best_rw == 1 || b->same8)) {
+    int best = 0, best_st = b->stages, best_rw = b->rows, best_th = b->tile_h;
+    auto report = [&]() {
         b->ctas_per_sm = best;
         b->stages = best_st;
         b->rows = best_rw;
+        b->tile_h = best_th;
         if (ctas_per_sm) *ctas_per_sm = best;
         if (stages) *stages = best_st;
         if (rows) *rows = best_rw;
+        if (tile_h) *tile_h = best_th;
+    };
+    if (cache_path && cache_lookup(cache_path, key, &best, &best_st, &best_rw, &best_th) &&
+        (!b->pipe ? best_rw == 1 && best_th == 32 : shape_fits(b, best_st, best_rw, best_th))) {
+        report();
         return SLIC_OK;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -654,34 +695,40 @@ slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stre
         return bfail(b, SLIC_ERR_CUDA, "cudaEventCreate failed");
     float best_ms = 1e30f;
     slic_status st = SLIC_OK;
-    // Search space: row groups per warp x pipeline stages x resident CTAs
-    // per SM (up to what fits).
+    // Search space: tile shape (32x32, or 32x64 with two row groups) x row
+    // groups per warp (pixels per thread and block size) x pipeline stages x
+    // resident CTAs per SM (up to what fits).
     const int st_lo = b->pipe ? 3 : b->stages, st_hi = b->pipe ? 4 : b->stages;
     const int rw_hi = (b->pipe && b->same8) ? 2 : 1;
-    for (int rw = 1; rw <= rw_hi && st == SLIC_OK; ++rw) {
-        for (int nst = st_lo; nst <= st_hi && st == SLIC_OK; ++nst) {
-            if (b->pipe && assign_pipe_occupancy(b->same, b->win_max, nst, rw) == 0) continue;
-            const int occ = std::max(b->occupancy, b->pipe ? pipe_occ(b, nst, rw) : 0);
-            for (int c = 1; c <= occ && st == SLIC_OK; ++c) {
-                b->ctas_per_sm = c;
-                b->stages = nst;
-                b->rows = rw;
-                if ((st = slic_batch_segment(b, stream)) != SLIC_OK) break;  // warm-up
-                float total = 0.0f;
-                for (int rep = 0; rep < 3 && st == SLIC_OK; ++rep) {
-                    cudaEventRecord(e0, s);
-                    st = slic_batch_segment(b, stream);
-                    cudaEventRecord(e1, s);
-                    float ms = 0.0f;
-                    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-                        st = bfail(b, SLIC_ERR_CUDA, "autotune timing failed");
-                    total += ms;
-                }
-                if (st == SLIC_OK && total / 3 < best_ms) {
-                    best_ms = total / 3;
-                    best = c;
-                    best_st = nst;
-                    best_rw = rw;
+    for (int th = 32; th <= 64 && st == SLIC_OK; th += 32) {
+        for (int rw = 1; rw <= rw_hi && st == SLIC_OK; ++rw) {
+            for (int nst = st_lo; nst <= st_hi && st == SLIC_OK; ++nst) {
+                if (b->pipe ? !shape_fits(b, nst, rw, th) : th != 32) continue;
+                const int occ = std::max(b->occupancy, b->pipe ? pipe_occ(b, nst, rw, th) : 0);
+                for (int c = 1; c <= occ && st == SLIC_OK; ++c) {
+                    b->ctas_per_sm = c;
+                    b->stages = nst;
+                    b->rows = rw;
+                    b->tile_h = th;
+                    if ((st = slic_batch_segment(b, stream)) != SLIC_OK) break;  // warm-up
+                    float total = 0.0f;
+                    for (int rep = 0; rep < 3 && st == SLIC_OK; ++rep) {
+                        cudaEventRecord(e0, s);
+                        st = slic_batch_segment(b, stream);
+                        cudaEventRecord(e1, s);
+                        float ms = 0.0f;
+                        if (cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                            st = bfail(b, SLIC_ERR_CUDA, "autotune timing failed");
+                        total += ms;
+                    }
+                    if (st == SLIC_OK && total / 3 < best_ms) {
+                        best_ms = total / 3;
+                        best = c;
+                        best_st = nst;
+                        best_rw = rw;
+                        best_th = th;
+                    }
                 }
             }
         }
@@ -689,24 +736,21 @@ slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stre
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != SLIC_OK) return st;
-    b->ctas_per_sm = best;
-    b->stages = best_st;
-    b->rows = best_rw;
-    if (cache_path) cache_store(cache_path, key, best, best_st, best_rw, best_ms);
-    if (ctas_per_sm) *ctas_per_sm = best;
-    if (stages) *stages = best_st;
-    if (rows) *rows = best_rw;
+    report();
+    if (cache_path) cache_store(cache_path, key, best, best_st, best_rw, best_th, best_ms);
     return SLIC_OK;
 }
 
 slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm,
-                            int *stages, int *rows) {
+                            int *stages, int *rows, int *tile_h) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (total_pixels) *total_pixels = b->total_pixels;
     if (launches) *launches = b->launches;
-    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : b->occupancy;
+    if (ctas_per_sm)  // resident CTAs per SM of the dominant assignment kernel
+        *ctas_per_sm = grid_for(b, b->pipe ? pipe_occ(b, b->stages, b->rows, b->tile_h) : b->occupancy) / b->sms;
     if (stages) *stages = b->pipe ? b->stages : 0;
     if (rows) *rows = b->pipe ? b->rows : 0;
+    if (tile_h) *tile_h = b->pipe ? b->tile_h : 32;
     return SLIC_OK;
 }
 

@@ -108,6 +108,8 @@ constexpr float kResidScale = 65536.0f;
 struct FrameArgs {
     CUtensorMap feat_map;   // features as a [3][H][P] f32 tensor, box 32x32x3 (batched path)
     CUtensorMap ctab_map;   // padded centre table as [(ns_r+2)][(ns_c+2)*kCtabRec] f32, box box_w*kCtabRec x box_h
+    CUtensorMap feat_map64; // the same for 32x64 tiles: box 32x64x3, and
+    CUtensorMap ctab_map64; // box box_w*kCtabRec x box_h64
     ConvConsts conv;
     const uint8_t *rgb;     // [H][W][C]
     float *feat;            // 3 planes [H][P]; plane stride H*P
@@ -131,6 +133,7 @@ struct FrameArgs {
     int centre_base;        // batch's concatenated lists (0 for a single
     int row_base;           // frame)
     int box_w, box_h;       // window box of the centre-table copies (cells)
+    int tile_base64, box_h64;  // the frame's first 32x64 tile; window rows of a 32x64 tile
     int32_t *assign_out;    // labels of the pipelined last pass (lbl_tmp when the
     int assign_vec;         // fused connectivity follows); 1: 4-pixel vector stores
     int strips_x;           // fused connectivity: strips per row and first
@@ -144,7 +147,7 @@ struct FrameArgs {
 
 // Shared memory for one assignment CTA whose tile spans at most win_n cells.
 size_t assign_smem_bytes(int win_n, bool first);
-int assign_max_window(int S, int ns_c, int ns_r);
+int assign_max_window(int S, int ns_c, int ns_r, int tile_h = 32);
 bool assign_direct_acc(int win_n);
 // Resident CTAs per SM of the batched assignment kernel.
 int assign_batch_occupancy(bool same, size_t smem);
@@ -198,14 +201,16 @@ cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_cent
 // 64-register build); rows = 2: 128 threads, 8 pixels per thread (two row
 // groups in one cell row: every frame's S a multiple of 8, `same` set).
 // check_stop: some frame has a stopping threshold (its tiles are then skipped
-// once it has stopped).
+// once it has stopped). tile_h = 64 (rows = 2 only): 32x64 tiles, 256
+// threads (8 warps of two row groups); total_tiles and win_max are then
+// those of 32x64 tiles.
 cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool last,
-                               int nst, int rows, int ctas_per_sm, int grid, int *err, int check_stop,
+                               int nst, int rows, int tile_h, int ctas_per_sm, int grid, int *err, int check_stop,
                                cudaStream_t s);
 // Shared memory and resident CTAs per SM of the pipelined kernel with nst
-// (3..4) stages and 1 or 2 row groups per warp.
-size_t assign_pipe_smem_bytes(int win_n, bool last, int nst, int rows);
-int assign_pipe_occupancy(bool same, int win_n, int nst, int rows);
+// (3..4) stages, 1 or 2 row groups per warp and tiles of tile_h rows.
+size_t assign_pipe_smem_bytes(int win_n, bool last, int nst, int rows, int tile_h = 32);
+int assign_pipe_occupancy(bool same, int win_n, int nst, int rows, int tile_h = 32);
 // Batched RGB -> features pre-pass (the pipelined path's first pass reads
 // the features it writes).
 cudaError_t launch_convert_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w, cudaStream_t s);

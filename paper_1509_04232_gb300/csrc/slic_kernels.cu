@@ -57,10 +57,14 @@ __device__ __forceinline__ int div_s(int x, unsigned s_mul, int S) {
 
 // Index of the frame whose [base, next base) range holds `idx` (frames are
 // sorted by base; base of frame 0 is 0).
-enum BaseField { kTileBase, kCentreBase, kRowBase, kStripBase };
+enum BaseField { kTileBase, kCentreBase, kRowBase, kStripBase, kTileBase64 };
 template <BaseField F>
 __device__ __forceinline__ int base_of(const FrameArgs &a) {
-    return F == kTileBase ? a.tile_base : F == kCentreBase ? a.centre_base : F == kRowBase ? a.row_base : a.strip_base;
+    return F == kTileBase ? a.tile_base
+           : F == kCentreBase ? a.centre_base
+           : F == kRowBase ? a.row_base
+           : F == kStripBase ? a.strip_base
+                             : a.tile_base64;
 }
 template <BaseField F>
 __device__ __forceinline__ int find_frame(const FrameArgs *frames, int n, int idx) {
@@ -291,9 +295,9 @@ __global__ void k_zero_acc(long long *acc, int n) {
 
 // Window of cells a tile can reference: the cells its pixels fall in plus
 // one ring, clamped to what the grid can offer.
-int assign_max_window(int S, int ns_c, int ns_r) {
+int assign_max_window(int S, int ns_c, int ns_r, int tile_h) {
     const int span = (kTileW - 1) / S + 2;  // cells a 32-px run can touch, misaligned
-    const int spanh = (kTileH - 1) / S + 2;
+    const int spanh = (tile_h - 1) / S + 2;
     const int wx = (span < ns_c ? span : ns_c) + 2;
     const int wy = (spanh < ns_r ? spanh : ns_r) + 2;
     return wx * wy;
@@ -690,20 +694,23 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_batch(const FrameArgs *f
 // Pipelined assignment for the passes after the first (batched path)
 // ---------------------------------------------------------------------------
 //
-// Persistent CTAs walk the batch's tiles with two shared-memory stages. While
-// the CTA evaluates tile i from stage s, one thread has already issued the
-// two tensor-map copies of tile i+1 into stage s^1 (cp.async.bulk.tensor,
-// completion counted on the stage's mbarrier): the 32x32x3 box of features
-// and the box of 32-byte centre records around the tile from the frame's
-// padded centre table (its sentinel ring makes every window in-bounds).
-// Warp w evaluates rows 4w..4w+3 of the tile, lane l the 4 pixels at column
-// 4*(l%8) of row l/8, so each quarter-warp reads one 128-byte row without
-// bank conflicts. One barrier per tile separates the accumulation into the
-// stage's private sums from their flush to the global sums.
+// Persistent CTAs walk the batch's tiles (32 columns by TH = 32 or 64 rows)
+// through 3 or 4 shared-memory stages. While the warps evaluate tile i, one
+// thread has already issued the two tensor-map copies of the next tiles
+// (cp.async.bulk.tensor, completion counted on the stage's mbarrier): the
+// 32xTHx3 box of features and the box of 48-byte centre records around the
+// tile from the frame's padded centre table (its sentinel ring makes every
+// window in-bounds). Lane l of a warp evaluates the 4 pixels at column
+// 4*(l%8) of row l/8 of each of its row groups (rows 4w..4w+3 with one row
+// group per warp, 8w..8w+3 and 8w+4..8w+7 with two), so each quarter-warp
+// reads one 128-byte row without bank conflicts. Stage reuse, the private
+// per-tile sums and their flush to the global sums are ordered by mbarriers
+// alone: there is no CTA-wide barrier inside the tile loop.
 
 namespace {
 
-constexpr size_t kStageFeatBytes = (size_t)3 * kTileH * kTileW * 4;  // 12288
+constexpr size_t kStageFeatBytes = (size_t)3 * kTileH * kTileW * 4;  // 12288 (32x32 tile)
+__host__ __device__ constexpr size_t stage_feat_bytes(int th) { return (size_t)3 * th * kTileW * 4; }
 constexpr int kMaxStages = 4;
 constexpr int kAccSets = 2;    // accumulator sets in flight: one filled while the other is flushed
 constexpr int kHdrSlots = 8;   // tile-header ring (>= stages + 2)
@@ -853,6 +860,7 @@ struct __align__(16) TileGeom {
     int skip;              // 1: the frame passed its stopping test (no copy was issued)
 };
 
+template <int TH>
 __device__ __forceinline__ TileGeom tile_geom(const FrameArgs &a, int local) {
     TileGeom g;
     g.W = a.W;
@@ -869,9 +877,9 @@ __device__ __forceinline__ TileGeom tile_geom(const FrameArgs &a, int local) {
     g.skip = 0;
     const int ty = local / a.tiles_x, tx = local - ty * a.tiles_x;
     g.tx0 = tx * kTileW;
-    g.ty0 = ty * kTileH;
+    g.ty0 = ty * TH;
     const int ccx0 = div_s(g.tx0, a.s_mul, a.S), ccx1 = div_s(min(g.tx0 + kTileW - 1, a.W - 1), a.s_mul, a.S);
-    const int ccy0 = div_s(g.ty0, a.s_mul, a.S), ccy1 = div_s(min(g.ty0 + kTileH - 1, a.H - 1), a.s_mul, a.S);
+    const int ccy0 = div_s(g.ty0, a.s_mul, a.S), ccy1 = div_s(min(g.ty0 + TH - 1, a.H - 1), a.s_mul, a.S);
     g.wx0 = ccx0 - 1;
     g.wy0 = ccy0 - 1;
     g.wnx = ccx1 - ccx0 + 3;
@@ -882,12 +890,14 @@ __device__ __forceinline__ TileGeom tile_geom(const FrameArgs &a, int local) {
 
 // One thread: arm the stage's mbarrier with the byte count of both boxes
 // and issue the two tensor copies.
+template <int TH>
 __device__ __forceinline__ void issue_tile(const FrameArgs &a, const TileGeom &g, unsigned char *stage,
                                            uint64_t *bar) {
-    const unsigned cen_bytes = (unsigned)a.box_w * (unsigned)a.box_h * (unsigned)(kCtabRec * 4);
-    mbar_expect_tx(bar, (unsigned)kStageFeatBytes + cen_bytes);
-    tma_load_3d(stage, &a.feat_map, g.tx0, g.ty0, 0, bar);
-    tma_load_2d(stage + kStageFeatBytes, &a.ctab_map, (g.wx0 + 1) * kCtabRec, g.wy0 + 1, bar);
+    const unsigned cen_bytes = (unsigned)a.box_w * (unsigned)(TH == 64 ? a.box_h64 : a.box_h) * (unsigned)(kCtabRec * 4);
+    mbar_expect_tx(bar, (unsigned)stage_feat_bytes(TH) + cen_bytes);
+    tma_load_3d(stage, TH == 64 ? &a.feat_map64 : &a.feat_map, g.tx0, g.ty0, 0, bar);
+    tma_load_2d(stage + stage_feat_bytes(TH), TH == 64 ? &a.ctab_map64 : &a.ctab_map, (g.wx0 + 1) * kCtabRec,
+                g.wy0 + 1, bar);
 }
 
 // Add tile j's private sums (the 8 copies of accumulator set j % 2, one per
@@ -896,7 +906,7 @@ __device__ __forceinline__ void issue_tile(const FrameArgs &a, const TileGeom &g
 // four words of every copy as one 16-byte load. The flushing warp waits
 // until every warp has filled the set and reports it free afterwards; the
 // others return at once. False when the wait timed out.
-template <int NW>
+template <int NW, int NCOPY>
 __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, unsigned *wacc0, size_t acc_words, int win_max,
                                            uint64_t *acc_done, uint64_t *acc_free, int j, int warp, int lane) {
     if (warp != j % NW) return true;
@@ -915,7 +925,10 @@ __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, unsigned *wacc0,
         long long l = 0, a = 0, b = 0;
         unsigned xs = 0, ys = 0, n = 0;
 #pragma unroll
-        for (int q = 0; q < kWarps; ++q) {
+        for (int q = 0; q < NCOPY; ++q) {
+            // copy q: rows 4q .. 4q+3 of the tile; its y field counts from the
+            // tile's first row (32-row tiles) or from 4q (64-row tiles, whose
+            // offsets would not fit the 12-bit field)
             uint4 *p = reinterpret_cast<uint4 *>(ws + (size_t)q * win_max * 4 + idx);
             const uint4 v = *p;
             *p = make_uint4(0u, 0u, 0u, 0u);
@@ -923,7 +936,7 @@ __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, unsigned *wacc0,
             a += (int)v.y;
             b += (int)v.z;
             xs += v.w & 0xFFFu;
-            ys += (v.w >> 12) & 0xFFFu;
+            ys += ((v.w >> 12) & 0xFFFu) + (NCOPY > kWarps ? 4u * (unsigned)q * (v.w >> 24) : 0u);
             n += v.w >> 24;
         }
         if (n != 0) {
@@ -944,35 +957,40 @@ __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, unsigned *wacc0,
 
 }  // namespace
 
-size_t assign_pipe_smem_bytes(int win_n, bool last, int nst, int rows) {
+size_t assign_pipe_smem_bytes(int win_n, bool last, int nst, int rows, int tile_h) {
     (void)rows;  // the sums keep one copy per 128 pixels whatever the warp count
-    const size_t stage = kStageFeatBytes + (((size_t)win_n * kCtabRec * 4 + 127) & ~(size_t)127);
-    const size_t acc = last ? 0 : (size_t)kWarps * win_n * 4 * sizeof(int);
+    const size_t stage = stage_feat_bytes(tile_h) + (((size_t)win_n * kCtabRec * 4 + 127) & ~(size_t)127);
+    const size_t acc = last ? 0 : (size_t)kWarps * (tile_h / kTileH) * win_n * 4 * sizeof(int);
     // nst stages, the accumulator sets, the mbarriers, the header ring, two
     // flags and base alignment
     return (size_t)nst * stage + kAccSets * acc + (size_t)(2 * kMaxStages + 2 * kAccSets) * 8 +
            (size_t)kHdrSlots * sizeof(TileGeom) + 16 + 128;
 }
 
-template <bool LAST, bool SAME, int MINB, int ROWS>
-__global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const FrameArgs *frames, int n_frames,
-                                                                       int total_tiles, int win_max, int nst,
-                                                                       int *err, int check_stop) {
+template <bool LAST, bool SAME, int MINB, int ROWS, int TH>
+__global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB) k_assign_pipe(const FrameArgs *frames,
+                                                                                   int n_frames, int total_tiles,
+                                                                                   int win_max, int nst, int *err,
+                                                                                   int check_stop) {
     // ROWS = 1: 8 warps, warp w evaluates rows 4w..4w+3 of the tile.
-    // ROWS = 2: 4 warps, warp w evaluates rows 8w..8w+3 and 8w+4..8w+7 (the
-    // same cell row when S is a multiple of 8), sharing the centre loads and
-    // the per-tile work between 8 pixels per thread.
+    // ROWS = 2: TH/8 warps, warp w evaluates rows 8w..8w+3 and 8w+4..8w+7
+    // (the same cell row when S is a multiple of 8), sharing the centre loads
+    // and the per-tile work between 8 pixels per thread. TH: tile rows (32,
+    // or 64 with ROWS = 2).
     static_assert(ROWS == 1 || (ROWS == 2 && SAME), "two row groups need cell-aligned 4-pixel groups");
-    constexpr int NW = kWarps / ROWS, NT = NW * 32;
+    static_assert(TH == 32 || (TH == 64 && ROWS == 2), "32x64 tiles with two row groups only");
+    constexpr int NW = kWarps / ROWS * (TH / 32), NT = NW * 32;
+    constexpr int NCOPY = NW * ROWS;  // private sums: one copy per 128 pixels (rows 4q .. 4q+3)
+    constexpr size_t kFeat = stage_feat_bytes(TH);
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     // Tensor copies want 128-byte aligned destinations.
     unsigned char *smem_raw =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~(uintptr_t)127);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const size_t stage_bytes = kStageFeatBytes + (((size_t)win_max * kCtabRec * 4 + 127) & ~(size_t)127);
+    const size_t stage_bytes = kFeat + (((size_t)win_max * kCtabRec * 4 + 127) & ~(size_t)127);
     // One private copy of the sums per 128 pixels (per warp and row group),
     // so a copy's packed x / y / count fields cannot overflow.
-    const size_t acc_words = LAST ? 0 : (size_t)kWarps * win_max * 4;
+    const size_t acc_words = LAST ? 0 : (size_t)NCOPY * win_max * 4;
     unsigned *const wacc0 = reinterpret_cast<unsigned *>(smem_raw + (size_t)nst * stage_bytes);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)nst * stage_bytes + kAccSets * acc_words * 4);
     uint64_t *empty = full + kMaxStages;       // stage released by every warp (count NW)
@@ -1015,8 +1033,8 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
         if (t >= total_tiles) return true;
         if (*reinterpret_cast<volatile int *>(&g_abort_copies)) return false;
         if (use > 0 && !mbar_wait(&empty[q], (use - 1) & 1)) return false;
-        const int f = find_frame<kTileBase>(frames, n_frames, t);
-        TileGeom g = tile_geom(frames[f], t - frames[f].tile_base);
+        const int f = find_frame<TH == 64 ? kTileBase64 : kTileBase>(frames, n_frames, t);
+        TileGeom g = tile_geom<TH>(frames[f], t - base_of<TH == 64 ? kTileBase64 : kTileBase>(frames[f]));
         g.f = f;
         g.skip = !LAST && check_stop && frame_stopped(frames[f]) ? 1 : 0;
         if (g.skip) g.H = 0;  // no pixel of the tile is evaluated or summed
@@ -1024,7 +1042,7 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
         if (g.skip)
             mbar_arrive(&full[q]);  // a stopped frame's tile: no copy, the stage completes at once
         else
-            issue_tile(frames[f], g, smem_raw + (size_t)q * stage_bytes, &full[q]);
+            issue_tile<TH>(frames[f], g, smem_raw + (size_t)q * stage_bytes, &full[q]);
         atomicMax(&flags[1], j);
         return true;
     };
@@ -1076,7 +1094,7 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
         const int W = g.W, H = g.H, S = g.S, ns_c = g.ns_c;
         const unsigned s_mul = g.s_mul;
         const float *feat = reinterpret_cast<const float *>(stage_s);
-        const float *cen = reinterpret_cast<const float *>(stage_s + kStageFeatBytes);
+        const float *cen = reinterpret_cast<const float *>(stage_s + kFeat);
         const int x = tx0 + lx;
         int y[ROWS];
         bool row_ok[ROWS];
@@ -1087,9 +1105,9 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
             y[r] = ty0 + ly;
             row_ok[r] = (y[r] < H) && (x < W);  // (H = 0 in a skipped tile's header)
             if (row_ok[r]) {
-                const float4 v0 = *reinterpret_cast<const float4 *>(feat + (0 * kTileH + ly) * kTileW + lx);
-                const float4 v1 = *reinterpret_cast<const float4 *>(feat + (1 * kTileH + ly) * kTileW + lx);
-                const float4 v2 = *reinterpret_cast<const float4 *>(feat + (2 * kTileH + ly) * kTileW + lx);
+                const float4 v0 = *reinterpret_cast<const float4 *>(feat + (0 * TH + ly) * kTileW + lx);
+                const float4 v1 = *reinterpret_cast<const float4 *>(feat + (1 * TH + ly) * kTileW + lx);
+                const float4 v2 = *reinterpret_cast<const float4 *>(feat + (2 * TH + ly) * kTileW + lx);
                 f0[r][0] = v0.x; f0[r][1] = v0.y; f0[r][2] = v0.z; f0[r][3] = v0.w;
                 f1[r][0] = v1.x; f1[r][1] = v1.y; f1[r][2] = v1.z; f1[r][3] = v1.w;
                 f2[r][0] = v2.x; f2[r][1] = v2.y; f2[r][2] = v2.z; f2[r][3] = v2.w;
@@ -1230,10 +1248,11 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
             }
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
-                const int ly = ly0 + 4 * r;
+                // copy q = warp * ROWS + r holds rows 4q .. 4q+3 (see flush_tile for y)
                 unsigned *my = wacc0 + (size_t)set * acc_words + (size_t)(warp * ROWS + r) * win_max * 4;
                 unsigned v[kPPT][4];
-                const unsigned xyn = (unsigned)lx + ((unsigned)ly << 12) + (1u << 24);
+                const unsigned yo = TH == 64 ? (unsigned)(lane >> 3) : (unsigned)(ly0 + 4 * r);
+                const unsigned xyn = (unsigned)lx + (yo << 12) + (1u << 24);
 #pragma unroll
                 for (int j = 0; j < kPPT; j += 2) {
                     fix_round2(f0[r][j], f0[r][j + 1], fs, v[j][0], v[j + 1][0]);
@@ -1261,7 +1280,8 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_done[set]);
             // Flush the previous tile's sums (one warp per tile).
-            if (it > 0 && !flush_tile<NW>(hdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
+            if (it > 0 &&
+                !flush_tile<NW, NCOPY>(hdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
                 if (lane == 0) {
                     *abort_flag = 1;
                     atomicOr(err, 1);
@@ -1272,7 +1292,7 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
         }
     }
     if (!LAST && ok && it > 0 &&
-        !flush_tile<NW>(hdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
+        !flush_tile<NW, NCOPY>(hdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
         if (lane == 0) {
             *abort_flag = 1;
             atomicOr(err, 1);
@@ -1289,19 +1309,20 @@ __global__ void __launch_bounds__(kThreads / ROWS, MINB) k_assign_pipe(const Fra
 
 // Resident CTAs per SM of one instantiation (the query honours the
 // kernel's dynamic shared memory opt-in, so that is raised first).
-template <bool L, bool SM, int MINB, int ROWS>
+template <bool L, bool SM, int MINB, int ROWS, int TH = 32>
 static int pipe_occupancy_of(size_t smem) {
     int blocks = 0;
-    if (cudaFuncSetAttribute(k_assign_pipe<L, SM, MINB, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_assign_pipe<L, SM, MINB, ROWS, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_assign_pipe<L, SM, MINB, ROWS>, kThreads / ROWS,
-                                                      smem) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_assign_pipe<L, SM, MINB, ROWS, TH>,
+                                                      kThreads / ROWS * (TH / 32), smem) != cudaSuccess)
         return 0;
     return blocks;
 }
 
-int assign_pipe_occupancy(bool same, int win_n, int nst, int rows) {
-    const size_t sm = assign_pipe_smem_bytes(win_n, false, nst, rows);
+int assign_pipe_occupancy(bool same, int win_n, int nst, int rows, int tile_h) {
+    const size_t sm = assign_pipe_smem_bytes(win_n, false, nst, rows, tile_h);
+    if (tile_h == 64) return rows == 2 && same ? pipe_occupancy_of<false, true, 2, 2, 64>(sm) : 0;
     if (rows == 2) return same ? pipe_occupancy_of<false, true, 4, 2>(sm) : 0;
     // The 4-CTA build (64 registers) where shared memory allows, else the 3-CTA build.
     const int o4 = same ? pipe_occupancy_of<false, true, 4, 1>(sm) : pipe_occupancy_of<false, false, 4, 1>(sm);
@@ -1309,26 +1330,33 @@ int assign_pipe_occupancy(bool same, int win_n, int nst, int rows) {
     return o4 >= 4 ? o4 : o3;
 }
 
-template <bool L, bool SM, int MINB, int ROWS>
+template <bool L, bool SM, int MINB, int ROWS, int TH = 32>
 static cudaError_t launch_pipe_as(const FrameArgs *d_frames, int n, int total_tiles, int win_max, int nst, int grid,
                                   size_t smem, int *err, int check_stop, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_assign_pipe<L, SM, MINB, ROWS>,
+    cudaError_t e = cudaFuncSetAttribute(k_assign_pipe<L, SM, MINB, ROWS, TH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_assign_pipe<L, SM, MINB, ROWS><<<grid, kThreads / ROWS, smem, s>>>(d_frames, n, total_tiles, win_max, nst, err,
-                                                                           check_stop);
+    k_assign_pipe<L, SM, MINB, ROWS, TH><<<grid, kThreads / ROWS * (TH / 32), smem, s>>>(d_frames, n, total_tiles,
+                                                                                           win_max, nst, err,
+                                                                                           check_stop);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool last,
-                               int nst, int rows, int ctas_per_sm, int grid, int *err, int check_stop,
+                               int nst, int rows, int tile_h, int ctas_per_sm, int grid, int *err, int check_stop,
                                cudaStream_t s) {
     if (grid > total_tiles) grid = total_tiles;
     if (grid < 1) grid = 1;
     if (nst < 3) nst = 3;
     if (nst > kMaxStages) nst = kMaxStages;
     if (rows == 2 && !same) return cudaErrorInvalidValue;
-    const size_t smem = assign_pipe_smem_bytes(win_max, last, nst, rows);
+    if (tile_h != 32 && (tile_h != 64 || rows != 2)) return cudaErrorInvalidValue;
+    const size_t smem = assign_pipe_smem_bytes(win_max, last, nst, rows, tile_h);
+    if (tile_h == 64)  // 256 threads at 128 registers: 2 CTAs per SM
+        return last ? launch_pipe_as<true, true, 2, 2, 64>(d_frames, n, total_tiles, win_max, nst, grid, smem, err,
+                                                           check_stop, s)
+                    : launch_pipe_as<false, true, 2, 2, 64>(d_frames, n, total_tiles, win_max, nst, grid, smem, err,
+                                                            check_stop, s);
     if (rows == 2)
         return last ? launch_pipe_as<true, true, 4, 2>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s)
                     : launch_pipe_as<false, true, 4, 2>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s);

@@ -98,15 +98,15 @@ def test_autotune_writes_and_reuses_cache(slic_gpu, tmp_path):
     bs = pkg.BatchSegmenter(frames, iterations=2)
     bs.bind([_cuda(synth.voronoi_frame(f["width"], f["height"], 20, 6.0, 5)) for f in frames])
     cache = str(tmp_path / "tune.jsonl")
-    c1, st1, rw1 = bs.autotune(cache)
-    assert c1 >= 1 and 3 <= st1 <= 4 and rw1 in (1, 2)
+    c1, st1, rw1, th1 = bs.autotune(cache)
+    assert c1 >= 1 and 3 <= st1 <= 4 and rw1 in (1, 2) and th1 in (32, 64)
     line = json.loads(open(cache).read().splitlines()[0])
-    assert line["ctas_per_sm"] == c1 and line["stages"] == st1 and line["rows"] == rw1
+    assert line["ctas_per_sm"] == c1 and line["stages"] == st1 and line["rows"] == rw1 and line["tile_h"] == th1
     assert "640x480s16" in line["key"]
-    bs.set_tuning(0, 3 if st1 != 3 else 4, 1)
-    assert bs.autotune(cache) == (c1, st1, rw1)   # served from the cache
+    bs.set_tuning(0, 3 if st1 != 3 else 4, 1, 32)
+    assert bs.autotune(cache) == (c1, st1, rw1, th1)   # served from the cache
     assert len(open(cache).read().splitlines()) == 1
-    assert bs.info[2] == c1 and bs.info[3] == st1 and bs.info[4] == rw1
+    assert bs.info[2:] == (c1, st1, rw1, th1)
 
 
 @pytest.mark.parametrize("stages", [3, 4])
@@ -137,12 +137,16 @@ def test_pipeline_depth_is_bit_exact(slic_gpu, stages):
             bs.set_tuning(0, bad)
     with pytest.raises(pkg.SlicError):        # S = 12 is not a multiple of 8
         bs.set_tuning(0, stages, 2)
+    with pytest.raises(pkg.SlicError):
+        bs.set_tuning(0, stages, 1, 64)
 
 
 @pytest.mark.parametrize("stages", [3, 4])
 def test_two_row_groups_are_bit_exact(slic_gpu, stages):
-    """The 128-thread, 8-pixels-per-thread build gives the single-frame
-    results bit for bit (S multiples of 8, ragged sizes included)."""
+    """The 8-pixels-per-thread builds give the single-frame results bit for
+    bit (S multiples of 8, ragged sizes included), with 32x32 tiles (128
+    threads) and 32x64 tiles (256 threads; the 211-row frame ends in a
+    partial 32x64 tile, the 480-row one in a 32x32 half)."""
     import torch
     pkg = slic_gpu
     frames = [dict(width=1920, height=1080, S=16), dict(width=333, height=211, S=8),
@@ -151,11 +155,11 @@ def test_two_row_groups_are_bit_exact(slic_gpu, stages):
             _cuda(synth.voronoi_frame(640, 480, 30, 6.0, 10))]
     bs = pkg.BatchSegmenter(frames, iterations=4)
     bs.bind(imgs)
-    for cps in (0, 2):
-        bs.set_tuning(cps, stages, 2)
+    for cps, th in ((0, 32), (2, 32), (0, 64), (1, 64)):
+        bs.set_tuning(cps, stages, 2, th)
         labels, centres = bs.segment()
         bs.status()
-        assert bs.info[4] == 2
+        assert bs.info[4] == 2 and bs.info[5] == th
         for i, f in enumerate(frames):
             seg = pkg.Segmenter(f["width"], f["height"], S=f["S"], m=f.get("m", 10.0), iterations=4)
             l1, c1 = seg.segment(imgs[i])
