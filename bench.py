@@ -50,7 +50,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 W, H, S, M = 1920, 1080, 16, 10.0
-ITERS = 5          # the plain throughput configuration (configs[1])
+ITERS = 5          # the plain throughput configuration: 32 frames 1920x1080, 5 iterations
 FULL_ITERS = 10    # the full-iteration result the agreement bar refers to
 EVAL_FRAMES = 64   # the evaluation set of the agreement bar
 AGREE_BAR = 0.99
@@ -251,6 +251,12 @@ def run_ours(args):
     build.build_all()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
+    if args.mixed_only:  # the mixed batch alone (a profiling command)
+        stream = torch.cuda.Stream(device=dev)
+        if rank == 0:
+            print(json.dumps({"mixed_batch": mixed_batch_throughput(args, pkg, stream, dev)}))
+        return 0
+
     B = args.batch
     seeds = frame_seeds(B, rank)
     host = torch.empty((B, H, W, 3), dtype=torch.uint8).pin_memory()
@@ -262,13 +268,20 @@ def run_ours(args):
     tune_cache = os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl")
 
     # --- the agreement bar: iteration sweeps of both methods on the eval set ---
-    quality, net_small = agreement_sweeps(args, pkg, dev, stream)
+    if args.iterations is not None:  # a fixed count (profiling commands): no sweep, no learned leg
+        quality, net_small = {"plain_iterations_at_99": args.iterations, "sweep": "skipped (--iterations)"}, None
+    else:
+        quality, net_small = agreement_sweeps(args, pkg, dev, stream)
     n_plain = quality["plain_iterations_at_99"]
     n_learned = quality.get("learned_iterations_at_99")
 
     # --- the plain path at its iteration count, autotuned, one graph per step ---
     bs = _plain_batch(pkg, frames, n_plain, dev)
-    tuning = bs.autotune(tune_cache, stream=stream)
+    if args.tuning:  # a fixed launch shape (profiling commands): no autotuning
+        tuning = tuple(int(v) for v in args.tuning.split(","))
+        bs.set_tuning(*tuning)
+    else:
+        tuning = bs.autotune(tune_cache, stream=stream)
     ctas_per_sm, stages, rows, tile_h = tuning
     K_EFF = bs.K_eff[0]
     n0 = bs.info[1]
@@ -403,13 +416,13 @@ def run_ours(args):
     for p_ in pair:
         p_[0].close()
 
-    # --- context: plain throughput at 5 iterations (configs[1]) ---
+    # --- context: plain throughput at 5 iterations ---
     b5 = _plain_batch(pkg, frames, ITERS, dev, tuning)
     g5 = _capture(lambda: b5.segment(stream=stream), stream)
     ms5 = _graph_ms(g5, stream, args, world, dev)
     thr5 = {"iterations": ITERS, "frames_per_s": world * B / (ms5 / 1e3), "ms_per_step": ms5,
             "megapixels_per_s": world * B * N / 1e6 / (ms5 / 1e3),
-            "agreement_with_10_iterations": quality["plain_agreement_by_iterations"].get(str(ITERS))}
+            "agreement_with_10_iterations": quality.get("plain_agreement_by_iterations", {}).get(str(ITERS))}
     b5.close()
 
     single = None if args.no_single else single_frame_latency(args, pkg, stream, dev, images[0])
@@ -479,8 +492,8 @@ def run_ours(args):
 
 def single_frame_latency(args, pkg, stream, dev, image):
     """slic_segment on one frame at a time, graph-captured: 1920x1080 at S=16
-    and 640x480 at K=1200 (the paper's image size), m=10, 5 iterations
-    (configs[1]); per-call latency percentiles over replays."""
+    and 640x480 at K=1200 (the paper's image size), m=10, 5 iterations;
+    per-call latency percentiles over replays."""
     import torch
     from paper_1509_04232_gb300 import synth
     out = {}
@@ -513,7 +526,7 @@ def single_frame_latency(args, pkg, stream, dev, image):
 
 
 def video_context(args, pkg, dev, net_small):
-    """configs[4]: 120 frames of 3840x2160 (regions moving 0-4 px per frame,
+    """Video: 120 frames of 3840x2160 (regions moving 0-4 px per frame,
     colour drift 2, noise 6), S=16, m=10, 8 frames per launch, 2 iterations
     per batch after a 10-iteration first batch: the previous batch's
     centres, the grid, and (with a trained network) the learned warm start
@@ -768,6 +781,13 @@ def main(argv=None):
     ap.add_argument("--no-mixed", action="store_true", help="skip the 256-frame mixed-resolution batch")
     ap.add_argument("--no-options", action="store_true",
                     help="skip the Sec. 2 options (stopping test, seed perturbation)")
+    ap.add_argument("--iterations", type=int, default=None,
+                    help="time the plain path at this iteration count instead of the one the agreement sweep "
+                         "finds (skips the sweep and the learned leg; for profiling)")
+    ap.add_argument("--tuning", default=None, metavar="CTAS,STAGES,ROWS,TILE_H",
+                    help="launch shape of the assignment passes instead of autotuning (for profiling)")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="run only the 256-frame mixed batch and print its line (for profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
