@@ -278,11 +278,11 @@ def run_ours(args):
     # --- the plain path at its iteration count, autotuned, one graph per step ---
     bs = _plain_batch(pkg, frames, n_plain, dev)
     if args.tuning:  # a fixed launch shape (profiling commands): no autotuning
-        tuning = tuple(int(v) for v in args.tuning.split(","))
+        tuning = (tuple(int(v) for v in args.tuning.split(",")) + (0,))[:5]
         bs.set_tuning(*tuning)
     else:
         tuning = bs.autotune(tune_cache, stream=stream)
-    ctas_per_sm, stages, rows, tile_h = tuning
+    ctas_per_sm, stages, rows, tile_h, fused = tuning
     K_EFF = bs.K_eff[0]
     n0 = bs.info[1]
     graph = _capture(lambda: bs.segment(stream=stream), stream)
@@ -330,33 +330,43 @@ def run_ours(args):
         launches_per_step = 0  # (the learned step: counted below)
 
     # --- dominant kernel: event-timed replays of the plain step ---
-    # Each replay records one event pair per assignment launch, in pass
-    # order 0..n; passes 1..n-1 run the dominant kernel (the pipelined middle
-    # pass, k_assign_pipe<0,1,MINB,ROWS>: MINB = 4 for the two-row-group
-    # build and for the one-row 64-register build the autotuner picks at 4
-    # CTAs per SM, else 3).
+    # Each replay records one event pair per assignment launch. One launch
+    # per pass: pass order 0..n, and passes 1..n-1 run the dominant kernel
+    # (the pipelined middle pass, k_assign_pipe<0,1,MINB,ROWS,TILE_H>: MINB
+    # = 2 for 32x64 tiles, 4 for the 32x32 two-row-group build and for the
+    # one-row 64-register build the autotuner picks at 4 CTAs per SM, else
+    # 3). Fused passes: the fused launch (passes 0..n-1 with their updates,
+    # k_assign_multi<1,MINB,ROWS,TILE_H>) and the last pass; the fused launch
+    # is the dominant kernel, with n passes' work.
     pb = bs if method["name"] == "plain" else _plain_batch(pkg, frames, n_plain, dev, tuning)
     pkg.slic_batch_profile_enable(pb.handle, True)
     graph_prof = _capture(lambda: pb.segment(stream=stream), stream)
     pkg.slic_batch_profile_enable(pb.handle, False)
     minb = 2 if tile_h == 64 else (4 if (rows == 2 or ctas_per_sm >= 4) else 3)
-    kname = f"k_assign_pipe<0,1,{minb},{rows},{tile_h}>"
+    fused_dom = bool(fused) and n_plain >= 1
+    kname = (f"k_assign_multi<1,{minb},{rows},{tile_h}>" if fused_dom else
+             f"k_assign_pipe<0,1,{minb},{rows},{tile_h}>")
+    passes_per_launch = n_plain if fused_dom else 1
     mid = []
     for _ in range(max(3, min(args.steps, 10))):
         with torch.cuda.stream(stream):
             graph_prof.replay()
         torch.cuda.synchronize()
         t = pkg.slic_batch_profile_times(pb.handle)
-        t = t[-(n_plain + 1):]  # this replay's passes
-        mid += [t[p] for p in (range(1, n_plain) if n_plain >= 2 else range(n_plain + 1))]
+        if fused_dom:
+            mid.append(t[-2])  # this replay's fused launch
+        else:
+            t = t[-(n_plain + 1):]  # this replay's passes
+            mid += [t[p] for p in (range(1, n_plain) if n_plain >= 2 else range(n_plain + 1))]
     mid_ms = float(np.mean(mid))
     N = W * H
     # Algorithmic work of one middle-pass launch (all B frames): 12 bytes of
     # features read per pixel (centre windows and sums are < 1%), 18 square
-    # roots per pixel (2 for each of the 9 candidates of Eq. 1).
-    bytes_per_launch = B * N * 12
+    # roots per pixel (2 for each of the 9 candidates of Eq. 1); a fused
+    # launch does that for each of its passes.
+    bytes_per_launch = B * N * 12 * passes_per_launch
     achieved_gbs = bytes_per_launch / (mid_ms / 1e3) / 1e9
-    sqrt_per_launch = B * N * 18
+    sqrt_per_launch = B * N * 18 * passes_per_launch
     peaks, peak_kind = measured_peaks()
     sm_max = clock_info.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     xu_peak = 16 * sms * sm_max * 1e6 / 1e12
@@ -368,7 +378,7 @@ def run_ours(args):
         # capture of the current kernel (removed whenever the kernel changes)
         kv = dict(line.split(None, 1) for line in open(tfile) if line.strip() and not line.startswith("#"))
         if kv.get("kernel", "").strip() == kname:
-            traffic = float(kv["dram_bytes_per_frame"]) * B
+            traffic = float(kv["dram_bytes_per_frame"]) * B * passes_per_launch
 
     # --- end to end through the C ABI with host buffers ---
     # slic_batch_segment_host: H2D copy of the step's frames, the step, D2H
@@ -383,7 +393,7 @@ def run_ours(args):
         eb = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=e_iters, device=dev)
         eb.dimg = torch.empty_like(images)  # one allocation: the step's frames move with one copy
         eb.bind([eb.dimg[f] for f in range(B)])
-        eb.set_tuning(ctas_per_sm, stages, rows, tile_h)
+        eb.set_tuning(ctas_per_sm, stages, rows, tile_h, fused=fused)
         if method["name"] == "learned":
             eb.set_warmstart(net)
         pair.append((eb, torch.cuda.Stream(device=dev), torch.empty((B, H, W), dtype=torch.int32).pin_memory(),
@@ -464,8 +474,9 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (B x 6.2 MB RGB + B x 8.3 MB labels per step)",
                        "graph": "one CUDA graph per step (one batched launch per stage)",
                        "ctas_per_sm": ctas_per_sm, "pipeline_stages": stages, "row_groups_per_warp": rows,
-                       "tile": f"32x{tile_h}"},
-            "roofline": {"kernel": f"{kname} (middle assignment pass, all frames)", "bound": "alu",
+                       "tile": f"32x{tile_h}", "fused_passes": bool(fused)},
+            "roofline": {"kernel": (f"{kname} (passes 0..{n_plain - 1} with their updates, all frames)" if fused_dom
+                                    else f"{kname} (middle assignment pass, all frames)"), "bound": "alu",
                          "unit": "Tsqrt/s", "achieved": achieved_tops, "peak": xu_peak, "frac": achieved_tops / xu_peak,
                          "peak_source": f"16 MUFU lanes/clk/SM x {sms} SMs x max SM clock (recipe unit counts)",
                          "traffic": traffic, "avg_launch_us": mid_ms * 1e3, "launches_timed": len(mid),
@@ -571,8 +582,8 @@ def mixed_batch_throughput(args, pkg, stream, dev):
     imgs = [torch.from_numpy(synth.mixed_batch_frame(f, w, h)).to(dev) for f, (w, h, _, _) in enumerate(specs)]
     bs = pkg.BatchSegmenter(frames, iterations=ITERS, device=dev)
     bs.bind(imgs)
-    ctas, stages, rows, tile_h = bs.autotune(os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl"),
-                                             stream=stream)
+    ctas, stages, rows, tile_h, fused = bs.autotune(os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl"),
+                                                    stream=stream)
     with torch.cuda.stream(stream):
         bs.segment(stream)
     torch.cuda.synchronize()
@@ -596,7 +607,7 @@ def mixed_batch_throughput(args, pkg, stream, dev):
     bs.close()
     return {"frames": len(specs), "megapixels": px / 1e6, "ms_per_step": ms, "frames_per_s": len(specs) / (ms / 1e3),
             "megapixels_per_s": px / 1e6 / (ms / 1e3), "steps": steps, "ctas_per_sm": ctas, "pipeline_stages": stages,
-            "row_groups_per_warp": rows, "tile": f"32x{tile_h}",
+            "row_groups_per_warp": rows, "tile": f"32x{tile_h}", "fused_passes": bool(fused),
             "iterations": ITERS}
 
 
@@ -784,7 +795,7 @@ def main(argv=None):
     ap.add_argument("--iterations", type=int, default=None,
                     help="time the plain path at this iteration count instead of the one the agreement sweep "
                          "finds (skips the sweep and the learned leg; for profiling)")
-    ap.add_argument("--tuning", default=None, metavar="CTAS,STAGES,ROWS,TILE_H",
+    ap.add_argument("--tuning", default=None, metavar="CTAS,STAGES,ROWS,TILE_H[,FUSED]",
                     help="launch shape of the assignment passes instead of autotuning (for profiling)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="run only the 256-frame mixed batch and print its line (for profiling)")

@@ -257,25 +257,42 @@ slic_status slic_batch_segment_host(slic_batch b, const uint8_t *const *host_ima
    memory. */
 slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages, int rows, int tile_h);
 
+/* Fused passes (enable = 1; the default is 0, the autotuner chooses): with
+   the pipelined kernel, the
+   assignment passes before the last and the centre updates after them
+   (Sec. 3 "Updating the cluster center", Sec. 4's loop) run as one
+   cooperative launch. In every pass each CTA takes a contiguous block of
+   the batch's tiles (frame after frame) and then the same share of the
+   frames' update work (chunks of 256 centres), so the CTAs that sum a
+   frame's pixels also update its centres. A frame's update starts when its
+   tiles of the pass are summed, and its tiles of the next pass start when
+   its update is done (per-frame phase counters; every wait is bounded, and
+   one that gives up is reported by slic_batch_status as SLIC_ERR_TIMEOUT).
+   No device-wide step separates the passes: one frame can be a pass ahead
+   of another. enable = 0: one launch per pass and per update. Results are
+   bit-identical either way. SLIC_ERR_INVALID for enable not 0 or 1. */
+slic_status slic_batch_set_fused(slic_batch b, int enable);
+
 /* Autotuner: time slic_batch_segment on the bound buffers for every launch
    shape that fits (3 timed runs each, CUDA events on `stream`; this waits
    for the device), keep the fastest, and append it to the JSON-lines file
    cache_path (may be NULL) under a key of GPU name, frame count,
    iterations and the distinct (width, height, S). When the key is already
    in the file its entry is used without timing. The search covers tile
-   shapes x row groups per warp x pipeline stages x CTAs per SM; the choice
-   is returned in *ctas_per_sm, *stages, *rows and *tile_h (any may be
+   shapes x row groups per warp x pipeline stages x CTAs per SM x fused
+   passes or not (slic_batch_set_fused); the choice is set on the batch and
+   returned in *ctas_per_sm, *stages, *rows, *tile_h and *fused (any may be
    NULL). */
 slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm, int *stages,
-                               int *rows, int *tile_h);
+                               int *rows, int *tile_h, int *fused);
 
 /* Pixels of all frames, kernel launches enqueued so far, and the launch
    shape of the assignment passes: CTAs per SM (as requested, capped by what
-   fits), pipeline stages, row groups per warp and tile rows
-   (stages and rows 0, tile rows 32, when the pipelined kernel is not used);
-   any pointer may be NULL. */
+   fits), pipeline stages, row groups per warp, tile rows and fused passes
+   (stages and rows 0, tile rows 32, fused 0 when the pipelined kernel is not
+   used); any pointer may be NULL. */
 slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm,
-                            int *stages, int *rows, int *tile_h);
+                            int *stages, int *rows, int *tile_h, int *fused);
 
 /* Grid of frame `frame` (Sec. 2): its S and ns_c x ns_r cells, K_eff =
    ns_c*ns_r centres (any pointer may be NULL); SLIC_ERR_INVALID for a frame
@@ -297,9 +314,11 @@ slic_status slic_batch_iterations_run(slic_batch b, int *out);
    slic_profile_read do for a handle. */
 slic_status slic_batch_profile_enable(slic_batch b, int enable);
 slic_status slic_batch_profile_read(slic_batch b, double *assign_ms, long long *assign_launches);
-/* The same records one by one, in enqueue order (pass 0, 1, ..., iterations
-   for each slic_batch_segment call): up to max_n durations (ms) into ms[],
-   their number into *n. */
+/* The same records one by one, in enqueue order, for each
+   slic_batch_segment call: with fused passes (slic_batch_set_fused) the
+   fused launch (passes 0 .. iterations-1 and their updates) and the last
+   pass, otherwise pass 0, 1, ..., iterations. Up to max_n durations (ms)
+   into ms[], their number into *n. */
 slic_status slic_batch_profile_times(slic_batch b, double *ms, int max_n, int *n);
 
 /* Release the batch (waits for the device first). NULL is accepted. */

@@ -45,6 +45,8 @@ struct slic_batch_ctx {
     bool any_conv = false;            // some frame has a stopping threshold
     int total_tiles = 0, total_centres = 0, total_rows = 0, max_w = 0, win_max = 0;
     int total_tiles64 = 0, win_max64 = 0;  // the same for 32x64 tiles
+    int total_chunks = 0;    // update chunks of all frames (fused passes)
+    bool fused = false;      // the passes before the last in one cooperative launch
     int total_units = 0;  // work units of the fused connectivity kernel
     long long total_pixels = 0;
     bool same = true;        // every frame's S a multiple of 4 (4-pixel groups share a cell)
@@ -200,8 +202,9 @@ std::string tune_key(const slic_batch_ctx *b) {
 }
 
 // Cache lines: {"key": "<key>", "ctas_per_sm": <int>, "stages": <int>, "rows": <int>, "tile_h": <int>,
-// "ms": <float>}
-bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stages, int *rows, int *tile_h) {
+// "fused": <0|1>, "ms": <float>}
+bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stages, int *rows, int *tile_h,
+                  int *fused) {
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
     char line[4096];
@@ -213,14 +216,17 @@ bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stag
             const char *r = std::strstr(line, "\"stages\":");
             const char *o = std::strstr(line, "\"rows\":");
             const char *t = std::strstr(line, "\"tile_h\":");
-            int v = 0, w = 0, u = 0, h = 0;
-            if (q && r && o && t && std::sscanf(q + 14, "%d", &v) == 1 && std::sscanf(r + 9, "%d", &w) == 1 &&
-                std::sscanf(o + 7, "%d", &u) == 1 && std::sscanf(t + 9, "%d", &h) == 1 && v > 0 && w >= 3 &&
-                w <= 4 && (u == 1 || u == 2) && (h == 32 || h == 64)) {
+            const char *z = std::strstr(line, "\"fused\":");
+            int v = 0, w = 0, u = 0, h = 0, fz = -1;
+            if (q && r && o && t && z && std::sscanf(q + 14, "%d", &v) == 1 && std::sscanf(r + 9, "%d", &w) == 1 &&
+                std::sscanf(o + 7, "%d", &u) == 1 && std::sscanf(t + 9, "%d", &h) == 1 &&
+                std::sscanf(z + 8, "%d", &fz) == 1 && v > 0 && w >= 3 && w <= 4 && (u == 1 || u == 2) &&
+                (h == 32 || h == 64) && (fz == 0 || fz == 1)) {
                 *ctas = v;
                 *stages = w;
                 *rows = u;
                 *tile_h = h;
+                *fused = fz;
                 found = true;
             }
         }
@@ -229,11 +235,14 @@ bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stag
     return found;
 }
 
-void cache_store(const char *path, const std::string &key, int ctas, int stages, int rows, int tile_h, float ms) {
+void cache_store(const char *path, const std::string &key, int ctas, int stages, int rows, int tile_h, int fused,
+                 float ms) {
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"stages\": %d, \"rows\": %d, \"tile_h\": %d, \"ms\": %.4f}\n",
-                 key.c_str(), ctas, stages, rows, tile_h, ms);
+    std::fprintf(f,
+                 "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"stages\": %d, \"rows\": %d, \"tile_h\": %d, "
+                 "\"fused\": %d, \"ms\": %.4f}\n",
+                 key.c_str(), ctas, stages, rows, tile_h, fused, ms);
     std::fclose(f);
 }
 
@@ -343,8 +352,11 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
         a.centre_base = (int)centres;
         a.row_base = (int)rows;
         a.tile_base64 = (int)tiles64;
-        tiles += (long long)a.tiles_x * ((p.height + kTileH - 1) / kTileH);
-        tiles64 += (long long)a.tiles_x * ((p.height + 2 * kTileH - 1) / (2 * kTileH));
+        a.n_tiles = a.tiles_x * ((p.height + kTileH - 1) / kTileH);
+        a.n_tiles64 = a.tiles_x * ((p.height + 2 * kTileH - 1) / (2 * kTileH));
+        a.n_chunks = (a.ns_c * a.ns_r + kUpdateChunk - 1) / kUpdateChunk;
+        tiles += a.n_tiles;
+        tiles64 += a.n_tiles64;
         centres += (long long)a.ns_c * a.ns_r;
         rows += p.height;
         if (tiles >= (1LL << 31) || centres >= (1LL << 31) || rows >= (1LL << 31)) {
@@ -394,6 +406,14 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
     b->tbl_bytes = b->tbl_img + align256(sizeof(const uint8_t *) * (size_t)n_frames);
     b->total_tiles = (int)tiles;
     b->total_tiles64 = (int)tiles64;
+    {
+        long long chunks = 0;  // the batch's update chunks (fused passes), frame after frame
+        for (FrameArgs &a : b->frames) {
+            a.chunk_base = (int)chunks;
+            chunks += a.n_chunks;
+        }
+        b->total_chunks = (int)chunks;  // (< total_centres, checked above)
+    }
     b->total_centres = (int)centres;
     b->total_rows = (int)rows;
     for (FrameArgs &a : b->frames) {
@@ -533,34 +553,54 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
         if (e == cudaSuccess) e = launch_update_batch(b->d_frames, b->n, b->total_centres, 0, s);
         n_launch += 2;
     }
-    for (int pass = 0; e == cudaSuccess && pass <= b->iterations; ++pass) {
-        if (pass > 0) {
-            e = launch_update_batch(b->d_frames, b->n, b->total_centres, pass, s);
-            ++n_launch;
-        }
-        if (e == cudaSuccess) {
-            cudaEvent_t e1 = nullptr;
-            if (b->profiling) {
-                if (b->ev_used == b->events.size()) {
-                    cudaEvent_t x, y;
-                    if (cudaEventCreate(&x) != cudaSuccess || cudaEventCreate(&y) != cudaSuccess)
-                        return bfail(b, SLIC_ERR_CUDA, "cudaEventCreate failed");
-                    b->events.emplace_back(x, y);
-                }
-                e = record_profile_event(b->events[b->ev_used].first, s);
-                e1 = b->events[b->ev_used++].second;
+    // Event pair around one assignment launch when profiling.
+    auto timed = [&](auto launch) -> cudaError_t {
+        cudaEvent_t e1 = nullptr;
+        if (b->profiling) {
+            if (b->ev_used == b->events.size()) {
+                cudaEvent_t x, y;
+                if (cudaEventCreate(&x) != cudaSuccess || cudaEventCreate(&y) != cudaSuccess)
+                    return cudaErrorMemoryAllocation;
+                b->events.emplace_back(x, y);
             }
-            if (e != cudaSuccess) break;
-            if (b->pipe)
-                e = launch_assign_pipe(b->d_frames, b->n, b->tile_h == 64 ? b->total_tiles64 : b->total_tiles,
-                                       b->tile_h == 64 ? b->win_max64 : b->win_max, b->same, pass == b->iterations,
-                                       b->stages, b->rows, b->tile_h, pipe_per_sm, grid_pipe, b->d_err,
-                                       b->any_conv ? 1 : 0, s);
-            else
-                e = launch_assign_batch(b->d_frames, b->n, b->total_tiles, b->win_max, b->same, pass == 0 && !warm,
-                                        pass == b->iterations, b->smem, grid, s);
-            if (e1 && e == cudaSuccess) e = record_profile_event(e1, s);
-            ++n_launch;
+            const cudaError_t r = record_profile_event(b->events[b->ev_used].first, s);
+            if (r != cudaSuccess) return r;
+            e1 = b->events[b->ev_used++].second;
+        }
+        cudaError_t r = launch();
+        if (e1 && r == cudaSuccess) r = record_profile_event(e1, s);
+        ++n_launch;
+        return r;
+    };
+    const int tiles_th = b->tile_h == 64 ? b->total_tiles64 : b->total_tiles;
+    const int win_th = b->tile_h == 64 ? b->win_max64 : b->win_max;
+    auto last_or_pass = [&](int pass) {
+        return [&, pass]() {
+            return b->pipe ? launch_assign_pipe(b->d_frames, b->n, tiles_th, win_th, b->same, pass == b->iterations,
+                                                b->stages, b->rows, b->tile_h, pipe_per_sm, grid_pipe, b->d_err,
+                                                b->any_conv ? 1 : 0, s)
+                           : launch_assign_batch(b->d_frames, b->n, b->total_tiles, b->win_max, b->same,
+                                                 pass == 0 && !warm, pass == b->iterations, b->smem, grid, s);
+        };
+    };
+    if (e == cudaSuccess && b->pipe && b->fused && b->iterations > 0) {
+        // Passes 0 .. n-1 with updates 1 .. n in one cooperative launch
+        // (per-frame phase counters order them), then the last pass.
+        const int occ = std::max(1, assign_pipe_occupancy(b->same, win_th, b->stages, b->rows, b->tile_h, true));
+        const int grid_multi = grid_for(b, occ);
+        e = timed([&]() {
+            return launch_assign_multi(b->d_frames, b->n, tiles_th,
+                                       b->total_chunks, win_th, b->same, b->iterations, b->stages, b->rows, b->tile_h, grid_multi / std::max(1, b->sms),
+                                       grid_multi, b->d_err, b->any_conv ? 1 : 0, s);
+        });
+        if (e == cudaSuccess) e = timed(last_or_pass(b->iterations));
+    } else {
+        for (int pass = 0; e == cudaSuccess && pass <= b->iterations; ++pass) {
+            if (pass > 0) {
+                e = launch_update_batch(b->d_frames, b->n, b->total_centres, pass, s);
+                ++n_launch;
+            }
+            if (e == cudaSuccess) e = timed(last_or_pass(pass));
         }
     }
     if (e == cudaSuccess && b->connectivity == 2) {
@@ -668,24 +708,33 @@ slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages, int
     return SLIC_OK;
 }
 
+slic_status slic_batch_set_fused(slic_batch b, int enable) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (enable != 0 && enable != 1) return bfail(b, SLIC_ERR_INVALID, "enable must be 0 or 1");
+    b->fused = enable == 1;
+    return SLIC_OK;
+}
+
 slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm, int *stages,
-                               int *rows, int *tile_h) {
+                               int *rows, int *tile_h, int *fused) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
     const std::string key = tune_key(b);
-    int best = 0, best_st = b->stages, best_rw = b->rows, best_th = b->tile_h;
+    int best = 0, best_st = b->stages, best_rw = b->rows, best_th = b->tile_h, best_fu = b->fused ? 1 : 0;
     auto report = [&]() {
         b->ctas_per_sm = best;
         b->stages = best_st;
         b->rows = best_rw;
         b->tile_h = best_th;
+        b->fused = best_fu == 1;
         if (ctas_per_sm) *ctas_per_sm = best;
         if (stages) *stages = best_st;
         if (rows) *rows = best_rw;
         if (tile_h) *tile_h = best_th;
+        if (fused) *fused = best_fu;
     };
-    if (cache_path && cache_lookup(cache_path, key, &best, &best_st, &best_rw, &best_th) &&
-        (!b->pipe ? best_rw == 1 && best_th == 32 : shape_fits(b, best_st, best_rw, best_th))) {
+    if (cache_path && cache_lookup(cache_path, key, &best, &best_st, &best_rw, &best_th, &best_fu) &&
+        (!b->pipe ? best_rw == 1 && best_th == 32 && best_fu == 0 : shape_fits(b, best_st, best_rw, best_th))) {
         report();
         return SLIC_OK;
     }
@@ -697,7 +746,8 @@ slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stre
     slic_status st = SLIC_OK;
     // Search space: tile shape (32x32, or 32x64 with two row groups) x row
     // groups per warp (pixels per thread and block size) x pipeline stages x
-    // resident CTAs per SM (up to what fits).
+    // resident CTAs per SM (up to what fits) x fused passes or not.
+    const int fu_hi = b->pipe && b->iterations > 0 ? 1 : 0;
     const int st_lo = b->pipe ? 3 : b->stages, st_hi = b->pipe ? 4 : b->stages;
     const int rw_hi = (b->pipe && b->same8) ? 2 : 1;
     for (int th = 32; th <= 64 && st == SLIC_OK; th += 32) {
@@ -705,11 +755,13 @@ slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stre
             for (int nst = st_lo; nst <= st_hi && st == SLIC_OK; ++nst) {
                 if (b->pipe ? !shape_fits(b, nst, rw, th) : th != 32) continue;
                 const int occ = std::max(b->occupancy, b->pipe ? pipe_occ(b, nst, rw, th) : 0);
-                for (int c = 1; c <= occ && st == SLIC_OK; ++c) {
+                for (int k = 0; k < occ * (fu_hi + 1) && st == SLIC_OK; ++k) {
+                    const int c = 1 + k / (fu_hi + 1), fu = k % (fu_hi + 1);
                     b->ctas_per_sm = c;
                     b->stages = nst;
                     b->rows = rw;
                     b->tile_h = th;
+                    b->fused = fu == 1;
                     if ((st = slic_batch_segment(b, stream)) != SLIC_OK) break;  // warm-up
                     float total = 0.0f;
                     for (int rep = 0; rep < 3 && st == SLIC_OK; ++rep) {
@@ -728,6 +780,7 @@ slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stre
                         best_st = nst;
                         best_rw = rw;
                         best_th = th;
+                        best_fu = fu;
                     }
                 }
             }
@@ -737,12 +790,12 @@ slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stre
     cudaEventDestroy(e1);
     if (st != SLIC_OK) return st;
     report();
-    if (cache_path) cache_store(cache_path, key, best, best_st, best_rw, best_th, best_ms);
+    if (cache_path) cache_store(cache_path, key, best, best_st, best_rw, best_th, best_fu, best_ms);
     return SLIC_OK;
 }
 
 slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm,
-                            int *stages, int *rows, int *tile_h) {
+                            int *stages, int *rows, int *tile_h, int *fused) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (total_pixels) *total_pixels = b->total_pixels;
     if (launches) *launches = b->launches;
@@ -751,6 +804,7 @@ slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *la
     if (stages) *stages = b->pipe ? b->stages : 0;
     if (rows) *rows = b->pipe ? b->rows : 0;
     if (tile_h) *tile_h = b->pipe ? b->tile_h : 32;
+    if (fused) *fused = b->pipe && b->fused ? 1 : 0;
     return SLIC_OK;
 }
 

@@ -99,6 +99,12 @@ struct ConvState {
     long long resid[3][kResidLanes];
     int done;
     int iters;
+    // Phase counters of the fused multi-pass assignment (reset with the
+    // rest by the initialisation): tiles of this frame whose sums are in the
+    // global sums, and warps that finished their part of an update chunk,
+    // both counted over all passes of one launch.
+    int tiles_done;
+    int chunks_done;
 };
 constexpr float kResidScale = 65536.0f;
 
@@ -143,7 +149,13 @@ struct FrameArgs {
     ConvState *cstate;      // the frame's stopping-test state (reset by the initialisation)
     const int32_t *init_labels;  // [H][W] labels whose member means replace the grid
                                  // centres (learned warm start), or null
+    // Fused multi-pass assignment: the frame's tiles per tile height, its
+    // update chunks (kUpdateChunk centres each) and its first chunk in the
+    // batch's list of chunks
+    int n_tiles, n_tiles64, n_chunks;
+    int chunk_base;
 };
+constexpr int kUpdateChunk = 256;  // centres per update work item of the fused assignment
 
 // Shared memory for one assignment CTA whose tile spans at most win_n cells.
 size_t assign_smem_bytes(int win_n, bool first);
@@ -207,10 +219,21 @@ cudaError_t launch_update_batch(const FrameArgs *d_frames, int n, int total_cent
 cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles, int win_max, bool same, bool last,
                                int nst, int rows, int tile_h, int ctas_per_sm, int grid, int *err, int check_stop,
                                cudaStream_t s);
+// Fused multi-pass form of the same kernel, one cooperative launch: passes
+// 0 .. passes-1 with the update after each (updates 1 .. passes), ordered
+// per frame by the phase counters in its ConvState (reset by the
+// initialisation); the last pass is a separate launch_assign_pipe. Each CTA
+// takes, in every pass, a contiguous block of the batch's total_tiles tiles
+// (of tile_h rows) and the same share of its total_chunks update chunks.
+// grid must not exceed the resident CTAs (a cooperative launch fails then).
+cudaError_t launch_assign_multi(const FrameArgs *d_frames, int n, int total_tiles, int total_chunks, int win_max,
+                                bool same, int passes, int nst, int rows, int tile_h, int ctas_per_sm, int grid,
+                                int *err, int check_stop, cudaStream_t s);
 // Shared memory and resident CTAs per SM of the pipelined kernel with nst
-// (3..4) stages, 1 or 2 row groups per warp and tiles of tile_h rows.
-size_t assign_pipe_smem_bytes(int win_n, bool last, int nst, int rows, int tile_h = 32);
-int assign_pipe_occupancy(bool same, int win_n, int nst, int rows, int tile_h = 32);
+// (3..4) stages, 1 or 2 row groups per warp and tiles of tile_h rows (multi:
+// the fused multi-pass build).
+size_t assign_pipe_smem_bytes(int win_n, bool last, int nst, int rows, int tile_h = 32, bool multi = false);
+int assign_pipe_occupancy(bool same, int win_n, int nst, int rows, int tile_h = 32, bool multi = false);
 // Batched RGB -> features pre-pass (the pipelined path's first pass reads
 // the features it writes).
 cudaError_t launch_convert_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w, cudaStream_t s);

@@ -57,14 +57,15 @@ __device__ __forceinline__ int div_s(int x, unsigned s_mul, int S) {
 
 // Index of the frame whose [base, next base) range holds `idx` (frames are
 // sorted by base; base of frame 0 is 0).
-enum BaseField { kTileBase, kCentreBase, kRowBase, kStripBase, kTileBase64 };
+enum BaseField { kTileBase, kCentreBase, kRowBase, kStripBase, kTileBase64, kChunkBase };
 template <BaseField F>
 __device__ __forceinline__ int base_of(const FrameArgs &a) {
     return F == kTileBase ? a.tile_base
            : F == kCentreBase ? a.centre_base
            : F == kRowBase ? a.row_base
            : F == kStripBase ? a.strip_base
-                             : a.tile_base64;
+           : F == kTileBase64 ? a.tile_base64
+                              : a.chunk_base;
 }
 template <BaseField F>
 __device__ __forceinline__ int find_frame(const FrameArgs *frames, int n, int idx) {
@@ -194,6 +195,8 @@ __device__ __forceinline__ void reset_conv(ConvState *cs) {
         for (int i = 0; i < 3 * kResidLanes; ++i) (&cs->resid[0][0])[i] = 0;
         cs->done = 0;
         cs->iters = 0;
+        cs->tiles_done = 0;
+        cs->chunks_done = 0;
     }
 }
 
@@ -860,6 +863,16 @@ struct __align__(16) TileGeom {
     int skip;              // 1: the frame passed its stopping test (no copy was issued)
 };
 
+// What the fused multi-pass assignment adds to an item's header (a ring of
+// its own, beside the tile headers): the item's kind (0: a tile; 1: an
+// update chunk, centres c0 .. c0+cn-1 of frame TileGeom::f), its pass (the
+// chunk's update is pass + 1) and, for a tile, its frame's counter of
+// flushed tiles.
+struct MultiHdr {
+    int kind, pass, c0, cn;
+    int *done_ctr;
+};
+
 template <int TH>
 __device__ __forceinline__ TileGeom tile_geom(const FrameArgs &a, int local) {
     TileGeom g;
@@ -906,9 +919,10 @@ __device__ __forceinline__ void issue_tile(const FrameArgs &a, const TileGeom &g
 // four words of every copy as one 16-byte load. The flushing warp waits
 // until every warp has filled the set and reports it free afterwards; the
 // others return at once. False when the wait timed out.
-template <int NW, int NCOPY>
-__device__ __forceinline__ bool flush_tile(const TileGeom *hdr, unsigned *wacc0, size_t acc_words, int win_max,
-                                           uint64_t *acc_done, uint64_t *acc_free, int j, int warp, int lane) {
+template <int NW, int NCOPY, bool MULTI>
+__device__ __forceinline__ bool flush_tile(const TileGeom *hdr, const MultiHdr *mhdr, unsigned *wacc0,
+                                           size_t acc_words, int win_max, uint64_t *acc_done, uint64_t *acc_free,
+                                           int j, int warp, int lane) {
     if (warp != j % NW) return true;
     const int set = j % kAccSets;
     if (!__all_sync(0xffffffffu, mbar_wait(&acc_done[set], (j / kAccSets) & 1))) return false;
@@ -951,27 +965,173 @@ __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, unsigned *wacc0,
         }
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(&acc_free[set]);
+    if (lane == 0) {
+        if constexpr (MULTI) {
+            // the tile's sums are in the frame's global sums: count it (release)
+            int *const ctr = mhdr[j % kHdrSlots].done_ctr;
+            if (ctr) {
+                __threadfence();
+                atomicAdd(ctr, 1);
+            }
+        }
+        mbar_arrive(&acc_free[set]);
+    }
     return true;
 }
 
+// Polls of wait_count: with a 256 ns sleep each, about 1 s in all.
+constexpr unsigned kCountPolls = 1u << 22;
+
+// Bounded wait of one thread until the counter at p reaches target (acquire
+// at device scope); false when it gives up, or as soon as *err is set.
+__device__ __forceinline__ bool wait_count(const int *p, int target, const int *err) {
+    for (unsigned i = 0; i < kCountPolls; ++i) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+        if (v >= target) return true;
+        if (*reinterpret_cast<const volatile int *>(err)) return false;
+        __nanosleep(256);
+    }
+    return false;
+}
+
+// Orders this thread's global accesses of the generic proxy with those of
+// the async proxy (the tensor copies): centre records written by one CTA
+// are read by another CTA's tensor copy in the same launch.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
 }  // namespace
 
-size_t assign_pipe_smem_bytes(int win_n, bool last, int nst, int rows, int tile_h) {
+// Member mean from the exact integer sums, in FP32 (this GPU's FP64 rate is
+// a small fraction of its FP32 rate): the sum rounded to float, scaled by the
+// power of two fix_inv (exact) and divided by the count (correctly rounded),
+// so within about one unit in the last place of the exact mean.
+// Returns the centre's move |dx| + |dy| (0 for an empty cluster, or when
+// want_move is false: the old position is then not read).
+__device__ __forceinline__ float update_centre(long long *ak, const float *ci, float *co, float fix_inv,
+                                               bool want_move) {
+    // (L2 loads: in the fused multi-pass assignment other CTAs wrote these in
+    // the same launch)
+    const longlong2 s01 = __ldcg(reinterpret_cast<const longlong2 *>(ak));
+    const longlong2 s23 = __ldcg(reinterpret_cast<const longlong2 *>(ak + 2));
+    const longlong2 s45 = __ldcg(reinterpret_cast<const longlong2 *>(ak + 4));
+    const long long n = s45.y;
+    float move = 0.0f;
+    if (n > 0) {
+        const float fn = (float)n;
+        const float x0 = want_move ? __ldcg(ci + 3) : 0.0f, y0 = want_move ? __ldcg(ci + 4) : 0.0f;
+        co[0] = __fdiv_rn((float)s01.x * fix_inv, fn);
+        co[1] = __fdiv_rn((float)s01.y * fix_inv, fn);
+        co[2] = __fdiv_rn((float)s23.x * fix_inv, fn);
+        const float xn = __fdiv_rn((float)s23.y, fn), yn = __fdiv_rn((float)s45.x, fn);
+        co[3] = xn;
+        co[4] = yn;
+        co[5] = fn;
+        if (want_move) move = fabsf(xn - x0) + fabsf(yn - y0);
+    } else {
+        if (co != ci) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) co[c] = __ldcg(ci + c);
+        }
+        co[5] = 0.0f;
+    }
+    longlong2 *az = reinterpret_cast<longlong2 *>(ak);
+    az[0] = make_longlong2(0, 0);
+    az[1] = make_longlong2(0, 0);
+    az[2] = make_longlong2(0, 0);
+    return move;
+}
+
+// Stopping test before update `it` (1-based): the frame stops when it has
+// stopped already or update it-1 moved its K centres by a mean L1 distance
+// below eps (so update it-1 and its assignment were the last). Every thread
+// decides from the same stored values.
+__device__ __forceinline__ bool conv_stop(const ConvState *cs, float eps, int K, int it) {
+    if (!cs || !(eps > 0.0f)) return false;
+    if (*reinterpret_cast<const volatile int *>(&cs->done)) return true;
+    if (it < 2) return false;
+    long long e = 0;
+#pragma unroll
+    for (int i = 0; i < kResidLanes; ++i) e += __ldcg(&cs->resid[(it - 1) % 3][i]);
+    return (double)e < (double)eps * (double)kResidScale * (double)K;
+}
+
+// After update `it`: with the stopping test on, the sum of this warp's
+// moves into one of the frame's counters of slot it % 3 (one atomic per
+// warp when all its lanes belong to `cs`'s frame); from the frame's first
+// centre, the update count and the cleared slot of update it+1.
+__device__ __forceinline__ void conv_record(ConvState *cs, bool uniform, bool test_on, float move, bool first,
+                                            int it) {
+    if (test_on) {
+        long long v = (long long)__float2ll_rn(move * kResidScale);
+        const int lane_slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % kResidLanes;
+        if (uniform) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0 && v != 0)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&cs->resid[it % 3][lane_slot]), (unsigned long long)v);
+        } else if (v != 0) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&cs->resid[it % 3][lane_slot]), (unsigned long long)v);
+        }
+    }
+    if (first) {
+        if (test_on) {
+#pragma unroll
+            for (int i = 0; i < kResidLanes; ++i) cs->resid[(it + 1) % 3][i] = 0;
+        }
+        cs->iters = it;
+    }
+}
+
+size_t assign_pipe_smem_bytes(int win_n, bool last, int nst, int rows, int tile_h, bool multi) {
     (void)rows;  // the sums keep one copy per 128 pixels whatever the warp count
     const size_t stage = stage_feat_bytes(tile_h) + (((size_t)win_n * kCtabRec * 4 + 127) & ~(size_t)127);
     const size_t acc = last ? 0 : (size_t)kWarps * (tile_h / kTileH) * win_n * 4 * sizeof(int);
     // nst stages, the accumulator sets, the mbarriers, the header ring, two
     // flags and base alignment
     return (size_t)nst * stage + kAccSets * acc + (size_t)(2 * kMaxStages + 2 * kAccSets) * 8 +
-           (size_t)kHdrSlots * sizeof(TileGeom) + 16 + 128;
+           (size_t)kHdrSlots * sizeof(TileGeom) + 16 + 128 + (multi ? (size_t)kHdrSlots * sizeof(MultiHdr) : 0);
 }
 
-template <bool LAST, bool SAME, int MINB, int ROWS, int TH>
-__global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB) k_assign_pipe(const FrameArgs *frames,
-                                                                                   int n_frames, int total_tiles,
-                                                                                   int win_max, int nst, int *err,
-                                                                                   int check_stop) {
+// An update chunk of the fused multi-pass assignment: update `it` of
+// centres c0 .. c0+cn-1 of one frame by the CTA's NT threads, as
+// k_update_batch does it (stopping test, member means, centre records,
+// cleared sums, the frame's move).
+template <int NT>
+__device__ __forceinline__ void update_chunk(const FrameArgs &a, int c0, int cn, int it, int tid) {
+    const int K = a.ns_c * a.ns_r;
+    for (int i = 0; i < kUpdateChunk; i += NT) {  // the same trip count on every lane
+        const int j = i + tid, kk = c0 + j;
+        const bool valid = j < cn;
+        float move = 0.0f;
+        bool stop = true;
+        if (valid) {
+            stop = conv_stop(a.cstate, a.conv_eps, K, it);
+            if (stop) {
+                if (kk == 0) a.cstate->done = 1;
+            } else {
+                const size_t k = (size_t)kk * 6;
+                move = update_centre(a.acc + k, a.centres_out + k, a.centres_out + k, 1.0f / a.fix_scale,
+                                     a.conv_eps > 0.0f);
+                const int r = kk / a.ns_c, c = kk - r * a.ns_c;
+                write_ctab(a.ctab + ((size_t)(r + 1) * (a.ns_c + 2) + c + 1) * kCtabRec, a.centres_out + k);
+            }
+        }
+        // (a frame stops for all its centres: a warp of valid lanes is all
+        // stopped or all running)
+        if (__all_sync(kFull, valid)) {
+            if (!stop) conv_record(a.cstate, true, a.conv_eps > 0.0f, move, kk == 0, it);
+        } else if (valid && !stop) {
+            conv_record(a.cstate, false, a.conv_eps > 0.0f, move, kk == 0, it);
+        }
+    }
+}
+
+// The pipelined assignment, as one pass (k_assign_pipe) or as the fused
+// passes before the last (k_assign_multi, MULTI).
+template <bool LAST, bool SAME, int MINB, int ROWS, int TH, bool MULTI>
+__device__ __forceinline__ void assign_pipe_body(const FrameArgs *frames, int n_frames, int total_tiles, int win_max,
+                                                 int nst, int *err, int check_stop, int passes, int total_chunks) {
     // ROWS = 1: 8 warps, warp w evaluates rows 4w..4w+3 of the tile.
     // ROWS = 2: TH/8 warps, warp w evaluates rows 8w..8w+3 and 8w+4..8w+7
     // (the same cell row when S is a multiple of 8), sharing the centre loads
@@ -979,6 +1139,7 @@ __global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB) k_assign_pi
     // or 64 with ROWS = 2).
     static_assert(ROWS == 1 || (ROWS == 2 && SAME), "two row groups need cell-aligned 4-pixel groups");
     static_assert(TH == 32 || (TH == 64 && ROWS == 2), "32x64 tiles with two row groups only");
+    static_assert(!(MULTI && LAST), "the fused passes accumulate sums; the last pass is a launch of its own");
     constexpr int NW = kWarps / ROWS * (TH / 32), NT = NW * 32;
     constexpr int NCOPY = NW * ROWS;  // private sums: one copy per 128 pixels (rows 4q .. 4q+3)
     constexpr size_t kFeat = stage_feat_bytes(TH);
@@ -998,8 +1159,27 @@ __global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB) k_assign_pi
     uint64_t *acc_free = acc_done + kAccSets;  // accumulator set flushed and cleared (count 1)
     TileGeom *hdr = reinterpret_cast<TileGeom *>(acc_free + kAccSets);  // ring of kHdrSlots tile headers
     int *flags = reinterpret_cast<int *>(hdr + kHdrSlots);              // [0] abort, [1] last tile issued
+    MultiHdr *mhdr = reinterpret_cast<MultiHdr *>(flags + 4);           // MULTI: ring of kHdrSlots records
     volatile int *abort_flag = flags;
     const int ahead = nst - 3;  // tiles issued beyond the next one: stage reuse lags two tiles
+    // Work items of this CTA. One pass: tiles blockIdx.x + i * gridDim.x of
+    // the batch. MULTI, in every pass: a contiguous block of the batch's
+    // tiles (frame after frame), tiles t_lo .. t_lo+n_t-1, then the same
+    // share of its update chunks, k_lo .. k_lo+n_k-1 (blocks of CTA c:
+    // [c*N/G, (c+1)*N/G)); item j is item j % n_local of pass j / n_local.
+    int n_local, t_lo = 0, n_t = 0, k_lo = 0;
+    if constexpr (MULTI) {
+        const long long G = gridDim.x, c = blockIdx.x;
+        t_lo = (int)(total_tiles * c / G);
+        n_t = (int)(total_tiles * (c + 1) / G) - t_lo;
+        k_lo = (int)(total_chunks * c / G);
+        n_local = n_t + (int)(total_chunks * (c + 1) / G) - k_lo;
+    } else {
+        n_local = (int)blockIdx.x < total_tiles
+                      ? (total_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                      : 0;
+    }
+    const int n_items = MULTI ? n_local * passes : n_local;
 
     if (tid == 0) {
         for (int q = 0; q < nst; ++q) {
@@ -1019,35 +1199,99 @@ __global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB) k_assign_pi
     }
     __syncthreads();
 
-    // Tile j of this CTA (global tile blockIdx.x + j * gridDim.x) goes to
-    // stage j % nst (its use j / nst of that stage) and header slot
-    // j % kHdrSlots. Its producer issues it at the top of iteration
-    // j - ahead - 1, once every warp has released the stage's previous tile
-    // j - nst (two iterations earlier); the producer role rotates over the
-    // warps. No CTA-wide barrier inside the loop: warps drift up to about two
-    // tiles apart, bounded by the mbarriers.
+    // Item j of this CTA goes to stage j % nst (its use j / nst of that
+    // stage) and header slot j % kHdrSlots. Its producer issues it at the top
+    // of iteration j - ahead - 1, once every warp has released the stage's
+    // previous item j - nst (two iterations earlier); the producer role
+    // rotates over the warps. No CTA-wide barrier inside the loop: warps
+    // drift up to about two items apart, bounded by the mbarriers.
     // q = j % nst and use = j / nst are passed in (kept incrementally: a
     // division by the run-time stage count costs tens of instructions).
+    //
+    // MULTI: an update chunk waits (bounded) until its frame's tiles of the
+    // pass are all in the global sums; a tile of pass p > 0 is issued once
+    // every chunk of its frame's update p is done. The CTAs sharing a frame's
+    // tiles share its chunks, so a frame's waits involve those CTAs only.
+    // Each wait is on items of an earlier level (pass, tiles before chunks),
+    // and a CTA waits only when its own items of earlier levels are
+    // finished: it flushes the previous item before a chunk waits, flushes a
+    // pass's last item at once, and issues no item of the next pass before
+    // that flush (no look-ahead across passes). With every CTA resident (a
+    // cooperative launch) the items of the earliest unfinished level can
+    // always proceed, so every wait ends.
+    // MULTI: the (frame, pass) whose dependency this producer thread last
+    // verified; its later tiles of the same frame and pass need no new check
+    // (the condition only becomes true once, and this thread's acquire and
+    // proxy fence precede all its later copies).
+    int dep_f = -1, dep_pass = -1;
     auto produce = [&](int j, int q, int use) -> bool {
-        const int t = blockIdx.x + j * gridDim.x;
-        if (t >= total_tiles) return true;
-        if (*reinterpret_cast<volatile int *>(&g_abort_copies)) return false;
-        if (use > 0 && !mbar_wait(&empty[q], (use - 1) & 1)) return false;
-        const int f = find_frame<TH == 64 ? kTileBase64 : kTileBase>(frames, n_frames, t);
-        TileGeom g = tile_geom<TH>(frames[f], t - base_of<TH == 64 ? kTileBase64 : kTileBase>(frames[f]));
-        g.f = f;
-        g.skip = !LAST && check_stop && frame_stopped(frames[f]) ? 1 : 0;
-        if (g.skip) g.H = 0;  // no pixel of the tile is evaluated or summed
-        hdr[j % kHdrSlots] = g;
-        if (g.skip)
-            mbar_arrive(&full[q]);  // a stopped frame's tile: no copy, the stage completes at once
-        else
-            issue_tile<TH>(frames[f], g, smem_raw + (size_t)q * stage_bytes, &full[q]);
-        atomicMax(&flags[1], j);
-        return true;
+        if constexpr (MULTI) {
+            if (j >= n_items) return true;
+            if (*reinterpret_cast<volatile int *>(&g_abort_copies)) return false;
+            if (use > 0 && !mbar_wait(&empty[q], (use - 1) & 1)) return false;
+            const int pass = j / n_local;
+            const int i = j - pass * n_local;
+            MultiHdr m;
+            m.pass = pass;
+            if (i < n_t) {
+                const int t = t_lo + i;
+                const int f = find_frame<TH == 64 ? kTileBase64 : kTileBase>(frames, n_frames, t);
+                if (pass > 0 && (f != dep_f || pass != dep_pass)) {
+                    if (!wait_count(&frames[f].cstate->chunks_done, frames[f].n_chunks * NW * pass, err))
+                        return false;
+                    fence_proxy_async_global();  // the chunks' centre records, before the tensor copy
+                    dep_f = f;
+                    dep_pass = pass;
+                }
+                TileGeom g = tile_geom<TH>(frames[f], t - base_of<TH == 64 ? kTileBase64 : kTileBase>(frames[f]));
+                g.f = f;
+                g.skip = check_stop && frame_stopped(frames[f]) ? 1 : 0;
+                if (g.skip) g.H = 0;  // no pixel of the tile is evaluated or summed
+                m.kind = 0;
+                m.c0 = m.cn = 0;
+                m.done_ctr = &frames[f].cstate->tiles_done;
+                hdr[j % kHdrSlots] = g;
+                mhdr[j % kHdrSlots] = m;
+                if (g.skip)
+                    mbar_arrive(&full[q]);
+                else
+                    issue_tile<TH>(frames[f], g, smem_raw + (size_t)q * stage_bytes, &full[q]);
+            } else {
+                const int k = k_lo + (i - n_t);
+                const int f = find_frame<kChunkBase>(frames, n_frames, k);
+                TileGeom g = TileGeom{};
+                g.f = f;
+                m.kind = 1;
+                m.c0 = (k - frames[f].chunk_base) * kUpdateChunk;
+                m.cn = min(kUpdateChunk, frames[f].ns_c * frames[f].ns_r - m.c0);
+                m.done_ctr = nullptr;
+                hdr[j % kHdrSlots] = g;
+                mhdr[j % kHdrSlots] = m;
+                mbar_arrive(&full[q]);  // no data: the stage completes at once
+            }
+            atomicMax(&flags[1], j);
+            return true;
+        } else {
+            const int t = blockIdx.x + j * gridDim.x;
+            if (t >= total_tiles) return true;
+            if (*reinterpret_cast<volatile int *>(&g_abort_copies)) return false;
+            if (use > 0 && !mbar_wait(&empty[q], (use - 1) & 1)) return false;
+            const int f = find_frame<TH == 64 ? kTileBase64 : kTileBase>(frames, n_frames, t);
+            TileGeom g = tile_geom<TH>(frames[f], t - base_of<TH == 64 ? kTileBase64 : kTileBase>(frames[f]));
+            g.f = f;
+            g.skip = !LAST && check_stop && frame_stopped(frames[f]) ? 1 : 0;
+            if (g.skip) g.H = 0;  // no pixel of the tile is evaluated or summed
+            hdr[j % kHdrSlots] = g;
+            if (g.skip)
+                mbar_arrive(&full[q]);  // a stopped frame's tile: no copy, the stage completes at once
+            else
+                issue_tile<TH>(frames[f], g, smem_raw + (size_t)q * stage_bytes, &full[q]);
+            atomicMax(&flags[1], j);
+            return true;
+        }
     };
     if (tid == 0) {
-        for (int j = 0; j <= ahead; ++j) produce(j, j, 0);
+        for (int j = 0; j <= ahead && (!MULTI || j < n_local); ++j) produce(j, j, 0);
     }
     __syncthreads();
     // Stage and phase of this iteration's tile, and of the tile its producer
@@ -1061,6 +1305,10 @@ __global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB) k_assign_pi
     const int lx = 4 * (lane & 7), ly0 = 4 * ROWS * warp + (lane >> 3);
     int it = 0;
     bool ok = true;
+    // MULTI: position of item `it` in its pass, the CTA's first item of the
+    // next pass, and whether item it-1 closed a pass (it was flushed then)
+    int pit = 0, pass_end = n_local;
+    bool prev_flushed = false;
     auto advance = [&]() {
         if (++s == nst) {
             s = 0;
@@ -1070,15 +1318,36 @@ __global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB) k_assign_pi
             sp = 0;
             ++usep;
         }
+        if constexpr (MULTI) {
+            if (++pit == n_local) {
+                pit = 0;
+                pass_end += n_local;
+            }
+        }
     };
-    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++it, advance()) {
+    for (int tile = blockIdx.x; MULTI ? it < n_items : tile < total_tiles; tile += gridDim.x, ++it, advance()) {
         if (*abort_flag) {
             ok = false;
             break;
         }
-        if (warp == it % NW && lane == 0 && !produce(it + ahead + 1, sp, usep)) {
-            *abort_flag = 1;
-            atomicOr(err, 1);
+        if (warp == it % NW && lane == 0) {
+            bool okp = true;
+            if constexpr (MULTI) {
+                if (pit == 0 && it > 0) {
+                    // A new pass: once this CTA's last item of the previous
+                    // pass is flushed, the pass's first items (held back)
+                    // are issued.
+                    okp = mbar_wait(&acc_free[(it - 1) % kAccSets], ((it - 1) / kAccSets) & 1);
+                    for (int j = it; okp && j <= it + ahead && j < pass_end; ++j) okp = produce(j, j % nst, j / nst);
+                }
+                if (okp && it + ahead + 1 < pass_end) okp = produce(it + ahead + 1, sp, usep);
+            } else {
+                okp = produce(it + ahead + 1, sp, usep);
+            }
+            if (!okp) {
+                *abort_flag = 1;
+                atomicOr(err, 1);
+            }
         }
         if (!__all_sync(0xffffffffu, mbar_wait(&full[s], ph & 1))) {
             if (lane == 0) {
@@ -1090,6 +1359,55 @@ __global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB) k_assign_pi
         }
         unsigned char *const stage_s = smem_raw + (size_t)s * stage_bytes;
         const TileGeom &g = hdr[it % kHdrSlots];
+        if constexpr (MULTI) {
+            const MultiHdr &mh = mhdr[it % kHdrSlots];
+            if (mh.kind == 1) {
+                // An update chunk: no data in the stage, no pixel sums.
+                const int cf = g.f, c0 = mh.c0, cn = mh.cn, cpass = mh.pass;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+                const int set = it % kAccSets;
+                bool okc =
+                    it < kAccSets || __all_sync(0xffffffffu, mbar_wait(&acc_free[set], ((it / kAccSets) - 1) & 1));
+                // The previous item's sums first: its tile may be one this
+                // chunk waits for.
+                if (okc && it > 0 && !prev_flushed)
+                    okc = flush_tile<NW, NCOPY, MULTI>(hdr, mhdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1,
+                                                       warp, lane);
+                const FrameArgs &a = frames[cf];
+                if (okc) {
+                    bool okw = true;
+                    if (lane == 0)
+                        okw = wait_count(&a.cstate->tiles_done, (TH == 64 ? a.n_tiles64 : a.n_tiles) * (cpass + 1),
+                                         err);
+                    okc = __shfl_sync(0xffffffffu, okw ? 1 : 0, 0) != 0;
+                }
+                if (okc) {
+                    update_chunk<NT>(a, c0, cn, cpass + 1, tid);
+                    __syncwarp();
+                    if (lane == 0) {
+                        // this warp's part of the chunk is done (release)
+                        fence_proxy_async_global();
+                        __threadfence();
+                        atomicAdd(&a.cstate->chunks_done, 1);
+                        mbar_arrive(&acc_done[set]);
+                    }
+                    if (pit == n_local - 1)
+                        okc = flush_tile<NW, NCOPY, MULTI>(hdr, mhdr, wacc0, acc_words, win_max, acc_done, acc_free, it,
+                                                           warp, lane);
+                    prev_flushed = pit == n_local - 1;
+                }
+                if (!okc) {
+                    if (lane == 0) {
+                        *abort_flag = 1;
+                        atomicOr(err, 1);
+                    }
+                    ok = false;
+                    break;
+                }
+                continue;
+            }
+        }
         const int bw = g.box_w, tx0 = g.tx0, ty0 = g.ty0, wx0 = g.wx0, wy0 = g.wy0;
         const int W = g.W, H = g.H, S = g.S, ns_c = g.ns_c;
         const unsigned s_mul = g.s_mul;
@@ -1280,8 +1598,9 @@ __global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB) k_assign_pi
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_done[set]);
             // Flush the previous tile's sums (one warp per tile).
-            if (it > 0 &&
-                !flush_tile<NW, NCOPY>(hdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
+            if (it > 0 && !(MULTI && prev_flushed) &&
+                !flush_tile<NW, NCOPY, MULTI>(hdr, mhdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp,
+                                              lane)) {
                 if (lane == 0) {
                     *abort_flag = 1;
                     atomicOr(err, 1);
@@ -1289,10 +1608,24 @@ __global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB) k_assign_pi
                 ok = false;
                 break;
             }
+            if constexpr (MULTI) {
+                // a pass's last item is flushed at once (see above)
+                if (pit == n_local - 1 &&
+                    !flush_tile<NW, NCOPY, MULTI>(hdr, mhdr, wacc0, acc_words, win_max, acc_done, acc_free, it, warp,
+                                                  lane)) {
+                    if (lane == 0) {
+                        *abort_flag = 1;
+                        atomicOr(err, 1);
+                    }
+                    ok = false;
+                    break;
+                }
+                prev_flushed = pit == n_local - 1;
+            }
         }
     }
-    if (!LAST && ok && it > 0 &&
-        !flush_tile<NW, NCOPY>(hdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
+    if (!LAST && !MULTI && ok && it > 0 &&
+        !flush_tile<NW, NCOPY, MULTI>(hdr, mhdr, wacc0, acc_words, win_max, acc_done, acc_free, it - 1, warp, lane)) {
         if (lane == 0) {
             *abort_flag = 1;
             atomicOr(err, 1);
@@ -1305,6 +1638,23 @@ __global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB) k_assign_pi
         const int last = flags[1];
         for (int j = max(0, last - nst + 1); j <= last; ++j) mbar_wait(&full[j % nst], (j / nst) & 1);
     }
+}
+
+template <bool LAST, bool SAME, int MINB, int ROWS, int TH>
+__global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB)
+    k_assign_pipe(const FrameArgs *frames, int n_frames, int total_tiles, int win_max, int nst, int *err,
+                  int check_stop) {
+    assign_pipe_body<LAST, SAME, MINB, ROWS, TH, false>(frames, n_frames, total_tiles, win_max, nst, err, check_stop,
+                                                        1, 0);
+}
+
+// The passes before the last with their updates, in one cooperative launch.
+template <bool SAME, int MINB, int ROWS, int TH>
+__global__ void __launch_bounds__(kThreads / ROWS * (TH / 32), MINB)
+    k_assign_multi(const FrameArgs *frames, int n_frames, int total_tiles, int total_chunks, int win_max, int nst,
+                   int *err, int check_stop, int passes) {
+    assign_pipe_body<false, SAME, MINB, ROWS, TH, true>(frames, n_frames, total_tiles, win_max, nst, err, check_stop,
+                                                        passes, total_chunks);
 }
 
 // Resident CTAs per SM of one instantiation (the query honours the
@@ -1320,8 +1670,26 @@ static int pipe_occupancy_of(size_t smem) {
     return blocks;
 }
 
-int assign_pipe_occupancy(bool same, int win_n, int nst, int rows, int tile_h) {
-    const size_t sm = assign_pipe_smem_bytes(win_n, false, nst, rows, tile_h);
+template <bool SM, int MINB, int ROWS, int TH>
+static int multi_occupancy_of(size_t smem) {
+    int blocks = 0;
+    if (cudaFuncSetAttribute(k_assign_multi<SM, MINB, ROWS, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_assign_multi<SM, MINB, ROWS, TH>,
+                                                      kThreads / ROWS * (TH / 32), smem) != cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+int assign_pipe_occupancy(bool same, int win_n, int nst, int rows, int tile_h, bool multi) {
+    const size_t sm = assign_pipe_smem_bytes(win_n, false, nst, rows, tile_h, multi);
+    if (multi) {
+        if (tile_h == 64) return rows == 2 && same ? multi_occupancy_of<true, 2, 2, 64>(sm) : 0;
+        if (rows == 2) return same ? multi_occupancy_of<true, 4, 2, 32>(sm) : 0;
+        const int o4 = same ? multi_occupancy_of<true, 4, 1, 32>(sm) : multi_occupancy_of<false, 4, 1, 32>(sm);
+        const int o3 = same ? multi_occupancy_of<true, 3, 1, 32>(sm) : multi_occupancy_of<false, 3, 1, 32>(sm);
+        return o4 >= 4 ? o4 : o3;
+    }
     if (tile_h == 64) return rows == 2 && same ? pipe_occupancy_of<false, true, 2, 2, 64>(sm) : 0;
     if (rows == 2) return same ? pipe_occupancy_of<false, true, 4, 2>(sm) : 0;
     // The 4-CTA build (64 registers) where shared memory allows, else the 3-CTA build.
@@ -1375,6 +1743,58 @@ cudaError_t launch_assign_pipe(const FrameArgs *d_frames, int n, int total_tiles
                 : launch_pipe_as<false, false, 3, 1>(d_frames, n, total_tiles, win_max, nst, grid, smem, err, check_stop, s);
 }
 
+// Cooperative launch (every CTA resident at once: the fused kernel's CTAs
+// wait on one another's phase counters).
+template <bool SM, int MINB, int ROWS, int TH>
+static cudaError_t launch_multi_as(const FrameArgs *d_frames, int n, int total_tiles, int total_chunks, int win_max,
+                                   int nst, int passes, int grid, size_t smem, int *err, int check_stop,
+                                   cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_assign_multi<SM, MINB, ROWS, TH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)(kThreads / ROWS * (TH / 32)));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_assign_multi<SM, MINB, ROWS, TH>, d_frames, n, total_tiles, total_chunks,
+                              win_max, nst, err, check_stop, passes);
+}
+
+cudaError_t launch_assign_multi(const FrameArgs *d_frames, int n, int total_tiles, int total_chunks, int win_max,
+                                bool same, int passes, int nst, int rows, int tile_h, int ctas_per_sm, int grid,
+                                int *err, int check_stop, cudaStream_t s) {
+    if (passes < 1) return cudaSuccess;
+    if (grid > total_tiles) grid = total_tiles;
+    if (grid < 1) grid = 1;
+    if (nst < 3) nst = 3;
+    if (nst > kMaxStages) nst = kMaxStages;
+    if (rows == 2 && !same) return cudaErrorInvalidValue;
+    if (tile_h != 32 && (tile_h != 64 || rows != 2)) return cudaErrorInvalidValue;
+    const size_t smem = assign_pipe_smem_bytes(win_max, false, nst, rows, tile_h, true);
+    if (tile_h == 64)
+        return launch_multi_as<true, 2, 2, 64>(d_frames, n, total_tiles, total_chunks, win_max, nst, passes, grid,
+                                               smem, err, check_stop, s);
+    if (rows == 2)
+        return launch_multi_as<true, 4, 2, 32>(d_frames, n, total_tiles, total_chunks, win_max, nst, passes, grid,
+                                               smem, err, check_stop, s);
+    const bool wide = ctas_per_sm >= 4;  // 64-register build
+    if (same)
+        return wide ? launch_multi_as<true, 4, 1, 32>(d_frames, n, total_tiles, total_chunks, win_max, nst, passes,
+                                                      grid, smem, err, check_stop, s)
+                    : launch_multi_as<true, 3, 1, 32>(d_frames, n, total_tiles, total_chunks, win_max, nst, passes,
+                                                      grid, smem, err, check_stop, s);
+    return wide ? launch_multi_as<false, 4, 1, 32>(d_frames, n, total_tiles, total_chunks, win_max, nst, passes, grid,
+                                                   smem, err, check_stop, s)
+                : launch_multi_as<false, 3, 1, 32>(d_frames, n, total_tiles, total_chunks, win_max, nst, passes, grid,
+                                                   smem, err, check_stop, s);
+}
+
 cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cudaStream_t s) {
     k_fill_ring<<<dim3((max_ring + 255) / 256, n), 256, 0, s>>>(d_frames, n, max_ring);
     return cudaGetLastError();
@@ -1383,85 +1803,6 @@ cudaError_t launch_fill_ring(const FrameArgs *d_frames, int n, int max_ring, cud
 // ---------------------------------------------------------------------------
 // Update: centre = member mean; empty centre keeps position and colour.
 // ---------------------------------------------------------------------------
-
-// Member mean from the exact integer sums, in FP32 (this GPU's FP64 rate is
-// a small fraction of its FP32 rate): the sum rounded to float, scaled by the
-// power of two fix_inv (exact) and divided by the count (correctly rounded),
-// so within about one unit in the last place of the exact mean.
-// Returns the centre's move |dx| + |dy| (0 for an empty cluster, or when
-// want_move is false: the old position is then not read).
-__device__ __forceinline__ float update_centre(long long *ak, const float *ci, float *co, float fix_inv,
-                                               bool want_move) {
-    const longlong2 s01 = *reinterpret_cast<const longlong2 *>(ak);
-    const longlong2 s23 = *reinterpret_cast<const longlong2 *>(ak + 2);
-    const longlong2 s45 = *reinterpret_cast<const longlong2 *>(ak + 4);
-    const long long n = s45.y;
-    float move = 0.0f;
-    if (n > 0) {
-        const float fn = (float)n;
-        const float x0 = want_move ? ci[3] : 0.0f, y0 = want_move ? ci[4] : 0.0f;
-        co[0] = __fdiv_rn((float)s01.x * fix_inv, fn);
-        co[1] = __fdiv_rn((float)s01.y * fix_inv, fn);
-        co[2] = __fdiv_rn((float)s23.x * fix_inv, fn);
-        const float xn = __fdiv_rn((float)s23.y, fn), yn = __fdiv_rn((float)s45.x, fn);
-        co[3] = xn;
-        co[4] = yn;
-        co[5] = fn;
-        if (want_move) move = fabsf(xn - x0) + fabsf(yn - y0);
-    } else {
-        if (co != ci) {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) co[c] = ci[c];
-        }
-        co[5] = 0.0f;
-    }
-    longlong2 *az = reinterpret_cast<longlong2 *>(ak);
-    az[0] = make_longlong2(0, 0);
-    az[1] = make_longlong2(0, 0);
-    az[2] = make_longlong2(0, 0);
-    return move;
-}
-
-// Stopping test before update `it` (1-based): the frame stops when it has
-// stopped already or update it-1 moved its K centres by a mean L1 distance
-// below eps (so update it-1 and its assignment were the last). Every thread
-// decides from the same stored values.
-__device__ __forceinline__ bool conv_stop(const ConvState *cs, float eps, int K, int it) {
-    if (!cs || !(eps > 0.0f)) return false;
-    if (*reinterpret_cast<const volatile int *>(&cs->done)) return true;
-    if (it < 2) return false;
-    long long e = 0;
-#pragma unroll
-    for (int i = 0; i < kResidLanes; ++i) e += cs->resid[(it - 1) % 3][i];
-    return (double)e < (double)eps * (double)kResidScale * (double)K;
-}
-
-// After update `it`: with the stopping test on, the sum of this warp's
-// moves into one of the frame's counters of slot it % 3 (one atomic per
-// warp when all its lanes belong to `cs`'s frame); from the frame's first
-// centre, the update count and the cleared slot of update it+1.
-__device__ __forceinline__ void conv_record(ConvState *cs, bool uniform, bool test_on, float move, bool first,
-                                            int it) {
-    if (test_on) {
-        long long v = (long long)__float2ll_rn(move * kResidScale);
-        const int lane_slot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % kResidLanes;
-        if (uniform) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if ((threadIdx.x & 31) == 0 && v != 0)
-                atomicAdd(reinterpret_cast<unsigned long long *>(&cs->resid[it % 3][lane_slot]), (unsigned long long)v);
-        } else if (v != 0) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(&cs->resid[it % 3][lane_slot]), (unsigned long long)v);
-        }
-    }
-    if (first) {
-        if (test_on) {
-#pragma unroll
-            for (int i = 0; i < kResidLanes; ++i) cs->resid[(it + 1) % 3][i] = 0;
-        }
-        cs->iters = it;
-    }
-}
 
 __global__ void k_update(long long *acc, const float *centres_in, float *centres_out, int K, float fix_inv,
                          ConvState *cs, float eps, int it) {

@@ -66,13 +66,20 @@ def test_batch_repeatable_and_launch_count(slic_gpu):
     n0 = bs.info[1]
     l2 = bs.segment()[0]
     torch.cuda.synchronize()
-    # conversion pre-pass, init, 5 assignments, 4 updates and one fused
-    # launch of both connectivity passes (pipelined kernel in use);
-    # independent of the number of frames
+    # conversion pre-pass, init, 5 assignments, 4 updates and one launch of
+    # both connectivity passes (pipelined kernel in use); independent of the
+    # number of frames
     assert bs.info[3] in (3, 4)
     assert bs.info[1] - n0 == 2 * 4 + 4
     for a, b in zip(l1, l2):
         assert torch.equal(a, b)
+    # fused: conversion, init, passes 0..3 with updates 1..4 in one launch,
+    # the last pass, connectivity
+    bs.set_fused(True)
+    n1 = bs.info[1]
+    l3 = bs.segment()[0]
+    assert bs.info[1] - n1 == 5 and bs.info[6] == 1
+    assert all(torch.equal(a, b) for a, b in zip(l1, l3))
 
 
 def test_batch_initial_centres(slic_gpu):
@@ -98,15 +105,16 @@ def test_autotune_writes_and_reuses_cache(slic_gpu, tmp_path):
     bs = pkg.BatchSegmenter(frames, iterations=2)
     bs.bind([_cuda(synth.voronoi_frame(f["width"], f["height"], 20, 6.0, 5)) for f in frames])
     cache = str(tmp_path / "tune.jsonl")
-    c1, st1, rw1, th1 = bs.autotune(cache)
-    assert c1 >= 1 and 3 <= st1 <= 4 and rw1 in (1, 2) and th1 in (32, 64)
+    c1, st1, rw1, th1, fu1 = bs.autotune(cache)
+    assert c1 >= 1 and 3 <= st1 <= 4 and rw1 in (1, 2) and th1 in (32, 64) and fu1 in (0, 1)
     line = json.loads(open(cache).read().splitlines()[0])
     assert line["ctas_per_sm"] == c1 and line["stages"] == st1 and line["rows"] == rw1 and line["tile_h"] == th1
+    assert line["fused"] == fu1
     assert "640x480s16" in line["key"]
-    bs.set_tuning(0, 3 if st1 != 3 else 4, 1, 32)
-    assert bs.autotune(cache) == (c1, st1, rw1, th1)   # served from the cache
+    bs.set_tuning(0, 3 if st1 != 3 else 4, 1, 32, fused=1 - fu1)
+    assert bs.autotune(cache) == (c1, st1, rw1, th1, fu1)   # served from the cache
     assert len(open(cache).read().splitlines()) == 1
-    assert bs.info[2:] == (c1, st1, rw1, th1)
+    assert bs.info[2:] == (c1, st1, rw1, th1, fu1)
 
 
 @pytest.mark.parametrize("stages", [3, 4])
@@ -190,7 +198,11 @@ def test_profile_timers_outside_capture(slic_gpu):
     pkg.slic_batch_profile_enable(bs.handle, True)
     bs.segment()
     times = pkg.slic_batch_profile_times(bs.handle)
-    assert len(times) == 4 and all(t > 0 for t in times)
+    assert len(times) == 4 and all(t > 0 for t in times)  # one per pass
+    bs.set_fused(True)
+    bs.segment()
+    times = pkg.slic_batch_profile_times(bs.handle)
+    assert len(times) == 4 + 2 and all(t > 0 for t in times)  # the fused passes 0..2, the last pass
     bs.status()
 
 
@@ -279,3 +291,79 @@ def test_rebind_is_stream_ordered(slic_gpu):
     for g, w in zip(got, (want_b, want_a, want_b, want_bi)):
         for x, y in zip(g[0] + g[1], w[0] + w[1]):
             assert torch.equal(x, y)
+
+
+def _fused_vs_passes(pkg, frames, imgs, iterations, shapes, **kw):
+    """Labels, centres and update counts of the fused launch equal one
+    launch per pass and per update, for each launch shape."""
+    import torch
+    bs = pkg.BatchSegmenter(frames, iterations=iterations, **kw)
+    bs.bind(imgs)
+    for shape in shapes:
+        bs.set_tuning(*shape)
+        bs.set_fused(False)
+        l0, c0 = bs.segment()
+        l0, c0 = [t.clone() for t in l0], [t.clone() for t in c0]
+        n0 = bs.iterations_run
+        bs.set_fused(True)
+        l1, c1 = bs.segment()
+        bs.status()
+        assert bs.iterations_run == n0, shape
+        for i in range(len(frames)):
+            assert torch.equal(l1[i], l0[i]), (shape, i)
+            assert torch.equal(c1[i], c0[i]), (shape, i)
+    bs.close()
+
+
+@pytest.mark.parametrize("iterations", [1, 4])
+def test_fused_passes_are_bit_exact(slic_gpu, iterations):
+    """Every build of the fused kernel (32x32 tiles with 4 or 8 pixels per
+    thread, 32x64 tiles; 1 to 4 CTAs per SM; 3 and 4 stages), on frames of
+    uneven size, S and m: a 1080p frame, ragged ones, a tiny one with fewer
+    tiles than CTAs, and one with the stopping test."""
+    pkg = slic_gpu
+    frames = [dict(width=1920, height=1080, S=16), dict(width=333, height=211, S=8),
+              dict(width=640, height=480, S=32, m=20.0), dict(width=64, height=48, S=16),
+              dict(width=1280, height=720, S=8, convergence=0.4)]
+    imgs = [_cuda(synth.hd_image(7)), _cuda(synth.voronoi_frame(333, 211, 15, 6.0, 11)),
+            _cuda(synth.voronoi_frame(640, 480, 30, 6.0, 12)), _cuda(synth.voronoi_frame(64, 48, 5, 6.0, 13)),
+            _cuda(synth.voronoi_frame(1280, 720, 200, 6.0, 14))]
+    shapes = [(0, 3, 1, 32), (4, 3, 1, 32), (0, 4, 1, 32), (0, 3, 2, 32), (2, 4, 2, 32), (0, 3, 2, 64),
+              (1, 3, 2, 64)]
+    _fused_vs_passes(pkg, frames, imgs, iterations, shapes)
+
+
+def test_fused_passes_other_cell_alignments(slic_gpu):
+    """S not a multiple of 4 (each pixel's own cell), in the 80- and
+    64-register builds; and one frame alone, whose pass holds its tiles and
+    its own update chunks only."""
+    pkg = slic_gpu
+    frames = [dict(width=333, height=257, S=13), dict(width=320, height=240, S=12), dict(width=97, height=61, S=7)]
+    imgs = [_cuda(synth.voronoi_frame(333, 257, 20, 6.0, 21)), _cuda(synth.small_image(22)),
+            _cuda(synth.voronoi_frame(97, 61, 8, 6.0, 23))]
+    _fused_vs_passes(pkg, frames, imgs, 3, [(0, 3, 1, 32), (4, 4, 1, 32)])
+    _fused_vs_passes(pkg, frames[:1], imgs[:1], 5, [(0, 3, 1, 32)])
+    _fused_vs_passes(pkg, [dict(width=1920, height=1080, S=16)], [_cuda(synth.hd_image(24))], 2,
+                     [(0, 3, 2, 64), (0, 3, 1, 32)])
+
+
+def test_fused_passes_full_bench_batch(slic_gpu):
+    """32 frames of 1920x1080 at 10 iterations (the throughput batch), in
+    the 32x64 shape: fused and per-pass launches agree bit for bit, and the
+    fused launch matches the single-frame path on two sampled frames."""
+    import torch
+    pkg = slic_gpu
+    host = [synth.voronoi_frame(1920, 1080, 400, 6.0, synth.seed_of(1, i)) for i in range(32)]
+    imgs = [_cuda(h) for h in host]
+    frames = [dict(width=1920, height=1080, S=16)] * 32
+    _fused_vs_passes(pkg, frames, imgs, 10, [(0, 3, 2, 64)])
+    bs = pkg.BatchSegmenter(frames, iterations=10)
+    bs.bind(imgs)
+    bs.set_tuning(0, 3, 2, 64)
+    labels, centres = bs.segment()
+    bs.status()
+    for i in (0, 31):
+        seg = pkg.Segmenter(1920, 1080, S=16, iterations=10)
+        l1, c1 = seg.segment(imgs[i])
+        assert torch.equal(labels[i], l1)
+        assert torch.equal(centres[i], c1)

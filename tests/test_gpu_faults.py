@@ -108,6 +108,35 @@ def test_pipelined_wait_timeout_is_reported(slic_gpu):
         assert torch.equal(a, b)
 
 
+def test_fused_passes_timeout_is_reported(slic_gpu):
+    """The same with the fused passes: the producers issue nothing, the
+    consumers' and the phase counters' bounded waits give up (the latter at
+    once when the error word is set), every CTA of the cooperative launch
+    exits, SLIC_ERR_TIMEOUT is reported once, and the next run is exact."""
+    import torch
+    pkg = slic_gpu
+    W, H = 320, 240
+    imgs = [_img(W, H, 90 + k) for k in range(3)]
+    bs = pkg.BatchSegmenter([dict(width=W, height=H, S=16)] * 3, iterations=2)
+    bs.bind(imgs)
+    bs.set_fused(True)
+    assert bs.info[6] == 1, "the fused passes are in use"
+    want = [l.clone() for l in bs.segment()[0]]
+    bs.status()
+    try:
+        pkg.slic_fault_inject(pkg.SLIC_FAULT_ABORT_COPIES, 1)
+        bs.segment()
+        with pytest.raises(pkg.SlicError) as ei:
+            bs.status()
+        assert ei.value.status == pkg.SLIC_ERR_TIMEOUT
+    finally:
+        pkg.slic_fault_inject(pkg.SLIC_FAULT_ABORT_COPIES, 0)
+    labels, _ = bs.segment()
+    bs.status()
+    for a, b in zip(labels, want):
+        assert torch.equal(a, b)
+
+
 def test_fault_inject_rejects_bad_arguments(slic_gpu):
     pkg = slic_gpu
     for kind, value in ((0, 1), (9, 1), (pkg.SLIC_FAULT_ALLOC, -1), (pkg.SLIC_FAULT_WALK_LIMIT, 1 << 40)):
