@@ -278,11 +278,11 @@ def run_ours(args):
     # --- the plain path at its iteration count, autotuned, one graph per step ---
     bs = _plain_batch(pkg, frames, n_plain, dev)
     if args.tuning:  # a fixed launch shape (profiling commands): no autotuning
-        tuning = (tuple(int(v) for v in args.tuning.split(",")) + (0,))[:5]
+        tuning = (tuple(int(v) for v in args.tuning.split(",")) + (0, 1))[:6]
         bs.set_tuning(*tuning)
     else:
         tuning = bs.autotune(tune_cache, stream=stream)
-    ctas_per_sm, stages, rows, tile_h, fused = tuning
+    ctas_per_sm, stages, rows, tile_h, fused, groups = tuning
     K_EFF = bs.K_eff[0]
     n0 = bs.info[1]
     graph = _capture(lambda: bs.segment(stream=stream), stream)
@@ -337,7 +337,9 @@ def run_ours(args):
     # one-row 64-register build the autotuner picks at 4 CTAs per SM, else
     # 3). Fused passes: the fused launch (passes 0..n-1 with their updates,
     # k_assign_multi<1,MINB,ROWS,TILE_H>) and the last pass; the fused launch
-    # is the dominant kernel, with n passes' work.
+    # is the dominant kernel, with n passes' work. With the timers on, the
+    # batch runs as one group of frames (concurrent groups would share the
+    # GPU during a launch, so its duration would not be its own).
     pb = bs if method["name"] == "plain" else _plain_batch(pkg, frames, n_plain, dev, tuning)
     pkg.slic_batch_profile_enable(pb.handle, True)
     graph_prof = _capture(lambda: pb.segment(stream=stream), stream)
@@ -393,7 +395,7 @@ def run_ours(args):
         eb = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=e_iters, device=dev)
         eb.dimg = torch.empty_like(images)  # one allocation: the step's frames move with one copy
         eb.bind([eb.dimg[f] for f in range(B)])
-        eb.set_tuning(ctas_per_sm, stages, rows, tile_h, fused=fused)
+        eb.set_tuning(ctas_per_sm, stages, rows, tile_h, fused=fused, groups=groups)
         if method["name"] == "learned":
             eb.set_warmstart(net)
         pair.append((eb, torch.cuda.Stream(device=dev), torch.empty((B, H, W), dtype=torch.int32).pin_memory(),
@@ -474,7 +476,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (B x 6.2 MB RGB + B x 8.3 MB labels per step)",
                        "graph": "one CUDA graph per step (one batched launch per stage)",
                        "ctas_per_sm": ctas_per_sm, "pipeline_stages": stages, "row_groups_per_warp": rows,
-                       "tile": f"32x{tile_h}", "fused_passes": bool(fused)},
+                       "tile": f"32x{tile_h}", "fused_passes": bool(fused), "frame_groups": groups},
             "roofline": {"kernel": (f"{kname} (passes 0..{n_plain - 1} with their updates, all frames)" if fused_dom
                                     else f"{kname} (middle assignment pass, all frames)"), "bound": "alu",
                          "unit": "Tsqrt/s", "achieved": achieved_tops, "peak": xu_peak, "frac": achieved_tops / xu_peak,
@@ -582,8 +584,8 @@ def mixed_batch_throughput(args, pkg, stream, dev):
     imgs = [torch.from_numpy(synth.mixed_batch_frame(f, w, h)).to(dev) for f, (w, h, _, _) in enumerate(specs)]
     bs = pkg.BatchSegmenter(frames, iterations=ITERS, device=dev)
     bs.bind(imgs)
-    ctas, stages, rows, tile_h, fused = bs.autotune(os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl"),
-                                                    stream=stream)
+    ctas, stages, rows, tile_h, fused, groups = bs.autotune(
+        os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl"), stream=stream)
     with torch.cuda.stream(stream):
         bs.segment(stream)
     torch.cuda.synchronize()
@@ -608,7 +610,7 @@ def mixed_batch_throughput(args, pkg, stream, dev):
     return {"frames": len(specs), "megapixels": px / 1e6, "ms_per_step": ms, "frames_per_s": len(specs) / (ms / 1e3),
             "megapixels_per_s": px / 1e6 / (ms / 1e3), "steps": steps, "ctas_per_sm": ctas, "pipeline_stages": stages,
             "row_groups_per_warp": rows, "tile": f"32x{tile_h}", "fused_passes": bool(fused),
-            "iterations": ITERS}
+            "frame_groups": groups, "iterations": ITERS}
 
 
 def _graph_ms(graph, stream, args, world, dev):
@@ -795,7 +797,7 @@ def main(argv=None):
     ap.add_argument("--iterations", type=int, default=None,
                     help="time the plain path at this iteration count instead of the one the agreement sweep "
                          "finds (skips the sweep and the learned leg; for profiling)")
-    ap.add_argument("--tuning", default=None, metavar="CTAS,STAGES,ROWS,TILE_H[,FUSED]",
+    ap.add_argument("--tuning", default=None, metavar="CTAS,STAGES,ROWS,TILE_H[,FUSED[,GROUPS]]",
                     help="launch shape of the assignment passes instead of autotuning (for profiling)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="run only the 256-frame mixed batch and print its line (for profiling)")

@@ -273,6 +273,20 @@ slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages, int
    bit-identical either way. SLIC_ERR_INVALID for enable not 0 or 1. */
 slic_status slic_batch_set_fused(slic_batch b, int enable);
 
+/* Frame groups (1 .. min(4, n_frames); default 1): the batch runs as
+   `groups` runs of consecutive frames of about equal pixel count, each
+   enqueued on its own stream (the caller's stream for the first, streams of
+   the batch for the others, forked from the caller's stream and joined back
+   to it by events, so the call stays stream-ordered and can be captured in
+   a CUDA graph). The groups' kernels run concurrently, so one group's pass
+   boundaries (the last tiles of a pass, the update) overlap another group's
+   passes. Results are bit-identical for any grouping. The learned warm
+   start, component connectivity (mode 2), the non-pipelined kernels and
+   profiling (slic_batch_profile_enable) run the batch as one group, as do
+   fused passes. A change after the buffers are bound waits for the device.
+   SLIC_ERR_INVALID outside the range. */
+slic_status slic_batch_set_groups(slic_batch b, int groups);
+
 /* Autotuner: time slic_batch_segment on the bound buffers for every launch
    shape that fits (3 timed runs each, CUDA events on `stream`; this waits
    for the device), keep the fastest, and append it to the JSON-lines file
@@ -280,19 +294,20 @@ slic_status slic_batch_set_fused(slic_batch b, int enable);
    iterations and the distinct (width, height, S). When the key is already
    in the file its entry is used without timing. The search covers tile
    shapes x row groups per warp x pipeline stages x CTAs per SM x fused
-   passes or not (slic_batch_set_fused); the choice is set on the batch and
-   returned in *ctas_per_sm, *stages, *rows, *tile_h and *fused (any may be
+   passes or not (slic_batch_set_fused) x frame groups (1, 2 or 4;
+   slic_batch_set_groups); the choice is set on the batch and returned in
+   *ctas_per_sm, *stages, *rows, *tile_h, *fused and *groups (any may be
    NULL). */
 slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm, int *stages,
-                               int *rows, int *tile_h, int *fused);
+                               int *rows, int *tile_h, int *fused, int *groups);
 
 /* Pixels of all frames, kernel launches enqueued so far, and the launch
    shape of the assignment passes: CTAs per SM (as requested, capped by what
-   fits), pipeline stages, row groups per warp, tile rows and fused passes
-   (stages and rows 0, tile rows 32, fused 0 when the pipelined kernel is not
-   used); any pointer may be NULL. */
+   fits), pipeline stages, row groups per warp, tile rows, fused passes and
+   frame groups (stages and rows 0, tile rows 32, fused 0 when the
+   pipelined kernel is not used); any pointer may be NULL. */
 slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm,
-                            int *stages, int *rows, int *tile_h, int *fused);
+                            int *stages, int *rows, int *tile_h, int *fused, int *groups);
 
 /* Grid of frame `frame` (Sec. 2): its S and ns_c x ns_r cells, K_eff =
    ns_c*ns_r centres (any pointer may be NULL); SLIC_ERR_INVALID for a frame

@@ -18,7 +18,8 @@ from ._binding import (SLIC_CIELAB, SLIC_ERR_CUDA, SLIC_ERR_INVALID, SLIC_ERR_NO
                        slic_batch_profile_enable, slic_batch_set_warmstart, slic_set_warmstart,
                        slic_batch_profile_read,
                        slic_batch_profile_times, slic_batch_segment, slic_batch_segment_host,
-                       slic_batch_rebind, slic_batch_set_buffers, slic_batch_set_fused, slic_batch_set_tuning,
+                       slic_batch_rebind, slic_batch_set_buffers, slic_batch_set_fused, slic_batch_set_groups,
+                       slic_batch_set_tuning,
                        slic_batch_status,
                        slic_connectivity_components, slic_connectivity_pass, slic_convert, slic_create,
                        slic_destroy, slic_grid, slic_status_check,
@@ -219,15 +220,23 @@ class BatchSegmenter:
                                 _stream_handle(stream))
 
     def autotune(self, cache_path=None, stream=None):
-        """Time the launch shapes that fit; -> (ctas_per_sm, stages, rows, tile_h, fused) chosen."""
+        """Time the launch shapes that fit; -> (ctas_per_sm, stages, rows, tile_h, fused, groups) chosen."""
         return slic_batch_autotune(self.handle, cache_path, _stream_handle(stream))
 
-    def set_tuning(self, ctas_per_sm: int, stages: int = 0, rows: int = 0, tile_h: int = 0, fused=None):
-        """A launch shape (as autotune returns it); fused None keeps the
-        fused-passes setting."""
+    def set_tuning(self, ctas_per_sm: int, stages: int = 0, rows: int = 0, tile_h: int = 0, fused=None,
+                   groups=None):
+        """A launch shape (as autotune returns it); fused / groups None keep
+        those settings."""
         slic_batch_set_tuning(self.handle, ctas_per_sm, stages, rows, tile_h)
         if fused is not None:
             slic_batch_set_fused(self.handle, bool(fused))
+        if groups is not None:
+            slic_batch_set_groups(self.handle, int(groups))
+
+    def set_groups(self, groups: int):
+        """Run the frames as `groups` runs of consecutive frames on
+        concurrent streams (1 .. min(4, frames))."""
+        slic_batch_set_groups(self.handle, groups)
 
     def set_fused(self, enable: bool = True):
         """The passes before the last and their updates in one cooperative

@@ -62,11 +62,12 @@ _SIGNATURES = {
     "slic_batch_segment_host": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
     "slic_batch_set_tuning": [_P, _I, _I, _I, _I],
     "slic_batch_set_fused": [_P, _I],
+    "slic_batch_set_groups": [_P, _I],
     "slic_batch_autotune": [_P, ctypes.c_char_p, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
-                            ctypes.POINTER(_I), ctypes.POINTER(_I)],
+                            ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "slic_batch_info": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                         ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
-                        ctypes.POINTER(_I)],
+                        ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "slic_batch_destroy": [_P],
     "slic_batch_status": [_P],
     "slic_batch_iterations_run": [_P, ctypes.POINTER(_I)],
@@ -272,21 +273,25 @@ def slic_batch_set_fused(b: int, enable: bool) -> None:
     _bcheck(lib().slic_batch_set_fused(b, 1 if enable else 0), b)
 
 
+def slic_batch_set_groups(b: int, groups: int) -> None:
+    _bcheck(lib().slic_batch_set_groups(b, int(groups)), b)
+
+
 def slic_batch_autotune(b: int, cache_path: str | None = None, stream: int = 0):
-    """-> (ctas_per_sm, stages, rows, tile_h, fused) chosen."""
-    c, st, rw, th, fu = _I(), _I(), _I(), _I(), _I()
+    """-> (ctas_per_sm, stages, rows, tile_h, fused, groups) chosen."""
+    c, st, rw, th, fu, gr = _I(), _I(), _I(), _I(), _I(), _I()
     path = cache_path.encode() if cache_path else None
     _bcheck(lib().slic_batch_autotune(b, path, stream or None, ctypes.byref(c), ctypes.byref(st), ctypes.byref(rw),
-                                      ctypes.byref(th), ctypes.byref(fu)), b)
-    return c.value, st.value, rw.value, th.value, fu.value
+                                      ctypes.byref(th), ctypes.byref(fu), ctypes.byref(gr)), b)
+    return c.value, st.value, rw.value, th.value, fu.value, gr.value
 
 
 def slic_batch_info(b: int):
-    """-> (total_pixels, launches, ctas_per_sm, stages, rows, tile_h, fused)."""
-    px, n, c, st, rw, th, fu = ctypes.c_longlong(), ctypes.c_longlong(), _I(), _I(), _I(), _I(), _I()
+    """-> (total_pixels, launches, ctas_per_sm, stages, rows, tile_h, fused, groups)."""
+    px, n, c, st, rw, th, fu, gr = ctypes.c_longlong(), ctypes.c_longlong(), _I(), _I(), _I(), _I(), _I(), _I()
     _bcheck(lib().slic_batch_info(b, ctypes.byref(px), ctypes.byref(n), ctypes.byref(c), ctypes.byref(st),
-                                  ctypes.byref(rw), ctypes.byref(th), ctypes.byref(fu)), b)
-    return px.value, n.value, c.value, st.value, rw.value, th.value, fu.value
+                                  ctypes.byref(rw), ctypes.byref(th), ctypes.byref(fu), ctypes.byref(gr)), b)
+    return px.value, n.value, c.value, st.value, rw.value, th.value, fu.value, gr.value
 
 
 def slic_connectivity_components(h: int, d_in: int, d_out: int, stream: int = 0) -> None:

@@ -47,6 +47,18 @@ struct slic_batch_ctx {
     int total_tiles64 = 0, win_max64 = 0;  // the same for 32x64 tiles
     int total_chunks = 0;    // update chunks of all frames (fused passes)
     bool fused = false;      // the passes before the last in one cooperative launch
+    // Groups: the frames run as `groups` runs of consecutive frames (split
+    // by pixel count), each enqueued on its own stream (the caller's for the
+    // first, internal ones for the others, forked from and joined back to
+    // the caller's stream by events), so one group's pass boundaries overlap
+    // another's passes. Each group has a frame table of its own in the tables
+    // block, its bases counted from its first frame.
+    int groups = 1;
+    std::vector<int> group_first;              // groups + 1 frame indices
+    size_t tbl_grp = 0;                        // offset of the group tables in the tables block
+    const FrameArgs *d_group_frames = nullptr; // (in the current tables block)
+    cudaStream_t gstream[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
     int total_units = 0;  // work units of the fused connectivity kernel
     long long total_pixels = 0;
     bool same = true;        // every frame's S a multiple of 4 (4-pixel groups share a cell)
@@ -202,9 +214,9 @@ std::string tune_key(const slic_batch_ctx *b) {
 }
 
 // Cache lines: {"key": "<key>", "ctas_per_sm": <int>, "stages": <int>, "rows": <int>, "tile_h": <int>,
-// "fused": <0|1>, "ms": <float>}
+// "fused": <0|1>, "groups": <int>, "ms": <float>}
 bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stages, int *rows, int *tile_h,
-                  int *fused) {
+                  int *fused, int *groups) {
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
     char line[4096];
@@ -217,11 +229,14 @@ bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stag
             const char *o = std::strstr(line, "\"rows\":");
             const char *t = std::strstr(line, "\"tile_h\":");
             const char *z = std::strstr(line, "\"fused\":");
-            int v = 0, w = 0, u = 0, h = 0, fz = -1;
-            if (q && r && o && t && z && std::sscanf(q + 14, "%d", &v) == 1 && std::sscanf(r + 9, "%d", &w) == 1 &&
-                std::sscanf(o + 7, "%d", &u) == 1 && std::sscanf(t + 9, "%d", &h) == 1 &&
-                std::sscanf(z + 8, "%d", &fz) == 1 && v > 0 && w >= 3 && w <= 4 && (u == 1 || u == 2) &&
-                (h == 32 || h == 64) && (fz == 0 || fz == 1)) {
+            const char *gp = std::strstr(line, "\"groups\":");
+            int v = 0, w = 0, u = 0, h = 0, fz = -1, gn = 0;
+            if (q && r && o && t && z && gp && std::sscanf(q + 14, "%d", &v) == 1 &&
+                std::sscanf(r + 9, "%d", &w) == 1 && std::sscanf(o + 7, "%d", &u) == 1 &&
+                std::sscanf(t + 9, "%d", &h) == 1 && std::sscanf(z + 8, "%d", &fz) == 1 &&
+                std::sscanf(gp + 9, "%d", &gn) == 1 && v > 0 && w >= 3 && w <= 4 && (u == 1 || u == 2) &&
+                (h == 32 || h == 64) && (fz == 0 || fz == 1) && gn >= 1 && gn <= 4) {
+                *groups = gn;
                 *ctas = v;
                 *stages = w;
                 *rows = u;
@@ -236,13 +251,13 @@ bool cache_lookup(const char *path, const std::string &key, int *ctas, int *stag
 }
 
 void cache_store(const char *path, const std::string &key, int ctas, int stages, int rows, int tile_h, int fused,
-                 float ms) {
+                 int groups, float ms) {
     FILE *f = std::fopen(path, "a");
     if (!f) return;
     std::fprintf(f,
                  "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"stages\": %d, \"rows\": %d, \"tile_h\": %d, "
-                 "\"fused\": %d, \"ms\": %.4f}\n",
-                 key.c_str(), ctas, stages, rows, tile_h, fused, ms);
+                 "\"fused\": %d, \"groups\": %d, \"ms\": %.4f}\n",
+                 key.c_str(), ctas, stages, rows, tile_h, fused, groups, ms);
     std::fclose(f);
 }
 
@@ -287,6 +302,23 @@ cudaError_t upload_tables(slic_batch_ctx *b, int k, cudaStream_t s) {
     std::memcpy(h, b->frames.data(), sizeof(FrameArgs) * b->n);
     if (b->connectivity == 2) std::memcpy(h + b->tbl_ccl, b->ccl_frames.data(), sizeof(CclFrame) * b->n);
     std::memcpy(h + b->tbl_img, b->images.data(), sizeof(const uint8_t *) * b->n);
+    // group tables: the frames again, each group's bases counted from its
+    // first frame (its kernels index tiles, centres, rows, connectivity
+    // units and update chunks from 0)
+    FrameArgs *gt = reinterpret_cast<FrameArgs *>(h + b->tbl_grp);
+    for (int g = 0; g < b->groups; ++g) {
+        const FrameArgs &a0 = b->frames[b->group_first[g]];
+        for (int f = b->group_first[g]; f < b->group_first[g + 1]; ++f) {
+            FrameArgs a = b->frames[f];
+            a.tile_base -= a0.tile_base;
+            a.tile_base64 -= a0.tile_base64;
+            a.centre_base -= a0.centre_base;
+            a.row_base -= a0.row_base;
+            a.strip_base -= a0.strip_base;
+            a.chunk_base -= a0.chunk_base;
+            gt[f] = a;
+        }
+    }
     e = cudaMemcpyAsync(d, h, b->tbl_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(b->staged[k], s);
     if (e != cudaSuccess) return e;
@@ -294,6 +326,7 @@ cudaError_t upload_tables(slic_batch_ctx *b, int k, cudaStream_t s) {
     b->d_frames = reinterpret_cast<FrameArgs *>(d);
     b->d_ccl = reinterpret_cast<CclFrame *>(d + b->tbl_ccl);
     b->d_img_table = reinterpret_cast<const uint8_t *const *>(d + b->tbl_img);
+    b->d_group_frames = reinterpret_cast<const FrameArgs *>(d + b->tbl_grp);
     return launch_fill_ring(b->d_frames, b->n, b->max_ring, s);
 }
 
@@ -403,7 +436,9 @@ slic_status slic_batch_create(const slic_params *params, int n_frames, slic_batc
     }
     b->tbl_ccl = align256(sizeof(FrameArgs) * (size_t)n_frames);
     b->tbl_img = b->tbl_ccl + align256(sizeof(CclFrame) * (size_t)n_frames);
-    b->tbl_bytes = b->tbl_img + align256(sizeof(const uint8_t *) * (size_t)n_frames);
+    b->tbl_grp = b->tbl_img + align256(sizeof(const uint8_t *) * (size_t)n_frames);
+    b->tbl_bytes = b->tbl_grp + align256(sizeof(FrameArgs) * (size_t)n_frames);
+    b->group_first = {0, n_frames};
     b->total_tiles = (int)tiles;
     b->total_tiles64 = (int)tiles64;
     {
@@ -478,6 +513,11 @@ slic_status slic_batch_destroy(slic_batch b) {
     cudaFreeHost(b->staging);
     for (cudaEvent_t ev : b->staged)
         if (ev) cudaEventDestroy(ev);
+    for (int g = 0; g < 3; ++g) {
+        if (b->gstream[g]) cudaStreamDestroy(b->gstream[g]);
+        if (b->ev_join[g]) cudaEventDestroy(b->ev_join[g]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     cudaFree(b->net_labels);
     for (auto &ev : b->events) {
         cudaEventDestroy(ev.first);
@@ -520,43 +560,77 @@ slic_status slic_batch_rebind(slic_batch b, const uint8_t *const *d_images, int3
     return SLIC_OK;
 }
 
-slic_status slic_batch_segment(slic_batch b, void *stream) {
-    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
-    if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
-    cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// A run of consecutive frames as the kernels see it: its device frame table
+// (bases counted from its first frame) and its totals.
+struct Span {
+    const FrameArgs *frames;
+    int n, tiles, tiles64, centres, rows, units, chunks;
+};
+
+// Group g of the batch (g < 0: the whole batch, with its own table).
+Span span_of(const slic_batch_ctx *b, int g) {
+    if (g < 0)
+        return Span{b->d_frames, b->n, b->total_tiles, b->total_tiles64, b->total_centres, b->total_rows,
+                    b->total_units, b->total_chunks};
+    const int f0 = b->group_first[g], f1 = b->group_first[g + 1];
+    const FrameArgs &a = b->frames[f0];
+    const bool end = f1 == b->n;
+    const FrameArgs *z = end ? nullptr : &b->frames[f1];
+    return Span{b->d_group_frames + f0, f1 - f0,
+                (end ? b->total_tiles : z->tile_base) - a.tile_base,
+                (end ? b->total_tiles64 : z->tile_base64) - a.tile_base64,
+                (end ? b->total_centres : z->centre_base) - a.centre_base,
+                (end ? b->total_rows : z->row_base) - a.row_base,
+                (end ? b->total_units : z->strip_base) - a.strip_base,
+                (end ? b->total_chunks : z->chunk_base) - a.chunk_base};
+}
+
+// Every stage of a segmentation of the span's frames, enqueued on s: the
+// conversion pre-pass (pipelined kernel) or the first pass's conversion,
+// the initialisation, the learned warm start (whole batch only), the passes
+// and updates (fused or one launch each), connectivity. `whole`: the span
+// is the whole batch (the warm start, component connectivity and the
+// profiling events need it).
+cudaError_t enqueue_span(slic_batch_ctx *b, const Span &sp, cudaStream_t s, bool whole, long long &n_launch,
+                         std::string &why) {
     const int grid = grid_for(b, b->occupancy);
     const int grid_pipe = b->pipe ? grid_for(b, pipe_occ(b, b->stages, b->rows, b->tile_h)) : grid;
     const int pipe_per_sm = grid_pipe / std::max(1, b->sms);
     // With the pipelined kernel every pass reads features: a conversion
     // pre-pass writes them, and the first pass is pipelined as well.
     cudaError_t e = cudaSuccess;
-    long long n_launch = 0;
     if (b->pipe) {
-        e = launch_convert_batch(b->d_frames, b->n, b->total_rows, b->max_w, s);
+        e = launch_convert_batch(sp.frames, sp.n, sp.rows, b->max_w, s);
         ++n_launch;
     }
-    if (e == cudaSuccess) e = launch_init_batch(b->d_frames, b->n, b->total_centres, s);
+    if (e == cudaSuccess) e = launch_init_batch(sp.frames, sp.n, sp.centres, s);
     ++n_launch;
-    const bool warm = b->net != nullptr;
+    const bool warm = whole && b->net != nullptr;
     if (warm) {
         // Learned warm start: the network's labels, their member sums (from
         // the features of the pre-pass) and one update without the stopping
         // test's bookkeeping (update 0) turn them into the initial centres.
         if (e == cudaSuccess && !b->pipe) {
-            e = launch_convert_batch(b->d_frames, b->n, b->total_rows, b->max_w, s);
+            e = launch_convert_batch(sp.frames, sp.n, sp.rows, b->max_w, s);
             ++n_launch;
         }
-        if (e == cudaSuccess && net_forward_labels(b->net, b->n, nullptr, b->d_img_table, b->net_C, b->net_labels,
-                                                   s) != cudaSuccess)
-            return bfail(b, SLIC_ERR_CUDA, std::string("network forward: ") + slic_net_last_error(b->net));
-        if (e == cudaSuccess) e = launch_accumulate_labels_batch(b->d_frames, b->n, b->total_rows, b->max_w, s);
-        if (e == cudaSuccess) e = launch_update_batch(b->d_frames, b->n, b->total_centres, 0, s);
+        if (e == cudaSuccess &&
+            net_forward_labels(b->net, b->n, nullptr, b->d_img_table, b->net_C, b->net_labels, s) != cudaSuccess) {
+            why = std::string("network forward: ") + slic_net_last_error(b->net);
+            return cudaErrorLaunchFailure;
+        }
+        if (e == cudaSuccess) e = launch_accumulate_labels_batch(sp.frames, sp.n, sp.rows, b->max_w, s);
+        if (e == cudaSuccess) e = launch_update_batch(sp.frames, sp.n, sp.centres, 0, s);
         n_launch += 2;
     }
     // Event pair around one assignment launch when profiling.
     auto timed = [&](auto launch) -> cudaError_t {
         cudaEvent_t e1 = nullptr;
-        if (b->profiling) {
+        if (b->profiling && whole) {
             if (b->ev_used == b->events.size()) {
                 cudaEvent_t x, y;
                 if (cudaEventCreate(&x) != cudaSuccess || cudaEventCreate(&y) != cudaSuccess)
@@ -572,32 +646,32 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
         ++n_launch;
         return r;
     };
-    const int tiles_th = b->tile_h == 64 ? b->total_tiles64 : b->total_tiles;
+    const int tiles_th = b->tile_h == 64 ? sp.tiles64 : sp.tiles;
     const int win_th = b->tile_h == 64 ? b->win_max64 : b->win_max;
     auto last_or_pass = [&](int pass) {
         return [&, pass]() {
-            return b->pipe ? launch_assign_pipe(b->d_frames, b->n, tiles_th, win_th, b->same, pass == b->iterations,
+            return b->pipe ? launch_assign_pipe(sp.frames, sp.n, tiles_th, win_th, b->same, pass == b->iterations,
                                                 b->stages, b->rows, b->tile_h, pipe_per_sm, grid_pipe, b->d_err,
                                                 b->any_conv ? 1 : 0, s)
-                           : launch_assign_batch(b->d_frames, b->n, b->total_tiles, b->win_max, b->same,
-                                                 pass == 0 && !warm, pass == b->iterations, b->smem, grid, s);
+                           : launch_assign_batch(sp.frames, sp.n, sp.tiles, b->win_max, b->same, pass == 0 && !warm,
+                                                 pass == b->iterations, b->smem, grid, s);
         };
     };
-    if (e == cudaSuccess && b->pipe && b->fused && b->iterations > 0) {
+    if (e == cudaSuccess && b->pipe && b->fused && whole && b->iterations > 0) {
         // Passes 0 .. n-1 with updates 1 .. n in one cooperative launch
         // (per-frame phase counters order them), then the last pass.
         const int occ = std::max(1, assign_pipe_occupancy(b->same, win_th, b->stages, b->rows, b->tile_h, true));
         const int grid_multi = grid_for(b, occ);
         e = timed([&]() {
-            return launch_assign_multi(b->d_frames, b->n, tiles_th,
-                                       b->total_chunks, win_th, b->same, b->iterations, b->stages, b->rows, b->tile_h, grid_multi / std::max(1, b->sms),
-                                       grid_multi, b->d_err, b->any_conv ? 1 : 0, s);
+            return launch_assign_multi(sp.frames, sp.n, tiles_th, sp.chunks, win_th, b->same, b->iterations,
+                                       b->stages, b->rows, b->tile_h, grid_multi / std::max(1, b->sms), grid_multi,
+                                       b->d_err, b->any_conv ? 1 : 0, s);
         });
         if (e == cudaSuccess) e = timed(last_or_pass(b->iterations));
     } else {
         for (int pass = 0; e == cudaSuccess && pass <= b->iterations; ++pass) {
             if (pass > 0) {
-                e = launch_update_batch(b->d_frames, b->n, b->total_centres, pass, s);
+                e = launch_update_batch(sp.frames, sp.n, sp.centres, pass, s);
                 ++n_launch;
             }
             if (e == cudaSuccess) e = timed(last_or_pass(pass));
@@ -610,15 +684,46 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
         n_launch += 9;
     } else if (e == cudaSuccess && b->connectivity) {
         if (b->pipe) {
-            e = launch_connectivity2_batch(b->d_frames, b->n, b->total_units, b->sms * 8, s);
+            e = launch_connectivity2_batch(sp.frames, sp.n, sp.units, b->sms * 8, s);
             n_launch += 1;
         } else {
-            e = launch_connectivity_batch(b->d_frames, b->n, b->total_rows, b->max_w, 0, s);
-            if (e == cudaSuccess) e = launch_connectivity_batch(b->d_frames, b->n, b->total_rows, b->max_w, 1, s);
+            e = launch_connectivity_batch(sp.frames, sp.n, sp.rows, b->max_w, 0, s);
+            if (e == cudaSuccess) e = launch_connectivity_batch(sp.frames, sp.n, sp.rows, b->max_w, 1, s);
             n_launch += 2;
         }
     }
-    if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+slic_status slic_batch_segment(slic_batch b, void *stream) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
+    cudaStream_t s = (cudaStream_t)stream;
+    long long n_launch = 0;
+    std::string why;
+    cudaError_t e = cudaSuccess;
+    // Groups run concurrently only on the plain pipelined path (the warm
+    // start, component connectivity and the per-launch timers take the
+    // whole batch at once).
+    const bool split = b->groups > 1 && b->pipe && !b->net && b->connectivity != 2 && !b->profiling;
+    if (!split) {
+        e = enqueue_span(b, span_of(b, -1), s, true, n_launch, why);
+    } else {
+        e = cudaEventRecord(b->ev_fork, s);
+        for (int g = 1; g < b->groups && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(b->gstream[g - 1], b->ev_fork, 0);
+        for (int g = 0; g < b->groups && e == cudaSuccess; ++g)
+            e = enqueue_span(b, span_of(b, g), g == 0 ? s : b->gstream[g - 1], false, n_launch, why);
+        for (int g = 1; g < b->groups && e == cudaSuccess; ++g) {
+            e = cudaEventRecord(b->ev_join[g - 1], b->gstream[g - 1]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join[g - 1], 0);
+        }
+    }
+    if (e != cudaSuccess)
+        return bfail(b, SLIC_ERR_CUDA, why.empty() ? std::string("kernel launch: ") + cudaGetErrorString(e) : why);
     b->launches += n_launch;
     return SLIC_OK;
 }
@@ -708,6 +813,41 @@ slic_status slic_batch_set_tuning(slic_batch b, int ctas_per_sm, int stages, int
     return SLIC_OK;
 }
 
+slic_status slic_batch_set_groups(slic_batch b, int groups) {
+    if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
+    if (groups < 1 || groups > 4 || groups > b->n)
+        return bfail(b, SLIC_ERR_INVALID, "groups must be in [1, min(4, n_frames)]");
+    if (groups == b->groups) return SLIC_OK;
+    for (int g = 0; g + 1 < groups; ++g) {  // internal streams and events, made once
+        if (!b->gstream[g] && cudaStreamCreateWithFlags(&b->gstream[g], cudaStreamNonBlocking) != cudaSuccess)
+            return bfail(b, SLIC_ERR_CUDA, "cudaStreamCreate failed");
+        if (!b->ev_join[g] && cudaEventCreateWithFlags(&b->ev_join[g], cudaEventDisableTiming) != cudaSuccess)
+            return bfail(b, SLIC_ERR_CUDA, "cudaEventCreate failed");
+    }
+    if (groups > 1 && !b->ev_fork && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        return bfail(b, SLIC_ERR_CUDA, "cudaEventCreate failed");
+    // group g starts at the first frame whose preceding pixels reach g/groups
+    // of the batch's pixels (at least one frame per group)
+    std::vector<int> first(groups + 1, b->n);
+    first[0] = 0;
+    long long px = 0;
+    int g = 1;
+    for (int f = 0; f < b->n && g < groups; ++f) {
+        if (f > first[g - 1] && px * groups >= b->total_pixels * g && b->n - f >= groups - g) first[g++] = f;
+        px += (long long)b->frames[f].W * b->frames[f].H;
+    }
+    for (; g < groups; ++g) first[g] = b->n - (groups - g);  // (few frames: the last ones, one each)
+    b->group_first = first;
+    b->groups = groups;
+    if (b->buffers_set) {  // the group tables live in the device tables block
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = upload_tables(b, b->tbl_cur, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
+    }
+    return SLIC_OK;
+}
+
 slic_status slic_batch_set_fused(slic_batch b, int enable) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (enable != 0 && enable != 1) return bfail(b, SLIC_ERR_INVALID, "enable must be 0 or 1");
@@ -716,71 +856,81 @@ slic_status slic_batch_set_fused(slic_batch b, int enable) {
 }
 
 slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stream, int *ctas_per_sm, int *stages,
-                               int *rows, int *tile_h, int *fused) {
+                               int *rows, int *tile_h, int *fused, int *groups) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
     const std::string key = tune_key(b);
-    int best = 0, best_st = b->stages, best_rw = b->rows, best_th = b->tile_h, best_fu = b->fused ? 1 : 0;
-    auto report = [&]() {
+    int best = 0, best_st = b->stages, best_rw = b->rows, best_th = b->tile_h, best_fu = b->fused ? 1 : 0,
+        best_gr = b->groups;
+    auto report = [&]() -> slic_status {
         b->ctas_per_sm = best;
         b->stages = best_st;
         b->rows = best_rw;
         b->tile_h = best_th;
         b->fused = best_fu == 1;
+        const slic_status r = slic_batch_set_groups(b, best_gr);
+        if (r != SLIC_OK) return r;
+        if (groups) *groups = best_gr;
         if (ctas_per_sm) *ctas_per_sm = best;
         if (stages) *stages = best_st;
         if (rows) *rows = best_rw;
         if (tile_h) *tile_h = best_th;
         if (fused) *fused = best_fu;
-    };
-    if (cache_path && cache_lookup(cache_path, key, &best, &best_st, &best_rw, &best_th, &best_fu) &&
-        (!b->pipe ? best_rw == 1 && best_th == 32 && best_fu == 0 : shape_fits(b, best_st, best_rw, best_th))) {
-        report();
         return SLIC_OK;
-    }
+    };
+    if (cache_path && cache_lookup(cache_path, key, &best, &best_st, &best_rw, &best_th, &best_fu, &best_gr) &&
+        best_gr <= b->n && (!b->pipe ? best_rw == 1 && best_th == 32 && best_fu == 0 : shape_fits(b, best_st, best_rw, best_th)))
+        return report();
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bfail(b, SLIC_ERR_CUDA, "cudaEventCreate failed");
     float best_ms = 1e30f;
     slic_status st = SLIC_OK;
-    // Search space: tile shape (32x32, or 32x64 with two row groups) x row
-    // groups per warp (pixels per thread and block size) x pipeline stages x
-    // resident CTAs per SM (up to what fits) x fused passes or not.
-    const int fu_hi = b->pipe && b->iterations > 0 ? 1 : 0;
+    // Search space: frame groups on concurrent streams (1, 2, 4; the plain
+    // pipelined path only) x tile shape (32x32, or 32x64 with two row
+    // groups) x row groups per warp (pixels per thread and block size) x
+    // pipeline stages x resident CTAs per SM (up to what fits) x fused passes
+    // or not (one group only).
+    const bool can_split = b->pipe && !b->net && b->connectivity != 2;
     const int st_lo = b->pipe ? 3 : b->stages, st_hi = b->pipe ? 4 : b->stages;
     const int rw_hi = (b->pipe && b->same8) ? 2 : 1;
-    for (int th = 32; th <= 64 && st == SLIC_OK; th += 32) {
-        for (int rw = 1; rw <= rw_hi && st == SLIC_OK; ++rw) {
-            for (int nst = st_lo; nst <= st_hi && st == SLIC_OK; ++nst) {
-                if (b->pipe ? !shape_fits(b, nst, rw, th) : th != 32) continue;
-                const int occ = std::max(b->occupancy, b->pipe ? pipe_occ(b, nst, rw, th) : 0);
-                for (int k = 0; k < occ * (fu_hi + 1) && st == SLIC_OK; ++k) {
-                    const int c = 1 + k / (fu_hi + 1), fu = k % (fu_hi + 1);
-                    b->ctas_per_sm = c;
-                    b->stages = nst;
-                    b->rows = rw;
-                    b->tile_h = th;
-                    b->fused = fu == 1;
-                    if ((st = slic_batch_segment(b, stream)) != SLIC_OK) break;  // warm-up
-                    float total = 0.0f;
-                    for (int rep = 0; rep < 3 && st == SLIC_OK; ++rep) {
-                        cudaEventRecord(e0, s);
-                        st = slic_batch_segment(b, stream);
-                        cudaEventRecord(e1, s);
-                        float ms = 0.0f;
-                        if (cudaEventSynchronize(e1) != cudaSuccess ||
-                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-                            st = bfail(b, SLIC_ERR_CUDA, "autotune timing failed");
-                        total += ms;
-                    }
-                    if (st == SLIC_OK && total / 3 < best_ms) {
-                        best_ms = total / 3;
-                        best = c;
-                        best_st = nst;
-                        best_rw = rw;
-                        best_th = th;
-                        best_fu = fu;
+    for (int gr = 1; gr <= (can_split ? std::min(4, b->n) : 1) && st == SLIC_OK; gr *= 2) {
+        if ((st = slic_batch_set_groups(b, gr)) != SLIC_OK) break;
+        const int fu_hi = b->pipe && b->iterations > 0 && gr == 1 ? 1 : 0;
+        for (int th = 32; th <= 64 && st == SLIC_OK; th += 32) {
+            for (int rw = 1; rw <= rw_hi && st == SLIC_OK; ++rw) {
+                for (int nst = st_lo; nst <= st_hi && st == SLIC_OK; ++nst) {
+                    if (b->pipe ? !shape_fits(b, nst, rw, th) : th != 32) continue;
+                    const int occ = std::max(b->occupancy, b->pipe ? pipe_occ(b, nst, rw, th) : 0);
+                    for (int k = 0; k < occ * (fu_hi + 1) && st == SLIC_OK; ++k) {
+                        const int c = 1 + k / (fu_hi + 1), fu = k % (fu_hi + 1);
+                        b->ctas_per_sm = c;
+                        b->stages = nst;
+                        b->rows = rw;
+                        b->tile_h = th;
+                        b->fused = fu == 1;
+                        if ((st = slic_batch_segment(b, stream)) != SLIC_OK) break;  // warm-up
+                        float total = 0.0f;
+                        for (int rep = 0; rep < 3 && st == SLIC_OK; ++rep) {
+                            cudaEventRecord(e0, s);
+                            st = slic_batch_segment(b, stream);
+                            cudaEventRecord(e1, s);
+                            float ms = 0.0f;
+                            if (cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                                st = bfail(b, SLIC_ERR_CUDA, "autotune timing failed");
+                            total += ms;
+                        }
+                        if (st == SLIC_OK && total / 3 < best_ms) {
+                            best_ms = total / 3;
+                            best = c;
+                            best_st = nst;
+                            best_rw = rw;
+                            best_th = th;
+                            best_fu = fu;
+                            best_gr = gr;
+                        }
                     }
                 }
             }
@@ -789,13 +939,13 @@ slic_status slic_batch_autotune(slic_batch b, const char *cache_path, void *stre
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != SLIC_OK) return st;
-    report();
-    if (cache_path) cache_store(cache_path, key, best, best_st, best_rw, best_th, best_fu, best_ms);
+    if ((st = report()) != SLIC_OK) return st;
+    if (cache_path) cache_store(cache_path, key, best, best_st, best_rw, best_th, best_fu, best_gr, best_ms);
     return SLIC_OK;
 }
 
 slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *launches, int *ctas_per_sm,
-                            int *stages, int *rows, int *tile_h, int *fused) {
+                            int *stages, int *rows, int *tile_h, int *fused, int *groups) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (total_pixels) *total_pixels = b->total_pixels;
     if (launches) *launches = b->launches;
@@ -805,6 +955,7 @@ slic_status slic_batch_info(slic_batch b, long long *total_pixels, long long *la
     if (rows) *rows = b->pipe ? b->rows : 0;
     if (tile_h) *tile_h = b->pipe ? b->tile_h : 32;
     if (fused) *fused = b->pipe && b->fused ? 1 : 0;
+    if (groups) *groups = b->groups;
     return SLIC_OK;
 }
 

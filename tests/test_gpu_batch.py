@@ -105,16 +105,16 @@ def test_autotune_writes_and_reuses_cache(slic_gpu, tmp_path):
     bs = pkg.BatchSegmenter(frames, iterations=2)
     bs.bind([_cuda(synth.voronoi_frame(f["width"], f["height"], 20, 6.0, 5)) for f in frames])
     cache = str(tmp_path / "tune.jsonl")
-    c1, st1, rw1, th1, fu1 = bs.autotune(cache)
-    assert c1 >= 1 and 3 <= st1 <= 4 and rw1 in (1, 2) and th1 in (32, 64) and fu1 in (0, 1)
+    c1, st1, rw1, th1, fu1, gr1 = bs.autotune(cache)
+    assert c1 >= 1 and 3 <= st1 <= 4 and rw1 in (1, 2) and th1 in (32, 64) and fu1 in (0, 1) and gr1 in (1, 2)
     line = json.loads(open(cache).read().splitlines()[0])
     assert line["ctas_per_sm"] == c1 and line["stages"] == st1 and line["rows"] == rw1 and line["tile_h"] == th1
-    assert line["fused"] == fu1
+    assert line["fused"] == fu1 and line["groups"] == gr1
     assert "640x480s16" in line["key"]
-    bs.set_tuning(0, 3 if st1 != 3 else 4, 1, 32, fused=1 - fu1)
-    assert bs.autotune(cache) == (c1, st1, rw1, th1, fu1)   # served from the cache
+    bs.set_tuning(0, 3 if st1 != 3 else 4, 1, 32, fused=1 - fu1, groups=3 - gr1)
+    assert bs.autotune(cache) == (c1, st1, rw1, th1, fu1, gr1)   # served from the cache
     assert len(open(cache).read().splitlines()) == 1
-    assert bs.info[2:] == (c1, st1, rw1, th1, fu1)
+    assert bs.info[2:] == (c1, st1, rw1, th1, fu1, gr1)
 
 
 @pytest.mark.parametrize("stages", [3, 4])
@@ -367,3 +367,60 @@ def test_fused_passes_full_bench_batch(slic_gpu):
         l1, c1 = seg.segment(imgs[i])
         assert torch.equal(labels[i], l1)
         assert torch.equal(centres[i], c1)
+
+
+def test_frame_groups_are_bit_exact(slic_gpu):
+    """Frames run as 1 to 4 groups on concurrent streams give the same
+    labels and centres, also with the stopping test, after a rebind, through
+    host buffers and under graph capture."""
+    import torch
+    pkg = slic_gpu
+    frames = [dict(width=1920, height=1080, S=16), dict(width=333, height=211, S=8),
+              dict(width=640, height=480, S=32, m=20.0), dict(width=64, height=48, S=16),
+              dict(width=1280, height=720, S=8, convergence=0.4), dict(width=320, height=240, S=16)]
+    host = [synth.hd_image(31), synth.voronoi_frame(333, 211, 15, 6.0, 32), synth.voronoi_frame(640, 480, 30, 6.0, 33),
+            synth.voronoi_frame(64, 48, 5, 6.0, 34), synth.voronoi_frame(1280, 720, 200, 6.0, 35), synth.small_image(36)]
+    imgs = [_cuda(h) for h in host]
+    bs = pkg.BatchSegmenter(frames, iterations=4)
+    bs.bind(imgs)
+    bs.set_tuning(0, 3, 2, 64)
+    want_l, want_c = [[t.clone() for t in x] for x in bs.segment()]
+    want_n = bs.iterations_run
+    for groups in (2, 3, 4):
+        bs.set_groups(groups)
+        assert bs.info[7] == groups
+        labels, centres = bs.segment()
+        bs.status()
+        assert bs.iterations_run == want_n
+        for i in range(len(frames)):
+            assert torch.equal(labels[i], want_l[i]) and torch.equal(centres[i], want_c[i]), (groups, i)
+    # a rebind (the group tables follow the new buffers), under capture
+    other = [torch.empty_like(t) for t in imgs]
+    for a, b in zip(other, imgs):
+        a.copy_(b)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        bs.bind(other, stream=stream)
+        bs.segment(stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        bs.segment(stream)
+    for lab in bs.labels:
+        lab.fill_(-1)
+    with torch.cuda.stream(stream):
+        g.replay()
+    torch.cuda.synchronize()
+    bs.status()
+    for i in range(len(frames)):
+        assert torch.equal(bs.labels[i], want_l[i]), i
+    # host buffers in and out
+    h_img = [torch.from_numpy(np.ascontiguousarray(h)).pin_memory() for h in host]
+    h_lab = [torch.empty(t.shape, dtype=torch.int32).pin_memory() for t in want_l]
+    bs.segment_host(h_img, h_lab, None, stream=stream)
+    stream.synchronize()
+    for a, b in zip(h_lab, want_l):
+        assert torch.equal(a, b.cpu())
+    with pytest.raises(pkg.SlicError):
+        bs.set_groups(5)
+    bs.close()
