@@ -341,10 +341,15 @@ def run_ours(args):
     # batch runs as one group of frames (concurrent groups would share the
     # GPU during a launch, so its duration would not be its own).
     pb = bs if method["name"] == "plain" else _plain_batch(pkg, frames, n_plain, dev, tuning)
+    # The kernel on its own: one group of frames at full occupancy in the
+    # tuned tile shape, stages and rows (the step itself runs its groups
+    # concurrently, each launch sharing the GPU with the others').
+    pb.set_tuning(0, stages, rows, tile_h, fused=fused, groups=1)
+    occ_alone = pb.info[2]
     pkg.slic_batch_profile_enable(pb.handle, True)
     graph_prof = _capture(lambda: pb.segment(stream=stream), stream)
     pkg.slic_batch_profile_enable(pb.handle, False)
-    minb = 2 if tile_h == 64 else (4 if (rows == 2 or ctas_per_sm >= 4) else 3)
+    minb = 2 if tile_h == 64 else (4 if (rows == 2 or occ_alone >= 4) else 3)
     fused_dom = bool(fused) and n_plain >= 1
     kname = (f"k_assign_multi<1,{minb},{rows},{tile_h}>" if fused_dom else
              f"k_assign_pipe<0,1,{minb},{rows},{tile_h}>")
@@ -373,6 +378,10 @@ def run_ours(args):
     sm_max = clock_info.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     xu_peak = 16 * sms * sm_max * 1e6 / 1e12
     achieved_tops = sqrt_per_launch / (mid_ms / 1e3) / 1e12
+    # In the step as timed: the square roots of all its assignment passes
+    # over the whole step time (conversion, updates and connectivity
+    # included, so a lower bound on the rate the passes ran at).
+    in_step_tops = B * N * 18 * (n_plain + 1) / (ms / 1e3) / 1e12 if method["name"] == "plain" else None
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "assign_traffic.txt")
     if os.path.exists(tfile):
@@ -482,6 +491,11 @@ def run_ours(args):
                          "unit": "Tsqrt/s", "achieved": achieved_tops, "peak": xu_peak, "frac": achieved_tops / xu_peak,
                          "peak_source": f"16 MUFU lanes/clk/SM x {sms} SMs x max SM clock (recipe unit counts)",
                          "traffic": traffic, "avg_launch_us": mid_ms * 1e3, "launches_timed": len(mid),
+                         "measured_as": f"one frame group at full occupancy ({occ_alone} CTAs/SM); the step runs "
+                                        f"{groups} group(s) concurrently at {ctas_per_sm} CTAs/SM each",
+                         "in_step": {"achieved": in_step_tops,
+                                     "frac": in_step_tops / xu_peak if in_step_tops else None,
+                                     "what": "all assignment passes' square roots / step time"},
                          "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
                                  "frac": achieved_gbs / peaks["hbm_gbs"], "unit": "GB/s",
                                  "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch}},
