@@ -2,9 +2,10 @@
 // -> 32 -> 9, ReLU between layers, zero padding) that predicts, for every
 // pixel, logits over the 9 cells of its 3x3 cell window (slot t = (dy+1)*3 +
 // (dx+1)). Weights and stored activations are bfloat16, every product sum is
-// accumulated in FP32 on the tensor cores: the forward convolutions on
-// tcgen05.mma with tensor-memory accumulators, the backward ones on
-// mma.sync m16n8k16 bf16. Training
+// accumulated in FP32 on the tensor cores: the forward convolutions and the
+// input gradients (the same kernel with mirrored taps) on tcgen05.mma with
+// tensor-memory accumulators, the weight gradients on mma.sync m16n8k16
+// bf16. Training
 // (softmax cross-entropy against the slots of reference labels, Adam with
 // FP32 master weights) and inference run entirely in the kernels below;
 // the C ABI is at the end of this file and declared in include/slic.h.
@@ -296,10 +297,16 @@ __device__ __forceinline__ void tc_arrive(unsigned long long *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem(bar)) : "memory");
 }
 
-template <int CIN, int COUT, bool RELU, bool OUTF32, bool LABELS, int NS>
+// BWD: the same convolution as the input gradient of a layer (Cout -> Cin):
+// the input is the layer's dZ, the weights are its [tap][ci][co] copy taken
+// with the tap mirrored (dA[y][x][ci] = sum over dy, dx, co of
+// dZ[y+dy-1][x+dx-1][co] w[2-dy][2-dx][co][ci]), no bias, and the epilogue
+// multiplies by the ReLU derivative of the previous layer's stored output
+// (mask > 0) before the bf16 store: the result is the previous layer's dZ.
+template <int CIN, int COUT, bool RELU, bool OUTF32, bool LABELS, int NS, bool BWD = false>
 __global__ void __launch_bounds__((tc_epi_warps(COUT) + 2) * 32) k_conv_fwd_tc(
     const __grid_constant__ CUtensorMap in_map, const __nv_bfloat16 *wf, const float *bias, void *out, int W, int H,
-    int n_img, int S, int *err) {
+    int n_img, int S, int *err, const __nv_bfloat16 *mask) {
     constexpr int NP = CIN / 8;                   // 8-channel planes
     constexpr int KC = CIN / 16;                  // K chunks per kernel row
     constexpr int ROWB = CIN * 2;                 // bytes of one staged position
@@ -315,6 +322,7 @@ __global__ void __launch_bounds__((tc_epi_warps(COUT) + 2) * 32) k_conv_fwd_tc(
     constexpr int PRODUCER = EW, ISSUER = EW + 1; // warp roles
     static_assert(BOX % 1024 == 0, "stages must keep the swizzle pattern aligned");
     static_assert(!STAGED || COUT == 32, "staged stores assume 64-byte output pixels");
+    static_assert(!BWD || (STAGED && !RELU), "the input gradient leaves as masked bf16");
     extern __shared__ __align__(16) unsigned char tc_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_dyn) + 1023) & ~(uintptr_t)1023);
     unsigned char *in_s = sm;                     // [NS][dy][128 positions][ROWB]
@@ -330,11 +338,13 @@ __global__ void __launch_bounds__((tc_epi_warps(COUT) + 2) * 32) k_conv_fwd_tc(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // Weights once per CTA: plane (dy, ci / 8), row dx * COUT + co holds
-    // w[dy][dx][co][ci .. ci+7] (global [tap][co][ci], tap = dy * 3 + dx).
+    // w[dy][dx][co][ci .. ci+7] (global [tap][co][ci], tap = dy * 3 + dx;
+    // BWD: global row (8 - tap) * COUT + co).
     for (int i = tid; i < 3 * NN * NP; i += NT) {
         const int pl = i % NP, r = i / NP;  // r = dy * NN + dx * COUT + co
         const int dy = r / NN, n = r - dy * NN;
-        const uint4 v = *reinterpret_cast<const uint4 *>(wf + (size_t)r * CIN + pl * 8);
+        const int src = BWD ? (8 - (dy * 3 + n / COUT)) * COUT + n % COUT : r;
+        const uint4 v = *reinterpret_cast<const uint4 *>(wf + (size_t)src * CIN + pl * 8);
         *reinterpret_cast<uint4 *>(w_s + (dy * NP + pl) * W_PLANE + n * 16) = v;
     }
     if (tid == 0) {
@@ -457,7 +467,7 @@ __global__ void __launch_bounds__((tc_epi_warps(COUT) + 2) * 32) k_conv_fwd_tc(
         const int quarter = warp & 3, c0 = (warp >> 2) * 16;
         float bv[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) bv[c] = c0 + c < COUT ? bias[c0 + c] : 0.0f;
+        for (int c = 0; c < 16; ++c) bv[c] = !BWD && c0 + c < COUT ? bias[c0 + c] : 0.0f;
         unsigned j = 0;
         for (unsigned t = blockIdx.x; t < total; t += G, ++j) {
             const int bf = (int)(j & 1u);
@@ -486,6 +496,20 @@ __global__ void __launch_bounds__((tc_epi_warps(COUT) + 2) * 32) k_conv_fwd_tc(
             const int y = (int)(ry % (unsigned)H), img = (int)(ry / (unsigned)H);
             const int xw = (int)tx * kTcOut + kTcSeg * quarter;  // output pixel of lane 0
             const size_t row0 = (size_t)img * H * W + (size_t)y * W;
+            if constexpr (BWD) {
+                // ReLU derivative of the previous layer: its stored output > 0
+                const int x = xw + lane;
+                if (lane < kTcSeg && x < W) {
+                    const uint4 *mp = reinterpret_cast<const uint4 *>(mask + (row0 + x) * COUT + c0);
+                    const uint4 m0 = mp[0], m1 = mp[1];
+                    const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const uint32_t h = (mw[c >> 1] >> (16 * (c & 1))) & 0xFFFFu;  // bf16 bits
+                        if (!(__uint_as_float(h << 16) > 0.0f)) v[c] = 0.0f;
+                    }
+                }
+            }
             if constexpr (STAGED) {
                 // Each lane packs its pixel's 32 bytes (16 channels) into the
                 // warp's staging rows (16-byte chunks swizzled by pixel
@@ -551,81 +575,6 @@ __global__ void __launch_bounds__((tc_epi_warps(COUT) + 2) * 32) k_conv_fwd_tc(
     if (warp == ISSUER) {
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(2 * BUFC));
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Input gradient: dA[p][ci] = sum_{tap,co} dZ[p - tap + (1,1)][co] w[tap][ci][co],
-// then times the ReLU derivative of the previous layer (its stored output
-// a_prev > 0): the result is the previous layer's dZ.
-// ---------------------------------------------------------------------------
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) k_conv_bwd_data(const __nv_bfloat16 *dz, const __nv_bfloat16 *wb,
-                                                       const __nv_bfloat16 *a_prev, __nv_bfloat16 *dz_prev, int W,
-                                                       int H) {
-    constexpr int CS = COUT + 8;
-    constexpr int WS = COUT + 8;
-    __shared__ __align__(16) __nv_bfloat16 g_s[(kTY + 2) * (kTX + 2) * CS];
-    __shared__ __align__(16) __nv_bfloat16 w_s[9 * CIN * WS];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int gid = lane >> 2, tig = lane & 3;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, img = blockIdx.z;
-    const size_t base = (size_t)img * H * W;
-
-    for (int i = tid; i < (kTY + 2) * (kTX + 2) * (COUT / 2); i += 128) {
-        const int c2 = i % (COUT / 2), pix = i / (COUT / 2);
-        const int lx = pix % (kTX + 2), ly = pix / (kTX + 2);
-        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        uint32_t v = 0u;
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H)
-            v = *reinterpret_cast<const uint32_t *>(dz + (base + (size_t)gy * W + gx) * COUT + 2 * c2);
-        *reinterpret_cast<uint32_t *>(&g_s[pix * CS + 2 * c2]) = v;
-    }
-    for (int i = tid; i < 9 * CIN * (COUT / 2); i += 128) {
-        const int c2 = i % (COUT / 2), row = i / (COUT / 2);
-        *reinterpret_cast<uint32_t *>(&w_s[row * WS + 2 * c2]) =
-            *reinterpret_cast<const uint32_t *>(wb + (size_t)row * COUT + 2 * c2);
-    }
-    __syncthreads();
-
-    float acc[CIN / 8][4];
-#pragma unroll
-    for (int n = 0; n < CIN / 8; ++n)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[n][q] = 0.0f;
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
-        // pixel (x0+i, y0+warp) reads dZ at (x0+i-dx+1, y0+warp-dy+1): tile row warp-dy+2, column i-dx+2
-        const __nv_bfloat16 *arow = &g_s[((warp - dy + 2) * (kTX + 2) + (2 - dx)) * CS];
-#pragma unroll
-        for (int kb = 0; kb < COUT / 16; ++kb) {
-            uint32_t a[4];
-            a[0] = lds32(arow + gid * CS + kb * 16 + 2 * tig);
-            a[1] = lds32(arow + (gid + 8) * CS + kb * 16 + 2 * tig);
-            a[2] = lds32(arow + gid * CS + kb * 16 + 2 * tig + 8);
-            a[3] = lds32(arow + (gid + 8) * CS + kb * 16 + 2 * tig + 8);
-#pragma unroll
-            for (int n = 0; n < CIN / 8; ++n) {
-                const __nv_bfloat16 *brow = &w_s[(tap * CIN + n * 8 + gid) * WS + kb * 16 + 2 * tig];
-                mma16816(acc[n], a, lds32(brow), lds32(brow + 8));
-            }
-        }
-    }
-    const int y = y0 + warp;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int x = x0 + gid + 8 * half;
-        if (x >= W || y >= H) continue;
-        const size_t px = base + (size_t)y * W + x;
-#pragma unroll
-        for (int n = 0; n < CIN / 8; ++n) {
-            const int ci = n * 8 + 2 * tig;
-            const __nv_bfloat162 ap = *reinterpret_cast<const __nv_bfloat162 *>(a_prev + px * CIN + ci);
-            const float v0 = __bfloat162float(ap.x) > 0.0f ? acc[n][2 * half] : 0.0f;
-            const float v1 = __bfloat162float(ap.y) > 0.0f ? acc[n][2 * half + 1] : 0.0f;
-            *reinterpret_cast<uint32_t *>(dz_prev + px * CIN + ci) = pack_bf16(v0, v1);
-        }
     }
 }
 
@@ -885,6 +834,9 @@ struct slic_net_ctx {
     // act[l] as a [max_batch][H][W][Cin_p] bf16 tensor, copied in 32 x Cin_p boxes
     // (32- or 64-byte swizzle) by the forward convolution of layer l
     CUtensorMap in_map[kLayers] = {};
+    // the gradient buffers as inputs of the input-gradient convolutions:
+    // dzA with 16 channels (dL/dlogits), dzB and dzA with 32
+    CUtensorMap dz_map[3] = {};
     int sms = 0;
     ConvConsts conv{};
     std::string err;
@@ -917,10 +869,10 @@ bool nalloc(slic_net_ctx *n, T **p, size_t count) {
 
 size_t wcount(int l) { return (size_t)9 * kCinPad[l] * kCoutPad[l]; }
 
-template <int CIN, int COUT, bool RELU, bool OUTF32, bool LABELS, int NS>
+template <int CIN, int COUT, bool RELU, bool OUTF32, bool LABELS, int NS, bool BWD = false>
 cudaError_t conv_fwd_tc(const CUtensorMap &in_map, const __nv_bfloat16 *wf, const float *b, void *out, int W, int H,
-                        int n, int S, int *err, int sms, cudaStream_t s) {
-    auto kern = k_conv_fwd_tc<CIN, COUT, RELU, OUTF32, LABELS, NS>;
+                        int n, int S, int *err, int sms, cudaStream_t s, const __nv_bfloat16 *mask = nullptr) {
+    auto kern = k_conv_fwd_tc<CIN, COUT, RELU, OUTF32, LABELS, NS, BWD>;
     const int smem = tc_smem_bytes(CIN, COUT, !OUTF32 && !LABELS, NS);
     const int threads = (tc_epi_warps(COUT) + 2) * 32;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -945,7 +897,7 @@ cudaError_t conv_fwd_tc(const CUtensorMap &in_map, const __nv_bfloat16 *wf, cons
     per_sm = std::max(per_sm, 1);
     const long long tiles = (long long)n * H * ((W + kTcOut - 1) / kTcOut);
     const int grid = (int)(tiles < (long long)per_sm * sms ? tiles : (long long)per_sm * sms);
-    kern<<<grid, threads, smem, s>>>(in_map, wf, b, out, W, H, n, S, err);
+    kern<<<grid, threads, smem, s>>>(in_map, wf, b, out, W, H, n, S, err, mask);
     return cudaGetLastError();
 }
 
@@ -988,7 +940,6 @@ slic_status backward_all(slic_net_ctx *n, int batch, const uint8_t *d_targets, c
         e = cudaGetLastError();
     }
     __nv_bfloat16 *dz = n->dzA, *dz_prev = n->dzB;
-    const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, batch);
     for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
         const int cin = kCinPad[l], cout = kCoutPad[l];
         // weight gradient of layer l from its input act[l] and dz
@@ -1006,15 +957,20 @@ slic_status backward_all(slic_net_ctx *n, int batch, const uint8_t *d_targets, c
             k_bias_grad<32><<<n->partial_blocks, 256, 0, s>>>(dz, n_px, n->bg[l]);
         else
             k_bias_grad<16><<<n->partial_blocks, 256, 0, s>>>(dz, n_px, n->bg[l]);
-        if (l > 0) {
-            // dz of layer l-1 (its output act[l] is layer l's input)
+        e = cudaGetLastError();
+        if (l > 0 && e == cudaSuccess) {
+            // dz of layer l-1 (its output act[l] is layer l's input), on the
+            // tensor cores: the forward convolution in its BWD form, reading
+            // dz through its tensor map (dzA: 16 channels for l = 3, else 32)
+            const CUtensorMap &m = n->dz_map[l == 3 ? 0 : (dz == n->dzB ? 1 : 2)];
             if (l < 3)
-                k_conv_bwd_data<32, 32><<<grid, 128, 0, s>>>(dz, n->wb[l], n->act[l], dz_prev, W, H);
+                e = conv_fwd_tc<32, 32, false, false, false, 3, true>(m, n->wb[l], nullptr, dz_prev, W, H, batch,
+                                                                      n->S, n->tc_err, n->sms, s, n->act[l]);
             else
-                k_conv_bwd_data<32, 16><<<grid, 128, 0, s>>>(dz, n->wb[l], n->act[l], dz_prev, W, H);
+                e = conv_fwd_tc<16, 32, false, false, false, 4, true>(m, n->wb[l], nullptr, dz_prev, W, H, batch,
+                                                                      n->S, n->tc_err, n->sms, s, n->act[l]);
             std::swap(dz, dz_prev);
         }
-        e = cudaGetLastError();
     }
     if (e != cudaSuccess) return nfail(n, SLIC_ERR_CUDA, std::string("network backward launch: ") + cudaGetErrorString(e));
     return SLIC_OK;
@@ -1102,6 +1058,16 @@ slic_status slic_net_create(int max_batch, int width, int height, int S, float m
         ok = enc && enc(&n->in_map[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, n->act[l], dims, strides, box, ones,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, c == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    for (int k = 0; k < 3 && ok; ++k) {
+        const cuuint64_t c = k == 0 ? 16 : 32;
+        const cuuint64_t dims[4] = {c, (cuuint64_t)width, (cuuint64_t)height, (cuuint64_t)max_batch};
+        const cuuint64_t strides[3] = {c * 2, c * 2 * width, c * 2 * width * height};
+        const cuuint32_t box[4] = {(cuuint32_t)c, 32, 1, 1};
+        const cuuint32_t ones[4] = {1, 1, 1, 1};
+        ok = enc(&n->dz_map[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, k == 1 ? n->dzB : n->dzA, dims, strides, box,
+                 ones, CU_TENSOR_MAP_INTERLEAVE_NONE, c == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
     if (!ok) {
         slic_net_destroy(n);
