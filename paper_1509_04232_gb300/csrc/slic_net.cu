@@ -2,10 +2,9 @@
 // -> 32 -> 9, ReLU between layers, zero padding) that predicts, for every
 // pixel, logits over the 9 cells of its 3x3 cell window (slot t = (dy+1)*3 +
 // (dx+1)). Weights and stored activations are bfloat16, every product sum is
-// accumulated in FP32 on the tensor cores: the forward convolutions and the
-// input gradients (the same kernel with mirrored taps) on tcgen05.mma with
-// tensor-memory accumulators, the weight gradients on mma.sync m16n8k16
-// bf16. Training
+// accumulated in FP32 on the 5th-generation tensor cores (tcgen05.mma with
+// tensor-memory accumulators): the forward convolutions, the input gradients
+// (the same kernel with mirrored taps) and the weight gradients. Training
 // (softmax cross-entropy against the slots of reference labels, Adam with
 // FP32 master weights) and inference run entirely in the kernels below;
 // the C ABI is at the end of this file and declared in include/slic.h.
@@ -14,8 +13,8 @@
 // of 16 (layer-1 input 16, hidden 32, logits 16 in FP32). Weights per layer:
 // master FP32 and gradients [9][Cin_p][Cout_p] (tap = dy*3 + dx), a bf16
 // copy [9][Cout_p][Cin_p] for the forward pass and one [9][Cin_p][Cout_p]
-// for the input-gradient pass, so every mma operand pair is two adjacent
-// bf16 values in shared memory.
+// for the input-gradient pass: each the K-major operand (K = the input
+// channels of its convolution) that the tensor-core kernel stages.
 #include "slic.h"
 #include "slic_internal.cuh"
 
@@ -47,15 +46,6 @@ constexpr int kCinReal[kLayers] = {14, 32, 32, 32};
 constexpr int kCoutReal[kLayers] = {32, 32, 32, 9};
 constexpr int kCinPad[kLayers] = {16, 32, 32, 32};
 constexpr int kCoutPad[kLayers] = {32, 32, 32, 16};
-constexpr int kTX = 16, kTY = 4;  // conv tile: 16 pixels x 4 rows, one warp per row
-
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -70,14 +60,6 @@ __device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
     return r;
 }
 
-__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
-
-// Two bf16 that may not be 4-byte aligned.
-__device__ __forceinline__ uint32_t lds_pair(const __nv_bfloat16 *p) {
-    const uint32_t lo = *reinterpret_cast<const unsigned short *>(p);
-    const uint32_t hi = *reinterpret_cast<const unsigned short *>(p + 1);
-    return lo | (hi << 16);
-}
 
 // Square root on the hardware approximation (relative error ~2^-22, far
 // below the bf16 rounding of the channels).
@@ -579,87 +561,184 @@ __global__ void __launch_bounds__((tc_epi_warps(COUT) + 2) * 32) k_conv_fwd_tc(
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradient: dW[tap][ci][co] = sum_p a_in[p + tap - (1,1)][ci] dZ[p][co].
-// Persistent CTAs of 9 warps (warp = tap) walk 16x4-pixel tiles of the batch;
-// each warp accumulates a CIN x COUT block (k = pixels) and writes its
-// partial once; k_reduce_partials adds the CTAs' partials.
+// Weight gradient on the tensor cores: dW[dy*3+dx][ci][co] = sum over pixels
+// (y, x) of a_in[y+dy-1][x+dx-1][ci] dZ[y][x][co] (zero outside the image).
+// A work tile is kWgK pixels of one image row. Kernel row dy has its own
+// accumulator in tensor memory, D_dy[m][co] with m = dx*CIN + ci (rows from
+// 3*CIN to 127 stay zero), fed by tcgen05.mma of M128 x N COUT x K16 over
+// the tile's pixels: A_dy[m][k] = a_in[y+dy-1][x0+k+dx-1][ci] and B[co][k] =
+// dZ[y][x0+k][co], both K-major in the unswizzled canonical layout (planes of
+// 8 pixels, one 16-byte row per m or co: the forward kernel's weight
+// layout). The CTA stages the raw NHWC rows (three input rows with a
+// one-pixel halo, one dZ row) with 16-byte loads, transposes them into one
+// of two operand stages, and one thread issues the MMAs; a stage is refilled
+// once the MMAs that read it have completed (tcgen05.commit on an mbarrier).
+// Each CTA writes its partial dW once; k_reduce_partials adds them.
 // ---------------------------------------------------------------------------
+constexpr int kWgK = 32;  // pixels per tile
+constexpr int kWgPlanes = kWgK / 8;
+constexpr int kWgThreads = 256;
+__host__ __device__ constexpr int wg_a_bytes() { return 3 * kWgPlanes * 128 * 16; }
+__host__ __device__ constexpr int wg_b_bytes(int cout) { return kWgPlanes * cout * 16; }
+__host__ __device__ constexpr int wg_raw_a(int cin) { return 3 * (kWgK + 2) * cin * 2; }
+__host__ __device__ constexpr int wg_raw_z(int cout) { return kWgK * cout * 2; }
+__host__ __device__ constexpr int wg_smem_bytes(int cin, int cout) {
+    return 128 + 2 * (wg_a_bytes() + wg_b_bytes(cout)) + wg_raw_a(cin) + wg_raw_z(cout) + 64;
+}
+
+// Two bf16 (as raw 16-bit patterns) in one 32-bit word, lo in the low half.
+__device__ __forceinline__ uint32_t bf16_pair(const __nv_bfloat16 &lo, const __nv_bfloat16 &hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(288) k_conv_bwd_weight(const __nv_bfloat16 *a_in, const __nv_bfloat16 *dz, int W,
-                                                         int H, int n_img, float *partial) {
-    constexpr int PS = (kTY + 2) * (kTX + 2) + 4;  // per-channel plane of the halo tile (pixels)
-    constexpr int GS = kTY * kTX + 8;             // per-channel plane of the dZ tile
-    __shared__ __align__(16) __nv_bfloat16 a_s[CIN * PS];
-    __shared__ __align__(16) __nv_bfloat16 g_s[COUT * GS];
+__global__ void __launch_bounds__(kWgThreads) k_conv_bwd_weight_tc(const __nv_bfloat16 *a_in,
+                                                                   const __nv_bfloat16 *dz, int W, int H, int n_img,
+                                                                   float *partial, int *err) {
+    constexpr int M_REAL = 3 * CIN;
+    constexpr int A_PLANE = 128 * 16, B_PLANE = COUT * 16;
+    constexpr int A_BYTES = wg_a_bytes(), B_BYTES = wg_b_bytes(COUT), STAGE = A_BYTES + B_BYTES;
+    constexpr int TCOLS = 128;  // tensor memory: the three accumulators of COUT columns
+    static_assert(M_REAL <= 128 && 3 * COUT <= TCOLS && (COUT == 16 || COUT == 32) && CIN % 8 == 0,
+                  "shapes of the weight-gradient kernel");
+    extern __shared__ __align__(16) unsigned char wg_dyn[];
+    unsigned char *op =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(wg_dyn) + 127) & ~(uintptr_t)127);
+    __nv_bfloat16 *ra = reinterpret_cast<__nv_bfloat16 *>(op + 2 * STAGE);  // [3][kWgK+2][CIN]
+    __nv_bfloat16 *rz = ra + wg_raw_a(CIN) / 2;                               // [kWgK][COUT]
+    unsigned long long *mma_done = reinterpret_cast<unsigned long long *>(rz + wg_raw_z(COUT) / 2);  // [2]
+    unsigned long long *fin = mma_done + 2;
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(fin + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int gid = lane >> 2, tig = lane & 3;
-    const int tiles_x = (W + kTX - 1) / kTX, tiles_y = (H + kTY - 1) / kTY;
-    const int total = tiles_x * tiles_y * n_img;
-    const int dy = warp / 3, dx = warp % 3;
 
-    float acc[CIN / 16][COUT / 8][4];
-#pragma unroll
-    for (int m = 0; m < CIN / 16; ++m)
-#pragma unroll
-        for (int n = 0; n < COUT / 8; ++n)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.0f;
+    // the padding rows of A in both stages stay zero
+    for (int i = tid; i < 2 * 3 * kWgPlanes * (128 - M_REAL); i += kWgThreads) {
+        const int r = M_REAL + i % (128 - M_REAL), q = i / (128 - M_REAL);
+        const int st = q / (3 * kWgPlanes), pl = q % (3 * kWgPlanes);
+        *reinterpret_cast<uint4 *>(op + st * STAGE + pl * A_PLANE + r * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mma_done[i])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(tmem_slot)),
+                     "n"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = *tmem_slot;
 
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const int img = t / (tiles_x * tiles_y), r = t % (tiles_x * tiles_y);
-        const int x0 = (r % tiles_x) * kTX, y0 = (r / tiles_x) * kTY;
+    const int segs = (W + kWgK - 1) / kWgK;
+    const long long total = (long long)n_img * H * segs;
+    int it = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+        const int seg = (int)(t % segs);
+        const long long ry = t / segs;
+        const int y = (int)(ry % H), img = (int)(ry / H);
+        const int x0 = seg * kWgK;
         const size_t base = (size_t)img * H * W;
-        __syncthreads();
-        // channel-major tiles: a_s[ci][pix] (halo), g_s[co][pix] (zeros outside the image)
-        for (int i = tid; i < (kTY + 2) * (kTX + 2) * CIN; i += 288) {
-            const int ci = i % CIN, pix = i / CIN;
-            const int gx = x0 + pix % (kTX + 2) - 1, gy = y0 + pix / (kTX + 2) - 1;
-            __nv_bfloat16 v = __float2bfloat16(0.0f);
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = a_in[(base + (size_t)gy * W + gx) * CIN + ci];
-            a_s[ci * PS + pix] = v;
+        // raw rows: input rows y-1 .. y+1 at x0-1 .. x0+kWgK, the dZ row at x0 ..
+        for (int i = tid; i < 3 * (kWgK + 2) * (CIN / 8); i += kWgThreads) {
+            const int v8 = i % (CIN / 8), r = i / (CIN / 8), px = r % (kWgK + 2), dy = r / (kWgK + 2);
+            const int gx = x0 - 1 + px, gy = y + dy - 1;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H)
+                v = *reinterpret_cast<const uint4 *>(a_in + (base + (size_t)gy * W + gx) * CIN + v8 * 8);
+            *reinterpret_cast<uint4 *>(ra + (size_t)r * CIN + v8 * 8) = v;
         }
-        for (int i = tid; i < kTY * kTX * COUT; i += 288) {
-            const int co = i % COUT, pix = i / COUT;
-            const int gx = x0 + pix % kTX, gy = y0 + pix / kTX;
-            __nv_bfloat16 v = __float2bfloat16(0.0f);
-            if (gx < W && gy < H) v = dz[(base + (size_t)gy * W + gx) * COUT + co];
-            g_s[co * GS + pix] = v;
+        for (int i = tid; i < kWgK * (COUT / 8); i += kWgThreads) {
+            const int v8 = i % (COUT / 8), px = i / (COUT / 8), gx = x0 + px;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gx < W) v = *reinterpret_cast<const uint4 *>(dz + (base + (size_t)y * W + gx) * COUT + v8 * 8);
+            *reinterpret_cast<uint4 *>(rz + px * COUT + v8 * 8) = v;
         }
+        // the stage this tile fills was read by the MMAs of tile it-2
+        const int s = it & 1;
+        const bool w_ok = it < 2 || tc_wait(&mma_done[s], ((it - 2) >> 1) & 1);
+        if (!__syncthreads_and(w_ok ? 1 : 0)) {  // (also: the raw rows are complete)
+            ok = false;
+            break;
+        }
+        unsigned char *A = op + s * STAGE, *B = A + A_BYTES;
+        for (int i = tid; i < 3 * kWgPlanes * M_REAL; i += kWgThreads) {
+            const int m = i % M_REAL, q = i / M_REAL, j = q % kWgPlanes, dy = q / kWgPlanes;
+            const int dx = m / CIN, ci = m - dx * CIN;
+            const __nv_bfloat16 *src = ra + ((size_t)dy * (kWgK + 2) + 8 * j + dx) * CIN + ci;
+            *reinterpret_cast<uint4 *>(A + (dy * kWgPlanes + j) * A_PLANE + m * 16) =
+                make_uint4(bf16_pair(src[0], src[CIN]), bf16_pair(src[2 * CIN], src[3 * CIN]),
+                           bf16_pair(src[4 * CIN], src[5 * CIN]), bf16_pair(src[6 * CIN], src[7 * CIN]));
+        }
+        for (int i = tid; i < kWgPlanes * COUT; i += kWgThreads) {
+            const int co = i % COUT, j = i / COUT;
+            const __nv_bfloat16 *src = rz + (size_t)(8 * j) * COUT + co;
+            *reinterpret_cast<uint4 *>(B + j * B_PLANE + co * 16) =
+                make_uint4(bf16_pair(src[0], src[COUT]), bf16_pair(src[2 * COUT], src[3 * COUT]),
+                           bf16_pair(src[4 * COUT], src[5 * COUT]), bf16_pair(src[6 * COUT], src[7 * COUT]));
+        }
+        // generic-proxy writes -> visible to the tensor core
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned idesc = tc_idesc(128, COUT);
+            const unsigned a0 = tc_smem(A), b0 = tc_smem(B);
 #pragma unroll
-        for (int row = 0; row < kTY; ++row) {
-            // k = the 16 pixels of tile row `row`; input pixel of tap (dy,dx): halo row row+dy, column i+dx
-            uint32_t a[CIN / 16][4];
+            for (int dy = 0; dy < 3; ++dy) {
 #pragma unroll
-            for (int m = 0; m < CIN / 16; ++m) {
-                const __nv_bfloat16 *p0 = &a_s[(m * 16 + gid) * PS + (row + dy) * (kTX + 2) + dx];
-                const __nv_bfloat16 *p8 = p0 + 8 * PS;
-                a[m][0] = lds_pair(p0 + 2 * tig);
-                a[m][1] = lds_pair(p8 + 2 * tig);
-                a[m][2] = lds_pair(p0 + 2 * tig + 8);
-                a[m][3] = lds_pair(p8 + 2 * tig + 8);
+                for (int kc = 0; kc < kWgK / 16; ++kc) {
+                    const unsigned long long ad = tc_desc(a0 + (dy * kWgPlanes + 2 * kc) * A_PLANE, A_PLANE, 128);
+                    const unsigned long long bd = tc_desc(b0 + 2 * kc * B_PLANE, B_PLANE, 128);
+                    const unsigned acc = (it > 0 || kc > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem +
+                                                                                              (unsigned)(dy * COUT)),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
             }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tc_smem(&mma_done[s]))
+                         : "memory");
+        }
+    }
+    // every MMA complete, then each accumulator row out: warp w (< 4) reads
+    // lanes 32w .. 32w+31 (rows m), columns dy*COUT .. +COUT-1
+    if (tid == 0)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc_smem(fin))
+                     : "memory");
+    const bool f_ok = tc_wait(fin, 0);
+    if (!__syncthreads_and(f_ok ? 1 : 0)) ok = false;
+    if (!ok && tid == 0) atomicOr(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp < 4) {
+        const int m = warp * 32 + lane;
+        const int dx = m / CIN, ci = m - dx * CIN;
 #pragma unroll
-            for (int n = 0; n < COUT / 8; ++n) {
-                const __nv_bfloat16 *q = &g_s[(n * 8 + gid) * GS + row * kTX + 2 * tig];
-                const uint32_t b0 = lds32(q), b1 = lds32(q + 8);
+        for (int dy = 0; dy < 3; ++dy) {
+            float v[COUT];
+            tc_ld_cols<COUT>(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(dy * COUT), v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (m < M_REAL) {
+                float4 *dst = reinterpret_cast<float4 *>(partial +
+                                                         (((size_t)blockIdx.x * 9 + dy * 3 + dx) * CIN + ci) * COUT);
 #pragma unroll
-                for (int m = 0; m < CIN / 16; ++m) mma16816(acc[m][n], a[m], b0, b1);
+                for (int q = 0; q < COUT / 4; ++q)
+                    dst[q] = it > 0 ? make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3])
+                                    : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
         }
     }
-    // partial[block][tap][ci][co]
-    float *dst = partial + ((size_t)blockIdx.x * 9 + warp) * CIN * COUT;
-#pragma unroll
-    for (int m = 0; m < CIN / 16; ++m)
-#pragma unroll
-        for (int n = 0; n < COUT / 8; ++n) {
-            const int ci = m * 16 + gid, co = n * 8 + 2 * tig;
-            dst[ci * COUT + co] = acc[m][n][0];
-            dst[ci * COUT + co + 1] = acc[m][n][1];
-            dst[(ci + 8) * COUT + co] = acc[m][n][2];
-            dst[(ci + 8) * COUT + co + 1] = acc[m][n][3];
-        }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TCOLS));
+    }
 }
 
 __global__ void k_reduce_partials(const float *partial, int n_blocks, int n, float *out) {
@@ -901,6 +980,17 @@ cudaError_t conv_fwd_tc(const CUtensorMap &in_map, const __nv_bfloat16 *wf, cons
     return cudaGetLastError();
 }
 
+template <int CIN, int COUT>
+cudaError_t conv_bwd_weight_tc(const __nv_bfloat16 *a_in, const __nv_bfloat16 *dz, int W, int H, int n,
+                               float *partial, int blocks, int *err, cudaStream_t s) {
+    auto kern = k_conv_bwd_weight_tc<CIN, COUT>;
+    const int smem = wg_smem_bytes(CIN, COUT);
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, kWgThreads, smem, s>>>(a_in, dz, W, H, n, partial, err);
+    return cudaGetLastError();
+}
+
 // Layer l of the forward pass on the tensor cores, reading its input through
 // the layer's tensor map. With `labels`, the last layer writes each pixel's
 // label (argmax of its valid slots) instead of its logits.
@@ -942,13 +1032,15 @@ slic_status backward_all(slic_net_ctx *n, int batch, const uint8_t *d_targets, c
     __nv_bfloat16 *dz = n->dzA, *dz_prev = n->dzB;
     for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
         const int cin = kCinPad[l], cout = kCoutPad[l];
-        // weight gradient of layer l from its input act[l] and dz
+        // weight gradient of layer l from its input act[l] and dz (per-CTA
+        // partials on the tensor cores, then their sum)
         if (l == 0)
-            k_conv_bwd_weight<16, 32><<<n->partial_blocks, 288, 0, s>>>(n->act[0], dz, W, H, batch, n->partial);
+            e = conv_bwd_weight_tc<16, 32>(n->act[0], dz, W, H, batch, n->partial, n->partial_blocks, n->tc_err, s);
         else if (l < 3)
-            k_conv_bwd_weight<32, 32><<<n->partial_blocks, 288, 0, s>>>(n->act[l], dz, W, H, batch, n->partial);
+            e = conv_bwd_weight_tc<32, 32>(n->act[l], dz, W, H, batch, n->partial, n->partial_blocks, n->tc_err, s);
         else
-            k_conv_bwd_weight<32, 16><<<n->partial_blocks, 288, 0, s>>>(n->act[l], dz, W, H, batch, n->partial);
+            e = conv_bwd_weight_tc<32, 16>(n->act[l], dz, W, H, batch, n->partial, n->partial_blocks, n->tc_err, s);
+        if (e != cudaSuccess) break;
         const int cnt = 9 * cin * cout;
         k_reduce_partials<<<(cnt + 255) / 256, 256, 0, s>>>(n->partial, n->partial_blocks, cnt, n->wg[l]);
         e = cudaMemsetAsync(n->bg[l], 0, sizeof(float) * cout, s);
