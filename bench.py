@@ -251,6 +251,18 @@ def run_ours(args):
     build.build_all()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
+    if args.train_only:  # the warm-start network's training alone (a profiling command)
+        from paper_1509_04232_gb300 import warmstart as ws
+        net = ws.WarmStartNet(256, 256, S, max_batch=64, seed=0, m=M)
+        t0 = time.time()
+        hist = ws.train(net, n_images=args.train_images, batch=64, epochs=1, lr=2e-3, log_every=50)
+        torch.cuda.synchronize()
+        net.status()
+        if rank == 0:
+            print(json.dumps({"training": {"images": args.train_images, "seconds": time.time() - t0,
+                                           "final_loss": hist[-1][1] if hist else None}}))
+        net.close()
+        return 0
     if args.mixed_only:  # the mixed batch alone (a profiling command)
         stream = torch.cuda.Stream(device=dev)
         if rank == 0:
@@ -813,6 +825,8 @@ def main(argv=None):
                          "finds (skips the sweep and the learned leg; for profiling)")
     ap.add_argument("--tuning", default=None, metavar="CTAS,STAGES,ROWS,TILE_H[,FUSED[,GROUPS]]",
                     help="launch shape of the assignment passes instead of autotuning (for profiling)")
+    ap.add_argument("--train-only", action="store_true",
+                    help="train the warm-start network on --train-images images and print its line (for profiling)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="run only the 256-frame mixed batch and print its line (for profiling)")
     args = ap.parse_args(argv)
