@@ -563,27 +563,33 @@ __global__ void __launch_bounds__((tc_epi_warps(COUT) + 2) * 32) k_conv_fwd_tc(
 // ---------------------------------------------------------------------------
 // Weight gradient on the tensor cores: dW[dy*3+dx][ci][co] = sum over pixels
 // (y, x) of a_in[y+dy-1][x+dx-1][ci] dZ[y][x][co] (zero outside the image).
-// A work tile is kWgK pixels of one image row. Kernel row dy has its own
-// accumulator in tensor memory, D_dy[m][co] with m = dx*CIN + ci (rows from
-// 3*CIN to 127 stay zero), fed by tcgen05.mma of M128 x N COUT x K16 over
-// the tile's pixels: A_dy[m][k] = a_in[y+dy-1][x0+k+dx-1][ci] and B[co][k] =
-// dZ[y][x0+k][co], both K-major in the unswizzled canonical layout (planes of
-// 8 pixels, one 16-byte row per m or co: the forward kernel's weight
-// layout). The CTA stages the raw NHWC rows (three input rows with a
-// one-pixel halo, one dZ row) with 16-byte loads, transposes them into one
-// of two operand stages, and one thread issues the MMAs; a stage is refilled
-// once the MMAs that read it have completed (tcgen05.commit on an mbarrier).
-// Each CTA writes its partial dW once; k_reduce_partials adds them.
+// Kernel row dy has its own accumulator in tensor memory, D_dy[m][co] with
+// m = dx*CIN + ci (rows from 3*CIN to 127 stay zero), fed by tcgen05.mma of
+// M128 x N COUT x K16 over pixels: for output row y and the kWgK columns
+// x0 .. of a work strip, A_dy[m][k] = a_in[y+dy-1][x0+k+dx-1][ci] and
+// B[co][k] = dZ[y][x0+k][co], both K-major in the unswizzled canonical
+// layout (planes of 8 pixels, one 16-byte row per m or co: the forward
+// kernel's weight layout).
+//
+// A CTA walks strips of kWgK columns by kWgBand rows. Each input row is
+// staged once (16-byte loads of its NHWC row with a one-pixel halo) and
+// transposed into one of four row slots; output row y then reads the slots
+// of rows y-1, y, y+1 as A_0, A_1, A_2 and its dZ row from one of two B
+// slots, so a row costs one input-row and one dZ-row transposition. One
+// thread issues the 3 x kWgK/16 MMAs of a row; a slot is refilled once the
+// MMAs that read it have completed (tcgen05.commit on an mbarrier). Each CTA
+// writes its partial dW once; k_reduce_partials adds them.
 // ---------------------------------------------------------------------------
-constexpr int kWgK = 32;  // pixels per tile
+constexpr int kWgK = 64;     // pixels (columns) of a strip
+constexpr int kWgBand = 32;  // rows of a strip
 constexpr int kWgPlanes = kWgK / 8;
 constexpr int kWgThreads = 256;
-__host__ __device__ constexpr int wg_a_bytes() { return 3 * kWgPlanes * 128 * 16; }
+__host__ __device__ constexpr int wg_slot_bytes() { return kWgPlanes * 128 * 16; }
 __host__ __device__ constexpr int wg_b_bytes(int cout) { return kWgPlanes * cout * 16; }
-__host__ __device__ constexpr int wg_raw_a(int cin) { return 3 * (kWgK + 2) * cin * 2; }
+__host__ __device__ constexpr int wg_raw_a(int cin) { return (kWgK + 2) * cin * 2; }
 __host__ __device__ constexpr int wg_raw_z(int cout) { return kWgK * cout * 2; }
 __host__ __device__ constexpr int wg_smem_bytes(int cin, int cout) {
-    return 128 + 2 * (wg_a_bytes() + wg_b_bytes(cout)) + wg_raw_a(cin) + wg_raw_z(cout) + 64;
+    return 128 + 4 * wg_slot_bytes() + 2 * wg_b_bytes(cout) + wg_raw_a(cin) + wg_raw_z(cout) + 64;
 }
 
 // Two bf16 (as raw 16-bit patterns) in one 32-bit word, lo in the low half.
@@ -597,25 +603,25 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_bwd_weight_tc(const __nv_bf
                                                                    float *partial, int *err) {
     constexpr int M_REAL = 3 * CIN;
     constexpr int A_PLANE = 128 * 16, B_PLANE = COUT * 16;
-    constexpr int A_BYTES = wg_a_bytes(), B_BYTES = wg_b_bytes(COUT), STAGE = A_BYTES + B_BYTES;
+    constexpr int SLOT = wg_slot_bytes(), BSLOT = wg_b_bytes(COUT);
     constexpr int TCOLS = 128;  // tensor memory: the three accumulators of COUT columns
     static_assert(M_REAL <= 128 && 3 * COUT <= TCOLS && (COUT == 16 || COUT == 32) && CIN % 8 == 0,
                   "shapes of the weight-gradient kernel");
     extern __shared__ __align__(16) unsigned char wg_dyn[];
-    unsigned char *op =
+    unsigned char *slots =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(wg_dyn) + 127) & ~(uintptr_t)127);
-    __nv_bfloat16 *ra = reinterpret_cast<__nv_bfloat16 *>(op + 2 * STAGE);  // [3][kWgK+2][CIN]
-    __nv_bfloat16 *rz = ra + wg_raw_a(CIN) / 2;                               // [kWgK][COUT]
+    unsigned char *bslots = slots + 4 * SLOT;
+    __nv_bfloat16 *ra = reinterpret_cast<__nv_bfloat16 *>(bslots + 2 * BSLOT);  // [kWgK+2][CIN]
+    __nv_bfloat16 *rz = ra + wg_raw_a(CIN) / 2;                                 // [kWgK][COUT]
     unsigned long long *mma_done = reinterpret_cast<unsigned long long *>(rz + wg_raw_z(COUT) / 2);  // [2]
     unsigned long long *fin = mma_done + 2;
     unsigned *tmem_slot = reinterpret_cast<unsigned *>(fin + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // the padding rows of A in both stages stay zero
-    for (int i = tid; i < 2 * 3 * kWgPlanes * (128 - M_REAL); i += kWgThreads) {
-        const int r = M_REAL + i % (128 - M_REAL), q = i / (128 - M_REAL);
-        const int st = q / (3 * kWgPlanes), pl = q % (3 * kWgPlanes);
-        *reinterpret_cast<uint4 *>(op + st * STAGE + pl * A_PLANE + r * 16) = make_uint4(0u, 0u, 0u, 0u);
+    // the padding rows of A in every slot stay zero
+    for (int i = tid; i < 4 * kWgPlanes * (128 - M_REAL); i += kWgThreads) {
+        const int r = M_REAL + i % (128 - M_REAL), pl = i / (128 - M_REAL);  // pl = slot * planes + plane
+        *reinterpret_cast<uint4 *>(slots + pl * A_PLANE + r * 16) = make_uint4(0u, 0u, 0u, 0u);
     }
     if (tid == 0) {
         for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mma_done[i])));
@@ -631,78 +637,104 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_bwd_weight_tc(const __nv_bf
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tmem_slot;
 
-    const int segs = (W + kWgK - 1) / kWgK;
-    const long long total = (long long)n_img * H * segs;
-    int it = 0;
-    bool ok = true;
-    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++it) {
-        const int seg = (int)(t % segs);
-        const long long ry = t / segs;
-        const int y = (int)(ry % H), img = (int)(ry / H);
-        const int x0 = seg * kWgK;
-        const size_t base = (size_t)img * H * W;
-        // raw rows: input rows y-1 .. y+1 at x0-1 .. x0+kWgK, the dZ row at x0 ..
-        for (int i = tid; i < 3 * (kWgK + 2) * (CIN / 8); i += kWgThreads) {
-            const int v8 = i % (CIN / 8), r = i / (CIN / 8), px = r % (kWgK + 2), dy = r / (kWgK + 2);
-            const int gx = x0 - 1 + px, gy = y + dy - 1;
+    // the input row yy of image img at x0-1 .. x0+kWgK into ra (zeros outside)
+    auto stage_row = [&](size_t base, int yy, int x0) {
+        for (int i = tid; i < (kWgK + 2) * (CIN / 8); i += kWgThreads) {
+            const int v8 = i % (CIN / 8), px = i / (CIN / 8), gx = x0 - 1 + px;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H)
-                v = *reinterpret_cast<const uint4 *>(a_in + (base + (size_t)gy * W + gx) * CIN + v8 * 8);
-            *reinterpret_cast<uint4 *>(ra + (size_t)r * CIN + v8 * 8) = v;
+            if (gx >= 0 && gx < W && yy >= 0 && yy < H)
+                v = *reinterpret_cast<const uint4 *>(a_in + (base + (size_t)yy * W + gx) * CIN + v8 * 8);
+            *reinterpret_cast<uint4 *>(ra + (size_t)px * CIN + v8 * 8) = v;
         }
-        for (int i = tid; i < kWgK * (COUT / 8); i += kWgThreads) {
-            const int v8 = i % (COUT / 8), px = i / (COUT / 8), gx = x0 + px;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (gx < W) v = *reinterpret_cast<const uint4 *>(dz + (base + (size_t)y * W + gx) * COUT + v8 * 8);
-            *reinterpret_cast<uint4 *>(rz + px * COUT + v8 * 8) = v;
-        }
-        // the stage this tile fills was read by the MMAs of tile it-2
-        const int s = it & 1;
-        const bool w_ok = it < 2 || tc_wait(&mma_done[s], ((it - 2) >> 1) & 1);
-        if (!__syncthreads_and(w_ok ? 1 : 0)) {  // (also: the raw rows are complete)
-            ok = false;
-            break;
-        }
-        unsigned char *A = op + s * STAGE, *B = A + A_BYTES;
-        for (int i = tid; i < 3 * kWgPlanes * M_REAL; i += kWgThreads) {
-            const int m = i % M_REAL, q = i / M_REAL, j = q % kWgPlanes, dy = q / kWgPlanes;
-            const int dx = m / CIN, ci = m - dx * CIN;
-            const __nv_bfloat16 *src = ra + ((size_t)dy * (kWgK + 2) + 8 * j + dx) * CIN + ci;
-            *reinterpret_cast<uint4 *>(A + (dy * kWgPlanes + j) * A_PLANE + m * 16) =
+    };
+    // ra transposed into a row slot: rows m = dx*CIN + ci, planes of 8 pixels
+    auto transpose_row = [&](int slot) {
+        unsigned char *A = slots + slot * SLOT;
+        for (int i = tid; i < kWgPlanes * M_REAL; i += kWgThreads) {
+            const int m = i % M_REAL, j = i / M_REAL, dx = m / CIN, ci = m - dx * CIN;
+            const __nv_bfloat16 *src = ra + (size_t)(8 * j + dx) * CIN + ci;
+            *reinterpret_cast<uint4 *>(A + j * A_PLANE + m * 16) =
                 make_uint4(bf16_pair(src[0], src[CIN]), bf16_pair(src[2 * CIN], src[3 * CIN]),
                            bf16_pair(src[4 * CIN], src[5 * CIN]), bf16_pair(src[6 * CIN], src[7 * CIN]));
         }
-        for (int i = tid; i < kWgPlanes * COUT; i += kWgThreads) {
-            const int co = i % COUT, j = i / COUT;
-            const __nv_bfloat16 *src = rz + (size_t)(8 * j) * COUT + co;
-            *reinterpret_cast<uint4 *>(B + j * B_PLANE + co * 16) =
-                make_uint4(bf16_pair(src[0], src[COUT]), bf16_pair(src[2 * COUT], src[3 * COUT]),
-                           bf16_pair(src[4 * COUT], src[5 * COUT]), bf16_pair(src[6 * COUT], src[7 * COUT]));
+    };
+    // the MMAs of output row `it` have completed (commits alternate on two barriers)
+    auto row_done = [&](int j) -> bool { return tc_wait(&mma_done[j & 1], (j >> 1) & 1); };
+
+    const int segs = (W + kWgK - 1) / kWgK, bands = (H + kWgBand - 1) / kWgBand;
+    const long long units = (long long)n_img * segs * bands;
+    int it = 0;  // output rows of this CTA so far
+    bool ok = true;
+    for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const int seg = (int)(u % segs);
+        const long long q = u / segs;
+        const int band = (int)(q % bands), img = (int)(q / bands);
+        const int x0 = seg * kWgK, y0 = band * kWgBand, y1 = min(y0 + kWgBand, H);
+        const size_t base = (size_t)img * H * W;
+        // the previous strip's MMAs read every slot: let them complete
+        const bool w = (it < 1 || row_done(it - 1)) && (it < 2 || row_done(it - 2));
+        if (!__syncthreads_and(w ? 1 : 0)) {
+            ok = false;
+            break;
         }
-        // generic-proxy writes -> visible to the tensor core
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned idesc = tc_idesc(128, COUT);
-            const unsigned a0 = tc_smem(A), b0 = tc_smem(B);
-#pragma unroll
-            for (int dy = 0; dy < 3; ++dy) {
-#pragma unroll
-                for (int kc = 0; kc < kWgK / 16; ++kc) {
-                    const unsigned long long ad = tc_desc(a0 + (dy * kWgPlanes + 2 * kc) * A_PLANE, A_PLANE, 128);
-                    const unsigned long long bd = tc_desc(b0 + 2 * kc * B_PLANE, B_PLANE, 128);
-                    const unsigned acc = (it > 0 || kc > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem +
-                                                                                              (unsigned)(dy * COUT)),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-                }
+        // input rows y0-1 and y0 into slots 0 and 1 (row yy in slot (yy - y0 + 1) % 4)
+        for (int p = 0; p < 2; ++p) {
+            stage_row(base, y0 - 1 + p, x0);
+            __syncthreads();
+            transpose_row(p);
+            __syncthreads();
+        }
+        for (int r = y0; r < y1; ++r, ++it) {
+            // raw rows: input row r+1 (its slot held row r-3, read by row it-2),
+            // dZ row r (B slot it % 2, read by row it-2)
+            stage_row(base, r + 1, x0);
+            for (int i = tid; i < kWgK * (COUT / 8); i += kWgThreads) {
+                const int v8 = i % (COUT / 8), px = i / (COUT / 8), gx = x0 + px;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (gx < W) v = *reinterpret_cast<const uint4 *>(dz + (base + (size_t)r * W + gx) * COUT + v8 * 8);
+                *reinterpret_cast<uint4 *>(rz + px * COUT + v8 * 8) = v;
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             tc_smem(&mma_done[s]))
-                         : "memory");
+            const bool w2 = r - y0 < 2 || row_done(it - 2);
+            if (!__syncthreads_and(w2 ? 1 : 0)) {  // (also: the raw rows are complete)
+                ok = false;
+                break;
+            }
+            const int sn = (r - y0 + 2) & 3;
+            transpose_row(sn);
+            unsigned char *B = bslots + (it & 1) * BSLOT;
+            for (int i = tid; i < kWgPlanes * COUT; i += kWgThreads) {
+                const int co = i % COUT, j = i / COUT;
+                const __nv_bfloat16 *src = rz + (size_t)(8 * j) * COUT + co;
+                *reinterpret_cast<uint4 *>(B + j * B_PLANE + co * 16) =
+                    make_uint4(bf16_pair(src[0], src[COUT]), bf16_pair(src[2 * COUT], src[3 * COUT]),
+                               bf16_pair(src[4 * COUT], src[5 * COUT]), bf16_pair(src[6 * COUT], src[7 * COUT]));
+            }
+            // generic-proxy writes -> visible to the tensor core
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned idesc = tc_idesc(128, COUT);
+                const unsigned b0 = tc_smem(B);
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) {
+                    const unsigned a0 = tc_smem(slots + ((r - y0 + dy) & 3) * SLOT);  // input row r-1+dy
+#pragma unroll
+                    for (int kc = 0; kc < kWgK / 16; ++kc) {
+                        const unsigned long long ad = tc_desc(a0 + 2 * kc * A_PLANE, A_PLANE, 128);
+                        const unsigned long long bd = tc_desc(b0 + 2 * kc * B_PLANE, B_PLANE, 128);
+                        const unsigned acc = (it > 0 || kc > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                                tmem + (unsigned)(dy * COUT)),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 tc_smem(&mma_done[it & 1]))
+                             : "memory");
+            }
         }
     }
     // every MMA complete, then each accumulator row out: warp w (< 4) reads
