@@ -799,32 +799,61 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
-// round(x * fs) (nearest, ties to even) as a two's-complement word, for
-// two values with one paired fused multiply-add on the FMA pipe: with
-// M = 1.5 * 2^23, x * fs + M lies in [2^23, 2^24) where the float spacing is
-// 1, so the one rounding of the fused multiply-add is the rounding to an
-// integer and the low mantissa bits are that integer + 2^22. Exact for
-// |x * fs| < 2^22 (features below 128 at the 2^15 colour scale, 8-bit
-// values at scale 1), and equal to __float2int_rn(x * fs) there since fs is
-// a power of two.
-__device__ __forceinline__ void fix_round2(float x0, float x1, float fs, unsigned &r0, unsigned &r1) {
-    const unsigned long long m = fma2(pack2(x0, x1), pack2(fs, fs), pack2(12582912.0f, 12582912.0f));
-    float m0, m1;
-    unpack2(m, m0, m1);
-    r0 = (unsigned)(__float_as_int(m0) - 0x4B400000);
-    r1 = (unsigned)(__float_as_int(m1) - 0x4B400000);
-}
-
 // min of two non-negative floats (a NaN operand loses), IEEE (no flush).
 __device__ __forceinline__ float fmin_nan(float a, float b) {
     float r;
     asm("min.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
     return r;
 }
+// The same over three operands (one instruction on sm_100 and later).
+__device__ __forceinline__ float fmin3_nan(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// round(x * fs) (nearest, ties to even) for two values with one paired
+// fused multiply-add on the FMA pipe, as a biased word: with M = 1.5 * 2^23,
+// x * fs + M lies in [2^23, 2^24) where the float spacing is 1, so the one
+// rounding of the fused multiply-add is the rounding to an integer, and the
+// float's bits are that integer + kFixBias (the bits of M). Exact for
+// |x * fs| < 2^22 (features below 128 at the 2^15 colour scale, 8-bit values
+// at scale 1), and equal to __float2int_rn(x * fs) + kFixBias there since fs
+// is a power of two. Sums of such words taken mod 2^32, minus count *
+// kFixBias, are the sums of the rounded values, exactly, whenever those fit
+// in 31 bits (at most 2^22 per value, 128 values per private copy).
+constexpr unsigned kFixBias = 0x4B400000u;
+__device__ __forceinline__ void fix_round2_biased(float x0, float x1, float fs, unsigned &r0, unsigned &r1) {
+    const unsigned long long m = fma2(pack2(x0, x1), pack2(fs, fs), pack2(12582912.0f, 12582912.0f));
+    float m0, m1;
+    unpack2(m, m0, m1);
+    r0 = __float_as_uint(m0);
+    r1 = __float_as_uint(m1);
+}
 
 // Eq. (1) for two pixels (colour pairs l, a, b; column pair x) against one
 // centre record: d_lab = sqrt(dl^2 + da^2 + db^2), d_xy = sqrt(dx^2 + dy^2),
-// D = (m/S) d_xy + d_lab, then the index-carrying running minimum.
+// D = (m/S) d_xy + d_lab, as the two pixels' keys (D & ~15) | t.
+__device__ __forceinline__ void eval_keys(const ulonglong2 &la, const ulonglong2 &bx, unsigned long long ddy2,
+                                          unsigned long long ww, unsigned long long l, unsigned long long a,
+                                          unsigned long long b, unsigned long long x, unsigned t, float &k0,
+                                          float &k1) {
+    const unsigned long long dl = sub2(la.x, l), da = sub2(la.y, a), db = sub2(bx.x, b);
+    const unsigned long long s = fma2(dl, dl, fma2(da, da, mul2(db, db)));
+    const unsigned long long dx = sub2(bx.y, x);
+    const unsigned long long q = fma2(dx, dx, ddy2);
+    float s0, s1, q0, q1;
+    unpack2(s, s0, s1);
+    unpack2(q, q0, q1);
+    const unsigned long long D = fma2(ww, pack2(fsqrt_approx(q0), fsqrt_approx(q1)),
+                                      pack2(fsqrt_approx(s0), fsqrt_approx(s1)));
+    float d0, d1;
+    unpack2(D, d0, d1);
+    k0 = __uint_as_float((__float_as_uint(d0) & ~15u) | t);
+    k1 = __uint_as_float((__float_as_uint(d1) & ~15u) | t);
+}
+
+// The same, folded into the running minimum.
 __device__ __forceinline__ void eval_pair(const ulonglong2 &la, const ulonglong2 &bx, unsigned long long ddy2,
                                           unsigned long long ww, unsigned long long l, unsigned long long a,
                                           unsigned long long b, unsigned long long x, unsigned t, float &bk0,
@@ -946,9 +975,11 @@ __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, const MultiHdr *
             uint4 *p = reinterpret_cast<uint4 *>(ws + (size_t)q * win_max * 4 + idx);
             const uint4 v = *p;
             *p = make_uint4(0u, 0u, 0u, 0u);
-            l += (int)v.x;
-            a += (int)v.y;
-            b += (int)v.z;
+            // the colour words carry kFixBias per pixel (fix_round2_biased)
+            const unsigned bias = (v.w >> 24) * kFixBias;
+            l += (int)(v.x - bias);
+            a += (int)(v.y - bias);
+            b += (int)(v.z - bias);
             xs += v.w & 0xFFFu;
             ys += ((v.w >> 12) & 0xFFFu) + (NCOPY > kWarps ? 4u * (unsigned)q * (v.w >> 24) : 0u);
             n += v.w >> 24;
@@ -1224,6 +1255,7 @@ __device__ __forceinline__ void assign_pipe_body(const FrameArgs *frames, int n_
     // (the condition only becomes true once, and this thread's acquire and
     // proxy fence precede all its later copies).
     int dep_f = -1, dep_pass = -1;
+    int pf = 0;  // frame of this producer thread's last tile (one launch per pass)
     auto produce = [&](int j, int q, int use) -> bool {
         if constexpr (MULTI) {
             if (j >= n_items) return true;
@@ -1276,7 +1308,10 @@ __device__ __forceinline__ void assign_pipe_body(const FrameArgs *frames, int n_
             if (t >= total_tiles) return true;
             if (*reinterpret_cast<volatile int *>(&g_abort_copies)) return false;
             if (use > 0 && !mbar_wait(&empty[q], (use - 1) & 1)) return false;
-            const int f = find_frame<TH == 64 ? kTileBase64 : kTileBase>(frames, n_frames, t);
+            // A producer thread's tiles come in increasing order: its frame
+            // index only moves forward.
+            while (pf + 1 < n_frames && base_of<TH == 64 ? kTileBase64 : kTileBase>(frames[pf + 1]) <= t) ++pf;
+            const int f = pf;
             TileGeom g = tile_geom<TH>(frames[f], t - base_of<TH == 64 ? kTileBase64 : kTileBase>(frames[f]));
             g.f = f;
             g.skip = !LAST && check_stop && frame_stopped(frames[f]) ? 1 : 0;
@@ -1484,19 +1519,36 @@ __device__ __forceinline__ void assign_pipe_body(const FrameArgs *frames, int n_
                 const float fx = (float)x;  // x + j exactly (x < 2^24)
                 const unsigned long long x01 = pack2(fx, fx + 1.0f), x23 = pack2(fx + 2.0f, fx + 3.0f);
                 const int own = rowoff + cx[0];
+                // Candidates two at a time: each pixel's running minimum takes
+                // both keys in one three-operand min (keys are distinct, so
+                // the grouping does not change the result).
 #pragma unroll
-                for (int t = 0; t < 9; ++t) {
-                    const float *rp = cen + (size_t)(own + (t / 3 - 1) * bw + (t % 3 - 1)) * kCtabRec;
-                    const ulonglong2 la = *reinterpret_cast<const ulonglong2 *>(rp);      // (L, L), (a, a)
-                    const ulonglong2 bx = *reinterpret_cast<const ulonglong2 *>(rp + 4);  // (b, b), (x, x)
-                    const unsigned long long yy = *reinterpret_cast<const unsigned long long *>(rp + 8);
+                for (int t0 = 0; t0 < 9; t0 += 2) {
+                    const int nt = t0 < 8 ? 2 : 1;
+                    float kk[2][ROWS][kPPT];
 #pragma unroll
-                    for (int r = 0; r < ROWS; ++r) {
-                        const unsigned long long ddy = sub2(yy, fyy[r]);
-                        const unsigned long long ddy2 = mul2(ddy, ddy);
-                        eval_pair(la, bx, ddy2, ww, l01[r], a01[r], b01[r], x01, (unsigned)t, bk[r][0], bk[r][1]);
-                        eval_pair(la, bx, ddy2, ww, l23[r], a23[r], b23[r], x23, (unsigned)t, bk[r][2], bk[r][3]);
+                    for (int u = 0; u < nt; ++u) {
+                        const int t = t0 + u;
+                        const float *rp = cen + (size_t)(own + (t / 3 - 1) * bw + (t % 3 - 1)) * kCtabRec;
+                        const ulonglong2 la = *reinterpret_cast<const ulonglong2 *>(rp);      // (L, L), (a, a)
+                        const ulonglong2 bx = *reinterpret_cast<const ulonglong2 *>(rp + 4);  // (b, b), (x, x)
+                        const unsigned long long yy = *reinterpret_cast<const unsigned long long *>(rp + 8);
+#pragma unroll
+                        for (int r = 0; r < ROWS; ++r) {
+                            const unsigned long long ddy = sub2(yy, fyy[r]);
+                            const unsigned long long ddy2 = mul2(ddy, ddy);
+                            eval_keys(la, bx, ddy2, ww, l01[r], a01[r], b01[r], x01, (unsigned)t, kk[u][r][0],
+                                      kk[u][r][1]);
+                            eval_keys(la, bx, ddy2, ww, l23[r], a23[r], b23[r], x23, (unsigned)t, kk[u][r][2],
+                                      kk[u][r][3]);
+                        }
                     }
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+                        for (int j = 0; j < kPPT; ++j)
+                            bk[r][j] = nt == 2 ? fmin3_nan(bk[r][j], kk[0][r][j], kk[1][r][j])
+                                               : fmin_nan(bk[r][j], kk[0][r][j]);
                 }
             } else {
                 const float fy = (float)y[0];
@@ -1573,9 +1625,9 @@ __device__ __forceinline__ void assign_pipe_body(const FrameArgs *frames, int n_
                 const unsigned xyn = (unsigned)lx + (yo << 12) + (1u << 24);
 #pragma unroll
                 for (int j = 0; j < kPPT; j += 2) {
-                    fix_round2(f0[r][j], f0[r][j + 1], fs, v[j][0], v[j + 1][0]);
-                    fix_round2(f1[r][j], f1[r][j + 1], fs, v[j][1], v[j + 1][1]);
-                    fix_round2(f2[r][j], f2[r][j + 1], fs, v[j][2], v[j + 1][2]);
+                    fix_round2_biased(f0[r][j], f0[r][j + 1], fs, v[j][0], v[j + 1][0]);
+                    fix_round2_biased(f1[r][j], f1[r][j + 1], fs, v[j][1], v[j + 1][1]);
+                    fix_round2_biased(f2[r][j], f2[r][j + 1], fs, v[j][2], v[j + 1][2]);
                     v[j][3] = xyn + (unsigned)j;
                     v[j + 1][3] = xyn + (unsigned)(j + 1);
                 }
