@@ -41,6 +41,7 @@ struct slic_batch_ctx {
     int *ccl = nullptr;               // component connectivity (mode 2): scratch over all frames' pixels
     CclFrame *d_ccl = nullptr;
     std::vector<CclFrame> ccl_frames;
+    int ccl_tiles_total = 0;          // 32x32 tiles of all frames (component connectivity)
     std::vector<const uint8_t *> images;
     bool any_conv = false;            // some frame has a stopping threshold
     int total_tiles = 0, total_centres = 0, total_rows = 0, max_w = 0, win_max = 0;
@@ -283,12 +284,14 @@ void bind_frames(slic_batch_ctx *b, const uint8_t *const *d_images, int32_t *con
     }
     if (b->connectivity == 2) {
         b->ccl_frames.assign(b->n, CclFrame{});
-        int base = 0;
+        int base = 0, tile_base = 0;
         for (int f = 0; f < b->n; ++f) {
             const FrameArgs &a = b->frames[f];
-            b->ccl_frames[f] = CclFrame{a.labels, a.labels, a.W, a.S * a.S / 4, base};
+            b->ccl_frames[f] = CclFrame{a.labels, a.labels, a.W, a.S * a.S / 4, base, a.H, tile_base};
             base += a.W * a.H;
+            tile_base += ccl_tiles(a.W, a.H);
         }
+        b->ccl_tiles_total = tile_base;
     }
 }
 
@@ -679,7 +682,8 @@ cudaError_t enqueue_span(slic_batch_ctx *b, const Span &sp, cudaStream_t s, bool
     }
     if (e == cudaSuccess && b->connectivity == 2) {
         // component-based connectivity over all frames at once, in place on the labels
-        e = launch_connectivity_components(b->d_ccl, b->ccl_frames[0], b->n, (int)b->total_pixels, b->ccl, b->d_err,
+        e = launch_connectivity_components(b->d_ccl, b->ccl_frames[0], b->n, (int)b->total_pixels, b->ccl_tiles_total,
+                                           b->ccl, b->d_err,
                                            s);
         n_launch += 9;
     } else if (e == cudaSuccess && b->connectivity) {

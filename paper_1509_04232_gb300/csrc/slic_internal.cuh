@@ -263,17 +263,23 @@ cudaError_t launch_connectivity_components(const int32_t *in, int32_t *out, int 
                                            int *scratch, int *err, cudaStream_t s);
 // Several frames at once: d_table[n] (device) describes each frame, base =
 // its first index in the concatenation of all frames' pixels (G in total,
-// below 2^31); scratch holds ccl_scratch_ints(G) ints. For n == 1, `one`
-// is used and d_table may be null.
+// below 2^31) and tile_base its first 32x32 tile in the concatenation of all
+// frames' tiles (`tiles` in total, ccl_tiles per frame); scratch holds
+// ccl_scratch_ints(G) ints. For n == 1, `one` is used and d_table may be
+// null.
 struct CclFrame {
     const int32_t *in;
     int32_t *out;
     int W;
     int min_size;
     int base;
+    int H;
+    int tile_base;  // first 32x32 tile of the frame in the call's list of tiles
 };
-cudaError_t launch_connectivity_components(const CclFrame *d_table, const CclFrame &one, int n, int G, int *scratch,
-                                           int *err, cudaStream_t s);
+// 32x32 tiles of a W x H frame (the unit of the component stages).
+int ccl_tiles(int W, int H);
+cudaError_t launch_connectivity_components(const CclFrame *d_table, const CclFrame &one, int n, int G, int tiles,
+                                           int *scratch, int *err, cudaStream_t s);
 // The learned warm start's network (slic_net.cu) as seen by the segmentation
 // drivers: its geometry, and the labels of `batch` images (uint8 [H][W][C],
 // C = 3 or 4; given by a device table of image pointers, or contiguous in

@@ -2283,11 +2283,27 @@ __global__ void __launch_bounds__(256, 4) k_connectivity2_batch(const FrameArgs 
 // is kept, and kept segments are numbered 0, 1, ... in scan order.
 //
 // Union-find over pixel indices: a pixel's parent always has a smaller
-// index, so each component's root is its first pixel in scan order. Every
-// walk is bounded; a walk that gives up sets bit 1 of *err.
+// index, so each component's root is its first pixel in scan order. The
+// pixels of all frames of a call form one index space (frame f holds base_f
+// .. base_f + W_f*H_f - 1). Stages:
+//   1. per 32x32 tile, union-find in shared memory; every pixel's parent is
+//      its tile-local root (the component's first pixel within the tile),
+//      which carries its size within the tile and goes into a list;
+//   2. unions across the tile edges (global memory), only for edge pixels;
+//   3. per tile-local root only: its component's root and the sizes;
+//   4-5. per component root only: keep it or join a neighbour's segment,
+//      then follow the joins to a kept root; kept roots are marked in a
+//      bitmap;
+//   6. ranks of the kept roots (a scan of the bitmap's population counts);
+//   7. per tile-local root: its segment's new label; then per pixel: the
+//      label of its tile-local root.
+// Every walk is bounded; a walk that gives up sets bit 1 of *err, and the
+// indices it leaves behind stay in range.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr unsigned kCclSteps = 1u << 22;
+constexpr int kCclTile = 32;                          // tile side (pixels)
+constexpr int kCclThreads = 128;                      // per tile: 8 pixels per thread
 constexpr int kScanThreads = 256, kScanPer = 8, kScanBlock = kScanThreads * kScanPer;
 }  // namespace
 
@@ -2326,125 +2342,270 @@ __device__ __forceinline__ void ccl_union(int *parent, int a, int b, int *err) {
     }
     atomicOr(err, 2);
 }
+
+// The same two operations on a tile's parents in shared memory.
+// (with path halving: an entry on the way is pointed at its grandparent,
+// an ancestor, which concurrent walks and links tolerate)
+__device__ __forceinline__ int ccl_find_s(int *par, int i, int *err) {
+    volatile int *vp = par;
+    const unsigned lim = g_ccl_steps;
+    for (unsigned n = 0; n < lim; ++n) {
+        const int p = vp[i];
+        if (p == i) return i;
+        const int gp = vp[p];
+        if (gp != p) vp[i] = gp;
+        i = gp;
+    }
+    atomicOr(err, 2);
+    return i;
+}
+__device__ __forceinline__ void ccl_union_s(int *par, int a, int b, int *err) {
+    const unsigned lim = g_ccl_steps;
+    for (unsigned n = 0; n < lim; ++n) {
+        a = ccl_find_s(par, a, err);
+        b = ccl_find_s(par, b, err);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicMin(par + a, b);
+        if (old == a) return;
+        a = old;
+    }
+    atomicOr(err, 2);
+}
 }  // namespace
 
-// The frames of a call: pixels of all frames form one index space (frame f
-// holds base_f .. base_f + W_f*H_f - 1), so parents and roots are global
-// indices and a pixel's left / upper neighbour is g - 1 / g - W_f. One frame
-// travels in the launch itself, several in a device table.
+// The frames of a call: one travels in the launch itself, several in a
+// device table.
 struct CclFrames {
     const CclFrame *table;
     CclFrame one;
     int n;
 };
 
+// The frame holding global pixel g (last base <= g), or tile t (last tile
+// base <= t).
 __device__ __forceinline__ CclFrame ccl_frame_of(const CclFrames &fr, int g) {
     if (fr.n == 1) return fr.one;
     int lo = 0, hi = fr.n - 1;
-    while (lo < hi) {  // last frame whose base <= g
+    while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (fr.table[mid].base <= g) lo = mid;
         else hi = mid - 1;
     }
     return fr.table[lo];
 }
-
-// Parent = the first pixel of the pixel's horizontal run within the warp's
-// 32 pixels, or the pixel before the warp when the run comes from there (a
-// run never crosses a row, hence never a frame).
-__global__ void k_ccl_init(CclFrames fr, int G, int *parent) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
-    const bool valid = g < G;
-    CclFrame f{};
-    int32_t v = 0;
-    int i = 0;
-    if (valid) {
-        f = ccl_frame_of(fr, g);
-        i = g - f.base;
-        v = f.in[i];
+__device__ __forceinline__ CclFrame ccl_frame_of_tile(const CclFrames &fr, int t) {
+    if (fr.n == 1) return fr.one;
+    int lo = 0, hi = fr.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (fr.table[mid].tile_base <= t) lo = mid;
+        else hi = mid - 1;
     }
-    const int32_t left = __shfl_up_sync(kFull, v, 1);
-    bool same_left = false;
-    if (valid && i % f.W > 0) same_left = lane == 0 ? f.in[i - 1] == v : left == v;
-    const unsigned starts = __ballot_sync(kFull, !same_left) & (kFull >> (31 - lane));
-    if (valid) parent[g] = starts ? g - lane + (31 - __clz(starts)) : g - lane - 1;
+    return fr.table[lo];
 }
 
-// Vertical links; a pixel whose left neighbour is in its run and has the same
-// link above needs none of its own.
-__global__ void k_ccl_merge(CclFrames fr, int G, int *parent, int *err) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= G) return;
-    const CclFrame f = ccl_frame_of(fr, g);
-    const int i = g - f.base, W = f.W;
-    if (i < W) return;
-    const int32_t v = f.in[i];
-    if (f.in[i - W] != v) return;
-    if (i % W > 0 && f.in[i - 1] == v && f.in[i - W - 1] == v) return;
-    ccl_union(parent, g, g - W, err);
-}
-
-__global__ void k_ccl_compress(int N, int *parent, int *err) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) parent[i] = ccl_find(parent, i, err);
-}
-
-// Segment sizes (count zeroed beforehand), one atomic per root per warp.
-__global__ void k_ccl_count(int N, const int *parent, int *count) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
-    const int r = i < N ? parent[i] : -1;
-    const unsigned peers = __match_any_sync(kFull, r);
-    if (r >= 0 && lane == __ffs(peers) - 1) atomicAdd(count + r, __popc(peers));
-}
-
-// Per root: itself when kept, else the root of its first pixel's left (or,
-// in column 0, upper) neighbour; a frame's first pixel is always kept.
-__global__ void k_ccl_decide(CclFrames fr, int G, const int *parent, const int *count, int *target) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= G || parent[g] != g) return;
-    const CclFrame f = ccl_frame_of(fr, g);
-    const int i = g - f.base;
-    int t = g;
-    if (i != 0 && count[g] <= f.min_size) t = parent[i % f.W > 0 ? g - 1 : g - f.W];
-    target[g] = t;
-}
-
-// Per root: follow the joins to the kept segment (chains point to smaller
-// indices and end at a kept root; in place, every value written stays on
-// the chain). After a walk of an earlier stage gave up, a chain may reach
-// an entry no stage wrote: every step is checked to stay in [0, N), and one
-// that would leave it ends the walk with the error bit set.
-__global__ void k_ccl_resolve(int N, const int *parent, int *target, int *err) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N || parent[i] != i) return;
-    int t = target[i];
-    unsigned n = 0;
-    const unsigned lim = g_ccl_steps;
-    for (; n < lim; ++n) {
-        const int u = __ldcg(target + t);
-        if (u == t) break;
-        if ((unsigned)u >= (unsigned)N) {
-            n = lim;
-            break;
+// Stage 1: a CTA per 32x32 tile, a warp per tile row at a time. Parents in
+// shared memory (tile-local indices in row-major order, which is scan order
+// within the tile): each pixel starts at the first pixel of its horizontal
+// run (a ballot over the row), vertical links join runs (a pixel whose left
+// neighbour makes the same vertical link needs none), then every pixel is
+// compressed to its tile-local root. Output: every pixel's global parent is
+// its tile-local root; a tile-local root's count is its size within the
+// tile, and it is appended to the list lroots[0 .. *n_lroots).
+__global__ void __launch_bounds__(kCclThreads) k_ccl_local(CclFrames fr, int *parent, int *count, int *lroots,
+                                                            int *n_lroots, int *err) {
+    __shared__ int32_t lab[kCclTile * kCclTile];
+    __shared__ int par[kCclTile * kCclTile];
+    __shared__ int cnt[kCclTile * kCclTile];
+    const CclFrame f = ccl_frame_of_tile(fr, blockIdx.x);
+    const int local = blockIdx.x - f.tile_base, tiles_x = (f.W + kCclTile - 1) / kCclTile;
+    const int ty = local / tiles_x, tx = local - ty * tiles_x;
+    const int x0 = tx * kCclTile, y0 = ty * kCclTile;
+    const int tw = min(kCclTile, f.W - x0), th = min(kCclTile, f.H - y0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kRowsPerPass = kCclThreads / 32;
+    const bool col_ok = lane < tw;
+    for (int ly = warp; ly < kCclTile; ly += kRowsPerPass) {
+        const int i = ly * kCclTile + lane;
+        const bool ok = col_ok && ly < th;
+        const int32_t v = ok ? f.in[(size_t)(y0 + ly) * f.W + x0 + lane] : 0;
+        lab[i] = v;
+        cnt[i] = 0;
+        const int32_t left = __shfl_up_sync(kFull, v, 1);
+        const bool start = lane == 0 || left != v;
+        const unsigned starts = __ballot_sync(kFull, start) & (kFull >> (31 - lane));
+        par[i] = ly * kCclTile + (31 - __clz(starts));
+    }
+    __syncthreads();
+    for (int ly = warp + (warp == 0 ? kRowsPerPass : 0); ly < th; ly += kRowsPerPass) {
+        if (!col_ok) continue;
+        const int i = ly * kCclTile + lane;
+        const int32_t v = lab[i];
+        if (lab[i - kCclTile] != v) continue;
+        if (lane > 0 && lab[i - 1] == v && lab[i - kCclTile - 1] == v) continue;
+        ccl_union_s(par, i, i - kCclTile, err);
+    }
+    __syncthreads();
+    // Roots are always run starts (a link goes from a root to a root), so
+    // only the starts need a walk: each adds its run's length to its root's
+    // size, and the run's pixels take its root (no parent points at a pixel
+    // that is not a run start, so those entries can change freely).
+    for (int ly = warp; ly < th; ly += kRowsPerPass) {
+        const int i = ly * kCclTile + lane;
+        const int32_t v = lab[i];
+        const bool start = col_ok && (lane == 0 || lab[i - 1] != v);
+        const unsigned st = __ballot_sync(kFull, start);
+        int r = i;
+        if (start) {
+            r = ccl_find_s(par, i, err);
+            const unsigned after = st & ~(kFull >> (31 - lane));
+            atomicAdd(&cnt[r], (after ? __ffs(after) - 1 : tw) - lane);
         }
-        t = u;
+        r = __shfl_sync(kFull, r, 31 - __clz(st & (kFull >> (31 - lane))));
+        if (col_ok) par[i] = r;
     }
-    if (n == lim) atomicOr(err, 2);
-    target[i] = t;
+    __syncthreads();
+    // Parents out; the tile's roots go into the list with one global atomic
+    // per tile (a slot range), ordered by warp and row within it.
+    __shared__ int wbase[kRowsPerPass + 1];
+    int mine = 0;
+    for (int ly = warp; ly < th; ly += kRowsPerPass) {
+        const int i = ly * kCclTile + lane;
+        const int r = par[i];
+        const int g = f.base + (y0 + ly) * f.W + x0 + lane;
+        if (col_ok) parent[g] = f.base + (y0 + r / kCclTile) * f.W + x0 + (r & (kCclTile - 1));
+        const bool is_root = col_ok && r == i;
+        if (is_root) count[g] = cnt[i];
+        mine += __popc(__ballot_sync(kFull, is_root));
+    }
+    if (lane == 0) wbase[warp] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < kRowsPerPass; ++w) {
+            const int c = wbase[w];
+            wbase[w] = run;
+            run += c;
+        }
+        wbase[kRowsPerPass] = run ? atomicAdd(n_lroots, run) : 0;
+    }
+    __syncthreads();
+    int slot = wbase[kRowsPerPass] + wbase[warp];
+    for (int ly = warp; ly < th; ly += kRowsPerPass) {
+        const int i = ly * kCclTile + lane;
+        const bool is_root = col_ok && par[i] == i;
+        const unsigned roots = __ballot_sync(kFull, is_root);
+        if (is_root) lroots[slot + __popc(roots & ((1u << lane) - 1))] = f.base + (y0 + ly) * f.W + x0 + lane;
+        slot += __popc(roots);
+    }
 }
 
-// Exclusive scan of the kept-root flags, block by block (kScanBlock pixels):
-// rank[i] within the block, totals[block] the block's count.
-__global__ void __launch_bounds__(kScanThreads) k_ccl_scan_block(int N, const int *parent, const int *target,
-                                                                  int *rank, int *totals) {
+// Stage 2: unions across the tile's left and upper edges (a thread per edge
+// pixel). A pair whose neighbours along the edge are an equal-labelled pair
+// is skipped: both sides are connected inside their tiles.
+__global__ void __launch_bounds__(2 * kCclTile) k_ccl_border(CclFrames fr, int *parent, int *err) {
+    const CclFrame f = ccl_frame_of_tile(fr, blockIdx.x);
+    const int local = blockIdx.x - f.tile_base, tiles_x = (f.W + kCclTile - 1) / kCclTile;
+    const int ty = local / tiles_x, tx = local - ty * tiles_x;
+    const int x0 = tx * kCclTile, y0 = ty * kCclTile, W = f.W;
+    const int tw = min(kCclTile, W - x0), th = min(kCclTile, f.H - y0);
+    const int t = threadIdx.x & (kCclTile - 1);
+    if (threadIdx.x < kCclTile) {  // left edge: (x0, y0 + t) with (x0 - 1, y0 + t)
+        if (x0 == 0 || t >= th) return;
+        const int i = (y0 + t) * W + x0;
+        const int32_t v = f.in[i];
+        if (f.in[i - 1] != v) return;
+        if (t > 0 && f.in[i - W] == v && f.in[i - W - 1] == v) return;
+        ccl_union(parent, f.base + i, f.base + i - 1, err);
+    } else {  // upper edge: (x0 + t, y0) with (x0 + t, y0 - 1)
+        if (y0 == 0 || t >= tw) return;
+        const int i = y0 * W + x0 + t;
+        const int32_t v = f.in[i];
+        if (f.in[i - W] != v) return;
+        if (t > 0 && f.in[i - 1] == v && f.in[i - W - 1] == v) return;
+        ccl_union(parent, f.base + i, f.base + i - W, err);
+    }
+}
+
+// Stage 3, per tile-local root L: its component's root R (the parent of L
+// becomes R), and L's size added into R's. R's own entry is only added into
+// (R is a tile-local root that finds itself), so the sums need no order.
+__global__ void k_ccl_roots(int G, const int *lroots, const int *n_lroots, int *parent, int *count, int *err) {
+    const int nr = *n_lroots;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
+        const int L = lroots[k];
+        int R = ccl_find(parent, L, err);
+        if ((unsigned)R >= (unsigned)G) R = L;  // (only after a walk gave up)
+        if (R != L) {
+            parent[L] = R;
+            atomicAdd(count + R, __ldcg(count + L));
+        }
+    }
+}
+
+// Stage 4, per component root R (a tile-local root that is its own parent):
+// itself when kept (marked in the bitmap of kept roots), else the root of
+// its first pixel's left (or, in column 0, upper) neighbour, two steps away
+// (pixel -> tile-local root -> root); a frame's first pixel is always kept.
+__global__ void k_ccl_decide(CclFrames fr, const int *lroots, const int *n_lroots, const int *parent,
+                             const int *count, int *target, unsigned *kept) {
+    const int nr = *n_lroots;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
+        const int g = lroots[k];
+        if (parent[g] != g) continue;
+        const CclFrame f = ccl_frame_of(fr, g);
+        const int i = g - f.base;
+        int t = g;
+        if (i != 0 && count[g] <= f.min_size) t = parent[parent[i % f.W > 0 ? g - 1 : g - f.W]];
+        target[g] = t;
+        if (t == g) atomicOr(kept + (g >> 5), 1u << (g & 31));
+    }
+}
+
+// Stage 5, per component root: follow the joins to the kept segment (chains
+// point to smaller indices and end at a kept root; in place, every value
+// written stays on the chain). Every step is checked to stay in [0, G).
+__global__ void k_ccl_resolve(int G, const int *lroots, const int *n_lroots, const int *parent, int *target,
+                              int *err) {
+    const int nr = *n_lroots;
+    const unsigned lim = g_ccl_steps;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
+        const int g = lroots[k];
+        if (parent[g] != g) continue;
+        int t = target[g];
+        unsigned n = 0;
+        for (; n < lim; ++n) {
+            if ((unsigned)t >= (unsigned)G) {
+                t = g;
+                n = lim;
+                break;
+            }
+            const int u = __ldcg(target + t);
+            if (u == t) break;
+            t = u;
+        }
+        if (n == lim) atomicOr(err, 2);
+        target[g] = t;
+    }
+}
+
+// Stage 6a: exclusive scan of the kept bitmap's population counts, block by
+// block (kScanBlock words): rank[w] within the block, totals[block].
+__global__ void __launch_bounds__(kScanThreads) k_ccl_scan_block(int nw, const unsigned *kept, int *rank,
+                                                                  int *totals) {
     __shared__ int warp_sum[kScanThreads / 32];
     const int base = blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int f[kScanPer], sum = 0;
 #pragma unroll
     for (int j = 0; j < kScanPer; ++j) {
-        const int i = base + j;
-        f[j] = (i < N && parent[i] == i && target[i] == i) ? 1 : 0;
+        const int w = base + j;
+        f[j] = w < nw ? __popc(kept[w]) : 0;
         sum += f[j];
     }
     int incl = sum;  // inclusive scan of the thread sums within the warp
@@ -2460,8 +2621,8 @@ __global__ void __launch_bounds__(kScanThreads) k_ccl_scan_block(int N, const in
     int run = before + incl - sum;
 #pragma unroll
     for (int j = 0; j < kScanPer; ++j) {
-        const int i = base + j;
-        if (i < N) rank[i] = run;
+        const int w = base + j;
+        if (w < nw) rank[w] = run;
         run += f[j];
     }
     if (threadIdx.x == kScanThreads - 1) totals[blockIdx.x] = run;
@@ -2494,18 +2655,52 @@ __global__ void __launch_bounds__(1024) k_ccl_scan_totals(int nb, int *totals) {
     }
 }
 
-// New label: the kept root's rank among all kept roots, less the number of
-// kept roots of the earlier frames (the rank at the frame's base).
-__global__ void k_ccl_relabel(CclFrames fr, int G, const int *parent, const int *target, const int *rank,
-                              const int *totals) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= G) return;
-    const CclFrame f = ccl_frame_of(fr, g);
-    int r = target[parent[g]];
-    // (out of range only after a walk gave up, which set the error flag:
-    // the label is then wrong, the access still in bounds)
-    if ((unsigned)r >= (unsigned)G) r = f.base;
-    f.out[g - f.base] = rank[r] + totals[r / kScanBlock] - (rank[f.base] + totals[f.base / kScanBlock]);
+namespace {
+// Number of kept roots before global index k.
+__device__ __forceinline__ int ccl_rank(const unsigned *kept, const int *rank, const int *totals, int k) {
+    const int w = k >> 5;
+    return rank[w] + totals[w / kScanBlock] + __popc(kept[w] & ((1u << (k & 31)) - 1u));
+}
+}  // namespace
+
+// Stage 7a, per tile-local root L: the new label of L's segment, the rank of
+// its kept root among all kept roots less the rank of the frame's first
+// pixel (a kept root, the frame's label 0), into count[L] (sizes are no
+// longer needed).
+__global__ void k_ccl_final(CclFrames fr, int G, const int *lroots, const int *n_lroots, const int *parent,
+                            const int *target, const unsigned *kept, const int *rank, const int *totals, int *count) {
+    const int nr = *n_lroots;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
+        const int L = lroots[k];
+        const CclFrame f = ccl_frame_of(fr, L);
+        int R = parent[L];
+        // (out of range only after a walk gave up, which set the error flag:
+        // the label is then wrong, the accesses still in bounds)
+        if ((unsigned)R >= (unsigned)G) R = L;
+        int t = target[R];
+        if ((unsigned)t >= (unsigned)G) t = f.base;
+        count[L] = ccl_rank(kept, rank, totals, t) - ccl_rank(kept, rank, totals, f.base);
+    }
+}
+
+// Stage 7b, a CTA per tile: every pixel takes the label of its parent -- its
+// tile-local root, or for a tile-local root its segment's root, itself a
+// tile-local root of the same segment.
+__global__ void __launch_bounds__(kCclThreads) k_ccl_relabel(CclFrames fr, int G, const int *parent,
+                                                              const int *labels_of) {
+    const CclFrame f = ccl_frame_of_tile(fr, blockIdx.x);
+    const int local = blockIdx.x - f.tile_base, tiles_x = (f.W + kCclTile - 1) / kCclTile;
+    const int ty = local / tiles_x, tx = local - ty * tiles_x;
+    const int x0 = tx * kCclTile, y0 = ty * kCclTile;
+    const int tw = min(kCclTile, f.W - x0), th = min(kCclTile, f.H - y0);
+    for (int i = threadIdx.x; i < kCclTile * kCclTile; i += kCclThreads) {
+        const int lx = i & (kCclTile - 1), ly = i / kCclTile;
+        if (lx >= tw || ly >= th) continue;
+        const int p = (y0 + ly) * f.W + x0 + lx;
+        int L = parent[f.base + p];
+        if ((unsigned)L >= (unsigned)G) L = f.base;  // (only after a walk gave up)
+        f.out[p] = labels_of[L];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -2681,37 +2876,49 @@ cudaError_t launch_connectivity(const int32_t *in, int32_t *out, int W, int H, c
     return cudaGetLastError();
 }
 
+// Scratch of launch_connectivity_components over N pixels: parents, sizes,
+// join targets and the list of tile-local roots (N ints each), the kept-root bitmap and
+// its ranks (one int per 32 pixels each), the block totals, the root count.
 size_t ccl_scratch_ints(long long N) {
-    return (size_t)N * 4 + (size_t)((N + kScanBlock - 1) / kScanBlock) + 64;
+    const long long nw = (N + 31) / 32;
+    return (size_t)N * 4 + (size_t)nw * 2 + (size_t)((nw + kScanBlock - 1) / kScanBlock) + 64;
 }
 
-cudaError_t launch_connectivity_components(const CclFrame *d_table, const CclFrame &one, int n, int G, int *scratch,
-                                           int *err, cudaStream_t s) {
+int ccl_tiles(int W, int H) { return ((W + kCclTile - 1) / kCclTile) * ((H + kCclTile - 1) / kCclTile); }
+
+cudaError_t launch_connectivity_components(const CclFrame *d_table, const CclFrame &one, int n, int G, int tiles,
+                                           int *scratch, int *err, cudaStream_t s) {
     CclFrames fr;
     fr.table = d_table;
     fr.one = one;
     fr.n = n;
-    const int nb = (G + kScanBlock - 1) / kScanBlock, g = (G + 255) / 256;
-    int *parent = scratch, *count = scratch + G, *target = scratch + 2 * (size_t)G, *rank = scratch + 3 * (size_t)G;
-    int *totals = scratch + 4 * (size_t)G;
-    k_ccl_init<<<g, 256, 0, s>>>(fr, G, parent);
-    k_ccl_merge<<<g, 256, 0, s>>>(fr, G, parent, err);
-    k_ccl_compress<<<g, 256, 0, s>>>(G, parent, err);
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)G, s);
+    const int nw = (G + 31) / 32, nb = (nw + kScanBlock - 1) / kScanBlock, g = (G + 255) / 256;
+    int *parent = scratch, *count = scratch + G, *target = scratch + 2 * (size_t)G, *lroots = scratch + 3 * (size_t)G;
+    unsigned *kept = reinterpret_cast<unsigned *>(scratch + 4 * (size_t)G);
+    int *rank = scratch + 4 * (size_t)G + nw, *totals = rank + nw, *n_lroots = totals + nb;
+    cudaError_t e = cudaMemsetAsync(kept, 0, sizeof(unsigned) * (size_t)nw, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n_lroots, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_ccl_count<<<g, 256, 0, s>>>(G, parent, count);
-    k_ccl_decide<<<g, 256, 0, s>>>(fr, G, parent, count, target);
-    k_ccl_resolve<<<g, 256, 0, s>>>(G, parent, target, err);
-    k_ccl_scan_block<<<nb, kScanThreads, 0, s>>>(G, parent, target, rank, totals);
+    // the root stages run over the root list with a grid sized for the device
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid_roots = std::max(1, std::min(sms * 8, g));
+    k_ccl_local<<<tiles, kCclThreads, 0, s>>>(fr, parent, count, lroots, n_lroots, err);
+    k_ccl_border<<<tiles, 2 * kCclTile, 0, s>>>(fr, parent, err);
+    k_ccl_roots<<<grid_roots, 256, 0, s>>>(G, lroots, n_lroots, parent, count, err);
+    k_ccl_decide<<<grid_roots, 256, 0, s>>>(fr, lroots, n_lroots, parent, count, target, kept);
+    k_ccl_resolve<<<grid_roots, 256, 0, s>>>(G, lroots, n_lroots, parent, target, err);
+    k_ccl_scan_block<<<nb, kScanThreads, 0, s>>>(nw, kept, rank, totals);
     k_ccl_scan_totals<<<1, 1024, 0, s>>>(nb, totals);
-    k_ccl_relabel<<<g, 256, 0, s>>>(fr, G, parent, target, rank, totals);
+    k_ccl_final<<<grid_roots, 256, 0, s>>>(fr, G, lroots, n_lroots, parent, target, kept, rank, totals, count);
+    k_ccl_relabel<<<tiles, kCclThreads, 0, s>>>(fr, G, parent, count);
     return cudaGetLastError();
 }
 
 cudaError_t launch_connectivity_components(const int32_t *in, int32_t *out, int W, int H, int min_size,
                                            int *scratch, int *err, cudaStream_t s) {
-    CclFrame one{in, out, W, min_size, 0};
-    return launch_connectivity_components(nullptr, one, 1, W * H, scratch, err, s);
+    CclFrame one{in, out, W, min_size, 0, H, 0};
+    return launch_connectivity_components(nullptr, one, 1, W * H, ccl_tiles(W, H), scratch, err, s);
 }
 
 cudaError_t launch_connectivity_batch(const FrameArgs *d_frames, int n, int total_rows, int max_w, int pass,
