@@ -268,6 +268,11 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"mixed_batch": mixed_batch_throughput(args, pkg, stream, dev)}))
         return 0
+    if args.components_only:  # component connectivity on the bench frames (a profiling command)
+        stream = torch.cuda.Stream(device=dev)
+        if rank == 0:
+            print(json.dumps({"component_connectivity": components_step(args, pkg, stream, dev)}))
+        return 0
 
     B = args.batch
     seeds = frame_seeds(B, rank)
@@ -598,6 +603,33 @@ def video_context(args, pkg, dev, net_small):
     return out
 
 
+def components_step(args, pkg, stream, dev):
+    """The bench step (--batch frames of 1920x1080, S=16, m=10; --iterations,
+    default 10) with component-based connectivity (mode 2) and with the
+    paper's local rule (mode 1), one captured graph each, in the launch shape
+    --tuning gives (else autotuned): ms per step for both and the difference."""
+    import torch
+    from paper_1509_04232_gb300 import synth
+    B, iters = args.batch, args.iterations if args.iterations is not None else FULL_ITERS
+    imgs = [torch.from_numpy(synth.voronoi_frame(W, H, 400, 6.0, synth.seed_of(1, f))).to(dev) for f in range(B)]
+    out = {"frames": B, "iterations": iters}
+    for mode in (2, 1):
+        bs = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=M)] * B, iterations=iters, device=dev,
+                                enforce_connectivity=mode)
+        bs.bind(imgs)
+        if args.tuning:
+            bs.set_tuning(*((tuple(int(v) for v in args.tuning.split(",")) + (0, 1))[:6]))
+        else:
+            bs.autotune(os.path.join(tempfile.gettempdir(), "slicgb_autotune.jsonl"), stream=stream)
+        g = _capture(lambda: bs.segment(stream=stream), stream)
+        out[f"mode{mode}_ms_per_step"] = _graph_ms(g, stream, args, 1, dev)
+        bs.status()
+        bs.close()
+    out["components_minus_local_rule_ms"] = out["mode2_ms_per_step"] - out["mode1_ms_per_step"]
+    out["frames_per_s"] = B / (out["mode2_ms_per_step"] / 1e3)
+    return out
+
+
 def mixed_batch_throughput(args, pkg, stream, dev):
     """The 256-frame mixed batch (64 each of 640x480, 1280x720, 1920x1080,
     3840x2160; S in {8,16,32}, m in {5,10,20}; 5 iterations): one captured
@@ -829,6 +861,8 @@ def main(argv=None):
                     help="train the warm-start network on --train-images images and print its line (for profiling)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="run only the 256-frame mixed batch and print its line (for profiling)")
+    ap.add_argument("--components-only", action="store_true",
+                    help="run only the bench step with component connectivity and print its line (for profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

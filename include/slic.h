@@ -354,8 +354,8 @@ const char *slic_batch_last_error(slic_batch b);
    until the process exits. Images whose scratch exceeds 32 MiB are rejected
    with SLIC_ERR_INVALID; the scratch is 256 + 12*height*P + 48*K_eff +
    4*width*height bytes (P = width rounded up to 4), plus
-   16*width*height + 4*ceil(width*height/2048) + 256 with
-   enforce_connectivity = 2, each part rounded up to 256 (plus a 256-byte
+   16*width*height + 8*ceil(width*height/32) + 4*ceil(width*height/65536) +
+   256 with enforce_connectivity = 2, each part rounded up to 256 (plus a 256-byte
    state record). That
    admits e.g. 1280x720 or 1024x1024 at S >= 4 with connectivity mode 0 or
    1, and 1280x720 in mode 2; 1024x1024 in mode 2 and 1920x1080 in any mode
