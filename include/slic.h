@@ -234,14 +234,19 @@ slic_status slic_batch_segment(slic_batch b, void *stream);
    host_images[f] (uint8 [H][W][C]) into the bound device image, segment as
    slic_batch_segment, then copy the bound labels and centres into
    host_labels[f] (int32 [H][W]) and host_centres[f] (float [K_eff_f][6]).
-   host_labels or host_centres may be NULL to skip those copies. One
-   cudaMemcpyAsync per run of frames whose buffers lie back to back both on
-   the host and on the device (a batch held in one host and one device
-   allocation moves with one copy per direction and buffer kind); host
-   memory must be page-locked for the copies to overlap other work. Returns once everything is enqueued: synchronise the
-   stream before reading the outputs. Two batches bound to different device
-   buffers, driven on two streams, overlap one batch's copies with the
-   other's kernels. SLIC_ERR_STATE before slic_batch_set_buffers. */
+   host_labels or host_centres (or an entry of them) may be NULL to skip
+   those copies. One cudaMemcpyAsync per run of frames whose buffers lie
+   back to back both on the host and on the device (a batch held in one
+   host and one device allocation moves with one copy per direction and
+   buffer kind); host memory must be page-locked for the copies to overlap
+   other work. With frame groups (slic_batch_set_groups) each group's stream
+   copies the group's frames in, segments them and copies its results out,
+   so one group's copies overlap the other groups' kernels; the streams are
+   forked from and joined back to `stream`. Returns once everything is
+   enqueued: synchronise the stream before reading the outputs. Two batches
+   bound to different device buffers, driven on two streams, overlap one
+   batch's copies with the other's kernels as well. SLIC_ERR_STATE before
+   slic_batch_set_buffers. */
 slic_status slic_batch_segment_host(slic_batch b, const uint8_t *const *host_images, int32_t *const *host_labels,
                                     float *const *host_centres, void *stream);
 

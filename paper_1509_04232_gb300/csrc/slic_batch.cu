@@ -703,6 +703,13 @@ cudaError_t enqueue_span(slic_batch_ctx *b, const Span &sp, cudaStream_t s, bool
 
 extern "C" {
 
+// Groups run concurrently only on the plain pipelined path (the warm start,
+// component connectivity and the per-launch timers take the whole batch at
+// once).
+static bool split_groups(const slic_batch_ctx *b) {
+    return b->groups > 1 && b->pipe && !b->net && b->connectivity != 2 && !b->profiling;
+}
+
 slic_status slic_batch_segment(slic_batch b, void *stream) {
     if (!b) return bfail(nullptr, SLIC_ERR_INVALID, "NULL batch");
     if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
@@ -710,11 +717,7 @@ slic_status slic_batch_segment(slic_batch b, void *stream) {
     long long n_launch = 0;
     std::string why;
     cudaError_t e = cudaSuccess;
-    // Groups run concurrently only on the plain pipelined path (the warm
-    // start, component connectivity and the per-launch timers take the
-    // whole batch at once).
-    const bool split = b->groups > 1 && b->pipe && !b->net && b->connectivity != 2 && !b->profiling;
-    if (!split) {
+    if (!split_groups(b)) {
         e = enqueue_span(b, span_of(b, -1), s, true, n_launch, why);
     } else {
         e = cudaEventRecord(b->ev_fork, s);
@@ -766,34 +769,65 @@ slic_status slic_batch_segment_host(slic_batch b, const uint8_t *const *host_ima
     if (!b->buffers_set) return bfail(b, SLIC_ERR_STATE, "slic_batch_set_buffers has not been called");
     cudaStream_t s = (cudaStream_t)stream;
     const int n = b->n;
-    std::vector<const void *> src(n);
-    std::vector<void *> dst(n);
-    std::vector<size_t> len(n);
-    for (int f = 0; f < n; ++f) {
-        const FrameArgs &a = b->frames[f];
+    for (int f = 0; f < n; ++f)
         if (!host_images[f]) return bfail(b, SLIC_ERR_INVALID, "NULL host image for frame " + std::to_string(f));
-        src[f] = host_images[f];
-        dst[f] = const_cast<uint8_t *>(a.rgb);
-        len[f] = (size_t)a.W * a.H * a.C;
+    // The copies of frames f0 .. f1-1: images in (pass 0), or labels
+    // (pass 1) and centres (pass 2) out, on stream t.
+    auto copy_frames = [&](int f0, int f1, int pass, cudaStream_t t) -> cudaError_t {
+        const int m = f1 - f0;
+        std::vector<const void *> src(m);
+        std::vector<void *> dst(m);
+        std::vector<size_t> len(m);
+        if (pass == 1 && !host_labels) return cudaSuccess;
+        if (pass == 2 && !host_centres) return cudaSuccess;
+        for (int i = 0; i < m; ++i) {
+            const FrameArgs &a = b->frames[f0 + i];
+            if (pass == 0) {
+                src[i] = host_images[f0 + i];
+                dst[i] = const_cast<uint8_t *>(a.rgb);
+                len[i] = (size_t)a.W * a.H * a.C;
+            } else {
+                src[i] = pass == 1 ? static_cast<const void *>(a.labels) : static_cast<const void *>(a.centres_out);
+                dst[i] = pass == 1 ? static_cast<void *>(host_labels[f0 + i]) : static_cast<void *>(host_centres[f0 + i]);
+                len[i] = pass == 1 ? sizeof(int32_t) * a.W * a.H : sizeof(float) * 6 * (size_t)a.ns_c * a.ns_r;
+                if (!dst[i]) src[i] = nullptr;
+            }
+        }
+        return copy_runs(m, src, dst, len, pass == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, t);
+    };
+    cudaError_t e = cudaSuccess;
+    if (split_groups(b)) {
+        // Frame groups: each group's stream copies its frames in, segments
+        // them and copies its results out, so one group's copies overlap
+        // the other groups' kernels within the call.
+        long long n_launch = 0;
+        std::string why;
+        e = cudaEventRecord(b->ev_fork, s);
+        for (int g = 1; g < b->groups && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(b->gstream[g - 1], b->ev_fork, 0);
+        for (int g = 0; g < b->groups && e == cudaSuccess; ++g) {
+            cudaStream_t t = g == 0 ? s : b->gstream[g - 1];
+            const int f0 = b->group_first[g], f1 = b->group_first[g + 1];
+            e = copy_frames(f0, f1, 0, t);
+            if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("image copy: ") + cudaGetErrorString(e));
+            e = enqueue_span(b, span_of(b, g), t, false, n_launch, why);
+            if (e != cudaSuccess)
+                return bfail(b, SLIC_ERR_CUDA, why.empty() ? std::string("kernel launch: ") + cudaGetErrorString(e) : why);
+            for (int pass = 1; pass <= 2 && e == cudaSuccess; ++pass) e = copy_frames(f0, f1, pass, t);
+            if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
+        }
+        for (int g = 1; g < b->groups && e == cudaSuccess; ++g) {
+            e = cudaEventRecord(b->ev_join[g - 1], b->gstream[g - 1]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join[g - 1], 0);
+        }
+        if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("stream join: ") + cudaGetErrorString(e));
+        b->launches += n_launch;
+        return SLIC_OK;
     }
-    cudaError_t e = copy_runs(n, src, dst, len, cudaMemcpyHostToDevice, s);
+    e = copy_frames(0, n, 0, s);
     if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("image copy: ") + cudaGetErrorString(e));
     const slic_status st = slic_batch_segment(b, stream);
     if (st != SLIC_OK) return st;
-    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
-        int32_t *const *hl = host_labels;
-        float *const *hc = host_centres;
-        if (pass == 0 && !hl) continue;
-        if (pass == 1 && !hc) continue;
-        for (int f = 0; f < n; ++f) {
-            const FrameArgs &a = b->frames[f];
-            src[f] = pass == 0 ? static_cast<const void *>(a.labels) : static_cast<const void *>(a.centres_out);
-            dst[f] = pass == 0 ? static_cast<void *>(hl[f]) : static_cast<void *>(hc[f]);
-            len[f] = pass == 0 ? sizeof(int32_t) * a.W * a.H : sizeof(float) * 6 * (size_t)a.ns_c * a.ns_r;
-            if (!dst[f]) src[f] = nullptr;
-        }
-        e = copy_runs(n, src, dst, len, cudaMemcpyDeviceToHost, s);
-    }
+    for (int pass = 1; pass <= 2 && e == cudaSuccess; ++pass) e = copy_frames(0, n, pass, s);
     if (e != cudaSuccess) return bfail(b, SLIC_ERR_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
     return SLIC_OK;
 }

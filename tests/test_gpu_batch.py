@@ -414,12 +414,16 @@ def test_frame_groups_are_bit_exact(slic_gpu):
     bs.status()
     for i in range(len(frames)):
         assert torch.equal(bs.labels[i], want_l[i]), i
-    # host buffers in and out
+    # host buffers in and out (each group's stream copies its own frames in
+    # and its results out); one frame's label copy skipped
     h_img = [torch.from_numpy(np.ascontiguousarray(h)).pin_memory() for h in host]
-    h_lab = [torch.empty(t.shape, dtype=torch.int32).pin_memory() for t in want_l]
-    bs.segment_host(h_img, h_lab, None, stream=stream)
+    h_lab = [torch.full(t.shape, -9, dtype=torch.int32).pin_memory() for t in want_l]
+    h_cen = [torch.empty(t.shape, dtype=torch.float32).pin_memory() for t in want_c]
+    bs.segment_host(h_img, h_lab[:3] + [None] + h_lab[4:], h_cen, stream=stream)
     stream.synchronize()
-    for a, b in zip(h_lab, want_l):
+    for i, (a, b) in enumerate(zip(h_lab, want_l)):
+        assert bool((a == -9).all()) if i == 3 else torch.equal(a, b.cpu()), i
+    for a, b in zip(h_cen, want_c):
         assert torch.equal(a, b.cpu())
     with pytest.raises(pkg.SlicError):
         bs.set_groups(5)
