@@ -712,7 +712,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_assign_batch(const FrameArgs *f
 
 namespace {
 
-constexpr size_t kStageFeatBytes = (size_t)3 * kTileH * kTileW * 4;  // 12288 (32x32 tile)
 __host__ __device__ constexpr size_t stage_feat_bytes(int th) { return (size_t)3 * th * kTileW * 4; }
 constexpr int kMaxStages = 4;
 constexpr int kAccSets = 2;    // accumulator sets in flight: one filled while the other is flushed
@@ -851,26 +850,6 @@ __device__ __forceinline__ void eval_keys(const ulonglong2 &la, const ulonglong2
     unpack2(D, d0, d1);
     k0 = __uint_as_float((__float_as_uint(d0) & ~15u) | t);
     k1 = __uint_as_float((__float_as_uint(d1) & ~15u) | t);
-}
-
-// The same, folded into the running minimum.
-__device__ __forceinline__ void eval_pair(const ulonglong2 &la, const ulonglong2 &bx, unsigned long long ddy2,
-                                          unsigned long long ww, unsigned long long l, unsigned long long a,
-                                          unsigned long long b, unsigned long long x, unsigned t, float &bk0,
-                                          float &bk1) {
-    const unsigned long long dl = sub2(la.x, l), da = sub2(la.y, a), db = sub2(bx.x, b);
-    const unsigned long long s = fma2(dl, dl, fma2(da, da, mul2(db, db)));
-    const unsigned long long dx = sub2(bx.y, x);
-    const unsigned long long q = fma2(dx, dx, ddy2);
-    float s0, s1, q0, q1;
-    unpack2(s, s0, s1);
-    unpack2(q, q0, q1);
-    const unsigned long long D = fma2(ww, pack2(fsqrt_approx(q0), fsqrt_approx(q1)),
-                                      pack2(fsqrt_approx(s0), fsqrt_approx(s1)));
-    float d0, d1;
-    unpack2(D, d0, d1);
-    bk0 = fmin_nan(bk0, __uint_as_float((__float_as_uint(d0) & ~15u) | t));
-    bk1 = fmin_nan(bk1, __uint_as_float((__float_as_uint(d1) & ~15u) | t));
 }
 
 // Tile header written by the tile's producer next to its stage: the tile's
