@@ -921,10 +921,11 @@ __device__ __forceinline__ void issue_tile(const FrameArgs &a, const TileGeom &g
                 g.wy0 + 1, bar);
 }
 
-// Add tile j's private sums (the 8 copies of accumulator set j % 2, one per
-// 128 pixels) to the frame's global sums and clear them. One of the NW warps
-// per tile does it (warp j % NW, so the duty rotates), a lane per window cell reading the cell's
-// four words of every copy as one 16-byte load. The flushing warp waits
+// Add tile j's private sums (the NCOPY copies of accumulator set j % 2, one
+// per 128 pixels) to the frame's global sums and clear them. One of the NW
+// warps per tile does it (warp j % NW, so the duty rotates), a lane per
+// window cell reading the cell's four words of every copy as one 16-byte
+// load. The flushing warp waits
 // until every warp has filled the set and reports it free afterwards; the
 // others return at once. False when the wait timed out.
 template <int NW, int NCOPY, bool MULTI>
@@ -948,9 +949,9 @@ __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, const MultiHdr *
         unsigned xs = 0, ys = 0, n = 0;
 #pragma unroll
         for (int q = 0; q < NCOPY; ++q) {
-            // copy q: rows 4q .. 4q+3 of the tile; its y field counts from the
-            // tile's first row (32-row tiles) or from 4q (64-row tiles, whose
-            // offsets would not fit the 12-bit field)
+            // copy q: its y field counts from the tile's first row (32-row
+            // tiles) or from its warp's first row, 8 (q / 2) (64-row tiles,
+            // whose offsets would not fit the 12-bit field)
             uint4 *p = reinterpret_cast<uint4 *>(ws + (size_t)q * win_max * 4 + idx);
             const uint4 v = *p;
             *p = make_uint4(0u, 0u, 0u, 0u);
@@ -960,7 +961,7 @@ __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, const MultiHdr *
             a += (int)(v.y - bias);
             b += (int)(v.z - bias);
             xs += v.w & 0xFFFu;
-            ys += ((v.w >> 12) & 0xFFFu) + (NCOPY > kWarps ? 4u * (unsigned)q * (v.w >> 24) : 0u);
+            ys += ((v.w >> 12) & 0xFFFu) + (NCOPY > kWarps ? 8u * (unsigned)(q >> 1) * (v.w >> 24) : 0u);
             n += v.w >> 24;
         }
         if (n != 0) {
@@ -1597,10 +1598,17 @@ __device__ __forceinline__ void assign_pipe_body(const FrameArgs *frames, int n_
             }
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
-                // copy q = warp * ROWS + r holds rows 4q .. 4q+3 (see flush_tile for y)
-                unsigned *my = wacc0 + (size_t)set * acc_words + (size_t)(warp * ROWS + r) * win_max * 4;
+                // One row group: copy q = warp holds rows 4q .. 4q+3. Two row
+                // groups: copy q = 2 warp + (lane >> 4), the lanes of one half
+                // of the warp in both groups (rows 8 warp + {2h, 2h+1, 2h+4,
+                // 2h+5}, h = q % 2), so an instruction's atomics go to two
+                // copies and fewer lanes meet on one address. y counts from the
+                // tile's first row (32-row tiles) or from the warp's first row
+                // (64-row tiles; see flush_tile).
+                const int q = ROWS == 2 ? 2 * warp + (lane >> 4) : warp;
+                unsigned *my = wacc0 + (size_t)set * acc_words + (size_t)q * win_max * 4;
                 unsigned v[kPPT][4];
-                const unsigned yo = TH == 64 ? (unsigned)(lane >> 3) : (unsigned)(ly0 + 4 * r);
+                const unsigned yo = TH == 64 ? (unsigned)((lane >> 3) + 4 * r) : (unsigned)(ly0 + 4 * r);
                 const unsigned xyn = (unsigned)lx + (yo << 12) + (1u << 24);
 #pragma unroll
                 for (int j = 0; j < kPPT; j += 2) {
