@@ -949,53 +949,35 @@ __device__ __forceinline__ bool flush_tile(const TileGeom *hdr, const MultiHdr *
     long long *const acc = g.acc;
     unsigned *const ws = wacc0 + (size_t)set * acc_words;
     const int n_cells = wnx * wny;
-    // A cell holds at most S^2 pixels, so for S <= 22 fewer than 512 of the
-    // tile's pixels are in one cell, and the colour words summed mod 2^32
-    // over all copies, minus n * kFixBias, are the cell's exact signed sums
-    // (at most 2^22 per pixel); larger cells remove the bias copy by copy
-    // and sum in 64 bits.
-    const bool small_cells = g.S <= 22;
     for (int cell = lane; cell < n_cells; cell += 32) {
         const int qy = (int)__umulhi((unsigned)cell, wnx_mul), qx = cell - qy * wnx;
         const int idx = (qy * bw + qx) * 4;
         long long l = 0, a = 0, b = 0;
         unsigned xs = 0, ys = 0, n = 0;
-        // copy q: its y field counts from the tile's first row (32-row tiles)
-        // or from its warp's first row, 8 (q / 2) (64-row tiles, whose
-        // offsets would not fit the 12-bit field)
-        if (small_cells) {
-            unsigned l32 = 0, a32 = 0, b32 = 0;
+        // Copies two at a time: the colour words carry kFixBias per pixel
+        // (fix_round2_biased), so a pair's words summed mod 2^32 minus its
+        // pixel count times kFixBias is the pair's signed sum, exact in 32
+        // bits (at most 256 pixels of at most 2^22 each); one 64-bit add per
+        // pair and channel. Copy q's y field counts from the tile's first row
+        // (32-row tiles) or from its warp's first row, 8 (q / 2) (64-row
+        // tiles, whose offsets would not fit the 12-bit field).
+        static_assert(NCOPY % 2 == 0, "copies are summed in pairs");
 #pragma unroll
-            for (int q = 0; q < NCOPY; ++q) {
-                uint4 *p = reinterpret_cast<uint4 *>(ws + (size_t)q * win_max * 4 + idx);
-                const uint4 v = *p;
-                *p = make_uint4(0u, 0u, 0u, 0u);
-                l32 += v.x;
-                a32 += v.y;
-                b32 += v.z;
-                xs += v.w & 0xFFFu;
-                ys += ((v.w >> 12) & 0xFFFu) + (NCOPY > kWarps ? 8u * (unsigned)(q >> 1) * (v.w >> 24) : 0u);
-                n += v.w >> 24;
-            }
-            const unsigned bias = n * kFixBias;
-            l = (int)(l32 - bias);
-            a = (int)(a32 - bias);
-            b = (int)(b32 - bias);
-        } else {
-#pragma unroll
-            for (int q = 0; q < NCOPY; ++q) {
-                uint4 *p = reinterpret_cast<uint4 *>(ws + (size_t)q * win_max * 4 + idx);
-                const uint4 v = *p;
-                *p = make_uint4(0u, 0u, 0u, 0u);
-                // the colour words carry kFixBias per pixel (fix_round2_biased)
-                const unsigned bias = (v.w >> 24) * kFixBias;
-                l += (int)(v.x - bias);
-                a += (int)(v.y - bias);
-                b += (int)(v.z - bias);
-                xs += v.w & 0xFFFu;
-                ys += ((v.w >> 12) & 0xFFFu) + (NCOPY > kWarps ? 8u * (unsigned)(q >> 1) * (v.w >> 24) : 0u);
-                n += v.w >> 24;
-            }
+        for (int q = 0; q < NCOPY; q += 2) {
+            uint4 *p0 = reinterpret_cast<uint4 *>(ws + (size_t)q * win_max * 4 + idx);
+            uint4 *p1 = reinterpret_cast<uint4 *>(ws + (size_t)(q + 1) * win_max * 4 + idx);
+            const uint4 v0 = *p0, v1 = *p1;
+            *p0 = make_uint4(0u, 0u, 0u, 0u);
+            *p1 = make_uint4(0u, 0u, 0u, 0u);
+            const unsigned n0 = v0.w >> 24, n1 = v1.w >> 24;
+            const unsigned bias = (n0 + n1) * kFixBias;
+            l += (int)(v0.x + v1.x - bias);
+            a += (int)(v0.y + v1.y - bias);
+            b += (int)(v0.z + v1.z - bias);
+            xs += (v0.w & 0xFFFu) + (v1.w & 0xFFFu);
+            ys += ((v0.w >> 12) & 0xFFFu) + ((v1.w >> 12) & 0xFFFu) +
+                  (NCOPY > kWarps ? 8u * (unsigned)(q >> 1) * (n0 + n1) : 0u);
+            n += n0 + n1;
         }
         if (n != 0) {
             unsigned long long *gs =

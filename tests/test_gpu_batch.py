@@ -175,6 +175,48 @@ def test_two_row_groups_are_bit_exact(slic_gpu, stages):
             assert torch.equal(centres[i], c1)
 
 
+def test_large_clusters_sum_exactly(slic_gpu):
+    """One centre wins far more pixels of a tile than its cell holds. The
+    image is black but for a white 48x48 square, the 3x3 cells around one
+    centre; the other eight centres in the square start on black dots, and m
+    is small, so every white pixel picks the white centre in every pass.
+    About 1000 pixels at L = 100 then go into one window cell of one tile,
+    more than a 32-bit sum of their fixed-point colours holds
+    (1000 x 100 x 2^15 > 2^31); the pipelined kernel's private copies and
+    flush must still give the single-frame results bit for bit, in every
+    tile shape."""
+    import torch
+    pkg = slic_gpu
+    W, H, S = 256, 128, 16
+    ns_c = -(-W // S)
+    img = np.zeros((H, W, 3), np.uint8)
+    img[2 * S:5 * S, 4 * S:7 * S] = 255  # cells (2..4, 4..6)
+    white = 3 * ns_c + 5
+    cen = oracle.init_centres(oracle.convert(img), S)
+    for r in (2, 3, 4):
+        for c in (4, 5, 6):
+            if r * ns_c + c != white:
+                x, y = (int(np.floor(v)) for v in cen[r * ns_c + c, 3:5])
+                img[y - 1:y + 2, x - 1:x + 2] = 0
+    d_img = _cuda(img)
+    seg = pkg.Segmenter(W, H, S=S, m=1.0, iterations=3, enforce_connectivity=False)
+    l1, c1 = seg.segment(d_img)
+    torch.cuda.synchronize()
+    lab = l1.cpu().numpy()
+    # the 32x32 tile at (64, 32) is white but for three 3x3 dots
+    assert np.sum(lab[2 * S:4 * S, 4 * S:6 * S] == white) >= 990
+    assert c1.cpu().numpy()[white, 0] > 99.0
+    bs = pkg.BatchSegmenter([dict(width=W, height=H, S=S, m=1.0)], iterations=3, enforce_connectivity=False)
+    bs.bind([d_img])
+    for cps, stages, rows, th in ((0, 3, 1, 32), (0, 3, 2, 32), (0, 3, 2, 64)):
+        bs.set_tuning(cps, stages, rows, th)
+        labels, centres = bs.segment()
+        bs.status()
+        assert bs.info[4] == rows and bs.info[5] == th
+        assert torch.equal(labels[0], l1)
+        assert torch.equal(centres[0], c1)
+
+
 def test_batch_errors(slic_gpu):
     pkg = slic_gpu
     from paper_1509_04232_gb300 import _binding
