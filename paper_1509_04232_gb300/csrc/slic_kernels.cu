@@ -2203,11 +2203,19 @@ __device__ __forceinline__ int32_t conn_majority(int32_t own, int32_t l, int32_t
     const int32_t res = el ? l : (eu ? u : (er ? r : fv));
     return res >= 0 ? res : own;
 }
+// The same where all four neighbours are labels (no sentinel): the first
+// valid one is the left one, and the result is always a label.
+__device__ __forceinline__ int32_t conn_majority_inner(int32_t l, int32_t u, int32_t r, int32_t d) {
+    const bool el = l == u || l == r || l == d, eu = u == r || u == d, er = r == d;
+    return el ? l : (eu ? u : (er ? r : l));
+}
 
 // One pass of the majority rule at row y for the lane's 4 pixels, from the
 // rows above, at and below y (left/right neighbours across lanes). A pixel
 // keeps its label when a neighbour shares it (the common case); the
-// majority is evaluated only when some pixel of the warp needs it.
+// majority is evaluated only when some pixel of the warp needs it. INNER:
+// every neighbour the warp's results depend on is inside the image.
+template <bool INNER>
 __device__ __forceinline__ int4 conn_rule4(const int4 &up, const int4 &c, const int4 &dn) {
     const int32_t left = __shfl_up_sync(0xffffffffu, c.w, 1), right = __shfl_down_sync(0xffffffffu, c.x, 1);
     const int32_t cc[4] = {c.x, c.y, c.z, c.w}, uu[4] = {up.x, up.y, up.z, up.w}, dd[4] = {dn.x, dn.y, dn.z, dn.w};
@@ -2224,7 +2232,7 @@ __device__ __forceinline__ int4 conn_rule4(const int4 &up, const int4 &c, const 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int32_t l = j > 0 ? cc[j - 1] : left, r = j < 3 ? cc[j + 1] : right;
-            if (need[j]) res[j] = conn_majority(cc[j], l, uu[j], r, dd[j]);
+            if (need[j]) res[j] = INNER ? conn_majority_inner(l, uu[j], r, dd[j]) : conn_majority(cc[j], l, uu[j], r, dd[j]);
         }
     }
     return make_int4(res[0], res[1], res[2], res[3]);
@@ -2248,14 +2256,25 @@ __global__ void __launch_bounds__(256, 4) k_connectivity2_batch(const FrameArgs 
         int4 a_m2 = conn_load_row(in, W, H, ry0 - 2, x0, vec), a_m1 = conn_load_row(in, W, H, ry0 - 1, x0, vec);
         int4 a0 = conn_load_row(in, W, H, ry0, x0, vec), a1 = conn_load_row(in, W, H, ry0 + 1, x0, vec);
         int4 a2 = conn_load_row(in, W, H, ry0 + 2, x0, vec);
-        int4 l_m1 = conn_mask_row(conn_rule4(a_m2, a_m1, a0), W, H, ry0 - 1, x0, edge_lane);
-        int4 l0 = conn_mask_row(conn_rule4(a_m1, a0, a1), W, H, ry0, x0, edge_lane);
+        int4 l_m1 = conn_mask_row(conn_rule4<false>(a_m2, a_m1, a0), W, H, ry0 - 1, x0, edge_lane);
+        int4 l0 = conn_mask_row(conn_rule4<false>(a_m1, a0, a1), W, H, ry0, x0, edge_lane);
+        // Columns sx - 4 .. sx + 123 all inside the image: no lane holds a
+        // sentinel column, so rows 1 .. H - 3 take the rule without them.
+        const bool inner_cols = sx >= 4 && sx + 124 <= W;
         const bool writer = lane >= 1 && lane <= 30;
         const bool out_vec = vec && a.labels_vec && x0 >= 0 && x0 + 3 < W;
         for (int q = ry0; q < ry1; ++q) {
             const int4 a3 = conn_load_row(in, W, H, q + 3, x0, vec);  // one row ahead of its use
-            const int4 l1 = conn_mask_row(conn_rule4(a0, a1, a2), W, H, q + 1, x0, edge_lane);
-            const int4 o = conn_rule4(l_m1, l0, l1);
+            int4 l1, o;
+            if (inner_cols && q >= 1 && q + 2 < H) {
+                // input rows q .. q + 2 and first-pass rows q - 1 .. q + 1
+                // are all inside the image
+                l1 = conn_rule4<true>(a0, a1, a2);
+                o = conn_rule4<true>(l_m1, l0, l1);
+            } else {
+                l1 = conn_mask_row(conn_rule4<false>(a0, a1, a2), W, H, q + 1, x0, edge_lane);
+                o = conn_rule4<false>(l_m1, l0, l1);
+            }
             if (writer) {
                 int32_t *out = a.labels + (size_t)q * W;
                 if (out_vec) {
